@@ -1,0 +1,313 @@
+"""The condensed QP and the solvers used to check the method, FP64 (oracle; test infrastructure only).
+
+QP (Sec. III-B, Eq. condensed_matrices, with the 1/2 convention of
+``oracle.condense``):
+
+    min 1/2 U^T H U + g^T U   s.t.   lo <= U <= hi,   C U <= d.
+
+Written with A~ = [I; C], l = [lo; -inf], h = [hi; d] as  l <= A~ U <= h.
+H is positive definite because Rbar is (R = 0.01 I), so the optimal U is unique;
+the multipliers may not be when the active rows are linearly dependent (LICQ,
+Sec. I).
+
+Contents:
+* ``kkt_certificate``   stationarity, feasibility, dual signs, complementarity;
+* ``solve_exact``       the definition of the optimum: a primal-dual interior
+                        point method to a tight KKT residual, then the equality-
+                        constrained solve on the active set it identifies;
+* ``admm``              the ADMM recurrence the GPU path runs (fixed rho,
+                        no relaxation, no scaling);
+* ``polish``            equality-constrained re-solve on the active set guessed
+                        from an ADMM iterate;
+* ``brute_force``       every active set, for tiny problems;
+* ``uncondensed``       the QP in (x, u) with the dynamics as equalities
+                        (Eq. ocp_dynamics), for tiny problems.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+def stack_rows(lo, hi, C, d):
+    """A~ = [I; C], l = [lo; -inf], h = [hi; d]."""
+    n = lo.size
+    C = np.zeros((0, n)) if C is None else np.asarray(C, np.float64)
+    d = np.zeros(0) if d is None else np.asarray(d, np.float64)
+    At = np.vstack([np.eye(n), C])
+    l = np.concatenate([np.asarray(lo, np.float64), np.full(C.shape[0], -np.inf)])
+    h = np.concatenate([np.asarray(hi, np.float64), d])
+    return At, l, h
+
+
+def kkt_certificate(H, g, At, l, h, U, y):
+    """Residuals of the KKT conditions of min 1/2 U'HU + g'U s.t. l <= A~U <= h.
+
+    y_r > 0 pushes against the upper bound, y_r < 0 against the lower bound.
+    """
+    a = At @ U
+    stat = np.abs(H @ U + g + At.T @ y).max() if U.size else 0.0
+    prim = max(0.0, np.max(a - h, initial=0.0), np.max(l - a, initial=0.0))
+    # a row without an upper bound may not push up (y <= 0), without a lower bound not down
+    dual = max(np.max(np.where(np.isinf(h), np.maximum(y, 0.0), 0.0), initial=0.0),
+               np.max(np.where(np.isinf(l), np.maximum(-y, 0.0), 0.0), initial=0.0))
+    up = np.maximum(y, 0.0) * np.abs(np.where(np.isinf(h), 0.0, h - a))
+    lo_ = np.maximum(-y, 0.0) * np.abs(np.where(np.isinf(l), 0.0, a - l))
+    comp = max(np.max(up, initial=0.0), np.max(lo_, initial=0.0))
+    return dict(stationarity=float(stat), primal=float(prim), dual=float(dual),
+                complementarity=float(comp))
+
+
+def _ineq_form(At, l, h):
+    """G U <= hh with one row per finite bound (upper rows +a, lower rows -a)."""
+    rows, rhs, owner, sign = [], [], [], []
+    for r in range(At.shape[0]):
+        if np.isfinite(h[r]):
+            rows.append(At[r]); rhs.append(h[r]); owner.append(r); sign.append(1.0)
+        if np.isfinite(l[r]):
+            rows.append(-At[r]); rhs.append(-l[r]); owner.append(r); sign.append(-1.0)
+    n = At.shape[1]
+    G = np.array(rows) if rows else np.zeros((0, n))
+    return G, np.array(rhs), np.array(owner, int), np.array(sign)
+
+
+def ipm(H, g, G, hh, tol=1e-13, max_iter=200):
+    """Mehrotra predictor-corrector primal-dual interior point for min 1/2x'Hx+g'x, Gx<=hh."""
+    n, m = H.shape[0], G.shape[0]
+    x = np.zeros(n)
+    if m == 0:
+        return np.linalg.solve(H, -g), np.zeros(0), np.zeros(0), 0
+    s = np.maximum(hh - G @ x, 1.0)
+    z = np.ones(m)
+    scale = max(1.0, np.abs(g).max(), np.abs(hh).max())
+    for it in range(max_iter):
+        rd = H @ x + g + G.T @ z
+        rp = G @ x + s - hh
+        mu = s @ z / m
+        if max(np.abs(rd).max(), np.abs(rp).max()) <= tol * scale and mu <= tol * scale:
+            return x, s, z, it
+
+        def solve(rc):
+            Wd = z / s
+            Kmat = H + G.T @ (Wd[:, None] * G)
+            rhs = -rd - G.T @ (Wd * rp - rc / s)
+            dx = np.linalg.solve(Kmat, rhs)
+            dz = Wd * (G @ dx + rp) - rc / s
+            ds = -(rc + s * dz) / z
+            return dx, ds, dz
+
+        def step_len(v, dv):
+            neg = dv < 0
+            return min(1.0, np.min(-v[neg] / dv[neg], initial=np.inf))
+
+        try:
+            dxa, dsa, dza = solve(s * z)
+        except np.linalg.LinAlgError:
+            return x, s, z, it            # the Newton matrix lost rank at a converged point
+        aa = min(step_len(s, dsa), step_len(z, dza))
+        mu_aff = (s + aa * dsa) @ (z + aa * dza) / m
+        sigma = (mu_aff / mu) ** 3
+        dx, ds, dz = solve(s * z + dsa * dza - sigma * mu)
+        a = 0.99 * min(step_len(s, ds), step_len(z, dz))
+        x, s, z = x + a * dx, s + a * ds, z + a * dz
+    return x, s, z, max_iter
+
+
+def equality_solve(H, g, At, l, h, upper, lower):
+    """Minimise 1/2U'HU+g'U with the rows in `upper` held at h and `lower` at l.
+
+    Returns (U, y) with y the full multiplier vector (zero off the active set),
+    or None if the KKT matrix is singular.
+    """
+    n = H.shape[0]
+    act = list(upper) + list(lower)
+    if not act:
+        return np.linalg.solve(H, -g), np.zeros(At.shape[0])
+    Ga = At[act]
+    ba = np.concatenate([h[list(upper)], l[list(lower)]])
+    K = np.block([[H, Ga.T], [Ga, np.zeros((len(act), len(act)))]])
+    rhs = np.concatenate([-g, ba])
+    try:
+        sol = np.linalg.solve(K, rhs)
+    except np.linalg.LinAlgError:
+        return None
+    if not np.all(np.isfinite(sol)):
+        return None
+    U = sol[:n]
+    y = np.zeros(At.shape[0])
+    y[act] = sol[n:]
+    return U, y
+
+
+def solve_exact(H, g, lo, hi, C=None, d=None):
+    """The optimum U* of the condensed QP and one valid multiplier vector.
+
+    Interior point to a tight residual, then the active set it identifies
+    (multiplier larger than slack) is re-solved as an equality QP; the re-solve
+    is kept when its KKT certificate is at least as good.
+    """
+    H = np.asarray(H, np.float64)
+    g = np.asarray(g, np.float64)
+    At, l, h = stack_rows(np.asarray(lo, np.float64), np.asarray(hi, np.float64), C, d)
+    G, hh, owner, sign = _ineq_form(At, l, h)
+    x, s, z, it = ipm(H, g, G, hh)
+    y = np.zeros(At.shape[0])
+    np.add.at(y, owner, sign * z)
+    best = (x, y)
+    cert = kkt_certificate(H, g, At, l, h, x, y)
+    best_err = max(cert.values())
+    act = z > s
+    upper = sorted({int(owner[k]) for k in np.nonzero(act & (sign > 0))[0]})
+    lower = sorted({int(owner[k]) for k in np.nonzero(act & (sign < 0))[0]})
+    res = equality_solve(H, g, At, l, h, upper, lower)
+    if res is not None:
+        c2 = kkt_certificate(H, g, At, l, h, *res)
+        if max(c2.values()) <= best_err:
+            best = res
+            best_err = max(c2.values())
+    return best[0], best[1], dict(ipm_iters=it, kkt=best_err)
+
+
+def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None, y0=None):
+    """ADMM on l <= A~U <= h (fixed rho, alpha = 1, sigma = 0, unscaled residuals).
+
+        P     = H + rho A~'A~                      (factored once)
+        z^0   = Pi(A~ U^0),  y^0 = 0 unless given
+        U     = P^{-1} (A~'(rho z - y) - g)
+        a     = A~ U
+        z     = Pi_[l,h](a + y / rho)
+        y     = y + rho (a - z)
+        r_p   = |a - z|_inf,   r_d = |H U + g + A~'y|_inf;  stop when both <= tol.
+
+    Returns U, z, y, iterations (number of U updates), r_p, r_d, converged.
+    """
+    H = np.asarray(H, np.float64)
+    g = np.asarray(g, np.float64)
+    At, l, h = stack_rows(np.asarray(lo, np.float64), np.asarray(hi, np.float64), C, d)
+    n = H.shape[0]
+    P = H + rho * At.T @ At
+    L = np.linalg.cholesky(P)
+    U = np.zeros(n) if U0 is None else np.asarray(U0, np.float64).copy()
+    y = np.zeros(At.shape[0]) if y0 is None else np.asarray(y0, np.float64).copy()
+    z = np.clip(At @ U, l, h)
+    r_p = r_d = np.inf
+    it = 0
+    for it in range(1, max_iter + 1):
+        rhs = At.T @ (rho * z - y) - g
+        U = np.linalg.solve(L.T, np.linalg.solve(L, rhs))
+        a = At @ U
+        z = np.clip(a + y / rho, l, h)
+        y = y + rho * (a - z)
+        r_p = np.abs(a - z).max()
+        r_d = np.abs(H @ U + g + At.T @ y).max()
+        if r_p <= tol and r_d <= tol:
+            return U, z, y, it, r_p, r_d, True
+    return U, z, y, it, r_p, r_d, False
+
+
+def polish(H, g, lo, hi, C, d, U, z, y):
+    """Re-solve on the active set guessed from (z, y): lower if z-l < -y, upper if h-z < y.
+
+    Returns (U, y, accepted) where accepted means the re-solve is primal feasible,
+    has correctly signed multipliers and a KKT certificate no worse than the input.
+    """
+    At, l, h = stack_rows(np.asarray(lo, np.float64), np.asarray(hi, np.float64), C, d)
+    upper = [r for r in range(At.shape[0]) if np.isfinite(h[r]) and h[r] - z[r] < y[r]]
+    lower = [r for r in range(At.shape[0]) if np.isfinite(l[r]) and z[r] - l[r] < -y[r]]
+    res = equality_solve(H, g, At, l, h, upper, lower)
+    if res is None:
+        return U, y, False
+    c0 = kkt_certificate(H, g, At, l, h, U, y)
+    c1 = kkt_certificate(H, g, At, l, h, *res)
+    if max(c1.values()) <= max(c0.values()):
+        return res[0], res[1], True
+    return U, y, False
+
+
+def brute_force(H, g, lo, hi, C=None, d=None, tol=1e-9):
+    """Try every active set (box rows: free/lower/upper; half-spaces: free/active)."""
+    At, l, h = stack_rows(np.asarray(lo, np.float64), np.asarray(hi, np.float64), C, d)
+    m = At.shape[0]
+    choices = [((0, 1, 2) if np.isfinite(l[r]) else (0, 1)) for r in range(m)]
+    best = None
+    for pick in itertools.product(*choices):
+        upper = [r for r in range(m) if pick[r] == 1]
+        lower = [r for r in range(m) if pick[r] == 2]
+        res = equality_solve(H, g, At, l, h, upper, lower)
+        if res is None:
+            continue
+        cert = kkt_certificate(H, g, At, l, h, *res)
+        if max(cert.values()) <= tol:
+            if best is not None and np.abs(best[0] - res[0]).max() > 1e-8:
+                raise AssertionError("two distinct KKT points of a strictly convex QP")
+            best = res
+    return best
+
+
+def uncondensed(A, B, c, x0, Qdiag, Rdiag, x_ref, u_ref, lo, hi, Cx, dx, tol=1e-9):
+    """Solve the QP in w = (x_0..x_N, u_0..u_{N-1}) with the dynamics as equalities.
+
+    Eq. ocp_cost_norm / ocp_dynamics / ocp_initial_state with the tracking cost of
+    Eq. linear_gnn_mpc_ocp_explicit (times 1/2).  Inequalities (input box and
+    position half-spaces of stages 1..N) are handled by brute force over their
+    active sets, each case a dense KKT solve.  Returns U.
+    """
+    N, nx, nu = B.shape
+    M = nx // 6
+    nX = (N + 1) * nx
+    nw = nX + N * nu
+    P = np.zeros((nw, nw))
+    q = np.zeros(nw)
+    Qd = np.asarray(Qdiag, np.float64).reshape(-1)
+    P[:nX, :nX] = np.diag(Qd)
+    q[:nX] = -Qd * np.asarray(x_ref, np.float64).reshape(-1)
+    Rd = np.asarray(Rdiag, np.float64).reshape(-1)
+    P[nX:, nX:] = np.diag(Rd)
+    q[nX:] = -Rd * np.asarray(u_ref, np.float64).reshape(-1)
+    Eq = np.zeros(((N + 1) * nx, nw))
+    be = np.zeros((N + 1) * nx)
+    Eq[:nx, :nx] = np.eye(nx)
+    be[:nx] = x0
+    for k in range(N):
+        r = (k + 1) * nx
+        Eq[r:r + nx, (k + 1) * nx:(k + 2) * nx] = np.eye(nx)
+        Eq[r:r + nx, k * nx:(k + 1) * nx] = -A[k]
+        Eq[r:r + nx, nX + k * nu:nX + (k + 1) * nu] = -B[k]
+        be[r:r + nx] = c[k]
+    rows, lows, highs = [], [], []
+    for k in range(N):
+        for a in range(nu):
+            e = np.zeros(nw); e[nX + k * nu + a] = 1.0
+            rows.append(e); lows.append(lo[k, a]); highs.append(hi[k, a])
+    n_c = 0 if Cx is None else Cx.shape[2]
+    for k in range(1, N + 1):
+        for i in range(M):
+            for s in range(n_c):
+                e = np.zeros(nw)
+                e[k * nx + 6 * i:k * nx + 6 * i + 3] = Cx[k - 1, i, s]
+                rows.append(e); lows.append(-np.inf); highs.append(dx[k - 1, i, s])
+    G = np.array(rows)
+    lw, hw = np.array(lows), np.array(highs)
+    m = G.shape[0]
+    choices = [((0, 1, 2) if np.isfinite(lw[r]) else (0, 1)) for r in range(m)]
+    for pick in itertools.product(*choices):
+        act = [r for r in range(m) if pick[r] != 0]
+        bnd = np.array([hw[r] if pick[r] == 1 else lw[r] for r in act])
+        Ga = np.vstack([Eq] + ([G[act]] if act else []))
+        ba = np.concatenate([be, bnd]) if act else be
+        K = np.block([[P, Ga.T], [Ga, np.zeros((Ga.shape[0], Ga.shape[0]))]])
+        try:
+            sol = np.linalg.solve(K, np.concatenate([-q, ba]))
+        except np.linalg.LinAlgError:
+            continue
+        w = sol[:nw]
+        lam = sol[nw + Eq.shape[0]:]
+        a = G @ w
+        if np.any(a > hw + tol) or np.any(a < lw - tol):
+            continue
+        sgn = np.array([1.0 if pick[r] == 1 else -1.0 for r in act])
+        if act and np.any(sgn * lam < -tol):
+            continue
+        return w[nX:].reshape(N, nu)
+    return None

@@ -1,0 +1,112 @@
+"""Pins of the oracle's QP solvers against brute force, the uncondensed QP and closed forms.  No GPU."""
+import numpy as np
+import pytest
+
+from oracle import condense as cd
+from oracle import qp
+from oracle import rti
+from synth import small_chain
+
+from test_oracle_condense import random_ltv
+
+
+def random_qp(n, m, seed, active=True):
+    rng = np.random.default_rng(seed)
+    L = rng.normal(0, 1, (n, n))
+    H = L @ L.T + 0.1 * np.eye(n)
+    g = rng.normal(0, 3.0 if active else 0.1, n)
+    lo = -np.ones(n)
+    hi = np.ones(n)
+    C = rng.normal(0, 1, (m, n))
+    d = rng.uniform(-0.2, 0.5, m) if active else np.full(m, 100.0)
+    return H, g, lo, hi, C, d
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_exact_solution_equals_brute_force_active_sets(seed):
+    H, g, lo, hi, C, d = random_qp(4, 3, seed)
+    U, y, info = qp.solve_exact(H, g, lo, hi, C, d)
+    bf = qp.brute_force(H, g, lo, hi, C, d)
+    assert bf is not None
+    assert np.abs(U - bf[0]).max() <= 1e-10
+    At, l, h = qp.stack_rows(lo, hi, C, d)
+    cert = qp.kkt_certificate(H, g, At, l, h, U, y)
+    assert max(cert.values()) <= 1e-9, cert
+
+
+def test_unconstrained_closed_form():
+    """Loose bounds: the optimum is U = -H^{-1} g."""
+    H, g, lo, hi, C, d = random_qp(6, 4, 1, active=False)
+    U, _, _ = qp.solve_exact(H, g, lo * 1e3, hi * 1e3, C, d)
+    assert np.allclose(U, np.linalg.solve(H, -g), atol=1e-11)
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_condensed_equals_uncondensed_qp(seed):
+    """The condensed QP's U* equals the (x, u) QP's U* with the dynamics as equalities (Sec. III-B)."""
+    M, N, nu = 2, 3, 2
+    A, B, c, x0, Qd, Rd, xr, ur, Cx, dx, nbh = random_ltv(M, N, nu, 1, seed, n_c=1, scale=0.3)
+    B *= 0.5
+    dx = dx + 2.0            # mostly loose half-spaces, some active
+    lo = -0.5 * np.ones((N, nu))
+    hi = 0.5 * np.ones((N, nu))
+    blocks = cd.blocks_from_dense(A, B, c, nbh)
+    H, g, Ct, dt, _, _ = cd.condense_recursive(blocks, x0, Qd, Rd, xr, ur, Cx, dx)
+    U, y, _ = qp.solve_exact(H, g, lo.reshape(-1), hi.reshape(-1), Ct, dt)
+    Uu = qp.uncondensed(A, B, c, x0, Qd, Rd, xr, ur, lo, hi, Cx, dx)
+    assert Uu is not None
+    assert np.abs(U - Uu.reshape(-1)).max() <= 1e-10
+    # the instance must exercise at least one active inequality
+    At, l, h = qp.stack_rows(lo.reshape(-1), hi.reshape(-1), Ct, dt)
+    assert np.any(np.abs(At @ U - h) < 1e-9) or np.any(np.abs(At @ U - l) < 1e-9)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_admm_converges_to_the_optimum(seed):
+    """The ADMM recurrence (fixed rho) reaches U* when run to a tight residual."""
+    H, g, lo, hi, C, d = random_qp(8, 6, 10 + seed)
+    U, y, _ = qp.solve_exact(H, g, lo, hi, C, d)
+    Ua, z, ya, it, rp, rd, ok = qp.admm(H, g, lo, hi, C, d, rho=1.0, tol=1e-11, max_iter=200000)
+    assert ok
+    assert np.abs(Ua - U).max() <= 1e-8
+
+
+def test_admm_dual_residual_identity():
+    """With an exact U-update, H U + g + A~'y = rho A~'(z_prev - z) at every iteration."""
+    H, g, lo, hi, C, d = random_qp(5, 4, 21)
+    At, l, h = qp.stack_rows(lo, hi, C, d)
+    rho = 0.7
+    P = H + rho * At.T @ At
+    U = np.zeros(5)
+    y = np.zeros(At.shape[0])
+    z = np.clip(At @ U, l, h)
+    for _ in range(30):
+        z_prev = z
+        U = np.linalg.solve(P, At.T @ (rho * z - y) - g)
+        a = At @ U
+        z = np.clip(a + y / rho, l, h)
+        y = y + rho * (a - z)
+        assert np.allclose(H @ U + g + At.T @ y, rho * At.T @ (z_prev - z), atol=1e-11)
+    # and the oracle's recurrence produces the same iterates
+    Ua, *_ = qp.admm(H, g, lo, hi, C, d, rho=rho, tol=0.0, max_iter=30)
+    assert np.allclose(Ua, U, atol=1e-12)
+
+
+def test_polish_recovers_the_optimum_from_a_loose_admm_iterate():
+    H, g, lo, hi, C, d = random_qp(8, 6, 31)
+    U, _, _ = qp.solve_exact(H, g, lo, hi, C, d)
+    Ua, z, ya, it, rp, rd, ok = qp.admm(H, g, lo, hi, C, d, rho=1.0, tol=1e-4, max_iter=100000)
+    assert ok and np.abs(Ua - U).max() > 1e-9
+    Up, yp, accepted = qp.polish(H, g, lo, hi, C, d, Ua, z, ya)
+    assert accepted
+    assert np.abs(Up - U).max() <= 1e-10
+
+
+def test_small_chain_optimum_certificate():
+    """Chain of 10 (N=10, nu=4): the oracle's U* carries an FP64 KKT certificate."""
+    wl = small_chain()
+    r = rti.rti_step(wl, return_all=True)
+    At, l, h = qp.stack_rows(wl.u_lo.reshape(-1).astype(float), wl.u_hi.reshape(-1).astype(float),
+                             r["Ct"] if r["Ct"].size else None, r["dt"] if r["dt"].size else None)
+    cert = qp.kkt_certificate(r["H"], r["g"], At, l, h, r["U"].reshape(-1), r["y"])
+    assert max(cert.values()) <= 1e-12
