@@ -1,0 +1,267 @@
+/*
+ * gm.h — C ABI of the B300 (sm_103a) GNN-MPC real-time-iteration library.
+ *
+ * One real-time iteration (Algorithm 1, one pass of its outer loop) of
+ * Graph Neural MPC: roll the GNN dynamics model out along the horizon,
+ * linearise it (Eq. linearized_dynamics), condense the states out with the
+ * per-node recursion of the Thm. 1 proof (Eq. sparse_gamma_i_xb,
+ * Eq. sparse_gamma_i_u, Eq. H, Eq. g and the stacked constraints), and solve
+ * the dense condensed QP (Eq. condensed_matrices) with ADMM.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns a gm_status.  On failure gm_last_error() returns
+ *   a message for the calling thread; outputs are then unspecified.
+ * - Handles are opaque.  gm_graph and gm_gnn live in host memory only.
+ *   gm_ctx lives in host memory and in a caller-provided device workspace;
+ *   the library itself never allocates device memory.
+ * - Array arguments of the compute calls are DEVICE pointers (float32 unless
+ *   noted), read or written in stream order on the given stream
+ *   (cudaStream_t passed as void*; NULL = legacy default stream).  Inputs
+ *   are only read during the call's kernels; outputs are caller-owned and
+ *   must not alias inputs.  The calls are asynchronous: results are valid
+ *   once the stream has reached them.
+ * - Indices are 0-based int32.  Node states are x^i = (p^i, v^i) in R^6
+ *   (position then velocity, Sec. V-A "Model").
+ * - Errors: GM_ERR_INVALID_ARG for bad sizes / NULL pointers / workspace too
+ *   small, GM_ERR_CUDA when a CUDA call fails (message holds the CUDA
+ *   error string).  There is no CPU fallback: without a CUDA device every
+ *   compute call returns GM_ERR_CUDA.
+ */
+#ifndef GM_H
+#define GM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gm_status;
+#define GM_OK                 0
+#define GM_ERR_INVALID_ARG    1
+#define GM_ERR_CUDA           2
+#define GM_ERR_WORKSPACE      3   /* workspace missing, too small or misaligned */
+#define GM_ERR_NOT_CONVERGED  4   /* ADMM hit max_iter; U holds the last iterate */
+#define GM_STALLED            5   /* warm-started ADMM stalled; cold restart used */
+#define GM_ERR_TIMEOUT        6   /* a bounded device-side wait gave up */
+#define GM_ERR_NUMERIC        7   /* NaN/Inf or a non-positive pivot */
+
+/* Precision forms of the step. */
+#define GM_PREC_FP32   0   /* every GNN, Jacobian, condensing and ADMM op in FP32 (SIMT);
+                              Cholesky of rho I + H (+ rho C~'C~) and the KKT check in FP64 */
+#define GM_PREC_MIXED  1   /* GNN MLPs and Jacobian products on tcgen05 tensor cores
+                              (BF16 operands, FP32 accumulate); the rest as GM_PREC_FP32 */
+
+typedef struct gm_graph gm_graph;
+typedef struct gm_gnn gm_gnn;
+typedef struct gm_ctx gm_ctx;
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* gm_last_error(void);
+/* Library version string. */
+const char* gm_version(void);
+
+/* ------------------------------------------------------------------------
+ * gm_graph_create — the interaction graph G = (V, E) (Sec. III-A) with the
+ * actuator attachment.
+ *   M          number of nodes (subsystems), M >= 1
+ *   E          number of directed edges, E >= 0
+ *   src, dst   HOST int32 [E]: edge k carries node src[k]'s state to node
+ *              dst[k] (e^{ij} with j = src, i = dst; N_i = { j : (j -> i) }).
+ *              Self-loops and duplicates are rejected (GM_ERR_INVALID_ARG).
+ *   nu         number of inputs, nu >= 1
+ *   act_node   HOST int32 [nu]: input a enters the node update of node
+ *              act_node[a] (node input [x^i, m^i * u], m^i one-hot).
+ * The arrays are copied; the caller keeps ownership.
+ * ---------------------------------------------------------------------- */
+gm_status gm_graph_create(int M, int E, const int32_t* src, const int32_t* dst,
+                          int nu, const int32_t* act_node, gm_graph** out);
+void gm_graph_destroy(gm_graph* g);
+
+/* ------------------------------------------------------------------------
+ * gm_gnn_load — the GNN dynamics model (Sec. V-A "Model", Eq. forward_dynamics)
+ * in encode-process-decode form with K message-passing steps:
+ *   h^0_i = MLP_ne([x^i, m^i u]),  e^0_ij = MLP_ee(x^i - x^j),
+ *   e^l_ij = e^{l-1}_ij + MLP_el([h^{l-1}_i, h^{l-1}_j, e^{l-1}_ij]),
+ *   h^l_i  = h^{l-1}_i + MLP_nl([h^{l-1}_i, sum_{j->i} e^l_ij]),
+ *   dv^i = MLP_d(h^K_i),  v+ = v + dv,  p+ = p + dt v+.
+ * Every MLP is Linear-ReLU-Linear with hidden width W; ReLU'(0) = 0.
+ *   desc.K >= 1, desc.W in {32, 64, 128}, desc.nu >= 1, desc.dt > 0.
+ *   blob   HOST float32 [n]: MLPs in the order node encoder (6+nu->W->W),
+ *          edge encoder (6->W->W), then per step edge update (3W->W->W) and
+ *          node update (2W->W->W), then decoder (W->W->3); inside each MLP
+ *          W1 [in][W] row-major, b1 [W], W2 [W][out] row-major, b2 [out].
+ *          n must equal that total (GM_ERR_INVALID_ARG otherwise).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int K;
+    int W;
+    int nu;
+    float dt;
+} gm_gnn_desc;
+
+gm_status gm_gnn_load(const gm_gnn_desc* desc, const float* blob, size_t n,
+                      gm_gnn** out);
+void gm_gnn_destroy(gm_gnn* m);
+
+/* ------------------------------------------------------------------------
+ * Settings of a context.
+ *   N          horizon (>= 1)
+ *   n_c        position half-spaces per node and stage (stages 1..N), >= 0
+ *   precision  GM_PREC_FP32 or GM_PREC_MIXED
+ *   rho        ADMM penalty (fixed, > 0)
+ *   tol        ADMM stop: |A~U - z|_inf <= tol and dual residual <= tol
+ *   max_iter   ADMM iteration cap (>= 1)
+ *   polish     1: after ADMM, re-solve the equality QP on the guessed active
+ *              set in FP64 and keep it if its KKT certificate is better
+ *   timeout_spins  cap on every device-side spin-wait (0 = default)
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int N;
+    int n_c;
+    int precision;
+    float rho;
+    float tol;
+    int max_iter;
+    int polish;
+    int timeout_spins;
+} gm_settings;
+
+/* Per-solve statistics, written to DEVICE memory by the QP calls. */
+typedef struct {
+    int32_t status;       /* gm_status of the solve */
+    int32_t iters;        /* ADMM iterations (U updates) */
+    int32_t converged;    /* 1 if both ADMM residuals reached tol */
+    int32_t polished;     /* 1 if the polished solution was kept */
+    float r_prim;         /* last ADMM primal residual |A~U - z|_inf */
+    float r_dual;         /* last ADMM dual residual */
+    double kkt_stat;      /* FP64 |H U + g + A~'y|_inf of the returned (U, y) */
+    double kkt_prim;      /* FP64 max bound violation of A~U */
+    double kkt_dual;      /* FP64 wrong-sign multiplier magnitude */
+    double kkt_comp;      /* FP64 max |y_r| * slack_r */
+} gm_stats;
+
+/* ------------------------------------------------------------------------
+ * gm_ctx_workspace_size / gm_ctx_create — a context binds a graph, a GNN and
+ * settings, and owns (inside the caller's device workspace) the device copy
+ * of both, the Jacobian sparsity pattern, every intermediate of the step and
+ * the linearisation inputs u_hat carried between steps (Algorithm 1).
+ *   workspace  DEVICE pointer, 256-byte aligned, >= the reported size; the
+ *              caller keeps ownership and frees it after gm_ctx_destroy.
+ *   stream     stream on which the static data is uploaded.
+ * gm_ctx_create copies graph and GNN; they may be destroyed afterwards.
+ * ---------------------------------------------------------------------- */
+gm_status gm_ctx_workspace_size(const gm_graph* g, const gm_gnn* m,
+                                const gm_settings* s, size_t* bytes);
+gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s,
+                        void* workspace, size_t bytes, void* stream, gm_ctx** out);
+void gm_ctx_destroy(gm_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * gm_jac_pattern — block sparsity of A_k (Assumption 1 with a K-step GNN):
+ * block row i holds A^{ij} for every j with a directed path of at most K
+ * edges into i (including i), columns ascending.  HOST arrays owned by the
+ * context: row_ptr [M+1], col [nnzb].
+ * ---------------------------------------------------------------------- */
+gm_status gm_jac_pattern(const gm_ctx* ctx, int* nnzb, const int32_t** row_ptr,
+                         const int32_t** col);
+
+/* ------------------------------------------------------------------------
+ * gm_linearize — rollout and local Jacobians (Eq. forward_dynamics,
+ * Eq. linearized_dynamics; Algorithm 1 "Linearize GNN dynamics").
+ *   x0     [M][6]                measured state x~(t)
+ *   u_hat  [N][nu]               linearisation inputs
+ *   x_hat  [N+1][M][6]   (out)   x_hat_0 = x0, x_hat_{k+1} = F(x_hat_k, u_hat_k)
+ *   A      [N][nnzb][6][6] (out) A^{ij}_k = d f^i / d x^j at (x_hat_k, u_hat_k),
+ *                                blocks in gm_jac_pattern order, row-major 6x6
+ *   B      [N][M][6][nu]   (out) B^i_k = d f^i / d u_k
+ *   c      [N][M][6]       (out) c^i_k = x_hat^i_{k+1} - sum_j A^{ij}_k x_hat^j_k - B^i_k u_hat_k
+ * Any of A, B, c may be NULL to skip writing it.
+ * ---------------------------------------------------------------------- */
+gm_status gm_linearize(gm_ctx* ctx, const float* x0, const float* u_hat, float* x_hat,
+                       float* A, float* B, float* c, void* stream);
+
+/* Cost of Eq. linear_gnn_mpc_ocp_explicit (diagonal Q^i_k, R_k). */
+typedef struct {
+    const float* Qdiag;   /* [N+1][M][6]  diagonal of Q^i_k, >= 0 */
+    const float* Rdiag;   /* [N][nu]      diagonal of R_k, > 0 */
+    const float* x_ref;   /* [N+1][M][6]  x^{i,r}_k */
+    const float* u_ref;   /* [N][nu]      u^r_k */
+} gm_cost;
+
+/* Constraints: input box U_k and node-position half-spaces X^i_k. */
+typedef struct {
+    const float* u_lo;    /* [N][nu] */
+    const float* u_hi;    /* [N][nu], u_lo <= u_hi */
+    const float* Cx;      /* [N][M][n_c][3]  C^{x,i}_k acting on p^i_k, stages k = 1..N (nullable if n_c = 0) */
+    const float* dx;      /* [N][M][n_c]     d^{x,i}_k */
+    int n_spheres;        /* > 0: ignore Cx/dx and linearise these spheres at x_hat instead
+                             (requires n_c == n_spheres) */
+    const float* spheres; /* [n_spheres][4]  centre xyz, radius */
+} gm_constr;
+
+/* ------------------------------------------------------------------------
+ * gm_condense — the condensed QP (Eq. condensed_matrices) by the per-node
+ * recursion (Eq. sparse_gamma_i_xb, Eq. sparse_gamma_i_u) and per-node
+ * aggregation (Eq. H, Eq. g, stacked C~ / d~), in the convention
+ *     min 1/2 U'HU + g'U   s.t.  u_lo <= U <= u_hi,  C~ U <= d~
+ * with H = Gu' Qbar Gu + Rbar and g = Gu' Qbar (Gx - x_ref) - Rbar u_ref
+ * (one half of the paper's objective; same minimiser).
+ *   x_hat, A, B, c   as produced by gm_linearize (A in gm_jac_pattern order)
+ *   H   [nU][nU]  (out) nU = N nu, row-major, symmetric
+ *   g   [nU]      (out)
+ *   Ct  (out) packed stage-major rows: stage k = 1..N holds M n_c rows of
+ *             length k nu (row (k, i, c) at float offset
+ *             M n_c nu k(k-1)/2 + (i n_c + c) k nu); total M n_c nu N(N+1)/2.
+ *             Columns >= k nu of a stage-k row are zero and not stored.
+ *   dt  [N][M][n_c]  (out)
+ * Ct and dt may be NULL when n_c == 0.
+ * ---------------------------------------------------------------------- */
+gm_status gm_condense(gm_ctx* ctx, const float* x_hat, const float* A, const float* B,
+                      const float* c, const gm_cost* cost, const gm_constr* cons,
+                      float* H, float* g, float* Ct, float* dt, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gm_qp_solve — ADMM on the condensed QP (fixed rho, no relaxation):
+ *   P = H + rho (I + C~'C~), factored in FP64 (Cholesky) once;
+ *   per iteration U = P^{-1}(A~'(rho z - y) - g), a = A~U,
+ *   z = clip(a + y/rho, l, h), y += rho (a - z), with A~ = [I; C~],
+ *   l = [u_lo; -inf], h = [u_hi; d~]; stop when |a - z|_inf <= tol and the
+ *   dual residual |H U + g + A~'y|_inf <= tol.  Then optional FP64 polish and
+ *   the FP64 KKT certificate into stats.
+ *   H, g, Ct, dt, u_lo, u_hi  as from gm_condense / gm_constr
+ *   warm_U [nU], warm_y [nU + N M n_c]  nullable warm start (U^0, y^0)
+ *   U [nU] (out), y [nU + N M n_c] (out, nullable)  multipliers, box rows first
+ *   stats  DEVICE gm_stats* (out, nullable)
+ * Returns GM_OK even when ADMM did not converge; stats->status says so.
+ * ---------------------------------------------------------------------- */
+gm_status gm_qp_solve(gm_ctx* ctx, const float* H, const float* g, const float* Ct,
+                      const float* dt, const float* u_lo, const float* u_hi,
+                      const float* warm_U, const float* warm_y, float* U, float* y,
+                      gm_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gm_rti_step — one iteration of Algorithm 1 on the device:
+ *   u_hat <- context trajectory (zero after gm_ctx_create / gm_ctx_reset,
+ *            else the shifted previous solution (U*_1..U*_{N-1}, U*_{N-1}));
+ *   x_hat <- rollout of x_meas; linearise; (spheres -> half-spaces at x_hat);
+ *   condense; ADMM (+ polish, KKT certificate); store U* for the next shift.
+ *   x_meas [M][6]      measured state x~(t)
+ *   U      [N][nu]     (out) U*
+ *   u0     [nu]        (out, nullable) first input to apply
+ *   stats  DEVICE gm_stats* (out, nullable)
+ * ---------------------------------------------------------------------- */
+gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost,
+                      const gm_constr* cons, float* U, float* u0, gm_stats* stats,
+                      void* stream);
+
+/* Reset the carried linearisation inputs u_hat to zero (Algorithm 1 "Initialize"). */
+gm_status gm_ctx_reset(gm_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GM_H */

@@ -1,0 +1,247 @@
+"""GNN-MPC real-time iteration on B300 (sm_103a) — Python binding of the C ABI.
+
+The functions here carry the names of the C entry points in include/gm.h and
+only marshal arguments: every step of the method runs in the CUDA kernels of
+libgm.so.  torch supplies device memory (tensors) and streams.  There is no
+CPU fallback: without the library, or without a CUDA device, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgm.so")
+
+GM_OK = 0
+GM_ERR_INVALID_ARG = 1
+GM_ERR_CUDA = 2
+GM_ERR_WORKSPACE = 3
+GM_ERR_NOT_CONVERGED = 4
+GM_STALLED = 5
+GM_ERR_TIMEOUT = 6
+GM_ERR_NUMERIC = 7
+GM_PREC_FP32 = 0
+GM_PREC_MIXED = 1
+
+STATUS_NAMES = {0: "GM_OK", 1: "GM_ERR_INVALID_ARG", 2: "GM_ERR_CUDA", 3: "GM_ERR_WORKSPACE",
+                4: "GM_ERR_NOT_CONVERGED", 5: "GM_STALLED", 6: "GM_ERR_TIMEOUT", 7: "GM_ERR_NUMERIC"}
+
+
+class GnnDesc(C.Structure):
+    _fields_ = [("K", C.c_int), ("W", C.c_int), ("nu", C.c_int), ("dt", C.c_float)]
+
+
+class Settings(C.Structure):
+    _fields_ = [("N", C.c_int), ("n_c", C.c_int), ("precision", C.c_int), ("rho", C.c_float),
+                ("tol", C.c_float), ("max_iter", C.c_int), ("polish", C.c_int),
+                ("timeout_spins", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("converged", C.c_int32),
+                ("polished", C.c_int32), ("r_prim", C.c_float), ("r_dual", C.c_float),
+                ("kkt_stat", C.c_double), ("kkt_prim", C.c_double), ("kkt_dual", C.c_double),
+                ("kkt_comp", C.c_double)]
+
+
+class Cost(C.Structure):
+    _fields_ = [("Qdiag", C.c_void_p), ("Rdiag", C.c_void_p), ("x_ref", C.c_void_p),
+                ("u_ref", C.c_void_p)]
+
+
+class Constr(C.Structure):
+    _fields_ = [("u_lo", C.c_void_p), ("u_hi", C.c_void_p), ("Cx", C.c_void_p),
+                ("dx", C.c_void_p), ("n_spheres", C.c_int), ("spheres", C.c_void_p)]
+
+
+STATS_BYTES = C.sizeof(Stats)
+
+
+class GMError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgm.so not built at {LIB_PATH}: run `python -m paper_2602_17601_b300.build`")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32p = C.c_void_p, C.POINTER(C.c_int32)
+    sig = {
+        "gm_last_error": ([], C.c_char_p),
+        "gm_version": ([], C.c_char_p),
+        "gm_graph_create": ([C.c_int, C.c_int, i32p, i32p, C.c_int, i32p, C.POINTER(vp)], C.c_int),
+        "gm_graph_destroy": ([vp], None),
+        "gm_gnn_load": ([C.POINTER(GnnDesc), C.POINTER(C.c_float), C.c_size_t, C.POINTER(vp)], C.c_int),
+        "gm_gnn_destroy": ([vp], None),
+        "gm_ctx_workspace_size": ([vp, vp, C.POINTER(Settings), C.POINTER(C.c_size_t)], C.c_int),
+        "gm_ctx_create": ([vp, vp, C.POINTER(Settings), vp, C.c_size_t, vp, C.POINTER(vp)], C.c_int),
+        "gm_ctx_destroy": ([vp], None),
+        "gm_jac_pattern": ([vp, C.POINTER(C.c_int), C.POINTER(i32p), C.POINTER(i32p)], C.c_int),
+        "gm_linearize": ([vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "gm_condense": ([vp, vp, vp, vp, vp, C.POINTER(Cost), C.POINTER(Constr), vp, vp, vp, vp, vp],
+                        C.c_int),
+        "gm_qp_solve": ([vp] * 12 + [vp], C.c_int),
+        "gm_rti_step": ([vp, vp, C.POINTER(Cost), C.POINTER(Constr), vp, vp, vp, vp], C.c_int),
+        "gm_ctx_reset": ([vp, vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_destroy",
+                    "gm_gnn_load", "gm_gnn_destroy", "gm_ctx_workspace_size", "gm_ctx_create",
+                    "gm_ctx_destroy", "gm_jac_pattern", "gm_linearize", "gm_condense",
+                    "gm_qp_solve", "gm_rti_step", "gm_ctx_reset")
+
+
+def lib():
+    return _lib
+
+
+def _check(fn, code):
+    if code != GM_OK:
+        raise GMError(fn, code, _lib.gm_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def gm_last_error():
+    return _lib.gm_last_error().decode()
+
+
+def gm_version():
+    return _lib.gm_version().decode()
+
+
+def gm_graph_create(M, src, dst, nu, act_node):
+    src = np.ascontiguousarray(src, np.int32)
+    dst = np.ascontiguousarray(dst, np.int32)
+    act = np.ascontiguousarray(act_node, np.int32)
+    out = C.c_void_p()
+    i32p = C.POINTER(C.c_int32)
+    _check("gm_graph_create",
+           _lib.gm_graph_create(int(M), int(src.size), src.ctypes.data_as(i32p), dst.ctypes.data_as(i32p),
+                                int(nu), act.ctypes.data_as(i32p), C.byref(out)))
+    return out
+
+
+def gm_graph_destroy(g):
+    _lib.gm_graph_destroy(g)
+
+
+def gm_gnn_load(K, W, nu, dt, blob):
+    blob = np.ascontiguousarray(blob, np.float32)
+    d = GnnDesc(int(K), int(W), int(nu), float(dt))
+    out = C.c_void_p()
+    _check("gm_gnn_load", _lib.gm_gnn_load(C.byref(d), blob.ctypes.data_as(C.POINTER(C.c_float)),
+                                           blob.size, C.byref(out)))
+    return out
+
+
+def gm_gnn_destroy(m):
+    _lib.gm_gnn_destroy(m)
+
+
+def make_settings(N, n_c=0, precision=GM_PREC_FP32, rho=0.1, tol=1e-6, max_iter=4000, polish=0,
+                  timeout_spins=0):
+    return Settings(int(N), int(n_c), int(precision), float(rho), float(tol), int(max_iter), int(polish),
+                    int(timeout_spins))
+
+
+def gm_ctx_workspace_size(graph, gnn, settings):
+    n = C.c_size_t()
+    _check("gm_ctx_workspace_size", _lib.gm_ctx_workspace_size(graph, gnn, C.byref(settings), C.byref(n)))
+    return n.value
+
+
+def gm_ctx_create(graph, gnn, settings, workspace, stream=None):
+    out = C.c_void_p()
+    _check("gm_ctx_create", _lib.gm_ctx_create(graph, gnn, C.byref(settings), _ptr(workspace),
+                                               workspace.numel() * workspace.element_size(),
+                                               _stream(stream), C.byref(out)))
+    return out
+
+
+def gm_ctx_destroy(ctx):
+    _lib.gm_ctx_destroy(ctx)
+
+
+def gm_ctx_reset(ctx, stream=None):
+    _check("gm_ctx_reset", _lib.gm_ctx_reset(ctx, _stream(stream)))
+
+
+def gm_jac_pattern(ctx, M):
+    """(row_ptr [M+1], col [nnzb]) of the block pattern of A_k (M = number of nodes)."""
+    nnzb = C.c_int()
+    rp = C.POINTER(C.c_int32)()
+    col = C.POINTER(C.c_int32)()
+    _check("gm_jac_pattern", _lib.gm_jac_pattern(ctx, C.byref(nnzb), C.byref(rp), C.byref(col)))
+    row_ptr = np.ctypeslib.as_array(rp, shape=(M + 1,)).copy()
+    return row_ptr, np.ctypeslib.as_array(col, shape=(nnzb.value,)).copy()
+
+
+def gm_linearize(ctx, x0, u_hat, x_hat, A=None, B=None, c=None, stream=None):
+    _check("gm_linearize", _lib.gm_linearize(ctx, _ptr(x0), _ptr(u_hat), _ptr(x_hat), _ptr(A), _ptr(B),
+                                             _ptr(c), _stream(stream)))
+
+
+def make_cost(Qdiag, Rdiag, x_ref, u_ref):
+    return Cost(_ptr(Qdiag), _ptr(Rdiag), _ptr(x_ref), _ptr(u_ref))
+
+
+def make_constr(u_lo, u_hi, Cx=None, dx=None, spheres=None):
+    ns = 0 if spheres is None else int(spheres.shape[0])
+    return Constr(_ptr(u_lo), _ptr(u_hi), _ptr(Cx), _ptr(dx), ns, _ptr(spheres))
+
+
+def gm_condense(ctx, x_hat, A, B, c, cost, constr, H, g, Ct=None, dt=None, stream=None):
+    _check("gm_condense", _lib.gm_condense(ctx, _ptr(x_hat), _ptr(A), _ptr(B), _ptr(c), C.byref(cost),
+                                           C.byref(constr), _ptr(H), _ptr(g), _ptr(Ct), _ptr(dt),
+                                           _stream(stream)))
+
+
+def gm_qp_solve(ctx, H, g, Ct, dt, u_lo, u_hi, U, y=None, stats=None, warm_U=None, warm_y=None,
+                stream=None):
+    _check("gm_qp_solve", _lib.gm_qp_solve(ctx, _ptr(H), _ptr(g), _ptr(Ct), _ptr(dt), _ptr(u_lo),
+                                           _ptr(u_hi), _ptr(warm_U), _ptr(warm_y), _ptr(U), _ptr(y),
+                                           _ptr(stats), _stream(stream)))
+
+
+def gm_rti_step(ctx, x_meas, cost, constr, U, u0=None, stats=None, stream=None):
+    _check("gm_rti_step", _lib.gm_rti_step(ctx, _ptr(x_meas), C.byref(cost), C.byref(constr), _ptr(U),
+                                           _ptr(u0), _ptr(stats), _stream(stream)))
+
+
+def read_stats(stats_tensor):
+    """gm_stats from a device buffer of STATS_BYTES bytes (synchronises on copy)."""
+    raw = stats_tensor.cpu().numpy().tobytes()
+    s = Stats.from_buffer_copy(raw[:STATS_BYTES])
+    return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+from .rti import RTIProblem  # noqa: E402,F401

@@ -1,0 +1,594 @@
+// C ABI of the GNN-MPC library: handles, workspace layout, and the order of
+// the kernels of one real-time iteration (Algorithm 1).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "ctx.h"
+#include "kernels.h"
+
+namespace gmi {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+// ---------------------------------------------------------------- reverse-mode cones
+// For every seed (output node) s: the nodes reaching s in at most r edges (BFS
+// over predecessors), and the edges into them.  See struct Cones.
+static int row_of(const std::vector<int>& node, const std::vector<int>& ptr, int s, int n) {
+    auto b = node.begin() + ptr[s], e = node.begin() + ptr[s + 1];
+    auto it = std::lower_bound(b, e, n);
+    return (it != e && *it == n) ? (int)(it - node.begin()) : -1;
+}
+
+static void build_cones(const gm_graph& g, int K, Cones& C) {
+    const int M = g.M;
+    C.K = K;
+    C.nr_node.assign(K + 1, {});
+    C.nr_seed.assign(K + 1, {});
+    C.nr_ptr.assign(K + 1, {});
+    C.nr_prev.assign(K + 1, {});
+    C.er_edge.assign(K, {});
+    C.er_dstrow.assign(K, {});
+    C.er_srcrow.assign(K, {});
+    C.er_prev.assign(K, {});
+    C.er_dst_ptr.assign(K, {});
+    C.er_src_ptr.assign(K, {});
+    C.er_src_list.assign(K, {});
+    std::vector<std::vector<std::pair<int, int>>> cone(M);
+    std::vector<int> dist(M, -1), frontier, next, touched;
+    for (int s = 0; s < M; ++s) {
+        touched.assign(1, s);
+        dist[s] = 0;
+        frontier.assign(1, s);
+        for (int d = 1; d <= K; ++d) {
+            next.clear();
+            for (int n : frontier)
+                for (int e = g.in_ptr[n]; e < g.in_ptr[n + 1]; ++e) {
+                    const int j = g.src[e];
+                    if (dist[j] < 0) {
+                        dist[j] = d;
+                        touched.push_back(j);
+                        next.push_back(j);
+                    }
+                }
+            frontier.swap(next);
+        }
+        for (int n : touched) cone[s].push_back({n, dist[n]});
+        std::sort(cone[s].begin(), cone[s].end());
+        for (int n : touched) dist[n] = -1;
+    }
+    for (int r = 0; r <= K; ++r) {
+        C.nr_ptr[r].push_back(0);
+        for (int s = 0; s < M; ++s) {
+            for (auto& nd : cone[s])
+                if (nd.second <= r) {
+                    C.nr_node[r].push_back(nd.first);
+                    C.nr_seed[r].push_back(s);
+                }
+            C.nr_ptr[r].push_back((int)C.nr_node[r].size());
+        }
+        C.nr_prev[r].assign(C.nr_node[r].size(), -1);
+        if (r > 0)
+            for (size_t q = 0; q < C.nr_node[r].size(); ++q)
+                C.nr_prev[r][q] = row_of(C.nr_node[r - 1], C.nr_ptr[r - 1], C.nr_seed[r][q], C.nr_node[r][q]);
+    }
+    for (int r = 0; r < K; ++r) {
+        const int Rn = (int)C.nr_node[r].size();
+        C.er_dst_ptr[r].assign(Rn + 1, 0);
+        for (int q = 0; q < Rn; ++q) {
+            C.er_dst_ptr[r][q] = (int)C.er_edge[r].size();
+            const int s = C.nr_seed[r][q], i = C.nr_node[r][q];
+            for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e) {
+                C.er_edge[r].push_back(e);
+                C.er_dstrow[r].push_back(q);
+                C.er_srcrow[r].push_back(row_of(C.nr_node[r + 1], C.nr_ptr[r + 1], s, g.src[e]));
+                int prev = -1;
+                if (r > 0) {
+                    const int qp = C.nr_prev[r][q];
+                    if (qp >= 0) prev = C.er_dst_ptr[r - 1][qp] + (e - g.in_ptr[i]);
+                }
+                C.er_prev[r].push_back(prev);
+            }
+        }
+        C.er_dst_ptr[r][Rn] = (int)C.er_edge[r].size();
+        const int Rn1 = (int)C.nr_node[r + 1].size();
+        std::vector<int> cnt(Rn1 + 1, 0);
+        for (int sr : C.er_srcrow[r]) cnt[sr + 1]++;
+        for (int q = 0; q < Rn1; ++q) cnt[q + 1] += cnt[q];
+        C.er_src_ptr[r] = cnt;
+        C.er_src_list[r].assign(C.er_edge[r].size(), 0);
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (size_t p = 0; p < C.er_srcrow[r].size(); ++p) C.er_src_list[r][fill[C.er_srcrow[r][p]]++] = (int)p;
+    }
+    // encoder level: ER_{K-1} rows grouped by the NR_K row of their destination
+    const int RK = (int)C.nr_node[K].size();
+    std::vector<int> dK(C.er_edge[K - 1].size());
+    for (size_t p = 0; p < dK.size(); ++p) {
+        const int q = C.er_dstrow[K - 1][p];
+        dK[p] = row_of(C.nr_node[K], C.nr_ptr[K], C.nr_seed[K - 1][q], C.nr_node[K - 1][q]);
+    }
+    C.enc_dst_ptr.assign(RK + 1, 0);
+    for (int v : dK) C.enc_dst_ptr[v + 1]++;
+    for (int q = 0; q < RK; ++q) C.enc_dst_ptr[q + 1] += C.enc_dst_ptr[q];
+    C.enc_dst_list.assign(dK.size(), 0);
+    {
+        std::vector<int> fill(C.enc_dst_ptr.begin(), C.enc_dst_ptr.end() - 1);
+        for (size_t p = 0; p < dK.size(); ++p) C.enc_dst_list[fill[dK[p]]++] = (int)p;
+    }
+    C.b_row.assign((size_t)M * g.nu, -1);
+    for (int s = 0; s < M; ++s)
+        for (int a = 0; a < g.nu; ++a) C.b_row[(size_t)s * g.nu + a] = row_of(C.nr_node[K], C.nr_ptr[K], s, g.act_node[a]);
+}
+
+// ---------------------------------------------------------------- weight layout
+static long put(std::vector<float>& w, const float* p, size_t n) {
+    while (w.size() % 32) w.push_back(0.f);
+    long o = (long)w.size();
+    w.insert(w.end(), p, p + n);
+    return o;
+}
+
+static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::vector<MlpOff>& offs) {
+    const int K = m.d.K, W = m.d.W;
+    std::vector<std::array<int, 3>> shapes;
+    shapes.push_back({6 + nu, W, W});
+    shapes.push_back({6, W, W});
+    for (int t = 0; t < K; ++t) {
+        shapes.push_back({3 * W, W, W});
+        shapes.push_back({2 * W, W, W});
+    }
+    shapes.push_back({W, W, 3});
+    const float* b = m.blob.data();
+    size_t off = 0;
+    offs.clear();
+    for (size_t idx = 0; idx < shapes.size(); ++idx) {
+        const int in = shapes[idx][0], hid = shapes[idx][1], out = shapes[idx][2];
+        const float* W1 = b + off; off += (size_t)in * hid;
+        const float* b1 = b + off; off += hid;
+        const float* W2 = b + off; off += (size_t)hid * out;
+        const float* b2 = b + off; off += out;
+        MlpOff mo;
+        mo.in = in; mo.hid = hid; mo.out = out;
+        mo.W1 = put(w, W1, (size_t)in * hid);
+        mo.b1 = put(w, b1, hid);
+        mo.W2 = put(w, W2, (size_t)hid * out);
+        mo.b2 = put(w, b2, out);
+        std::vector<float> t((size_t)out * hid);
+        for (int o = 0; o < out; ++o)
+            for (int j = 0; j < hid; ++j) t[(size_t)o * hid + j] = W2[(size_t)j * out + o];
+        mo.W2t = put(w, t.data(), t.size());
+        t.assign((size_t)hid * in, 0.f);
+        for (int j = 0; j < hid; ++j)
+            for (int i = 0; i < in; ++i) t[(size_t)j * in + i] = W1[(size_t)i * hid + j];
+        mo.W1t = put(w, t.data(), t.size());
+        const bool edge_mp = idx >= 2 && idx < 2 + 2 * (size_t)K && (idx % 2 == 0);
+        if (edge_mp) {
+            t.assign((size_t)hid * W, 0.f);
+            for (int j = 0; j < hid; ++j)
+                for (int n = 0; n < W; ++n) t[(size_t)j * W + n] = W1[(size_t)(2 * W + n) * hid + j];
+            mo.Wc = put(w, t.data(), t.size());
+            t.assign((size_t)2 * W * W, 0.f);
+            for (int j = 0; j < W; ++j)
+                for (int n = 0; n < W; ++n) {
+                    t[(size_t)j * W + n] = W1[(size_t)n * hid + j];
+                    t[(size_t)(W + j) * W + n] = W1[(size_t)(W + n) * hid + j];
+                }
+            mo.Bab = put(w, t.data(), t.size());
+        }
+        offs.push_back(mo);
+    }
+}
+
+static size_t blob_floats(int K, int W, int nu) {
+    auto mlp = [](size_t i, size_t h, size_t o) { return i * h + h + h * o + o; };
+    size_t n = mlp(6 + nu, W, W) + mlp(6, W, W) + mlp(W, W, 3);
+    n += (size_t)K * (mlp(3 * W, W, W) + mlp(2 * W, W, W));
+    return n;
+}
+
+// ---------------------------------------------------------------- workspace layout
+static constexpr int kMaxAdmmGrid = 2048;
+static constexpr int kMaxGramSplit = 64;
+
+static void plan(gm_ctx* c, Carver& cv) {
+    const Cones& C = c->cones;
+    const int M = c->M, E = c->E, K = c->K, W = c->W, N = c->N, nu = c->nu, nU = c->nU;
+    const long RK = (long)C.nr_node[K].size(), RK1 = (long)C.nr_node[K - 1].size();
+    const long RE = (long)C.er_edge[K - 1].size();
+    // stages per reverse chunk: keep the per-chunk buffers near 2 GB
+    const long per_stage = 4L * (2 * RK * 3 * W + 2 * RK1 * 3 * W + 3 * RE * 3 * W + RK * 3 * (6 + nu) + RE * 18);
+    c->stage_chunk = (int)std::max(1L, std::min((long)N, (2L << 30) / std::max(1L, per_stage)));
+    const long Ns = c->stage_chunk;
+    std::vector<float> wdummy;
+    c->d_src = cv.take<int>(std::max(E, 1));
+    c->d_dst = cv.take<int>(std::max(E, 1));
+    c->d_in_ptr = cv.take<int>(M + 1);
+    c->d_act = cv.take<int>(nu);
+    c->d_jac_col = cv.take<int>(c->nnzb);
+    c->d_wts = cv.take<float>(c->wts_host.size());
+    for (int r = 0; r <= K; ++r) {
+        c->dc.nr_count[r] = (int)C.nr_node[r].size();
+        c->dc.nr_node[r] = cv.take<int>(C.nr_node[r].size() + 1);
+        c->dc.nr_prev[r] = cv.take<int>(C.nr_prev[r].size() + 1);
+    }
+    for (int r = 0; r < K; ++r) {
+        c->dc.er_count[r] = (int)C.er_edge[r].size();
+        c->dc.er_edge[r] = cv.take<int>(C.er_edge[r].size() + 1);
+        c->dc.er_dstrow[r] = cv.take<int>(C.er_dstrow[r].size() + 1);
+        c->dc.er_prev[r] = cv.take<int>(C.er_prev[r].size() + 1);
+        c->dc.er_dst_ptr[r] = cv.take<int>(C.er_dst_ptr[r].size());
+        c->dc.er_src_ptr[r] = cv.take<int>(C.er_src_ptr[r].size());
+        c->dc.er_src_list[r] = cv.take<int>(C.er_src_list[r].size() + 1);
+    }
+    c->dc.enc_dst_ptr = cv.take<int>(C.enc_dst_ptr.size());
+    c->dc.enc_dst_list = cv.take<int>(C.enc_dst_list.size() + 1);
+    c->dc.nr_ptr_K = cv.take<int>(M + 1);
+    c->dc.b_row = cv.take<int>((size_t)M * nu);
+    const int ww = W / 32;
+    c->d_h = cv.take<float>((size_t)M * W);
+    c->d_e = cv.take<float>((size_t)std::max(E, 1) * W);
+    c->d_agg = cv.take<float>((size_t)M * W);
+    c->d_mask_node = cv.take<uint32_t>((size_t)N * (K + 2) * M * ww);
+    c->d_mask_edge = cv.take<uint32_t>((size_t)N * (K + 1) * std::max(E, 1) * ww);
+    c->d_dhA = cv.take<float>(Ns * RK * 3 * W);
+    c->d_dhB = cv.take<float>(Ns * RK * 3 * W);
+    c->d_dacc = cv.take<float>(Ns * RK1 * 3 * W);
+    c->d_dagg = cv.take<float>(Ns * RK1 * 3 * W);
+    c->d_deA = cv.take<float>(Ns * std::max(RE, 1L) * 3 * W);
+    c->d_deB = cv.take<float>(Ns * std::max(RE, 1L) * 3 * W);
+    c->d_ehid = cv.take<float>(Ns * std::max(RE, 1L) * 3 * W);
+    c->d_dxn = cv.take<float>(Ns * RK * 3 * (6 + nu));
+    c->d_dd = cv.take<float>(Ns * std::max(RE, 1L) * 18);
+    c->d_u_hat = cv.take<float>((size_t)N * nu);
+    c->d_x_hat = cv.take<float>((size_t)(N + 1) * M * 6);
+    c->d_A = cv.take<float>((size_t)N * c->nnzb * 36);
+    c->d_B = cv.take<float>((size_t)N * M * 6 * nu);
+    c->d_c = cv.take<float>((size_t)N * M * 6);
+    c->d_Cx = cv.take<float>(std::max(1L, c->rows_c * 3));
+    c->d_dx = cv.take<float>(std::max(1L, c->rows_c));
+    c->d_Gu = cv.take<float>((size_t)M * 6 * nu * ((size_t)N * (N + 1) / 2));
+    c->d_Gx = cv.take<float>((size_t)(N + 1) * M * 6);
+    c->d_H = cv.take<float>((size_t)nU * nU);
+    c->d_g = cv.take<float>(nU);
+    c->d_Ct = cv.take<float>(std::max(1L, c->ct_len));
+    c->d_dt = cv.take<float>(std::max(1L, c->rows_c));
+    c->d_U = cv.take<float>(nU);
+    c->d_y = cv.take<float>(nU + c->rows_c);
+    c->d_z = cv.take<float>(nU + c->rows_c);
+    const long T = (nU + 31) / 32;
+    c->d_gram_part = cv.take<float>(std::max((long)kMaxGramSplit * T * T * 1024, 4L * 1024 * nU));
+    c->d_L = cv.take<double>((size_t)nU * nU);
+    c->d_Linv = cv.take<double>((size_t)nU * nU);
+    c->d_P = cv.take<float>((size_t)nU * nU);
+    c->d_Pinv = cv.take<float>((size_t)nU * nU);
+    c->d_acc = cv.take<float>(3 * (2 * (size_t)nU + 1));
+    c->d_bar = cv.take<unsigned>(4);
+    c->d_status = cv.take<int>(4);
+    c->d_row_begin = cv.take<int>(kMaxAdmmGrid + 1);
+    c->d_kkt = cv.take<double>(nU + 4);
+    c->d_stats = cv.take<gm_stats>(1);
+}
+
+}  // namespace gmi
+
+using namespace gmi;
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* gm_last_error(void) { return g_err.c_str(); }
+const char* gm_version(void) { return "gnnmpc-b300 0.1 (sm_103a)"; }
+
+gm_status gm_graph_create(int M, int E, const int32_t* src, const int32_t* dst, int nu,
+                          const int32_t* act_node, gm_graph** out) {
+    clear_error();
+    GM_CHECK_ARG(out, "out is NULL");
+    GM_CHECK_ARG(M >= 1, "M must be >= 1 (got %d)", M);
+    GM_CHECK_ARG(E >= 0, "E must be >= 0 (got %d)", E);
+    GM_CHECK_ARG(E == 0 || (src && dst), "src/dst are NULL");
+    GM_CHECK_ARG(nu >= 1 && act_node, "nu must be >= 1 with act_node given");
+    std::vector<std::pair<int, int>> ed(E);
+    for (int k = 0; k < E; ++k) {
+        GM_CHECK_ARG(src[k] >= 0 && src[k] < M && dst[k] >= 0 && dst[k] < M,
+                     "edge %d (%d -> %d) out of range [0, %d)", k, src[k], dst[k], M);
+        GM_CHECK_ARG(src[k] != dst[k], "edge %d is a self-loop", k);
+        ed[k] = {dst[k], src[k]};
+    }
+    std::sort(ed.begin(), ed.end());
+    for (int k = 1; k < E; ++k) GM_CHECK_ARG(ed[k] != ed[k - 1], "duplicate edge %d -> %d", ed[k].second, ed[k].first);
+    for (int a = 0; a < nu; ++a) GM_CHECK_ARG(act_node[a] >= 0 && act_node[a] < M, "act_node[%d] = %d out of range", a, act_node[a]);
+    auto* g = new gm_graph;
+    g->M = M; g->E = E; g->nu = nu;
+    g->src.resize(E); g->dst.resize(E);
+    g->in_ptr.assign(M + 1, 0);
+    for (int k = 0; k < E; ++k) {
+        g->dst[k] = ed[k].first;
+        g->src[k] = ed[k].second;
+        g->in_ptr[ed[k].first + 1]++;
+    }
+    for (int i = 0; i < M; ++i) g->in_ptr[i + 1] += g->in_ptr[i];
+    g->act_node.assign(act_node, act_node + nu);
+    *out = g;
+    return GM_OK;
+}
+
+void gm_graph_destroy(gm_graph* g) { delete g; }
+
+gm_status gm_gnn_load(const gm_gnn_desc* d, const float* blob, size_t n, gm_gnn** out) {
+    clear_error();
+    GM_CHECK_ARG(d && blob && out, "NULL argument");
+    GM_CHECK_ARG(d->K >= 1 && d->K <= 6, "K must be in [1, 6] (got %d)", d->K);
+    GM_CHECK_ARG(d->W == 32 || d->W == 64 || d->W == 128, "W must be 32, 64 or 128 (got %d)", d->W);
+    GM_CHECK_ARG(d->nu >= 1 && d->nu <= 64, "nu must be in [1, 64] (got %d)", d->nu);
+    GM_CHECK_ARG(d->dt > 0.f, "dt must be > 0");
+    const size_t need = blob_floats(d->K, d->W, d->nu);
+    GM_CHECK_ARG(n == need, "blob has %zu floats, (K=%d, W=%d, nu=%d) needs %zu", n, d->K, d->W, d->nu, need);
+    for (size_t i = 0; i < n; ++i) GM_CHECK_ARG(std::isfinite(blob[i]), "blob[%zu] is not finite", i);
+    auto* m = new gm_gnn;
+    m->d = *d;
+    m->blob.assign(blob, blob + n);
+    *out = m;
+    return GM_OK;
+}
+
+void gm_gnn_destroy(gm_gnn* m) { delete m; }
+
+static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* s, gm_ctx* c) {
+    GM_CHECK_ARG(g && m && s, "NULL argument");
+    GM_CHECK_ARG(g->nu == m->d.nu, "graph has nu=%d, GNN has nu=%d", g->nu, m->d.nu);
+    GM_CHECK_ARG(s->N >= 1 && s->N <= 64, "N must be in [1, 64] (got %d)", s->N);
+    GM_CHECK_ARG(s->n_c >= 0 && s->n_c <= 64, "n_c must be in [0, 64]");
+    GM_CHECK_ARG(s->precision == GM_PREC_FP32 || s->precision == GM_PREC_MIXED, "unknown precision %d", s->precision);
+    GM_CHECK_ARG(s->rho > 0.f && s->tol > 0.f && s->max_iter >= 1, "rho, tol must be > 0 and max_iter >= 1");
+    GM_CHECK_ARG((long)s->N * g->nu <= 256, "N * nu must be <= 256 (got %d)", s->N * g->nu);
+    c->s = *s;
+    c->M = g->M; c->E = g->E; c->nu = g->nu; c->K = m->d.K; c->W = m->d.W; c->N = s->N;
+    c->nU = s->N * g->nu; c->n_c = s->n_c; c->dt = m->d.dt;
+    c->rows_c = (long)c->N * c->M * c->n_c;
+    c->ct_len = (long)c->M * c->n_c * c->nu * ((long)c->N * (c->N + 1) / 2);
+    c->graph = *g;
+    build_cones(*g, c->K, c->cones);
+    c->jac_row_ptr = c->cones.nr_ptr[c->K];
+    c->jac_col = c->cones.nr_node[c->K];
+    c->nnzb = (int)c->jac_col.size();
+    build_weights(*m, g->nu, c->wts_host, c->mlp);
+    return GM_OK;
+}
+
+gm_status gm_ctx_workspace_size(const gm_graph* g, const gm_gnn* m, const gm_settings* s, size_t* bytes) {
+    clear_error();
+    GM_CHECK_ARG(bytes, "bytes is NULL");
+    gm_ctx c;
+    GM_TRY(prepare(g, m, s, &c));
+    Carver cv;
+    plan(&c, cv);
+    *bytes = cv.off + 256;
+    return GM_OK;
+}
+
+}  // extern "C"
+
+template <class T>
+static gm_status up(T* d, const std::vector<T>& h, cudaStream_t st) {
+    if (h.empty()) return GM_OK;
+    GM_CUDA_TRY(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return GM_OK;
+}
+
+extern "C" {
+
+gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s, void* workspace,
+                        size_t bytes, void* stream, gm_ctx** out) {
+    clear_error();
+    GM_CHECK_ARG(out, "out is NULL");
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+        set_error("workspace is NULL or not 256-byte aligned");
+        return GM_ERR_WORKSPACE;
+    }
+    auto* c = new gm_ctx;
+    gm_status stt = prepare(g, m, s, c);
+    if (stt != GM_OK) { delete c; return stt; }
+    Carver probe;
+    plan(c, probe);
+    if (probe.off + 256 > bytes) {
+        set_error("workspace has %zu bytes, needs %zu", bytes, probe.off + 256);
+        delete c;
+        return GM_ERR_WORKSPACE;
+    }
+    Carver cv;
+    cv.base = static_cast<char*>(workspace);
+    plan(c, cv);
+    c->ws = static_cast<char*>(workspace);
+    c->ws_bytes = bytes;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    auto fail = [&](gm_status e) { delete c; return e; };
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        set_error("no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(GM_ERR_CUDA);
+    }
+    const Cones& C = c->cones;
+    const int K = c->K;
+    std::vector<gm_status> rs;
+    rs.push_back(up(c->d_src, c->graph.src, st));
+    rs.push_back(up(c->d_dst, c->graph.dst, st));
+    rs.push_back(up(c->d_in_ptr, c->graph.in_ptr, st));
+    rs.push_back(up(c->d_act, c->graph.act_node, st));
+    rs.push_back(up(c->d_jac_col, c->jac_col, st));
+    rs.push_back(up(c->d_wts, c->wts_host, st));
+    for (int r = 0; r <= K; ++r) {
+        rs.push_back(up(c->dc.nr_node[r], C.nr_node[r], st));
+        rs.push_back(up(c->dc.nr_prev[r], C.nr_prev[r], st));
+    }
+    for (int r = 0; r < K; ++r) {
+        rs.push_back(up(c->dc.er_edge[r], C.er_edge[r], st));
+        rs.push_back(up(c->dc.er_dstrow[r], C.er_dstrow[r], st));
+        rs.push_back(up(c->dc.er_prev[r], C.er_prev[r], st));
+        rs.push_back(up(c->dc.er_dst_ptr[r], C.er_dst_ptr[r], st));
+        rs.push_back(up(c->dc.er_src_ptr[r], C.er_src_ptr[r], st));
+        rs.push_back(up(c->dc.er_src_list[r], C.er_src_list[r], st));
+    }
+    rs.push_back(up(c->dc.enc_dst_ptr, C.enc_dst_ptr, st));
+    rs.push_back(up(c->dc.enc_dst_list, C.enc_dst_list, st));
+    rs.push_back(up(c->dc.nr_ptr_K, C.nr_ptr[K], st));
+    rs.push_back(up(c->dc.b_row, C.b_row, st));
+    // ADMM: one CTA per SM (co-resident, cooperative), C~ rows split by non-zeros
+    {
+        int occ = 0;
+        if (cudaFuncSetAttribute(admm_kernel_ptr(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)admm_smem_bytes(c)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, admm_kernel_ptr(c), 256, admm_smem_bytes(c)) != cudaSuccess) {
+            set_error("ADMM occupancy query failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(GM_ERR_CUDA);
+        }
+        occ = std::max(occ, 1);
+        long want = c->rows_c > 0 ? std::max(1L, std::min((long)occ * c->num_sms, c->rows_c / 16)) : 1;
+        c->admm_grid = (int)std::min<long>(want, kMaxAdmmGrid);
+        const long Mnc = (long)c->M * c->n_c;
+        double total = 0;
+        for (int k = 1; k <= c->N; ++k) total += (double)Mnc * k * c->nu;
+        std::vector<int> rb(c->admm_grid + 1, 0);
+        double acc = 0;
+        int b = 1;
+        for (long r = 0; r < c->rows_c && b < c->admm_grid; ++r) {
+            acc += (double)((r / std::max(1L, Mnc)) + 1) * c->nu;
+            while (b < c->admm_grid && acc >= total * b / c->admm_grid) rb[b++] = (int)(r + 1);
+        }
+        for (; b <= c->admm_grid; ++b) rb[b] = (int)c->rows_c;
+        rs.push_back(up(c->d_row_begin, rb, st));
+        // every upload above reads host vectors that must outlive the copies
+    }
+    for (gm_status r : rs)
+        if (r != GM_OK) return fail(r);
+    if (cudaMemsetAsync(c->d_u_hat, 0, sizeof(float) * c->N * c->nu, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("context upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(GM_ERR_CUDA);
+    }
+    *out = c;
+    return GM_OK;
+}
+
+void gm_ctx_destroy(gm_ctx* ctx) { delete ctx; }
+
+gm_status gm_jac_pattern(const gm_ctx* ctx, int* nnzb, const int32_t** row_ptr, const int32_t** col) {
+    clear_error();
+    GM_CHECK_ARG(ctx && nnzb && row_ptr && col, "NULL argument");
+    *nnzb = ctx->nnzb;
+    *row_ptr = ctx->jac_row_ptr.data();
+    *col = ctx->jac_col.data();
+    return GM_OK;
+}
+
+gm_status gm_ctx_reset(gm_ctx* ctx, void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx, "ctx is NULL");
+    GM_CUDA_TRY(cudaMemsetAsync(ctx->d_u_hat, 0, sizeof(float) * ctx->N * ctx->nu, static_cast<cudaStream_t>(stream)));
+    return GM_OK;
+}
+
+gm_status gm_linearize(gm_ctx* ctx, const float* x0, const float* u_hat, float* x_hat, float* A, float* B,
+                       float* c, void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx && x0 && u_hat && x_hat, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GM_TRY(gnn_rollout(ctx, x0, u_hat, x_hat, st));
+    GM_TRY(gnn_jacobians(ctx, x_hat, u_hat, A, B, c, st));
+    return GM_OK;
+}
+
+static gm_status check_cost(const gm_ctx* ctx, const gm_cost* cost, const gm_constr* cons) {
+    GM_CHECK_ARG(cost && cost->Qdiag && cost->Rdiag && cost->x_ref && cost->u_ref, "cost has NULL members");
+    GM_CHECK_ARG(cons && cons->u_lo && cons->u_hi, "constraints have NULL bounds");
+    if (cons->n_spheres > 0) {
+        GM_CHECK_ARG(cons->spheres, "spheres is NULL");
+        GM_CHECK_ARG(cons->n_spheres == ctx->n_c, "n_spheres (%d) must equal settings.n_c (%d)", cons->n_spheres, ctx->n_c);
+    } else if (ctx->n_c > 0) {
+        GM_CHECK_ARG(cons->Cx && cons->dx, "Cx/dx are NULL with n_c = %d", ctx->n_c);
+    }
+    return GM_OK;
+}
+
+gm_status gm_condense(gm_ctx* ctx, const float* x_hat, const float* A, const float* B, const float* c,
+                      const gm_cost* cost, const gm_constr* cons, float* H, float* g, float* Ct, float* dt,
+                      void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx && x_hat && A && B && c && H && g, "NULL argument");
+    GM_TRY(check_cost(ctx, cost, cons));
+    GM_CHECK_ARG(ctx->n_c == 0 || (Ct && dt), "Ct/dt are NULL with n_c = %d", ctx->n_c);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float* Cx = cons->Cx;
+    const float* dx = cons->dx;
+    if (cons->n_spheres > 0) {
+        GM_TRY(sphere_halfspaces(ctx, x_hat, cons->spheres, cons->n_spheres, ctx->d_Cx, ctx->d_dx, st));
+        Cx = ctx->d_Cx;
+        dx = ctx->d_dx;
+    }
+    return condense(ctx, x_hat, A, B, c, cost, Cx, dx, H, g, Ct, dt, st);
+}
+
+gm_status gm_qp_solve(gm_ctx* ctx, const float* H, const float* g, const float* Ct, const float* dt,
+                      const float* u_lo, const float* u_hi, const float* warm_U, const float* warm_y,
+                      float* U, float* y, gm_stats* stats, void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx && H && g && u_lo && u_hi && U, "NULL argument");
+    GM_CHECK_ARG(ctx->n_c == 0 || (Ct && dt), "Ct/dt are NULL with n_c = %d", ctx->n_c);
+    return qp_solve(ctx, H, g, Ct, dt, u_lo, u_hi, warm_U, warm_y, U, y, stats ? stats : ctx->d_stats,
+                    static_cast<cudaStream_t>(stream));
+}
+
+gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
+                      float* u0, gm_stats* stats, void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx && x_meas && U, "NULL argument");
+    GM_TRY(check_cost(ctx, cost, cons));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    gm_ctx* c = ctx;
+    GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
+    GM_TRY(gnn_jacobians(c, c->d_x_hat, c->d_u_hat, c->d_A, c->d_B, c->d_c, st));
+    const float* Cx = cons->Cx;
+    const float* dx = cons->dx;
+    if (cons->n_spheres > 0) {
+        GM_TRY(sphere_halfspaces(c, c->d_x_hat, cons->spheres, cons->n_spheres, c->d_Cx, c->d_dx, st));
+        Cx = c->d_Cx;
+        dx = c->d_dx;
+    }
+    GM_TRY(condense(c, c->d_x_hat, c->d_A, c->d_B, c->d_c, cost, Cx, dx, c->d_H, c->d_g, c->d_Ct, c->d_dt, st));
+    GM_TRY(qp_solve(c, c->d_H, c->d_g, c->d_Ct, c->d_dt, cons->u_lo, cons->u_hi, nullptr, nullptr, c->d_U,
+                    c->d_y, stats ? stats : c->d_stats, st));
+    GM_CUDA_TRY(cudaMemcpyAsync(U, c->d_U, sizeof(float) * c->nU, cudaMemcpyDeviceToDevice, st));
+    if (u0) GM_CUDA_TRY(cudaMemcpyAsync(u0, c->d_U, sizeof(float) * c->nu, cudaMemcpyDeviceToDevice, st));
+    GM_TRY(shift_inputs(c, c->d_U, c->d_u_hat, st));
+    return GM_OK;
+}
+
+}  // extern "C"
+
+namespace gmi {
+
+// Algorithm 1 "update lin. trajectory": u_hat_k = U*_{k+1} (k < N-1), u_hat_{N-1} = U*_{N-1}.
+__global__ void shift_kernel(int N, int nu, const float* __restrict__ U, float* __restrict__ u_hat) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * nu) return;
+    int k = t / nu, a = t % nu;
+    int src = k + 1 < N ? k + 1 : N - 1;
+    u_hat[t] = U[src * nu + a];
+}
+
+gm_status shift_inputs(gm_ctx* c, const float* U, float* u_hat, cudaStream_t st) {
+    shift_kernel<<<cdiv(c->N * c->nu, 128), 128, 0, st>>>(c->N, c->nu, U, u_hat);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
+}  // namespace gmi

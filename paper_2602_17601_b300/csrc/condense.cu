@@ -1,0 +1,282 @@
+// Condensing (Thm. 1 proof): per-node recursion for Gamma_u^i, Gamma_x^i
+// (Eq. sparse_gamma_i_u, Eq. sparse_gamma_i_xb), per-node aggregation of H
+// and g (Eq. H, Eq. g) and the stacked constraint rows C~^i, d~^i.  FP32.
+//
+// Gamma_u is kept stage-major and packed: stage k (1..N) holds, for every node
+// i and state component a, the k nu non-zero columns of block row k of
+// Gamma_u^i.  Stage k reads stage k-1 of the nodes in the K-hop neighbourhood
+// of i only, so one stage costs O(M) (Thm. 1).
+#include "ctx.h"
+#include "kernels.h"
+
+namespace gmi {
+
+__global__ void sphere_kernel(int N, int M, int S, const float* __restrict__ x_hat,
+                              const float* __restrict__ spheres, float* __restrict__ Cx,
+                              float* __restrict__ dx) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)N * M * S) return;
+    int s = (int)(t % S);
+    long ki = t / S;
+    int i = (int)(ki % M);
+    int k = (int)(ki / M) + 1;                 // stages 1..N
+    const float* p = x_hat + ((long)k * M + i) * 6;
+    float ox = spheres[s * 4 + 0], oy = spheres[s * 4 + 1], oz = spheres[s * 4 + 2];
+    float r = spheres[s * 4 + 3];
+    float dxv = p[0] - ox, dyv = p[1] - oy, dzv = p[2] - oz;
+    float nrm = sqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
+    float nx = 0.f, ny = 0.f, nz = 1.f;
+    if (nrm > 0.f) {
+        nx = dxv / nrm; ny = dyv / nrm; nz = dzv / nrm;
+    }
+    // keep p on the far side of the tangent plane: -n'p <= -r - n'o
+    Cx[t * 3 + 0] = -nx;
+    Cx[t * 3 + 1] = -ny;
+    Cx[t * 3 + 2] = -nz;
+    dx[t] = -r - (nx * ox + ny * oy + nz * oz);
+}
+
+gm_status sphere_halfspaces(gm_ctx* c, const float* x_hat, const float* spheres, int S, float* Cx,
+                            float* dx, cudaStream_t st) {
+    long n = (long)c->N * c->M * S;
+    if (n == 0) return GM_OK;
+    sphere_kernel<<<cdiv(n, 256), 256, 0, st>>>(c->N, c->M, S, x_hat, spheres, Cx, dx);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
+__host__ __device__ static inline long gu_offset(int M, int nu, int k) {   // start of stage k (k >= 1)
+    return (long)M * 6 * nu * ((long)k * (k - 1) / 2);
+}
+
+// Stage k -> k+1 for one node per block:
+//   (Gamma_u^i)_{k+1} last block row = [sum_j A^{ij}_k (Gamma_u^j)_k last row , B^i_k]
+//   (Gamma_x^i)_{k+1} last block     =  sum_j A^{ij}_k (Gamma_x^j)_k last block + c^i_k
+__global__ void recursion_kernel(int k, int M, int nu, const int* __restrict__ row_ptr,
+                                 const int* __restrict__ col, const float* __restrict__ A,
+                                 const float* __restrict__ B, const float* __restrict__ cvec,
+                                 const float* __restrict__ Gu_k, const float* __restrict__ Gx_k,
+                                 float* __restrict__ Gu_k1, float* __restrict__ Gx_k1) {
+    extern __shared__ float sA[];
+    const int i = blockIdx.x;
+    const int b0 = row_ptr[i], nb = row_ptr[i + 1] - b0;
+    int* sj = reinterpret_cast<int*>(sA + nb * 36);
+    for (int t = threadIdx.x; t < nb * 36; t += blockDim.x) sA[t] = A[(long)b0 * 36 + t];
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) sj[t] = col[b0 + t];
+    __syncthreads();
+    const int Lk = k * nu, Lk1 = (k + 1) * nu;
+    for (int cc = threadIdx.x; cc <= Lk1; cc += blockDim.x) {
+        float o[6] = {0, 0, 0, 0, 0, 0};
+        if (cc < Lk) {
+            for (int b = 0; b < nb; ++b) {
+                const int j = sj[b];
+#pragma unroll
+                for (int t = 0; t < 6; ++t) {
+                    const float s = Gu_k[((long)j * 6 + t) * Lk + cc];
+#pragma unroll
+                    for (int a = 0; a < 6; ++a) o[a] = fmaf(sA[b * 36 + a * 6 + t], s, o[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 6; ++a) Gu_k1[((long)i * 6 + a) * Lk1 + cc] = o[a];
+        } else if (cc < Lk1) {
+#pragma unroll
+            for (int a = 0; a < 6; ++a)
+                Gu_k1[((long)i * 6 + a) * Lk1 + cc] = B[((long)i * 6 + a) * nu + (cc - Lk)];
+        } else {
+#pragma unroll
+            for (int a = 0; a < 6; ++a) o[a] = cvec[(long)i * 6 + a];
+            for (int b = 0; b < nb; ++b) {
+                const int j = sj[b];
+#pragma unroll
+                for (int t = 0; t < 6; ++t) {
+                    const float s = Gx_k[(long)j * 6 + t];
+#pragma unroll
+                    for (int a = 0; a < 6; ++a) o[a] = fmaf(sA[b * 36 + a * 6 + t], s, o[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 6; ++a) Gx_k1[(long)i * 6 + a] = o[a];
+        }
+    }
+}
+
+// Gram matrices over packed stage-major rows: G = sum_rows w_r x_r x_r^T, where a
+// stage-k row has k nu leading non-zeros.  Tile (ti, tj), ti >= tj, 32 x 32 per
+// block; the rows of each contributing stage are split over gridDim.y.
+__global__ void gram_kernel(GramRows R, int n, float* __restrict__ part) {
+    const int T = (n + 31) / 32;
+    int lt = blockIdx.x, ti = 0;
+    while (lt > ti) { lt -= ti + 1; ++ti; }
+    const int tj = lt;
+    const int nsplit = gridDim.y, sp = blockIdx.y;
+    __shared__ float X1[32][33], X2[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 8 x 32
+    float acc[4] = {0, 0, 0, 0};
+    const int kmin = (ti * 32) / R.nu + 1;   // stage k contributes iff k nu > ti*32
+    for (int k = kmin; k <= R.N; ++k) {
+        const int L = k * R.nu;
+        const long base = (long)R.rows_per_stage * R.nu * ((long)k * (k - 1) / 2);
+        const int per = (R.rows_per_stage + nsplit - 1) / nsplit;
+        const int r0 = sp * per, r1 = min(R.rows_per_stage, r0 + per);
+        for (int rb = r0; rb < r1; rb += 32) {
+            for (int t = threadIdx.x; t < 32 * 32; t += 256) {
+                const int rr = t / 32, cc = t % 32;
+                const int r = rb + rr;
+                float w = 0.f, v1 = 0.f, v2 = 0.f;
+                if (r < r1) {
+                    w = R.wts ? R.wts[(long)k * R.rows_per_stage + r] : 1.f;
+                    const int c1 = ti * 32 + cc, c2 = tj * 32 + cc;
+                    const float* xr = R.X + base + (long)r * L;
+                    if (c1 < L) v1 = xr[c1];
+                    if (c2 < L) v2 = xr[c2];
+                }
+                X1[rr][cc] = v1 * w;
+                X2[rr][cc] = v2;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const float b = X2[rr][tx];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = fmaf(X1[rr][ty * 4 + q], b, acc[q]);
+            }
+            __syncthreads();
+        }
+    }
+    float* P = part + ((long)sp * T * T + (long)ti * T + tj) * 1024;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) P[(ty * 4 + q) * 32 + tx] = acc[q];
+}
+
+// G[c1][c2] = sum over splits (lower tiles, mirrored) + diag_add[c1] on the diagonal.
+__global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
+                                   const float* __restrict__ diag_add, float diag_scale,
+                                   float* __restrict__ G) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)n * n) return;
+    int c1 = (int)(t / n), c2 = (int)(t % n);
+    int a = c1 >= c2 ? c1 : c2, b = c1 >= c2 ? c2 : c1;     // lower-triangle element (a, b)
+    const int T = (n + 31) / 32;
+    int ti = a / 32, tj = b / 32;
+    float s = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp)
+        s += part[((long)sp * T * T + (long)ti * T + tj) * 1024 + (a % 32) * 32 + (b % 32)];
+    if (c1 == c2 && diag_add) s += diag_scale * diag_add[c1];
+    G[t] = s;
+}
+
+gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, float diag_scale,
+               float* G, cudaStream_t st) {
+    const int n = c->nU;
+    const int T = (n + 31) / 32;
+    dim3 grid(T * (T + 1) / 2, nsplit);
+    gram_kernel<<<grid, 256, 0, st>>>(R, n, c->d_gram_part);
+    GM_LAUNCH_CHECK();
+    gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, c->d_gram_part, diag_add,
+                                                              diag_scale, G);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
+// g = -Rbar u_ref + sum_k sum_{i,a} Gu_k[i,a]^T Q^i_k[a] (Gx_k[i,a] - x_ref_k[i,a])
+__global__ void grad_kernel(int n, int M, int nu, int N, const float* __restrict__ Gu,
+                            const float* __restrict__ Gx, const float* __restrict__ Q,
+                            const float* __restrict__ xr, float* __restrict__ part) {
+    const int sp = blockIdx.x, nsplit = gridDim.x;
+    const int rows = M * 6;
+    for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
+        float acc = 0.f;
+        const int kmin = cc / nu + 1;
+        for (int k = kmin; k <= N; ++k) {
+            const int L = k * nu;
+            const long base = gu_offset(M, nu, k);
+            const int per = (rows + nsplit - 1) / nsplit;
+            const int r0 = sp * per, r1 = min(rows, r0 + per);
+            for (int r = r0; r < r1; ++r) {
+                const long qi = (long)k * rows + r;
+                const float w = Q[qi] * (Gx[qi] - xr[qi]);
+                if (w != 0.f) acc = fmaf(Gu[base + (long)r * L + cc], w, acc);
+            }
+        }
+        part[(long)sp * n + cc] = acc;
+    }
+}
+
+__global__ void grad_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
+                                   const float* __restrict__ Rd, const float* __restrict__ ur,
+                                   float* __restrict__ g) {
+    int cc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cc >= n) return;
+    float s = -Rd[cc] * ur[cc];
+    for (int sp = 0; sp < nsplit; ++sp) s += part[(long)sp * n + cc];
+    g[cc] = s;
+}
+
+// C~ row (k, i, c) = C^{x,i}_k[c] . Gamma_u^i position rows of stage k; d~ = d - C . Gamma_x position.
+// One warp per (k, i).
+__global__ void constraint_kernel(int N, int M, int nu, int n_c, const float* __restrict__ Gu,
+                                  const float* __restrict__ Gx, const float* __restrict__ Cx,
+                                  const float* __restrict__ dx, float* __restrict__ Ct,
+                                  float* __restrict__ dt) {
+    const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (long)N * M) return;
+    const int k = (int)(w / M) + 1, i = (int)(w % M);
+    const int L = k * nu;
+    const float* g0 = Gu + gu_offset(M, nu, k) + (long)i * 6 * L;
+    const long cbase = (long)M * n_c * nu * ((long)k * (k - 1) / 2);
+    for (int cc = 0; cc < n_c; ++cc) {
+        const long crow = (((long)(k - 1) * M + i) * n_c + cc);
+        const float a0 = Cx[crow * 3 + 0], a1 = Cx[crow * 3 + 1], a2 = Cx[crow * 3 + 2];
+        float* out = Ct + cbase + (long)(i * n_c + cc) * L;
+        for (int col = lane; col < L; col += 32)
+            out[col] = a0 * g0[col] + a1 * g0[L + col] + a2 * g0[2 * L + col];
+        if (lane == 0) {
+            const float* gx = Gx + ((long)k * M + i) * 6;
+            dt[crow] = dx[crow] - (a0 * gx[0] + a1 * gx[1] + a2 * gx[2]);
+        }
+    }
+}
+
+gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B, const float* cvec,
+                   const gm_cost* cost, const float* Cx, const float* dx, float* H, float* g,
+                   float* Ct, float* dt, cudaStream_t st) {
+    const int M = c->M, nu = c->nu, N = c->N;
+    // Gamma_x stage 0 is the measured state (x_hat_0)
+    GM_CUDA_TRY(cudaMemcpyAsync(c->d_Gx, x_hat, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, st));
+    int maxnb = 0;
+    for (int i = 0; i < M; ++i) maxnb = std::max(maxnb, c->jac_row_ptr[i + 1] - c->jac_row_ptr[i]);
+    const size_t smem = (size_t)maxnb * 36 * sizeof(float) + (size_t)maxnb * sizeof(int);
+    for (int k = 0; k < N; ++k) {
+        const float* Guk = k > 0 ? c->d_Gu + gu_offset(M, nu, k) : nullptr;
+        recursion_kernel<<<M, 128, smem, st>>>(
+            k, M, nu, c->dc.nr_ptr_K, c->d_jac_col, A + (long)k * c->nnzb * 36,
+            B + (long)k * M * 6 * nu, cvec + (long)k * M * 6, Guk, c->d_Gx + (long)k * M * 6,
+            c->d_Gu + gu_offset(M, nu, k + 1), c->d_Gx + (long)(k + 1) * M * 6);
+        GM_LAUNCH_CHECK();
+    }
+    // Eq. H: sum of per-node local Hessians + Rbar
+    GramRows R{c->d_Gu, M * 6, nu, N, cost->Qdiag};
+    const int T = (c->nU + 31) / 32;
+    const int nsplit = std::max(1, std::min(64, (2 * c->num_sms) / std::max(1, T * (T + 1) / 2)));
+    GM_TRY(gram(c, R, nsplit, cost->Rdiag, 1.f, H, st));
+    // Eq. g
+    const int gsplit = std::max(1, std::min(4 * c->num_sms, M * 6 / 8));
+    grad_kernel<<<gsplit, 256, 0, st>>>(c->nU, M, nu, N, c->d_Gu, c->d_Gx, cost->Qdiag, cost->x_ref,
+                                       c->d_gram_part);
+    GM_LAUNCH_CHECK();
+    grad_reduce_kernel<<<cdiv(c->nU, 128), 128, 0, st>>>(c->nU, gsplit, c->d_gram_part, cost->Rdiag,
+                                                        cost->u_ref, g);
+    GM_LAUNCH_CHECK();
+    // stacked constraints
+    if (c->n_c > 0) {
+        const long warps = (long)N * M;
+        constraint_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(N, M, nu, c->n_c, c->d_Gu, c->d_Gx,
+                                                                Cx, dx, Ct, dt);
+        GM_LAUNCH_CHECK();
+    }
+    return GM_OK;
+}
+
+}  // namespace gmi

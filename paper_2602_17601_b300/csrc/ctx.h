@@ -1,0 +1,118 @@
+// Internal state of graphs, GNN models and contexts, shared by the .cu files.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+struct gm_graph {
+    int M = 0, E = 0, nu = 0;
+    std::vector<int> src, dst;      // edges sorted by (dst, src)
+    std::vector<int> in_ptr;        // [M+1] CSR by destination
+    std::vector<int> act_node;      // [nu]
+};
+
+struct gm_gnn {
+    gm_gnn_desc d{};
+    std::vector<float> blob;
+};
+
+namespace gmi {
+
+// One 2-layer MLP as stored on the device (offsets into the weight array).
+struct MlpOff {
+    int in = 0, hid = 0, out = 0;
+    long W1 = 0, b1 = 0, W2 = 0, b2 = 0;   // forward: W1 [in][hid], W2 [hid][out]
+    long W2t = 0;                           // backward GEMM1 operand: W2^T [out][hid]
+    long W1t = 0;                           // backward GEMM2 operand: W1^T [hid][in]
+    // edge-update MLPs only: the split of W1 by input block [h_dst | h_src | e]
+    long Wc = 0;                            // [hid][W]:  Wc[j][n]  = W1[2W + n][j]
+    long Bab = 0;                           // [2W][W]:   Bab[j][n] = W1[n][j], Bab[W+j][n] = W1[W+n][j]
+};
+
+// Rows of the reverse-mode cones (one seed = one output node s, 3 cotangent
+// channels for dv^s).  Level r holds the pairs (s, n) with n reaching s in at
+// most r edges (NR_r), and the edges into those nodes (ER_r).
+struct Cones {
+    int K = 0;
+    std::vector<std::vector<int>> nr_node, nr_seed, nr_ptr, nr_prev;  // r = 0..K
+    std::vector<std::vector<int>> er_edge, er_dstrow, er_srcrow, er_prev;  // r = 0..K-1
+    std::vector<std::vector<int>> er_dst_ptr;              // [|NR_r|+1] rows of ER_r per NR_r row
+    std::vector<std::vector<int>> er_src_ptr, er_src_list; // CSR: NR_{r+1} row -> ER_r rows
+    // encoder level: ER_{K-1} rows grouped by the NR_K row of their dst
+    std::vector<int> enc_dst_ptr, enc_dst_list;            // CSR: NR_K row -> ER_{K-1} rows
+    std::vector<int> b_row;                                // [M][nu] NR_K row of (s, act_node[a]) or -1
+};
+
+// Device copies of the cone arrays.
+struct DCones {
+    int* nr_node[8];
+    int* nr_prev[8];
+    int* er_edge[8];
+    int* er_dstrow[8];
+    int* er_prev[8];
+    int* er_dst_ptr[8];
+    int* er_src_ptr[8];
+    int* er_src_list[8];
+    int* enc_dst_ptr;
+    int* enc_dst_list;
+    int* nr_ptr_K;       // per-seed offsets of NR_K = Jacobian pattern row_ptr
+    int* b_row;
+    int nr_count[8];
+    int er_count[8];
+};
+
+}  // namespace gmi
+
+struct gm_ctx {
+    gm_settings s{};
+    int M = 0, E = 0, nu = 0, K = 0, W = 0, N = 0, nU = 0, n_c = 0;
+    float dt = 0.f;
+    long rows_c = 0;          // N * M * n_c
+    long ct_len = 0;          // packed C~ length
+    int num_sms = 0;
+    int stage_chunk = 1;      // stages per reverse-pass launch group
+
+    // host copies
+    gm_graph graph;
+    std::vector<float> wts_host;
+    std::vector<int> jac_row_ptr, jac_col;
+    gmi::Cones cones;
+    std::vector<gmi::MlpOff> mlp;   // blob order: ne, ee, (em, nm) x K, dec
+    int nnzb = 0;
+
+    // device pointers carved from the workspace
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int *d_src = nullptr, *d_dst = nullptr, *d_in_ptr = nullptr, *d_act = nullptr;
+    int *d_jac_col = nullptr;
+    float* d_wts = nullptr;
+    gmi::DCones dc{};
+    // rollout
+    float *d_h = nullptr, *d_e = nullptr, *d_agg = nullptr;
+    uint32_t *d_mask_node = nullptr, *d_mask_edge = nullptr;   // [N][layers][units][W/32]
+    // reverse pass (per stage chunk)
+    float *d_dhA = nullptr, *d_dhB = nullptr, *d_dacc = nullptr, *d_dagg = nullptr;
+    float *d_deA = nullptr, *d_deB = nullptr, *d_ehid = nullptr;
+    float *d_dxn = nullptr, *d_dd = nullptr;
+    // step state
+    float *d_u_hat = nullptr, *d_x_hat = nullptr, *d_A = nullptr, *d_B = nullptr, *d_c = nullptr;
+    float *d_Cx = nullptr, *d_dx = nullptr;
+    float *d_Gu = nullptr, *d_Gx = nullptr;
+    float *d_H = nullptr, *d_g = nullptr, *d_Ct = nullptr, *d_dt = nullptr;
+    float *d_U = nullptr, *d_y = nullptr, *d_z = nullptr;
+    float *d_gram_part = nullptr;
+    double *d_L = nullptr, *d_Linv = nullptr;
+    float *d_P = nullptr, *d_Pinv = nullptr;
+    float *d_acc = nullptr;      // ADMM reduction buffers [3][2 nU + 2]
+    unsigned* d_bar = nullptr;   // grid barrier counters
+    int* d_status = nullptr;     // device status word(s)
+    int* d_row_begin = nullptr;  // ADMM row partition [grid+1]
+    double* d_kkt = nullptr;     // KKT accumulators
+    double* d_pol = nullptr;     // polish scratch (FP64)
+    int* d_pol_idx = nullptr;
+    float* d_U_pol = nullptr;
+    float* d_y_pol = nullptr;
+    gm_stats* d_stats = nullptr; // internal stats when the caller passes none
+    int admm_grid = 0;
+};

@@ -1,0 +1,700 @@
+// GNN rollout (Eq. forward_dynamics) and exact local Jacobians by reverse mode
+// over per-node cones (Eq. linearized_dynamics), FP32 SIMT form.
+//
+// Every layer of the encode-process-decode GNN is a 2-layer MLP whose input
+// rows are gathered from node / edge latents.  One fused kernel computes
+//     hid = relu(X W1 + b1)  (forward, ReLU mask saved as bits)
+//     hid = (X W2^T) * mask  (reverse, mask of the unit the row belongs to)
+// followed by the second product and a layer-specific epilogue (residual,
+// scatter into the next level, Euler update).
+//
+// Reverse mode: the Jacobian row block of node s (dv^s, 3 outputs) is the
+// cotangent of 3 seeds e_0, e_1, e_2 at s's decoder output pulled back through
+// the layers.  At MP step l the cotangent is non-zero only on the nodes that
+// reach s in at most K-l edges and on the edges into them (the cone of s); the
+// rows of every level are the (seed, unit) pairs of all cones, precomputed on
+// the host.  This differentiates each subsystem's local dynamics independently
+// (Sec. V-A "Linearization") with work proportional to the cone sizes.
+#include "ctx.h"
+#include "kernels.h"
+
+namespace gmi {
+
+constexpr int BM = 64;
+constexpr int BK = 16;
+constexpr int NT = 128;   // threads per block: 8 row groups x 16 column groups
+
+template <int W>
+struct TileShape {
+    static constexpr int TN = W / 16;
+    static constexpr int VEC = TN < 4 ? TN : 4;
+    static constexpr int NH = TN / VEC;
+    __device__ static int col(int tx, int j) { return tx * VEC + (j % VEC) + (j / VEC) * 16 * VEC; }
+};
+
+struct RowCtx {
+    int a, b, c, d, e, f;
+};
+
+// Fused MLP kernel.  Op provides:
+//   rows, kin, nout, B1 [kin][W], b1 (nullable), B2 [W][nout], b2 (nullable)
+//   prep(row) -> RowCtx, in(ctx, k), out(ctx, n, v)
+//   kMode: 0 forward (bias+ReLU, store mask bits), 1 reverse (gathered mask), 2 single GEMM
+//   kStoreHid: store the masked hidden row (reverse only)
+template <int W, class Op>
+__global__ void __launch_bounds__(NT) mlp2_kernel(Op op) {
+    using T = TileShape<W>;
+    constexpr int TM = 8;
+    __shared__ __align__(16) float As[BK][BM];
+    __shared__ __align__(16) float Bs[BK][W];
+    __shared__ __align__(16) float Hs[BM][W + 4];
+    __shared__ RowCtx rc[BM];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long row0 = (long)blockIdx.x * BM;
+    const long rows = op.rows;
+    for (int m = tid; m < BM; m += NT) rc[m] = op.prep(row0 + m < rows ? row0 + m : -1);
+    __syncthreads();
+
+    float acc[TM][T::TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < T::TN; ++j) acc[i][j] = 0.f;
+
+    const int kin = op.kin;
+    for (int k0 = 0; k0 < kin; k0 += BK) {
+        for (int t = tid; t < BM * BK; t += NT) {
+            int m = t / BK, kk = t % BK;
+            float v = 0.f;
+            if (row0 + m < rows && k0 + kk < kin) v = op.in(rc[m], k0 + kk);
+            As[kk][m] = v;
+        }
+        for (int t = tid; t < BK * W; t += NT) {
+            int kk = t / W, n = t % W;
+            Bs[kk][n] = (k0 + kk < kin) ? op.B1[(long)(k0 + kk) * W + n] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[TM], b[T::TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+            for (int j = 0; j < T::TN; ++j) b[j] = Bs[kk][T::col(tx, j)];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < T::TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+    if constexpr (Op::kMode == 2) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            int m = ty * TM + i;
+            if (row0 + m >= rows) continue;
+#pragma unroll
+            for (int j = 0; j < T::TN; ++j) {
+                int n = T::col(tx, j);
+                if (n < op.nout) op.out(rc[m], n, acc[i][j]);
+            }
+        }
+        return;
+    } else {
+        // hidden layer: bias + ReLU (forward) or the saved mask (reverse)
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            int m = ty * TM + i;
+#pragma unroll
+            for (int j = 0; j < T::TN; ++j) {
+                int n = T::col(tx, j);
+                float v = acc[i][j];
+                if constexpr (Op::kMode == 0) {
+                    v += op.b1[n];
+                    v = v > 0.f ? v : 0.f;
+                } else {
+                    uint32_t w = (row0 + m < rows) ? op.mask_word(rc[m], n >> 5) : 0u;
+                    v = ((w >> (n & 31)) & 1u) ? v : 0.f;
+                }
+                Hs[m][n] = v;
+            }
+        }
+        __syncthreads();
+        if constexpr (Op::kMode == 0) {
+            for (int t = tid; t < BM * (W / 32); t += NT) {
+                int m = t / (W / 32), wd = t % (W / 32);
+                if (row0 + m >= rows) continue;
+                uint32_t bits = 0;
+#pragma unroll
+                for (int b = 0; b < 32; ++b) bits |= (Hs[m][wd * 32 + b] > 0.f ? 1u : 0u) << b;
+                op.store_mask(rc[m], wd, bits);
+            }
+        }
+        if constexpr (Op::kStoreHid) {
+            for (int t = tid; t < BM * W; t += NT) {
+                int m = t / W, n = t % W;
+                if (row0 + m < rows) op.store_hid(rc[m], n, Hs[m][n]);
+            }
+        }
+        const int nout = op.nout;
+        for (int n0 = 0; n0 < nout; n0 += W) {
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < T::TN; ++j) acc[i][j] = 0.f;
+            for (int k0 = 0; k0 < W; k0 += BK) {
+                for (int t = tid; t < BK * W; t += NT) {
+                    int kk = t / W, n = t % W;
+                    Bs[kk][n] = (n0 + n < nout) ? op.B2[(long)(k0 + kk) * nout + n0 + n] : 0.f;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    float a[TM], b[T::TN];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i) a[i] = Hs[ty * TM + i][k0 + kk];
+#pragma unroll
+                    for (int j = 0; j < T::TN; ++j) b[j] = Bs[kk][T::col(tx, j)];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < T::TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                int m = ty * TM + i;
+                if (row0 + m >= rows) continue;
+#pragma unroll
+                for (int j = 0; j < T::TN; ++j) {
+                    int n = n0 + T::col(tx, j);
+                    if (n < nout) {
+                        float v = acc[i][j];
+                        if (op.b2) v += op.b2[n];
+                        op.out(rc[m], n, v);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ======================================================================= forward ops
+struct FwdBase {
+    static constexpr int kMode = 0;
+    static constexpr bool kStoreHid = false;
+    long rows;
+    int kin, nout;
+    const float *B1, *b1, *B2, *b2;
+    uint32_t* mask;   // [units][W/32] of this layer and stage
+    int wwords;
+    __device__ void store_mask(const RowCtx& c, int wd, uint32_t bits) const {
+        mask[(long)c.a * wwords + wd] = bits;
+    }
+    __device__ void store_hid(const RowCtx&, int, float) const {}
+    __device__ uint32_t mask_word(const RowCtx&, int) const { return 0u; }
+};
+
+struct NodeEncFwd : FwdBase {
+    const float* x;      // [M][6]
+    const float* u;      // [nu]
+    const int* act;      // [nu]
+    float* h;            // [M][W]
+    int W, nu;
+    __device__ RowCtx prep(long r) const { return RowCtx{(int)r, 0, 0, 0, 0, 0}; }
+    __device__ float in(const RowCtx& c, int k) const {
+        if (k < 6) return x[c.a * 6 + k];
+        int a = k - 6;
+        return act[a] == c.a ? u[a] : 0.f;
+    }
+    __device__ void out(const RowCtx& c, int n, float v) const { h[(long)c.a * W + n] = v; }
+};
+
+struct EdgeEncFwd : FwdBase {
+    const float* x;
+    const int *src, *dst;
+    float* e;
+    int W;
+    __device__ RowCtx prep(long r) const {
+        return r < 0 ? RowCtx{0, 0, 0, 0, 0, 0} : RowCtx{(int)r, src[r], dst[r], 0, 0, 0};
+    }
+    __device__ float in(const RowCtx& c, int k) const { return x[c.c * 6 + k] - x[c.b * 6 + k]; }
+    __device__ void out(const RowCtx& c, int n, float v) const { e[(long)c.a * W + n] = v; }
+};
+
+struct EdgeMpFwd : FwdBase {
+    const float* h;
+    const int *src, *dst;
+    float* e;
+    int W;
+    __device__ RowCtx prep(long r) const {
+        return r < 0 ? RowCtx{0, 0, 0, 0, 0, 0} : RowCtx{(int)r, src[r], dst[r], 0, 0, 0};
+    }
+    __device__ float in(const RowCtx& c, int k) const {
+        if (k < W) return h[(long)c.c * W + k];
+        if (k < 2 * W) return h[(long)c.b * W + k - W];
+        return e[(long)c.a * W + k - 2 * W];
+    }
+    // residual update in place: the block's own rows were fully read by GEMM1
+    __device__ void out(const RowCtx& c, int n, float v) const { e[(long)c.a * W + n] += v; }
+};
+
+struct NodeMpFwd : FwdBase {
+    float* h;
+    const float* agg;
+    int W;
+    __device__ RowCtx prep(long r) const { return RowCtx{(int)r, 0, 0, 0, 0, 0}; }
+    __device__ float in(const RowCtx& c, int k) const {
+        return k < W ? h[(long)c.a * W + k] : agg[(long)c.a * W + k - W];
+    }
+    __device__ void out(const RowCtx& c, int n, float v) const { h[(long)c.a * W + n] += v; }
+};
+
+struct DecFwd : FwdBase {
+    const float* h;
+    const float* x;      // [M][6] stage k
+    float* xn;           // [M][6] stage k+1
+    float dt;
+    int W;
+    __device__ RowCtx prep(long r) const { return RowCtx{(int)r, 0, 0, 0, 0, 0}; }
+    __device__ float in(const RowCtx& c, int k) const { return h[(long)c.a * W + k]; }
+    __device__ void out(const RowCtx& c, int n, float dv) const {
+        // semi-implicit Euler: v+ = v + dv, p+ = p + dt v+
+        float v1 = x[c.a * 6 + 3 + n] + dv;
+        xn[c.a * 6 + 3 + n] = v1;
+        xn[c.a * 6 + n] = x[c.a * 6 + n] + dt * v1;
+    }
+};
+
+__global__ void agg_kernel(int M, int W, const int* __restrict__ in_ptr, const float* __restrict__ e,
+                           float* __restrict__ agg) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)M * W) return;
+    int n = (int)(t / W), c = (int)(t % W);
+    float s = 0.f;
+    for (int q = in_ptr[n]; q < in_ptr[n + 1]; ++q) s += e[(long)q * W + c];
+    agg[t] = s;
+}
+
+template <class Op>
+static gm_status launch_mlp(int W, const Op& op, cudaStream_t st) {
+    if (op.rows <= 0) return GM_OK;
+    int grid = cdiv(op.rows, BM);
+    switch (W) {
+        case 32: mlp2_kernel<32, Op><<<grid, NT, 0, st>>>(op); break;
+        case 64: mlp2_kernel<64, Op><<<grid, NT, 0, st>>>(op); break;
+        case 128: mlp2_kernel<128, Op><<<grid, NT, 0, st>>>(op); break;
+        default: set_error("unsupported W %d", W); return GM_ERR_INVALID_ARG;
+    }
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
+template <class Op>
+static void fill_fwd(Op& op, const gm_ctx* c, int mlp_idx, long rows, uint32_t* mask) {
+    const MlpOff& m = c->mlp[mlp_idx];
+    op.rows = rows;
+    op.kin = m.in;
+    op.nout = m.out;
+    op.B1 = c->d_wts + m.W1;
+    op.b1 = c->d_wts + m.b1;
+    op.B2 = c->d_wts + m.W2;
+    op.b2 = c->d_wts + m.b2;
+    op.mask = mask;
+    op.wwords = c->W / 32;
+}
+
+uint32_t* node_mask(const gm_ctx* c, int k, int layer) {
+    return c->d_mask_node + ((long)(k * (c->K + 2) + layer) * c->M) * (c->W / 32);
+}
+uint32_t* edge_mask(const gm_ctx* c, int k, int layer) {
+    return c->d_mask_edge + ((long)(k * (c->K + 1) + layer) * c->E) * (c->W / 32);
+}
+
+// x_hat[0] = x0; x_hat[k+1] = F(x_hat[k], u_hat[k]); ReLU masks of every layer kept.
+gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat,
+                      cudaStream_t st) {
+    const int M = c->M, E = c->E, W = c->W, K = c->K;
+    GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < c->N; ++k) {
+        const float* xk = x_hat + (long)k * M * 6;
+        float* xn = x_hat + (long)(k + 1) * M * 6;
+        NodeEncFwd ne{};
+        fill_fwd(ne, c, 0, M, node_mask(c, k, 0));
+        ne.x = xk; ne.u = u_hat + (long)k * c->nu; ne.act = c->d_act; ne.h = c->d_h; ne.W = W; ne.nu = c->nu;
+        GM_TRY(launch_mlp(W, ne, st));
+        if (E > 0) {
+            EdgeEncFwd ee{};
+            fill_fwd(ee, c, 1, E, edge_mask(c, k, 0));
+            ee.x = xk; ee.src = c->d_src; ee.dst = c->d_dst; ee.e = c->d_e; ee.W = W;
+            GM_TRY(launch_mlp(W, ee, st));
+        }
+        for (int t = 0; t < K; ++t) {
+            if (E > 0) {
+                EdgeMpFwd em{};
+                fill_fwd(em, c, 2 + 2 * t, E, edge_mask(c, k, 1 + t));
+                em.h = c->d_h; em.src = c->d_src; em.dst = c->d_dst; em.e = c->d_e; em.W = W;
+                GM_TRY(launch_mlp(W, em, st));
+                agg_kernel<<<cdiv((long)M * W, 256), 256, 0, st>>>(M, W, c->d_in_ptr, c->d_e, c->d_agg);
+                GM_LAUNCH_CHECK();
+            } else {
+                GM_CUDA_TRY(cudaMemsetAsync(c->d_agg, 0, sizeof(float) * M * W, st));
+            }
+            NodeMpFwd nm{};
+            fill_fwd(nm, c, 3 + 2 * t, M, node_mask(c, k, 1 + t));
+            nm.h = c->d_h; nm.agg = c->d_agg; nm.W = W;
+            GM_TRY(launch_mlp(W, nm, st));
+        }
+        DecFwd de{};
+        fill_fwd(de, c, 2 + 2 * K, M, node_mask(c, k, K + 1));
+        de.h = c->d_h; de.x = xk; de.xn = xn; de.dt = c->dt; de.W = W;
+        GM_TRY(launch_mlp(W, de, st));
+    }
+    return GM_OK;
+}
+
+// ======================================================================= reverse ops
+// Rows of a level are ((st * R + q) * 3 + ch): stage st of the chunk, level row q,
+// cotangent channel ch (component of dv^s).
+struct BwdBase {
+    static constexpr int kMode = 1;
+    static constexpr bool kStoreHid = false;
+    long rows;
+    int kin, nout;
+    const float *B1, *b1 = nullptr, *B2, *b2 = nullptr;
+    const uint32_t* mask;   // mask of stage k0: [layer units][W/32]; stage stride mstride
+    long mstride;
+    int wwords;
+    int R;                  // level row count
+    int W;
+    __device__ void store_mask(const RowCtx&, int, uint32_t) const {}
+    __device__ void store_hid(const RowCtx&, int, float) const {}
+    // RowCtx: a = st, b = q, c = ch, d = unit, e/f op-specific
+    __device__ void decode(long r, RowCtx& x) const {
+        x.c = (int)(r % 3);
+        long t = r / 3;
+        x.b = (int)(t % R);
+        x.a = (int)(t / R);
+    }
+    __device__ uint32_t mask_word(const RowCtx& x, int wd) const {
+        return mask[x.a * mstride + (long)x.d * wwords + wd];
+    }
+};
+
+struct DecBwd : BwdBase {
+    float* dh;                                  // [rows][W]
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, 0};
+        if (r < 0) return x;
+        decode(r, x);
+        x.d = x.b;                              // NR_0 row q is seed q
+        x.e = (int)r;
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int k) const { return k == x.c ? 1.f : 0.f; }
+    __device__ void out(const RowCtx& x, int n, float v) const { dh[(long)x.e * W + n] = v; }
+};
+
+struct NodeMpBwd : BwdBase {
+    const float* dh;       // Dh^l on NR_r
+    float* dacc;           // Dh^l + dh-part
+    float* dagg;           // agg-part
+    const int* nr_node;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, 0};
+        if (r < 0) return x;
+        decode(r, x);
+        x.d = nr_node[x.b];
+        x.e = (int)r;
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int k) const { return dh[(long)x.e * W + k]; }
+    __device__ void out(const RowCtx& x, int n, float v) const {
+        if (n < W) dacc[(long)x.e * W + n] = dh[(long)x.e * W + n] + v;
+        else dagg[(long)x.e * W + n - W] = v;
+    }
+};
+
+struct EdgeMpBwd : BwdBase {
+    static constexpr bool kStoreHid = true;
+    const float* dagg;       // on NR_r
+    const float* de_in;      // carry on ER_{r-1} (nullable)
+    float* ehid;             // on ER_r
+    float* de_out;           // carry on ER_r
+    const int *er_edge, *er_dstrow, *er_prev;
+    int Rn, Rp;              // |NR_r|, |ER_{r-1}|
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, 0};
+        if (r < 0) return x;
+        decode(r, x);
+        x.d = er_edge[x.b];
+        x.e = (x.a * Rn + er_dstrow[x.b]) * 3 + x.c;            // Dagg row
+        int p = er_prev[x.b];
+        x.f = p >= 0 ? (x.a * Rp + p) * 3 + x.c : -1;            // carry-in row
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int k) const {
+        float v = dagg[(long)x.e * W + k];
+        if (x.f >= 0) v += de_in[(long)x.f * W + k];
+        return v;
+    }
+    __device__ long self(const RowCtx& x) const { return ((long)x.a * R + x.b) * 3 + x.c; }
+    __device__ void store_hid(const RowCtx& x, int n, float v) const { ehid[self(x) * W + n] = v; }
+    __device__ void out(const RowCtx& x, int n, float v) const { de_out[self(x) * W + n] = in(x, n) + v; }
+};
+
+struct NodeSumBwd : BwdBase {
+    static constexpr int kMode = 2;
+    const float* ehid;       // on ER_r
+    const float* dacc;       // on NR_r
+    float* dh_next;          // on NR_{r+1}
+    const int *nr_prev, *dst_ptr, *src_ptr, *src_list;
+    int Rr, Re;              // |NR_r|, |ER_r|
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, 0};
+        if (r < 0) return x;
+        decode(r, x);
+        x.d = nr_prev[x.b];                                      // row in NR_r or -1
+        x.e = (int)r;
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int k) const {
+        float s = 0.f;
+        const long base = (long)x.a * Re;
+        if (k < W) {
+            if (x.d >= 0)
+                for (int p = dst_ptr[x.d]; p < dst_ptr[x.d + 1]; ++p)
+                    s += ehid[((base + p) * 3 + x.c) * W + k];
+        } else {
+            for (int p = src_ptr[x.b]; p < src_ptr[x.b + 1]; ++p)
+                s += ehid[((base + src_list[p]) * 3 + x.c) * W + k - W];
+        }
+        return s;
+    }
+    __device__ void out(const RowCtx& x, int n, float v) const {
+        float a = x.d >= 0 ? dacc[(((long)x.a * Rr + x.d) * 3 + x.c) * W + n] : 0.f;
+        dh_next[(long)x.e * W + n] = a + v;
+    }
+    __device__ uint32_t mask_word(const RowCtx&, int) const { return 0u; }
+};
+
+struct NodeEncBwd : BwdBase {
+    const float* dh;
+    float* dxn;              // [rows][nout]
+    const int* nr_node;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, 0};
+        if (r < 0) return x;
+        decode(r, x);
+        x.d = nr_node[x.b];
+        x.e = (int)r;
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int k) const { return dh[(long)x.e * W + k]; }
+    __device__ void out(const RowCtx& x, int n, float v) const { dxn[(long)x.e * nout + n] = v; }
+};
+
+struct EdgeEncBwd : BwdBase {
+    const float* de;
+    float* dd;               // [rows][6]
+    const int* er_edge;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, 0};
+        if (r < 0) return x;
+        decode(r, x);
+        x.d = er_edge[x.b];
+        x.e = (int)r;
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int k) const { return de[(long)x.e * W + k]; }
+    __device__ void out(const RowCtx& x, int n, float v) const { dd[(long)x.e * 6 + n] = v; }
+};
+
+// One warp per (stage, seed s): A^{s n}, B^s and c^s from the pulled-back cotangents.
+//   J[a][t] = d dv^s_a / d x^n_t = Dxn(s,n)[a][t] + sum_{edges into n} Dd - sum_{edges out of n} Dd
+//   velocity rows: J + [0 I]·delta_sn ; position rows: dt J + [I dt I]·delta_sn
+__global__ void jac_assemble_kernel(int Ns, int k0, int M, int nu, int K, float dt,
+                                    const int* __restrict__ nr_ptr_K, const int* __restrict__ nr_node_K,
+                                    const int* __restrict__ enc_dst_ptr, const int* __restrict__ enc_dst_list,
+                                    const int* __restrict__ src_ptr, const int* __restrict__ src_list,
+                                    const int* __restrict__ b_row, int RK, int RE,
+                                    const float* __restrict__ dxn, const float* __restrict__ dd,
+                                    const float* __restrict__ x_hat, const float* __restrict__ u_hat,
+                                    float* A, float* B, float* cvec, long nnzb) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= Ns * M) return;
+    const int st = warp / M, s = warp % M;
+    const int k = k0 + st;
+    const int ncol = 6 + nu;
+    const float* xk = x_hat + (long)k * M * 6;
+    const float* xk1 = x_hat + (long)(k + 1) * M * 6;
+    float cacc[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = nr_ptr_K[s] + lane; q < nr_ptr_K[s + 1]; q += 32) {
+        const int n = nr_node_K[q];
+        float J[3][6];
+        for (int a = 0; a < 3; ++a) {
+            const long row = ((long)st * RK + q) * 3 + a;
+            for (int t = 0; t < 6; ++t) J[a][t] = dxn[row * ncol + t];
+            for (int p = enc_dst_ptr[q]; p < enc_dst_ptr[q + 1]; ++p) {
+                const long er = ((long)st * RE + enc_dst_list[p]) * 3 + a;
+                for (int t = 0; t < 6; ++t) J[a][t] += dd[er * 6 + t];
+            }
+            for (int p = src_ptr[q]; p < src_ptr[q + 1]; ++p) {
+                const long er = ((long)st * RE + src_list[p]) * 3 + a;
+                for (int t = 0; t < 6; ++t) J[a][t] -= dd[er * 6 + t];
+            }
+        }
+        float blk[36];
+        const bool diag = (n == s);
+        for (int a6 = 0; a6 < 6; ++a6)
+            for (int t = 0; t < 6; ++t) {
+                float v;
+                if (a6 >= 3) {
+                    v = J[a6 - 3][t] + ((diag && t == a6) ? 1.f : 0.f);
+                } else {
+                    v = dt * J[a6][t];
+                    if (diag) v += (t == a6 ? 1.f : 0.f) + (t == a6 + 3 ? dt : 0.f);
+                }
+                blk[a6 * 6 + t] = v;
+            }
+        if (A) {
+            float* Ab = A + ((long)k * nnzb + q) * 36;
+            for (int i = 0; i < 36; ++i) Ab[i] = blk[i];
+        }
+        for (int a6 = 0; a6 < 6; ++a6) {
+            float acc = 0.f;
+            for (int t = 0; t < 6; ++t) acc += blk[a6 * 6 + t] * xk[n * 6 + t];
+            cacc[a6] += acc;
+        }
+    }
+    for (int a6 = 0; a6 < 6; ++a6)
+        for (int o = 16; o > 0; o >>= 1) cacc[a6] += __shfl_xor_sync(0xffffffffu, cacc[a6], o);
+    // B^s: the node-encoder cotangent of input channel 6 + a at the actuator's node
+    float bu[6] = {0, 0, 0, 0, 0, 0};
+    for (int a = lane; a < nu; a += 32) {
+        const int q = b_row[s * nu + a];
+        float col[6];
+        for (int ch = 0; ch < 3; ++ch) {
+            float v = q >= 0 ? dxn[(((long)st * RK + q) * 3 + ch) * ncol + 6 + a] : 0.f;
+            col[3 + ch] = v;
+            col[ch] = dt * v;
+        }
+        const float ua = u_hat[(long)k * nu + a];
+        for (int r6 = 0; r6 < 6; ++r6) {
+            if (B) B[(((long)k * M + s) * 6 + r6) * nu + a] = col[r6];
+            bu[r6] += col[r6] * ua;
+        }
+    }
+    for (int r6 = 0; r6 < 6; ++r6)
+        for (int o = 16; o > 0; o >>= 1) bu[r6] += __shfl_xor_sync(0xffffffffu, bu[r6], o);
+    if (lane == 0 && cvec) {
+        for (int r6 = 0; r6 < 6; ++r6)
+            cvec[((long)k * M + s) * 6 + r6] = xk1[s * 6 + r6] - cacc[r6] - bu[r6];
+    }
+}
+
+template <class Op>
+static void fill_bwd(Op& op, const gm_ctx* c, const MlpOff& m, int k0, int layer, bool edge,
+                     long rows, int R, int nout_override = -1) {
+    op.rows = rows;
+    op.kin = m.out;                      // reverse: input is the MLP's output cotangent
+    op.nout = nout_override >= 0 ? nout_override : m.in;
+    op.B1 = c->d_wts + m.W2t;
+    op.B2 = c->d_wts + m.W1t;
+    op.wwords = c->W / 32;
+    op.R = R;
+    op.W = c->W;
+    if (edge) {
+        op.mask = edge_mask(c, k0, layer);
+        op.mstride = (long)(c->K + 1) * c->E * (c->W / 32);
+    } else {
+        op.mask = node_mask(c, k0, layer);
+        op.mstride = (long)(c->K + 2) * c->M * (c->W / 32);
+    }
+}
+
+// Reverse pass over all stages (in chunks): A, B, c of Eq. linearized_dynamics.
+gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float* A, float* B,
+                        float* cvec, cudaStream_t st) {
+    const int K = c->K, W = c->W, M = c->M;
+    const DCones& d = c->dc;
+    for (int k0 = 0; k0 < c->N; k0 += c->stage_chunk) {
+        const int Ns = std::min(c->stage_chunk, c->N - k0);
+        float* X = c->d_dhA;
+        float* Y = c->d_dhB;
+        float* de_in = nullptr;
+        float* de_out = c->d_deA;
+        {   // decoder: seeds e_0, e_1, e_2 at dv^s
+            DecBwd op{};
+            fill_bwd(op, c, c->mlp[2 + 2 * K], k0, K + 1, false, (long)Ns * M * 3, M, W);
+            op.kin = 3;
+            op.dh = X;
+            GM_TRY(launch_mlp(W, op, st));
+        }
+        for (int t = K - 1; t >= 0; --t) {
+            const int r = K - 1 - t;
+            const int Rn = d.nr_count[r], Re = d.er_count[r];
+            {
+                NodeMpBwd op{};
+                fill_bwd(op, c, c->mlp[3 + 2 * t], k0, 1 + t, false, (long)Ns * Rn * 3, Rn, 2 * W);
+                op.dh = X; op.dacc = c->d_dacc; op.dagg = c->d_dagg; op.nr_node = d.nr_node[r];
+                GM_TRY(launch_mlp(W, op, st));
+            }
+            if (Re > 0) {
+                EdgeMpBwd op{};
+                const MlpOff& m = c->mlp[2 + 2 * t];
+                fill_bwd(op, c, m, k0, 1 + t, true, (long)Ns * Re * 3, Re, W);
+                op.B2 = c->d_wts + m.Wc;             // only the e-part of W1 (carry of e)
+                op.dagg = c->d_dagg; op.de_in = de_in; op.ehid = c->d_ehid; op.de_out = de_out;
+                op.er_edge = d.er_edge[r]; op.er_dstrow = d.er_dstrow[r]; op.er_prev = d.er_prev[r];
+                op.Rn = Rn; op.Rp = r > 0 ? d.er_count[r - 1] : 0;
+                GM_TRY(launch_mlp(W, op, st));
+            }
+            {
+                const int Rn1 = d.nr_count[r + 1];
+                NodeSumBwd op{};
+                const MlpOff& m = c->mlp[2 + 2 * t];
+                op.rows = (long)Ns * Rn1 * 3; op.kin = 2 * W; op.nout = W;
+                op.B1 = c->d_wts + m.Bab;            // [Sdst | Ssrc] -> dh
+                op.B2 = nullptr; op.wwords = W / 32; op.R = Rn1; op.W = W;
+                op.mask = nullptr; op.mstride = 0;
+                op.ehid = c->d_ehid; op.dacc = c->d_dacc; op.dh_next = Y;
+                op.nr_prev = d.nr_prev[r + 1]; op.dst_ptr = d.er_dst_ptr[r];
+                op.src_ptr = d.er_src_ptr[r]; op.src_list = d.er_src_list[r];
+                op.Rr = Rn; op.Re = Re;
+                GM_TRY(launch_mlp(W, op, st));
+            }
+            std::swap(X, Y);
+            de_in = de_out;
+            de_out = (de_out == c->d_deA) ? c->d_deB : c->d_deA;
+        }
+        {
+            const int RK = d.nr_count[K];
+            NodeEncBwd op{};
+            fill_bwd(op, c, c->mlp[0], k0, 0, false, (long)Ns * RK * 3, RK);
+            op.dh = X; op.dxn = c->d_dxn; op.nr_node = d.nr_node[K];
+            GM_TRY(launch_mlp(W, op, st));
+        }
+        const int RE = d.er_count[K - 1];
+        if (RE > 0) {
+            EdgeEncBwd op{};
+            fill_bwd(op, c, c->mlp[1], k0, 0, true, (long)Ns * RE * 3, RE);
+            op.de = de_in; op.dd = c->d_dd; op.er_edge = d.er_edge[K - 1];
+            GM_TRY(launch_mlp(W, op, st));
+        }
+        {
+            const long warps = (long)Ns * M;
+            jac_assemble_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(
+                Ns, k0, M, c->nu, K, c->dt, d.nr_ptr_K, d.nr_node[K], d.enc_dst_ptr,
+                d.enc_dst_list, d.er_src_ptr[K - 1], d.er_src_list[K - 1], d.b_row, d.nr_count[K],
+                RE, c->d_dxn, c->d_dd, x_hat, u_hat, A, B, cvec, c->nnzb);
+            GM_LAUNCH_CHECK();
+        }
+    }
+    return GM_OK;
+}
+
+}  // namespace gmi

@@ -1,0 +1,40 @@
+// Launchers shared between the .cu files of the library (internal).
+#pragma once
+
+#include "ctx.h"
+
+namespace gmi {
+
+// gnn.cu
+gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, cudaStream_t st);
+gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float* A, float* B,
+                        float* cvec, cudaStream_t st);
+
+// condense.cu
+// Packed stage-major rows (a stage-k row has k nu leading non-zeros) for Gram products.
+struct GramRows {
+    const float* X;         // packed rows
+    int rows_per_stage;     // rows of one stage (M*6 or M*n_c)
+    int nu, N;
+    const float* wts;       // [N+1][rows_per_stage] weights indexed by stage k (nullable: 1)
+};
+gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, float diag_scale,
+               float* G, cudaStream_t st);
+gm_status sphere_halfspaces(gm_ctx* c, const float* x_hat, const float* spheres, int S, float* Cx,
+                            float* dx, cudaStream_t st);
+gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B, const float* cvec,
+                   const gm_cost* cost, const float* Cx, const float* dx, float* H, float* g,
+                   float* Ct, float* dt, cudaStream_t st);
+
+// qp.cu
+gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, const float* dt,
+                   const float* u_lo, const float* u_hi, const float* warm_U, const float* warm_y,
+                   float* U, float* y, gm_stats* stats, cudaStream_t st);
+
+size_t admm_smem_bytes(const gm_ctx* c);
+const void* admm_kernel_ptr(const gm_ctx* c);
+
+// small device utilities (api.cu)
+gm_status shift_inputs(gm_ctx* c, const float* U, float* u_hat, cudaStream_t st);
+
+}  // namespace gmi

@@ -1,0 +1,123 @@
+"""A context plus its device-resident problem data, around the C entry points.
+
+RTIProblem allocates (with torch) the workspace and the device copies of the
+cost and constraint arrays, creates the graph / GNN / context handles, and
+exposes one method per C call.  It holds no arithmetic of the method.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import (GM_PREC_FP32, STATS_BYTES, gm_condense, gm_ctx_create, gm_ctx_destroy, gm_ctx_reset,
+               gm_ctx_workspace_size, gm_gnn_destroy, gm_gnn_load, gm_graph_create, gm_graph_destroy,
+               gm_jac_pattern, gm_linearize, gm_qp_solve, gm_rti_step, make_constr, make_cost,
+               make_settings, read_stats)
+
+
+class RTIProblem:
+    """Device state for one MPC instance.
+
+    Arguments mirror the paper's problem statement: graph (M, src, dst), inputs
+    (nu, act_node), GNN (K, W, dt, weight blob), horizon N, cost (Qdiag, Rdiag,
+    x_ref, u_ref), input box (u_lo, u_hi) and either explicit position
+    half-spaces (Cx, dx) or spheres linearised at the rollout.
+    """
+
+    def __init__(self, M, src, dst, nu, act_node, K, W, dt, blob, N, Qdiag, Rdiag, x_ref, u_ref, u_lo,
+                 u_hi, Cx=None, dx=None, spheres=None, rho=0.1, tol=1e-6, max_iter=4000,
+                 precision=GM_PREC_FP32, polish=0, timeout_spins=0, device="cuda"):
+        import torch
+        self.torch = torch
+        self.M, self.nu, self.N, self.K, self.W = int(M), int(nu), int(N), int(K), int(W)
+        self.nU = self.N * self.nu
+        f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=device)  # noqa: E731
+        self.spheres = None if spheres is None or len(spheres) == 0 else f32(spheres)
+        if self.spheres is not None:
+            n_c = int(self.spheres.shape[0])
+            self.Cx = self.dx = None
+        elif Cx is not None:
+            n_c = int(np.asarray(Cx).shape[2])
+            self.Cx, self.dx = f32(Cx), f32(dx)
+        else:
+            n_c = 0
+            self.Cx = self.dx = None
+        self.n_c = n_c
+        self.rows_c = self.N * self.M * n_c
+        self.ct_len = self.M * n_c * self.nu * self.N * (self.N + 1) // 2
+        self.graph = gm_graph_create(M, src, dst, nu, act_node)
+        self.gnn = gm_gnn_load(K, W, nu, dt, blob)
+        self.settings = make_settings(N, n_c, precision, rho, tol, max_iter, polish, timeout_spins)
+        nbytes = gm_ctx_workspace_size(self.graph, self.gnn, self.settings)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.ctx = gm_ctx_create(self.graph, self.gnn, self.settings, self.workspace)
+        self.Qdiag, self.Rdiag, self.x_ref, self.u_ref = f32(Qdiag), f32(Rdiag), f32(x_ref), f32(u_ref)
+        self.u_lo, self.u_hi = f32(u_lo), f32(u_hi)
+        self.cost = make_cost(self.Qdiag, self.Rdiag, self.x_ref, self.u_ref)
+        self.constr = make_constr(self.u_lo, self.u_hi, self.Cx, self.dx, self.spheres)
+        self.row_ptr, self.col = gm_jac_pattern(self.ctx, self.M)
+        self.nnzb = int(self.col.size)
+        self.stats = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=device)
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        """Build from any object with the workload attributes (see synth.Workload)."""
+        args = dict(rho=wl.rho, tol=wl.tol, max_iter=wl.max_iter)
+        args.update(kw)
+        return cls(wl.M, wl.src, wl.dst, wl.nu, wl.act_node, wl.K, wl.W, wl.dt, wl.blob, wl.N, wl.Qdiag,
+                   wl.Rdiag, wl.x_ref, wl.u_ref, wl.u_lo, wl.u_hi, spheres=wl.spheres, **args)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            gm_ctx_destroy(self.ctx)
+            gm_gnn_destroy(self.gnn)
+            gm_graph_destroy(self.graph)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, *shape):
+        return self.torch.empty(*shape, dtype=self.torch.float32, device=self.Qdiag.device)
+
+    def linearize(self, x0, u_hat):
+        t = self.torch
+        x0 = t.as_tensor(x0, dtype=t.float32, device=self.Qdiag.device).contiguous()
+        u_hat = t.as_tensor(u_hat, dtype=t.float32, device=self.Qdiag.device).contiguous()
+        x_hat = self.empty(self.N + 1, self.M, 6)
+        A = self.empty(self.N, self.nnzb, 6, 6)
+        B = self.empty(self.N, self.M, 6, self.nu)
+        c = self.empty(self.N, self.M, 6)
+        gm_linearize(self.ctx, x0, u_hat, x_hat, A, B, c)
+        return x_hat, A, B, c
+
+    def condense(self, x_hat, A, B, c):
+        H = self.empty(self.nU, self.nU)
+        g = self.empty(self.nU)
+        Ct = self.empty(max(self.ct_len, 1))
+        dt = self.empty(max(self.rows_c, 1))
+        gm_condense(self.ctx, x_hat, A, B, c, self.cost, self.constr, H, g,
+                    Ct if self.n_c else None, dt if self.n_c else None)
+        return H, g, Ct[:self.ct_len], dt[:self.rows_c]
+
+    def qp_solve(self, H, g, Ct=None, dt=None, warm_U=None, warm_y=None):
+        U = self.empty(self.nU)
+        y = self.empty(self.nU + self.rows_c)
+        gm_qp_solve(self.ctx, H, g, Ct if self.n_c else None, dt if self.n_c else None, self.u_lo,
+                    self.u_hi, U, y, self.stats, warm_U, warm_y)
+        return U, y
+
+    def step(self, x_meas, U=None, u0=None):
+        t = self.torch
+        x_meas = t.as_tensor(x_meas, dtype=t.float32, device=self.Qdiag.device).contiguous()
+        U = self.empty(self.nU) if U is None else U
+        gm_rti_step(self.ctx, x_meas, self.cost, self.constr, U, u0, self.stats)
+        return U
+
+    def reset(self):
+        gm_ctx_reset(self.ctx)
+
+    def read_stats(self):
+        return read_stats(self.stats)

@@ -1,0 +1,88 @@
+"""The C-ABI library loads, exports every entry point of include/gm.h, and validates
+its arguments on the host.  No GPU: only host-side calls (no compute)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "gm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_header_function():
+    import paper_2602_17601_b300 as gm
+    lib = ctypes.CDLL(gm.LIB_PATH)
+    names = header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(gm.HEADER_FUNCTIONS) <= set(names)
+
+
+def test_graph_and_gnn_validation():
+    import paper_2602_17601_b300 as gm
+    from synth import small_chain
+    wl = small_chain()
+    g = gm.gm_graph_create(wl.M, wl.src, wl.dst, wl.nu, wl.act_node)
+    m = gm.gm_gnn_load(wl.K, wl.W, wl.nu, wl.dt, wl.blob)
+    s = gm.make_settings(wl.N)
+    assert gm.gm_ctx_workspace_size(g, m, s) > 0
+    bad = [
+        lambda: gm.gm_graph_create(3, [0, 1], [1, 1], 1, [0]),        # self-loop
+        lambda: gm.gm_graph_create(3, [0, 0], [1, 1], 1, [0]),        # duplicate
+        lambda: gm.gm_graph_create(3, [0], [3], 1, [0]),              # out of range
+        lambda: gm.gm_graph_create(3, [0], [1], 1, [5]),              # actuator out of range
+        lambda: gm.gm_gnn_load(wl.K, wl.W, wl.nu, wl.dt, wl.blob[:-1]),   # wrong size
+        lambda: gm.gm_gnn_load(wl.K, 48, wl.nu, wl.dt, wl.blob),          # unsupported width
+        lambda: gm.gm_ctx_workspace_size(g, m, gm.make_settings(0)),      # N = 0
+        lambda: gm.gm_ctx_workspace_size(g, gm.gm_gnn_load(wl.K, wl.W, 3, wl.dt,
+                                                           np.zeros(_blob(wl.K, wl.W, 3), np.float32)), s),
+    ]
+    for f in bad:
+        with pytest.raises(gm.GMError) as e:
+            f()
+        assert e.value.code == gm.GM_ERR_INVALID_ARG
+    nan_blob = wl.blob.copy()
+    nan_blob[3] = np.nan
+    with pytest.raises(gm.GMError):
+        gm.gm_gnn_load(wl.K, wl.W, wl.nu, wl.dt, nan_blob)
+    gm.gm_gnn_destroy(m)
+    gm.gm_graph_destroy(g)
+
+
+def _blob(K, W, nu):
+    from synth import gnn_blob_size
+    return gnn_blob_size(K, W, nu)
+
+
+def test_workspace_grows_linearly_in_nodes():
+    """Thm. 1: memory O(M) for fixed n_x-bar, n_u, N and neighbourhood size."""
+    import paper_2602_17601_b300 as gm
+    from synth import paper_chain
+    sizes = []
+    Ms = [200, 400, 800]
+    for M in Ms:
+        wl = paper_chain(M=M, N=5, nu=4)
+        g = gm.gm_graph_create(wl.M, wl.src, wl.dst, wl.nu, wl.act_node)
+        m = gm.gm_gnn_load(wl.K, wl.W, wl.nu, wl.dt, wl.blob)
+        sizes.append(gm.gm_ctx_workspace_size(g, m, gm.make_settings(wl.N, 5)))
+    slope = np.polyfit(np.log(Ms), np.log(sizes), 1)[0]
+    assert abs(slope - 1.0) < 0.1, (sizes, slope)
+
+
+def test_no_cuda_device_fails_loudly():
+    """Without a CUDA device the compute path raises; there is no CPU fallback."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import paper_2602_17601_b300 as gm
+    from synth import small_chain
+    with pytest.raises(Exception):
+        gm.RTIProblem.from_workload(small_chain())
