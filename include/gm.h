@@ -117,6 +117,10 @@ void gm_gnn_destroy(gm_gnn* m);
  *   polish     1: after ADMM, re-solve the equality QP on the guessed active
  *              set in FP64 and keep it if its KKT certificate is better
  *   timeout_spins  cap on every device-side spin-wait (0 = default)
+ *   scale_rows 1: ADMM runs on the half-space rows divided by their 2-norms
+ *              (same feasible set and U*; multipliers are returned for the
+ *              original rows).  Rows of C~ can be many orders of magnitude
+ *              smaller than 1, and unscaled fixed-rho ADMM stalls on them.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N;
@@ -127,6 +131,7 @@ typedef struct {
     int max_iter;
     int polish;
     int timeout_spins;
+    int scale_rows;
 } gm_settings;
 
 /* Per-solve statistics, written to DEVICE memory by the QP calls. */
@@ -259,6 +264,45 @@ gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost,
 
 /* Reset the carried linearisation inputs u_hat to zero (Algorithm 1 "Initialize"). */
 gm_status gm_ctx_reset(gm_ctx* ctx, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement helpers (no counterpart in the paper's method; they report on
+ * the calls above).
+ * ---------------------------------------------------------------------- */
+
+/* Sizes and algorithmic work of one step of this context (host, no GPU work).
+ * flops_* count 2 x the multiply-adds of the products the kernels perform
+ * (the reverse-mode Jacobian counts the cone rows it actually processes);
+ * bytes_* count the bytes a pass must move at least once. */
+typedef struct {
+    int M, E, nu, K, W, N, n_c, nU;
+    int nnzb;                     /* blocks of the Jacobian pattern */
+    long long rows_c;             /* half-space rows of C~ */
+    long long cone_node_rows;     /* (seed, node) rows over all reverse levels */
+    long long cone_edge_rows;     /* (seed, edge) rows over all reverse levels */
+    double flops_rollout;         /* per step: N GNN forwards */
+    double flops_jacobian;        /* per step: reverse pass over all stages */
+    double flops_condense;        /* per step: recursion + H + g + C~ */
+    double flops_qp_setup;        /* per step: C~'C~, Cholesky, inverse */
+    double flops_admm_iter;       /* per ADMM iteration */
+    double bytes_admm_iter;       /* per ADMM iteration: C~, d~, z, y */
+    size_t workspace_bytes;
+    int stage_chunk;              /* stages per reverse-pass launch group */
+    int admm_grid;                /* CTAs of the persistent ADMM kernel */
+} gm_info;
+
+gm_status gm_ctx_info(const gm_ctx* ctx, gm_info* out);
+
+/* Phase timing: when on, gm_rti_step records CUDA events on its stream at the
+ * boundaries of rollout, Jacobians, condensing, QP set-up (C~'C~, Cholesky,
+ * inverse) and ADMM + KKT check.  gm_ctx_phase_ms waits for the recorded
+ * events, writes the summed milliseconds of the 5 phases and the number of
+ * recorded steps, and clears the record. */
+gm_status gm_ctx_set_timing(gm_ctx* ctx, int on);
+gm_status gm_ctx_phase_ms(gm_ctx* ctx, float* ms5, int* steps);
+
+/* Number of CUDA kernels this library has launched in this process. */
+unsigned long long gm_launch_count(void);
 
 #ifdef __cplusplus
 }

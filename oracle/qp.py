@@ -169,7 +169,14 @@ def solve_exact(H, g, lo, hi, C=None, d=None):
     return best[0], best[1], dict(ipm_iters=it, kkt=best_err)
 
 
-def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None, y0=None):
+def row_scaling(C):
+    """s_r = 1 / |C_r|_2, and 1 for a row that is exactly zero."""
+    nr = np.sqrt((np.asarray(C, np.float64) ** 2).sum(axis=1))
+    return np.where(nr > 0.0, 1.0 / np.where(nr > 0.0, nr, 1.0), 1.0)
+
+
+def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None, y0=None,
+         scale_rows=False):
     """ADMM on l <= A~U <= h (fixed rho, alpha = 1, sigma = 0, unscaled residuals).
 
         P     = H + rho A~'A~                      (factored once)
@@ -180,12 +187,23 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
         y     = y + rho (a - z)
         r_p   = |a - z|_inf,   r_d = |H U + g + A~'y|_inf;  stop when both <= tol.
 
+    scale_rows: run the recurrence on the half-space rows divided by their
+    2-norms (C_r / |C_r|, d_r / |C_r|), which leaves the feasible set and U*
+    unchanged; z and y are returned for the original rows (y_r = s_r y'_r).
+
     Returns U, z, y, iterations (number of U updates), r_p, r_d, converged.
     """
     H = np.asarray(H, np.float64)
     g = np.asarray(g, np.float64)
-    At, l, h = stack_rows(np.asarray(lo, np.float64), np.asarray(hi, np.float64), C, d)
     n = H.shape[0]
+    s = None
+    if scale_rows and C is not None and np.asarray(C).shape[0] > 0:
+        s = row_scaling(C)
+        C = np.asarray(C, np.float64) * s[:, None]
+        d = np.asarray(d, np.float64) * s
+        if y0 is not None:
+            y0 = np.concatenate([y0[:n], y0[n:] / s])
+    At, l, h = stack_rows(np.asarray(lo, np.float64), np.asarray(hi, np.float64), C, d)
     P = H + rho * At.T @ At
     L = np.linalg.cholesky(P)
     U = np.zeros(n) if U0 is None else np.asarray(U0, np.float64).copy()
@@ -193,6 +211,7 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
     z = np.clip(At @ U, l, h)
     r_p = r_d = np.inf
     it = 0
+    ok = False
     for it in range(1, max_iter + 1):
         rhs = At.T @ (rho * z - y) - g
         U = np.linalg.solve(L.T, np.linalg.solve(L, rhs))
@@ -202,8 +221,12 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
         r_p = np.abs(a - z).max()
         r_d = np.abs(H @ U + g + At.T @ y).max()
         if r_p <= tol and r_d <= tol:
-            return U, z, y, it, r_p, r_d, True
-    return U, z, y, it, r_p, r_d, False
+            ok = True
+            break
+    if s is not None:
+        y = np.concatenate([y[:n], y[n:] * s])
+        z = np.concatenate([z[:n], z[n:] / s])
+    return U, z, y, it, r_p, r_d, ok
 
 
 def polish(H, g, lo, hi, C, d, U, z, y):

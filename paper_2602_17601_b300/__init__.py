@@ -37,7 +37,7 @@ class GnnDesc(C.Structure):
 class Settings(C.Structure):
     _fields_ = [("N", C.c_int), ("n_c", C.c_int), ("precision", C.c_int), ("rho", C.c_float),
                 ("tol", C.c_float), ("max_iter", C.c_int), ("polish", C.c_int),
-                ("timeout_spins", C.c_int)]
+                ("timeout_spins", C.c_int), ("scale_rows", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -57,6 +57,18 @@ class Constr(C.Structure):
                 ("dx", C.c_void_p), ("n_spheres", C.c_int), ("spheres", C.c_void_p)]
 
 
+class Info(C.Structure):
+    _fields_ = [("M", C.c_int), ("E", C.c_int), ("nu", C.c_int), ("K", C.c_int), ("W", C.c_int),
+                ("N", C.c_int), ("n_c", C.c_int), ("nU", C.c_int), ("nnzb", C.c_int),
+                ("rows_c", C.c_longlong), ("cone_node_rows", C.c_longlong),
+                ("cone_edge_rows", C.c_longlong), ("flops_rollout", C.c_double),
+                ("flops_jacobian", C.c_double), ("flops_condense", C.c_double),
+                ("flops_qp_setup", C.c_double), ("flops_admm_iter", C.c_double),
+                ("bytes_admm_iter", C.c_double), ("workspace_bytes", C.c_size_t),
+                ("stage_chunk", C.c_int), ("admm_grid", C.c_int)]
+
+
+PHASES = ("rollout", "jacobian", "condense", "qp_setup", "admm_kkt")
 STATS_BYTES = C.sizeof(Stats)
 
 
@@ -88,6 +100,10 @@ def _load():
         "gm_qp_solve": ([vp] * 12 + [vp], C.c_int),
         "gm_rti_step": ([vp, vp, C.POINTER(Cost), C.POINTER(Constr), vp, vp, vp, vp], C.c_int),
         "gm_ctx_reset": ([vp, vp], C.c_int),
+        "gm_ctx_info": ([vp, C.POINTER(Info)], C.c_int),
+        "gm_ctx_set_timing": ([vp, C.c_int], C.c_int),
+        "gm_ctx_phase_ms": ([vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
+        "gm_launch_count": ([], C.c_ulonglong),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -100,7 +116,30 @@ _lib = _load()
 HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_destroy",
                     "gm_gnn_load", "gm_gnn_destroy", "gm_ctx_workspace_size", "gm_ctx_create",
                     "gm_ctx_destroy", "gm_jac_pattern", "gm_linearize", "gm_condense",
-                    "gm_qp_solve", "gm_rti_step", "gm_ctx_reset")
+                    "gm_qp_solve", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
+                    "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count")
+
+
+def gm_ctx_info(ctx):
+    out = Info()
+    _check("gm_ctx_info", _lib.gm_ctx_info(ctx, C.byref(out)))
+    return {f: getattr(out, f) for f, _ in Info._fields_}
+
+
+def gm_ctx_set_timing(ctx, on):
+    _check("gm_ctx_set_timing", _lib.gm_ctx_set_timing(ctx, int(bool(on))))
+
+
+def gm_ctx_phase_ms(ctx):
+    """(dict phase -> summed ms, number of recorded steps); waits for the events."""
+    ms = (C.c_float * 5)()
+    n = C.c_int()
+    _check("gm_ctx_phase_ms", _lib.gm_ctx_phase_ms(ctx, ms, C.byref(n)))
+    return dict(zip(PHASES, list(ms))), n.value
+
+
+def gm_launch_count():
+    return int(_lib.gm_launch_count())
 
 
 def lib():
@@ -168,9 +207,9 @@ def gm_gnn_destroy(m):
 
 
 def make_settings(N, n_c=0, precision=GM_PREC_FP32, rho=0.1, tol=1e-6, max_iter=4000, polish=0,
-                  timeout_spins=0):
+                  timeout_spins=0, scale_rows=1):
     return Settings(int(N), int(n_c), int(precision), float(rho), float(tol), int(max_iter), int(polish),
-                    int(timeout_spins))
+                    int(timeout_spins), int(scale_rows))
 
 
 def gm_ctx_workspace_size(graph, gnn, settings):

@@ -1,6 +1,7 @@
 """Build the CUDA library libgm.so in-tree for sm_103a (B300).
 
-Usage: python -m paper_2602_17601_b300.build  (or build() from Python).
+Usage: python paper_2602_17601_b300/build.py  (or __graft_entry__.build()); run it as a
+file, not as a package module, so that an old library is not loaded first.
 Each .cu file is compiled to an object in parallel, then linked into a shared
 library next to this file.  Objects are rebuilt when a source or header is newer.
 """

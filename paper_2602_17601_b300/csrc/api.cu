@@ -1,6 +1,7 @@
 // C ABI of the GNN-MPC library: handles, workspace layout, and the order of
 // the kernels of one real-time iteration (Algorithm 1).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <numeric>
 
@@ -10,6 +11,9 @@
 namespace gmi {
 
 static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     char buf[1024];
@@ -265,6 +269,7 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_U = cv.take<float>(nU);
     c->d_y = cv.take<float>(nU + c->rows_c);
     c->d_z = cv.take<float>(nU + c->rows_c);
+    c->d_rs = cv.take<float>(std::max(1L, c->rows_c));
     const long T = (nU + 31) / 32;
     c->d_gram_part = cv.take<float>(std::max((long)kMaxGramSplit * T * T * 1024, 4L * 1024 * nU));
     c->d_L = cv.take<double>((size_t)nU * nU);
@@ -490,6 +495,87 @@ gm_status gm_jac_pattern(const gm_ctx* ctx, int* nnzb, const int32_t** row_ptr, 
     return GM_OK;
 }
 
+gm_status gm_ctx_info(const gm_ctx* ctx, gm_info* o) {
+    clear_error();
+    GM_CHECK_ARG(ctx && o, "NULL argument");
+    const gm_ctx* c = ctx;
+    const Cones& C = c->cones;
+    const double W = c->W, M = c->M, E = c->E, nu = c->nu, N = c->N, K = c->K;
+    *o = gm_info{};
+    o->M = c->M; o->E = c->E; o->nu = c->nu; o->K = c->K; o->W = c->W; o->N = c->N; o->n_c = c->n_c;
+    o->nU = c->nU; o->nnzb = c->nnzb; o->rows_c = c->rows_c;
+    for (int r = 0; r <= c->K; ++r) o->cone_node_rows += (long long)C.nr_node[r].size();
+    for (int r = 0; r < c->K; ++r) o->cone_edge_rows += (long long)C.er_edge[r].size();
+    // rollout: every MLP of every stage, 2 (in W + W out) flops per row
+    double fwd = M * 2 * ((6 + nu) * W + W * W) + E * 2 * (6 * W + W * W) + M * 2 * (W * W + 3 * W);
+    fwd += K * (E * 2 * (3 * W * W + W * W) + M * 2 * (2 * W * W + W * W));
+    o->flops_rollout = N * fwd;
+    // reverse pass over the cone rows (3 cotangent channels per row)
+    double bwd = M * 3 * 2 * (3 * W + W * W);
+    for (int r = 0; r < c->K; ++r) {
+        const double nr = (double)C.nr_node[r].size(), er = (double)C.er_edge[r].size();
+        const double nr1 = (double)C.nr_node[r + 1].size();
+        bwd += nr * 3 * 2 * (W * W + W * 2 * W) + er * 3 * 2 * (W * W + W * W) + nr1 * 3 * 2 * (2 * W * W);
+    }
+    bwd += (double)C.nr_node[c->K].size() * 3 * 2 * (W * W + W * (6 + nu));
+    bwd += (double)C.er_edge[c->K - 1].size() * 3 * 2 * (W * W + 6 * W);
+    o->flops_jacobian = N * bwd;
+    double cond = 0;
+    for (int k = 1; k <= c->N; ++k) {
+        const double L = k * nu;
+        cond += c->nnzb * 36.0 * 2 * (L - nu + 1);          // recursion into stage k
+        cond += M * 6 * L * (L + 1);                         // H (lower triangle), 2 flops each
+        cond += M * 6 * 2 * L;                               // g
+        cond += M * c->n_c * 2 * 3 * L;                      // C~ rows
+    }
+    o->flops_condense = cond;
+    double setup = 0, iter = 0, bytes = 0;
+    for (int k = 1; k <= c->N; ++k) {
+        const double L = k * nu, rows = M * c->n_c;
+        setup += rows * L * (L + 1);                         // C~'C~ lower triangle
+        iter += rows * 2 * 2 * L;                            // C~ u and C~' w per row
+        bytes += rows * (L * 4 + 4 + 8);                     // row, d~, z and y
+    }
+    const double n = c->nU;
+    setup += n * n * n / 3 + n * n * n / 3 + n * n * n / 3;  // Cholesky, L^{-1}, L^{-T} L^{-1}
+    iter += 2 * 2 * n * n;                                   // P^{-1} rhs and H U
+    o->flops_qp_setup = setup;
+    o->flops_admm_iter = iter;
+    o->bytes_admm_iter = bytes;
+    o->workspace_bytes = c->ws_bytes;
+    o->stage_chunk = c->stage_chunk;
+    o->admm_grid = c->admm_grid;
+    return GM_OK;
+}
+
+gm_status gm_ctx_set_timing(gm_ctx* ctx, int on) {
+    clear_error();
+    GM_CHECK_ARG(ctx, "ctx is NULL");
+    ctx->timing = on != 0;
+    return GM_OK;
+}
+
+gm_status gm_ctx_phase_ms(gm_ctx* ctx, float* ms5, int* steps) {
+    clear_error();
+    GM_CHECK_ARG(ctx && ms5, "NULL argument");
+    for (int p = 0; p < 5; ++p) ms5[p] = 0.f;
+    for (auto& e : ctx->events) {
+        GM_CUDA_TRY(cudaEventSynchronize(e[5]));
+        for (int p = 0; p < 5; ++p) {
+            float t = 0.f;
+            GM_CUDA_TRY(cudaEventElapsedTime(&t, e[p], e[p + 1]));
+            ms5[p] += t;
+        }
+    }
+    if (steps) *steps = (int)ctx->events.size();
+    for (auto& e : ctx->events)
+        for (auto ev : e) cudaEventDestroy(ev);
+    ctx->events.clear();
+    return GM_OK;
+}
+
+unsigned long long gm_launch_count(void) { return g_launches.load(); }
+
 gm_status gm_ctx_reset(gm_ctx* ctx, void* stream) {
     clear_error();
     GM_CHECK_ARG(ctx, "ctx is NULL");
@@ -554,8 +640,17 @@ gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, con
     GM_TRY(check_cost(ctx, cost, cons));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     gm_ctx* c = ctx;
+    std::array<cudaEvent_t, 6> ev{};
+    const bool timed = c->timing && c->events.size() < 100000;
+    if (timed) {
+        for (auto& e : ev) GM_CUDA_TRY(cudaEventCreate(&e));
+        c->events.push_back(ev);
+        GM_CUDA_TRY(cudaEventRecord(ev[0], st));
+    }
     GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
+    if (timed) GM_CUDA_TRY(cudaEventRecord(ev[1], st));
     GM_TRY(gnn_jacobians(c, c->d_x_hat, c->d_u_hat, c->d_A, c->d_B, c->d_c, st));
+    if (timed) GM_CUDA_TRY(cudaEventRecord(ev[2], st));
     const float* Cx = cons->Cx;
     const float* dx = cons->dx;
     if (cons->n_spheres > 0) {
@@ -564,8 +659,10 @@ gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, con
         dx = c->d_dx;
     }
     GM_TRY(condense(c, c->d_x_hat, c->d_A, c->d_B, c->d_c, cost, Cx, dx, c->d_H, c->d_g, c->d_Ct, c->d_dt, st));
+    if (timed) GM_CUDA_TRY(cudaEventRecord(ev[3], st));
     GM_TRY(qp_solve(c, c->d_H, c->d_g, c->d_Ct, c->d_dt, cons->u_lo, cons->u_hi, nullptr, nullptr, c->d_U,
-                    c->d_y, stats ? stats : c->d_stats, st));
+                    c->d_y, stats ? stats : c->d_stats, st, timed ? ev[4] : nullptr));
+    if (timed) GM_CUDA_TRY(cudaEventRecord(ev[5], st));
     GM_CUDA_TRY(cudaMemcpyAsync(U, c->d_U, sizeof(float) * c->nU, cudaMemcpyDeviceToDevice, st));
     if (u0) GM_CUDA_TRY(cudaMemcpyAsync(u0, c->d_U, sizeof(float) * c->nu, cudaMemcpyDeviceToDevice, st));
     GM_TRY(shift_inputs(c, c->d_U, c->d_u_hat, st));

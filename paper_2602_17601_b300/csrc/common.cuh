@@ -38,8 +38,13 @@ void clear_error();
         }                                                                          \
     } while (0)
 
+// Every kernel launch of the library is followed by GM_LAUNCH_CHECK, which also
+// counts it (gm_launch_count).
+void count_launch();
+
 #define GM_LAUNCH_CHECK()                                                           \
     do {                                                                            \
+        ::gmi::count_launch();                                                      \
         cudaError_t _e = cudaGetLastError();                                        \
         if (_e != cudaSuccess) {                                                    \
             ::gmi::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(_e), \

@@ -125,7 +125,8 @@ __global__ void gram_kernel(GramRows R, int n, float* __restrict__ part) {
                 const int r = rb + rr;
                 float w = 0.f, v1 = 0.f, v2 = 0.f;
                 if (r < r1) {
-                    w = R.wts ? R.wts[(long)k * R.rows_per_stage + r] : 1.f;
+                    w = R.wts ? R.wts[(long)(k - R.wts_k0) * R.rows_per_stage + r] : 1.f;
+                    if (R.wts_square) w *= w;
                     const int c1 = ti * 32 + cc, c2 = tj * 32 + cc;
                     const float* xr = R.X + base + (long)r * L;
                     if (c1 < L) v1 = xr[c1];
@@ -257,7 +258,7 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
         GM_LAUNCH_CHECK();
     }
     // Eq. H: sum of per-node local Hessians + Rbar
-    GramRows R{c->d_Gu, M * 6, nu, N, cost->Qdiag};
+    GramRows R{c->d_Gu, M * 6, nu, N, cost->Qdiag, 0, 0};
     const int T = (c->nU + 31) / 32;
     const int nsplit = std::max(1, std::min(64, (2 * c->num_sms) / std::max(1, T * (T + 1) / 2)));
     GM_TRY(gram(c, R, nsplit, cost->Rdiag, 1.f, H, st));

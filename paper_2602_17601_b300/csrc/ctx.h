@@ -100,7 +100,7 @@ struct gm_ctx {
     float *d_Cx = nullptr, *d_dx = nullptr;
     float *d_Gu = nullptr, *d_Gx = nullptr;
     float *d_H = nullptr, *d_g = nullptr, *d_Ct = nullptr, *d_dt = nullptr;
-    float *d_U = nullptr, *d_y = nullptr, *d_z = nullptr;
+    float *d_U = nullptr, *d_y = nullptr, *d_z = nullptr, *d_rs = nullptr;
     float *d_gram_part = nullptr;
     double *d_L = nullptr, *d_Linv = nullptr;
     float *d_P = nullptr, *d_Pinv = nullptr;
@@ -115,4 +115,12 @@ struct gm_ctx {
     float* d_y_pol = nullptr;
     gm_stats* d_stats = nullptr; // internal stats when the caller passes none
     int admm_grid = 0;
+    // phase timing of gm_rti_step (events on the caller's stream)
+    bool timing = false;
+    std::vector<std::array<cudaEvent_t, 6>> events;
+
+    ~gm_ctx() {
+        for (auto& e : events)
+            for (auto ev : e) cudaEventDestroy(ev);
+    }
 };

@@ -16,7 +16,9 @@ struct GramRows {
     const float* X;         // packed rows
     int rows_per_stage;     // rows of one stage (M*6 or M*n_c)
     int nu, N;
-    const float* wts;       // [N+1][rows_per_stage] weights indexed by stage k (nullable: 1)
+    const float* wts;       // weights, index (k - wts_k0) * rows_per_stage + r (nullable: 1)
+    int wts_k0 = 0;         // first stage the weight array covers
+    int wts_square = 0;     // use w*w instead of w
 };
 gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, float diag_scale,
                float* G, cudaStream_t st);
@@ -27,9 +29,10 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
                    float* Ct, float* dt, cudaStream_t st);
 
 // qp.cu
+// ev_mid (nullable) is recorded between the set-up (P, Cholesky, inverse) and the iterations.
 gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, const float* dt,
                    const float* u_lo, const float* u_hi, const float* warm_U, const float* warm_y,
-                   float* U, float* y, gm_stats* stats, cudaStream_t st);
+                   float* U, float* y, gm_stats* stats, cudaStream_t st, cudaEvent_t ev_mid = nullptr);
 
 size_t admm_smem_bytes(const gm_ctx* c);
 const void* admm_kernel_ptr(const gm_ctx* c);

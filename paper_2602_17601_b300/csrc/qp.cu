@@ -27,6 +27,24 @@ __global__ void form_p_kernel(int n, const float* __restrict__ H, const float* _
     P[t] = v;
 }
 
+// s_r = 1 / |C~_r|_2 (1 for an exactly zero row), one warp per packed row.
+__global__ void row_norm_kernel(long rows, int nu, int Mnc, const float* __restrict__ Ct,
+                                float* __restrict__ rs) {
+    const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const int ks = (int)(r / Mnc);
+    const int L = (ks + 1) * nu;
+    const long off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (r - (long)ks * Mnc) * L;
+    double s = 0.0;
+    for (int c = lane; c < L; c += 32) {
+        const double v = Ct[off + c];
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) rs[r] = s > 0.0 ? (float)(1.0 / sqrt(s)) : 1.f;
+}
+
 // Right-looking Cholesky P = L L' in FP64, one CTA; a non-positive pivot sets GM_ERR_NUMERIC.
 __global__ void cholesky_kernel(int n, const float* __restrict__ P, double* __restrict__ L,
                                 int* status) {
@@ -90,6 +108,7 @@ struct AdmmArgs {
     int n, nu, Mnc;
     long rows;
     const float *Ct, *dt, *lo, *hi, *g, *H, *Pinv, *U0, *y0;
+    const float* rs;         // per-row scale 1/|C~_r| (nullable: unscaled)
     float *U, *y, *z, *acc;
     unsigned* bar;
     int* status;
@@ -169,11 +188,13 @@ __global__ void __launch_bounds__(ADMM_THREADS) admm_kernel(AdmmArgs a) {
                 v[m] = c < L ? a.Ct[off + c] : 0.f;
                 if (c < L) dot = fmaf(v[m], su[c], dot);
             }
-            dot = warp_sum(dot);
-            const float d = a.dt[r];
+            // the recurrence runs on the scaled row s_r C~_r <= s_r d~_r
+            const float sr = a.rs ? a.rs[r] : 1.f;
+            dot = warp_sum(dot) * sr;
+            const float d = a.dt[r] * sr;
             float yr, zr;
             if (init) {
-                yr = a.y0 ? a.y0[n + r] : 0.f;
+                yr = a.y0 ? a.y0[n + r] / sr : 0.f;
                 zr = fminf(dot, d);
             } else {
                 yr = a.y[n + r];
@@ -185,11 +206,12 @@ __global__ void __launch_bounds__(ADMM_THREADS) admm_kernel(AdmmArgs a) {
                 a.y[n + r] = yr;
                 a.z[n + r] = zr;
             }
-            const float w = rho * zr - yr;
+            const float w = (rho * zr - yr) * sr;
+            const float ys = yr * sr;
 #pragma unroll
             for (int m = 0; m < ADMM_MAXC; ++m) {
                 pw[m] = fmaf(v[m], w, pw[m]);
-                py[m] = fmaf(v[m], yr, py[m]);
+                py[m] = fmaf(v[m], ys, py[m]);
             }
         }
 #pragma unroll
@@ -294,6 +316,13 @@ __global__ void __launch_bounds__(ADMM_THREADS) admm_kernel(AdmmArgs a) {
             }
         }
     }
+    // own rows back to the original scaling: y_r = s_r y'_r, z_r = z'_r / s_r
+    if (a.rs)
+        for (long r = r0 + tid; r < r1; r += ADMM_THREADS) {
+            const float sr = a.rs[r];
+            a.y[n + r] *= sr;
+            a.z[n + r] /= sr;
+        }
     if (blockIdx.x == 0) {
         for (int c = tid; c < n; c += ADMM_THREADS) {
             a.U[c] = su[c];
@@ -432,7 +461,7 @@ const void* admm_kernel_ptr(const gm_ctx* c) {
 
 gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, const float* dt,
                    const float* u_lo, const float* u_hi, const float* warm_U, const float* warm_y,
-                   float* U, float* y, gm_stats* stats, cudaStream_t st) {
+                   float* U, float* y, gm_stats* stats, cudaStream_t st, cudaEvent_t ev_mid) {
     const int n = c->nU;
     const long rows = c->rows_c;
     float* yv = y ? y : c->d_y;
@@ -440,7 +469,13 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     // P = H + rho (I + C~'C~)
     const float* CtC = nullptr;
     if (rows > 0) {
-        GramRows R{Ct, c->M * c->n_c, c->nu, c->N, nullptr};
+        const float* rs = nullptr;
+        if (c->s.scale_rows) {
+            row_norm_kernel<<<cdiv(rows * 32, 256), 256, 0, st>>>(rows, c->nu, c->M * c->n_c, Ct, c->d_rs);
+            GM_LAUNCH_CHECK();
+            rs = c->d_rs;
+        }
+        GramRows R{Ct, c->M * c->n_c, c->nu, c->N, rs, 1, 1};
         const int T = (n + 31) / 32;
         const int nsplit = std::max(1, std::min(64, (2 * c->num_sms) / std::max(1, T * (T + 1) / 2)));
         GM_TRY(gram(c, R, nsplit, nullptr, 0.f, c->d_Pinv, st));   // C~'C~ into Pinv (scratch)
@@ -454,6 +489,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     GM_LAUNCH_CHECK();
     pinv_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, c->d_Linv, c->d_Pinv);
     GM_LAUNCH_CHECK();
+    if (ev_mid) GM_CUDA_TRY(cudaEventRecord(ev_mid, st));
     // ADMM
     GM_CUDA_TRY(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned) * 4, st));
     GM_CUDA_TRY(cudaMemsetAsync(c->d_acc, 0, sizeof(float) * (2 * n + 1), st));
@@ -465,6 +501,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     a.row_begin = c->d_row_begin; a.rho = c->s.rho; a.tol = c->s.tol; a.max_iter = c->s.max_iter;
     a.max_spins = c->s.timeout_spins > 0 ? c->s.timeout_spins : (1LL << 26);
     a.stats = stats;
+    a.rs = (rows > 0 && c->s.scale_rows) ? c->d_rs : nullptr;
     const bool smem_mats = admm_smem_mats(n);
     const size_t smem = admm_smem_bytes(c);
     GM_CUDA_TRY(cudaFuncSetAttribute(admm_kernel_ptr(c), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -483,6 +520,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     } else {
         GM_CUDA_TRY(cudaLaunchKernelEx(&cfg, admm_kernel<false>, a));
     }
+    GM_LAUNCH_CHECK();
     // FP64 KKT certificate of (U, y)
     GM_CUDA_TRY(cudaMemsetAsync(c->d_kkt, 0, sizeof(double) * (n + 4), st));
     if (rows > 0) {
