@@ -169,10 +169,13 @@ def solve_exact(H, g, lo, hi, C=None, d=None):
     return best[0], best[1], dict(ipm_iters=it, kkt=best_err)
 
 
+ROW_NORM_FLOOR = 1e-8
+
+
 def row_scaling(C):
-    """s_r = 1 / |C_r|_2, and 1 for a row that is exactly zero."""
+    """s_r = 1 / max(|C_r|_2, 1e-8): unit rows, except rows that barely depend on U."""
     nr = np.sqrt((np.asarray(C, np.float64) ** 2).sum(axis=1))
-    return np.where(nr > 0.0, 1.0 / np.where(nr > 0.0, nr, 1.0), 1.0)
+    return 1.0 / np.maximum(nr, ROW_NORM_FLOOR)
 
 
 def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None, y0=None,

@@ -70,6 +70,15 @@ struct DevStatus {
 
 __device__ __forceinline__ void dev_fail(int* status, int code) { atomicOr(status, 1 << code); }
 
+// Maxima of residuals that keep a NaN (fmax drops it, which would let a NaN
+// iterate pass a convergence test).
+__device__ __forceinline__ float nmaxf(float a, float b) {
+    return (a != a || b != b) ? __int_as_float(0x7fc00000) : fmaxf(a, b);
+}
+__device__ __forceinline__ double nmax(double a, double b) {
+    return (a != a || b != b) ? __longlong_as_double(0x7ff8000000000000LL) : fmax(a, b);
+}
+
 // ---------------------------------------------------------------- grid barrier
 // A monotone arrival counter: barrier number `phase` (1, 2, ...) completes when
 // counter >= phase * nblocks.  The counter is zeroed by the host before the

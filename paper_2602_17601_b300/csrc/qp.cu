@@ -27,7 +27,7 @@ __global__ void form_p_kernel(int n, const float* __restrict__ H, const float* _
     P[t] = v;
 }
 
-// s_r = 1 / |C~_r|_2 (1 for an exactly zero row), one warp per packed row.
+// s_r = 1 / max(|C~_r|_2, 1e-8), one warp per packed row (rows below the floor barely depend on U).
 __global__ void row_norm_kernel(long rows, int nu, int Mnc, const float* __restrict__ Ct,
                                 float* __restrict__ rs) {
     const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -42,7 +42,7 @@ __global__ void row_norm_kernel(long rows, int nu, int Mnc, const float* __restr
         s += v * v;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) rs[r] = s > 0.0 ? (float)(1.0 / sqrt(s)) : 1.f;
+    if (lane == 0) rs[r] = (float)(1.0 / fmax(sqrt(s), 1e-8));   // floor keeps s_r^2 finite in FP32
 }
 
 // Right-looking Cholesky P = L L' in FP64, one CTA; a non-positive pivot sets GM_ERR_NUMERIC.
@@ -127,7 +127,7 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 __device__ __forceinline__ float warp_max(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = nmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(ADMM_THREADS) admm_kernel(AdmmArgs a) {
                 zr = fminf(dot + yr / rho, d);
                 yr = yr + rho * (dot - zr);
             }
-            rp = fmaxf(rp, fabsf(dot - zr));
+            rp = nmaxf(rp, fabsf(dot - zr));
             if (lane == 0) {
                 a.y[n + r] = yr;
                 a.z[n + r] = zr;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(ADMM_THREADS) admm_kernel(AdmmArgs a) {
         }
         if (tid == 0) {
             float m = 0.f;
-            for (int w = 0; w < NW; ++w) m = fmaxf(m, wmax[w]);
+            for (int w = 0; w < NW; ++w) m = nmaxf(m, wmax[w]);
             atomicMax(reinterpret_cast<unsigned*>(accw + 2 * n), __float_as_uint(m));
         }
     };
@@ -262,21 +262,23 @@ __global__ void __launch_bounds__(ADMM_THREADS) admm_kernel(AdmmArgs a) {
                     float s = 0.f;
                     for (int j = lane; j < n; j += 32) s = fmaf(H[(long)c * n + j], su[j], s);
                     s = warp_sum(s);
-                    m = fmaxf(m, fabsf(s + a.g[c] + saty[c]));
+                    m = nmaxf(m, fabsf(s + a.g[c] + saty[c]));
                 }
                 if (lane == 0) wmax[warp] = m;
                 __syncthreads();
                 if (tid == 0) {
                     float mm = 0.f;
-                    for (int w = 0; w < NW; ++w) mm = fmaxf(mm, wmax[w]);
+                    for (int w = 0; w < NW; ++w) mm = nmaxf(mm, wmax[w]);
                     s_rd = mm;
                 }
                 __syncthreads();
-                rp_last = fmaxf(__uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 2 * n))),
+                rp_last = nmaxf(__uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 2 * n))),
                                 s_rpbox);
                 rd_last = s_rd;
                 converged = (rp_last <= a.tol && rd_last <= a.tol) ? 1 : 0;
-                if (converged || it - 1 >= a.max_iter) {
+                const bool bad = (rp_last != rp_last) || (rd_last != rd_last);
+                if (bad && blockIdx.x == 0 && tid == 0) dev_fail(a.status, GM_ERR_NUMERIC);
+                if (converged || bad || it - 1 >= a.max_iter) {
                     it_done = it - 1;
                     break;
                 }
@@ -296,14 +298,14 @@ __global__ void __launch_bounds__(ADMM_THREADS) admm_kernel(AdmmArgs a) {
                 const float zn = fminf(fmaxf(av + yb[c] / rho, a.lo[c]), a.hi[c]);
                 yb[c] = yb[c] + rho * (av - zn);
                 zb[c] = zn;
-                m = fmaxf(m, fabsf(av - zn));
+                m = nmaxf(m, fabsf(av - zn));
             }
             m = warp_max(m);
             if (lane == 0) wmax[warp] = m;
             __syncthreads();
             if (tid == 0) {
                 float mm = 0.f;
-                for (int w = 0; w < NW; ++w) mm = fmaxf(mm, wmax[w]);
+                for (int w = 0; w < NW; ++w) mm = nmaxf(mm, wmax[w]);
                 s_rpbox = mm;
             }
             if (blockIdx.x == 0)
@@ -373,9 +375,9 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
         }
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
         const double d = dt[r];
-        prim = fmax(prim, dot - d);
-        dual = fmax(dual, -yr);
-        comp = fmax(comp, fmax(yr, 0.0) * fabs(d - dot));
+        prim = nmax(prim, dot - d);
+        dual = nmax(dual, -yr);
+        comp = nmax(comp, nmax(yr, 0.0) * fabs(d - dot));
     }
     for (int m = 0; m < ADMM_MAXC; ++m) {
         const int c = lane + 32 * m;
@@ -388,8 +390,8 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
         atomicAdd(kkt + c, s);
     }
     if (lane == 0) {
-        atomic_max_pos(kkt + n, fmax(prim, 0.0));
-        atomic_max_pos(kkt + n + 1, fmax(dual, 0.0));
+        atomic_max_pos(kkt + n, nmax(prim, 0.0));
+        atomic_max_pos(kkt + n + 1, nmax(dual, 0.0));
         atomic_max_pos(kkt + n + 2, comp);
     }
 }
@@ -404,17 +406,17 @@ __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         double s = (double)g[c] + (double)y[c] + kkt[c];
         for (int j = 0; j < n; ++j) s += (double)H[(long)c * n + j] * (double)U[j];
-        stat = fmax(stat, fabs(s));
+        stat = nmax(stat, fabs(s));
         const double u = U[c], l = lo[c], h = hi[c], yc = y[c];
-        prim = fmax(prim, fmax(u - h, l - u));
-        comp = fmax(comp, fmax(yc, 0.0) * fabs(h - u));
-        comp = fmax(comp, fmax(-yc, 0.0) * fabs(u - l));
+        prim = nmax(prim, nmax(u - h, l - u));
+        comp = nmax(comp, nmax(yc, 0.0) * fabs(h - u));
+        comp = nmax(comp, nmax(-yc, 0.0) * fabs(u - l));
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) {
-        stat = fmax(stat, __shfl_xor_sync(0xffffffffu, stat, o));
-        prim = fmax(prim, __shfl_xor_sync(0xffffffffu, prim, o));
-        comp = fmax(comp, __shfl_xor_sync(0xffffffffu, comp, o));
+        stat = nmax(stat, __shfl_xor_sync(0xffffffffu, stat, o));
+        prim = nmax(prim, __shfl_xor_sync(0xffffffffu, prim, o));
+        comp = nmax(comp, __shfl_xor_sync(0xffffffffu, comp, o));
     }
     if (lane == 0) {
         red[0][w] = stat;
@@ -425,14 +427,14 @@ __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float
     if (threadIdx.x == 0) {
         const int nw = blockDim.x >> 5;
         for (int i = 1; i < nw; ++i) {
-            stat = fmax(stat, red[0][i]);
-            prim = fmax(prim, red[1][i]);
-            comp = fmax(comp, red[2][i]);
+            stat = nmax(stat, red[0][i]);
+            prim = nmax(prim, red[1][i]);
+            comp = nmax(comp, red[2][i]);
         }
         stats->kkt_stat = stat;
-        stats->kkt_prim = fmax(fmax(prim, 0.0), kkt[n]);
+        stats->kkt_prim = nmax(nmax(prim, 0.0), kkt[n]);
         stats->kkt_dual = kkt[n + 1];
-        stats->kkt_comp = fmax(comp, kkt[n + 2]);
+        stats->kkt_comp = nmax(comp, kkt[n + 2]);
         int st = *status;
         int code = GM_OK;
         if (st & (1 << GM_ERR_TIMEOUT)) code = GM_ERR_TIMEOUT;

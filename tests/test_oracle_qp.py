@@ -92,6 +92,24 @@ def test_admm_dual_residual_identity():
     assert np.allclose(Ua, U, atol=1e-12)
 
 
+def test_row_scaled_admm_reaches_the_same_optimum():
+    """Dividing half-space rows by their norms changes neither the feasible set nor U*.
+
+    Rows are given norms from 1e-7 to 1e2; the scaled recurrence reaches the
+    exact optimum and returns multipliers certified for the original rows.
+    """
+    H, g, lo, hi, C, d = random_qp(8, 6, 41)
+    f = np.array([1e-7, 1e-4, 1e-2, 1.0, 10.0, 100.0])
+    C, d = C * f[:, None], d * f
+    U, y, _ = qp.solve_exact(H, g, lo, hi, C, d)
+    Ua, za, ya, it, rp, rd, ok = qp.admm(H, g, lo, hi, C, d, rho=1.0, tol=1e-11, max_iter=200000,
+                                         scale_rows=True)
+    assert ok and np.abs(Ua - U).max() <= 1e-8
+    At, l, h = qp.stack_rows(lo, hi, C, d)
+    cert = qp.kkt_certificate(H, g, At, l, h, Ua, ya)
+    assert cert["stationarity"] <= 1e-9 and cert["dual"] <= 1e-12
+
+
 def test_polish_recovers_the_optimum_from_a_loose_admm_iterate():
     H, g, lo, hi, C, d = random_qp(8, 6, 31)
     U, _, _ = qp.solve_exact(H, g, lo, hi, C, d)
