@@ -304,6 +304,41 @@ gm_status gm_ctx_phase_ms(gm_ctx* ctx, float* ms5, int* steps);
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long gm_launch_count(void);
 
+/* ------------------------------------------------------------------------
+ * gm_qp_solve_noalloc — the ADMM solve of gm_qp_solve for callers that
+ * cannot allocate device memory at all.  The paper has no counterpart: it
+ * exists for hosts such as a real-time control loop that must not call
+ * cudaMalloc once running (an allocation can synchronise the device and has
+ * no latency bound), or a plug-in living inside another runtime that owns
+ * the whole device-memory budget and hands out no workspace.  Such a caller
+ * cannot create a gm_ctx (its workspace is caller-allocated device memory),
+ * so this call needs no context.
+ *
+ * All scratch (P and its factors, ADMM z / y / row scales, reduction buffers,
+ * barrier counters, KKT accumulators) lives in one fixed array of
+ * GM_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
+ * it until the process exits.  The call allocates nothing.
+ *   Limits: N * nu <= GM_NOALLOC_MAX_NU, N * Mnc <= GM_NOALLOC_MAX_ROWS;
+ *           larger problems are rejected with GM_ERR_INVALID_ARG.
+ *   N, nu, Mnc  horizon, inputs, half-space rows per stage (M * n_c)
+ *   s           rho, tol, max_iter, scale_rows, timeout_spins are used
+ *   H, g, Ct, dt, u_lo, u_hi, U, y, stats   as for gm_qp_solve (device
+ *           pointers; Ct/dt NULL when Mnc == 0; y and stats nullable)
+ * The first call on a device looks up the array's device address on that
+ * device (the device must be current); make that first call before any
+ * stream capture.  Every call uses the same array and leaves the last
+ * call's contents in it (the call clears what must start at zero): calls
+ * whose kernels overlap on the GPU (other streams, other host threads) race
+ * and give wrong results; serialise them.
+ * ---------------------------------------------------------------------- */
+#define GM_NOALLOC_MAX_NU 64
+#define GM_NOALLOC_MAX_ROWS 8192
+#define GM_NOALLOC_SCRATCH_BYTES (512 * 1024)
+gm_status gm_qp_solve_noalloc(int N, int nu, int Mnc, const gm_settings* s, const float* H,
+                              const float* g, const float* Ct, const float* dt,
+                              const float* u_lo, const float* u_hi, float* U, float* y,
+                              gm_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

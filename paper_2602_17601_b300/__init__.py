@@ -104,6 +104,7 @@ def _load():
         "gm_ctx_set_timing": ([vp, C.c_int], C.c_int),
         "gm_ctx_phase_ms": ([vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
         "gm_launch_count": ([], C.c_ulonglong),
+        "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -117,7 +118,23 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_gnn_load", "gm_gnn_destroy", "gm_ctx_workspace_size", "gm_ctx_create",
                     "gm_ctx_destroy", "gm_jac_pattern", "gm_linearize", "gm_condense",
                     "gm_qp_solve", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
-                    "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count")
+                    "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count", "gm_qp_solve_noalloc")
+
+GM_NOALLOC_MAX_NU = 64
+GM_NOALLOC_MAX_ROWS = 8192
+
+
+def gm_qp_solve_noalloc(N, nu, Mnc, settings, H, g, Ct, dt, u_lo, u_hi, U, y=None, stats=None, stream=None):
+    """ADMM solve of gm_qp_solve with no context and no device allocation (library-held scratch).
+
+    For callers that must not allocate device memory; sizes are capped at
+    N*nu <= GM_NOALLOC_MAX_NU and N*Mnc <= GM_NOALLOC_MAX_ROWS.  Calls must not
+    overlap on the GPU: they share one scratch array.
+    """
+    _check("gm_qp_solve_noalloc",
+           _lib.gm_qp_solve_noalloc(int(N), int(nu), int(Mnc), C.byref(settings), _ptr(H), _ptr(g), _ptr(Ct),
+                                    _ptr(dt), _ptr(u_lo), _ptr(u_hi), _ptr(U), _ptr(y), _ptr(stats),
+                                    _stream(stream)))
 
 
 def gm_ctx_info(ctx):

@@ -22,6 +22,10 @@ struct GramRows {
 };
 gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, float diag_scale,
                float* G, cudaStream_t st);
+__global__ void gram_kernel(GramRows R, int n, float* __restrict__ part);
+__global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
+                                   const float* __restrict__ diag_add, float diag_scale,
+                                   float* __restrict__ G);
 gm_status sphere_halfspaces(gm_ctx* c, const float* x_hat, const float* spheres, int S, float* Cx,
                             float* dx, cudaStream_t st);
 gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B, const float* cvec,

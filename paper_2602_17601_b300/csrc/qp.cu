@@ -15,6 +15,8 @@
 #include "ctx.h"
 #include "kernels.h"
 
+#include <mutex>
+
 namespace gmi {
 
 __global__ void form_p_kernel(int n, const float* __restrict__ H, const float* __restrict__ CtC,
@@ -538,3 +540,152 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
 }
 
 }  // namespace gmi
+
+// ======================================================================= no-allocation variant
+// gm_qp_solve_noalloc keeps every scratch buffer of the solve in this one
+// array.  It is part of the library image, so a process that loads the
+// library holds it on every GPU it uses until exit, and no call allocates.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GM_NOALLOC_SCRATCH_BYTES];
+
+namespace gmi {
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};   // device address of g_noalloc_scratch, per device ordinal
+constexpr int kNoAllocGrid = 64;
+constexpr int kNoAllocSplit = 8;
+}  // namespace
+
+// C~ rows split over `grid` CTAs by non-zeros (one thread; the row count is bounded).
+__global__ void noalloc_partition_kernel(long rows, int nu, int Mnc, int grid, int* rb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double total = 0.0;
+    for (long r = 0; r < rows; ++r) total += (double)((r / Mnc) + 1) * nu;
+    rb[0] = 0;
+    int b = 1;
+    double acc = 0.0;
+    for (long r = 0; r < rows && b < grid; ++r) {
+        acc += (double)((r / Mnc) + 1) * nu;
+        while (b < grid && acc >= total * b / grid) rb[b++] = (int)(r + 1);
+    }
+    for (; b <= grid; ++b) rb[b] = (int)rows;
+}
+
+}  // namespace gmi
+
+extern "C" gm_status gm_qp_solve_noalloc(int N, int nu, int Mnc, const gm_settings* s, const float* H,
+                                         const float* g, const float* Ct, const float* dt,
+                                         const float* u_lo, const float* u_hi, float* U, float* y,
+                                         gm_stats* stats, void* stream) {
+    using namespace gmi;
+    clear_error();
+    GM_CHECK_ARG(s && H && g && u_lo && u_hi && U, "NULL argument");
+    GM_CHECK_ARG(N >= 1 && nu >= 1 && Mnc >= 0, "need N >= 1, nu >= 1, Mnc >= 0");
+    const int n = N * nu;
+    const long rows = (long)N * Mnc;
+    GM_CHECK_ARG(n <= GM_NOALLOC_MAX_NU, "N * nu = %d exceeds the no-allocation limit %d", n, GM_NOALLOC_MAX_NU);
+    GM_CHECK_ARG(rows <= GM_NOALLOC_MAX_ROWS, "N * Mnc = %ld half-space rows exceed the no-allocation limit %d",
+                 rows, GM_NOALLOC_MAX_ROWS);
+    GM_CHECK_ARG(rows == 0 || (Ct && dt), "Ct/dt are NULL with Mnc = %d", Mnc);
+    GM_CHECK_ARG(s->rho > 0.f && s->tol > 0.f && s->max_iter >= 1, "rho, tol must be > 0 and max_iter >= 1");
+    int dev = 0;
+    GM_CUDA_TRY(cudaGetDevice(&dev));
+    GM_CHECK_ARG(dev >= 0 && dev < 256, "device ordinal %d out of range", dev);
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) GM_CUDA_TRY(cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch));
+        base = g_noalloc_addr[dev];
+    }
+    Carver cv;
+    cv.base = static_cast<char*>(base);
+    float* P = cv.take<float>((size_t)n * n);
+    float* Pinv = cv.take<float>((size_t)n * n);
+    double* L = cv.take<double>((size_t)n * n);
+    double* Linv = cv.take<double>((size_t)n * n);
+    float* z = cv.take<float>(n + rows);
+    float* ys = cv.take<float>(n + rows);
+    float* rs = cv.take<float>(std::max(rows, 1L));
+    float* acc = cv.take<float>(3 * (2 * (size_t)n + 1));
+    unsigned* bar = cv.take<unsigned>(4);
+    int* status = cv.take<int>(4);
+    int* rb = cv.take<int>(kNoAllocGrid + 1);
+    double* kkt = cv.take<double>(n + 4);
+    gm_stats* st_s = cv.take<gm_stats>(1);
+    const int T = (n + 31) / 32;
+    float* part = cv.take<float>((size_t)kNoAllocSplit * T * T * 1024);
+    if (cv.off > (size_t)GM_NOALLOC_SCRATCH_BYTES) {
+        set_error("no-allocation scratch too small (%zu > %d bytes)", cv.off, GM_NOALLOC_SCRATCH_BYTES);
+        return GM_ERR_INVALID_ARG;
+    }
+    float* yv = y ? y : ys;
+    gm_stats* stv = stats ? stats : st_s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int sms = 1;
+    GM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = rows > 0 ? (int)std::max(1L, std::min<long>(std::min(kNoAllocGrid, sms), rows / 16)) : 1;
+    const bool scale = rows > 0 && s->scale_rows;
+    GM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int) * 4, st));
+    if (rows > 0) {
+        if (scale) {
+            row_norm_kernel<<<cdiv(rows * 32, 256), 256, 0, st>>>(rows, nu, Mnc, Ct, rs);
+            GM_LAUNCH_CHECK();
+        }
+        GramRows R{Ct, Mnc, nu, N, scale ? rs : nullptr, 1, 1};
+        gram_kernel<<<dim3(T * (T + 1) / 2, kNoAllocSplit), 256, 0, st>>>(R, n, part);
+        GM_LAUNCH_CHECK();
+        gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, kNoAllocSplit, part, nullptr, 0.f, Pinv);
+        GM_LAUNCH_CHECK();
+    }
+    form_p_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, H, rows > 0 ? Pinv : nullptr, s->rho, P);
+    GM_LAUNCH_CHECK();
+    cholesky_kernel<<<1, 1024, 0, st>>>(n, P, L, status);
+    GM_LAUNCH_CHECK();
+    trinv_kernel<<<cdiv((long)n * 32, 128), 128, 0, st>>>(n, L, Linv);
+    GM_LAUNCH_CHECK();
+    pinv_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, Linv, Pinv);
+    GM_LAUNCH_CHECK();
+    GM_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, st));
+    GM_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(float) * (2 * n + 1), st));
+    noalloc_partition_kernel<<<1, 32, 0, st>>>(rows, nu, std::max(Mnc, 1), grid, rb);
+    GM_LAUNCH_CHECK();
+    AdmmArgs a{};
+    a.n = n; a.nu = nu; a.Mnc = std::max(Mnc, 1); a.rows = rows;
+    a.Ct = Ct; a.dt = dt; a.lo = u_lo; a.hi = u_hi; a.g = g; a.H = H; a.Pinv = Pinv;
+    a.U0 = nullptr; a.y0 = nullptr; a.rs = scale ? rs : nullptr;
+    a.U = U; a.y = yv; a.z = z; a.acc = acc; a.bar = bar; a.status = status; a.row_begin = rb;
+    a.rho = s->rho; a.tol = s->tol; a.max_iter = s->max_iter;
+    a.max_spins = s->timeout_spins > 0 ? s->timeout_spins : (1LL << 26);
+    a.stats = stv;
+    const bool mats = admm_smem_mats(n);
+    const size_t smem = (mats ? (size_t)2 * n * n * sizeof(float) : 0) +
+                        (size_t)(5 * n + (ADMM_THREADS / 32) * 2 * n + ADMM_THREADS / 32) * sizeof(float);
+    const void* fn = mats ? (const void*)admm_kernel<true> : (const void*)admm_kernel<false>;
+    GM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(ADMM_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (mats) {
+        GM_CUDA_TRY(cudaLaunchKernelEx(&cfg, admm_kernel<true>, a));
+    } else {
+        GM_CUDA_TRY(cudaLaunchKernelEx(&cfg, admm_kernel<false>, a));
+    }
+    GM_LAUNCH_CHECK();
+    GM_CUDA_TRY(cudaMemsetAsync(kkt, 0, sizeof(double) * (n + 4), st));
+    if (rows > 0) {
+        const int threads = 256;
+        kkt_rows_kernel<<<std::max(1, std::min(4 * sms, cdiv(rows, 8))), threads, (threads / 32) * n * sizeof(double),
+                          st>>>(n, nu, std::max(Mnc, 1), rows, Ct, dt, U, yv, kkt);
+        GM_LAUNCH_CHECK();
+    }
+    kkt_final_kernel<<<1, 256, 0, st>>>(n, H, g, u_lo, u_hi, U, yv, kkt, status, stv);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
