@@ -121,6 +121,10 @@ void gm_gnn_destroy(gm_gnn* m);
  *              (same feasible set and U*; multipliers are returned for the
  *              original rows).  Rows of C~ can be many orders of magnitude
  *              smaller than 1, and unscaled fixed-rho ADMM stalls on them.
+ *   adapt_rho  1: every 25 iterations compare the primal and dual residuals,
+ *              each relative to its scale, and re-factor P with
+ *              rho sqrt(ratio) (clamped to [1e-6, 1e6]) when that changes rho
+ *              by more than 5x, at most 5 times per solve; 0: fixed rho.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N;
@@ -132,6 +136,7 @@ typedef struct {
     int polish;
     int timeout_spins;
     int scale_rows;
+    int adapt_rho;
 } gm_settings;
 
 /* Per-solve statistics, written to DEVICE memory by the QP calls. */

@@ -179,7 +179,7 @@ def row_scaling(C):
 
 
 def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None, y0=None,
-         scale_rows=False):
+         scale_rows=False, adapt_every=0, max_updates=5):
     """ADMM on l <= A~U <= h (fixed rho, alpha = 1, sigma = 0, unscaled residuals).
 
         P     = H + rho A~'A~                      (factored once)
@@ -193,6 +193,12 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
     scale_rows: run the recurrence on the half-space rows divided by their
     2-norms (C_r / |C_r|, d_r / |C_r|), which leaves the feasible set and U*
     unchanged; z and y are returned for the original rows (y_r = s_r y'_r).
+
+    adapt_every > 0: after every adapt_every-th iteration (at most max_updates
+    times) compare the residuals relative to their scales,
+        ratio = (r_p / max(|a|, |z|)) / (r_d / max(|H U|, |A~'y|, |g|)),
+    and re-factor P with rho sqrt(ratio) (clamped to [1e-6, 1e6]) when that
+    changes rho by more than a factor 5.
 
     Returns U, z, y, iterations (number of U updates), r_p, r_d, converged.
     """
@@ -215,6 +221,7 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
     r_p = r_d = np.inf
     it = 0
     ok = False
+    updates = 0
     for it in range(1, max_iter + 1):
         rhs = At.T @ (rho * z - y) - g
         U = np.linalg.solve(L.T, np.linalg.solve(L, rhs))
@@ -226,6 +233,15 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
         if r_p <= tol and r_d <= tol:
             ok = True
             break
+        if adapt_every and it % adapt_every == 0 and updates < max_updates:
+            ps = max(np.abs(a).max(), np.abs(z).max(), 1e-30)
+            ds = max(np.abs(H @ U).max(), np.abs(At.T @ y).max(), np.abs(g).max(), 1e-30)
+            ratio = (r_p / ps) / max(r_d / ds, 1e-30)
+            rn = min(max(rho * np.sqrt(ratio), 1e-6), 1e6)
+            if rn > 5 * rho or rn < 0.2 * rho:
+                rho = rn
+                updates += 1
+                L = np.linalg.cholesky(H + rho * At.T @ At)
     if s is not None:
         y = np.concatenate([y[:n], y[n:] * s])
         z = np.concatenate([z[:n], z[n:] / s])

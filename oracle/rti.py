@@ -42,7 +42,7 @@ def linearize_dense(gnn, g, x_hat, u_hat):
 
 
 def rti_step(wl, u_hat=None, activation="relu", solver="exact", condensing="recursive",
-             return_all=False, scale_rows=True):
+             return_all=False, scale_rows=True, adapt_every=25):
     """One RTI step on workload wl.  Returns U* [N, nu] (and intermediates)."""
     gnn, g = model_of(wl, activation)
     u_hat = np.zeros((wl.N, wl.nu)) if u_hat is None else np.asarray(u_hat, np.float64)
@@ -72,7 +72,8 @@ def rti_step(wl, u_hat=None, activation="relu", solver="exact", condensing="recu
         U, y, info = qp.solve_exact(H, gv, lo, hi, Ct, dt)
     else:
         U, z, y, it, rp, rd, ok = qp.admm(H, gv, lo, hi, Ct, dt, rho=wl.rho, tol=wl.tol,
-                                          max_iter=wl.max_iter, scale_rows=scale_rows)
+                                          max_iter=wl.max_iter, scale_rows=scale_rows,
+                                          adapt_every=adapt_every)
         info = dict(iters=it, r_p=rp, r_d=rd, converged=ok)
     U = U.reshape(wl.N, wl.nu)
     if not return_all:

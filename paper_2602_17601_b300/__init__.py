@@ -37,7 +37,7 @@ class GnnDesc(C.Structure):
 class Settings(C.Structure):
     _fields_ = [("N", C.c_int), ("n_c", C.c_int), ("precision", C.c_int), ("rho", C.c_float),
                 ("tol", C.c_float), ("max_iter", C.c_int), ("polish", C.c_int),
-                ("timeout_spins", C.c_int), ("scale_rows", C.c_int)]
+                ("timeout_spins", C.c_int), ("scale_rows", C.c_int), ("adapt_rho", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -224,9 +224,9 @@ def gm_gnn_destroy(m):
 
 
 def make_settings(N, n_c=0, precision=GM_PREC_FP32, rho=0.1, tol=1e-6, max_iter=4000, polish=0,
-                  timeout_spins=0, scale_rows=1):
+                  timeout_spins=0, scale_rows=1, adapt_rho=1):
     return Settings(int(N), int(n_c), int(precision), float(rho), float(tol), int(max_iter), int(polish),
-                    int(timeout_spins), int(scale_rows))
+                    int(timeout_spins), int(scale_rows), int(adapt_rho))
 
 
 def gm_ctx_workspace_size(graph, gnn, settings):

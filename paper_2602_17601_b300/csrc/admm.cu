@@ -1,0 +1,585 @@
+// ADMM on the condensed QP (Eq. condensed_matrices), with rho adaptation.
+//
+//   l <= A~ U <= h,  A~ = [I; s .* C~]  (s: optional row scales 1/|C~_r|)
+//   U = P(rho)^{-1} (A~'(rho z - y) - g),  P(rho) = H + rho (I + C~' D C~)
+//   a = A~ U,  z = clip(a + y/rho, l, h),  y += rho (a - z)
+//   r_p = |a - z|_inf,   r_d = |H U + g + A~'y|_inf = rho |A~'(z_prev - z)|_inf
+//
+// The dual residual uses the identity on the right (it holds for the exact
+// U-update; the FP64 KKT check afterwards reports the residual by definition).
+//
+// Rho adaptation: every adapt_every iterations the ratio of the primal and dual
+// residuals, each relative to its scale, gives rho_new = rho sqrt(ratio); a
+// change by more than 5x ends the launch with the iterate kept in a device
+// state, the next round re-forms and re-factors P(rho_new) in FP64, and the
+// next ADMM launch resumes.  A fixed number of rounds is issued; device flags
+// make the unneeded ones return at once, so the host never waits.
+//
+// One launch is a persistent cooperative kernel.  Each CTA owns a contiguous
+// range of C~ rows, split by cost (16 + row length per row), streams it as
+// stage tiles (contiguous rows of one length) into shared memory with
+// cp.async double buffering, computes the row dots with lane groups sized to
+// the row length, updates z and y, and sums s C~'z and s C~'y by a column
+// sweep of the tile.  Block sums go to one of three rotating global
+// accumulators; a bounded grid barrier separates iterations.  The box rows
+// are evaluated redundantly by every CTA.
+#include "admm.h"
+
+namespace gmi {
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ float wsum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float wmaxf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = nmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void admm_state_init_kernel(AdmmState* S, float rho0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        S->rho = rho0;
+        S->need_factor = 1;
+        S->done = 0;
+        S->started = 0;
+        S->iters = 0;
+        S->updates = 0;
+        S->converged = 0;
+        S->rp = S->rd = 0.f;
+    }
+}
+
+// P = H + rho (I + G), rho from the state; skipped when no factorisation is due.
+__global__ void admm_form_p_kernel(int n, const float* __restrict__ H, const float* __restrict__ G,
+                                   const AdmmState* S, float* __restrict__ P) {
+    if (S->done || !S->need_factor) return;
+    const float rho = S->rho;
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)n * n) return;
+    int i = (int)(t / n), j = (int)(t % n);
+    float v = H[t] + (G ? rho * G[t] : 0.f);
+    if (i == j) v += rho;
+    P[t] = v;
+}
+
+// Tile of one stage: rows [t0, t0 + tr) of length L, starting at float offset off.
+struct Tile {
+    long t0, off;
+    int tr, L;
+};
+
+// Next tile of the row range [r, r1) after a tile ending at row r.
+__device__ __forceinline__ Tile next_tile(long r, long r1, int Mnc, int nu, int tile_floats, int tile_rows) {
+    Tile t;
+    const int ks = (int)(r / Mnc);
+    t.L = (ks + 1) * nu;
+    const long stage_end = min((long)(ks + 1) * Mnc, r1);
+    int tr = max(1, tile_floats / t.L);
+    tr = min(tr, tile_rows);
+    tr = (int)min((long)tr, stage_end - r);
+    t.t0 = r;
+    t.tr = tr;
+    t.off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (r - (long)ks * Mnc) * t.L;
+    return t;
+}
+
+template <bool PSMEM>
+__global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
+    extern __shared__ __align__(16) float sm[];
+    AdmmState* S = a.S;
+    if (S->done) return;                                      // uniform across the grid
+    const int n = a.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = ADMM_T / 32;
+    // shared layout
+    float* sP = sm;                                           // n*n if PSMEM
+    float* p = sm + (PSMEM ? n * n : 0);
+    float* su = p;          p += n;
+    float* srhs = p;        p += n;
+    float* zb = p;          p += n;
+    float* yb = p;          p += n;
+    float* atz = p;         p += n;                           // A~'z of the last pass (box + rows)
+    float* aty = p;         p += n;
+    float* sacc = p;        p += 2 * n;                       // block sums of s C~'z, s C~'y
+    float* wred = p;        p += 4 * NW;
+    p = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+    float* tbuf[2];
+    tbuf[0] = p;            p += a.tile_floats;
+    tbuf[1] = p;            p += a.tile_floats;
+    float* rstate[2];                                         // per tile: y, z, d, s (tile_rows each)
+    rstate[0] = p;          p += 4 * a.tile_rows;
+    rstate[1] = p;          p += 4 * a.tile_rows;
+    float* wz = p;          p += a.tile_rows;                 // s z_r and s y_r of the current tile
+    float* wy = p;          p += a.tile_rows;
+    __shared__ float s_misc[8];
+
+    const float* Pinv = a.Pinv;
+    if (PSMEM) {
+        for (int t = tid; t < n * n; t += ADMM_T) sP[t] = a.Pinv[t];
+        Pinv = sP;
+    }
+    const long r0 = a.row_begin[blockIdx.x], r1 = a.row_begin[blockIdx.x + 1];
+    const unsigned G = gridDim.x;
+    const int stride = 2 * n + 4;
+    float rho = S->rho;
+    const bool first = !S->started;
+    int it = S->iters;
+    for (int c = tid; c < n; c += ADMM_T) {
+        if (first) {
+            su[c] = a.U0 ? a.U0[c] : 0.f;
+            yb[c] = a.y0 ? a.y0[c] : 0.f;
+            zb[c] = fminf(fmaxf(su[c], a.lo[c]), a.hi[c]);
+        } else {
+            su[c] = S->u[c];
+            zb[c] = S->zb[c];
+            yb[c] = S->yb[c];
+            atz[c] = S->atz[c];
+            aty[c] = S->aty[c];
+        }
+    }
+    __syncthreads();
+
+    // --------------------------------------------------------------- one pass over the CTA's rows
+    // init: z = clip(a), y = y0; else the ADMM update.  Adds s C~'z, s C~'y and the maxima
+    // (|a - z|, |a|, |z|) into the accumulator accw.
+    auto row_pass = [&](bool init, float* accw) {
+        for (int c = tid; c < 2 * n; c += ADMM_T) sacc[c] = 0.f;
+        float rp = 0.f, am = 0.f, zm = 0.f;
+        float pz = 0.f, py = 0.f;                              // column-sweep partials
+        int cur_L = -1;
+        __syncthreads();
+        auto issue = [&](const Tile& t, int b) {
+            float* dst = tbuf[b];
+            const float* src = a.Ct + t.off;
+            const int cnt = t.tr * t.L;
+            if (a.vec4) {
+                for (int q = tid; q < cnt / 4; q += ADMM_T) cp_async16(dst + 4 * q, src + 4 * q);
+            } else {
+                for (int q = tid; q < cnt; q += ADMM_T) cp_async4(dst + q, src + q);
+            }
+            float* rsb = rstate[b];
+            for (int i = tid; i < t.tr; i += ADMM_T) {
+                const long r = t.t0 + i;
+                if (init) {
+                    if (a.y0) cp_async4(rsb + i, a.y0 + n + r);
+                } else {
+                    cp_async4(rsb + i, a.y + n + r);
+                    cp_async4(rsb + a.tile_rows + i, a.z + n + r);
+                }
+                cp_async4(rsb + 2 * a.tile_rows + i, a.dt + r);
+                if (a.rs) cp_async4(rsb + 3 * a.tile_rows + i, a.rs + r);
+            }
+            cp_async_commit();
+        };
+        long rnext = r0;
+        Tile cur{}, nxt{};
+        bool have = rnext < r1;
+        if (have) {
+            cur = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows);
+            rnext = cur.t0 + cur.tr;
+            issue(cur, 0);
+        }
+        int b = 0;
+        while (have) {
+            const bool more = rnext < r1;
+            if (more) {
+                nxt = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows);
+                rnext = nxt.t0 + nxt.tr;
+                issue(nxt, b ^ 1);
+                cp_async_wait_1();
+            } else {
+                cp_async_wait_0();
+            }
+            __syncthreads();
+            const float* T = tbuf[b];
+            float* rsb = rstate[b];
+            const int L = cur.L, tr = cur.tr;
+            // flush the column sweep when the row length changes
+            if (L != cur_L) {
+                if (cur_L > 0) {
+                    const int c = tid % cur_L;
+                    if (tid / cur_L < ADMM_T / cur_L) {
+                        atomicAdd(&sacc[c], pz);
+                        atomicAdd(&sacc[n + c], py);
+                    }
+                }
+                pz = py = 0.f;
+                cur_L = L;
+            }
+            // phase 1: dots with groups of gs lanes per row, then the row updates
+            const int gs = L >= 128 ? 32 : L >= 64 ? 16 : L >= 32 ? 8 : L >= 16 ? 4 : L >= 8 ? 2 : 1;
+            const int j = tid & (gs - 1);
+            for (int i0 = tid / gs; i0 < ((tr + (ADMM_T / gs) - 1) / (ADMM_T / gs)) * (ADMM_T / gs);
+                 i0 += ADMM_T / gs) {
+                const int i = i0;
+                float dot = 0.f;
+                if (i < tr)
+                    for (int c = j; c < L; c += gs) dot = fmaf(T[i * L + c], su[c], dot);
+                for (int o = gs >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                if (i < tr && j == 0) {
+                    const float s = a.rs ? rsb[3 * a.tile_rows + i] : 1.f;
+                    const float av = dot * s;
+                    const float d = rsb[2 * a.tile_rows + i] * s;
+                    float yv, zv;
+                    if (init) {
+                        yv = a.y0 ? rsb[i] / s : 0.f;
+                        zv = fminf(av, d);
+                    } else {
+                        yv = rsb[i];
+                        zv = fminf(av + yv / rho, d);
+                        yv = yv + rho * (av - zv);
+                    }
+                    rp = nmaxf(rp, fabsf(av - zv));
+                    am = nmaxf(am, fabsf(av));
+                    zm = nmaxf(zm, fabsf(zv));
+                    rsb[i] = yv;
+                    rsb[a.tile_rows + i] = zv;
+                    wz[i] = zv * s;
+                    wy[i] = yv * s;
+                }
+            }
+            __syncthreads();
+            // write back y, z of the tile; phase 2: column sweep of s C~'z and s C~'y
+            for (int i = tid; i < tr; i += ADMM_T) {
+                a.y[n + cur.t0 + i] = rsb[i];
+                a.z[n + cur.t0 + i] = rsb[a.tile_rows + i];
+            }
+            {
+                const int G2 = ADMM_T / L;
+                const int c = tid % L, g2 = tid / L;
+                if (g2 < G2)
+                    for (int i = g2; i < tr; i += G2) {
+                        const float v = T[i * L + c];
+                        pz = fmaf(v, wz[i], pz);
+                        py = fmaf(v, wy[i], py);
+                    }
+            }
+            __syncthreads();
+            cur = nxt;
+            have = more;
+            b ^= 1;
+        }
+        if (cur_L > 0) {
+            const int c = tid % cur_L;
+            if (tid / cur_L < ADMM_T / cur_L) {
+                atomicAdd(&sacc[c], pz);
+                atomicAdd(&sacc[n + c], py);
+            }
+        }
+        rp = wmaxf(rp);
+        am = wmaxf(am);
+        zm = wmaxf(zm);
+        if (lane == 0) {
+            wred[warp] = rp;
+            wred[NW + warp] = am;
+            wred[2 * NW + warp] = zm;
+        }
+        __syncthreads();
+        if (r1 > r0)
+            for (int c = tid; c < 2 * n; c += ADMM_T) atomicAdd(accw + c, sacc[c]);
+        if (tid < 3) {
+            float m = 0.f;
+            for (int w = 0; w < NW; ++w) m = nmaxf(m, wred[tid * NW + w]);
+            atomicMax(reinterpret_cast<unsigned*>(accw + 2 * n + tid), __float_as_uint(m));
+        }
+    };
+
+    // read a completed pass: A~'z, A~'y (box rows added), residual maxima
+    auto read_pass = [&](const float* accr, float& rp_rows, float& am_rows, float& zm_rows) {
+        for (int c = tid; c < n; c += ADMM_T) {
+            srhs[c] = __ldcg(accr + c) + zb[c];               // new A~'z (temporarily in srhs)
+        }
+        rp_rows = __uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 2 * n)));
+        am_rows = __uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 2 * n + 1)));
+        zm_rows = __uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 2 * n + 2)));
+    };
+
+    unsigned phase = 0;
+    int pass = 0;
+    bool ok = true, done = false, converged = false, adapt = false;
+    float rp_last = S->rp, rd_last = S->rd;
+    if (first) {
+        if (blockIdx.x == 0)
+            for (int t = tid; t < stride; t += ADMM_T) a.acc[stride + t] = 0.f;
+        row_pass(true, a.acc);
+        ++phase;
+        ok = grid_barrier(a.bar, G, phase, a.max_spins, a.status);
+        if (ok) {
+            float rpr, amr, zmr;
+            read_pass(a.acc, rpr, amr, zmr);
+            __syncthreads();
+            for (int c = tid; c < n; c += ADMM_T) {
+                atz[c] = srhs[c];
+                aty[c] = __ldcg(a.acc + n + c) + yb[c];
+            }
+            __syncthreads();
+        }
+        pass = 1;
+    }
+    while (ok) {
+        // U = P^{-1} (rho A~'z - A~'y - g)
+        for (int c = tid; c < n; c += ADMM_T) srhs[c] = rho * atz[c] - aty[c] - a.g[c];
+        __syncthreads();
+        for (int c = warp; c < n; c += NW) {
+            float s = 0.f;
+            for (int q = lane; q < n; q += 32) s = fmaf(Pinv[(long)c * n + q], srhs[q], s);
+            s = wsum(s);
+            if (lane == 0) su[c] = s;
+        }
+        __syncthreads();
+        // box rows
+        float rpb = 0.f, amb = 0.f, zmb = 0.f;
+        for (int c = tid; c < n; c += ADMM_T) {
+            const float av = su[c];
+            const float zn = fminf(fmaxf(av + yb[c] / rho, a.lo[c]), a.hi[c]);
+            yb[c] = yb[c] + rho * (av - zn);
+            zb[c] = zn;
+            rpb = nmaxf(rpb, fabsf(av - zn));
+            amb = nmaxf(amb, fabsf(av));
+            zmb = nmaxf(zmb, fabsf(zn));
+        }
+        rpb = wmaxf(rpb);
+        amb = wmaxf(amb);
+        zmb = wmaxf(zmb);
+        if (lane == 0) {
+            wred[warp] = rpb;
+            wred[NW + warp] = amb;
+            wred[2 * NW + warp] = zmb;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+            for (int w = 0; w < NW; ++w) {
+                m0 = nmaxf(m0, wred[w]);
+                m1 = nmaxf(m1, wred[NW + w]);
+                m2 = nmaxf(m2, wred[2 * NW + w]);
+            }
+            s_misc[0] = m0;
+            s_misc[1] = m1;
+            s_misc[2] = m2;
+        }
+        float* accw = a.acc + (pass % 3) * stride;
+        if (blockIdx.x == 0)
+            for (int t = tid; t < stride; t += ADMM_T) a.acc[((pass + 1) % 3) * stride + t] = 0.f;
+        row_pass(false, accw);
+        ++phase;
+        if (!grid_barrier(a.bar, G, phase, a.max_spins, a.status)) {
+            ok = false;
+            break;
+        }
+        ++it;
+        float rpr, amr, zmr;
+        read_pass(accw, rpr, amr, zmr);
+        __syncthreads();
+        // r_d = rho |A~'z_prev - A~'z|_inf ; new A~'y
+        float m = 0.f;
+        for (int c = tid; c < n; c += ADMM_T) {
+            m = nmaxf(m, fabsf(srhs[c] - atz[c]));
+            atz[c] = srhs[c];
+            aty[c] = __ldcg(accw + n + c) + yb[c];
+        }
+        m = wmaxf(m);
+        if (lane == 0) wred[3 * NW + warp] = m;
+        __syncthreads();
+        float mm = 0.f;
+        for (int w = 0; w < NW; ++w) mm = nmaxf(mm, wred[3 * NW + w]);
+        const float rp = nmaxf(rpr, s_misc[0]);
+        const float rd = rho * mm;
+        const float amax = nmaxf(amr, s_misc[1]);
+        const float zmax = nmaxf(zmr, s_misc[2]);
+        rp_last = rp;
+        rd_last = rd;
+        ++pass;
+        const bool bad = (rp != rp) || (rd != rd);
+        converged = rp <= a.tol && rd <= a.tol;
+        if (bad && blockIdx.x == 0 && tid == 0) dev_fail(a.status, GM_ERR_NUMERIC);
+        if (converged || bad || it >= a.max_iter) {
+            done = true;
+            break;
+        }
+        if (a.adapt_every > 0 && !a.last_round && it % a.adapt_every == 0) {
+            // relative residuals: r_p / max(|a|, |z|) against r_d / max(|H U|, |A~'y|, |g|)
+            float hu = 0.f, gm = 0.f, ym = 0.f;
+            for (int c = warp; c < n; c += NW) {
+                float s = 0.f;
+                for (int q = lane; q < n; q += 32) s = fmaf(a.H[(long)c * n + q], su[q], s);
+                s = wsum(s);
+                hu = nmaxf(hu, fabsf(s));
+            }
+            for (int c = lane; c < n; c += 32) {
+                gm = nmaxf(gm, fabsf(a.g[c]));
+                ym = nmaxf(ym, fabsf(aty[c]));
+            }
+            gm = wmaxf(gm);
+            ym = wmaxf(ym);
+            if (lane == 0) wred[warp] = hu;
+            __syncthreads();
+            float hm = 0.f;
+            for (int w = 0; w < NW; ++w) hm = nmaxf(hm, wred[w]);
+            const float ps = fmaxf(fmaxf(amax, zmax), 1e-30f);
+            const float ds = fmaxf(fmaxf(hm, fmaxf(ym, gm)), 1e-30f);
+            const float ratio = (rp / ps) / fmaxf(rd / ds, 1e-30f);
+            float rn = rho * sqrtf(fmaxf(ratio, 0.f));
+            rn = fminf(fmaxf(rn, 1e-6f), 1e6f);
+            __syncthreads();
+            if (rn > 5.f * rho || rn < 0.2f * rho) {
+                adapt = true;
+                if (blockIdx.x == 0 && tid == 0) {
+                    S->rho = rn;
+                    S->updates = S->updates + 1;
+                }
+                break;
+            }
+        }
+    }
+    // save the state (CTA 0) / finish
+    if (blockIdx.x == 0) {
+        for (int c = tid; c < n; c += ADMM_T) {
+            S->u[c] = su[c];
+            S->zb[c] = zb[c];
+            S->yb[c] = yb[c];
+            S->atz[c] = atz[c];
+            S->aty[c] = aty[c];
+        }
+        if (tid == 0) {
+            S->iters = it;
+            S->started = 1;
+            S->rp = rp_last;
+            S->rd = rd_last;
+            S->converged = converged ? 1 : 0;
+            S->need_factor = adapt ? 1 : 0;
+            S->done = (done || !ok) ? 1 : 0;
+        }
+    }
+    if (done || !ok) {
+        // rows back to the original scaling: y_r = s_r y'_r, z_r = z'_r / s_r
+        if (a.rs)
+            for (long r = r0 + tid; r < r1; r += ADMM_T) {
+                const float s = a.rs[r];
+                a.y[n + r] *= s;
+                a.z[n + r] /= s;
+            }
+        if (blockIdx.x == 0) {
+            for (int c = tid; c < n; c += ADMM_T) {
+                a.U[c] = su[c];
+                a.y[c] = yb[c];
+                a.z[c] = zb[c];
+            }
+            if (tid == 0 && a.stats) {
+                a.stats->iters = it;
+                a.stats->converged = (converged && ok) ? 1 : 0;
+                a.stats->r_prim = rp_last;
+                a.stats->r_dual = rd_last;
+                a.stats->polished = 0;
+            }
+        }
+    }
+}
+
+// C~ rows split over `grid` CTAs by cost 16 + row length: boundary b is the first row
+// count whose cumulative cost reaches b/grid of the total (stage-major rows, so the
+// cumulative cost is piecewise linear; one thread per boundary).
+__global__ void admm_partition_kernel(long rows, int nu, int Mnc, int grid, int* rb) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > grid) return;
+    const int N = (int)(rows / Mnc);
+    double total = 0.0;
+    for (int k = 0; k < N; ++k) total += (double)Mnc * (16.0 + (double)(k + 1) * nu);
+    if (b == 0) { rb[0] = 0; return; }
+    if (b == grid) { rb[grid] = (int)rows; return; }
+    const double target = total * b / grid;
+    double cum = 0.0;
+    long m = rows;
+    for (int k = 0; k < N; ++k) {
+        const double per = 16.0 + (double)(k + 1) * nu;
+        if (cum + Mnc * per >= target) {
+            long j = (long)ceil((target - cum) / per);
+            j = j < 1 ? 1 : (j > Mnc ? Mnc : j);
+            m = (long)k * Mnc + j;
+            break;
+        }
+        cum += Mnc * per;
+    }
+    rb[b] = (int)m;
+}
+
+static size_t admm2_smem(int n, bool psmem, int tile_floats, int tile_rows) {
+    size_t f = (psmem ? (size_t)n * n : 0) + 8 * (size_t)n + 4 * (ADMM_T / 32) + 4;
+    f += 2 * (size_t)tile_floats + 8 * (size_t)tile_rows + 2 * (size_t)tile_rows;
+    return f * sizeof(float);
+}
+
+bool admm2_psmem(int n) { return admm2_smem(n, true, kAdmmTileFloats, kAdmmTileRows) <= 220 * 1024; }
+
+size_t admm2_smem_bytes(int n) { return admm2_smem(n, admm2_psmem(n), kAdmmTileFloats, kAdmmTileRows); }
+
+const void* admm2_kernel_ptr(int n) {
+    return admm2_psmem(n) ? (const void*)admm2_kernel<true> : (const void*)admm2_kernel<false>;
+}
+
+gm_status admm_solve(const AdmmPlan& p) {
+    cudaStream_t st = p.st;
+    const int n = p.n;
+    admm_state_init_kernel<<<1, 32, 0, st>>>(p.S, p.rho0);
+    GM_LAUNCH_CHECK();
+    admm_partition_kernel<<<cdiv(p.grid + 1, 128), 128, 0, st>>>(p.rows, p.nu, std::max(p.Mnc, 1), p.grid,
+                                                                 p.row_begin);
+    GM_LAUNCH_CHECK();
+    Admm2Args a{};
+    a.n = n; a.nu = p.nu; a.Mnc = std::max(p.Mnc, 1); a.rows = p.rows;
+    a.Ct = p.Ct; a.dt = p.dt; a.lo = p.lo; a.hi = p.hi; a.g = p.g; a.H = p.H; a.Pinv = p.Pinv;
+    a.rs = p.rs; a.U0 = p.U0; a.y0 = p.y0; a.U = p.U; a.y = p.y; a.z = p.z; a.acc = p.acc;
+    a.bar = p.bar; a.status = p.status; a.row_begin = p.row_begin; a.S = p.S; a.stats = p.stats;
+    a.tol = p.tol; a.max_iter = p.max_iter; a.adapt_every = p.adapt_every; a.max_spins = p.max_spins;
+    a.tile_floats = kAdmmTileFloats;
+    a.tile_rows = kAdmmTileRows;
+    a.vec4 = (p.nu % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.Ct) & 15) == 0);
+    const bool psmem = admm2_psmem(n);
+    const size_t smem = admm2_smem_bytes(n);
+    GM_CUDA_TRY(cudaFuncSetAttribute(admm2_kernel_ptr(n), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int r = 0; r < p.rounds; ++r) {
+        admm_form_p_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, p.H, p.Gram, p.S, p.P);
+        GM_LAUNCH_CHECK();
+        cholesky_kernel<<<1, 1024, 0, st>>>(n, p.P, p.L, p.status, p.S);
+        GM_LAUNCH_CHECK();
+        trinv_kernel<<<cdiv((long)n * 32, 128), 128, 0, st>>>(n, p.L, p.Linv, p.S);
+        GM_LAUNCH_CHECK();
+        pinv_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, p.Linv, p.Pinv, p.S);
+        GM_LAUNCH_CHECK();
+        if (r == 0 && p.ev_mid) GM_CUDA_TRY(cudaEventRecord(p.ev_mid, st));
+        GM_CUDA_TRY(cudaMemsetAsync(p.bar, 0, sizeof(unsigned) * 4, st));
+        GM_CUDA_TRY(cudaMemsetAsync(p.acc, 0, sizeof(float) * (2 * n + 4), st));
+        a.last_round = (r == p.rounds - 1) ? 1 : 0;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(p.grid);
+        cfg.blockDim = dim3(ADMM_T);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (psmem) {
+            GM_CUDA_TRY(cudaLaunchKernelEx(&cfg, admm2_kernel<true>, a));
+        } else {
+            GM_CUDA_TRY(cudaLaunchKernelEx(&cfg, admm2_kernel<false>, a));
+        }
+        GM_LAUNCH_CHECK();
+    }
+    return GM_OK;
+}
+
+}  // namespace gmi

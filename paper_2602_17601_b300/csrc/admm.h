@@ -1,0 +1,78 @@
+// ADMM solve of the condensed QP: device state, kernel arguments, launcher (internal).
+#pragma once
+
+#include "ctx.h"
+
+namespace gmi {
+
+constexpr int ADMM_T = 512;             // threads per CTA of the persistent kernel
+constexpr int kAdmmTileFloats = 8192;   // C~ floats per shared-memory tile (x2 buffers)
+constexpr int kAdmmTileRows = 512;      // rows per tile at most
+constexpr int kAdmmMaxN = 256;          // N nu
+
+// Iterate and control flags kept on the device between the launches of one solve.
+struct AdmmState {
+    float rho;
+    int need_factor;   // P(rho) must be formed and factored before the next launch
+    int done;          // converged, iteration cap reached, or failed
+    int started;       // initial pass done
+    int iters;
+    int updates;       // rho changes so far
+    int converged;
+    float rp, rd;
+    float u[kAdmmMaxN], zb[kAdmmMaxN], yb[kAdmmMaxN], atz[kAdmmMaxN], aty[kAdmmMaxN];
+};
+
+struct Admm2Args {
+    int n, nu, Mnc;
+    long rows;
+    const float *Ct, *dt, *lo, *hi, *g, *H, *Pinv, *rs, *U0, *y0;
+    float *U, *y, *z, *acc;
+    unsigned* bar;
+    int* status;
+    const int* row_begin;
+    AdmmState* S;
+    gm_stats* stats;
+    float tol;
+    int max_iter, adapt_every, last_round, tile_floats, tile_rows;
+    long long max_spins;
+    bool vec4;
+};
+
+// Everything one solve needs; scratch pointers come from a context workspace or
+// from the library-held scratch of gm_qp_solve_noalloc.
+struct AdmmPlan {
+    int n, nu, Mnc, N;
+    long rows;
+    const float *Ct, *dt, *lo, *hi, *g, *H, *U0, *y0;
+    const float* rs;       // row scales or nullptr
+    const float* Gram;     // C~' D C~ or nullptr when there are no half-space rows
+    float *U, *y, *z;      // y, z: [n + rows]
+    float *P, *Pinv;       // [n n]
+    double *L, *Linv;      // [n n]
+    float* acc;            // [3 (2n + 4)]
+    unsigned* bar;         // [4]
+    int* status;           // [4]
+    int* row_begin;        // [grid + 1]
+    AdmmState* S;
+    gm_stats* stats;
+    float rho0, tol;
+    int max_iter, adapt_every, rounds, grid;
+    long long max_spins;
+    cudaStream_t st;
+    cudaEvent_t ev_mid;    // recorded after the first factorisation (nullable)
+};
+
+gm_status admm_solve(const AdmmPlan& p);
+size_t admm2_smem_bytes(int n);
+const void* admm2_kernel_ptr(int n);
+
+// FP64 factor kernels (qp.cu); gate (nullable) skips them when no factorisation is due.
+__global__ void cholesky_kernel(int n, const float* __restrict__ P, double* __restrict__ L, int* status,
+                                const AdmmState* gate);
+__global__ void trinv_kernel(int n, const double* __restrict__ L, double* __restrict__ Linv,
+                             const AdmmState* gate);
+__global__ void pinv_kernel(int n, const double* __restrict__ Linv, float* __restrict__ Pinv,
+                            const AdmmState* gate);
+
+}  // namespace gmi

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "admm.h"
 #include "ctx.h"
 #include "kernels.h"
 
@@ -276,7 +277,9 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_Linv = cv.take<double>((size_t)nU * nU);
     c->d_P = cv.take<float>((size_t)nU * nU);
     c->d_Pinv = cv.take<float>((size_t)nU * nU);
-    c->d_acc = cv.take<float>(3 * (2 * (size_t)nU + 1));
+    c->d_G = cv.take<float>((size_t)nU * nU);
+    c->d_admm = cv.take<AdmmState>(1);
+    c->d_acc = cv.take<float>(3 * (2 * (size_t)nU + 4));
     c->d_bar = cv.take<unsigned>(4);
     c->d_status = cv.take<int>(4);
     c->d_row_begin = cv.take<int>(kMaxAdmmGrid + 1);
@@ -447,30 +450,19 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
     rs.push_back(up(c->dc.enc_dst_list, C.enc_dst_list, st));
     rs.push_back(up(c->dc.nr_ptr_K, C.nr_ptr[K], st));
     rs.push_back(up(c->dc.b_row, C.b_row, st));
-    // ADMM: one CTA per SM (co-resident, cooperative), C~ rows split by non-zeros
+    // ADMM: co-resident CTAs (cooperative launch); the row split is made on the device per solve
     {
         int occ = 0;
         if (cudaFuncSetAttribute(admm_kernel_ptr(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)admm_smem_bytes(c)) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, admm_kernel_ptr(c), 256, admm_smem_bytes(c)) != cudaSuccess) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, admm_kernel_ptr(c), ADMM_T, admm_smem_bytes(c)) !=
+                cudaSuccess) {
             set_error("ADMM occupancy query failed: %s", cudaGetErrorString(cudaGetLastError()));
             return fail(GM_ERR_CUDA);
         }
         occ = std::max(occ, 1);
         long want = c->rows_c > 0 ? std::max(1L, std::min((long)occ * c->num_sms, c->rows_c / 16)) : 1;
         c->admm_grid = (int)std::min<long>(want, kMaxAdmmGrid);
-        const long Mnc = (long)c->M * c->n_c;
-        double total = 0;
-        for (int k = 1; k <= c->N; ++k) total += (double)Mnc * k * c->nu;
-        std::vector<int> rb(c->admm_grid + 1, 0);
-        double acc = 0;
-        int b = 1;
-        for (long r = 0; r < c->rows_c && b < c->admm_grid; ++r) {
-            acc += (double)((r / std::max(1L, Mnc)) + 1) * c->nu;
-            while (b < c->admm_grid && acc >= total * b / c->admm_grid) rb[b++] = (int)(r + 1);
-        }
-        for (; b <= c->admm_grid; ++b) rb[b] = (int)c->rows_c;
-        rs.push_back(up(c->d_row_begin, rb, st));
         // every upload above reads host vectors that must outlive the copies
     }
     for (gm_status r : rs)

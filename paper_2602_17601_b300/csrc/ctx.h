@@ -19,6 +19,8 @@ struct gm_gnn {
 
 namespace gmi {
 
+struct AdmmState;
+
 // One 2-layer MLP as stored on the device (offsets into the weight array).
 struct MlpOff {
     int in = 0, hid = 0, out = 0;
@@ -103,7 +105,8 @@ struct gm_ctx {
     float *d_U = nullptr, *d_y = nullptr, *d_z = nullptr, *d_rs = nullptr;
     float *d_gram_part = nullptr;
     double *d_L = nullptr, *d_Linv = nullptr;
-    float *d_P = nullptr, *d_Pinv = nullptr;
+    float *d_P = nullptr, *d_Pinv = nullptr, *d_G = nullptr;
+    gmi::AdmmState* d_admm = nullptr;
     float *d_acc = nullptr;      // ADMM reduction buffers [3][2 nU + 2]
     unsigned* d_bar = nullptr;   // grid barrier counters
     int* d_status = nullptr;     // device status word(s)

@@ -127,7 +127,7 @@ def test_qp_parity(lib, constrained):
     hi = wl.u_hi.reshape(-1).astype(np.float64)
     Ua, za, ya, it_o, rp_o, rd_o, ok_o = oqp.admm(H64, g64, lo, hi, Ct64 if Cx.shape[2] else None,
                                                   dt64 if Cx.shape[2] else None, rho=wl.rho, tol=wl.tol,
-                                                  max_iter=wl.max_iter, scale_rows=True)
+                                                  max_iter=wl.max_iter, scale_rows=True, adapt_every=25)
     Ux, yx, _ = oqp.solve_exact(H64, g64, lo, hi, Ct64 if Cx.shape[2] else None,
                                 dt64 if Cx.shape[2] else None)
     n_c = Cx.shape[2]
