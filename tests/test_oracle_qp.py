@@ -114,7 +114,8 @@ def test_row_scaled_admm_reaches_the_same_optimum():
 def test_adaptive_rho_admm_reaches_the_optimum(seed):
     """Re-factoring with an adapted rho keeps the fixed point: the same U* is reached."""
     H, g, lo, hi, C, d = random_qp(8, 6, 50 + seed)
-    C = C * np.array([1e-5, 1e-3, 1.0, 1.0, 30.0, 1e2])[:, None]
+    f = np.array([1e-5, 1e-3, 1.0, 1.0, 30.0, 1e2])
+    C, d = C * f[:, None], d * f
     U, y, _ = qp.solve_exact(H, g, lo, hi, C, d)
     Ua, za, ya, it, rp, rd, ok = qp.admm(H, g, lo, hi, C, d, rho=0.1, tol=1e-11, max_iter=100000,
                                          scale_rows=True, adapt_every=25)
