@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--form", default="fp32", choices=["fp32", "mixed"])
+    p.add_argument("--form", default="fp32", choices=["fp32", "mixed", "bf16"])
     p.add_argument("--workload", default="chain1000", choices=["chain1000", "chain10"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -224,7 +224,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     wl = workload(args.workload)
-    prec = gm.GM_PREC_MIXED if args.form == "mixed" else gm.GM_PREC_FP32
+    prec = {"fp32": gm.GM_PREC_FP32, "mixed": gm.GM_PREC_MIXED, "bf16": gm.GM_PREC_BF16}[args.form]
     prob = gm.RTIProblem.from_workload(wl, precision=prec)
     info = gm.gm_ctx_info(prob.ctx)
     stream = torch.cuda.current_stream()

@@ -51,8 +51,11 @@ typedef int gm_status;
 /* Precision forms of the step. */
 #define GM_PREC_FP32   0   /* every GNN, Jacobian, condensing and ADMM op in FP32 (SIMT);
                               Cholesky of rho I + H (+ rho C~'C~) and the KKT check in FP64 */
-#define GM_PREC_MIXED  1   /* GNN MLPs and Jacobian products on tcgen05 tensor cores
-                              (BF16 operands, FP32 accumulate); the rest as GM_PREC_FP32 */
+#define GM_PREC_MIXED  1   /* GNN MLPs and Jacobian products on tcgen05 tensor cores with
+                              split BF16 operands (x = hi + lo, three products, FP32
+                              accumulate: about FP32 accuracy); the rest as GM_PREC_FP32 */
+#define GM_PREC_BF16   2   /* as GM_PREC_MIXED with one BF16 product (hi parts only):
+                              about 1e-2 relative error in the Jacobians */
 
 typedef struct gm_graph gm_graph;
 typedef struct gm_gnn gm_gnn;

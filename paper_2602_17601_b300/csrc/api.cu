@@ -143,7 +143,43 @@ static long put(std::vector<float>& w, const float* p, size_t n) {
     return o;
 }
 
-static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::vector<MlpOff>& offs) {
+// BF16 bit pattern of a float, round to nearest even (NaN kept quiet).
+static uint16_t to_bf16(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// [rows][cols] matrix with entry (r, c) = f(r, c), appended 128-byte aligned.
+static float from_bf16(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// hi = bf16(f), lo = bf16(f - hi): the two parts of the split tensor-core operands.
+template <class F>
+static long put_bf(std::vector<uint16_t>& wb, std::vector<uint16_t>& wl, int rows, int cols, F f) {
+    while (wb.size() % 64) {
+        wb.push_back(0);
+        wl.push_back(0);
+    }
+    long o = (long)wb.size();
+    for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) {
+            const float v = f(r, c);
+            const uint16_t h = to_bf16(v);
+            wb.push_back(h);
+            wl.push_back(to_bf16(v - from_bf16(h)));
+        }
+    return o;
+}
+
+static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::vector<MlpOff>& offs,
+                          std::vector<uint16_t>& wb, std::vector<uint16_t>& wl) {
     const int K = m.d.K, W = m.d.W;
     std::vector<std::array<int, 3>> shapes;
     shapes.push_back({6 + nu, W, W});
@@ -190,6 +226,20 @@ static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::v
                 }
             mo.Bab = put(w, t.data(), t.size());
         }
+        // K-major BF16 operands of the tensor-core products (see MlpOff)
+        auto up16 = [](int v) { return (v + 15) / 16 * 16; };
+        mo.in_p = up16(in);
+        mo.out_p = up16(out);
+        mo.fk1 = put_bf(wb, wl, hid, mo.in_p, [&](int j, int i) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
+        mo.fk2 = put_bf(wb, wl, mo.out_p, hid, [&](int o, int j) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
+        mo.bk1 = put_bf(wb, wl, hid, mo.out_p, [&](int j, int o) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
+        mo.bk2 = put_bf(wb, wl, mo.in_p, hid, [&](int i, int j) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
+        if (edge_mp) {
+            mo.wck = put_bf(wb, wl, W, hid, [&](int n, int j) { return W1[(size_t)(2 * W + n) * hid + j]; });
+            mo.babk = put_bf(wb, wl, W, 2 * W, [&](int n, int k) {
+                return k < W ? W1[(size_t)n * hid + k] : W1[(size_t)(W + n) * hid + (k - W)];
+            });
+        }
         offs.push_back(mo);
     }
 }
@@ -221,6 +271,8 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_act = cv.take<int>(nu);
     c->d_jac_col = cv.take<int>(c->nnzb);
     c->d_wts = cv.take<float>(c->wts_host.size());
+    c->d_wbf = cv.take<uint16_t>(std::max<size_t>(c->wbf_host.size(), 1));
+    c->d_wbl = cv.take<uint16_t>(std::max<size_t>(c->wbl_host.size(), 1));
     for (int r = 0; r <= K; ++r) {
         c->dc.nr_count[r] = (int)C.nr_node[r].size();
         c->dc.nr_node[r] = cv.take<int>(C.nr_node[r].size() + 1);
@@ -356,7 +408,8 @@ static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* 
     GM_CHECK_ARG(g->nu == m->d.nu, "graph has nu=%d, GNN has nu=%d", g->nu, m->d.nu);
     GM_CHECK_ARG(s->N >= 1 && s->N <= 64, "N must be in [1, 64] (got %d)", s->N);
     GM_CHECK_ARG(s->n_c >= 0 && s->n_c <= 64, "n_c must be in [0, 64]");
-    GM_CHECK_ARG(s->precision == GM_PREC_FP32 || s->precision == GM_PREC_MIXED, "unknown precision %d", s->precision);
+    GM_CHECK_ARG(s->precision == GM_PREC_FP32 || s->precision == GM_PREC_MIXED || s->precision == GM_PREC_BF16,
+                 "unknown precision %d", s->precision);
     GM_CHECK_ARG(s->rho > 0.f && s->tol > 0.f && s->max_iter >= 1, "rho, tol must be > 0 and max_iter >= 1");
     GM_CHECK_ARG((long)s->N * g->nu <= 256, "N * nu must be <= 256 (got %d)", s->N * g->nu);
     c->s = *s;
@@ -369,7 +422,7 @@ static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* 
     c->jac_row_ptr = c->cones.nr_ptr[c->K];
     c->jac_col = c->cones.nr_node[c->K];
     c->nnzb = (int)c->jac_col.size();
-    build_weights(*m, g->nu, c->wts_host, c->mlp);
+    build_weights(*m, g->nu, c->wts_host, c->mlp, c->wbf_host, c->wbl_host);
     return GM_OK;
 }
 
@@ -434,6 +487,8 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
     rs.push_back(up(c->d_act, c->graph.act_node, st));
     rs.push_back(up(c->d_jac_col, c->jac_col, st));
     rs.push_back(up(c->d_wts, c->wts_host, st));
+    rs.push_back(up(c->d_wbf, c->wbf_host, st));
+    rs.push_back(up(c->d_wbl, c->wbl_host, st));
     for (int r = 0; r <= K; ++r) {
         rs.push_back(up(c->dc.nr_node[r], C.nr_node[r], st));
         rs.push_back(up(c->dc.nr_prev[r], C.nr_prev[r], st));
@@ -467,7 +522,8 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
     }
     for (gm_status r : rs)
         if (r != GM_OK) return fail(r);
-    if (cudaMemsetAsync(c->d_u_hat, 0, sizeof(float) * c->N * c->nu, st) != cudaSuccess ||
+    if (cudaMemsetAsync(c->d_status, 0, sizeof(int) * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(c->d_u_hat, 0, sizeof(float) * c->N * c->nu, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("context upload failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(GM_ERR_CUDA);
@@ -580,6 +636,7 @@ gm_status gm_linearize(gm_ctx* ctx, const float* x0, const float* u_hat, float* 
     clear_error();
     GM_CHECK_ARG(ctx && x0 && u_hat && x_hat, "NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GM_CUDA_TRY(cudaMemsetAsync(ctx->d_status + 2, 0, sizeof(int), st));
     GM_TRY(gnn_rollout(ctx, x0, u_hat, x_hat, st));
     GM_TRY(gnn_jacobians(ctx, x_hat, u_hat, A, B, c, st));
     return GM_OK;
@@ -639,6 +696,7 @@ gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, con
         c->events.push_back(ev);
         GM_CUDA_TRY(cudaEventRecord(ev[0], st));
     }
+    GM_CUDA_TRY(cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), st));
     GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
     if (timed) GM_CUDA_TRY(cudaEventRecord(ev[1], st));
     GM_TRY(gnn_jacobians(c, c->d_x_hat, c->d_u_hat, c->d_A, c->d_B, c->d_c, st));

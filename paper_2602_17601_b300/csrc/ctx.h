@@ -30,6 +30,11 @@ struct MlpOff {
     // edge-update MLPs only: the split of W1 by input block [h_dst | h_src | e]
     long Wc = 0;                            // [hid][W]:  Wc[j][n]  = W1[2W + n][j]
     long Bab = 0;                           // [2W][W]:   Bab[j][n] = W1[n][j], Bab[W+j][n] = W1[W+n][j]
+    // BF16 K-major copies for the tensor-core kernels ([N rows][K], K and N padded to 16)
+    int in_p = 0, out_p = 0;                // in, out rounded up to a multiple of 16
+    long fk1 = 0, fk2 = 0;                  // forward:  W1^T [hid][in_p], W2^T [out_p][hid]
+    long bk1 = 0, bk2 = 0;                  // reverse:  W2 [hid][out_p],   W1 [in_p][hid]
+    long wck = 0, babk = 0;                 // edge MLPs: Wc^T [W][W], Bab^T [W][2W]
 };
 
 // Rows of the reverse-mode cones (one seed = one output node s, 3 cotangent
@@ -78,6 +83,7 @@ struct gm_ctx {
     // host copies
     gm_graph graph;
     std::vector<float> wts_host;
+    std::vector<uint16_t> wbf_host, wbl_host;   // BF16 hi / lo parts of the tensor-core operands
     std::vector<int> jac_row_ptr, jac_col;
     gmi::Cones cones;
     std::vector<gmi::MlpOff> mlp;   // blob order: ne, ee, (em, nm) x K, dec
@@ -89,6 +95,7 @@ struct gm_ctx {
     int *d_src = nullptr, *d_dst = nullptr, *d_in_ptr = nullptr, *d_act = nullptr;
     int *d_jac_col = nullptr;
     float* d_wts = nullptr;
+    uint16_t *d_wbf = nullptr, *d_wbl = nullptr;
     gmi::DCones dc{};
     // rollout
     float *d_h = nullptr, *d_e = nullptr, *d_agg = nullptr;

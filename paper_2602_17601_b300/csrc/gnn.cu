@@ -19,6 +19,14 @@
 #include "kernels.h"
 
 namespace gmi {
+struct RowCtx {
+    int a, b, c, d, e, f;
+};
+}  // namespace gmi
+
+#include "tc_mlp.cuh"
+
+namespace gmi {
 
 constexpr int BM = 64;
 constexpr int BK = 16;
@@ -30,10 +38,6 @@ struct TileShape {
     static constexpr int VEC = TN < 4 ? TN : 4;
     static constexpr int NH = TN / VEC;
     __device__ static int col(int tx, int j) { return tx * VEC + (j % VEC) + (j / VEC) * 16 * VEC; }
-};
-
-struct RowCtx {
-    int a, b, c, d, e, f;
 };
 
 // Fused MLP kernel.  Op provides:
@@ -182,9 +186,26 @@ __global__ void __launch_bounds__(NT) mlp2_kernel(Op op) {
 }
 
 // ======================================================================= forward ops
+// 8 consecutive floats (16-byte aligned rows): v = p[0..7], or v += p[0..7]
+__device__ __forceinline__ void ld8(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void add8(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w; v[4] += b.x; v[5] += b.y; v[6] += b.z; v[7] += b.w;
+}
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
 struct FwdBase {
     static constexpr int kMode = 0;
     static constexpr bool kStoreHid = false;
+    static constexpr bool kHasIn8 = false;
+    static constexpr bool kHasOut4 = false;
     long rows;
     int kin, nout;
     const float *B1, *b1, *B2, *b2;
@@ -210,6 +231,8 @@ struct NodeEncFwd : FwdBase {
         return act[a] == c.a ? u[a] : 0.f;
     }
     __device__ void out(const RowCtx& c, int n, float v) const { h[(long)c.a * W + n] = v; }
+    static constexpr bool kHasOut4 = true;
+    __device__ void out4(const RowCtx& c, int n, float4 v) const { st4(h + (long)c.a * W + n, v); }
 };
 
 struct EdgeEncFwd : FwdBase {
@@ -222,6 +245,8 @@ struct EdgeEncFwd : FwdBase {
     }
     __device__ float in(const RowCtx& c, int k) const { return x[c.c * 6 + k] - x[c.b * 6 + k]; }
     __device__ void out(const RowCtx& c, int n, float v) const { e[(long)c.a * W + n] = v; }
+    static constexpr bool kHasOut4 = true;
+    __device__ void out4(const RowCtx& c, int n, float4 v) const { st4(e + (long)c.a * W + n, v); }
 };
 
 struct EdgeMpFwd : FwdBase {
@@ -239,6 +264,16 @@ struct EdgeMpFwd : FwdBase {
     }
     // residual update in place: the block's own rows were fully read by GEMM1
     __device__ void out(const RowCtx& c, int n, float v) const { e[(long)c.a * W + n] += v; }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true;
+    __device__ void in8(const RowCtx& c, int k0, float* v) const {
+        const float* p = k0 < W ? h + (long)c.c * W + k0
+                                : (k0 < 2 * W ? h + (long)c.b * W + k0 - W : e + (long)c.a * W + k0 - 2 * W);
+        ld8(p, v);
+    }
+    __device__ void out4(const RowCtx& c, int n, float4 v) const {
+        float* p = e + (long)c.a * W + n;
+        st4(p, add4(ld4(p), v));
+    }
 };
 
 struct NodeMpFwd : FwdBase {
@@ -250,6 +285,14 @@ struct NodeMpFwd : FwdBase {
         return k < W ? h[(long)c.a * W + k] : agg[(long)c.a * W + k - W];
     }
     __device__ void out(const RowCtx& c, int n, float v) const { h[(long)c.a * W + n] += v; }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true;
+    __device__ void in8(const RowCtx& c, int k0, float* v) const {
+        ld8(k0 < W ? h + (long)c.a * W + k0 : agg + (long)c.a * W + k0 - W, v);
+    }
+    __device__ void out4(const RowCtx& c, int n, float4 v) const {
+        float* p = h + (long)c.a * W + n;
+        st4(p, add4(ld4(p), v));
+    }
 };
 
 struct DecFwd : FwdBase {
@@ -260,6 +303,8 @@ struct DecFwd : FwdBase {
     int W;
     __device__ RowCtx prep(long r) const { return RowCtx{(int)r, 0, 0, 0, 0, 0}; }
     __device__ float in(const RowCtx& c, int k) const { return h[(long)c.a * W + k]; }
+    static constexpr bool kHasIn8 = true;
+    __device__ void in8(const RowCtx& c, int k0, float* v) const { ld8(h + (long)c.a * W + k0, v); }
     __device__ void out(const RowCtx& c, int n, float dv) const {
         // semi-implicit Euler: v+ = v + dv, p+ = p + dt v+
         float v1 = x[c.a * 6 + 3 + n] + dv;
@@ -278,18 +323,69 @@ __global__ void agg_kernel(int M, int W, const int* __restrict__ in_ptr, const f
     agg[t] = s;
 }
 
-template <class Op>
-static gm_status launch_mlp(int W, const Op& op, cudaStream_t st) {
-    if (op.rows <= 0) return GM_OK;
-    int grid = cdiv(op.rows, BM);
+template <int W, int SPLIT, class Op>
+static gm_status launch_tc(const Op& op, const TcW& tw, cudaStream_t st) {
+    constexpr size_t smem = tc_smem_bytes<W, SPLIT>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_kernel<W, Op, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        attr_set = true;
+    }
+    tc_mlp_kernel<W, Op, SPLIT><<<cdiv(op.rows, TC_M), TC_T, smem, st>>>(op, tw);
+    return GM_OK;
+}
+
+template <int SPLIT, class Op>
+static gm_status launch_tc_w(int W, const Op& op, const TcW& tw, cudaStream_t st) {
     switch (W) {
-        case 32: mlp2_kernel<32, Op><<<grid, NT, 0, st>>>(op); break;
-        case 64: mlp2_kernel<64, Op><<<grid, NT, 0, st>>>(op); break;
-        case 128: mlp2_kernel<128, Op><<<grid, NT, 0, st>>>(op); break;
+        case 32: return launch_tc<32, SPLIT>(op, tw, st);
+        case 64: return launch_tc<64, SPLIT>(op, tw, st);
+        case 128: return launch_tc<128, SPLIT>(op, tw, st);
         default: set_error("unsupported W %d", W); return GM_ERR_INVALID_ARG;
+    }
+}
+
+// FP32 SIMT kernel, or the tcgen05 kernel in the mixed-precision forms.
+template <class Op>
+static gm_status launch_mlp(const gm_ctx* c, const Op& op, const TcW& tw, cudaStream_t st) {
+    if (op.rows <= 0) return GM_OK;
+    const int W = c->W;
+    if (c->s.precision == GM_PREC_MIXED) {
+        GM_TRY(launch_tc_w<3>(W, op, tw, st));
+    } else if (c->s.precision == GM_PREC_BF16) {
+        GM_TRY(launch_tc_w<1>(W, op, tw, st));
+    } else {
+        int grid = cdiv(op.rows, BM);
+        switch (W) {
+            case 32: mlp2_kernel<32, Op><<<grid, NT, 0, st>>>(op); break;
+            case 64: mlp2_kernel<64, Op><<<grid, NT, 0, st>>>(op); break;
+            case 128: mlp2_kernel<128, Op><<<grid, NT, 0, st>>>(op); break;
+            default: set_error("unsupported W %d", W); return GM_ERR_INVALID_ARG;
+        }
     }
     GM_LAUNCH_CHECK();
     return GM_OK;
+}
+
+// Tensor-core operands of one MLP (see MlpOff): forward, reverse, and the edge-update splits.
+static const __nv_bfloat16* bf(const gm_ctx* c, long off) {
+    return reinterpret_cast<const __nv_bfloat16*>(c->d_wbf + off);
+}
+static const __nv_bfloat16* bl(const gm_ctx* c, long off) {
+    return reinterpret_cast<const __nv_bfloat16*>(c->d_wbl + off);
+}
+static TcW tc_fwd(const gm_ctx* c, const MlpOff& m) {
+    return TcW{bf(c, m.fk1), bf(c, m.fk2), bl(c, m.fk1), bl(c, m.fk2), m.in_p, m.out_p, c->d_status + 2};
+}
+static TcW tc_bwd(const gm_ctx* c, const MlpOff& m) {
+    return TcW{bf(c, m.bk1), bf(c, m.bk2), bl(c, m.bk1), bl(c, m.bk2), m.out_p, m.in_p, c->d_status + 2};
+}
+static TcW tc_edge_bwd(const gm_ctx* c, const MlpOff& m) {
+    return TcW{bf(c, m.bk1), bf(c, m.wck), bl(c, m.bk1), bl(c, m.wck), m.out_p, c->W, c->d_status + 2};
+}
+static TcW tc_nodesum(const gm_ctx* c, const MlpOff& m) {
+    return TcW{bf(c, m.babk), nullptr, bl(c, m.babk), nullptr, 2 * c->W, 0, c->d_status + 2};
 }
 
 template <class Op>
@@ -324,19 +420,19 @@ gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_h
         NodeEncFwd ne{};
         fill_fwd(ne, c, 0, M, node_mask(c, k, 0));
         ne.x = xk; ne.u = u_hat + (long)k * c->nu; ne.act = c->d_act; ne.h = c->d_h; ne.W = W; ne.nu = c->nu;
-        GM_TRY(launch_mlp(W, ne, st));
+        GM_TRY(launch_mlp(c, ne, tc_fwd(c, c->mlp[0]), st));
         if (E > 0) {
             EdgeEncFwd ee{};
             fill_fwd(ee, c, 1, E, edge_mask(c, k, 0));
             ee.x = xk; ee.src = c->d_src; ee.dst = c->d_dst; ee.e = c->d_e; ee.W = W;
-            GM_TRY(launch_mlp(W, ee, st));
+            GM_TRY(launch_mlp(c, ee, tc_fwd(c, c->mlp[1]), st));
         }
         for (int t = 0; t < K; ++t) {
             if (E > 0) {
                 EdgeMpFwd em{};
                 fill_fwd(em, c, 2 + 2 * t, E, edge_mask(c, k, 1 + t));
                 em.h = c->d_h; em.src = c->d_src; em.dst = c->d_dst; em.e = c->d_e; em.W = W;
-                GM_TRY(launch_mlp(W, em, st));
+                GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * t]), st));
                 agg_kernel<<<cdiv((long)M * W, 256), 256, 0, st>>>(M, W, c->d_in_ptr, c->d_e, c->d_agg);
                 GM_LAUNCH_CHECK();
             } else {
@@ -345,12 +441,12 @@ gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_h
             NodeMpFwd nm{};
             fill_fwd(nm, c, 3 + 2 * t, M, node_mask(c, k, 1 + t));
             nm.h = c->d_h; nm.agg = c->d_agg; nm.W = W;
-            GM_TRY(launch_mlp(W, nm, st));
+            GM_TRY(launch_mlp(c, nm, tc_fwd(c, c->mlp[3 + 2 * t]), st));
         }
         DecFwd de{};
         fill_fwd(de, c, 2 + 2 * K, M, node_mask(c, k, K + 1));
         de.h = c->d_h; de.x = xk; de.xn = xn; de.dt = c->dt; de.W = W;
-        GM_TRY(launch_mlp(W, de, st));
+        GM_TRY(launch_mlp(c, de, tc_fwd(c, c->mlp[2 + 2 * K]), st));
     }
     return GM_OK;
 }
@@ -361,6 +457,8 @@ gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_h
 struct BwdBase {
     static constexpr int kMode = 1;
     static constexpr bool kStoreHid = false;
+    static constexpr bool kHasIn8 = false;
+    static constexpr bool kHasOut4 = false;
     long rows;
     int kin, nout;
     const float *B1, *b1 = nullptr, *B2, *b2 = nullptr;
@@ -395,6 +493,8 @@ struct DecBwd : BwdBase {
     }
     __device__ float in(const RowCtx& x, int k) const { return k == x.c ? 1.f : 0.f; }
     __device__ void out(const RowCtx& x, int n, float v) const { dh[(long)x.e * W + n] = v; }
+    static constexpr bool kHasOut4 = true;
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(dh + (long)x.e * W + n, v); }
 };
 
 struct NodeMpBwd : BwdBase {
@@ -414,6 +514,12 @@ struct NodeMpBwd : BwdBase {
     __device__ void out(const RowCtx& x, int n, float v) const {
         if (n < W) dacc[(long)x.e * W + n] = dh[(long)x.e * W + n] + v;
         else dagg[(long)x.e * W + n - W] = v;
+    }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(dh + (long)x.e * W + k0, v); }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const {
+        if (n < W) st4(dacc + (long)x.e * W + n, add4(ld4(dh + (long)x.e * W + n), v));
+        else st4(dagg + (long)x.e * W + n - W, v);
     }
 };
 
@@ -443,6 +549,17 @@ struct EdgeMpBwd : BwdBase {
     __device__ long self(const RowCtx& x) const { return ((long)x.a * R + x.b) * 3 + x.c; }
     __device__ void store_hid(const RowCtx& x, int n, float v) const { ehid[self(x) * W + n] = v; }
     __device__ void out(const RowCtx& x, int n, float v) const { de_out[self(x) * W + n] = in(x, n) + v; }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const {
+        ld8(dagg + (long)x.e * W + k0, v);
+        if (x.f >= 0) add8(de_in + (long)x.f * W + k0, v);
+    }
+    __device__ void store_hid4(const RowCtx& x, int n, float4 v) const { st4(ehid + self(x) * W + n, v); }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const {
+        float4 a = ld4(dagg + (long)x.e * W + n);
+        if (x.f >= 0) a = add4(a, ld4(de_in + (long)x.f * W + n));
+        st4(de_out + self(x) * W + n, add4(a, v));
+    }
 };
 
 struct NodeSumBwd : BwdBase {
@@ -478,6 +595,23 @@ struct NodeSumBwd : BwdBase {
         dh_next[(long)x.e * W + n] = a + v;
     }
     __device__ uint32_t mask_word(const RowCtx&, int) const { return 0u; }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        const long base = (long)x.a * Re;
+        if (k0 < W) {
+            if (x.d >= 0)
+                for (int p = dst_ptr[x.d]; p < dst_ptr[x.d + 1]; ++p) add8(ehid + ((base + p) * 3 + x.c) * W + k0, v);
+        } else {
+            for (int p = src_ptr[x.b]; p < src_ptr[x.b + 1]; ++p)
+                add8(ehid + ((base + src_list[p]) * 3 + x.c) * W + k0 - W, v);
+        }
+    }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const {
+        if (x.d >= 0) v = add4(v, ld4(dacc + (((long)x.a * Rr + x.d) * 3 + x.c) * W + n));
+        st4(dh_next + (long)x.e * W + n, v);
+    }
 };
 
 struct NodeEncBwd : BwdBase {
@@ -494,6 +628,8 @@ struct NodeEncBwd : BwdBase {
     }
     __device__ float in(const RowCtx& x, int k) const { return dh[(long)x.e * W + k]; }
     __device__ void out(const RowCtx& x, int n, float v) const { dxn[(long)x.e * nout + n] = v; }
+    static constexpr bool kHasIn8 = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(dh + (long)x.e * W + k0, v); }
 };
 
 struct EdgeEncBwd : BwdBase {
@@ -510,6 +646,8 @@ struct EdgeEncBwd : BwdBase {
     }
     __device__ float in(const RowCtx& x, int k) const { return de[(long)x.e * W + k]; }
     __device__ void out(const RowCtx& x, int n, float v) const { dd[(long)x.e * 6 + n] = v; }
+    static constexpr bool kHasIn8 = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(de + (long)x.e * W + k0, v); }
 };
 
 // One warp per (stage, seed s): A^{s n}, B^s and c^s from the pulled-back cotangents.
@@ -632,7 +770,7 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
             fill_bwd(op, c, c->mlp[2 + 2 * K], k0, K + 1, false, (long)Ns * M * 3, M, W);
             op.kin = 3;
             op.dh = X;
-            GM_TRY(launch_mlp(W, op, st));
+            GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[2 + 2 * K]), st));
         }
         for (int t = K - 1; t >= 0; --t) {
             const int r = K - 1 - t;
@@ -641,7 +779,7 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
                 NodeMpBwd op{};
                 fill_bwd(op, c, c->mlp[3 + 2 * t], k0, 1 + t, false, (long)Ns * Rn * 3, Rn, 2 * W);
                 op.dh = X; op.dacc = c->d_dacc; op.dagg = c->d_dagg; op.nr_node = d.nr_node[r];
-                GM_TRY(launch_mlp(W, op, st));
+                GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[3 + 2 * t]), st));
             }
             if (Re > 0) {
                 EdgeMpBwd op{};
@@ -651,7 +789,7 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
                 op.dagg = c->d_dagg; op.de_in = de_in; op.ehid = c->d_ehid; op.de_out = de_out;
                 op.er_edge = d.er_edge[r]; op.er_dstrow = d.er_dstrow[r]; op.er_prev = d.er_prev[r];
                 op.Rn = Rn; op.Rp = r > 0 ? d.er_count[r - 1] : 0;
-                GM_TRY(launch_mlp(W, op, st));
+                GM_TRY(launch_mlp(c, op, tc_edge_bwd(c, m), st));
             }
             {
                 const int Rn1 = d.nr_count[r + 1];
@@ -665,7 +803,7 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
                 op.nr_prev = d.nr_prev[r + 1]; op.dst_ptr = d.er_dst_ptr[r];
                 op.src_ptr = d.er_src_ptr[r]; op.src_list = d.er_src_list[r];
                 op.Rr = Rn; op.Re = Re;
-                GM_TRY(launch_mlp(W, op, st));
+                GM_TRY(launch_mlp(c, op, tc_nodesum(c, m), st));
             }
             std::swap(X, Y);
             de_in = de_out;
@@ -676,14 +814,14 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
             NodeEncBwd op{};
             fill_bwd(op, c, c->mlp[0], k0, 0, false, (long)Ns * RK * 3, RK);
             op.dh = X; op.dxn = c->d_dxn; op.nr_node = d.nr_node[K];
-            GM_TRY(launch_mlp(W, op, st));
+            GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[0]), st));
         }
         const int RE = d.er_count[K - 1];
         if (RE > 0) {
             EdgeEncBwd op{};
             fill_bwd(op, c, c->mlp[1], k0, 0, true, (long)Ns * RE * 3, RE);
             op.de = de_in; op.dd = c->d_dd; op.er_edge = d.er_edge[K - 1];
-            GM_TRY(launch_mlp(W, op, st));
+            GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[1]), st));
         }
         {
             const long warps = (long)Ns * M;

@@ -193,7 +193,7 @@ __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float
         stats->kkt_prim = nmax(nmax(prim, 0.0), kkt[n]);
         stats->kkt_dual = kkt[n + 1];
         stats->kkt_comp = nmax(comp, kkt[n + 2]);
-        int st = *status;
+        int st = status[0] | status[2];
         int code = GM_OK;
         if (st & (1 << GM_ERR_TIMEOUT)) code = GM_ERR_TIMEOUT;
         else if (st & (1 << GM_ERR_NUMERIC)) code = GM_ERR_NUMERIC;
@@ -208,7 +208,8 @@ static gm_status solve_with(AdmmPlan& p, int sms, int nsplit, float* gram_part, 
     const int n = p.n;
     const long rows = p.rows;
     cudaStream_t st = p.st;
-    GM_CUDA_TRY(cudaMemsetAsync(p.status, 0, sizeof(int) * 4, st));
+    // status[0..1]: this solve; status[2]: the GNN kernels of the same step (kept)
+    GM_CUDA_TRY(cudaMemsetAsync(p.status, 0, sizeof(int) * 2, st));
     if (rows > 0) {
         if (scale) {
             row_norm_kernel<<<cdiv(rows * 32, 256), 256, 0, st>>>(rows, p.nu, p.Mnc, p.Ct, const_cast<float*>(p.rs));
@@ -348,5 +349,6 @@ extern "C" gm_status gm_qp_solve_noalloc(int N, int nu, int Mnc, const gm_settin
     p.max_spins = s->timeout_spins > 0 ? s->timeout_spins : (1LL << 26);
     p.st = static_cast<cudaStream_t>(stream);
     p.ev_mid = nullptr;
+    GM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int) * 4, p.st));
     return solve_with(p, sms, kNoAllocSplit, part, scale, kkt);
 }
