@@ -160,26 +160,27 @@ static float from_bf16(uint16_t h) {
     return f;
 }
 
-// hi = bf16(f), lo = bf16(f - hi): the two parts of the split tensor-core operands.
+// The three BF16 pieces of a split tensor-core operand: p0 = bf16(f), p1 = bf16(f - p0),
+// p2 = bf16(f - p0 - p1); p0 + p1 + p2 carries about 24 significant bits of f.
 template <class F>
-static long put_bf(std::vector<uint16_t>& wb, std::vector<uint16_t>& wl, int rows, int cols, F f) {
-    while (wb.size() % 64) {
-        wb.push_back(0);
-        wl.push_back(0);
-    }
-    long o = (long)wb.size();
+static long put_bf(std::vector<uint16_t>* wp, int rows, int cols, F f) {
+    while (wp[0].size() % 64)
+        for (int p = 0; p < 3; ++p) wp[p].push_back(0);
+    long o = (long)wp[0].size();
     for (int r = 0; r < rows; ++r)
         for (int c = 0; c < cols; ++c) {
-            const float v = f(r, c);
-            const uint16_t h = to_bf16(v);
-            wb.push_back(h);
-            wl.push_back(to_bf16(v - from_bf16(h)));
+            float v = f(r, c);
+            for (int p = 0; p < 3; ++p) {
+                const uint16_t h = to_bf16(v);
+                wp[p].push_back(h);
+                v -= from_bf16(h);
+            }
         }
     return o;
 }
 
 static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::vector<MlpOff>& offs,
-                          std::vector<uint16_t>& wb, std::vector<uint16_t>& wl) {
+                          std::vector<uint16_t>* wp) {
     const int K = m.d.K, W = m.d.W;
     std::vector<std::array<int, 3>> shapes;
     shapes.push_back({6 + nu, W, W});
@@ -230,13 +231,13 @@ static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::v
         auto up16 = [](int v) { return (v + 15) / 16 * 16; };
         mo.in_p = up16(in);
         mo.out_p = up16(out);
-        mo.fk1 = put_bf(wb, wl, hid, mo.in_p, [&](int j, int i) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
-        mo.fk2 = put_bf(wb, wl, mo.out_p, hid, [&](int o, int j) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
-        mo.bk1 = put_bf(wb, wl, hid, mo.out_p, [&](int j, int o) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
-        mo.bk2 = put_bf(wb, wl, mo.in_p, hid, [&](int i, int j) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
+        mo.fk1 = put_bf(wp, hid, mo.in_p, [&](int j, int i) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
+        mo.fk2 = put_bf(wp, mo.out_p, hid, [&](int o, int j) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
+        mo.bk1 = put_bf(wp, hid, mo.out_p, [&](int j, int o) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
+        mo.bk2 = put_bf(wp, mo.in_p, hid, [&](int i, int j) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
         if (edge_mp) {
-            mo.wck = put_bf(wb, wl, W, hid, [&](int n, int j) { return W1[(size_t)(2 * W + n) * hid + j]; });
-            mo.babk = put_bf(wb, wl, W, 2 * W, [&](int n, int k) {
+            mo.wck = put_bf(wp, W, hid, [&](int n, int j) { return W1[(size_t)(2 * W + n) * hid + j]; });
+            mo.babk = put_bf(wp, W, 2 * W, [&](int n, int k) {
                 return k < W ? W1[(size_t)n * hid + k] : W1[(size_t)(W + n) * hid + (k - W)];
             });
         }
@@ -271,8 +272,7 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_act = cv.take<int>(nu);
     c->d_jac_col = cv.take<int>(c->nnzb);
     c->d_wts = cv.take<float>(c->wts_host.size());
-    c->d_wbf = cv.take<uint16_t>(std::max<size_t>(c->wbf_host.size(), 1));
-    c->d_wbl = cv.take<uint16_t>(std::max<size_t>(c->wbl_host.size(), 1));
+    for (int p = 0; p < 3; ++p) c->d_wbp[p] = cv.take<uint16_t>(std::max<size_t>(c->wbp_host[p].size(), 1));
     for (int r = 0; r <= K; ++r) {
         c->dc.nr_count[r] = (int)C.nr_node[r].size();
         c->dc.nr_node[r] = cv.take<int>(C.nr_node[r].size() + 1);
@@ -422,7 +422,7 @@ static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* 
     c->jac_row_ptr = c->cones.nr_ptr[c->K];
     c->jac_col = c->cones.nr_node[c->K];
     c->nnzb = (int)c->jac_col.size();
-    build_weights(*m, g->nu, c->wts_host, c->mlp, c->wbf_host, c->wbl_host);
+    build_weights(*m, g->nu, c->wts_host, c->mlp, c->wbp_host);
     return GM_OK;
 }
 
@@ -487,8 +487,7 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
     rs.push_back(up(c->d_act, c->graph.act_node, st));
     rs.push_back(up(c->d_jac_col, c->jac_col, st));
     rs.push_back(up(c->d_wts, c->wts_host, st));
-    rs.push_back(up(c->d_wbf, c->wbf_host, st));
-    rs.push_back(up(c->d_wbl, c->wbl_host, st));
+    for (int p = 0; p < 3; ++p) rs.push_back(up(c->d_wbp[p], c->wbp_host[p], st));
     for (int r = 0; r <= K; ++r) {
         rs.push_back(up(c->dc.nr_node[r], C.nr_node[r], st));
         rs.push_back(up(c->dc.nr_prev[r], C.nr_prev[r], st));

@@ -83,7 +83,8 @@ struct gm_ctx {
     // host copies
     gm_graph graph;
     std::vector<float> wts_host;
-    std::vector<uint16_t> wbf_host, wbl_host;   // BF16 hi / lo parts of the tensor-core operands
+    // BF16 pieces of the tensor-core weight operands: p0 = bf16(x), p1 = bf16(x - p0), p2 = bf16(x - p0 - p1)
+    std::vector<uint16_t> wbp_host[3];
     std::vector<int> jac_row_ptr, jac_col;
     gmi::Cones cones;
     std::vector<gmi::MlpOff> mlp;   // blob order: ne, ee, (em, nm) x K, dec
@@ -95,7 +96,7 @@ struct gm_ctx {
     int *d_src = nullptr, *d_dst = nullptr, *d_in_ptr = nullptr, *d_act = nullptr;
     int *d_jac_col = nullptr;
     float* d_wts = nullptr;
-    uint16_t *d_wbf = nullptr, *d_wbl = nullptr;
+    uint16_t* d_wbp[3] = {nullptr, nullptr, nullptr};
     gmi::DCones dc{};
     // rollout
     float *d_h = nullptr, *d_e = nullptr, *d_agg = nullptr;

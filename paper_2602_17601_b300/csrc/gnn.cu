@@ -323,36 +323,43 @@ __global__ void agg_kernel(int M, int W, const int* __restrict__ in_ptr, const f
     agg[t] = s;
 }
 
-template <int W, int SPLIT, class Op>
+template <int W, int P, class Op>
 static gm_status launch_tc(const Op& op, const TcW& tw, cudaStream_t st) {
-    constexpr size_t smem = tc_smem_bytes<W, SPLIT>();
+    constexpr size_t smem = tc_smem_bytes<W, P>();
     static bool attr_set = false;
     if (!attr_set) {
-        GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_kernel<W, Op, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_kernel<W, Op, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
         attr_set = true;
     }
-    tc_mlp_kernel<W, Op, SPLIT><<<cdiv(op.rows, TC_M), TC_T, smem, st>>>(op, tw);
+    tc_mlp_kernel<W, Op, P><<<cdiv(op.rows, TC_M), TC_T, smem, st>>>(op, tw);
     return GM_OK;
 }
 
-template <int SPLIT, class Op>
+template <int P, class Op>
 static gm_status launch_tc_w(int W, const Op& op, const TcW& tw, cudaStream_t st) {
     switch (W) {
-        case 32: return launch_tc<32, SPLIT>(op, tw, st);
-        case 64: return launch_tc<64, SPLIT>(op, tw, st);
-        case 128: return launch_tc<128, SPLIT>(op, tw, st);
+        case 32: return launch_tc<32, P>(op, tw, st);
+        case 64: return launch_tc<64, P>(op, tw, st);
+        case 128: return launch_tc<128, P>(op, tw, st);
         default: set_error("unsupported W %d", W); return GM_ERR_INVALID_ARG;
     }
 }
 
-// FP32 SIMT kernel, or the tcgen05 kernel in the mixed-precision forms.
+// FP32 SIMT kernel, or the tcgen05 kernel in the BF16 forms.  GM_PREC_MIXED evaluates the
+// forward rollout with three-piece operands (FP32 operand precision, so that the ReLU
+// pattern and x_hat match an FP32 evaluation) and the Jacobian products with two pieces;
+// GM_PREC_BF16 uses one piece everywhere.
 template <class Op>
 static gm_status launch_mlp(const gm_ctx* c, const Op& op, const TcW& tw, cudaStream_t st) {
     if (op.rows <= 0) return GM_OK;
     const int W = c->W;
     if (c->s.precision == GM_PREC_MIXED) {
-        GM_TRY(launch_tc_w<3>(W, op, tw, st));
+        if constexpr (Op::kMode == 0) {
+            GM_TRY(launch_tc_w<3>(W, op, tw, st));
+        } else {
+            GM_TRY(launch_tc_w<2>(W, op, tw, st));
+        }
     } else if (c->s.precision == GM_PREC_BF16) {
         GM_TRY(launch_tc_w<1>(W, op, tw, st));
     } else {
@@ -369,24 +376,21 @@ static gm_status launch_mlp(const gm_ctx* c, const Op& op, const TcW& tw, cudaSt
 }
 
 // Tensor-core operands of one MLP (see MlpOff): forward, reverse, and the edge-update splits.
-static const __nv_bfloat16* bf(const gm_ctx* c, long off) {
-    return reinterpret_cast<const __nv_bfloat16*>(c->d_wbf + off);
+static TcW tc_w(const gm_ctx* c, long off1, long off2, int K1p, int N2p) {
+    TcW w{};
+    for (int p = 0; p < 3; ++p) {
+        w.B1[p] = reinterpret_cast<const __nv_bfloat16*>(c->d_wbp[p] + off1);
+        w.B2[p] = off2 >= 0 ? reinterpret_cast<const __nv_bfloat16*>(c->d_wbp[p] + off2) : nullptr;
+    }
+    w.K1p = K1p;
+    w.N2p = N2p;
+    w.status = c->d_status + 2;
+    return w;
 }
-static const __nv_bfloat16* bl(const gm_ctx* c, long off) {
-    return reinterpret_cast<const __nv_bfloat16*>(c->d_wbl + off);
-}
-static TcW tc_fwd(const gm_ctx* c, const MlpOff& m) {
-    return TcW{bf(c, m.fk1), bf(c, m.fk2), bl(c, m.fk1), bl(c, m.fk2), m.in_p, m.out_p, c->d_status + 2};
-}
-static TcW tc_bwd(const gm_ctx* c, const MlpOff& m) {
-    return TcW{bf(c, m.bk1), bf(c, m.bk2), bl(c, m.bk1), bl(c, m.bk2), m.out_p, m.in_p, c->d_status + 2};
-}
-static TcW tc_edge_bwd(const gm_ctx* c, const MlpOff& m) {
-    return TcW{bf(c, m.bk1), bf(c, m.wck), bl(c, m.bk1), bl(c, m.wck), m.out_p, c->W, c->d_status + 2};
-}
-static TcW tc_nodesum(const gm_ctx* c, const MlpOff& m) {
-    return TcW{bf(c, m.babk), nullptr, bl(c, m.babk), nullptr, 2 * c->W, 0, c->d_status + 2};
-}
+static TcW tc_fwd(const gm_ctx* c, const MlpOff& m) { return tc_w(c, m.fk1, m.fk2, m.in_p, m.out_p); }
+static TcW tc_bwd(const gm_ctx* c, const MlpOff& m) { return tc_w(c, m.bk1, m.bk2, m.out_p, m.in_p); }
+static TcW tc_edge_bwd(const gm_ctx* c, const MlpOff& m) { return tc_w(c, m.bk1, m.wck, m.out_p, c->W); }
+static TcW tc_nodesum(const gm_ctx* c, const MlpOff& m) { return tc_w(c, m.babk, -1, 2 * c->W, 0); }
 
 template <class Op>
 static void fill_fwd(Op& op, const gm_ctx* c, int mlp_idx, long rows, uint32_t* mask) {

@@ -1,14 +1,16 @@
 // Tensor-core (tcgen05) form of the fused 2-layer MLP kernel: BF16 operands,
 // FP32 accumulation in tensor memory.  Same Op functors as mlp2_kernel.
 //
-//   GEMM1  D1[128 x W]    = X[128 x Kin] . B1       (K in chunks of 64)
+//   GEMM1  D1[128 x W]    = X[128 x Kin] . B1       (K in staged chunks)
 //   hidden                = relu(D1 + b1) (mask bits saved) or D1 * saved mask
-//   GEMM2  D2[128 x Nout] = hid . B2                (K = W in chunks of 64)
+//   GEMM2  D2[128 x Nout] = hid . B2                (K = W in staged chunks)
 //   out(row, n, D2 + b2)
 //
-// SPLIT = 3 keeps FP32-level accuracy with BF16 tensor cores: every operand
-// is stored as hi = bf16(x) and lo = bf16(x - hi), and D = Ah Bh + Ah Bl + Al Bh
-// (the Al Bl term is below FP32 rounding).  SPLIT = 1 uses hi only.
+// P pieces per operand trade tensor work for accuracy with BF16 tensor cores:
+// x = x0 + x1 + ... with x0 = bf16(x), x1 = bf16(x - x0), ..., and
+// D = sum over i + j < P of A_i B_j.  P = 1: plain BF16 (8 bits).  P = 2: three
+// products, about 16 bits.  P = 3: six products, about 24 bits, i.e. FP32
+// operand precision (the dropped pairs lie below the last piece's rounding).
 //
 // Operands are staged in shared memory by the threads in the canonical
 // no-swizzle K-major layout of core matrices (8 rows x 16 bytes): element
@@ -24,7 +26,6 @@
 namespace gmi {
 
 constexpr int TC_M = 128;        // rows per CTA tile (MMA M)
-constexpr int TC_KC = 64;        // K per staged chunk
 constexpr int TC_T = 256;        // threads per CTA
 constexpr int TC_TMEM_COLS = 512;
 constexpr int TC_NB = 256;       // largest product width staged (N of GEMM2)
@@ -98,26 +99,28 @@ __device__ __forceinline__ unsigned bf2(float a, float b) {
     return *reinterpret_cast<unsigned*>(&h);
 }
 
-// 8 values -> BF16 hi part (and lo = bf16(v - hi) for the split form)
-template <int SPLIT>
-__device__ __forceinline__ void pack8(const float* v, uint4& hi, uint4& lo) {
-    hi = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
-    if constexpr (SPLIT == 3) {
-        float r[8];
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&hi);
+// 8 values -> P BF16 pieces: piece p = bf16(v - pieces 0..p-1).
+template <int P>
+__device__ __forceinline__ void pack8(const float* v, uint4* out) {
+    float r[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) r[j] = v[j] - __bfloat162float(h[j]);
-        lo = make_uint4(bf2(r[0], r[1]), bf2(r[2], r[3]), bf2(r[4], r[5]), bf2(r[6], r[7]));
+    for (int j = 0; j < 8; ++j) r[j] = v[j];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        out[p] = make_uint4(bf2(r[0], r[1]), bf2(r[2], r[3]), bf2(r[4], r[5]), bf2(r[6], r[7]));
+        if (p + 1 < P) {
+            const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&out[p]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r[j] -= __bfloat162float(h[j]);
+        }
     }
 }
 
-// Operand pointers of one launch: K-major BF16 copies [Npad][Kpad] of the two products
-// (hi parts, and lo parts for the split form).
+// Operand pointers of one launch: K-major BF16 copies [Npad][Kpad] of the two products,
+// one array per piece (only the first P are read).
 struct TcW {
-    const __nv_bfloat16* B1;     // [W][K1p]
-    const __nv_bfloat16* B2;     // [N2p][W]  (unused in single-product mode)
-    const __nv_bfloat16* B1lo;
-    const __nv_bfloat16* B2lo;
+    const __nv_bfloat16* B1[3];  // [W][K1p]
+    const __nv_bfloat16* B2[3];  // [N2p][W]  (unused in single-product mode)
     int K1p, N2p;
     int* status;
 };
@@ -154,53 +157,63 @@ __device__ __forceinline__ void tc_out32(const Op& op, const RowCtx& rc, int c0,
     }
 }
 
-// Stage rows [0, nrows) x K-chunk [k0, k0 + kc) of a K-major BF16 matrix (row length ld) into smem.
-template <int SPLIT>
-__device__ __forceinline__ void tc_stage_b(unsigned char* dst_hi, unsigned char* dst_lo, const __nv_bfloat16* hi,
-                                           const __nv_bfloat16* lo, int nrows, int ld, int k0, int kc, int tid) {
+// Stage rows [0, nrows) x K-chunk [k0, k0 + kc) of the P pieces of a K-major BF16 matrix
+// (row length ld) into smem; piece p lands piece_bytes further on.
+template <int P, int KC>
+__device__ __forceinline__ void tc_stage_b(unsigned char* dst, int piece_bytes, const __nv_bfloat16* const* src,
+                                           int nrows, int ld, int k0, int kc, int tid) {
     const int nv = nrows * (kc / 8);
     for (int v = tid; v < nv; v += TC_T) {
         const int n = v / (kc / 8), kv = v % (kc / 8);
         const long g = (long)n * ld + k0 + kv * 8;
-        *reinterpret_cast<uint4*>(dst_hi + tc_off(n, kv * 8, TC_KC)) = *reinterpret_cast<const uint4*>(hi + g);
-        if constexpr (SPLIT == 3)
-            *reinterpret_cast<uint4*>(dst_lo + tc_off(n, kv * 8, TC_KC)) = *reinterpret_cast<const uint4*>(lo + g);
+        const int o = tc_off(n, kv * 8, KC);
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            *reinterpret_cast<uint4*>(dst + p * piece_bytes + o) = *reinterpret_cast<const uint4*>(src[p] + g);
     }
 }
 
-// MMAs of one staged chunk: D (+)= A.B^T, split-product terms for SPLIT = 3.
-template <int SPLIT>
-__device__ __forceinline__ void tc_issue(unsigned tD, unsigned a_hi, unsigned a_lo, unsigned a_sbo, unsigned b_hi,
-                                         unsigned b_lo, int kc, int N, bool first) {
+// MMAs of one staged chunk: D (+)= sum over piece pairs (i, j) with i + j < P of A_i . B_j^T
+// (1, 3 or 6 products; the dropped pairs are below the last kept piece's rounding).
+template <int P, int KC>
+__device__ __forceinline__ void tc_issue(unsigned tD, unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b0,
+                                         unsigned b_piece, int kc, int N, bool first) {
     const unsigned idesc = tc_idesc(TC_M, N);
+    bool acc = !first;
     for (int kk = 0; kk < kc / 16; ++kk) {
-        const unsigned long long ah = tc_desc(a_hi + kk * 256, a_sbo);
-        const unsigned long long bh = tc_desc(b_hi + kk * 256, TC_KC * 16);
-        tc_mma(tD, ah, bh, idesc, (first && kk == 0) ? 0u : 1u);
-        if constexpr (SPLIT == 3) {
-            const unsigned long long al = tc_desc(a_lo + kk * 256, a_sbo);
-            const unsigned long long bl = tc_desc(b_lo + kk * 256, TC_KC * 16);
-            tc_mma(tD, ah, bl, idesc, 1u);
-            tc_mma(tD, al, bh, idesc, 1u);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const unsigned long long ad = tc_desc(a0 + i * a_piece + kk * 256, a_sbo);
+#pragma unroll
+            for (int j = 0; i + j < P; ++j) {
+                const unsigned long long bd = tc_desc(b0 + j * b_piece + kk * 256, KC * 16);
+                tc_mma(tD, ad, bd, idesc, acc ? 1u : 0u);
+                acc = true;
+            }
         }
     }
 }
 
-template <int W, int SPLIT>
-constexpr size_t tc_smem_bytes() {
-    // A chunk (hi, lo) + B chunk (hi, lo; up to TC_NB rows) + hidden (hi, lo)
-    return (size_t)2 * TC_M * TC_KC * 2 + (size_t)2 * TC_NB * TC_KC * 2 + (size_t)2 * TC_M * W * 2;
+// K per staged chunk: 64, or 32 with three pieces so that all pieces fit in shared memory.
+template <int P>
+__host__ __device__ constexpr int tc_kc() {
+    return P == 3 ? 32 : 64;
 }
 
-template <int W, class Op, int SPLIT>
+template <int W, int P>
+__host__ __device__ constexpr size_t tc_smem_bytes() {
+    // per piece: A chunk + B chunk (up to TC_NB rows) + hidden tile
+    return (size_t)P * ((size_t)TC_M * tc_kc<P>() * 2 + (size_t)TC_NB * tc_kc<P>() * 2 + (size_t)TC_M * W * 2);
+}
+
+template <int W, class Op, int P>
 __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
+    constexpr int KC = tc_kc<P>();
+    constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = TC_NB * KC * 2, H_BYTES = TC_M * W * 2;
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char* sAh = tsm;
-    unsigned char* sAl = sAh + TC_M * TC_KC * 2;
-    unsigned char* sBh = sAl + TC_M * TC_KC * 2;
-    unsigned char* sBl = sBh + TC_NB * TC_KC * 2;
-    unsigned char* sHh = sBl + TC_NB * TC_KC * 2;      // hidden, K-major with K = W
-    unsigned char* sHl = sHh + TC_M * W * 2;
+    unsigned char* sA = tsm;                    // P pieces of the A chunk, K-major with K = KC
+    unsigned char* sB = sA + P * A_BYTES;       // P pieces of the B chunk
+    unsigned char* sH = sB + P * B_BYTES;       // P pieces of the hidden tile, K-major with K = W
     __shared__ RowCtx rc[TC_M];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ unsigned tmem_base;
@@ -225,10 +238,10 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     unsigned phase = 0;
 
     // ---------------- GEMM1 over K chunks
-    const int nch = (w.K1p + TC_KC - 1) / TC_KC;
+    const int nch = (w.K1p + KC - 1) / KC;
     for (int c = 0; c < nch; ++c) {
-        const int k0 = c * TC_KC;
-        const int kc = min(TC_KC, w.K1p - k0);        // multiple of 16
+        const int k0 = c * KC;
+        const int kc = min(KC, w.K1p - k0);        // multiple of 16
         const int nva = TC_M * (kc / 8);
         for (int v = tid; v < nva; v += TC_T) {
             const int m = v / (kc / 8), kv = v % (kc / 8);
@@ -239,18 +252,19 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) x[j] = 0.f;
             }
-            uint4 hi, lo;
-            pack8<SPLIT>(x, hi, lo);
-            *reinterpret_cast<uint4*>(sAh + tc_off(m, kv * 8, TC_KC)) = hi;
-            if constexpr (SPLIT == 3) *reinterpret_cast<uint4*>(sAl + tc_off(m, kv * 8, TC_KC)) = lo;
+            uint4 pc[P];
+            pack8<P>(x, pc);
+            const int o = tc_off(m, kv * 8, KC);
+#pragma unroll
+            for (int p = 0; p < P; ++p) *reinterpret_cast<uint4*>(sA + p * A_BYTES + o) = pc[p];
         }
-        tc_stage_b<SPLIT>(sBh, sBl, w.B1, w.B1lo, W, w.K1p, k0, kc, tid);
+        tc_stage_b<P, KC>(sB, B_BYTES, w.B1, W, w.K1p, k0, kc, tid);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (tid == 0) {
-            tc_issue<SPLIT>(tD1, smem_u32(sAh), smem_u32(sAl), TC_KC * 16, smem_u32(sBh), smem_u32(sBl), kc, W, c == 0);
+            tc_issue<P, KC>(tD1, smem_u32(sA), A_BYTES, KC * 16, smem_u32(sB), B_BYTES, kc, W, c == 0);
             tc_commit(&mbar);
         }
         ok = tc_wait(&mbar, phase & 1, w.status) && ok;   // the chunk buffers are free again
@@ -299,24 +313,25 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                uint4 hi, lo;
-                pack8<SPLIT>(v + q * 8, hi, lo);
-                *reinterpret_cast<uint4*>(sHh + tc_off(lrow, c0 + q * 8, W)) = hi;
-                if constexpr (SPLIT == 3) *reinterpret_cast<uint4*>(sHl + tc_off(lrow, c0 + q * 8, W)) = lo;
+                uint4 pc[P];
+                pack8<P>(v + q * 8, pc);
+                const int o = tc_off(lrow, c0 + q * 8, W);
+#pragma unroll
+                for (int p = 0; p < P; ++p) *reinterpret_cast<uint4*>(sH + p * H_BYTES + o) = pc[p];
             }
         }
-        // ---------------- GEMM2 over K = W in chunks of 64 (B2 staged chunk by chunk)
-        for (int k0 = 0; k0 < W; k0 += TC_KC) {
-            const int kc = min(TC_KC, W - k0);
-            tc_stage_b<SPLIT>(sBh, sBl, w.B2, w.B2lo, w.N2p, W, k0, kc, tid);
+        // ---------------- GEMM2 over K = W in chunks of KC (B2 staged chunk by chunk)
+        for (int k0 = 0; k0 < W; k0 += KC) {
+            const int kc = min(KC, W - k0);
+            tc_stage_b<P, KC>(sB, B_BYTES, w.B2, w.N2p, W, k0, kc, tid);
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
             if (tid == 0) {
                 // hidden tile: K-major with K = W; the chunk starts k0/8 core matrices along K
-                tc_issue<SPLIT>(tD2, smem_u32(sHh) + (k0 / 8) * 128, smem_u32(sHl) + (k0 / 8) * 128, W * 16,
-                                smem_u32(sBh), smem_u32(sBl), kc, w.N2p, k0 == 0);
+                tc_issue<P, KC>(tD2, smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, smem_u32(sB), B_BYTES, kc,
+                                w.N2p, k0 == 0);
                 tc_commit(&mbar);
             }
             ok = tc_wait(&mbar, phase & 1, w.status) && ok;
