@@ -325,7 +325,12 @@ __global__ void agg_kernel(int M, int W, const int* __restrict__ in_ptr, const f
 
 template <int W, int P, class Op>
 static gm_status launch_tc(const Op& op, const TcW& tw, cudaStream_t st) {
-    constexpr size_t smem = tc_smem_bytes<W, P>();
+    constexpr size_t smem = tc_smem_bytes<W, P>() > TC_SMEM_MIN ? tc_smem_bytes<W, P>() : TC_SMEM_MIN;
+    static_assert(W <= TC_NB, "GEMM1 width must fit the staged B chunk");
+    if (tw.N2p > TC_TMEM_COLS || tw.N2p % 16 || tw.K1p % 16) {
+        set_error("tensor-core MLP shape out of range (K1p %d, N2p %d)", tw.K1p, tw.N2p);
+        return GM_ERR_INVALID_ARG;
+    }
     static bool attr_set = false;
     if (!attr_set) {
         GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_kernel<W, Op, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,

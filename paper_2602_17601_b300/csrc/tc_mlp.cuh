@@ -27,8 +27,8 @@ namespace gmi {
 
 constexpr int TC_M = 128;        // rows per CTA tile (MMA M)
 constexpr int TC_T = 256;        // threads per CTA
-constexpr int TC_TMEM_COLS = 512;
-constexpr int TC_NB = 256;       // largest product width staged (N of GEMM2)
+constexpr int TC_TMEM_COLS = 256;  // D1, then D2 in the same columns (N <= 256); two CTAs per SM
+constexpr int TC_NB = 128;         // rows of the staged B chunk
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -157,27 +157,87 @@ __device__ __forceinline__ void tc_out32(const Op& op, const RowCtx& rc, int c0,
     }
 }
 
+// Thread v of a staging loop handles one 16-byte vector (8 K-elements of one row).
+// Rows vary fastest within each 8-row core matrix, so the 8 lanes of a quarter warp
+// write one contiguous 128-byte core matrix (no shared-memory bank conflicts).
+__device__ __forceinline__ void tc_vec_rc(int v, int kv8, int& r, int& kv) {
+    const int rest = v >> 3;
+    kv = rest % kv8;
+    r = (rest / kv8) * 8 + (v & 7);
+}
+
 // Stage rows [0, nrows) x K-chunk [k0, k0 + kc) of the P pieces of a K-major BF16 matrix
-// (row length ld) into smem; piece p lands piece_bytes further on.
-template <int P, int KC>
+// (row length ld) into smem laid out with K = kdim; piece p lands piece_bytes further on.
+template <int P>
 __device__ __forceinline__ void tc_stage_b(unsigned char* dst, int piece_bytes, const __nv_bfloat16* const* src,
-                                           int nrows, int ld, int k0, int kc, int tid) {
-    const int nv = nrows * (kc / 8);
+                                           int nrows, int ld, int k0, int kc, int kdim, int tid) {
+    const int kv8 = kc / 8;
+    const int nv = nrows * kv8;            // nrows is a multiple of 16
     for (int v = tid; v < nv; v += TC_T) {
-        const int n = v / (kc / 8), kv = v % (kc / 8);
+        int n, kv;
+        tc_vec_rc(v, kv8, n, kv);
         const long g = (long)n * ld + k0 + kv * 8;
-        const int o = tc_off(n, kv * 8, KC);
+        const int o = tc_off(n, kv * 8, kdim);
 #pragma unroll
         for (int p = 0; p < P; ++p)
             *reinterpret_cast<uint4*>(dst + p * piece_bytes + o) = *reinterpret_cast<const uint4*>(src[p] + g);
     }
 }
 
+// Stage the A chunk (tile rows x K [k0, k0 + kc)) from the op's input rows, split into P
+// pieces.  Full chunks issue every thread's loads before converting and storing.
+template <int P, int KC, class Op>
+__device__ __forceinline__ void tc_stage_a(const Op& op, const RowCtx* rc, long row0, long rows, unsigned char* sA,
+                                           int a_piece, int k0, int kc, int tid) {
+    auto put = [&](int m, int kv, const float* x) {
+        uint4 pc[P];
+        pack8<P>(x, pc);
+        const int o = tc_off(m, kv * 8, KC);
+#pragma unroll
+        for (int p = 0; p < P; ++p) *reinterpret_cast<uint4*>(sA + p * a_piece + o) = pc[p];
+    };
+    if (kc == KC) {
+        constexpr int IT = TC_M * (KC / 8) / TC_T;
+        float x[IT][8];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            int m, kv;
+            tc_vec_rc(tid + i * TC_T, KC / 8, m, kv);
+            if (row0 + m < rows) {
+                tc_load8(op, rc[m], k0 + kv * 8, x[i]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[i][j] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            int m, kv;
+            tc_vec_rc(tid + i * TC_T, KC / 8, m, kv);
+            put(m, kv, x[i]);
+        }
+    } else {
+        const int kv8 = kc / 8;
+        for (int v = tid; v < TC_M * kv8; v += TC_T) {
+            int m, kv;
+            tc_vec_rc(v, kv8, m, kv);
+            float x[8];
+            if (row0 + m < rows) {
+                tc_load8(op, rc[m], k0 + kv * 8, x);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[j] = 0.f;
+            }
+            put(m, kv, x);
+        }
+    }
+}
+
 // MMAs of one staged chunk: D (+)= sum over piece pairs (i, j) with i + j < P of A_i . B_j^T
 // (1, 3 or 6 products; the dropped pairs are below the last kept piece's rounding).
-template <int P, int KC>
+template <int P>
 __device__ __forceinline__ void tc_issue(unsigned tD, unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b0,
-                                         unsigned b_piece, int kc, int N, bool first) {
+                                         unsigned b_piece, unsigned b_sbo, int kc, int N, bool first) {
     const unsigned idesc = tc_idesc(TC_M, N);
     bool acc = !first;
     for (int kk = 0; kk < kc / 16; ++kk) {
@@ -186,7 +246,7 @@ __device__ __forceinline__ void tc_issue(unsigned tD, unsigned a0, unsigned a_pi
             const unsigned long long ad = tc_desc(a0 + i * a_piece + kk * 256, a_sbo);
 #pragma unroll
             for (int j = 0; i + j < P; ++j) {
-                const unsigned long long bd = tc_desc(b0 + j * b_piece + kk * 256, KC * 16);
+                const unsigned long long bd = tc_desc(b0 + j * b_piece + kk * 256, b_sbo);
                 tc_mma(tD, ad, bd, idesc, acc ? 1u : 0u);
                 acc = true;
             }
@@ -200,20 +260,30 @@ __host__ __device__ constexpr int tc_kc() {
     return P == 3 ? 32 : 64;
 }
 
+// Shared memory: [A chunk | hidden tile] (the hidden tile reuses the A buffer once GEMM1
+// is done) followed by the B chunk (TC_NB rows x KC; GEMM2 products wider than TC_NB
+// stage half-K chunks of the same size).
+template <int W, int P>
+__host__ __device__ constexpr size_t tc_region_a() {
+    return (size_t)P * ((size_t)TC_M * tc_kc<P>() * 2 > (size_t)TC_M * W * 2 ? (size_t)TC_M * tc_kc<P>() * 2
+                                                                               : (size_t)TC_M * W * 2);
+}
 template <int W, int P>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-    // per piece: A chunk + B chunk (up to TC_NB rows) + hidden tile
-    return (size_t)P * ((size_t)TC_M * tc_kc<P>() * 2 + (size_t)TC_NB * tc_kc<P>() * 2 + (size_t)TC_M * W * 2);
+    return tc_region_a<W, P>() + (size_t)P * TC_NB * tc_kc<P>() * 2;
 }
+// Launch size: at least TC_SMEM_MIN so that no more than two CTAs share an SM, which is
+// what two TC_TMEM_COLS allocations fill.
+constexpr size_t TC_SMEM_MIN = 100 * 1024;
 
 template <int W, class Op, int P>
 __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     constexpr int KC = tc_kc<P>();
     constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = TC_NB * KC * 2, H_BYTES = TC_M * W * 2;
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char* sA = tsm;                    // P pieces of the A chunk, K-major with K = KC
-    unsigned char* sB = sA + P * A_BYTES;       // P pieces of the B chunk
-    unsigned char* sH = sB + P * B_BYTES;       // P pieces of the hidden tile, K-major with K = W
+    unsigned char* sA = tsm;                          // P pieces of the A chunk, K-major with K = KC
+    unsigned char* sH = tsm;                          // P pieces of the hidden tile, K = W (after GEMM1)
+    unsigned char* sB = tsm + tc_region_a<W, P>();    // P pieces of the B chunk
     __shared__ RowCtx rc[TC_M];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ unsigned tmem_base;
@@ -232,8 +302,8 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const unsigned tmem = tmem_base;
-    const unsigned tD1 = tmem, tD2 = tmem + W;
+    // D1 [128 x W] and, once the hidden epilogue has read it, D2 [128 x N2p] in the same columns
+    const unsigned tD = tmem_base;
     bool ok = true;
     unsigned phase = 0;
 
@@ -242,29 +312,14 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     for (int c = 0; c < nch; ++c) {
         const int k0 = c * KC;
         const int kc = min(KC, w.K1p - k0);        // multiple of 16
-        const int nva = TC_M * (kc / 8);
-        for (int v = tid; v < nva; v += TC_T) {
-            const int m = v / (kc / 8), kv = v % (kc / 8);
-            float x[8];
-            if (row0 + m < rows) {
-                tc_load8(op, rc[m], k0 + kv * 8, x);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) x[j] = 0.f;
-            }
-            uint4 pc[P];
-            pack8<P>(x, pc);
-            const int o = tc_off(m, kv * 8, KC);
-#pragma unroll
-            for (int p = 0; p < P; ++p) *reinterpret_cast<uint4*>(sA + p * A_BYTES + o) = pc[p];
-        }
-        tc_stage_b<P, KC>(sB, B_BYTES, w.B1, W, w.K1p, k0, kc, tid);
+        tc_stage_a<P, KC>(op, rc, row0, rows, sA, A_BYTES, k0, kc, tid);
+        tc_stage_b<P>(sB, B_BYTES, w.B1, W, w.K1p, k0, kc, KC, tid);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (tid == 0) {
-            tc_issue<P, KC>(tD1, smem_u32(sA), A_BYTES, KC * 16, smem_u32(sB), B_BYTES, kc, W, c == 0);
+            tc_issue<P>(tD, smem_u32(sA), A_BYTES, KC * 16, smem_u32(sB), B_BYTES, KC * 16, kc, W, c == 0);
             tc_commit(&mbar);
         }
         ok = tc_wait(&mbar, phase & 1, w.status) && ok;   // the chunk buffers are free again
@@ -282,13 +337,13 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     if (kSingle) {
         for (int c0 = chalf * 32; c0 < W; c0 += 64) {
             float v[32];
-            if (ok) tc_ld32(tD1 + lane_off + (unsigned)c0, v);
+            if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
             if (valid) tc_out32(op, rc[lrow], c0, v, op.nout, nullptr);
         }
     } else {
         for (int c0 = chalf * 32; c0 < W; c0 += 64) {
             float v[32];
-            if (ok) tc_ld32(tD1 + lane_off + (unsigned)c0, v);
+            if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
             if constexpr (Op::kMode == 0) {
                 uint32_t bits = 0;
 #pragma unroll
@@ -320,18 +375,20 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
                 for (int p = 0; p < P; ++p) *reinterpret_cast<uint4*>(sH + p * H_BYTES + o) = pc[p];
             }
         }
-        // ---------------- GEMM2 over K = W in chunks of KC (B2 staged chunk by chunk)
-        for (int k0 = 0; k0 < W; k0 += KC) {
-            const int kc = min(KC, W - k0);
-            tc_stage_b<P, KC>(sB, B_BYTES, w.B2, w.N2p, W, k0, kc, tid);
+        // ---------------- GEMM2 over K = W in chunks (B2 staged chunk by chunk; products
+        // wider than TC_NB rows take half-K chunks so that the B buffer still holds them)
+        const int kc2 = w.N2p > TC_NB ? KC / 2 : KC;
+        for (int k0 = 0; k0 < W; k0 += kc2) {
+            const int kc = min(kc2, W - k0);
+            tc_stage_b<P>(sB, B_BYTES, w.B2, w.N2p, W, k0, kc, kc2, tid);
             fence_async_smem();
             tc_fence_before();
-            __syncthreads();
+            __syncthreads();                   // also: every warp's TMEM reads of D1 are done
             tc_fence_after();
             if (tid == 0) {
                 // hidden tile: K-major with K = W; the chunk starts k0/8 core matrices along K
-                tc_issue<P, KC>(tD2, smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, smem_u32(sB), B_BYTES, kc,
-                                w.N2p, k0 == 0);
+                tc_issue<P>(tD, smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, smem_u32(sB), B_BYTES, kc2 * 16, kc,
+                            w.N2p, k0 == 0);
                 tc_commit(&mbar);
             }
             ok = tc_wait(&mbar, phase & 1, w.status) && ok;
@@ -342,14 +399,14 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
         const bool valid2 = ok && (row0 + lrow < rows);
         for (int c0 = chalf * 32; c0 < w.N2p; c0 += 64) {
             float v[32];
-            if (ok) tc_ld32(tD2 + lane_off + (unsigned)c0, v);
+            if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
             if (valid2) tc_out32(op, rc[lrow], c0, v, op.nout, op.b2);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(TC_TMEM_COLS));
 }
 
 }  // namespace gmi
