@@ -161,21 +161,28 @@ static float from_bf16(uint16_t h) {
 }
 
 // The three BF16 pieces of a split tensor-core operand: p0 = bf16(f), p1 = bf16(f - p0),
-// p2 = bf16(f - p0 - p1); p0 + p1 + p2 carries about 24 significant bits of f.
+// p2 = bf16(f - p0 - p1); p0 + p1 + p2 carries about 24 significant bits of f.  The
+// [rows][cols] K-major operand with entry (r, c) = f(r, c) is stored in the tiled chunk
+// layout (tc_tile_off) with chunk width kcw, 128-byte aligned; rows and cols are multiples of 16.
 template <class F>
-static long put_bf(std::vector<uint16_t>* wp, int rows, int cols, F f) {
+static long put_bf(std::vector<uint16_t>* wp, int rows, int cols, int kcw, F f) {
     while (wp[0].size() % 64)
         for (int p = 0; p < 3; ++p) wp[p].push_back(0);
-    long o = (long)wp[0].size();
-    for (int r = 0; r < rows; ++r)
-        for (int c = 0; c < cols; ++c) {
-            float v = f(r, c);
-            for (int p = 0; p < 3; ++p) {
-                const uint16_t h = to_bf16(v);
-                wp[p].push_back(h);
-                v -= from_bf16(h);
+    const long o = (long)wp[0].size();
+    for (int p = 0; p < 3; ++p) wp[p].resize(o + (size_t)rows * cols, 0);
+    for (int k0 = 0; k0 < cols; k0 += kcw) {
+        const int kc = std::min(kcw, cols - k0);
+        const long base = o + (long)rows * k0;
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < kc; ++c) {
+                float v = f(r, k0 + c);
+                for (int p = 0; p < 3; ++p) {
+                    const uint16_t h = to_bf16(v);
+                    wp[p][base + tc_tile_off(r, c, kc)] = h;
+                    v -= from_bf16(h);
+                }
             }
-        }
+    }
     return o;
 }
 
@@ -231,13 +238,13 @@ static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::v
         auto up16 = [](int v) { return (v + 15) / 16 * 16; };
         mo.in_p = up16(in);
         mo.out_p = up16(out);
-        mo.fk1 = put_bf(wp, hid, mo.in_p, [&](int j, int i) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
-        mo.fk2 = put_bf(wp, mo.out_p, hid, [&](int o, int j) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
-        mo.bk1 = put_bf(wp, hid, mo.out_p, [&](int j, int o) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
-        mo.bk2 = put_bf(wp, mo.in_p, hid, [&](int i, int j) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
+        mo.fk1 = put_bf(wp, hid, mo.in_p, TC_CHUNK, [&](int j, int i) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
+        mo.fk2 = put_bf(wp, mo.out_p, hid, tc_chunk_b2(mo.out_p), [&](int o, int j) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
+        mo.bk1 = put_bf(wp, hid, mo.out_p, TC_CHUNK, [&](int j, int o) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
+        mo.bk2 = put_bf(wp, mo.in_p, hid, tc_chunk_b2(mo.in_p), [&](int i, int j) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
         if (edge_mp) {
-            mo.wck = put_bf(wp, W, hid, [&](int n, int j) { return W1[(size_t)(2 * W + n) * hid + j]; });
-            mo.babk = put_bf(wp, W, 2 * W, [&](int n, int k) {
+            mo.wck = put_bf(wp, W, hid, tc_chunk_b2(W), [&](int n, int j) { return W1[(size_t)(2 * W + n) * hid + j]; });
+            mo.babk = put_bf(wp, W, 2 * W, TC_CHUNK, [&](int n, int k) {
                 return k < W ? W1[(size_t)n * hid + k] : W1[(size_t)(W + n) * hid + (k - W)];
             });
         }

@@ -24,6 +24,21 @@ struct RowCtx {
 };
 }  // namespace gmi
 
+// 8 consecutive floats (16-byte aligned rows): v = p[0..7], or v += p[0..7]
+__device__ __forceinline__ void ld8(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void add8(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w; v[4] += b.x; v[5] += b.y; v[6] += b.z; v[7] += b.w;
+}
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
 #include "tc_mlp.cuh"
 
 namespace gmi {
@@ -186,26 +201,12 @@ __global__ void __launch_bounds__(NT) mlp2_kernel(Op op) {
 }
 
 // ======================================================================= forward ops
-// 8 consecutive floats (16-byte aligned rows): v = p[0..7], or v += p[0..7]
-__device__ __forceinline__ void ld8(const float* p, float* v) {
-    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-}
-__device__ __forceinline__ void add8(const float* p, float* v) {
-    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
-    v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w; v[4] += b.x; v[5] += b.y; v[6] += b.z; v[7] += b.w;
-}
-__device__ __forceinline__ float4 add4(float4 a, float4 b) {
-    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-
 struct FwdBase {
     static constexpr int kMode = 0;
     static constexpr bool kStoreHid = false;
     static constexpr bool kHasIn8 = false;
     static constexpr bool kHasOut4 = false;
+    static constexpr bool kHasResid = false;   // out4 value = resid4 + product (loads first)
     long rows;
     int kin, nout;
     const float *B1, *b1, *B2, *b2;
@@ -270,10 +271,9 @@ struct EdgeMpFwd : FwdBase {
                                 : (k0 < 2 * W ? h + (long)c.b * W + k0 - W : e + (long)c.a * W + k0 - 2 * W);
         ld8(p, v);
     }
-    __device__ void out4(const RowCtx& c, int n, float4 v) const {
-        float* p = e + (long)c.a * W + n;
-        st4(p, add4(ld4(p), v));
-    }
+    static constexpr bool kHasResid = true;
+    __device__ float4 resid4(const RowCtx& c, int n) const { return ld4(e + (long)c.a * W + n); }
+    __device__ void out4(const RowCtx& c, int n, float4 v) const { st4(e + (long)c.a * W + n, v); }
 };
 
 struct NodeMpFwd : FwdBase {
@@ -289,10 +289,9 @@ struct NodeMpFwd : FwdBase {
     __device__ void in8(const RowCtx& c, int k0, float* v) const {
         ld8(k0 < W ? h + (long)c.a * W + k0 : agg + (long)c.a * W + k0 - W, v);
     }
-    __device__ void out4(const RowCtx& c, int n, float4 v) const {
-        float* p = h + (long)c.a * W + n;
-        st4(p, add4(ld4(p), v));
-    }
+    static constexpr bool kHasResid = true;
+    __device__ float4 resid4(const RowCtx& c, int n) const { return ld4(h + (long)c.a * W + n); }
+    __device__ void out4(const RowCtx& c, int n, float4 v) const { st4(h + (long)c.a * W + n, v); }
 };
 
 struct DecFwd : FwdBase {
@@ -468,6 +467,7 @@ struct BwdBase {
     static constexpr bool kStoreHid = false;
     static constexpr bool kHasIn8 = false;
     static constexpr bool kHasOut4 = false;
+    static constexpr bool kHasResid = false;   // out4 value = resid4 + product (loads first)
     long rows;
     int kin, nout;
     const float *B1, *b1 = nullptr, *B2, *b2 = nullptr;
@@ -526,8 +526,12 @@ struct NodeMpBwd : BwdBase {
     }
     static constexpr bool kHasIn8 = true, kHasOut4 = true;
     __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(dh + (long)x.e * W + k0, v); }
+    static constexpr bool kHasResid = true;
+    __device__ float4 resid4(const RowCtx& x, int n) const {
+        return n < W ? ld4(dh + (long)x.e * W + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     __device__ void out4(const RowCtx& x, int n, float4 v) const {
-        if (n < W) st4(dacc + (long)x.e * W + n, add4(ld4(dh + (long)x.e * W + n), v));
+        if (n < W) st4(dacc + (long)x.e * W + n, v);
         else st4(dagg + (long)x.e * W + n - W, v);
     }
 };
@@ -564,11 +568,13 @@ struct EdgeMpBwd : BwdBase {
         if (x.f >= 0) add8(de_in + (long)x.f * W + k0, v);
     }
     __device__ void store_hid4(const RowCtx& x, int n, float4 v) const { st4(ehid + self(x) * W + n, v); }
-    __device__ void out4(const RowCtx& x, int n, float4 v) const {
+    static constexpr bool kHasResid = true;
+    __device__ float4 resid4(const RowCtx& x, int n) const {
         float4 a = ld4(dagg + (long)x.e * W + n);
         if (x.f >= 0) a = add4(a, ld4(de_in + (long)x.f * W + n));
-        st4(de_out + self(x) * W + n, add4(a, v));
+        return a;
     }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(de_out + self(x) * W + n, v); }
 };
 
 struct NodeSumBwd : BwdBase {
@@ -617,10 +623,11 @@ struct NodeSumBwd : BwdBase {
                 add8(ehid + ((base + src_list[p]) * 3 + x.c) * W + k0 - W, v);
         }
     }
-    __device__ void out4(const RowCtx& x, int n, float4 v) const {
-        if (x.d >= 0) v = add4(v, ld4(dacc + (((long)x.a * Rr + x.d) * 3 + x.c) * W + n));
-        st4(dh_next + (long)x.e * W + n, v);
+    static constexpr bool kHasResid = true;
+    __device__ float4 resid4(const RowCtx& x, int n) const {
+        return x.d >= 0 ? ld4(dacc + (((long)x.a * Rr + x.d) * 3 + x.c) * W + n) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(dh_next + (long)x.e * W + n, v); }
 };
 
 struct NodeEncBwd : BwdBase {

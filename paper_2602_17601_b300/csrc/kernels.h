@@ -5,6 +5,17 @@
 
 namespace gmi {
 
+// Tensor-core weight operands ([N rows][K] K-major BF16, three pieces) are stored tiled so that
+// one bulk copy moves one K chunk of one piece: K in chunks of kc columns (the last chunk may be
+// narrower), each chunk an N x kc block of 8 x 8 core matrices with element (n, k) at
+// (n/8)*8*kc + (k/8)*64 + (n%8)*8 + k%8.  kc = 64, except 32 for second-product operands
+// wider than 128 rows, whose chunks must still fit the 128 x 64 staging buffer.
+constexpr int TC_CHUNK = 64;
+inline __host__ __device__ int tc_chunk_b2(int rows) { return rows > 128 ? TC_CHUNK / 2 : TC_CHUNK; }
+inline __host__ __device__ long tc_tile_off(int n, int k, int kc) {
+    return (long)(n >> 3) * 8 * kc + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
+}
+
 // gnn.cu
 gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, cudaStream_t st);
 gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float* A, float* B,

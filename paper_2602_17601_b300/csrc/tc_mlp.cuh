@@ -26,7 +26,7 @@
 namespace gmi {
 
 constexpr int TC_M = 128;        // rows per CTA tile (MMA M)
-constexpr int TC_T = 256;        // threads per CTA
+constexpr int TC_T = 512;        // threads per CTA: four warp groups
 constexpr int TC_TMEM_COLS = 256;  // D1, then D2 in the same columns (N <= 256); two CTAs per SM
 constexpr int TC_NB = 128;         // rows of the staged B chunk
 
@@ -135,19 +135,35 @@ __device__ __forceinline__ void tc_load8(const Op& op, const RowCtx& rc, int k0,
     }
 }
 
+// Output of 32 columns [c0, c0 + 32) of one row: value = product (+ bias), plus the op's
+// residual where it has one.  Residual loads are all issued before the first store.
 template <class Op>
 __device__ __forceinline__ void tc_out32(const Op& op, const RowCtx& rc, int c0, const float* v, int nout,
                                          const float* bias) {
+    float4 f[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int n = c0 + 4 * q;
+        f[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        if (bias && n + 3 < nout) {
+            f[q].x += bias[n]; f[q].y += bias[n + 1]; f[q].z += bias[n + 2]; f[q].w += bias[n + 3];
+        }
+    }
+    if constexpr (Op::kHasOut4 && Op::kHasResid) {
+        float4 r[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (c0 + 4 * q + 3 < nout) r[q] = op.resid4(rc, c0 + 4 * q);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (c0 + 4 * q + 3 < nout) f[q] = add4(f[q], r[q]);
+    }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int n = c0 + 4 * q;
         if constexpr (Op::kHasOut4) {
             if (n + 3 < nout) {
-                float4 f = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                if (bias) {
-                    f.x += bias[n]; f.y += bias[n + 1]; f.z += bias[n + 2]; f.w += bias[n + 3];
-                }
-                op.out4(rc, n, f);
+                op.out4(rc, n, f[q]);
                 continue;
             }
         }
@@ -166,22 +182,22 @@ __device__ __forceinline__ void tc_vec_rc(int v, int kv8, int& r, int& kv) {
     r = (rest / kv8) * 8 + (v & 7);
 }
 
-// Stage rows [0, nrows) x K-chunk [k0, k0 + kc) of the P pieces of a K-major BF16 matrix
-// (row length ld) into smem laid out with K = kdim; piece p lands piece_bytes further on.
+// Bulk copy (TMA engine) of K chunk [k0, k0 + kc) of the P pieces of a tiled weight operand
+// with nrows rows (tc_tile_off layout: the chunk of one piece is one contiguous block) into
+// the staging buffer; completion is counted in bytes on mbarrier bar.  One thread calls it.
 template <int P>
-__device__ __forceinline__ void tc_stage_b(unsigned char* dst, int piece_bytes, const __nv_bfloat16* const* src,
-                                           int nrows, int ld, int k0, int kc, int kdim, int tid) {
-    const int kv8 = kc / 8;
-    const int nv = nrows * kv8;            // nrows is a multiple of 16
-    for (int v = tid; v < nv; v += TC_T) {
-        int n, kv;
-        tc_vec_rc(v, kv8, n, kv);
-        const long g = (long)n * ld + k0 + kv * 8;
-        const int o = tc_off(n, kv * 8, kdim);
+__device__ __forceinline__ void tc_load_b(unsigned char* dst, int piece_bytes, const __nv_bfloat16* const* src,
+                                          int nrows, int k0, int kc, void* bar) {
+    const unsigned bytes = (unsigned)nrows * kc * 2;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes * P)
+                 : "memory");
 #pragma unroll
-        for (int p = 0; p < P; ++p)
-            *reinterpret_cast<uint4*>(dst + p * piece_bytes + o) = *reinterpret_cast<const uint4*>(src[p] + g);
-    }
+    for (int p = 0; p < P; ++p)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(dst + p * piece_bytes)),
+            "l"(src[p] + (long)nrows * k0), "r"(bytes), "r"(smem_u32(bar))
+            : "memory");
 }
 
 // Stage the A chunk (tile rows x K [k0, k0 + kc)) from the op's input rows, split into P
@@ -254,10 +270,10 @@ __device__ __forceinline__ void tc_issue(unsigned tD, unsigned a0, unsigned a_pi
     }
 }
 
-// K per staged chunk: 64, or 32 with three pieces so that all pieces fit in shared memory.
+// K per staged chunk (the tiled weight layout's chunk width).
 template <int P>
 __host__ __device__ constexpr int tc_kc() {
-    return P == 3 ? 32 : 64;
+    return TC_CHUNK;
 }
 
 // Shared memory: [A chunk | hidden tile] (the hidden tile reuses the A buffer once GEMM1
@@ -283,22 +299,33 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char* sA = tsm;                          // P pieces of the A chunk, K-major with K = KC
     unsigned char* sH = tsm;                          // P pieces of the hidden tile, K = W (after GEMM1)
-    unsigned char* sB = tsm + tc_region_a<W, P>();    // P pieces of the B chunk
+    unsigned char* sB = tsm + tc_region_a<W, P>();    // P pieces of the B chunk (bulk copies)
     __shared__ RowCtx rc[TC_M];
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long mbar;    // MMA completion (tcgen05.commit)
+    __shared__ __align__(8) unsigned long long bbar;    // B chunk arrival (bulk-copy bytes)
     __shared__ unsigned tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long row0 = (long)blockIdx.x * TC_M;
     const long rows = op.rows;
     constexpr bool kSingle = (Op::kMode == 2);
+    const int nch = (w.K1p + KC - 1) / KC;
+    const int kc2 = tc_chunk_b2(w.N2p);
+    unsigned bphase = 0;        // thread 0: completed B chunk arrivals
+    bool b_pending = false;     // thread 0: a bulk copy has been issued and not yet waited for
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_load_b<P>(sB, B_BYTES, w.B1, W, 0, min(KC, w.K1p), &bbar);   // first chunk, under the prologue
+        b_pending = true;
+    }
     for (int m = tid; m < TC_M; m += TC_T) rc[m] = op.prep(row0 + m < rows ? row0 + m : -1);
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "n"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -307,41 +334,62 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     bool ok = true;
     unsigned phase = 0;
 
+    // thread 0: wait for the staged B chunk, issue the chunk's MMAs, commit them to mbar (the
+    // commit arrives even when nothing was issued, so the other threads never wait in vain)
+    auto issue = [&](unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b_sbo, int kc, int N, bool first) {
+        bool okb = false;
+        if (b_pending) {
+            okb = tc_wait(&bbar, bphase & 1, w.status);
+            if (okb) {
+                ++bphase;
+                b_pending = false;
+            }
+        }
+        if (okb) tc_issue<P>(tD, a0, a_piece, a_sbo, smem_u32(sB), B_BYTES, b_sbo, kc, N, first);
+        tc_commit(&mbar);
+        return okb;
+    };
+
     // ---------------- GEMM1 over K chunks
-    const int nch = (w.K1p + KC - 1) / KC;
     for (int c = 0; c < nch; ++c) {
         const int k0 = c * KC;
         const int kc = min(KC, w.K1p - k0);        // multiple of 16
         tc_stage_a<P, KC>(op, rc, row0, rows, sA, A_BYTES, k0, kc, tid);
-        tc_stage_b<P>(sB, B_BYTES, w.B1, W, w.K1p, k0, kc, KC, tid);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (tid == 0) {
-            tc_issue<P>(tD, smem_u32(sA), A_BYTES, KC * 16, smem_u32(sB), B_BYTES, KC * 16, kc, W, c == 0);
-            tc_commit(&mbar);
-        }
-        ok = tc_wait(&mbar, phase & 1, w.status) && ok;   // the chunk buffers are free again
+        if (tid == 0) ok = issue(smem_u32(sA), A_BYTES, KC * 16, kc * 16, kc, W, c == 0) && ok;
+        ok = tc_wait(&mbar, phase & 1, w.status) && ok;   // A and B buffers are free again
         ++phase;
+        if (tid == 0 && ok && !b_pending) {
+            if (c + 1 < nch) {
+                tc_load_b<P>(sB, B_BYTES, w.B1, W, k0 + KC, min(KC, w.K1p - k0 - KC), &bbar);
+                b_pending = true;
+            } else if (!kSingle) {
+                tc_load_b<P>(sB, B_BYTES, w.B2, w.N2p, 0, min(kc2, W), &bbar);   // under the epilogue
+                b_pending = true;
+            }
+        }
     }
     ok = __syncthreads_and(ok) != 0;           // warp-collective TMEM loads below need a uniform decision
     tc_fence_after();
 
-    // ---------------- hidden layer / single-product epilogue; 32-column blocks alternate
-    // between the two warp groups; TMEM lane = tile row
+    // ---------------- hidden layer / single-product epilogue; 32-column blocks rotate
+    // over the warp groups; TMEM lane = tile row (warp w reads lanes 32 (w % 4) ..)
+    constexpr int CSTEP = 32 * (TC_T / 128);
     const int lrow = (warp & 3) * 32 + lane;
-    const int chalf = warp >> 2;
+    const int cgrp = warp >> 2;
     const bool valid = ok && (row0 + lrow < rows);
     const unsigned lane_off = (unsigned)((warp & 3) * 32) << 16;
     if (kSingle) {
-        for (int c0 = chalf * 32; c0 < W; c0 += 64) {
+        for (int c0 = cgrp * 32; c0 < W; c0 += CSTEP) {
             float v[32];
             if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
             if (valid) tc_out32(op, rc[lrow], c0, v, op.nout, nullptr);
         }
     } else {
-        for (int c0 = chalf * 32; c0 < W; c0 += 64) {
+        for (int c0 = cgrp * 32; c0 < W; c0 += CSTEP) {
             float v[32];
             if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
             if constexpr (Op::kMode == 0) {
@@ -375,34 +423,33 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
                 for (int p = 0; p < P; ++p) *reinterpret_cast<uint4*>(sH + p * H_BYTES + o) = pc[p];
             }
         }
-        // ---------------- GEMM2 over K = W in chunks (B2 staged chunk by chunk; products
-        // wider than TC_NB rows take half-K chunks so that the B buffer still holds them)
-        const int kc2 = w.N2p > TC_NB ? KC / 2 : KC;
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();                       // sH complete; every warp's TMEM reads of D1 are done
+        tc_fence_after();
+        // ---------------- GEMM2 over K = W in chunks of kc2 (B2 chunks by bulk copy)
         for (int k0 = 0; k0 < W; k0 += kc2) {
             const int kc = min(kc2, W - k0);
-            tc_stage_b<P>(sB, B_BYTES, w.B2, w.N2p, W, k0, kc, kc2, tid);
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();                   // also: every warp's TMEM reads of D1 are done
-            tc_fence_after();
-            if (tid == 0) {
-                // hidden tile: K-major with K = W; the chunk starts k0/8 core matrices along K
-                tc_issue<P>(tD, smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, smem_u32(sB), B_BYTES, kc2 * 16, kc,
-                            w.N2p, k0 == 0);
-                tc_commit(&mbar);
-            }
+            // hidden tile: K-major with K = W; the chunk starts k0/8 core matrices along K
+            if (tid == 0) ok = issue(smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, kc * 16, kc, w.N2p, k0 == 0) && ok;
             ok = tc_wait(&mbar, phase & 1, w.status) && ok;
             ++phase;
+            if (tid == 0 && ok && !b_pending && k0 + kc2 < W) {
+                tc_load_b<P>(sB, B_BYTES, w.B2, w.N2p, k0 + kc2, min(kc2, W - k0 - kc2), &bbar);
+                b_pending = true;
+            }
         }
         ok = __syncthreads_and(ok) != 0;
         tc_fence_after();
         const bool valid2 = ok && (row0 + lrow < rows);
-        for (int c0 = chalf * 32; c0 < w.N2p; c0 += 64) {
+        for (int c0 = cgrp * 32; c0 < w.N2p; c0 += CSTEP) {
             float v[32];
             if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
             if (valid2) tc_out32(op, rc[lrow], c0, v, op.nout, op.b2);
         }
     }
+    // a bulk copy whose wait gave up may still be landing: wait (bounded) before the CTA exits
+    if (tid == 0 && b_pending) tc_wait(&bbar, bphase & 1, nullptr);
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
