@@ -173,6 +173,76 @@ __device__ __forceinline__ void tc_out32(const Op& op, const RowCtx& rc, int c0,
     }
 }
 
+// Coalesced output of D [128 x ncols] (TMEM columns from tD) for ops with row-vector
+// output (kHasOut4): every warp moves 32-column blocks of its TMEM lane quarter into a padded
+// FP32 tile in shared memory; then each warp writes whole rows with its 32 lanes along the
+// columns, residual loads of a batch of rows issued before the stores.  Columns go in passes
+// of TC_OUT_COLS; the tile needs TC_M x (TC_OUT_COLS + 4) floats.  Called by all threads with
+// a uniform ok; contains barriers.
+constexpr int TC_OUT_COLS = 128;
+constexpr size_t TC_OUT_BYTES = (size_t)TC_M * (TC_OUT_COLS + 4) * 4;
+
+template <class Op>
+__device__ __forceinline__ void tc_out_rows(const Op& op, const RowCtx* rc, unsigned char* smem, unsigned tD,
+                                            int ncols, const float* bias, long row0, long rows, bool ok) {
+    constexpr int TS = TC_OUT_COLS + 4;       // row stride (floats): 16-byte stores of 8 lanes hit distinct banks
+    constexpr int NW = TC_T / 32;
+    constexpr int RB = 4;                     // rows per batch of loads
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lrow = (warp & 3) * 32 + lane;
+    const unsigned lane_off = (unsigned)((warp & 3) * 32) << 16;
+    float* T = reinterpret_cast<float*>(smem);
+    const int nout = op.nout;
+    for (int cb = 0; cb < ncols; cb += TC_OUT_COLS) {
+        const int nc = min(TC_OUT_COLS, ncols - cb);
+        if (ok) {
+            for (int c0 = cb + (warp >> 2) * 32; c0 < cb + nc; c0 += 32 * (TC_T / 128)) {
+                float v[32];
+                tc_ld32(tD + lane_off + (unsigned)c0, v);
+                float* t = T + lrow * TS + (c0 - cb);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    *reinterpret_cast<float4*>(t + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+        __syncthreads();
+        if (ok) {
+            const int nv = max(0, min(nc, nout - cb)) / 4;     // whole float4 columns of this pass
+            for (int rb = warp * RB; rb < TC_M; rb += NW * RB) {
+                for (int f = lane; f < nv; f += 32) {
+                    const int n = cb + 4 * f;
+                    float4 x[RB];
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) {
+                        x[i] = *reinterpret_cast<const float4*>(T + (rb + i) * TS + 4 * f);
+                        if (bias) {
+                            x[i].x += bias[n]; x[i].y += bias[n + 1]; x[i].z += bias[n + 2]; x[i].w += bias[n + 3];
+                        }
+                    }
+                    if constexpr (Op::kHasResid) {
+                        float4 r[RB];
+#pragma unroll
+                        for (int i = 0; i < RB; ++i)
+                            if (row0 + rb + i < rows) r[i] = op.resid4(rc[rb + i], n);
+#pragma unroll
+                        for (int i = 0; i < RB; ++i)
+                            if (row0 + rb + i < rows) x[i] = add4(x[i], r[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < RB; ++i)
+                        if (row0 + rb + i < rows) op.out4(rc[rb + i], n, x[i]);
+                }
+                // columns of a ragged nout (not a multiple of 4) element by element
+                for (int n = cb + 4 * nv + lane; n < min(cb + nc, nout); n += 32)
+                    for (int i = 0; i < RB; ++i)
+                        if (row0 + rb + i < rows)
+                            op.out(rc[rb + i], n, T[(rb + i) * TS + (n - cb)] + (bias ? bias[n] : 0.f));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Thread v of a staging loop handles one 16-byte vector (8 K-elements of one row).
 // Rows vary fastest within each 8-row core matrix, so the 8 lanes of a quarter warp
 // write one contiguous 128-byte core matrix (no shared-memory bank conflicts).
@@ -288,9 +358,10 @@ template <int W, int P>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
     return tc_region_a<W, P>() + (size_t)P * TC_NB * tc_kc<P>() * 2;
 }
-// Launch size: at least TC_SMEM_MIN so that no more than two CTAs share an SM, which is
-// what two TC_TMEM_COLS allocations fill.
+// Launch size: at least TC_SMEM_MIN, so that no more than two CTAs share an SM (what two
+// TC_TMEM_COLS allocations fill) and the output tile of tc_out_rows fits.
 constexpr size_t TC_SMEM_MIN = 100 * 1024;
+static_assert(TC_OUT_BYTES <= TC_SMEM_MIN, "output tile must fit the minimum launch size");
 
 template <int W, class Op, int P>
 __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
@@ -383,10 +454,14 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     const bool valid = ok && (row0 + lrow < rows);
     const unsigned lane_off = (unsigned)((warp & 3) * 32) << 16;
     if (kSingle) {
-        for (int c0 = cgrp * 32; c0 < W; c0 += CSTEP) {
-            float v[32];
-            if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
-            if (valid) tc_out32(op, rc[lrow], c0, v, op.nout, nullptr);
+        if constexpr (Op::kHasOut4) {
+            tc_out_rows(op, rc, tsm, tD, W, nullptr, row0, rows, ok);
+        } else {
+            for (int c0 = cgrp * 32; c0 < W; c0 += CSTEP) {
+                float v[32];
+                if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
+                if (valid) tc_out32(op, rc[lrow], c0, v, op.nout, nullptr);
+            }
         }
     } else {
         for (int c0 = cgrp * 32; c0 < W; c0 += CSTEP) {
@@ -441,11 +516,15 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
         }
         ok = __syncthreads_and(ok) != 0;
         tc_fence_after();
-        const bool valid2 = ok && (row0 + lrow < rows);
-        for (int c0 = cgrp * 32; c0 < w.N2p; c0 += CSTEP) {
-            float v[32];
-            if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
-            if (valid2) tc_out32(op, rc[lrow], c0, v, op.nout, op.b2);
+        if constexpr (Op::kHasOut4) {
+            tc_out_rows(op, rc, tsm, tD, w.N2p, op.b2, row0, rows, ok);   // A/H and B buffers are free
+        } else {
+            const bool valid2 = ok && (row0 + lrow < rows);
+            for (int c0 = cgrp * 32; c0 < w.N2p; c0 += CSTEP) {
+                float v[32];
+                if (ok) tc_ld32(tD + lane_off + (unsigned)c0, v);
+                if (valid2) tc_out32(op, rc[lrow], c0, v, op.nout, op.b2);
+            }
         }
     }
     // a bulk copy whose wait gave up may still be landing: wait (bounded) before the CTA exits
