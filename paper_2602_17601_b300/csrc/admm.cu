@@ -552,12 +552,7 @@ gm_status admm_solve(const AdmmPlan& p) {
     for (int r = 0; r < p.rounds; ++r) {
         admm_form_p_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, p.H, p.Gram, p.S, p.P);
         GM_LAUNCH_CHECK();
-        cholesky_kernel<<<1, 1024, 0, st>>>(n, p.P, p.L, p.status, p.S);
-        GM_LAUNCH_CHECK();
-        trinv_kernel<<<cdiv((long)n * 32, 128), 128, 0, st>>>(n, p.L, p.Linv, p.S);
-        GM_LAUNCH_CHECK();
-        pinv_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, p.Linv, p.Pinv, p.S);
-        GM_LAUNCH_CHECK();
+        GM_TRY(factor_pinv(n, p.P, p.L, p.Linv, p.Pinv, p.status, p.S, p.bar, p.max_spins, st));
         if (r == 0 && p.ev_mid) GM_CUDA_TRY(cudaEventRecord(p.ev_mid, st));
         GM_CUDA_TRY(cudaMemsetAsync(p.bar, 0, sizeof(unsigned) * 4, st));
         GM_CUDA_TRY(cudaMemsetAsync(p.acc, 0, sizeof(float) * (2 * n + 4), st));

@@ -49,7 +49,7 @@ struct AdmmPlan {
     const float* Gram;     // C~' D C~ or nullptr when there are no half-space rows
     float *U, *y, *z;      // y, z: [n + rows]
     float *P, *Pinv;       // [n n]
-    double *L, *Linv;      // [n n]
+    double *L, *Linv;      // [factor_pad(n)^2]
     float* acc;            // [3 (2n + 4)]
     unsigned* bar;         // [4]
     int* status;           // [4]
@@ -67,12 +67,11 @@ gm_status admm_solve(const AdmmPlan& p);
 size_t admm2_smem_bytes(int n);
 const void* admm2_kernel_ptr(int n);
 
-// FP64 factor kernels (qp.cu); gate (nullable) skips them when no factorisation is due.
-__global__ void cholesky_kernel(int n, const float* __restrict__ P, double* __restrict__ L, int* status,
-                                const AdmmState* gate);
-__global__ void trinv_kernel(int n, const double* __restrict__ L, double* __restrict__ Linv,
-                             const AdmmState* gate);
-__global__ void pinv_kernel(int n, const double* __restrict__ Linv, float* __restrict__ Pinv,
-                            const AdmmState* gate);
+// FP64 Cholesky of P and P^{-1} = L^{-T} L^{-1} (stored FP32) in one cooperative launch
+// (factor.cu); gate (nullable) skips it when no factorisation is due.  L and Linv hold
+// factor_pad(n)^2 doubles; bar[0] is used (and reset) as the grid barrier counter.
+int factor_pad(int n);
+gm_status factor_pinv(int n, const float* P, double* L, double* Linv, float* Pinv, int* status,
+                      const AdmmState* gate, unsigned* bar, long long max_spins, cudaStream_t st);
 
 }  // namespace gmi

@@ -332,8 +332,8 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_rs = cv.take<float>(std::max(1L, c->rows_c));
     const long T = (nU + 31) / 32;
     c->d_gram_part = cv.take<float>(std::max((long)kMaxGramSplit * T * T * 1024, 4L * 1024 * nU));
-    c->d_L = cv.take<double>((size_t)nU * nU);
-    c->d_Linv = cv.take<double>((size_t)nU * nU);
+    c->d_L = cv.take<double>((size_t)factor_pad(nU) * factor_pad(nU));
+    c->d_Linv = cv.take<double>((size_t)factor_pad(nU) * factor_pad(nU));
     c->d_P = cv.take<float>((size_t)nU * nU);
     c->d_Pinv = cv.take<float>((size_t)nU * nU);
     c->d_G = cv.take<float>((size_t)nU * nU);

@@ -1,0 +1,238 @@
+// FP64 Cholesky factorisation of the ADMM x-update matrix P = H + rho (I + C~' S^2 C~)
+// (Sec. V-B; the paper factors rho I + H once per solve) and the explicit inverse
+// P^{-1} = L^{-T} L^{-1} used by the FP32 iterations, in one cooperative launch.
+//
+// FP64 issues at about 2 FMA per clock per SM on this part, so a one-CTA factorisation
+// of n = 160 is held at ~0.5 ms by the pipe alone.  The work is spread over the grid
+// in 16 x 16 blocks (the matrix padded with an identity block to np = 16 nb):
+//   right-looking blocked Cholesky: per block column k, CTA 0 factors the diagonal
+//   block and inverts it (D_k = L_kk^{-1}); the panel L_ik = A_ik D_k^T and the
+//   trailing update A_ij -= L_ik L_jk^T run entry-parallel on all CTAs.  CTA 0
+//   updates the next diagonal block itself and factors it at once, so a block
+//   column costs two grid barriers;
+//   X = L^{-1} by block rows: X_ii = D_i, X_ij = -sum_{m=j}^{i-1} (D_i L_im) X_mj;
+//   P^{-1}[a][b] = sum_{q >= max(a,b)} X[q][a] X[q][b], stored FP32.
+// Items of the thin phases are dealt to CTAs round-robin so that no single SM's FP64
+// pipe carries a phase.  Values written by other CTAs are read through L2 (ld.cg).
+#include "admm.h"
+#include "common.cuh"
+
+namespace gmi {
+
+namespace {
+
+constexpr int FB = 16;            // block size
+constexpr int FT = 256;           // threads per CTA
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+// Factor the FB x FB block S (row-major, lower part valid) in place with warp 0 and
+// invert it: S <- L_kk, Dm <- L_kk^{-1}; both also written to global (L and Linv at
+// block (k, k)).  A non-positive pivot sets GM_ERR_NUMERIC and continues with 1.
+__device__ void factor_diag(double (*S)[FB + 1], double (*Dm)[FB + 1], int k, int np, double* L, double* Linv,
+                            int* status) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        for (int j = 0; j < FB; ++j) {
+            if (lane == 0) {
+                double d = S[j][j];
+                if (!(d > 0.0)) {
+                    dev_fail(status, GM_ERR_NUMERIC);
+                    d = 1.0;
+                }
+                S[j][j] = sqrt(d);
+            }
+            __syncwarp();
+            if (lane > j && lane < FB) S[lane][j] /= S[j][j];
+            __syncwarp();
+            if (lane > j && lane < FB)
+                for (int c = j + 1; c <= lane; ++c) S[lane][c] -= S[lane][j] * S[c][j];
+            __syncwarp();
+        }
+        // column c of the inverse by forward substitution (lane c)
+        if (lane < FB) {
+            const int c = lane;
+            for (int r = 0; r < FB; ++r) {
+                if (r < c) {
+                    Dm[r][c] = 0.0;
+                    continue;
+                }
+                double s = (r == c) ? 1.0 : 0.0;
+                for (int q = c; q < r; ++q) s -= S[r][q] * Dm[q][c];
+                Dm[r][c] = s / S[r][r];
+            }
+        }
+        __syncwarp();
+        for (int e = lane; e < FB * FB; e += 32) {
+            const int r = e / FB, c = e % FB;
+            const long g = (long)(k * FB + r) * np + k * FB + c;
+            L[g] = c <= r ? S[r][c] : 0.0;
+            Linv[g] = Dm[r][c];
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* __restrict__ P, double* L,
+                                                    double* Linv, float* __restrict__ Pinv, int* status,
+                                                    const AdmmState* gate, unsigned* bar, long long max_spins) {
+    if (gate && (gate->done || !gate->need_factor)) return;     // uniform over the grid
+    __shared__ double S[FB][FB + 1];
+    __shared__ double Dm[FB][FB + 1];
+    const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nb = np / FB;
+    unsigned phase = 0;
+    bool ok = true;
+    auto sync = [&]() { ok = grid_barrier(bar, G, ++phase, max_spins, status) && ok; };
+
+    // ---- L <- sym(P), padded with the identity; Linv <- 0
+    for (long t = (long)b * FT + tid; t < (long)np * np; t += (long)G * FT) {
+        const int r = (int)(t / np), c = (int)(t % np);
+        double v = 0.0;
+        if (c <= r && r < n) v = 0.5 * ((double)P[(long)r * n + c] + (double)P[(long)c * n + r]);
+        else if (r == c) v = 1.0;
+        L[t] = v;
+        Linv[t] = 0.0;
+    }
+    sync();
+    if (!ok) return;
+    if (b == 0) {
+        for (int e = tid; e < FB * FB; e += FT) S[e / FB][e % FB] = ldcg(&L[(long)(e / FB) * np + e % FB]);
+        __syncthreads();
+        factor_diag(S, Dm, 0, np, L, Linv, status);
+    }
+    for (int k = 0; k < nb; ++k) {
+        sync();                                  // L_kk and D_k final
+        if (!ok) return;
+        if (k == nb - 1) break;
+        const int k0 = k * FB, r0 = k0 + FB;
+        // ---- panel: L_ik = A_ik D_k^T for the rows below the block (one warp per row)
+        if (tid < FB * FB) Dm[tid / FB][tid % FB] = ldcg(&Linv[(long)(k0 + tid / FB) * np + k0 + tid % FB]);
+        __syncthreads();
+        for (int r = r0 + b + G * warp; r < np; r += G * (FT / 32)) {
+            const double a = lane < FB ? ldcg(&L[(long)r * np + k0 + lane]) : 0.0;
+            double s = 0.0;
+#pragma unroll
+            for (int m = 0; m < FB; ++m) {
+                const double am = __shfl_sync(0xffffffffu, a, m);
+                s += lane < FB ? am * Dm[lane][m] : 0.0;
+            }
+            if (lane < FB) L[(long)r * np + k0 + lane] = s;
+        }
+        sync();
+        if (!ok) return;
+        // ---- trailing update of the lower triangle below/right of the block
+        const int m = np - r0;                    // trailing size
+        if (b == 0) {
+            // the next diagonal block, into shared memory, then factored at once
+            for (int e = tid; e < FB * FB; e += FT) {
+                const int r = e / FB, c = e % FB;
+                if (c <= r) {
+                    double v = ldcg(&L[(long)(r0 + r) * np + r0 + c]);
+                    for (int q = 0; q < FB; ++q)
+                        v -= ldcg(&L[(long)(r0 + r) * np + k0 + q]) * ldcg(&L[(long)(r0 + c) * np + k0 + q]);
+                    S[r][c] = v;
+                }
+            }
+            __syncthreads();
+            factor_diag(S, Dm, k + 1, np, L, Linv, status);
+        } else {
+            // entries (r, c), r0 <= c <= r < np, outside the next diagonal block, dealt over CTAs 1..G-1
+            const long ntri = (long)m * (m + 1) / 2;
+            for (long t = (b - 1) + (long)(G - 1) * tid; t < ntri; t += (long)(G - 1) * FT) {
+                // row-major lower-triangle index -> (r, c)
+                int r = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+                while ((long)(r + 1) * (r + 2) / 2 <= t) ++r;
+                while ((long)r * (r + 1) / 2 > t) --r;
+                const int c = (int)(t - (long)r * (r + 1) / 2);
+                if (r < FB) continue;             // inside the next diagonal block (CTA 0)
+                double v = 0.0;
+                for (int q = 0; q < FB; ++q)
+                    v += ldcg(&L[(long)(r0 + r) * np + k0 + q]) * ldcg(&L[(long)(r0 + c) * np + k0 + q]);
+                double* e = &L[(long)(r0 + r) * np + r0 + c];
+                *e = ldcg(e) - v;                 // last written by another CTA: read through L2
+            }
+        }
+    }
+    // ---- Lt_im = D_i L_im for m < i, in place in L (one item per block row i and column of L)
+    for (int it = b + G * tid; it < (nb * (nb - 1) / 2) * FB; it += G * FT) {
+        int i = 1, rem = it;
+        while (rem >= i * FB) {
+            rem -= i * FB;
+            ++i;
+        }
+        const int col = rem;                      // column in [0, 16 i)
+        double Lc[FB];
+        for (int s = 0; s < FB; ++s) Lc[s] = ldcg(&L[(long)(i * FB + s) * np + col]);
+        for (int r = 0; r < FB; ++r) {
+            double v = 0.0;
+            for (int s = 0; s <= r; ++s) v += ldcg(&Linv[(long)(i * FB + r) * np + i * FB + s]) * Lc[s];
+            L[(long)(i * FB + r) * np + col] = v;
+        }
+    }
+    sync();
+    if (!ok) return;
+    // ---- X = L^{-1} by block rows (X_ii = D_i already in Linv)
+    for (int i = 1; i < nb; ++i) {
+        const int ncol = i * FB;                  // columns left of the diagonal block
+        for (int t = b + G * tid; t < FB * ncol; t += G * FT) {
+            const int r = t / ncol, c = t % ncol;
+            const int j0 = (c / FB) * FB;         // first column of block j
+            double v = 0.0;
+            for (int q = j0; q < i * FB; ++q)
+                v -= ldcg(&L[(long)(i * FB + r) * np + q]) * ldcg(&Linv[(long)q * np + c]);
+            Linv[(long)(i * FB + r) * np + c] = v;
+        }
+        sync();
+        if (!ok) return;
+    }
+    // ---- P^{-1} = X' X (lower triangle computed, both halves stored)
+    const long ntri = (long)n * (n + 1) / 2;
+    for (long t = b + (long)G * tid; t < ntri; t += (long)G * FT) {
+        int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((long)(a + 1) * (a + 2) / 2 <= t) ++a;
+        while ((long)a * (a + 1) / 2 > t) --a;
+        const int c = (int)(t - (long)a * (a + 1) / 2);   // c <= a
+        double v = 0.0;
+        for (int q = a; q < np; ++q) v += ldcg(&Linv[(long)q * np + a]) * ldcg(&Linv[(long)q * np + c]);
+        Pinv[(long)a * n + c] = (float)v;
+        Pinv[(long)c * n + a] = (float)v;
+    }
+}
+
+int factor_pad(int n) { return (n + FB - 1) / FB * FB; }
+
+int factor_grid() {
+    static int g = 0;
+    if (!g) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g = sms >= 128 ? 128 : (sms > 2 ? sms : 2);   // the trailing update needs CTAs besides CTA 0
+    }
+    return g;
+}
+
+gm_status factor_pinv(int n, const float* P, double* L, double* Linv, float* Pinv, int* status,
+                      const AdmmState* gate, unsigned* bar, long long max_spins, cudaStream_t st) {
+    const int np = factor_pad(n);
+    GM_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(factor_grid());
+    cfg.blockDim = dim3(FT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GM_CUDA_TRY(cudaLaunchKernelEx(&cfg, factor_kernel, n, np, P, L, Linv, Pinv, status, gate, bar, max_spins));
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
+}  // namespace gmi

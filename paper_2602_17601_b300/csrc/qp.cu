@@ -31,74 +31,6 @@ __global__ void row_norm_kernel(long rows, int nu, int Mnc, const float* __restr
     if (lane == 0) rs[r] = (float)(1.0 / fmax(sqrt(s), 1e-8));   // floor keeps s_r^2 finite in FP32
 }
 
-__device__ __forceinline__ bool gated_off(const AdmmState* gate) {
-    return gate && (gate->done || !gate->need_factor);
-}
-
-// Right-looking Cholesky P = L L' in FP64, one CTA; a non-positive pivot sets GM_ERR_NUMERIC.
-__global__ void cholesky_kernel(int n, const float* __restrict__ P, double* __restrict__ L, int* status,
-                                const AdmmState* gate) {
-    if (gated_off(gate)) return;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (long t = tid; t < (long)n * n; t += nt) {
-        int i = (int)(t / n), j = (int)(t % n);
-        L[t] = (j <= i) ? 0.5 * ((double)P[t] + (double)P[(long)j * n + i]) : 0.0;
-    }
-    __syncthreads();
-    __shared__ double djj;
-    for (int j = 0; j < n; ++j) {
-        if (tid == 0) {
-            double d = L[(long)j * n + j];
-            if (!(d > 0.0)) {
-                dev_fail(status, GM_ERR_NUMERIC);
-                d = 1.0;
-            }
-            djj = sqrt(d);
-            L[(long)j * n + j] = djj;
-        }
-        __syncthreads();
-        for (int i = j + 1 + tid; i < n; i += nt) L[(long)i * n + j] /= djj;
-        __syncthreads();
-        const int tx = tid & 31, ty = tid >> 5, ny = nt >> 5;
-        for (int i = j + 1 + ty; i < n; i += ny) {
-            const double lij = L[(long)i * n + j];
-            for (int k = j + 1 + tx; k <= i; k += 32) L[(long)i * n + k] -= lij * L[(long)k * n + j];
-        }
-        __syncthreads();
-    }
-}
-
-// Column j of L^{-1} by forward substitution, one warp per column.
-__global__ void trinv_kernel(int n, const double* __restrict__ L, double* __restrict__ Linv,
-                             const AdmmState* gate) {
-    if (gated_off(gate)) return;
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (j >= n) return;
-    for (int i = lane; i < j; i += 32) Linv[(long)i * n + j] = 0.0;
-    for (int i = j; i < n; ++i) {
-        double s = 0.0;
-        for (int k = j + lane; k < i; k += 32) s += L[(long)i * n + k] * Linv[(long)k * n + j];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const double xi = ((i == j ? 1.0 : 0.0) - s) / L[(long)i * n + i];
-        if (lane == 0) Linv[(long)i * n + j] = xi;
-        __syncwarp();
-    }
-}
-
-// P^{-1} = L^{-T} L^{-1}, accumulated in FP64, stored FP32 for the iterations.
-__global__ void pinv_kernel(int n, const double* __restrict__ Linv, float* __restrict__ Pinv,
-                            const AdmmState* gate) {
-    if (gated_off(gate)) return;
-    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)n * n) return;
-    int i = (int)(t / n), j = (int)(t % n);
-    int k0 = i > j ? i : j;
-    double s = 0.0;
-    for (int k = k0; k < n; ++k) s += Linv[(long)k * n + i] * Linv[(long)k * n + j];
-    Pinv[t] = (float)s;
-}
-
 // ---------------------------------------------------------------- FP64 KKT certificate
 // kkt[0..n): A~'y (rows part), kkt[n]: max primal violation, kkt[n+1]: max wrong-sign y,
 // kkt[n+2]: max complementarity, all over the C~ rows.
@@ -312,8 +244,8 @@ extern "C" gm_status gm_qp_solve_noalloc(int N, int nu, int Mnc, const gm_settin
     float* P = cv.take<float>((size_t)n * n);
     float* Pinv = cv.take<float>((size_t)n * n);
     float* Gm = cv.take<float>((size_t)n * n);
-    double* L = cv.take<double>((size_t)n * n);
-    double* Linv = cv.take<double>((size_t)n * n);
+    double* L = cv.take<double>((size_t)factor_pad(n) * factor_pad(n));
+    double* Linv = cv.take<double>((size_t)factor_pad(n) * factor_pad(n));
     float* z = cv.take<float>(n + rows);
     float* ys = cv.take<float>(n + rows);
     float* rs = cv.take<float>(std::max(rows, 1L));
