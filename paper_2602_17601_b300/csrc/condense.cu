@@ -101,56 +101,86 @@ __global__ void recursion_kernel(int k, int M, int nu, const int* __restrict__ r
     }
 }
 
-// Gram matrices over packed stage-major rows: G = sum_rows w_r x_r x_r^T, where a
-// stage-k row has k nu leading non-zeros.  Tile (ti, tj), ti >= tj, 32 x 32 per
-// block; the rows of each contributing stage are split over gridDim.y.
-__global__ void gram_kernel(GramRows R, int n, float* __restrict__ part) {
+// Partial sums of G = sum_r w_r x_r x_r' over one share of every stage's rows: CTA
+// (block, sp) computes the 64 x 64 block (I, J), I >= J, over split sp, and stores it as
+// the four 32 x 32 tiles (ti, tj) of part[sp] (tiles past the matrix edge are skipped).
+// Rows of stage k have length k nu, so stages with k nu <= 64 I add nothing to row block I.
+// 16 x 16 threads, 4 x 4 outputs each; 16 rows of both column blocks staged per step.
+__global__ void __launch_bounds__(256) gram_kernel(GramRows R, int n, float* __restrict__ part) {
     const int T = (n + 31) / 32;
-    int lt = blockIdx.x, ti = 0;
-    while (lt > ti) { lt -= ti + 1; ++ti; }
-    const int tj = lt;
+    int lt = blockIdx.x, I = 0;
+    while (lt > I) { lt -= I + 1; ++I; }
+    const int J = lt;
     const int nsplit = gridDim.y, sp = blockIdx.y;
-    __shared__ float X1[32][33], X2[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 8 x 32
-    float acc[4] = {0, 0, 0, 0};
-    const int kmin = (ti * 32) / R.nu + 1;   // stage k contributes iff k nu > ti*32
+    __shared__ __align__(16) float X1[16][64];
+    __shared__ __align__(16) float X2[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const int c1b = I * 64, c2b = J * 64;
+    const int kmin = c1b / R.nu + 1;
     for (int k = kmin; k <= R.N; ++k) {
         const int L = k * R.nu;
         const long base = (long)R.rows_per_stage * R.nu * ((long)k * (k - 1) / 2);
         const int per = (R.rows_per_stage + nsplit - 1) / nsplit;
         const int r0 = sp * per, r1 = min(R.rows_per_stage, r0 + per);
-        for (int rb = r0; rb < r1; rb += 32) {
-            for (int t = threadIdx.x; t < 32 * 32; t += 256) {
-                const int rr = t / 32, cc = t % 32;
+        for (int rb = r0; rb < r1; rb += 16) {
+            for (int t = tid; t < 16 * 64; t += 256) {
+                const int rr = t >> 6, cc = t & 63;
                 const int r = rb + rr;
                 float w = 0.f, v1 = 0.f, v2 = 0.f;
                 if (r < r1) {
                     w = R.wts ? R.wts[(long)(k - R.wts_k0) * R.rows_per_stage + r] : 1.f;
                     if (R.wts_square) w *= w;
-                    const int c1 = ti * 32 + cc, c2 = tj * 32 + cc;
                     const float* xr = R.X + base + (long)r * L;
-                    if (c1 < L) v1 = xr[c1];
-                    if (c2 < L) v2 = xr[c2];
+                    if (c1b + cc < L) v1 = xr[c1b + cc];
+                    if (c2b + cc < L) v2 = xr[c2b + cc];
                 }
                 X1[rr][cc] = v1 * w;
                 X2[rr][cc] = v2;
             }
             __syncthreads();
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-                const float b = X2[rr][tx];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = fmaf(X1[rr][ty * 4 + q], b, acc[q]);
+            for (int rr = 0; rr < 16; ++rr) {
+                const float4 a = *reinterpret_cast<const float4*>(&X1[rr][ty * 4]);
+                const float4 b = *reinterpret_cast<const float4*>(&X2[rr][tx * 4]);
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
             }
             __syncthreads();
         }
     }
-    float* P = part + ((long)sp * T * T + (long)ti * T + tj) * 1024;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) P[(ty * 4 + q) * 32 + tx] = acc[q];
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c1 = c1b + ty * 4 + i, c2 = c2b + tx * 4 + j;
+            const int ti = c1 >> 5, tj = c2 >> 5;
+            if (ti < T && tj < T) part[(((long)sp * T + ti) * T + tj) * 1024 + (c1 & 31) * 32 + (c2 & 31)] = acc[i][j];
+        }
 }
 
-// G[c1][c2] = sum over splits (lower tiles, mirrored) + diag_add[c1] on the diagonal.
+int gram_blocks(int n) {
+    const int T64 = (n + 63) / 64;
+    return T64 * (T64 + 1) / 2;
+}
+
+int gram_split(int n, int sms, int cap) {
+    return std::max(1, std::min(cap, (2 * sms) / gram_blocks(n)));
+}
+
+gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStream_t st) {
+    gram_kernel<<<dim3(gram_blocks(n), nsplit), 256, 0, st>>>(R, n, part);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
 __global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
                                    const float* __restrict__ diag_add, float diag_scale,
                                    float* __restrict__ G) {
@@ -170,10 +200,7 @@ __global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ 
 gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, float diag_scale,
                float* G, cudaStream_t st) {
     const int n = c->nU;
-    const int T = (n + 31) / 32;
-    dim3 grid(T * (T + 1) / 2, nsplit);
-    gram_kernel<<<grid, 256, 0, st>>>(R, n, c->d_gram_part);
-    GM_LAUNCH_CHECK();
+    GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st));
     gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, c->d_gram_part, diag_add,
                                                               diag_scale, G);
     GM_LAUNCH_CHECK();
@@ -259,9 +286,7 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
     }
     // Eq. H: sum of per-node local Hessians + Rbar
     GramRows R{c->d_Gu, M * 6, nu, N, cost->Qdiag, 0, 0};
-    const int T = (c->nU + 31) / 32;
-    const int nsplit = std::max(1, std::min(64, (2 * c->num_sms) / std::max(1, T * (T + 1) / 2)));
-    GM_TRY(gram(c, R, nsplit, cost->Rdiag, 1.f, H, st));
+    GM_TRY(gram(c, R, gram_split(c->nU, c->num_sms, 64), cost->Rdiag, 1.f, H, st));
     // Eq. g
     const int gsplit = std::max(1, std::min(4 * c->num_sms, M * 6 / 8));
     grad_kernel<<<gsplit, 256, 0, st>>>(c->nU, M, nu, N, c->d_Gu, c->d_Gx, cost->Qdiag, cost->x_ref,

@@ -26,49 +26,41 @@ constexpr int FT = 256;           // threads per CTA
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
-// Factor the FB x FB block S (row-major, lower part valid) in place with warp 0 and
-// invert it: S <- L_kk, Dm <- L_kk^{-1}; both also written to global (L and Linv at
-// block (k, k)).  A non-positive pivot sets GM_ERR_NUMERIC and continues with 1.
-__device__ void factor_diag(double (*S)[FB + 1], double (*Dm)[FB + 1], int k, int np, double* L, double* Linv,
-                            int* status) {
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
-        for (int j = 0; j < FB; ++j) {
-            if (lane == 0) {
-                double d = S[j][j];
-                if (!(d > 0.0)) {
-                    dev_fail(status, GM_ERR_NUMERIC);
-                    d = 1.0;
-                }
-                S[j][j] = sqrt(d);
+// Factor the FB x FB block S (row-major, lower part valid) in place with all threads of
+// the CTA: S <- L_kk, written to L at block (k, k), and rd[j] = 1 / L_kk[j][j].  A
+// non-positive pivot sets GM_ERR_NUMERIC and continues with 1.
+__device__ void factor_diag(double (*S)[FB + 1], double* rd, int k, int np, double* L, int* status) {
+    const int tid = threadIdx.x;
+    for (int j = 0; j < FB; ++j) {
+        if (tid == 0) {
+            double d = S[j][j];
+            if (!(d > 0.0)) {
+                dev_fail(status, GM_ERR_NUMERIC);
+                d = 1.0;
             }
-            __syncwarp();
-            if (lane > j && lane < FB) S[lane][j] /= S[j][j];
-            __syncwarp();
-            if (lane > j && lane < FB)
-                for (int c = j + 1; c <= lane; ++c) S[lane][c] -= S[lane][j] * S[c][j];
-            __syncwarp();
+            d = sqrt(d);
+            S[j][j] = d;
+            rd[j] = 1.0 / d;
         }
-        // column c of the inverse by forward substitution (lane c)
-        if (lane < FB) {
-            const int c = lane;
-            for (int r = 0; r < FB; ++r) {
-                if (r < c) {
-                    Dm[r][c] = 0.0;
-                    continue;
-                }
-                double s = (r == c) ? 1.0 : 0.0;
-                for (int q = c; q < r; ++q) s -= S[r][q] * Dm[q][c];
-                Dm[r][c] = s / S[r][r];
+        __syncthreads();
+        if (tid > j && tid < FB) S[tid][j] *= rd[j];
+        __syncthreads();
+        // rank-1 update of the trailing lower triangle: entry (r, c), j < c <= r
+        const int m = FB - 1 - j;
+        if (tid < m * (m + 1) / 2) {
+            int r = 0, t = tid;
+            while (t > r) {
+                t -= r + 1;
+                ++r;
             }
+            const int rr = j + 1 + r, cc = j + 1 + t;
+            S[rr][cc] -= S[rr][j] * S[cc][j];
         }
-        __syncwarp();
-        for (int e = lane; e < FB * FB; e += 32) {
-            const int r = e / FB, c = e % FB;
-            const long g = (long)(k * FB + r) * np + k * FB + c;
-            L[g] = c <= r ? S[r][c] : 0.0;
-            Linv[g] = Dm[r][c];
-        }
+        __syncthreads();
+    }
+    for (int e = tid; e < FB * FB; e += blockDim.x) {
+        const int r = e / FB, c = e % FB;
+        L[(long)(k * FB + r) * np + k * FB + c] = c <= r ? S[r][c] : 0.0;
     }
     __syncthreads();
 }
@@ -81,6 +73,8 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
     if (gate && (gate->done || !gate->need_factor)) return;     // uniform over the grid
     __shared__ double S[FB][FB + 1];
     __shared__ double Dm[FB][FB + 1];
+    __shared__ double Pr[FB][FB + 1];             // panel rows of the next diagonal block
+    __shared__ double rd[FB];
     const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int nb = np / FB;
@@ -102,43 +96,54 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
     if (b == 0) {
         for (int e = tid; e < FB * FB; e += FT) S[e / FB][e % FB] = ldcg(&L[(long)(e / FB) * np + e % FB]);
         __syncthreads();
-        factor_diag(S, Dm, 0, np, L, Linv, status);
+        factor_diag(S, rd, 0, np, L, status);
     }
     for (int k = 0; k < nb; ++k) {
         sync();                                  // L_kk and D_k final
         if (!ok) return;
         if (k == nb - 1) break;
         const int k0 = k * FB, r0 = k0 + FB;
-        // ---- panel: L_ik = A_ik D_k^T for the rows below the block (one warp per row)
-        if (tid < FB * FB) Dm[tid / FB][tid % FB] = ldcg(&Linv[(long)(k0 + tid / FB) * np + k0 + tid % FB]);
+        // ---- panel: L_ik = A_ik L_kk^{-T}, row by row (forward substitution, one thread per row)
+        if (tid < FB * FB) Dm[tid / FB][tid % FB] = ldcg(&L[(long)(k0 + tid / FB) * np + k0 + tid % FB]);
+        if (tid < FB) rd[tid] = 1.0 / ldcg(&L[(long)(k0 + tid) * np + k0 + tid]);
         __syncthreads();
-        for (int r = r0 + b + G * warp; r < np; r += G * (FT / 32)) {
-            const double a = lane < FB ? ldcg(&L[(long)r * np + k0 + lane]) : 0.0;
-            double s = 0.0;
+        for (int r = r0 + b + G * tid; r < np; r += G * FT) {
+            double x[FB];
 #pragma unroll
-            for (int m = 0; m < FB; ++m) {
-                const double am = __shfl_sync(0xffffffffu, a, m);
-                s += lane < FB ? am * Dm[lane][m] : 0.0;
+            for (int c = 0; c < FB; ++c) x[c] = ldcg(&L[(long)r * np + k0 + c]);
+#pragma unroll
+            for (int c = 0; c < FB; ++c) {
+                double v = x[c];
+#pragma unroll
+                for (int q = 0; q < c; ++q) v -= x[q] * Dm[c][q];
+                x[c] = v * rd[c];
             }
-            if (lane < FB) L[(long)r * np + k0 + lane] = s;
+#pragma unroll
+            for (int c = 0; c < FB; ++c) L[(long)r * np + k0 + c] = x[c];
         }
         sync();
         if (!ok) return;
         // ---- trailing update of the lower triangle below/right of the block
         const int m = np - r0;                    // trailing size
         if (b == 0) {
-            // the next diagonal block, into shared memory, then factored at once
-            for (int e = tid; e < FB * FB; e += FT) {
-                const int r = e / FB, c = e % FB;
+            // the next diagonal block: its panel rows staged once, updated into shared memory,
+            // then factored at once
+            if (tid < FB * FB) {
+                Pr[tid / FB][tid % FB] = ldcg(&L[(long)(r0 + tid / FB) * np + k0 + tid % FB]);
+                S[tid / FB][tid % FB] = ldcg(&L[(long)(r0 + tid / FB) * np + r0 + tid % FB]);
+            }
+            __syncthreads();
+            if (tid < FB * FB) {
+                const int r = tid / FB, c = tid % FB;
                 if (c <= r) {
-                    double v = ldcg(&L[(long)(r0 + r) * np + r0 + c]);
-                    for (int q = 0; q < FB; ++q)
-                        v -= ldcg(&L[(long)(r0 + r) * np + k0 + q]) * ldcg(&L[(long)(r0 + c) * np + k0 + q]);
+                    double v = S[r][c];
+#pragma unroll
+                    for (int q = 0; q < FB; ++q) v -= Pr[r][q] * Pr[c][q];
                     S[r][c] = v;
                 }
             }
             __syncthreads();
-            factor_diag(S, Dm, k + 1, np, L, Linv, status);
+            factor_diag(S, rd, k + 1, np, L, status);
         } else {
             // entries (r, c), r0 <= c <= r < np, outside the next diagonal block, dealt over CTAs 1..G-1
             const long ntri = (long)m * (m + 1) / 2;
@@ -157,6 +162,28 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
             }
         }
     }
+    // ---- D_i = L_ii^{-1} into the diagonal blocks of Linv (block i on CTA i mod G; column c by
+    // forward substitution on thread c)
+    for (int i = b; i < nb; i += G) {
+        if (tid < FB * FB) S[tid / FB][tid % FB] = ldcg(&L[(long)(i * FB + tid / FB) * np + i * FB + tid % FB]);
+        __syncthreads();
+        if (tid < FB) {
+            const int c = tid;
+            double col[FB];
+#pragma unroll
+            for (int r = 0; r < FB; ++r) {
+                double v = (r == c) ? 1.0 : 0.0;
+#pragma unroll
+                for (int q = 0; q < r; ++q) v -= S[r][q] * col[q];
+                col[r] = r < c ? 0.0 : v / S[r][r];
+            }
+#pragma unroll
+            for (int r = 0; r < FB; ++r) Linv[(long)(i * FB + r) * np + i * FB + c] = col[r];
+        }
+        __syncthreads();
+    }
+    sync();
+    if (!ok) return;
     // ---- Lt_im = D_i L_im for m < i, in place in L (one item per block row i and column of L)
     for (int it = b + G * tid; it < (nb * (nb - 1) / 2) * FB; it += G * FT) {
         int i = 1, rem = it;

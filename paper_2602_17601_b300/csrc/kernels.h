@@ -34,6 +34,11 @@ struct GramRows {
 gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, float diag_scale,
                float* G, cudaStream_t st);
 __global__ void gram_kernel(GramRows R, int n, float* __restrict__ part);
+// Partial Gram sums over nsplit row shares into part [nsplit][T][T][32 x 32] (T = ceil(n/32));
+// gram_split picks nsplit (at most cap) for about two CTAs per SM.
+int gram_blocks(int n);
+int gram_split(int n, int sms, int cap);
+gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStream_t st);
 __global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
                                    const float* __restrict__ diag_add, float diag_scale,
                                    float* __restrict__ G);

@@ -147,10 +147,8 @@ static gm_status solve_with(AdmmPlan& p, int sms, int nsplit, float* gram_part, 
             row_norm_kernel<<<cdiv(rows * 32, 256), 256, 0, st>>>(rows, p.nu, p.Mnc, p.Ct, const_cast<float*>(p.rs));
             GM_LAUNCH_CHECK();
         }
-        const int T = (n + 31) / 32;
         GramRows R{p.Ct, p.Mnc, p.nu, p.N, scale ? p.rs : nullptr, 1, 1};
-        gram_kernel<<<dim3(T * (T + 1) / 2, nsplit), 256, 0, st>>>(R, n, gram_part);
-        GM_LAUNCH_CHECK();
+        GM_TRY(launch_gram(R, n, nsplit, gram_part, st));
         gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, gram_part, nullptr, 0.f,
                                                                   const_cast<float*>(p.Gram));
         GM_LAUNCH_CHECK();
@@ -193,9 +191,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     p.max_spins = c->s.timeout_spins > 0 ? c->s.timeout_spins : (1LL << 26);
     p.st = st;
     p.ev_mid = ev_mid;
-    const int T = (n + 31) / 32;
-    const int nsplit = std::max(1, std::min(64, (2 * c->num_sms) / std::max(1, T * (T + 1) / 2)));
-    return solve_with(p, c->num_sms, nsplit, c->d_gram_part, scale, c->d_kkt);
+    return solve_with(p, c->num_sms, gram_split(n, c->num_sms, 64), c->d_gram_part, scale, c->d_kkt);
 }
 
 }  // namespace gmi
