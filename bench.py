@@ -13,7 +13,13 @@ FP64 KKT check) on device-resident inputs; `e2e` adds the host->device copy of
 the measured state and the device->host copy of U* each step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--form fp32|mixed] [--workload chain1000|chain10]
+                  [--form mixed|bf16|fp32] [--no-graph] [--no-plain] [--workload chain1000|chain10]
+
+The chosen form (default): GNN MLPs and their Jacobian products on tcgen05 tensor
+cores with split-BF16 operands (forward rollout three pieces, reverse two), FP32
+condensing and ADMM, FP64 Cholesky and KKT check, the whole step replayed as a
+CUDA graph.  The same run times the plain GPU form (FP32 everywhere, eager
+launches) on the same inputs to the same ADMM residual and reports the speedup.
 
 Multi-GPU: one process per GPU (torchrun); every rank runs its own MPC
 instance (the path does not shard inside an instance: replicas), value = all
@@ -43,7 +49,9 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--form", default="fp32", choices=["fp32", "mixed", "bf16"])
+    p.add_argument("--form", default="mixed", choices=["fp32", "mixed", "bf16"])
+    p.add_argument("--no-graph", action="store_true", help="eager launches instead of CUDA-graph replay")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     p.add_argument("--workload", default="chain1000", choices=["chain1000", "chain10"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -194,22 +202,42 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def kernel_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if its source is unchanged."""
+KERNEL_TC = "tc_mlp_kernel<128, EdgeMpBwd, 2> (reverse edge-update MLP, split-BF16 tcgen05)"
+KERNEL_FP32 = "mlp2_kernel<128, EdgeMpBwd> (reverse edge-update MLP, FP32 SIMT)"
+TRAFFIC_SOURCES = ("paper_2602_17601_b300/csrc/tc_mlp.cuh", "paper_2602_17601_b300/csrc/gnn.cu")
+
+
+def sources_sha256():
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()
+
+
+def kernel_traffic(form):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the
+    kernel sources are unchanged since it was taken (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        d = json.load(open(path))
-        ent = d.get(kernel)
-        if not ent:
-            return None
-        src = open(os.path.join(ROOT, ent["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != ent["source_sha256"]:
+        ent = json.load(open(path)).get(form)
+        if not ent or ent.get("sources_sha256") != sources_sha256():
             return None
         return ent["dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+def timed_steps(torch, prob, x_dev, U, steps, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        prob.step(x_dev, U)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
 
 
 def run_ours(args):
@@ -224,59 +252,54 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     wl = workload(args.workload)
-    prec = {"fp32": gm.GM_PREC_FP32, "mixed": gm.GM_PREC_MIXED, "bf16": gm.GM_PREC_BF16}[args.form]
-    prob = gm.RTIProblem.from_workload(wl, precision=prec)
+    precs = {"fp32": gm.GM_PREC_FP32, "mixed": gm.GM_PREC_MIXED, "bf16": gm.GM_PREC_BF16}
+    graph = not args.no_graph
+    prob = gm.RTIProblem.from_workload(wl, precision=precs[args.form], graph=graph)
     info = gm.gm_ctx_info(prob.ctx)
     stream = torch.cuda.current_stream()
     x_dev = torch.as_tensor(wl.x0, device="cuda").contiguous()
     U = prob.empty(prob.nU)
+    warmup = max(args.warmup, 3)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    def step_all(n):
-        for _ in range(n):
-            prob.step(x_dev, U)
+    def max_over_ranks(v):
+        t = torch.tensor([v], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
-    # device-resident steps
+    # ---- the chosen form, device-resident inputs; the first warm-up step runs eagerly and
+    # counts the kernels of one step, the second is captured (graph replay from then on)
     prob.reset()
-    step_all(args.warmup)
+    gm.gm_ctx_set_kernel_timing(prob.ctx, True)
+    l0 = gm.gm_launch_count()
+    prob.step(x_dev, U)
+    torch.cuda.synchronize()
+    kernels_per_step = gm.gm_launch_count() - l0
+    for _ in range(warmup - 1):
+        prob.step(x_dev, U)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    gm.gm_ctx_set_timing(prob.ctx, True)
-    gm.gm_ctx_phase_ms(prob.ctx)          # clear
-    launches0 = gm.gm_launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    iters = []
-    e0.record(stream)
-    for _ in range(args.steps):
-        prob.step(x_dev, U)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    launches = gm.gm_launch_count() - launches0
+    ms = timed_steps(torch, prob, x_dev, U, args.steps, stream)
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    gm.gm_ctx_set_timing(prob.ctx, False)
-    phases, nrec = gm.gm_ctx_phase_ms(prob.ctx)
+    kst = gm.gm_ctx_kernel_stats(prob.ctx)        # dominant kernel, last timed step
+    replayed, captures = prob.graph_state()
     st = prob.read_stats()
-    iters.append(st["iters"])
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms)
 
-    # end to end through the public API: pinned host state in, U* out, every step
+    # ---- end to end through the public API: pinned host state in, U* out, every step
     x_host = torch.as_tensor(wl.x0).pin_memory()
     U_host = torch.empty(prob.nU, dtype=torch.float32).pin_memory()
     prob.reset()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         x_dev.copy_(x_host, non_blocking=True)
         prob.step(x_dev, U)
         U_host.copy_(U, non_blocking=True)
@@ -291,56 +314,83 @@ def run_ours(args):
         U_host.copy_(U, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3) / args.steps
-    t = torch.tensor([ms_e2e], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3) / args.steps)
+
+    # ---- per-phase breakdown (events at phase boundaries force eager steps: not timed above)
+    gm.gm_ctx_set_kernel_timing(prob.ctx, False)
+    gm.gm_ctx_set_timing(prob.ctx, True)
+    gm.gm_ctx_phase_ms(prob.ctx)
+    for _ in range(3):
+        prob.step(x_dev, U)
+    phases, nrec = gm.gm_ctx_phase_ms(prob.ctx)
+    gm.gm_ctx_set_timing(prob.ctx, False)
+    per_phase = {k: v / max(nrec, 1) for k, v in phases.items()}
+
+    # ---- the plain GPU form: FP32 everywhere, eager launches, same inputs and residual
+    plain = None
+    if not args.no_plain and args.form != "fp32":
+        del prob
+        torch.cuda.empty_cache()
+        pp = gm.RTIProblem.from_workload(wl, precision=gm.GM_PREC_FP32, graph=False)
+        pp.reset()
+        for _ in range(warmup):
+            pp.step(x_dev, U)
+        torch.cuda.synchronize()
+        barrier()
+        ms_p = max_over_ranks(timed_steps(torch, pp, x_dev, U, args.steps, stream))
+        sp = pp.read_stats()
+        plain = {"form": "fp32, eager launches", "value": world * 1000.0 / ms_p, "unit": "steps/s",
+                 "ms_per_step": ms_p, "admm_iters_last_step": sp["iters"], "kkt_stat_last_step": sp["kkt_stat"],
+                 "r_dual_last_step": sp["r_dual"], "status_last_step": sp["status"]}
+        del pp
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant phase
-    per_phase = {k: v / max(nrec, 1) for k, v in phases.items()}
-    dom = max(per_phase, key=per_phase.get)
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
         peaks = json.load(open(pk))
-    sm_max = (clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0)
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s
-    flops = {"rollout": info["flops_rollout"], "jacobian": info["flops_jacobian"],
-             "condense": info["flops_condense"], "qp_setup": info["flops_qp_setup"],
-             "admm_kkt": info["flops_admm_iter"] * max(st["iters"], 1)}
-    achieved = flops[dom] / (per_phase[dom] * 1e-3) / 1e12
-    roof = {"kernel": {"jacobian": "mlp2_kernel (reverse-mode cone MLPs)",
-                       "rollout": "mlp2_kernel (forward MLPs)", "condense": "recursion/gram kernels",
-                       "qp_setup": "cholesky/trinv/pinv", "admm_kkt": "admm_kernel"}[dom],
-            "phase": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak,
-            "peak_source": "FP32 FFMA: SMs x 128 lanes x 2 flop x max SM clock (derived, not measured)",
-            "traffic": kernel_traffic("mlp2_kernel_reverse") if dom == "jacobian" else None,
-            "phase_ms": per_phase, "phase_flops": flops}
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_peak else "fallback 6400 GB/s"
+    hbm_peak = hbm_peak or 6400.0
+    k_ms = kst["ms"]
+    achieved = kst["bytes"] / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    products = {"mixed": 3, "bf16": 1, "fp32": 1}[args.form]
+    roof = {"kernel": KERNEL_FP32 if args.form == "fp32" else KERNEL_TC.replace(", 2>", ", 1>" if args.form == "bf16" else ", 2>"),
+            "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "peak_source": peak_src,
+            "traffic": kernel_traffic(args.form),
+            "launches_per_step": kst["launches"], "ms_per_step": k_ms,
+            "algorithmic_bytes_per_launch": kst["bytes"] / max(kst["launches"], 1),
+            "avg_launch_ms": k_ms / max(kst["launches"], 1),
+            "tensor_tflops": kst["flops"] * products / (k_ms * 1e-3) / 1e12 if k_ms > 0 else 0.0,
+            "tensor_peak_tflops": peaks.get("bf16_tflops_sustained"),
+            "share_of_step": k_ms / ms,
+            "phase_ms": per_phase}
     out = {"metric": METRIC, "value": world * 1000.0 / ms, "unit": "steps/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "steps": args.steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32 (FP64 Cholesky and KKT)" if args.form == "fp32" else "bf16/f32/f64",
+           "dtype": {"fp32": "f32", "mixed": "bf16x3/f32", "bf16": "bf16/f32"}[args.form] + " (f64 Cholesky, KKT)",
            "data": "synthetic (seeded)",
            "config": config_of(wl, args.form, {
+               "graph_replay": bool(replayed), "graph_captures": captures,
                "parallelism": f"replicas{world}",
                "l2": "inputs larger than L2: the step streams ~2 GB of Jacobian/condensing buffers",
                "admm_iters_last_step": st["iters"], "kkt_stat_last_step": st["kkt_stat"],
-               "status_last_step": st["status"]}),
+               "r_dual_last_step": st["r_dual"], "status_last_step": st["status"]}),
            "clocks": clocks,
            "e2e": {"value": world * 1000.0 / ms_e2e, "unit": "steps/s",
-                   "h2d_bytes_per_step": int(wl.x0.nbytes), "d2h_bytes_per_step": int(prob.nU * 4)},
-           "gpu_launches": int(launches),
+                   "h2d_bytes_per_step": int(wl.x0.nbytes), "d2h_bytes_per_step": int(prob_nU(wl) * 4)},
+           "gpu_launches": int(kernels_per_step * args.steps),
            "roofline": roof,
            "context": "paper: 100 Hz closed loop up to 1000 nodes, N=20 on RTX 4090 + Ryzen 9 7950X3D "
                       "with its own (unstated-size) trunk GNN; not this workload"}
+    if plain is not None:
+        out["plain_gpu_form"] = plain
+        out["speedup_vs_plain"] = plain["ms_per_step"] / ms
     if world == 1 and not args.no_cpu_baseline:
         secs, parts = oracle_sample_seconds(wl, n_jac=24)
         out["cpu_baseline"] = {"value": 1.0 / secs, "unit": "steps/s", "cores": cpu_cores(),
@@ -349,6 +399,10 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def prob_nU(wl):
+    return wl.N * wl.nu
 
 
 def main():

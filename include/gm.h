@@ -312,6 +312,31 @@ gm_status gm_ctx_phase_ms(gm_ctx* ctx, float* ms5, int* steps);
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long gm_launch_count(void);
 
+/* CUDA-graph replay of gm_rti_step (no paper counterpart: a launch-overhead
+ * measure for the real-time loop).  When on, the first gm_rti_step runs as
+ * usual; the next one is captured once into a CUDA graph (on an internal
+ * stream) and every later call replays that graph on the caller's stream.
+ * The graph bakes in every pointer and scalar of the call (x_meas, cost,
+ * constraints, U, u0, stats, settings); a call that changes any of them is
+ * captured anew.  Phase timing (gm_ctx_set_timing) runs the steps eagerly.
+ * If the capture fails the context falls back to eager steps and
+ * gm_ctx_graph_state reports 0.  gm_ctx_graph_state: 1 when the last step
+ * replayed a graph, 0 otherwise; captures counts the captures so far. */
+gm_status gm_ctx_set_graph(gm_ctx* ctx, int on);
+gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures);
+
+/* Launch timing of the dominant kernel, the reverse edge-update MLP (one launch per
+ * message-passing level and stage chunk; Eq. linearized_dynamics).  When on,
+ * gm_rti_step records a CUDA event pair around each of these launches (inside
+ * the captured graph in graph mode) and notes each launch's algorithmic DRAM
+ * bytes (rows x 4W for the hidden and carry outputs, 4W per carried input row
+ * and per distinct aggregate row, W/8 per distinct edge mask) and FLOPs
+ * (4 W^2 per row, one product).  gm_ctx_kernel_stats waits for the last
+ * recorded step and returns its launch count, summed milliseconds, bytes and
+ * FLOPs (all zero before the first recorded step). */
+gm_status gm_ctx_set_kernel_timing(gm_ctx* ctx, int on);
+gm_status gm_ctx_kernel_stats(gm_ctx* ctx, int* launches, double* ms, double* bytes, double* flops);
+
 /* ------------------------------------------------------------------------
  * gm_qp_solve_noalloc — the ADMM solve of gm_qp_solve for callers that
  * cannot allocate device memory at all.  The paper has no counterpart: it

@@ -105,6 +105,10 @@ def _load():
         "gm_ctx_set_timing": ([vp, C.c_int], C.c_int),
         "gm_ctx_phase_ms": ([vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
         "gm_launch_count": ([], C.c_ulonglong),
+        "gm_ctx_set_graph": ([vp, C.c_int], C.c_int),
+        "gm_ctx_graph_state": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+        "gm_ctx_set_kernel_timing": ([vp, C.c_int], C.c_int),
+        "gm_ctx_kernel_stats": ([vp, C.POINTER(C.c_int)] + [C.POINTER(C.c_double)] * 3, C.c_int),
         "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -119,7 +123,9 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_gnn_load", "gm_gnn_destroy", "gm_ctx_workspace_size", "gm_ctx_create",
                     "gm_ctx_destroy", "gm_jac_pattern", "gm_linearize", "gm_condense",
                     "gm_qp_solve", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
-                    "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count", "gm_qp_solve_noalloc")
+                    "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count", "gm_qp_solve_noalloc",
+                    "gm_ctx_set_graph", "gm_ctx_graph_state", "gm_ctx_set_kernel_timing",
+                    "gm_ctx_kernel_stats")
 
 GM_NOALLOC_MAX_NU = 64
 GM_NOALLOC_MAX_ROWS = 8192
@@ -158,6 +164,29 @@ def gm_ctx_phase_ms(ctx):
 
 def gm_launch_count():
     return int(_lib.gm_launch_count())
+
+
+def gm_ctx_set_graph(ctx, on):
+    _check("gm_ctx_set_graph", _lib.gm_ctx_set_graph(ctx, int(bool(on))))
+
+
+def gm_ctx_set_kernel_timing(ctx, on):
+    _check("gm_ctx_set_kernel_timing", _lib.gm_ctx_set_kernel_timing(ctx, int(bool(on))))
+
+
+def gm_ctx_kernel_stats(ctx):
+    """Last recorded step's reverse edge-MLP launches: dict(launches, ms, bytes, flops)."""
+    n = C.c_int()
+    ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+    _check("gm_ctx_kernel_stats", _lib.gm_ctx_kernel_stats(ctx, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
+    return dict(launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
+
+
+def gm_ctx_graph_state(ctx):
+    """(1 if the last gm_rti_step replayed a CUDA graph else 0, captures so far)."""
+    r, n = C.c_int(), C.c_int()
+    _check("gm_ctx_graph_state", _lib.gm_ctx_graph_state(ctx, C.byref(r), C.byref(n)))
+    return r.value, n.value
 
 
 def lib():

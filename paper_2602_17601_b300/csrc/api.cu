@@ -688,21 +688,16 @@ gm_status gm_qp_solve(gm_ctx* ctx, const float* H, const float* g, const float* 
                     static_cast<cudaStream_t>(stream));
 }
 
-gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
-                      float* u0, gm_stats* stats, void* stream) {
-    clear_error();
-    GM_CHECK_ARG(ctx && x_meas && U, "NULL argument");
-    GM_TRY(check_cost(ctx, cost, cons));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    gm_ctx* c = ctx;
+static gm_status rti_body(gm_ctx* c, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
+                          float* u0, gm_stats* stats, cudaStream_t st, bool timed) {
     std::array<cudaEvent_t, 6> ev{};
-    const bool timed = c->timing && c->events.size() < 100000;
     if (timed) {
         for (auto& e : ev) GM_CUDA_TRY(cudaEventCreate(&e));
         c->events.push_back(ev);
         GM_CUDA_TRY(cudaEventRecord(ev[0], st));
     }
     GM_CUDA_TRY(cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), st));
+    c->kev_n = 0;
     GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
     if (timed) GM_CUDA_TRY(cudaEventRecord(ev[1], st));
     GM_TRY(gnn_jacobians(c, c->d_x_hat, c->d_u_hat, c->d_A, c->d_B, c->d_c, st));
@@ -722,6 +717,115 @@ gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, con
     GM_CUDA_TRY(cudaMemcpyAsync(U, c->d_U, sizeof(float) * c->nU, cudaMemcpyDeviceToDevice, st));
     if (u0) GM_CUDA_TRY(cudaMemcpyAsync(u0, c->d_U, sizeof(float) * c->nu, cudaMemcpyDeviceToDevice, st));
     GM_TRY(shift_inputs(c, c->d_U, c->d_u_hat, st));
+    return GM_OK;
+}
+
+// Everything a captured step bakes in.
+static std::vector<uintptr_t> graph_key(const gm_ctx* c, const float* x_meas, const gm_cost* cost,
+                                        const gm_constr* cons, float* U, float* u0, gm_stats* stats) {
+    auto P = [](const void* p) { return reinterpret_cast<uintptr_t>(p); };
+    std::vector<uintptr_t> k = {P(x_meas), P(cost->Qdiag), P(cost->Rdiag), P(cost->x_ref), P(cost->u_ref),
+                                P(cons->u_lo), P(cons->u_hi), P(cons->Cx), P(cons->dx), (uintptr_t)cons->n_spheres,
+                                P(cons->spheres), P(U), P(u0), P(stats)};
+    uint32_t rho, tol;
+    std::memcpy(&rho, &c->s.rho, 4);
+    std::memcpy(&tol, &c->s.tol, 4);
+    k.insert(k.end(), {(uintptr_t)rho, (uintptr_t)tol, (uintptr_t)c->s.max_iter, (uintptr_t)c->s.scale_rows,
+                       (uintptr_t)c->s.adapt_rho, (uintptr_t)c->s.timeout_spins, (uintptr_t)c->s.polish});
+    return k;
+}
+
+gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
+                      float* u0, gm_stats* stats, void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx && x_meas && U, "NULL argument");
+    GM_TRY(check_cost(ctx, cost, cons));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    gm_ctx* c = ctx;
+    const bool timed = c->timing && c->events.size() < 100000;
+    c->graph_replayed = false;
+    if (!c->graph_on || c->graph_failed || timed) return rti_body(c, x_meas, cost, cons, U, u0, stats, st, timed);
+    auto key = graph_key(c, x_meas, cost, cons, U, u0, stats);
+    if (c->graph_exec && key == c->graph_key) {
+        GM_CUDA_TRY(cudaGraphLaunch(c->graph_exec, st));
+        c->graph_replayed = true;
+        return GM_OK;
+    }
+    if (c->graph_eager++ == 0) return rti_body(c, x_meas, cost, cons, U, u0, stats, st, false);
+    // capture on an internal stream (the caller's may be the legacy default stream), replay on st
+    if (!c->cap_stream) GM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    GM_CUDA_TRY(cudaStreamSynchronize(st));
+    GM_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+    const gm_status body = rti_body(c, x_meas, cost, cons, U, u0, stats, c->cap_stream, false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+    cudaGraphExec_t exec = nullptr;
+    if (body == GM_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+        cudaGraphDestroy(g);
+        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = exec;
+        c->graph_key = key;
+        ++c->graph_captures;
+        GM_CUDA_TRY(cudaGraphLaunch(c->graph_exec, st));
+        c->graph_replayed = true;
+        return GM_OK;
+    }
+    // capture unsupported here: eager steps from now on
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    c->graph_failed = true;
+    return rti_body(c, x_meas, cost, cons, U, u0, stats, st, false);
+}
+
+gm_status gm_ctx_set_graph(gm_ctx* ctx, int on) {
+    clear_error();
+    GM_CHECK_ARG(ctx, "ctx is NULL");
+    ctx->graph_on = on != 0;
+    ctx->graph_failed = false;
+    ctx->graph_eager = 0;
+    if (!ctx->graph_on && ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+        ctx->graph_key.clear();
+    }
+    return GM_OK;
+}
+
+gm_status gm_ctx_set_kernel_timing(gm_ctx* ctx, int on) {
+    clear_error();
+    GM_CHECK_ARG(ctx, "ctx is NULL");
+    if ((on != 0) != ctx->ktiming && ctx->graph_exec) {     // the captured step changes: capture anew
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+        ctx->graph_key.clear();
+    }
+    ctx->ktiming = on != 0;
+    ctx->kev_n = 0;
+    return GM_OK;
+}
+
+gm_status gm_ctx_kernel_stats(gm_ctx* ctx, int* launches, double* ms, double* bytes, double* flops) {
+    clear_error();
+    GM_CHECK_ARG(ctx && launches && ms && bytes && flops, "NULL argument");
+    *launches = 0;
+    *ms = *bytes = *flops = 0.0;
+    for (int i = 0; i < ctx->kev_n && i < (int)ctx->kev.size(); ++i) {
+        GM_CUDA_TRY(cudaEventSynchronize(ctx->kev[i][1]));
+        float t = 0.f;
+        GM_CUDA_TRY(cudaEventElapsedTime(&t, ctx->kev[i][0], ctx->kev[i][1]));
+        *ms += t;
+        *bytes += ctx->kev_bytes[i];
+        *flops += ctx->kev_flops[i];
+        ++*launches;
+    }
+    return GM_OK;
+}
+
+gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures) {
+    clear_error();
+    GM_CHECK_ARG(ctx, "ctx is NULL");
+    if (replayed) *replayed = ctx->graph_replayed ? 1 : 0;
+    if (captures) *captures = ctx->graph_captures;
     return GM_OK;
 }
 

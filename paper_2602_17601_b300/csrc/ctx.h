@@ -129,9 +129,24 @@ struct gm_ctx {
     // phase timing of gm_rti_step (events on the caller's stream)
     bool timing = false;
     std::vector<std::array<cudaEvent_t, 6>> events;
+    // CUDA-graph replay of gm_rti_step
+    bool graph_on = false, graph_failed = false, graph_replayed = false;
+    int graph_eager = 0, graph_captures = 0;
+    std::vector<uintptr_t> graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    // launch timing of the reverse edge-update MLP (events around each launch of the last step)
+    bool ktiming = false;
+    int kev_n = 0;
+    std::vector<std::array<cudaEvent_t, 2>> kev;
+    std::vector<double> kev_bytes, kev_flops;
 
     ~gm_ctx() {
+        for (auto& e : kev)
+            for (auto ev : e) cudaEventDestroy(ev);
         for (auto& e : events)
             for (auto ev : e) cudaEventDestroy(ev);
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
     }
 };

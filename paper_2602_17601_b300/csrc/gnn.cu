@@ -770,6 +770,45 @@ static void fill_bwd(Op& op, const gm_ctx* c, const MlpOff& m, int k0, int layer
     }
 }
 
+// Event record that a stream capture keeps as a node of the graph (the external flag is
+// only accepted while the stream is capturing).
+static cudaError_t record_kev(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, st);
+}
+
+// Launch timing of the reverse edge-update MLP: event pair kev[i] for the i-th launch of
+// the step, with the launch's algorithmic bytes and FLOPs (level r, Ns stages).
+static int kernel_timing_begin(gm_ctx* c, int r, int Ns, cudaStream_t st) {
+    const int i = c->kev_n++;
+    if ((int)c->kev.size() <= i) {
+        std::array<cudaEvent_t, 2> e{};
+        if (cudaEventCreate(&e[0]) != cudaSuccess || cudaEventCreate(&e[1]) != cudaSuccess) return -1;
+        c->kev.push_back(e);
+        c->kev_bytes.push_back(0.0);
+        c->kev_flops.push_back(0.0);
+    }
+    const Cones& C = c->cones;
+    const double W = c->W, Re = (double)C.er_edge[r].size(), Rn = (double)C.nr_node[r].size();
+    double carried = 0.0;
+    for (int p : C.er_prev[r]) carried += p >= 0 ? 1.0 : 0.0;
+    std::vector<char> seen(c->E, 0);
+    double edges = 0.0;
+    for (int e : C.er_edge[r])
+        if (!seen[e]) {
+            seen[e] = 1;
+            edges += 1.0;
+        }
+    const double rows = 3.0 * Ns * Re;
+    c->kev_bytes[i] = 4.0 * W * (2.0 * rows + 3.0 * Ns * carried + 3.0 * Ns * Rn) + Ns * edges * W / 8.0;
+    c->kev_flops[i] = 4.0 * W * W * rows;
+    if (record_kev(c->kev[i][0], st) != cudaSuccess) return -1;
+    return i;
+}
+
 // Reverse pass over all stages (in chunks): A, B, c of Eq. linearized_dynamics.
 gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float* A, float* B,
                         float* cvec, cudaStream_t st) {
@@ -805,7 +844,9 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
                 op.dagg = c->d_dagg; op.de_in = de_in; op.ehid = c->d_ehid; op.de_out = de_out;
                 op.er_edge = d.er_edge[r]; op.er_dstrow = d.er_dstrow[r]; op.er_prev = d.er_prev[r];
                 op.Rn = Rn; op.Rp = r > 0 ? d.er_count[r - 1] : 0;
+                const int kt = c->ktiming ? kernel_timing_begin(c, r, Ns, st) : -1;
                 GM_TRY(launch_mlp(c, op, tc_edge_bwd(c, m), st));
+                if (kt >= 0) GM_CUDA_TRY(record_kev(c->kev[kt][1], st));
             }
             {
                 const int Rn1 = d.nr_count[r + 1];

@@ -8,8 +8,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (GM_PREC_FP32, STATS_BYTES, gm_condense, gm_ctx_create, gm_ctx_destroy, gm_ctx_reset,
-               gm_ctx_workspace_size, gm_gnn_destroy, gm_gnn_load, gm_graph_create, gm_graph_destroy,
+from . import (GM_PREC_FP32, STATS_BYTES, gm_condense, gm_ctx_create, gm_ctx_destroy, gm_ctx_graph_state,
+               gm_ctx_reset, gm_ctx_set_graph, gm_ctx_workspace_size, gm_gnn_destroy, gm_gnn_load, gm_graph_create, gm_graph_destroy,
                gm_jac_pattern, gm_linearize, gm_qp_solve, gm_rti_step, make_constr, make_cost,
                make_settings, read_stats)
 
@@ -26,7 +26,7 @@ class RTIProblem:
     def __init__(self, M, src, dst, nu, act_node, K, W, dt, blob, N, Qdiag, Rdiag, x_ref, u_ref, u_lo,
                  u_hi, Cx=None, dx=None, spheres=None, rho=0.1, tol=1e-6, max_iter=4000,
                  precision=GM_PREC_FP32, polish=0, timeout_spins=0, scale_rows=1, adapt_rho=1,
-                 device="cuda"):
+                 graph=False, device="cuda"):
         import torch
         self.torch = torch
         self.M, self.nu, self.N, self.K, self.W = int(M), int(nu), int(N), int(K), int(W)
@@ -59,6 +59,11 @@ class RTIProblem:
         self.row_ptr, self.col = gm_jac_pattern(self.ctx, self.M)
         self.nnzb = int(self.col.size)
         self.stats = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=device)
+        # fixed step buffers, so that a captured step (graph=True) keeps its pointers
+        self._x = torch.zeros(self.M * 6, dtype=torch.float32, device=device)
+        self._U = torch.zeros(self.nU, dtype=torch.float32, device=device)
+        if graph:
+            gm_ctx_set_graph(self.ctx, 1)
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -112,11 +117,17 @@ class RTIProblem:
         return U, y
 
     def step(self, x_meas, U=None, u0=None):
+        """One RTI step from measured state x_meas [M*6].  Without U the result lands in a
+        buffer of this object that the next step overwrites."""
         t = self.torch
-        x_meas = t.as_tensor(x_meas, dtype=t.float32, device=self.Qdiag.device).contiguous()
-        U = self.empty(self.nU) if U is None else U
-        gm_rti_step(self.ctx, x_meas, self.cost, self.constr, U, u0, self.stats)
+        self._x.copy_(t.as_tensor(x_meas, dtype=t.float32).reshape(-1), non_blocking=True)
+        U = self._U if U is None else U
+        gm_rti_step(self.ctx, self._x, self.cost, self.constr, U, u0, self.stats)
         return U
+
+    def graph_state(self):
+        """(1 if the last step replayed a CUDA graph, number of captures)."""
+        return gm_ctx_graph_state(self.ctx)
 
     def reset(self):
         gm_ctx_reset(self.ctx)
