@@ -237,8 +237,10 @@ gm_status gm_condense(gm_ctx* ctx, const float* x_hat, const float* A, const flo
                       float* H, float* g, float* Ct, float* dt, void* stream);
 
 /* ------------------------------------------------------------------------
- * gm_qp_solve — ADMM on the condensed QP (fixed rho, no relaxation):
- *   P = H + rho (I + C~'C~), factored in FP64 (Cholesky) once;
+ * gm_qp_solve — ADMM on the condensed QP (no relaxation):
+ *   P = H + rho (I + C~'S^2 C~) (S the row scaling when settings.scale_rows),
+ *   factored in FP64 (Cholesky) once, and again after each adaptive rho
+ *   update (settings.adapt_rho: every 25 iterations, at most 5 updates);
  *   per iteration U = P^{-1}(A~'(rho z - y) - g), a = A~U,
  *   z = clip(a + y/rho, l, h), y += rho (a - z), with A~ = [I; C~],
  *   l = [u_lo; -inf], h = [u_hi; d~]; stop when |a - z|_inf <= tol and the
@@ -336,6 +338,44 @@ gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures);
  * FLOPs (all zero before the first recorded step). */
 gm_status gm_ctx_set_kernel_timing(gm_ctx* ctx, int on);
 gm_status gm_ctx_kernel_stats(gm_ctx* ctx, int* launches, double* ms, double* bytes, double* flops);
+
+/* ------------------------------------------------------------------------
+ * Learned ADMM warm start (no paper counterpart; an added systems pattern).
+ * A 3-layer MLP  in -> H -> H -> out  (Linear-ReLU-Linear-ReLU-Linear) maps
+ * the features of an MPC instance to a primal input sequence and box duals
+ * (out = 2 nU: U^0 then y^0), which warm-start gm_qp_solve.  Cold-start
+ * ADMM stays the judge: it runs whenever the warm-started solve does not
+ * converge.  Features (gm_ws_features, [2W + 3M]): the mean and the max over
+ * nodes of the final node latents h^K of stage 0 at (x_meas, the context's
+ * current u_hat[0]; zeros after gm_ctx_reset), then the stage-1 reference
+ * positions x_ref[1][i][0..2].  Inputs and outputs are standardised with
+ * stored means and deviations (norm = [in mean | in std | out mean | out std]).
+ * Parameters are packed [W0 (in x H) | b0 | W1 (H x H) | b1 | W2 (H x out) | b2],
+ * each W row-major [fan-in][fan-out].  All arrays are device pointers on the
+ * given stream (params/norm may be host pointers in set/get).
+ *   gm_ws_workspace_size / gm_ws_create: caller-owned workspace (256-byte
+ *     aligned) holding parameters, gradients, Adam moments and activations for
+ *     batches up to max_batch; the library allocates nothing.
+ *   gm_ws_set_params: parameters and normalisation; resets Adam.
+ *   gm_ws_forward: out [B][n_out] for feat [B][n_in].
+ *   gm_ws_train_step: one Adam step (bias-corrected) on the mean squared error
+ *     of the standardised outputs against target [B][n_out]; loss (device
+ *     float, nullable) receives that loss before the step.
+ *   gm_ws_grad: the gradient of the last train step (packed like params).
+ * ---------------------------------------------------------------------- */
+typedef struct gm_ws gm_ws;
+size_t gm_ws_workspace_size(int n_in, int n_hidden, int n_out, int max_batch);
+gm_status gm_ws_create(int n_in, int n_hidden, int n_out, int max_batch, void* workspace, size_t bytes,
+                       gm_ws** out);
+void gm_ws_destroy(gm_ws* w);
+long long gm_ws_param_count(const gm_ws* w);
+gm_status gm_ws_set_params(gm_ws* w, const float* params, const float* norm, void* stream);
+gm_status gm_ws_get_params(const gm_ws* w, float* params, float* norm, void* stream);
+gm_status gm_ws_forward(gm_ws* w, const float* feat, int B, float* out, void* stream);
+gm_status gm_ws_train_step(gm_ws* w, const float* feat, const float* target, int B, float lr, float beta1,
+                           float beta2, float eps, float* loss, void* stream);
+gm_status gm_ws_grad(gm_ws* w, float* grad, void* stream);
+gm_status gm_ws_features(gm_ctx* ctx, const float* x_meas, const float* x_ref, float* feat, void* stream);
 
 /* ------------------------------------------------------------------------
  * gm_qp_solve_noalloc — the ADMM solve of gm_qp_solve for callers that

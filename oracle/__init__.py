@@ -19,11 +19,16 @@ speed:
                 then an equality-constrained solve on the identified active
                 set), the ADMM recurrence, KKT certificates, brute force over
                 active sets and the uncondensed (x, u) QP for tiny cases;
-* ``rti``       one iteration of Algorithm 1 assembled from the above.
+* ``rti``       one iteration of Algorithm 1 assembled from the above;
+* ``warmstart`` the learned ADMM warm start (an addition, not in the paper):
+                pooled GNN-latent features, the MLP, its loss gradient and
+                the Adam step.
 
 Pins (tests marked ``not gpu``): central finite differences, closed forms for
 identity-activation GNNs, the N=1 worked case of the Thm. 1 proof, recursion
 versus textbook condensing, the condensed cost versus a direct simulation of
 the linear system, the condensed QP versus the uncondensed QP, brute-force
-active sets, KKT certificates and Thm. 1's linear flop count.
+active sets, KKT certificates and Thm. 1's linear flop count; for the warm
+start, finite differences of the loss, the linear regime of the MLP, the first
+Adam step's sign property and pooling invariances.
 """

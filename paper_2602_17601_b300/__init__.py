@@ -108,6 +108,16 @@ def _load():
         "gm_ctx_set_graph": ([vp, C.c_int], C.c_int),
         "gm_ctx_graph_state": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "gm_ctx_set_kernel_timing": ([vp, C.c_int], C.c_int),
+        "gm_ws_workspace_size": ([C.c_int] * 4, C.c_size_t),
+        "gm_ws_create": ([C.c_int] * 4 + [vp, C.c_size_t, C.POINTER(vp)], C.c_int),
+        "gm_ws_destroy": ([vp], None),
+        "gm_ws_param_count": ([vp], C.c_longlong),
+        "gm_ws_set_params": ([vp, vp, vp, vp], C.c_int),
+        "gm_ws_get_params": ([vp, vp, vp, vp], C.c_int),
+        "gm_ws_forward": ([vp, vp, C.c_int, vp, vp], C.c_int),
+        "gm_ws_train_step": ([vp, vp, vp, C.c_int] + [C.c_float] * 4 + [vp, vp], C.c_int),
+        "gm_ws_grad": ([vp, vp, vp], C.c_int),
+        "gm_ws_features": ([vp, vp, vp, vp, vp], C.c_int),
         "gm_ctx_kernel_stats": ([vp, C.POINTER(C.c_int)] + [C.POINTER(C.c_double)] * 3, C.c_int),
         "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
@@ -125,7 +135,9 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_qp_solve", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
                     "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count", "gm_qp_solve_noalloc",
                     "gm_ctx_set_graph", "gm_ctx_graph_state", "gm_ctx_set_kernel_timing",
-                    "gm_ctx_kernel_stats")
+                    "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
+                    "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
+                    "gm_ws_train_step", "gm_ws_grad", "gm_ws_features")
 
 GM_NOALLOC_MAX_NU = 64
 GM_NOALLOC_MAX_ROWS = 8192

@@ -777,6 +777,15 @@ gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, con
     return rti_body(c, x_meas, cost, cons, U, u0, stats, st, false);
 }
 
+gm_status gm_ws_features(gm_ctx* ctx, const float* x_meas, const float* x_ref, float* feat, void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx && x_meas && x_ref && feat, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GM_TRY(gnn_latents(ctx, x_meas, ctx->d_u_hat, st));
+    GM_TRY(ws_features(ctx, ctx->d_h, x_ref, feat, st));
+    return GM_OK;
+}
+
 gm_status gm_ctx_set_graph(gm_ctx* ctx, int on) {
     clear_error();
     GM_CHECK_ARG(ctx, "ctx is NULL");

@@ -417,46 +417,58 @@ uint32_t* edge_mask(const gm_ctx* c, int k, int layer) {
     return c->d_mask_edge + ((long)(k * (c->K + 1) + layer) * c->E) * (c->W / 32);
 }
 
-// x_hat[0] = x0; x_hat[k+1] = F(x_hat[k], u_hat[k]); ReLU masks of every layer kept.
-gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat,
-                      cudaStream_t st) {
+// One stage of F: encoders and the K message-passing steps into c->d_h (node latents), then,
+// when xn is given, the decoder and the Euler update x_{k+1} = xn.  ReLU masks of stage k kept.
+static gm_status forward_stage(gm_ctx* c, int k, const float* xk, const float* uk, float* xn, cudaStream_t st) {
     const int M = c->M, E = c->E, W = c->W, K = c->K;
-    GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, st));
-    for (int k = 0; k < c->N; ++k) {
-        const float* xk = x_hat + (long)k * M * 6;
-        float* xn = x_hat + (long)(k + 1) * M * 6;
-        NodeEncFwd ne{};
-        fill_fwd(ne, c, 0, M, node_mask(c, k, 0));
-        ne.x = xk; ne.u = u_hat + (long)k * c->nu; ne.act = c->d_act; ne.h = c->d_h; ne.W = W; ne.nu = c->nu;
-        GM_TRY(launch_mlp(c, ne, tc_fwd(c, c->mlp[0]), st));
+    NodeEncFwd ne{};
+    fill_fwd(ne, c, 0, M, node_mask(c, k, 0));
+    ne.x = xk; ne.u = uk; ne.act = c->d_act; ne.h = c->d_h; ne.W = W; ne.nu = c->nu;
+    GM_TRY(launch_mlp(c, ne, tc_fwd(c, c->mlp[0]), st));
+    if (E > 0) {
+        EdgeEncFwd ee{};
+        fill_fwd(ee, c, 1, E, edge_mask(c, k, 0));
+        ee.x = xk; ee.src = c->d_src; ee.dst = c->d_dst; ee.e = c->d_e; ee.W = W;
+        GM_TRY(launch_mlp(c, ee, tc_fwd(c, c->mlp[1]), st));
+    }
+    for (int t = 0; t < K; ++t) {
         if (E > 0) {
-            EdgeEncFwd ee{};
-            fill_fwd(ee, c, 1, E, edge_mask(c, k, 0));
-            ee.x = xk; ee.src = c->d_src; ee.dst = c->d_dst; ee.e = c->d_e; ee.W = W;
-            GM_TRY(launch_mlp(c, ee, tc_fwd(c, c->mlp[1]), st));
+            EdgeMpFwd em{};
+            fill_fwd(em, c, 2 + 2 * t, E, edge_mask(c, k, 1 + t));
+            em.h = c->d_h; em.src = c->d_src; em.dst = c->d_dst; em.e = c->d_e; em.W = W;
+            GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * t]), st));
+            agg_kernel<<<cdiv((long)M * W, 256), 256, 0, st>>>(M, W, c->d_in_ptr, c->d_e, c->d_agg);
+            GM_LAUNCH_CHECK();
+        } else {
+            GM_CUDA_TRY(cudaMemsetAsync(c->d_agg, 0, sizeof(float) * M * W, st));
         }
-        for (int t = 0; t < K; ++t) {
-            if (E > 0) {
-                EdgeMpFwd em{};
-                fill_fwd(em, c, 2 + 2 * t, E, edge_mask(c, k, 1 + t));
-                em.h = c->d_h; em.src = c->d_src; em.dst = c->d_dst; em.e = c->d_e; em.W = W;
-                GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * t]), st));
-                agg_kernel<<<cdiv((long)M * W, 256), 256, 0, st>>>(M, W, c->d_in_ptr, c->d_e, c->d_agg);
-                GM_LAUNCH_CHECK();
-            } else {
-                GM_CUDA_TRY(cudaMemsetAsync(c->d_agg, 0, sizeof(float) * M * W, st));
-            }
-            NodeMpFwd nm{};
-            fill_fwd(nm, c, 3 + 2 * t, M, node_mask(c, k, 1 + t));
-            nm.h = c->d_h; nm.agg = c->d_agg; nm.W = W;
-            GM_TRY(launch_mlp(c, nm, tc_fwd(c, c->mlp[3 + 2 * t]), st));
-        }
+        NodeMpFwd nm{};
+        fill_fwd(nm, c, 3 + 2 * t, M, node_mask(c, k, 1 + t));
+        nm.h = c->d_h; nm.agg = c->d_agg; nm.W = W;
+        GM_TRY(launch_mlp(c, nm, tc_fwd(c, c->mlp[3 + 2 * t]), st));
+    }
+    if (xn) {
         DecFwd de{};
         fill_fwd(de, c, 2 + 2 * K, M, node_mask(c, k, K + 1));
         de.h = c->d_h; de.x = xk; de.xn = xn; de.dt = c->dt; de.W = W;
         GM_TRY(launch_mlp(c, de, tc_fwd(c, c->mlp[2 + 2 * K]), st));
     }
     return GM_OK;
+}
+
+// x_hat[0] = x0; x_hat[k+1] = F(x_hat[k], u_hat[k]); ReLU masks of every layer kept.
+gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, cudaStream_t st) {
+    const int M = c->M;
+    GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < c->N; ++k)
+        GM_TRY(forward_stage(c, k, x_hat + (long)k * M * 6, u_hat + (long)k * c->nu, x_hat + (long)(k + 1) * M * 6,
+                             st));
+    return GM_OK;
+}
+
+// Final node latents h^K of stage 0 at (x0, u0), left in c->d_h.
+gm_status gnn_latents(gm_ctx* c, const float* x0, const float* u0, cudaStream_t st) {
+    return forward_stage(c, 0, x0, u0, nullptr, st);
 }
 
 // ======================================================================= reverse ops

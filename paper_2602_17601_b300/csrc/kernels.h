@@ -36,6 +36,9 @@ gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, 
 __global__ void gram_kernel(GramRows R, int n, float* __restrict__ part);
 // Partial Gram sums over nsplit row shares into part [nsplit][T][T][32 x 32] (T = ceil(n/32));
 // gram_split picks nsplit (at most cap) for about two CTAs per SM.
+// Final node latents of stage 0 into c->d_h; their pooled features (warm start, ws.cu).
+gm_status gnn_latents(gm_ctx* c, const float* x0, const float* u0, cudaStream_t st);
+gm_status ws_features(gm_ctx* c, const float* h, const float* x_ref, float* feat, cudaStream_t st);
 int gram_blocks(int n);
 int gram_split(int n, int sms, int cap);
 gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStream_t st);
