@@ -174,16 +174,23 @@ def solve_with_fallback(prob, H, g, Ct, dt, warm, stats):
 
 
 def evaluate(prob, net, instances):
-    """Held-out comparison at the context's tolerance: iterations and device time of
-    (features + net + warm ADMM) against cold ADMM, per instance, on the same H, g."""
+    """Held-out comparison at the context's tolerance on the same H, g: iterations and device
+    time of cold ADMM against features + net inference + warm-started ADMM (plus the cold
+    solve when the warm one does not converge)."""
+    from . import gm_qp_solve
     t = prob.torch
     nU, F = prob.nU, features_size(prob)
     feat = t.empty(F, dtype=t.float32, device="cuda")
-    stats = t.empty(STATS_BYTES, dtype=t.uint8, device="cuda")
+    sc_t = t.empty(STATS_BYTES, dtype=t.uint8, device="cuda")
+    sw_t = t.empty(STATS_BYTES, dtype=t.uint8, device="cuda")
     x_dev = t.empty(prob.M * 6, dtype=t.float32, device="cuda")
     zeros_u = t.zeros(prob.N, prob.nu, dtype=t.float32, device="cuda")
-    ev = [t.cuda.Event(enable_timing=True) for _ in range(4)]
-    from . import gm_qp_solve
+    y0 = t.zeros(nU + prob.rows_c, dtype=t.float32, device="cuda")
+    Uc = t.empty(nU, dtype=t.float32, device="cuda")
+    Uw = t.empty(nU, dtype=t.float32, device="cuda")
+    ev = [t.cuda.Event(enable_timing=True) for _ in range(7)]
+    ct = lambda: Ct if prob.n_c else None  # noqa: E731
+    dtt = lambda: dt if prob.n_c else None  # noqa: E731
     rows = []
     for x0, x_ref in instances:
         x_dev.copy_(t.as_tensor(np.asarray(x0, np.float32).reshape(-1)))
@@ -191,24 +198,33 @@ def evaluate(prob, net, instances):
         prob.reset()
         x_hat, A, B, c = prob.linearize(x_dev, zeros_u)
         H, g, Ct, dt = prob.condense(x_hat, A, B, c)
-        Uc = t.empty(nU, dtype=t.float32, device="cuda")
         ev[0].record()
-        gm_qp_solve(prob.ctx, H, g, Ct if prob.n_c else None, dt if prob.n_c else None, prob.u_lo, prob.u_hi,
-                    Uc, None, stats, None, None)
+        gm_qp_solve(prob.ctx, H, g, ct(), dtt(), prob.u_lo, prob.u_hi, Uc, None, sc_t, None, None)
         ev[1].record()
-        t.cuda.synchronize()
-        sc = read_stats(stats)
         prob.reset()
         ev[2].record()
         features(prob, x_dev, prob.x_ref, feat)
         warm = net.forward(feat.view(1, F)).view(-1)
-        Uw, fell_back = solve_with_fallback(prob, H, g, Ct, dt, warm, stats)
+        y0[:nU].copy_(warm[nU:])
         ev[3].record()
+        gm_qp_solve(prob.ctx, H, g, ct(), dtt(), prob.u_lo, prob.u_hi, Uw, None, sw_t, warm[:nU].contiguous(), y0)
+        ev[4].record()
         t.cuda.synchronize()
-        sw = read_stats(stats)
+        sc, sw = read_stats(sc_t), read_stats(sw_t)
+        fallback_ms, fell_back = 0.0, False
+        if not sw["converged"]:
+            fell_back = True
+            ev[5].record()
+            gm_qp_solve(prob.ctx, H, g, ct(), dtt(), prob.u_lo, prob.u_hi, Uw, None, sw_t, None, None)
+            ev[6].record()
+            t.cuda.synchronize()
+            fallback_ms = ev[5].elapsed_time(ev[6])
+            sw = read_stats(sw_t)
+        net_ms, solve_ms = ev[2].elapsed_time(ev[3]), ev[3].elapsed_time(ev[4])
         rows.append(dict(cold_iters=sc["iters"], warm_iters=sw["iters"], cold_ms=ev[0].elapsed_time(ev[1]),
-                         warm_ms=ev[2].elapsed_time(ev[3]), fallback=fell_back,
-                         du=float((Uw - Uc).abs().max().item()), pred_err=float((warm[:nU] - Uc).abs().max().item()),
+                         warm_ms=net_ms + solve_ms + fallback_ms, net_ms=net_ms, warm_solve_ms=solve_ms,
+                         fallback=fell_back, du=float((Uw - Uc).abs().max().item()),
+                         pred_err=float((warm[:nU] - Uc).abs().max().item()),
                          cold_ok=sc["converged"], warm_ok=sw["converged"]))
     return rows
 
@@ -220,6 +236,7 @@ def summarise(rows):
             "cold_iters_median": float(np.median(f("cold_iters"))),
             "warm_iters_median": float(np.median(f("warm_iters"))),
             "cold_ms_mean": float(f("cold_ms").mean()), "warm_ms_mean": float(f("warm_ms").mean()),
+            "warm_net_ms_mean": float(f("net_ms").mean()), "warm_solve_ms_mean": float(f("warm_solve_ms").mean()),
             "fallbacks": int(f("fallback").sum()), "max_du": float(f("du").max()),
             "pred_err_mean": float(f("pred_err").mean()),
             "all_converged": bool(f("cold_ok").all() and f("warm_ok").all())}
@@ -229,3 +246,57 @@ def timed(fn):
     t0 = time.perf_counter()
     out = fn()
     return out, time.perf_counter() - t0
+
+
+def cfg5_instances(n, first_seed=10**6, **kw):
+    """(x0, x_ref) of n chain-of-10 instances: seeds first_seed + s for the state and the
+    reference, the GNN and graph of seed 0 (the chain of 10 workload)."""
+    from synth import small_chain
+    out = []
+    for s in range(n):
+        w = small_chain(seed=first_seed + s, w_seed=0, **kw)
+        out.append((w.x0, w.x_ref))
+    return out
+
+
+def main(argv=None):
+    """Train and evaluate the warm start on chain-of-10 instances (90/10 split); print a JSON report."""
+    import argparse
+    import json
+
+    import torch
+
+    from synth import small_chain
+    from .rti import RTIProblem
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=100000)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--hidden", type=int, default=512)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval", type=int, default=2000, help="held-out instances timed (of the 10%%)")
+    a = ap.parse_args(argv)
+    wl = small_chain(tol=a.tol)
+    prob = RTIProblem.from_workload(wl)
+    inst, t_inst = timed(lambda: cfg5_instances(a.n))
+    n_train = int(0.9 * a.n)
+    (feat, target, iters), t_gen = timed(lambda: generate(prob, inst[:n_train]))
+    net = WarmStartNet(feat.shape[1], target.shape[1], n_hidden=a.hidden, max_batch=max(a.batch, 1))
+    hist, t_fit = timed(lambda: fit(net, feat, target, epochs=a.epochs, batch=a.batch, lr=a.lr))
+    held = inst[n_train:][:a.eval]
+    rows, t_eval = timed(lambda: evaluate(prob, net, held))
+    rep = {"workload": "chain10_K2_W32_N10_nu4 (GNN of seed 0; state and reference from seeds 1e6 + s)",
+           "tol": a.tol, "instances": a.n, "train": n_train, "held_out_timed": len(held),
+           "net": f"{feat.shape[1]} -> {a.hidden} -> {a.hidden} -> {target.shape[1]}",
+           "epochs": a.epochs, "batch": a.batch, "lr": a.lr,
+           "train_cold_iters_mean": float(iters.mean()), "loss_first_last": [hist[0], hist[-1]],
+           "held_out": summarise(rows),
+           "seconds": {"instances": t_inst, "generate": t_gen, "fit": t_fit, "evaluate": t_eval},
+           "device": torch.cuda.get_device_name()}
+    print(json.dumps(rep), flush=True)
+    return rep
+
+
+if __name__ == "__main__":
+    main()
