@@ -128,6 +128,11 @@ void gm_gnn_destroy(gm_gnn* m);
  *              each relative to its scale, and re-factor P with
  *              rho sqrt(ratio) (clamped to [1e-6, 1e6]) when that changes rho
  *              by more than 5x, at most 5 times per solve; 0: fixed rho.
+ *   admm_grid    CTAs of the cooperative ADMM kernel (0: one per resident slot
+ *                on every SM); smaller grids let batched instances run side by side
+ *   factor_grid  CTAs of the cooperative FP64 factor kernel (0: 128)
+ *   chunk_mb     device memory budget of the reverse-pass cotangent buffers in
+ *                MB (0: 2048); fewer stages per launch group when smaller
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N;
@@ -140,6 +145,9 @@ typedef struct {
     int timeout_spins;
     int scale_rows;
     int adapt_rho;
+    int admm_grid;
+    int factor_grid;
+    int chunk_mb;
 } gm_settings;
 
 /* Per-solve statistics, written to DEVICE memory by the QP calls. */
@@ -325,6 +333,26 @@ unsigned long long gm_launch_count(void);
  * gm_ctx_graph_state reports 0.  gm_ctx_graph_state: 1 when the last step
  * replayed a graph, 0 otherwise; captures counts the captures so far. */
 gm_status gm_ctx_set_graph(gm_ctx* ctx, int on);
+
+/* Batched real-time iterations (no paper counterpart: many independent MPC
+ * instances on one GPU).  A batch holds n contexts of any sizes (node count,
+ * horizon, inputs, GNN); gm_batch_rti_step runs gm_rti_step on every instance
+ * i with (x_meas[i], costs[i], cons[i], U[i], stats[i]).  The first call runs
+ * the instances one after another with plain launches; the next captures
+ * every instance's step as a child graph of one parent graph with no
+ * dependencies between instances, and every later call with the same
+ * arguments replays that graph with a single launch on the stream, the
+ * instances' kernels running side by side.  Changing any argument captures
+ * anew.  x_meas, U, stats: host arrays of n device pointers (stats may be
+ * NULL); costs, cons: host arrays of n structs.  Contexts of a batch must not
+ * be stepped elsewhere while the batch runs.  gm_batch_state: as
+ * gm_ctx_graph_state. */
+typedef struct gm_batch gm_batch;
+gm_status gm_batch_create(gm_ctx* const* ctxs, int n, gm_batch** out);
+void gm_batch_destroy(gm_batch* b);
+gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_cost* costs, const gm_constr* cons,
+                            float* const* U, gm_stats* const* stats, void* stream);
+gm_status gm_batch_state(const gm_batch* b, int* replayed, int* captures);
 gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures);
 
 /* Launch timing of the dominant kernel, the reverse edge-update MLP (one launch per

@@ -38,7 +38,8 @@ class GnnDesc(C.Structure):
 class Settings(C.Structure):
     _fields_ = [("N", C.c_int), ("n_c", C.c_int), ("precision", C.c_int), ("rho", C.c_float),
                 ("tol", C.c_float), ("max_iter", C.c_int), ("polish", C.c_int),
-                ("timeout_spins", C.c_int), ("scale_rows", C.c_int), ("adapt_rho", C.c_int)]
+                ("timeout_spins", C.c_int), ("scale_rows", C.c_int), ("adapt_rho", C.c_int),
+                ("admm_grid", C.c_int), ("factor_grid", C.c_int), ("chunk_mb", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -118,6 +119,10 @@ def _load():
         "gm_ws_train_step": ([vp, vp, vp, C.c_int] + [C.c_float] * 4 + [vp, vp], C.c_int),
         "gm_ws_grad": ([vp, vp, vp], C.c_int),
         "gm_ws_features": ([vp, vp, vp, vp, vp], C.c_int),
+        "gm_batch_create": ([C.POINTER(vp), C.c_int, C.POINTER(vp)], C.c_int),
+        "gm_batch_destroy": ([vp], None),
+        "gm_batch_rti_step": ([vp, C.POINTER(vp), vp, vp, C.POINTER(vp), C.POINTER(vp), vp], C.c_int),
+        "gm_batch_state": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "gm_ctx_kernel_stats": ([vp, C.POINTER(C.c_int)] + [C.POINTER(C.c_double)] * 3, C.c_int),
         "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
@@ -137,7 +142,8 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_ctx_set_graph", "gm_ctx_graph_state", "gm_ctx_set_kernel_timing",
                     "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
-                    "gm_ws_train_step", "gm_ws_grad", "gm_ws_features")
+                    "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
+                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state")
 
 GM_NOALLOC_MAX_NU = 64
 GM_NOALLOC_MAX_ROWS = 8192
@@ -266,9 +272,10 @@ def gm_gnn_destroy(m):
 
 
 def make_settings(N, n_c=0, precision=GM_PREC_FP32, rho=0.1, tol=1e-6, max_iter=4000, polish=0,
-                  timeout_spins=0, scale_rows=1, adapt_rho=1):
+                  timeout_spins=0, scale_rows=1, adapt_rho=1, admm_grid=0, factor_grid=0, chunk_mb=0):
     return Settings(int(N), int(n_c), int(precision), float(rho), float(tol), int(max_iter), int(polish),
-                    int(timeout_spins), int(scale_rows), int(adapt_rho))
+                    int(timeout_spins), int(scale_rows), int(adapt_rho), int(admm_grid), int(factor_grid),
+                    int(chunk_mb))
 
 
 def gm_ctx_workspace_size(graph, gnn, settings):

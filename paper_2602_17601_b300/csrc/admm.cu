@@ -552,7 +552,7 @@ gm_status admm_solve(const AdmmPlan& p) {
     for (int r = 0; r < p.rounds; ++r) {
         admm_form_p_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, p.H, p.Gram, p.S, p.P);
         GM_LAUNCH_CHECK();
-        GM_TRY(factor_pinv(n, p.P, p.L, p.Linv, p.Pinv, p.status, p.S, p.bar, p.max_spins, st));
+        GM_TRY(factor_pinv(n, p.P, p.L, p.Linv, p.Pinv, p.status, p.S, p.bar, p.max_spins, p.factor_grid, st));
         if (r == 0 && p.ev_mid) GM_CUDA_TRY(cudaEventRecord(p.ev_mid, st));
         GM_CUDA_TRY(cudaMemsetAsync(p.bar, 0, sizeof(unsigned) * 4, st));
         GM_CUDA_TRY(cudaMemsetAsync(p.acc, 0, sizeof(float) * (2 * n + 4), st));

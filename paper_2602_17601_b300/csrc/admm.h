@@ -58,6 +58,7 @@ struct AdmmPlan {
     gm_stats* stats;
     float rho0, tol;
     int max_iter, adapt_every, rounds, grid;
+    int factor_grid;       // CTAs of the factor kernel (0: default)
     long long max_spins;
     cudaStream_t st;
     cudaEvent_t ev_mid;    // recorded after the first factorisation (nullable)
@@ -72,6 +73,6 @@ const void* admm2_kernel_ptr(int n);
 // factor_pad(n)^2 doubles; bar[0] is used (and reset) as the grid barrier counter.
 int factor_pad(int n);
 gm_status factor_pinv(int n, const float* P, double* L, double* Linv, float* Pinv, int* status,
-                      const AdmmState* gate, unsigned* bar, long long max_spins, cudaStream_t st);
+                      const AdmmState* gate, unsigned* bar, long long max_spins, int grid, cudaStream_t st);
 
 }  // namespace gmi

@@ -270,7 +270,8 @@ static void plan(gm_ctx* c, Carver& cv) {
     const long RE = (long)C.er_edge[K - 1].size();
     // stages per reverse chunk: keep the per-chunk buffers near 2 GB
     const long per_stage = 4L * (2 * RK * 3 * W + 2 * RK1 * 3 * W + 3 * RE * 3 * W + RK * 3 * (6 + nu) + RE * 18);
-    c->stage_chunk = (int)std::max(1L, std::min((long)N, (2L << 30) / std::max(1L, per_stage)));
+    const long budget = c->s.chunk_mb > 0 ? (long)c->s.chunk_mb << 20 : (2L << 30);
+    c->stage_chunk = (int)std::max(1L, std::min((long)N, budget / std::max(1L, per_stage)));
     const long Ns = c->stage_chunk;
     std::vector<float> wdummy;
     c->d_src = cv.take<int>(std::max(E, 1));
@@ -418,6 +419,8 @@ static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* 
     GM_CHECK_ARG(s->precision == GM_PREC_FP32 || s->precision == GM_PREC_MIXED || s->precision == GM_PREC_BF16,
                  "unknown precision %d", s->precision);
     GM_CHECK_ARG(s->rho > 0.f && s->tol > 0.f && s->max_iter >= 1, "rho, tol must be > 0 and max_iter >= 1");
+    GM_CHECK_ARG(s->admm_grid >= 0 && s->factor_grid >= 0 && s->chunk_mb >= 0,
+                 "admm_grid, factor_grid and chunk_mb must be >= 0");
     GM_CHECK_ARG((long)s->N * g->nu <= 256, "N * nu must be <= 256 (got %d)", s->N * g->nu);
     c->s = *s;
     c->M = g->M; c->E = g->E; c->nu = g->nu; c->K = m->d.K; c->W = m->d.W; c->N = s->N;
@@ -523,6 +526,7 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
         }
         occ = std::max(occ, 1);
         long want = c->rows_c > 0 ? std::max(1L, std::min((long)occ * c->num_sms, c->rows_c / 16)) : 1;
+        if (c->s.admm_grid > 0) want = std::min<long>(want, c->s.admm_grid);
         c->admm_grid = (int)std::min<long>(want, kMaxAdmmGrid);
         // every upload above reads host vectors that must outlive the copies
     }
@@ -735,6 +739,25 @@ static std::vector<uintptr_t> graph_key(const gm_ctx* c, const float* x_meas, co
     return k;
 }
 
+// One step of c with these arguments captured into a graph on c's internal stream.
+static gm_status capture_step(gm_ctx* c, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
+                              float* u0, gm_stats* stats, cudaGraph_t* out) {
+    *out = nullptr;
+    if (!c->cap_stream) GM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    GM_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+    const gm_status body = rti_body(c, x_meas, cost, cons, U, u0, stats, c->cap_stream, false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+    if (body != GM_OK || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        if (body == GM_OK) set_error("stream capture failed: %s", cudaGetErrorString(ce));
+        return body != GM_OK ? body : GM_ERR_CUDA;
+    }
+    *out = g;
+    return GM_OK;
+}
+
 gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
                       float* u0, gm_stats* stats, void* stream) {
     clear_error();
@@ -753,14 +776,9 @@ gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, con
     }
     if (c->graph_eager++ == 0) return rti_body(c, x_meas, cost, cons, U, u0, stats, st, false);
     // capture on an internal stream (the caller's may be the legacy default stream), replay on st
-    if (!c->cap_stream) GM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-    GM_CUDA_TRY(cudaStreamSynchronize(st));
-    GM_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
-    const gm_status body = rti_body(c, x_meas, cost, cons, U, u0, stats, c->cap_stream, false);
     cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
     cudaGraphExec_t exec = nullptr;
-    if (body == GM_OK && ce == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+    if (capture_step(c, x_meas, cost, cons, U, u0, stats, &g) == GM_OK && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
         cudaGraphDestroy(g);
         if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = exec;
@@ -783,6 +801,89 @@ gm_status gm_ws_features(gm_ctx* ctx, const float* x_meas, const float* x_ref, f
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     GM_TRY(gnn_latents(ctx, x_meas, ctx->d_u_hat, st));
     GM_TRY(ws_features(ctx, ctx->d_h, x_ref, feat, st));
+    return GM_OK;
+}
+
+gm_status gm_batch_create(gm_ctx* const* ctxs, int n, gm_batch** out) {
+    clear_error();
+    GM_CHECK_ARG(ctxs && out && n >= 1, "NULL argument or empty batch");
+    for (int i = 0; i < n; ++i) {
+        GM_CHECK_ARG(ctxs[i], "ctxs[%d] is NULL", i);
+        for (int j = 0; j < i; ++j) GM_CHECK_ARG(ctxs[j] != ctxs[i], "ctxs[%d] repeats ctxs[%d]", i, j);
+    }
+    gm_batch* b = new gm_batch;
+    b->ctx.assign(ctxs, ctxs + n);
+    *out = b;
+    return GM_OK;
+}
+
+void gm_batch_destroy(gm_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
+}
+
+gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_cost* costs, const gm_constr* cons,
+                            float* const* U, gm_stats* const* stats, void* stream) {
+    clear_error();
+    GM_CHECK_ARG(b && x_meas && costs && cons && U, "NULL argument");
+    const int n = (int)b->ctx.size();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<uintptr_t> key;
+    for (int i = 0; i < n; ++i) {
+        GM_CHECK_ARG(x_meas[i] && U[i], "instance %d: NULL argument", i);
+        GM_TRY(check_cost(b->ctx[i], &costs[i], &cons[i]));
+        auto k = graph_key(b->ctx[i], x_meas[i], &costs[i], &cons[i], U[i], nullptr, stats ? stats[i] : nullptr);
+        key.insert(key.end(), k.begin(), k.end());
+    }
+    b->replayed = false;
+    if (b->exec && key == b->key) {
+        GM_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+        b->replayed = true;
+        return GM_OK;
+    }
+    if (b->eager++ == 0) {        // first call: plain launches (one-time kernel attributes, cone uploads)
+        for (int i = 0; i < n; ++i)
+            GM_TRY(rti_body(b->ctx[i], x_meas[i], &costs[i], &cons[i], U[i], nullptr, stats ? stats[i] : nullptr,
+                            st, false));
+        return GM_OK;
+    }
+    // every instance's step as a child graph of one parent, no edges between instances
+    cudaGraph_t parent = nullptr;
+    GM_CUDA_TRY(cudaGraphCreate(&parent, 0));
+    gm_status r = GM_OK;
+    for (int i = 0; i < n && r == GM_OK; ++i) {
+        cudaGraph_t g = nullptr;
+        r = capture_step(b->ctx[i], x_meas[i], &costs[i], &cons[i], U[i], nullptr, stats ? stats[i] : nullptr, &g);
+        if (r != GM_OK) break;
+        cudaGraphNode_t node;
+        if (cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, g) != cudaSuccess) {
+            set_error("adding instance %d to the batch graph failed", i);
+            r = GM_ERR_CUDA;
+        }
+        cudaGraphDestroy(g);           // the child node holds its own copy
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (r == GM_OK && cudaGraphInstantiate(&exec, parent, 0) != cudaSuccess) {
+        set_error("batch graph instantiation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        r = GM_ERR_CUDA;
+    }
+    cudaGraphDestroy(parent);
+    if (r != GM_OK) return r;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = exec;
+    b->key = std::move(key);
+    ++b->captures;
+    GM_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    b->replayed = true;
+    return GM_OK;
+}
+
+gm_status gm_batch_state(const gm_batch* b, int* replayed, int* captures) {
+    clear_error();
+    GM_CHECK_ARG(b, "batch is NULL");
+    if (replayed) *replayed = b->replayed ? 1 : 0;
+    if (captures) *captures = b->captures;
     return GM_OK;
 }
 

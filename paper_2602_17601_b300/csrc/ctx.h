@@ -17,6 +17,17 @@ struct gm_gnn {
     std::vector<float> blob;
 };
 
+struct gm_ctx;
+
+// A batch of contexts stepped as one CUDA graph (gm_batch_rti_step).
+struct gm_batch {
+    std::vector<gm_ctx*> ctx;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uintptr_t> key;
+    int eager = 0, captures = 0;
+    bool replayed = false;
+};
+
 namespace gmi {
 
 struct AdmmState;

@@ -244,11 +244,12 @@ int factor_grid() {
 }
 
 gm_status factor_pinv(int n, const float* P, double* L, double* Linv, float* Pinv, int* status,
-                      const AdmmState* gate, unsigned* bar, long long max_spins, cudaStream_t st) {
+                      const AdmmState* gate, unsigned* bar, long long max_spins, int grid, cudaStream_t st) {
     const int np = factor_pad(n);
     GM_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(factor_grid());
+    // at least 2 CTAs: the trailing update runs on the CTAs other than CTA 0
+    cfg.gridDim = dim3(grid > 0 ? std::max(2, std::min(grid, factor_grid())) : factor_grid());
     cfg.blockDim = dim3(FT);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;

@@ -188,6 +188,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     p.adapt_every = c->s.adapt_rho ? 25 : 0;
     p.rounds = c->s.adapt_rho ? 6 : 1;
     p.grid = c->admm_grid;
+    p.factor_grid = c->s.factor_grid;
     p.max_spins = c->s.timeout_spins > 0 ? c->s.timeout_spins : (1LL << 26);
     p.st = st;
     p.ev_mid = ev_mid;
