@@ -29,7 +29,7 @@ __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 // Factor the FB x FB block S (row-major, lower part valid) in place with all threads of
 // the CTA: S <- L_kk, written to L at block (k, k), and rd[j] = 1 / L_kk[j][j].  A
 // non-positive pivot sets GM_ERR_NUMERIC and continues with 1.
-__device__ void factor_diag(double (*S)[FB + 1], double* rd, int k, int np, double* L, int* status) {
+__device__ void factor_diag(double (*S)[FB + 1], double* rd, int k, int np, double* L, double* Linv, int* status) {
     const int tid = threadIdx.x;
     for (int j = 0; j < FB; ++j) {
         if (tid == 0) {
@@ -38,9 +38,9 @@ __device__ void factor_diag(double (*S)[FB + 1], double* rd, int k, int np, doub
                 dev_fail(status, GM_ERR_NUMERIC);
                 d = 1.0;
             }
-            d = sqrt(d);
-            S[j][j] = d;
-            rd[j] = 1.0 / d;
+            const double r = rsqrt(d);
+            S[j][j] = d * r;
+            rd[j] = r;
         }
         __syncthreads();
         if (tid > j && tid < FB) S[tid][j] *= rd[j];
@@ -62,6 +62,9 @@ __device__ void factor_diag(double (*S)[FB + 1], double* rd, int k, int np, doub
         const int r = e / FB, c = e % FB;
         L[(long)(k * FB + r) * np + k * FB + c] = c <= r ? S[r][c] : 0.0;
     }
+    // the pivot reciprocals, parked on the diagonal of Linv for the panel phase (the
+    // diagonal-block inverses overwrite them later)
+    if (tid < FB) Linv[(long)(k * FB + tid) * np + k * FB + tid] = rd[tid];
     __syncthreads();
 }
 
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
     if (b == 0) {
         for (int e = tid; e < FB * FB; e += FT) S[e / FB][e % FB] = ldcg(&L[(long)(e / FB) * np + e % FB]);
         __syncthreads();
-        factor_diag(S, rd, 0, np, L, status);
+        factor_diag(S, rd, 0, np, L, Linv, status);
     }
     for (int k = 0; k < nb; ++k) {
         sync();                                  // L_kk and D_k final
@@ -105,18 +108,18 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
         const int k0 = k * FB, r0 = k0 + FB;
         // ---- panel: L_ik = A_ik L_kk^{-T}, row by row (forward substitution, one thread per row)
         if (tid < FB * FB) Dm[tid / FB][tid % FB] = ldcg(&L[(long)(k0 + tid / FB) * np + k0 + tid % FB]);
-        if (tid < FB) rd[tid] = 1.0 / ldcg(&L[(long)(k0 + tid) * np + k0 + tid]);
+        if (tid < FB) rd[tid] = ldcg(&Linv[(long)(k0 + tid) * np + k0 + tid]);
         __syncthreads();
         for (int r = r0 + b + G * tid; r < np; r += G * FT) {
             double x[FB];
 #pragma unroll
             for (int c = 0; c < FB; ++c) x[c] = ldcg(&L[(long)r * np + k0 + c]);
+            // right-looking: once x_c is final it updates all later entries (independent FMAs)
 #pragma unroll
             for (int c = 0; c < FB; ++c) {
-                double v = x[c];
+                x[c] *= rd[c];
 #pragma unroll
-                for (int q = 0; q < c; ++q) v -= x[q] * Dm[c][q];
-                x[c] = v * rd[c];
+                for (int q = c + 1; q < FB; ++q) x[q] -= x[c] * Dm[q][c];
             }
 #pragma unroll
             for (int c = 0; c < FB; ++c) L[(long)r * np + k0 + c] = x[c];
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
                 }
             }
             __syncthreads();
-            factor_diag(S, rd, k + 1, np, L, status);
+            factor_diag(S, rd, k + 1, np, L, Linv, status);
         } else {
             // entries (r, c), r0 <= c <= r < np, outside the next diagonal block, dealt over CTAs 1..G-1
             const long ntri = (long)m * (m + 1) / 2;

@@ -404,6 +404,19 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     const unsigned tD = tmem_base;
     bool ok = true;
     unsigned phase = 0;
+    constexpr int CSTEP = 32 * (TC_T / 128);
+    const int lrow = (warp & 3) * 32 + lane;
+    const int cgrp = warp >> 2;
+    // reverse mode: the ReLU mask words of this thread's row and column blocks, fetched under GEMM1
+    constexpr int NMW = (W + CSTEP - 1) / CSTEP;
+    uint32_t mwv[NMW];
+    if constexpr (Op::kMode == 1) {
+#pragma unroll
+        for (int q = 0; q < NMW; ++q) {
+            const int c0 = cgrp * 32 + q * CSTEP;
+            mwv[q] = (c0 < W && row0 + lrow < rows) ? op.mask_word(rc[lrow], c0 >> 5) : 0u;
+        }
+    }
 
     // thread 0: wait for the staged B chunk, issue the chunk's MMAs, commit them to mbar (the
     // commit arrives even when nothing was issued, so the other threads never wait in vain)
@@ -448,9 +461,6 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
 
     // ---------------- hidden layer / single-product epilogue; 32-column blocks rotate
     // over the warp groups; TMEM lane = tile row (warp w reads lanes 32 (w % 4) ..)
-    constexpr int CSTEP = 32 * (TC_T / 128);
-    const int lrow = (warp & 3) * 32 + lane;
-    const int cgrp = warp >> 2;
     const bool valid = ok && (row0 + lrow < rows);
     const unsigned lane_off = (unsigned)((warp & 3) * 32) << 16;
     if (kSingle) {
@@ -478,7 +488,7 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
                 }
                 if (valid) op.store_mask(rc[lrow], c0 >> 5, bits);
             } else {
-                const uint32_t mw = valid ? op.mask_word(rc[lrow], c0 >> 5) : 0u;
+                const uint32_t mw = valid ? mwv[(c0 - cgrp * 32) / CSTEP] : 0u;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = ((mw >> j) & 1u) ? v[j] : 0.f;
                 if constexpr (Op::kStoreHid) {
