@@ -319,6 +319,45 @@ __device__ __forceinline__ void tc_stage_a(const Op& op, const RowCtx* rc, long 
     }
 }
 
+// A full chunk in registers: vectors tid + i TC_T (i < IT) of 8 inputs each.
+template <int KC>
+struct TcAReg {
+    static constexpr int IT = TC_M * (KC / 8) / TC_T;
+    float x[IT][8];
+};
+
+// Load a full chunk (K [k0, k0 + KC)) of the op's input rows into registers.
+template <int KC, class Op>
+__device__ __forceinline__ void tc_load_a_full(const Op& op, const RowCtx* rc, long row0, long rows, int k0,
+                                               int tid, TcAReg<KC>& a) {
+#pragma unroll
+    for (int i = 0; i < TcAReg<KC>::IT; ++i) {
+        int m, kv;
+        tc_vec_rc(tid + i * TC_T, KC / 8, m, kv);
+        if (row0 + m < rows) {
+            tc_load8(op, rc[m], k0 + kv * 8, a.x[i]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a.x[i][j] = 0.f;
+        }
+    }
+}
+
+// Split a register-held chunk into P BF16 pieces in the core-matrix layout.
+template <int P, int KC>
+__device__ __forceinline__ void tc_store_a_full(unsigned char* sA, int a_piece, int tid, const TcAReg<KC>& a) {
+#pragma unroll
+    for (int i = 0; i < TcAReg<KC>::IT; ++i) {
+        int m, kv;
+        tc_vec_rc(tid + i * TC_T, KC / 8, m, kv);
+        uint4 pc[P];
+        pack8<P>(a.x[i], pc);
+        const int o = tc_off(m, kv * 8, KC);
+#pragma unroll
+        for (int p = 0; p < P; ++p) *reinterpret_cast<uint4*>(sA + p * a_piece + o) = pc[p];
+    }
+}
+
 // MMAs of one staged chunk: D (+)= sum over piece pairs (i, j) with i + j < P of A_i . B_j^T
 // (1, 3 or 6 products; the dropped pairs are below the last kept piece's rounding).
 template <int P>
@@ -434,16 +473,23 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
         return okb;
     };
 
-    // ---------------- GEMM1 over K chunks
+    // ---------------- GEMM1 over K chunks; a full chunk's inputs are loaded into registers one
+    // chunk ahead, under the previous chunk's MMAs (not for the gather-sum inputs of the
+    // single-product form, whose variable-length loops measured slower that way)
+    constexpr bool kAhead = !kSingle;
+    TcAReg<KC> xa;
+    if (kAhead && nch > 0 && KC <= w.K1p) tc_load_a_full<KC>(op, rc, row0, rows, 0, tid, xa);
     for (int c = 0; c < nch; ++c) {
         const int k0 = c * KC;
         const int kc = min(KC, w.K1p - k0);        // multiple of 16
-        tc_stage_a<P, KC>(op, rc, row0, rows, sA, A_BYTES, k0, kc, tid);
+        if (kAhead && kc == KC) tc_store_a_full<P, KC>(sA, A_BYTES, tid, xa);
+        else tc_stage_a<P, KC>(op, rc, row0, rows, sA, A_BYTES, k0, kc, tid);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (tid == 0) ok = issue(smem_u32(sA), A_BYTES, KC * 16, kc * 16, kc, W, c == 0) && ok;
+        if (kAhead && k0 + 2 * KC <= w.K1p) tc_load_a_full<KC>(op, rc, row0, rows, k0 + KC, tid, xa);
         ok = tc_wait(&mbar, phase & 1, w.status) && ok;   // A and B buffers are free again
         ++phase;
         if (tid == 0 && ok && !b_pending) {
