@@ -38,6 +38,13 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// wait until at most k (< 4) of this thread's most recent cp.async groups are pending
+__device__ __forceinline__ void cp_async_wait_le(int k) {
+    if (k <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    else if (k == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else if (k == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else asm volatile("cp.async.wait_group 3;" ::: "memory");
+}
 
 __device__ __forceinline__ float wsum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -115,12 +122,18 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
     float* sacc = p;        p += 2 * n;                       // block sums of s C~'z, s C~'y
     float* wred = p;        p += 4 * NW;
     p = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
-    float* tbuf[2];
-    tbuf[0] = p;            p += a.tile_floats;
-    tbuf[1] = p;            p += a.tile_floats;
-    float* rstate[2];                                         // per tile: y, z, d, s (tile_rows each)
-    rstate[0] = p;          p += 4 * a.tile_rows;
-    rstate[1] = p;          p += 4 * a.tile_rows;
+    // NB tile buffers: C~ rows staged NB - 1 tiles ahead of the one being processed
+    constexpr int NB = PSMEM ? 2 : 3;
+    float* tbuf[NB];
+    for (int q = 0; q < NB; ++q) {
+        tbuf[q] = p;
+        p += a.tile_floats;
+    }
+    float* rstate[NB];                                        // per tile: y, z, d, s (tile_rows each)
+    for (int q = 0; q < NB; ++q) {
+        rstate[q] = p;
+        p += 4 * a.tile_rows;
+    }
     float* wz = p;          p += a.tile_rows;                 // s z_r and s y_r of the current tile
     float* wy = p;          p += a.tile_rows;
     __shared__ float s_misc[8];
@@ -134,6 +147,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
     const unsigned G = gridDim.x;
     const int stride = 2 * n + 4;
     float rho = S->rho;
+    const float inv_rho = 1.f / rho;
     const bool first = !S->started;
     int it = S->iters;
     for (int c = tid; c < n; c += ADMM_T) {
@@ -184,25 +198,26 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             cp_async_commit();
         };
         long rnext = r0;
-        Tile cur{}, nxt{};
-        bool have = rnext < r1;
-        if (have) {
-            cur = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows);
-            rnext = cur.t0 + cur.tr;
-            issue(cur, 0);
+        Tile q[NB];
+        int head = 0, nq = 0;                                  // tiles in flight: slots head .. head+nq-1
+        for (int k = 0; k < NB - 1 && rnext < r1; ++k) {
+            q[k] = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows);
+            rnext = q[k].t0 + q[k].tr;
+            issue(q[k], k);
+            ++nq;
         }
-        int b = 0;
-        while (have) {
-            const bool more = rnext < r1;
-            if (more) {
-                nxt = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows);
-                rnext = nxt.t0 + nxt.tr;
-                issue(nxt, b ^ 1);
-                cp_async_wait_1();
-            } else {
-                cp_async_wait_0();
+        while (nq > 0) {
+            if (rnext < r1 && nq < NB) {
+                const int sl = (head + nq) % NB;
+                q[sl] = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows);
+                rnext = q[sl].t0 + q[sl].tr;
+                issue(q[sl], sl);
+                ++nq;
             }
+            cp_async_wait_le(nq - 1);                          // the oldest tile has landed
             __syncthreads();
+            const int b = head;
+            const Tile cur = q[b];
             const float* T = tbuf[b];
             float* rsb = rstate[b];
             const int L = cur.L, tr = cur.tr;
@@ -218,36 +233,62 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
                 pz = py = 0.f;
                 cur_L = L;
             }
-            // phase 1: dots with groups of gs lanes per row, then the row updates
-            const int gs = L >= 128 ? 32 : L >= 64 ? 16 : L >= 32 ? 8 : L >= 16 ? 4 : L >= 8 ? 2 : 1;
-            const int j = tid & (gs - 1);
-            for (int i0 = tid / gs; i0 < ((tr + (ADMM_T / gs) - 1) / (ADMM_T / gs)) * (ADMM_T / gs);
-                 i0 += ADMM_T / gs) {
-                const int i = i0;
-                float dot = 0.f;
-                if (i < tr)
-                    for (int c = j; c < L; c += gs) dot = fmaf(T[i * L + c], su[c], dot);
-                for (int o = gs >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-                if (i < tr && j == 0) {
-                    const float s = a.rs ? rsb[3 * a.tile_rows + i] : 1.f;
-                    const float av = dot * s;
-                    const float d = rsb[2 * a.tile_rows + i] * s;
-                    float yv, zv;
-                    if (init) {
-                        yv = a.y0 ? rsb[i] / s : 0.f;
-                        zv = fminf(av, d);
-                    } else {
-                        yv = rsb[i];
-                        zv = fminf(av + yv / rho, d);
-                        yv = yv + rho * (av - zv);
+            // phase 1: the row dots a_r = C~_r . u, then the row updates (update_row)
+            auto update_row = [&](int i, float dot) {
+                const float s = a.rs ? rsb[3 * a.tile_rows + i] : 1.f;
+                const float av = dot * s;
+                const float d = rsb[2 * a.tile_rows + i] * s;
+                float yv, zv;
+                if (init) {
+                    yv = a.y0 ? rsb[i] / s : 0.f;
+                    zv = fminf(av, d);
+                } else {
+                    yv = rsb[i];
+                    zv = fminf(av + yv * inv_rho, d);
+                    yv = yv + rho * (av - zv);
+                }
+                rp = nmaxf(rp, fabsf(av - zv));
+                am = nmaxf(am, fabsf(av));
+                zm = nmaxf(zm, fabsf(zv));
+                rsb[i] = yv;
+                rsb[a.tile_rows + i] = zv;
+                wz[i] = zv * s;
+                wy[i] = yv * s;
+            };
+            if (L >= 64) {
+                // long rows: a warp takes 8 rows at once, lanes along the columns (8 independent
+                // accumulators and reductions)
+                constexpr int RW = 8;
+                for (int i0 = warp * RW; i0 < tr; i0 += NW * RW) {
+                    float acc[RW];
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) acc[r] = 0.f;
+                    for (int c = lane; c < L; c += 32) {
+                        const float uc = su[c];
+#pragma unroll
+                        for (int r = 0; r < RW; ++r)
+                            if (i0 + r < tr) acc[r] = fmaf(T[(i0 + r) * L + c], uc, acc[r]);
                     }
-                    rp = nmaxf(rp, fabsf(av - zv));
-                    am = nmaxf(am, fabsf(av));
-                    zm = nmaxf(zm, fabsf(zv));
-                    rsb[i] = yv;
-                    rsb[a.tile_rows + i] = zv;
-                    wz[i] = zv * s;
-                    wy[i] = yv * s;
+                    float mine = 0.f;
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) {
+                        const float v = wsum(acc[r]);
+                        if (lane == r) mine = v;
+                    }
+                    if (lane < RW && i0 + lane < tr) update_row(i0 + lane, mine);
+                }
+            } else {
+                // short rows: groups of gs lanes per row
+                const int gs = L >= 32 ? 8 : L >= 16 ? 4 : L >= 8 ? 2 : 1;
+                const int j = tid & (gs - 1);
+                for (int i0 = tid / gs; i0 < ((tr + (ADMM_T / gs) - 1) / (ADMM_T / gs)) * (ADMM_T / gs);
+                     i0 += ADMM_T / gs) {
+                    const int i = i0;
+                    float dot = 0.f;
+                    if (i < tr)
+                        for (int c = j; c < L; c += gs) dot = fmaf(T[i * L + c], su[c], dot);
+                    for (int o = gs >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                    if (i < tr && j == 0) update_row(i, dot);
                 }
             }
             __syncthreads();
@@ -259,17 +300,28 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             {
                 const int G2 = ADMM_T / L;
                 const int c = tid % L, g2 = tid / L;
-                if (g2 < G2)
-                    for (int i = g2; i < tr; i += G2) {
+                if (g2 < G2) {
+                    float pz2 = 0.f, py2 = 0.f;                // a second chain for latency
+                    int i = g2;
+                    for (; i + G2 < tr; i += 2 * G2) {
+                        const float v = T[i * L + c], v2 = T[(i + G2) * L + c];
+                        pz = fmaf(v, wz[i], pz);
+                        py = fmaf(v, wy[i], py);
+                        pz2 = fmaf(v2, wz[i + G2], pz2);
+                        py2 = fmaf(v2, wy[i + G2], py2);
+                    }
+                    if (i < tr) {
                         const float v = T[i * L + c];
                         pz = fmaf(v, wz[i], pz);
                         py = fmaf(v, wy[i], py);
                     }
+                    pz += pz2;
+                    py += py2;
+                }
             }
             __syncthreads();
-            cur = nxt;
-            have = more;
-            b ^= 1;
+            head = (head + 1) % NB;
+            --nq;
         }
         if (cur_L > 0) {
             const int c = tid % cur_L;
@@ -516,14 +568,21 @@ __global__ void admm_partition_kernel(long rows, int nu, int Mnc, int grid, int*
 }
 
 static size_t admm2_smem(int n, bool psmem, int tile_floats, int tile_rows) {
-    size_t f = (psmem ? (size_t)n * n : 0) + 8 * (size_t)n + 4 * (ADMM_T / 32) + 4;
-    f += 2 * (size_t)tile_floats + 8 * (size_t)tile_rows + 2 * (size_t)tile_rows;
+    const size_t nb = psmem ? 2 : 3;
+    size_t f = (psmem ? (size_t)n * n : 0) + 8 * (size_t)n + 4 * (ADMM_T / 32) + 4 + 4;
+    f += nb * (size_t)tile_floats + nb * 4 * (size_t)tile_rows + 2 * (size_t)tile_rows;
     return f * sizeof(float);
 }
 
-bool admm2_psmem(int n) { return admm2_smem(n, true, kAdmmTileFloats, kAdmmTileRows) <= 220 * 1024; }
+// Layout: P^{-1} in shared memory with two 8192-float tiles, or P^{-1} read from L2 with three
+// larger tiles (the row pass then keeps two tiles in flight).
+bool admm2_psmem(int n) {
+    return kAdmmPinvShared && admm2_smem(n, true, kAdmmTileFloats, kAdmmTileRows) <= 220 * 1024;
+}
 
-size_t admm2_smem_bytes(int n) { return admm2_smem(n, admm2_psmem(n), kAdmmTileFloats, kAdmmTileRows); }
+static int admm2_tile_floats(int n) { return admm2_psmem(n) ? kAdmmTileFloats : kAdmmTileFloatsL2; }
+
+size_t admm2_smem_bytes(int n) { return admm2_smem(n, admm2_psmem(n), admm2_tile_floats(n), kAdmmTileRows); }
 
 const void* admm2_kernel_ptr(int n) {
     return admm2_psmem(n) ? (const void*)admm2_kernel<true> : (const void*)admm2_kernel<false>;
@@ -543,7 +602,7 @@ gm_status admm_solve(const AdmmPlan& p) {
     a.rs = p.rs; a.U0 = p.U0; a.y0 = p.y0; a.U = p.U; a.y = p.y; a.z = p.z; a.acc = p.acc;
     a.bar = p.bar; a.status = p.status; a.row_begin = p.row_begin; a.S = p.S; a.stats = p.stats;
     a.tol = p.tol; a.max_iter = p.max_iter; a.adapt_every = p.adapt_every; a.max_spins = p.max_spins;
-    a.tile_floats = kAdmmTileFloats;
+    a.tile_floats = admm2_tile_floats(n);
     a.tile_rows = kAdmmTileRows;
     a.vec4 = (p.nu % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.Ct) & 15) == 0);
     const bool psmem = admm2_psmem(n);

@@ -6,7 +6,9 @@
 namespace gmi {
 
 constexpr int ADMM_T = 512;             // threads per CTA of the persistent kernel
-constexpr int kAdmmTileFloats = 8192;   // C~ floats per shared-memory tile (x2 buffers)
+constexpr int kAdmmTileFloats = 8192;   // C~ floats per shared-memory tile (x2 buffers, P^{-1} in smem)
+constexpr int kAdmmTileFloatsL2 = 12288; // C~ floats per tile (x3 buffers, P^{-1} from L2)
+constexpr bool kAdmmPinvShared = false;  // keep P^{-1} in shared memory when it fits
 constexpr int kAdmmTileRows = 512;      // rows per tile at most
 constexpr int kAdmmMaxN = 256;          // N nu
 
