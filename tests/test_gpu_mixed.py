@@ -23,7 +23,7 @@ its error is measured against the largest of those terms.
 import numpy as np
 import pytest
 
-from gpu_helpers import blocks_to_dense, max_rel_err, oracle_linearize, orti
+from gpu_helpers import blocks_to_dense, max_rel_err, ocd, oracle_linearize, orti
 from oracle import gnn as ognn
 from synth import random_instance
 
@@ -101,6 +101,27 @@ def test_mixed_linearize_parity(lib, W):
     prob, got = _linearize(lib, wl, u_hat, GM_PREC_MIXED)
     errs = _errors(prob, wl, u_hat, got, oracle_linearize(wl, u_hat.astype(np.float64)))
     assert max(errs.values()) <= REL_MIXED, errs
+
+
+@pytest.mark.parametrize("W", [64, 128])
+def test_mixed_condensed_h_g(lib, W):
+    """H and g (Eq. H, Eq. g) from the split-BF16 linearisation, condensed on the GPU, against the
+    oracle's condensing of its own linearisation.  H's learned part (H - Rbar) and g are compared
+    to 1e-4 of their max-abs; both are sums of products of Jacobian entries, so they carry the
+    Jacobians' relative error."""
+    wl, u_hat = _kink_free(W)
+    prob, (x_hat, A, B, c) = _linearize(lib, wl, u_hat, GM_PREC_MIXED)
+    torch = prob.torch
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda")  # noqa: E731
+    H, g, _, _ = (t.cpu().numpy().astype(np.float64) for t in prob.condense(dev(x_hat), dev(A), dev(B), dev(c)))
+    xo, Ao, Bo, co = oracle_linearize(wl, u_hat.astype(np.float64))
+    nbh = [list(prob.col[prob.row_ptr[i]:prob.row_ptr[i + 1]]) for i in range(wl.M)]
+    blocks = ocd.blocks_from_dense(Ao, Bo, co, nbh)
+    Ho, go, _, _, _, _ = ocd.condense_recursive(blocks, xo[0].reshape(-1), wl.Qdiag, wl.Rdiag, wl.x_ref, wl.u_ref,
+                                                np.zeros((wl.N, wl.M, 0, 3)), np.zeros((wl.N, wl.M, 0)))
+    R = np.diag(wl.Rdiag.reshape(-1).astype(np.float64))
+    eh, eg = max_rel_err(H - R, Ho - R), max_rel_err(g, go)
+    assert eh <= REL_MIXED and eg <= REL_MIXED, (eh, eg)
 
 
 def test_mixed_rti_step_u(lib):
