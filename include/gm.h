@@ -190,6 +190,15 @@ gm_status gm_jac_pattern(const gm_ctx* ctx, int* nnzb, const int32_t** row_ptr,
                          const int32_t** col);
 
 /* ------------------------------------------------------------------------
+ * gm_rollout — the GNN dynamics alone (Eq. forward_dynamics): x_out[0] = x0,
+ * x_out[k+1] = F(x_out[k], u[k]) for k < n_steps (1 <= n_steps <= N); the
+ * plant of a closed loop that uses the model itself, or a prediction.
+ *   x0 [M][6], u [n_steps][nu], x_out [n_steps+1][M][6] (out; may alias x0
+ *   at its first block).  Shares the context's scratch with the other calls.
+ * ---------------------------------------------------------------------- */
+gm_status gm_rollout(gm_ctx* ctx, const float* x0, const float* u, int n_steps, float* x_out, void* stream);
+
+/* ------------------------------------------------------------------------
  * gm_linearize — rollout and local Jacobians (Eq. forward_dynamics,
  * Eq. linearized_dynamics; Algorithm 1 "Linearize GNN dynamics").
  *   x0     [M][6]                measured state x~(t)

@@ -120,6 +120,7 @@ def _load():
         "gm_ws_grad": ([vp, vp, vp], C.c_int),
         "gm_ws_features": ([vp, vp, vp, vp, vp], C.c_int),
         "gm_batch_create": ([C.POINTER(vp), C.c_int, C.POINTER(vp)], C.c_int),
+        "gm_rollout": ([vp, vp, vp, C.c_int, vp, vp], C.c_int),
         "gm_batch_destroy": ([vp], None),
         "gm_batch_rti_step": ([vp, C.POINTER(vp), vp, vp, C.POINTER(vp), C.POINTER(vp), vp], C.c_int),
         "gm_batch_state": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
@@ -143,7 +144,7 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
                     "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
-                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state")
+                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_rollout")
 
 GM_NOALLOC_MAX_NU = 64
 GM_NOALLOC_MAX_ROWS = 8192
@@ -313,6 +314,10 @@ def gm_jac_pattern(ctx, M):
 def gm_linearize(ctx, x0, u_hat, x_hat, A=None, B=None, c=None, stream=None):
     _check("gm_linearize", _lib.gm_linearize(ctx, _ptr(x0), _ptr(u_hat), _ptr(x_hat), _ptr(A), _ptr(B),
                                              _ptr(c), _stream(stream)))
+
+
+def gm_rollout(ctx, x0, u, n_steps, x_out, stream=None):
+    _check("gm_rollout", _lib.gm_rollout(ctx, _ptr(x0), _ptr(u), int(n_steps), _ptr(x_out), _stream(stream)))
 
 
 def make_cost(Qdiag, Rdiag, x_ref, u_ref):

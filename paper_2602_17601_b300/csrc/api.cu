@@ -652,6 +652,16 @@ gm_status gm_linearize(gm_ctx* ctx, const float* x0, const float* u_hat, float* 
     return GM_OK;
 }
 
+gm_status gm_rollout(gm_ctx* ctx, const float* x0, const float* u, int n_steps, float* x_out, void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx && x0 && u && x_out, "NULL argument");
+    GM_CHECK_ARG(n_steps >= 1 && n_steps <= ctx->N, "n_steps must be in [1, N] (got %d)", n_steps);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GM_CUDA_TRY(cudaMemsetAsync(ctx->d_status + 2, 0, sizeof(int), st));
+    GM_TRY(gnn_rollout_steps(ctx, x0, u, x_out, n_steps, st));
+    return GM_OK;
+}
+
 static gm_status check_cost(const gm_ctx* ctx, const gm_cost* cost, const gm_constr* cons) {
     GM_CHECK_ARG(cost && cost->Qdiag && cost->Rdiag && cost->x_ref && cost->u_ref, "cost has NULL members");
     GM_CHECK_ARG(cons && cons->u_lo && cons->u_hi, "constraints have NULL bounds");

@@ -456,14 +456,19 @@ static gm_status forward_stage(gm_ctx* c, int k, const float* xk, const float* u
     return GM_OK;
 }
 
-// x_hat[0] = x0; x_hat[k+1] = F(x_hat[k], u_hat[k]); ReLU masks of every layer kept.
-gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, cudaStream_t st) {
+// x_hat[0] = x0; x_hat[k+1] = F(x_hat[k], u_hat[k]) for k < n_steps; ReLU masks of every layer kept.
+gm_status gnn_rollout_steps(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, int n_steps,
+                            cudaStream_t st) {
     const int M = c->M;
-    GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, st));
-    for (int k = 0; k < c->N; ++k)
+    if (x_hat != x0) GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < n_steps; ++k)
         GM_TRY(forward_stage(c, k, x_hat + (long)k * M * 6, u_hat + (long)k * c->nu, x_hat + (long)(k + 1) * M * 6,
                              st));
     return GM_OK;
+}
+
+gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, cudaStream_t st) {
+    return gnn_rollout_steps(c, x0, u_hat, x_hat, c->N, st);
 }
 
 // Final node latents h^K of stage 0 at (x0, u0), left in c->d_h.

@@ -18,6 +18,8 @@ inline __host__ __device__ long tc_tile_off(int n, int k, int kc) {
 
 // gnn.cu
 gm_status gnn_rollout(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, cudaStream_t st);
+gm_status gnn_rollout_steps(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, int n_steps,
+                            cudaStream_t st);
 gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float* A, float* B,
                         float* cvec, cudaStream_t st);
 
