@@ -47,6 +47,7 @@ typedef int gm_status;
 #define GM_STALLED            5   /* warm-started ADMM stalled; cold restart used */
 #define GM_ERR_TIMEOUT        6   /* a bounded device-side wait gave up */
 #define GM_ERR_NUMERIC        7   /* NaN/Inf or a non-positive pivot */
+#define GM_ERR_INFEASIBLE     8   /* ADMM found a certificate that no U satisfies the constraints */
 
 /* Precision forms of the step. */
 #define GM_PREC_FP32   0   /* every GNN, Jacobian, condensing and ADMM op in FP32 (SIMT);
@@ -263,6 +264,13 @@ gm_status gm_condense(gm_ctx* ctx, const float* x_hat, const float* A, const flo
  *   l = [u_lo; -inf], h = [u_hi; d~]; stop when |a - z|_inf <= tol and the
  *   dual residual |H U + g + A~'y|_inf <= tol.  Then optional FP64 polish and
  *   the FP64 KKT certificate into stats.
+ *   Every 10th iteration tests the primal-infeasibility certificate of
+ *   Banjac et al. (2019) on the dual step dy = y - y_prev (scaled rows):
+ *   |A~'dy|_inf <= 1e-4 |dy|_inf, dy >= -1e-4 |dy|_inf on rows whose lower
+ *   bound is -inf (and dy <= 1e-4 |dy|_inf where the upper bound is +inf),
+ *   and h'max(dy, 0) + l'min(dy, 0) <= -1e-4 |dy|_inf over the finite
+ *   bounds; when it holds no U satisfies the constraints, ADMM stops and
+ *   stats->status is GM_ERR_INFEASIBLE (U holds the last iterate).
  *   H, g, Ct, dt, u_lo, u_hi  as from gm_condense / gm_constr
  *   warm_U [nU], warm_y [nU + N M n_c]  nullable warm start (U^0, y^0)
  *   U [nU] (out), y [nU + N M n_c] (out, nullable)  multipliers, box rows first

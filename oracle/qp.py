@@ -17,6 +17,8 @@ Contents:
                         constrained solve on the active set it identifies;
 * ``admm``              the ADMM recurrence the GPU path runs (fixed rho,
                         no relaxation, no scaling);
+* ``primal_infeasible`` the certificate ADMM's dual step gives when no U
+                        satisfies the constraints;
 * ``polish``            equality-constrained re-solve on the active set guessed
                         from an ADMM iterate;
 * ``brute_force``       every active set, for tiny problems;
@@ -170,6 +172,34 @@ def solve_exact(H, g, lo, hi, C=None, d=None):
 
 
 ROW_NORM_FLOOR = 1e-8
+INFEAS_EVERY = 10          # ADMM iterations between infeasibility tests
+INFEAS_EPS = 1e-4          # relative tolerance of the certificate
+
+
+def primal_infeasible(At, l, h, dy, eps=INFEAS_EPS):
+    """True when dy certifies that no U satisfies l <= A~U <= h, up to eps.
+
+    Farkas' lemma: the set is empty iff some v has A~'v = 0 and support
+    sup_{l <= s <= h} v's = h'max(v, 0) + l'min(v, 0) < 0; a component of v
+    whose sign meets an infinite bound makes the support +inf.  For ADMM,
+    Banjac, Goulart, Stellato and Boyd (2019, "Infeasibility detection in the
+    alternating direction method of multipliers for convex optimization")
+    show that the dual step dy = y^k - y^(k-1) converges to such a v when the
+    constraints are infeasible.  The relative test (eps scales |dy|_inf):
+        |A~'dy|_inf <= eps |dy|_inf,
+        dy_r >= -eps |dy|_inf where l_r = -inf,  dy_r <= eps |dy|_inf where h_r = +inf,
+        sum over finite bounds of h_r max(dy_r, 0) + l_r min(dy_r, 0) <= -eps |dy|_inf.
+    """
+    dy = np.asarray(dy, np.float64)
+    dmax = np.abs(dy).max(initial=0.0)
+    if dmax == 0.0:
+        return False
+    e = eps * dmax
+    up, dn = np.maximum(dy, 0.0), np.minimum(dy, 0.0)
+    hfin, lfin = np.isfinite(h), np.isfinite(l)
+    wrong = max(np.max(up[~hfin], initial=0.0), np.max(-dn[~lfin], initial=0.0))
+    support = float(np.sum(h[hfin] * up[hfin]) + np.sum(l[lfin] * dn[lfin]))
+    return bool(np.abs(At.T @ dy).max() <= e and wrong <= e and support <= -e)
 
 
 def row_scaling(C):
@@ -179,7 +209,7 @@ def row_scaling(C):
 
 
 def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None, y0=None,
-         scale_rows=False, adapt_every=0, max_updates=5):
+         scale_rows=False, adapt_every=0, max_updates=5, detect_infeasible=True, return_info=False):
     """ADMM on l <= A~U <= h (fixed rho, alpha = 1, sigma = 0, unscaled residuals).
 
         P     = H + rho A~'A~                      (factored once)
@@ -200,7 +230,12 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
     and re-factor P with rho sqrt(ratio) (clamped to [1e-6, 1e6]) when that
     changes rho by more than a factor 5.
 
-    Returns U, z, y, iterations (number of U updates), r_p, r_d, converged.
+    detect_infeasible: after every INFEAS_EVERY-th iteration that has not
+    converged, stop when the dual step y - y_prev (on the rows the recurrence
+    runs on) passes ``primal_infeasible``.
+
+    Returns U, z, y, iterations (number of U updates), r_p, r_d, converged;
+    return_info adds a dict {infeasible, dy} (dy for the original rows).
     """
     H = np.asarray(H, np.float64)
     g = np.asarray(g, np.float64)
@@ -220,19 +255,26 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
     z = np.clip(At @ U, l, h)
     r_p = r_d = np.inf
     it = 0
-    ok = False
+    ok = infeasible = False
+    dy = np.zeros_like(y)
     updates = 0
     for it in range(1, max_iter + 1):
         rhs = At.T @ (rho * z - y) - g
         U = np.linalg.solve(L.T, np.linalg.solve(L, rhs))
         a = At @ U
         z = np.clip(a + y / rho, l, h)
+        y_prev = y
         y = y + rho * (a - z)
         r_p = np.abs(a - z).max()
         r_d = np.abs(H @ U + g + At.T @ y).max()
         if r_p <= tol and r_d <= tol:
             ok = True
             break
+        if detect_infeasible and it % INFEAS_EVERY == 0:
+            dy = y - y_prev
+            if primal_infeasible(At, l, h, dy):
+                infeasible = True
+                break
         if adapt_every and it % adapt_every == 0 and updates < max_updates:
             ps = max(np.abs(a).max(), np.abs(z).max(), 1e-30)
             ds = max(np.abs(H @ U).max(), np.abs(At.T @ y).max(), np.abs(g).max(), 1e-30)
@@ -245,6 +287,9 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
     if s is not None:
         y = np.concatenate([y[:n], y[n:] * s])
         z = np.concatenate([z[:n], z[n:] / s])
+        dy = np.concatenate([dy[:n], dy[n:] * s])
+    if return_info:
+        return U, z, y, it, r_p, r_d, ok, dict(infeasible=infeasible, dy=dy)
     return U, z, y, it, r_p, r_d, ok
 
 

@@ -23,12 +23,14 @@ GM_ERR_NOT_CONVERGED = 4
 GM_STALLED = 5
 GM_ERR_TIMEOUT = 6
 GM_ERR_NUMERIC = 7
+GM_ERR_INFEASIBLE = 8
 GM_PREC_FP32 = 0
 GM_PREC_MIXED = 1
 GM_PREC_BF16 = 2
 
 STATUS_NAMES = {0: "GM_OK", 1: "GM_ERR_INVALID_ARG", 2: "GM_ERR_CUDA", 3: "GM_ERR_WORKSPACE",
-                4: "GM_ERR_NOT_CONVERGED", 5: "GM_STALLED", 6: "GM_ERR_TIMEOUT", 7: "GM_ERR_NUMERIC"}
+                4: "GM_ERR_NOT_CONVERGED", 5: "GM_STALLED", 6: "GM_ERR_TIMEOUT", 7: "GM_ERR_NUMERIC",
+                8: "GM_ERR_INFEASIBLE"}
 
 
 class GnnDesc(C.Structure):

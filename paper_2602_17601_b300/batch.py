@@ -14,7 +14,7 @@ import ctypes as C
 
 import numpy as np
 
-from . import STATS_BYTES, Constr, Cost, _check, _lib, _stream
+from . import GM_ERR_INFEASIBLE, STATS_BYTES, Constr, Cost, _check, _lib, _stream
 
 
 class Batch:
@@ -149,6 +149,7 @@ def main(argv=None):
            "batched_instance_steps_per_s": a.n * 1000.0 / ms_batch, "speedup": ms_seq / ms_batch,
            "graph": dict(zip(("replayed", "captures"), batch.state())),
            "converged": int(sum(s["converged"] for s in st)), "status_nonzero": int(sum(s["status"] != 0 for s in st)),
+           "infeasible": int(sum(s["status"] == GM_ERR_INFEASIBLE for s in st)),
            "admm_iters_mean": float(np.mean([s["iters"] for s in st])), "admm_max_iter": a.max_iter,
            "admm_iters_converged_mean": float(np.mean([s["iters"] for s in st if s["converged"]] or [0])),
            "workspace_gb": float(sum(p.workspace.numel() for p in probs) / 2**30),

@@ -25,6 +25,8 @@
 // are evaluated redundantly by every CTA.
 #include "admm.h"
 
+#include <type_traits>
+
 namespace gmi {
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -119,8 +121,9 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
     float* yb = p;          p += n;
     float* atz = p;         p += n;                           // A~'z of the last pass (box + rows)
     float* aty = p;         p += n;
-    float* sacc = p;        p += 2 * n;                       // block sums of s C~'z, s C~'y
-    float* wred = p;        p += 4 * NW;
+    float* sdy = p;         p += n;                           // box-row dual step (test iterations)
+    float* sacc = p;        p += 3 * n;                       // block sums of s C~'z, s C~'y, s C~'dy
+    float* wred = p;        p += 6 * NW;
     p = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     // NB tile buffers: C~ rows staged NB - 1 tiles ahead of the one being processed
     constexpr int NB = PSMEM ? 2 : 3;
@@ -136,6 +139,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
     }
     float* wz = p;          p += a.tile_rows;                 // s z_r and s y_r of the current tile
     float* wy = p;          p += a.tile_rows;
+    float* wd = p;          p += a.tile_rows;                 // s dy_r (test iterations)
     __shared__ float s_misc[8];
 
     const float* Pinv = a.Pinv;
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
     }
     const long r0 = a.row_begin[blockIdx.x], r1 = a.row_begin[blockIdx.x + 1];
     const unsigned G = gridDim.x;
-    const int stride = 2 * n + 4;
+    const int stride = admm_acc_stride(n);
     float rho = S->rho;
     const float inv_rho = 1.f / rho;
     const bool first = !S->started;
@@ -167,11 +171,15 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
 
     // --------------------------------------------------------------- one pass over the CTA's rows
     // init: z = clip(a), y = y0; else the ADMM update.  Adds s C~'z, s C~'y and the maxima
-    // (|a - z|, |a|, |z|) into the accumulator accw.
-    auto row_pass = [&](bool init, float* accw) {
-        for (int c = tid; c < 2 * n; c += ADMM_T) sacc[c] = 0.f;
+    // (|a - z|, |a|, |z|) into the accumulator accw.  chk (an iteration that tests the
+    // infeasibility certificate) also adds s C~'dy, max |dy|, the largest dy of the wrong sign
+    // (dy < 0 on a row whose lower bound is -inf) and the support sum d_r max(dy_r, 0).
+    auto row_pass = [&](bool init, bool chk, float* accw) {
+        const int ns = chk ? 3 * n : 2 * n;
+        for (int c = tid; c < ns; c += ADMM_T) sacc[c] = 0.f;
         float rp = 0.f, am = 0.f, zm = 0.f;
-        float pz = 0.f, py = 0.f;                              // column-sweep partials
+        float dym = 0.f, dng = 0.f, dsp = 0.f;
+        float pz = 0.f, py = 0.f, pd = 0.f;                    // column-sweep partials
         int cur_L = -1;
         __syncthreads();
         auto issue = [&](const Tile& t, int b) {
@@ -228,9 +236,10 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
                     if (tid / cur_L < ADMM_T / cur_L) {
                         atomicAdd(&sacc[c], pz);
                         atomicAdd(&sacc[n + c], py);
+                        if (chk) atomicAdd(&sacc[2 * n + c], pd);
                     }
                 }
-                pz = py = 0.f;
+                pz = py = pd = 0.f;
                 cur_L = L;
             }
             // phase 1: the row dots a_r = C~_r . u, then the row updates (update_row)
@@ -243,9 +252,17 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
                     yv = a.y0 ? rsb[i] / s : 0.f;
                     zv = fminf(av, d);
                 } else {
-                    yv = rsb[i];
-                    zv = fminf(av + yv * inv_rho, d);
-                    yv = yv + rho * (av - zv);
+                    const float yo = rsb[i];
+                    zv = fminf(av + yo * inv_rho, d);
+                    yv = yo + rho * (av - zv);
+                    if (chk) {
+                        const float dy = yv - yo;
+                        dym = nmaxf(dym, fabsf(dy));
+                        if (dy < 0.f) dng = nmaxf(dng, -dy);
+                        else if (d < 1e30f) dsp = fmaf(d, dy, dsp);
+                        else dng = nmaxf(dng, dy);
+                        wd[i] = dy * s;
+                    }
                 }
                 rp = nmaxf(rp, fabsf(av - zv));
                 am = nmaxf(am, fabsf(av));
@@ -297,11 +314,12 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
                 a.y[n + cur.t0 + i] = rsb[i];
                 a.z[n + cur.t0 + i] = rsb[a.tile_rows + i];
             }
-            {
+            auto sweep = [&](auto with_dy) {
+                constexpr bool D = decltype(with_dy)::value;
                 const int G2 = ADMM_T / L;
                 const int c = tid % L, g2 = tid / L;
                 if (g2 < G2) {
-                    float pz2 = 0.f, py2 = 0.f;                // a second chain for latency
+                    float pz2 = 0.f, py2 = 0.f, pd2 = 0.f;     // a second chain for latency
                     int i = g2;
                     for (; i + G2 < tr; i += 2 * G2) {
                         const float v = T[i * L + c], v2 = T[(i + G2) * L + c];
@@ -309,16 +327,24 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
                         py = fmaf(v, wy[i], py);
                         pz2 = fmaf(v2, wz[i + G2], pz2);
                         py2 = fmaf(v2, wy[i + G2], py2);
+                        if (D) {
+                            pd = fmaf(v, wd[i], pd);
+                            pd2 = fmaf(v2, wd[i + G2], pd2);
+                        }
                     }
                     if (i < tr) {
                         const float v = T[i * L + c];
                         pz = fmaf(v, wz[i], pz);
                         py = fmaf(v, wy[i], py);
+                        if (D) pd = fmaf(v, wd[i], pd);
                     }
                     pz += pz2;
                     py += py2;
+                    if (D) pd += pd2;
                 }
-            }
+            };
+            if (chk) sweep(std::true_type{});
+            else sweep(std::false_type{});
             __syncthreads();
             head = (head + 1) % NB;
             --nq;
@@ -328,34 +354,47 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             if (tid / cur_L < ADMM_T / cur_L) {
                 atomicAdd(&sacc[c], pz);
                 atomicAdd(&sacc[n + c], py);
+                if (chk) atomicAdd(&sacc[2 * n + c], pd);
             }
         }
         rp = wmaxf(rp);
         am = wmaxf(am);
         zm = wmaxf(zm);
+        if (chk) {
+            dym = wmaxf(dym);
+            dng = wmaxf(dng);
+            dsp = wsum(dsp);
+        }
         if (lane == 0) {
             wred[warp] = rp;
             wred[NW + warp] = am;
             wred[2 * NW + warp] = zm;
+            wred[3 * NW + warp] = dym;
+            wred[4 * NW + warp] = dng;
+            wred[5 * NW + warp] = dsp;
         }
         __syncthreads();
         if (r1 > r0)
-            for (int c = tid; c < 2 * n; c += ADMM_T) atomicAdd(accw + c, sacc[c]);
-        if (tid < 3) {
+            for (int c = tid; c < ns; c += ADMM_T) atomicAdd(accw + c, sacc[c]);
+        if (tid < (chk ? 5 : 3)) {
             float m = 0.f;
             for (int w = 0; w < NW; ++w) m = nmaxf(m, wred[tid * NW + w]);
-            atomicMax(reinterpret_cast<unsigned*>(accw + 2 * n + tid), __float_as_uint(m));
+            atomicMax(reinterpret_cast<unsigned*>(accw + 3 * n + tid), __float_as_uint(m));
+        } else if (chk && tid == 5) {
+            float sum = 0.f;
+            for (int w = 0; w < NW; ++w) sum += wred[5 * NW + w];
+            atomicAdd(accw + 3 * n + 5, sum);
         }
     };
 
-    // read a completed pass: A~'z, A~'y (box rows added), residual maxima
-    auto read_pass = [&](const float* accr, float& rp_rows, float& am_rows, float& zm_rows) {
+    // read a completed pass: A~'z (box rows added) and the row scalars (max |a - z|, |a|, |z|,
+    // |dy|, wrong-sign dy; support sum)
+    auto read_pass = [&](const float* accr, float (&v)[6]) {
         for (int c = tid; c < n; c += ADMM_T) {
             srhs[c] = __ldcg(accr + c) + zb[c];               // new A~'z (temporarily in srhs)
         }
-        rp_rows = __uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 2 * n)));
-        am_rows = __uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 2 * n + 1)));
-        zm_rows = __uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 2 * n + 2)));
+        for (int k = 0; k < 5; ++k) v[k] = __uint_as_float(__ldcg(reinterpret_cast<const unsigned*>(accr + 3 * n + k)));
+        v[5] = __ldcg(accr + 3 * n + 5);
     };
 
     unsigned phase = 0;
@@ -365,12 +404,12 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
     if (first) {
         if (blockIdx.x == 0)
             for (int t = tid; t < stride; t += ADMM_T) a.acc[stride + t] = 0.f;
-        row_pass(true, a.acc);
+        row_pass(true, false, a.acc);
         ++phase;
         ok = grid_barrier(a.bar, G, phase, a.max_spins, a.status);
         if (ok) {
-            float rpr, amr, zmr;
-            read_pass(a.acc, rpr, amr, zmr);
+            float v[6];
+            read_pass(a.acc, v);
             __syncthreads();
             for (int c = tid; c < n; c += ADMM_T) {
                 atz[c] = srhs[c];
@@ -391,73 +430,121 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             if (lane == 0) su[c] = s;
         }
         __syncthreads();
+        // this iteration tests the primal-infeasibility certificate (uniform over the grid)
+        const bool chk = (it + 1) % kInfeasEvery == 0;
         // box rows
-        float rpb = 0.f, amb = 0.f, zmb = 0.f;
+        float rpb = 0.f, amb = 0.f, zmb = 0.f, dyb = 0.f, dnb = 0.f, dsb = 0.f;
         for (int c = tid; c < n; c += ADMM_T) {
             const float av = su[c];
-            const float zn = fminf(fmaxf(av + yb[c] / rho, a.lo[c]), a.hi[c]);
-            yb[c] = yb[c] + rho * (av - zn);
+            const float yo = yb[c];
+            const float zn = fminf(fmaxf(av + yo / rho, a.lo[c]), a.hi[c]);
+            const float yn = yo + rho * (av - zn);
+            yb[c] = yn;
             zb[c] = zn;
             rpb = nmaxf(rpb, fabsf(av - zn));
             amb = nmaxf(amb, fabsf(av));
             zmb = nmaxf(zmb, fabsf(zn));
+            if (chk) {
+                // support of dy over [lo, hi]; an infinite bound takes no dy of its sign
+                const float dy = yn - yo;
+                sdy[c] = dy;
+                dyb = nmaxf(dyb, fabsf(dy));
+                if (dy > 0.f) {
+                    if (a.hi[c] < 1e30f) dsb = fmaf(a.hi[c], dy, dsb);
+                    else dnb = nmaxf(dnb, dy);
+                } else if (dy < 0.f) {
+                    if (a.lo[c] > -1e30f) dsb = fmaf(a.lo[c], dy, dsb);
+                    else dnb = nmaxf(dnb, -dy);
+                }
+            }
         }
         rpb = wmaxf(rpb);
         amb = wmaxf(amb);
         zmb = wmaxf(zmb);
+        if (chk) {
+            dyb = wmaxf(dyb);
+            dnb = wmaxf(dnb);
+            dsb = wsum(dsb);
+        }
         if (lane == 0) {
             wred[warp] = rpb;
             wred[NW + warp] = amb;
             wred[2 * NW + warp] = zmb;
+            wred[3 * NW + warp] = dyb;
+            wred[4 * NW + warp] = dnb;
+            wred[5 * NW + warp] = dsb;
         }
         __syncthreads();
         if (tid == 0) {
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+            float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, s5 = 0.f;
             for (int w = 0; w < NW; ++w) {
                 m0 = nmaxf(m0, wred[w]);
                 m1 = nmaxf(m1, wred[NW + w]);
                 m2 = nmaxf(m2, wred[2 * NW + w]);
+                m3 = nmaxf(m3, wred[3 * NW + w]);
+                m4 = nmaxf(m4, wred[4 * NW + w]);
+                s5 += wred[5 * NW + w];
             }
             s_misc[0] = m0;
             s_misc[1] = m1;
             s_misc[2] = m2;
+            s_misc[3] = m3;
+            s_misc[4] = m4;
+            s_misc[5] = s5;
         }
         float* accw = a.acc + (pass % 3) * stride;
         if (blockIdx.x == 0)
             for (int t = tid; t < stride; t += ADMM_T) a.acc[((pass + 1) % 3) * stride + t] = 0.f;
-        row_pass(false, accw);
+        row_pass(false, chk, accw);
         ++phase;
         if (!grid_barrier(a.bar, G, phase, a.max_spins, a.status)) {
             ok = false;
             break;
         }
         ++it;
-        float rpr, amr, zmr;
-        read_pass(accw, rpr, amr, zmr);
+        float v[6];
+        read_pass(accw, v);
         __syncthreads();
-        // r_d = rho |A~'z_prev - A~'z|_inf ; new A~'y
-        float m = 0.f;
+        // r_d = rho |A~'z_prev - A~'z|_inf ; new A~'y ; on test iterations |A~'dy|_inf
+        float m = 0.f, atd = 0.f;
         for (int c = tid; c < n; c += ADMM_T) {
             m = nmaxf(m, fabsf(srhs[c] - atz[c]));
             atz[c] = srhs[c];
             aty[c] = __ldcg(accw + n + c) + yb[c];
+            if (chk) atd = nmaxf(atd, fabsf(__ldcg(accw + 2 * n + c) + sdy[c]));
         }
         m = wmaxf(m);
-        if (lane == 0) wred[3 * NW + warp] = m;
+        if (chk) atd = wmaxf(atd);
+        if (lane == 0) {
+            wred[3 * NW + warp] = m;
+            wred[4 * NW + warp] = atd;
+        }
         __syncthreads();
-        float mm = 0.f;
-        for (int w = 0; w < NW; ++w) mm = nmaxf(mm, wred[3 * NW + w]);
-        const float rp = nmaxf(rpr, s_misc[0]);
+        float mm = 0.f, ad = 0.f;
+        for (int w = 0; w < NW; ++w) {
+            mm = nmaxf(mm, wred[3 * NW + w]);
+            ad = nmaxf(ad, wred[4 * NW + w]);
+        }
+        const float rp = nmaxf(v[0], s_misc[0]);
         const float rd = rho * mm;
-        const float amax = nmaxf(amr, s_misc[1]);
-        const float zmax = nmaxf(zmr, s_misc[2]);
+        const float amax = nmaxf(v[1], s_misc[1]);
+        const float zmax = nmaxf(v[2], s_misc[2]);
         rp_last = rp;
         rd_last = rd;
         ++pass;
         const bool bad = (rp != rp) || (rd != rd);
         converged = rp <= a.tol && rd <= a.tol;
+        // primal infeasibility (Farkas): dy = y - y_prev with |A~'dy| <= eps |dy|, no dy of the
+        // sign an infinite bound forbids, and support h'max(dy, 0) + l'min(dy, 0) <= -eps |dy|
+        bool infeasible = false;
+        if (chk && !converged) {
+            const float dmax = nmaxf(v[3], s_misc[3]);
+            const float e = kInfeasEps * dmax;
+            infeasible = dmax > 0.f && ad <= e && nmaxf(v[4], s_misc[4]) <= e && v[5] + s_misc[5] <= -e;
+        }
         if (bad && blockIdx.x == 0 && tid == 0) dev_fail(a.status, GM_ERR_NUMERIC);
-        if (converged || bad || it >= a.max_iter) {
+        if (infeasible && blockIdx.x == 0 && tid == 0) dev_fail(a.status, GM_ERR_INFEASIBLE);
+        if (converged || bad || infeasible || it >= a.max_iter) {
             done = true;
             break;
         }
@@ -569,8 +656,8 @@ __global__ void admm_partition_kernel(long rows, int nu, int Mnc, int grid, int*
 
 static size_t admm2_smem(int n, bool psmem, int tile_floats, int tile_rows) {
     const size_t nb = psmem ? 2 : 3;
-    size_t f = (psmem ? (size_t)n * n : 0) + 8 * (size_t)n + 4 * (ADMM_T / 32) + 4 + 4;
-    f += nb * (size_t)tile_floats + nb * 4 * (size_t)tile_rows + 2 * (size_t)tile_rows;
+    size_t f = (psmem ? (size_t)n * n : 0) + 10 * (size_t)n + 6 * (ADMM_T / 32) + 4 + 4;
+    f += nb * (size_t)tile_floats + nb * 4 * (size_t)tile_rows + 3 * (size_t)tile_rows;
     return f * sizeof(float);
 }
 
@@ -614,7 +701,7 @@ gm_status admm_solve(const AdmmPlan& p) {
         GM_TRY(factor_pinv(n, p.P, p.L, p.Linv, p.Pinv, p.status, p.S, p.bar, p.max_spins, p.factor_grid, st));
         if (r == 0 && p.ev_mid) GM_CUDA_TRY(cudaEventRecord(p.ev_mid, st));
         GM_CUDA_TRY(cudaMemsetAsync(p.bar, 0, sizeof(unsigned) * 4, st));
-        GM_CUDA_TRY(cudaMemsetAsync(p.acc, 0, sizeof(float) * (2 * n + 4), st));
+        GM_CUDA_TRY(cudaMemsetAsync(p.acc, 0, sizeof(float) * admm_acc_stride(n), st));
         a.last_round = (r == p.rounds - 1) ? 1 : 0;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(p.grid);

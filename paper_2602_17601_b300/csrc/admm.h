@@ -11,6 +11,12 @@ constexpr int kAdmmTileFloatsL2 = 12288; // C~ floats per tile (x3 buffers, P^{-
 constexpr bool kAdmmPinvShared = false;  // keep P^{-1} in shared memory when it fits
 constexpr int kAdmmTileRows = 512;      // rows per tile at most
 constexpr int kAdmmMaxN = 256;          // N nu
+constexpr int kInfeasEvery = 10;        // iterations between primal-infeasibility tests
+constexpr float kInfeasEps = 1e-4f;     // relative tolerance of the infeasibility certificate
+
+// Floats of one rotating accumulator: sums of s C~'z, s C~'y, s C~'dy ([3n]) and 8 scalars
+// (max |a - z|, |a|, |z|, |dy|, wrong-sign dy; sum of the bound support of dy).
+__host__ __device__ inline int admm_acc_stride(int n) { return 3 * n + 8; }
 
 // Iterate and control flags kept on the device between the launches of one solve.
 struct AdmmState {
@@ -52,7 +58,7 @@ struct AdmmPlan {
     float *U, *y, *z;      // y, z: [n + rows]
     float *P, *Pinv;       // [n n]
     double *L, *Linv;      // [factor_pad(n)^2]
-    float* acc;            // [3 (2n + 4)]
+    float* acc;            // [3 admm_acc_stride(n)]
     unsigned* bar;         // [4]
     int* status;           // [4]
     int* row_begin;        // [grid + 1]

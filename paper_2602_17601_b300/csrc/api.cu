@@ -339,7 +339,7 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_Pinv = cv.take<float>((size_t)nU * nU);
     c->d_G = cv.take<float>((size_t)nU * nU);
     c->d_admm = cv.take<AdmmState>(1);
-    c->d_acc = cv.take<float>(3 * (2 * (size_t)nU + 4));
+    c->d_acc = cv.take<float>(3 * (size_t)admm_acc_stride(nU));
     c->d_bar = cv.take<unsigned>(4);
     c->d_status = cv.take<int>(4);
     c->d_row_begin = cv.take<int>(kMaxAdmmGrid + 1);

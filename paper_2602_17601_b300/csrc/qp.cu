@@ -129,6 +129,7 @@ __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float
         int code = GM_OK;
         if (st & (1 << GM_ERR_TIMEOUT)) code = GM_ERR_TIMEOUT;
         else if (st & (1 << GM_ERR_NUMERIC)) code = GM_ERR_NUMERIC;
+        else if (st & (1 << GM_ERR_INFEASIBLE)) code = GM_ERR_INFEASIBLE;
         else if (!stats->converged) code = GM_ERR_NOT_CONVERGED;
         if (!(stat == stat)) code = GM_ERR_NUMERIC;
         stats->status = code;
@@ -246,7 +247,7 @@ extern "C" gm_status gm_qp_solve_noalloc(int N, int nu, int Mnc, const gm_settin
     float* z = cv.take<float>(n + rows);
     float* ys = cv.take<float>(n + rows);
     float* rs = cv.take<float>(std::max(rows, 1L));
-    float* acc = cv.take<float>(3 * (2 * (size_t)n + 4));
+    float* acc = cv.take<float>(3 * (size_t)admm_acc_stride(n));
     unsigned* bar = cv.take<unsigned>(4);
     int* status = cv.take<int>(4);
     int* rb = cv.take<int>(kNoAllocGrid + 1);

@@ -140,3 +140,71 @@ def test_small_chain_optimum_certificate():
                              r["Ct"] if r["Ct"].size else None, r["dt"] if r["dt"].size else None)
     cert = qp.kkt_certificate(r["H"], r["g"], At, l, h, r["U"].reshape(-1), r["y"])
     assert max(cert.values()) <= 1e-12
+
+
+# ------------------------------------------------------------------ primal infeasibility
+def _box_row_conflict(n=3):
+    """|U_i| <= 1 and U_0 <= -2: infeasible; the Farkas direction is -1 on the lower bound of
+    box row 0 and +1 on the half-space row (A~'v = 0, support 1 - 2 = -1)."""
+    lo, hi = -np.ones(n), np.ones(n)
+    C = np.zeros((1, n))
+    C[0, 0] = 1.0
+    return lo, hi, C, np.array([-2.0])
+
+
+def test_certificate_by_farkas_on_a_hand_made_direction():
+    lo, hi, C, d = _box_row_conflict()
+    At, l, h = qp.stack_rows(lo, hi, C, d)
+    v = np.array([-1.0, 0.0, 0.0, 1.0])
+    assert qp.primal_infeasible(At, l, h, v)
+    assert qp.primal_infeasible(At, l, h, 7.5 * v)              # scale-free
+    assert not qp.primal_infeasible(At, l, h, -v)               # -v: dy < 0 on a row with l = -inf
+    assert not qp.primal_infeasible(At, l, h, v + np.array([0, 0.1, 0, 0]))   # A~'v != 0
+    assert not qp.primal_infeasible(At, l, h, np.zeros(4))
+    # the same direction with a feasible bound d = -0.5: support 1 - 0.5 > 0
+    At2, l2, h2 = qp.stack_rows(lo, hi, C, np.array([-0.5]))
+    assert not qp.primal_infeasible(At2, l2, h2, v)
+
+
+@pytest.mark.parametrize("scale_rows", [False, True])
+def test_admm_stops_on_a_constructed_infeasible_qp(scale_rows):
+    """ADMM's dual step converges to the Farkas direction (up to scale) and the run stops."""
+    lo, hi, C, d = _box_row_conflict()
+    H, g = np.diag([1.0, 2.0, 3.0]), np.array([0.3, -0.2, 0.1])
+    *_, ok, info = qp.admm(H, g, lo, hi, C * 4.0, d * 4.0, rho=0.1, tol=1e-8, max_iter=5000,
+                           scale_rows=scale_rows, adapt_every=25, return_info=True)
+    assert not ok and info["infeasible"]
+    v = info["dy"] / np.abs(info["dy"]).max()
+    # original rows: box row 0 gets -1 and the half-space row (C scaled by 4) gets +1/4
+    assert np.abs(v / v[0] * -1 - np.array([-1.0, 0.0, 0.0, 0.25])).max() <= 1e-3, v
+
+
+def _lp_margin(lo, hi, C, d):
+    """t* = min t over lo <= U <= hi, C U <= d + t (scipy's HiGHS): the set is feasible iff t* <= 0."""
+    from scipy.optimize import linprog
+    n, m = lo.size, C.shape[0]
+    res = linprog(np.r_[np.zeros(n), 1.0], A_ub=np.hstack([C, -np.ones((m, 1))]), b_ub=d,
+                  bounds=[(a, b) for a, b in zip(lo, hi)] + [(None, None)], method="highs")
+    assert res.status == 0
+    return res.fun
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_infeasibility_verdict_matches_linear_programming(seed):
+    """On random box + half-space sets, ADMM flags infeasibility exactly when an LP says the
+    set is empty (sets within 0.05 of the boundary are skipped)."""
+    rng = np.random.default_rng(100 + seed)
+    n, m = 5, 8
+    H, g, lo, hi, C, _ = random_qp(n, m, 200 + seed)
+    d = rng.uniform(-2.0, 1.0, m)
+    t = _lp_margin(lo, hi, C, d)
+    if abs(t) < 0.05:
+        pytest.skip(f"margin {t:.3f} too close to the boundary")
+    *_, ok, info = qp.admm(H, g, lo, hi, C, d, rho=0.1, tol=1e-7, max_iter=20000, scale_rows=True,
+                           adapt_every=25, return_info=True)
+    if t > 0:
+        assert info["infeasible"] and not ok
+        At, l, h = qp.stack_rows(lo, hi, C, d)
+        assert qp.primal_infeasible(At, l, h, info["dy"], eps=1e-3)
+    else:
+        assert ok and not info["infeasible"]
