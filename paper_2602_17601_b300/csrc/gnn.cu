@@ -37,9 +37,20 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
     return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// 16-byte read-only load under a predicate (no access and zeros where pred is false)
+__device__ __forceinline__ float4 ldg4_if(const float* p, bool pred) {
+    float4 v;
+    asm("{\n.reg .pred q;\nsetp.ne.u32 q, %5, 0;\n"
+        "mov.f32 %0, 0f00000000;\nmov.f32 %1, 0f00000000;\nmov.f32 %2, 0f00000000;\nmov.f32 %3, 0f00000000;\n"
+        "@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];\n}\n"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p), "r"((unsigned)pred));
+    return v;
+}
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
 #include "tc_mlp.cuh"
+#include "tc_ws.cuh"
 
 namespace gmi {
 
@@ -350,6 +361,24 @@ static gm_status launch_tc_w(int W, const Op& op, const TcW& tw, cudaStream_t st
     }
 }
 
+// Reverse edge-update MLP in the mixed form at W = 128: the warp-specialised persistent
+// kernel (tc_ws.cuh), one CTA per SM.
+template <class Op>
+static gm_status launch_ws_bwd(const gm_ctx* c, const Op& op, const TcW& tw, cudaStream_t st) {
+    if (op.rows <= 0) return GM_OK;
+    static bool attr_set = false;
+    if (!attr_set) {
+        GM_CUDA_TRY(cudaFuncSetAttribute(tc_ws_bwd_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)WS_SMEM));
+        attr_set = true;
+    }
+    const long tiles = cdiv(op.rows, TC_M);
+    const int grid = (int)std::min<long>(tiles, std::max(1, c->num_sms));
+    tc_ws_bwd_kernel<Op><<<grid, WS_T, WS_SMEM, st>>>(op, tw);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
 // FP32 SIMT kernel, or the tcgen05 kernel in the BF16 forms.  GM_PREC_MIXED evaluates the
 // forward rollout with three-piece operands (FP32 operand precision, so that the ReLU
 // pattern and x_hat match an FP32 evaluation) and the Jacobian products with two pieces;
@@ -592,6 +621,16 @@ struct EdgeMpBwd : BwdBase {
         return a;
     }
     __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(de_out + self(x) * W + n, v); }
+    // the two input rows of an 8-float vector as separate loads with no branch between them
+    // (the carry row is predicated off where the row has none): a = Dagg row, b = carry or 0
+    __device__ void in8_pair(const RowCtx& x, int k0, float4* a, float4* b) const {
+        const float* pa = dagg + (long)x.e * W + k0;
+        a[0] = __ldg(reinterpret_cast<const float4*>(pa));
+        a[1] = __ldg(reinterpret_cast<const float4*>(pa + 4));
+        const float* pb = de_in + (long)(x.f >= 0 ? x.f : 0) * W + k0;
+        b[0] = ldg4_if(pb, x.f >= 0);
+        b[1] = ldg4_if(pb + 4, x.f >= 0);
+    }
 };
 
 struct NodeSumBwd : BwdBase {
@@ -862,7 +901,12 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
                 op.er_edge = d.er_edge[r]; op.er_dstrow = d.er_dstrow[r]; op.er_prev = d.er_prev[r];
                 op.Rn = Rn; op.Rp = r > 0 ? d.er_count[r - 1] : 0;
                 const int kt = c->ktiming ? kernel_timing_begin(c, r, Ns, st) : -1;
-                GM_TRY(launch_mlp(c, op, tc_edge_bwd(c, m), st));
+                const TcW tw = tc_edge_bwd(c, m);
+                if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_W) {
+                    GM_TRY(launch_ws_bwd(c, op, tw, st));
+                } else {
+                    GM_TRY(launch_mlp(c, op, tw, st));
+                }
                 if (kt >= 0) GM_CUDA_TRY(record_kev(c->kev[kt][1], st));
             }
             {
