@@ -429,6 +429,21 @@ static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* 
     c->ct_len = (long)c->M * c->n_c * c->nu * ((long)c->N * (c->N + 1) / 2);
     c->graph = *g;
     build_cones(*g, c->K, c->cones);
+    {   // the reverse node-sum keeps an edge range as first position | count << 24
+        int maxc = 0;
+        long maxp = 0;
+        for (int r = 0; r < c->K; ++r) {
+            const Cones& C = c->cones;
+            for (size_t q = 0; q + 1 < C.er_dst_ptr[r].size(); ++q)
+                maxc = std::max(maxc, C.er_dst_ptr[r][q + 1] - C.er_dst_ptr[r][q]);
+            for (size_t q = 0; q + 1 < C.er_src_ptr[r].size(); ++q)
+                maxc = std::max(maxc, C.er_src_ptr[r][q + 1] - C.er_src_ptr[r][q]);
+            maxp = std::max(maxp, (long)C.er_edge[r].size());
+        }
+        GM_CHECK_ARG(maxc <= 255 && maxp < (1L << 24),
+                     "graph too dense for the reverse pass: %d edges into or out of one node, %ld cone edges "
+                     "(limits 255 and 2^24)", maxc, maxp);
+    }
     c->jac_row_ptr = c->cones.nr_ptr[c->K];
     c->jac_col = c->cones.nr_node[c->K];
     c->nnzb = (int)c->jac_col.size();

@@ -333,6 +333,24 @@ __global__ void agg_kernel(int M, int W, const int* __restrict__ in_ptr, const f
     agg[t] = s;
 }
 
+// Launch with programmatic stream serialization: the kernel may start while the previous
+// kernel of the stream finishes; it waits (griddepcontrol.wait) before reading its inputs.
+template <class... KArgs, class... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <int W, int P, class Op>
 static gm_status launch_tc(const Op& op, const TcW& tw, cudaStream_t st) {
     constexpr size_t smem = tc_smem_bytes<W, P>() > TC_SMEM_MIN ? tc_smem_bytes<W, P>() : TC_SMEM_MIN;
@@ -347,7 +365,7 @@ static gm_status launch_tc(const Op& op, const TcW& tw, cudaStream_t st) {
                                          (int)smem));
         attr_set = true;
     }
-    tc_mlp_kernel<W, Op, P><<<cdiv(op.rows, TC_M), TC_T, smem, st>>>(op, tw);
+    GM_CUDA_TRY(launch_pdl(tc_mlp_kernel<W, Op, P>, dim3((unsigned)cdiv(op.rows, TC_M)), dim3(TC_T), smem, st, op, tw));
     return GM_OK;
 }
 
@@ -361,8 +379,8 @@ static gm_status launch_tc_w(int W, const Op& op, const TcW& tw, cudaStream_t st
     }
 }
 
-// Reverse edge-update MLP in the mixed form at W = 128: the warp-specialised persistent
-// kernel (tc_ws.cuh), one CTA per SM.
+// Reverse edge-update and edge-encoder MLPs in the mixed form at W = 128: the
+// warp-specialised persistent kernel (tc_ws.cuh), one CTA per SM.
 template <class Op>
 static gm_status launch_ws_bwd(const gm_ctx* c, const Op& op, const TcW& tw, cudaStream_t st) {
     if (op.rows <= 0) return GM_OK;
@@ -374,7 +392,7 @@ static gm_status launch_ws_bwd(const gm_ctx* c, const Op& op, const TcW& tw, cud
     }
     const long tiles = cdiv(op.rows, TC_M);
     const int grid = (int)std::min<long>(tiles, std::max(1, c->num_sms));
-    tc_ws_bwd_kernel<Op><<<grid, WS_T, WS_SMEM, st>>>(op, tw);
+    GM_CUDA_TRY(launch_pdl(tc_ws_bwd_kernel<Op>, dim3((unsigned)grid), dim3(WS_T), WS_SMEM, st, op, tw));
     GM_LAUNCH_CHECK();
     return GM_OK;
 }
@@ -514,6 +532,8 @@ struct BwdBase {
     static constexpr bool kHasIn8 = false;
     static constexpr bool kHasOut4 = false;
     static constexpr bool kHasResid = false;   // out4 value = resid4 + product (loads first)
+    static constexpr bool kWsHid = false;      // warp-specialised kernel: store the masked hidden
+    static constexpr bool kWsResid = false;    // warp-specialised kernel: out = A + product
     long rows;
     int kin, nout;
     const float *B1, *b1 = nullptr, *B2, *b2 = nullptr;
@@ -584,6 +604,7 @@ struct NodeMpBwd : BwdBase {
 
 struct EdgeMpBwd : BwdBase {
     static constexpr bool kStoreHid = true;
+    static constexpr bool kWsHid = true, kWsResid = true;
     const float* dagg;       // on NR_r
     const float* de_in;      // carry on ER_{r-1} (nullable)
     float* ehid;             // on ER_r
@@ -640,50 +661,76 @@ struct NodeSumBwd : BwdBase {
     float* dh_next;          // on NR_{r+1}
     const int *nr_prev, *dst_ptr, *src_ptr, *src_list;
     int Rr, Re;              // |NR_r|, |ER_r|
+    // RowCtx: d = row in NR_r or -1; e, f = the in-edge and out-edge ranges of the row's node
+    // as first position | count << 24 (positions in ER_r order, resp. in src_list)
     __device__ RowCtx prep(long r) const {
         RowCtx x{0, 0, 0, 0, 0, 0};
         if (r < 0) return x;
         decode(r, x);
-        x.d = nr_prev[x.b];                                      // row in NR_r or -1
-        x.e = (int)r;
+        x.d = nr_prev[x.b];
+        if (x.d >= 0) {
+            const int p0 = dst_ptr[x.d];
+            x.e = p0 | ((dst_ptr[x.d + 1] - p0) << 24);
+        }
+        const int q0 = src_ptr[x.b];
+        x.f = q0 | ((src_ptr[x.b + 1] - q0) << 24);
         return x;
     }
+    __device__ long self(const RowCtx& x) const { return ((long)x.a * R + x.b) * 3 + x.c; }
     __device__ float in(const RowCtx& x, int k) const {
         float s = 0.f;
         const long base = (long)x.a * Re;
-        if (k < W) {
-            if (x.d >= 0)
-                for (int p = dst_ptr[x.d]; p < dst_ptr[x.d + 1]; ++p)
-                    s += ehid[((base + p) * 3 + x.c) * W + k];
-        } else {
-            for (int p = src_ptr[x.b]; p < src_ptr[x.b + 1]; ++p)
-                s += ehid[((base + src_list[p]) * 3 + x.c) * W + k - W];
+        const bool dsum = k < W;
+        const int pk = dsum ? x.e : x.f;
+        const int p0 = pk & 0xFFFFFF, cnt = (int)((unsigned)pk >> 24);
+        for (int t = 0; t < cnt; ++t) {
+            const int er = dsum ? p0 + t : src_list[p0 + t];
+            s += ehid[((base + er) * 3 + x.c) * W + (dsum ? k : k - W)];
         }
         return s;
     }
     __device__ void out(const RowCtx& x, int n, float v) const {
         float a = x.d >= 0 ? dacc[(((long)x.a * Rr + x.d) * 3 + x.c) * W + n] : 0.f;
-        dh_next[(long)x.e * W + n] = a + v;
+        dh_next[self(x) * W + n] = a + v;
     }
     __device__ uint32_t mask_word(const RowCtx&, int) const { return 0u; }
     static constexpr bool kHasIn8 = true, kHasOut4 = true;
+    // sum over the node's in-edges (k0 < W) or out-edges of 8 hidden-cotangent columns; the
+    // rows of four edges are loaded together (predicated past the end of the range)
     __device__ void in8(const RowCtx& x, int k0, float* v) const {
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = 0.f;
         const long base = (long)x.a * Re;
-        if (k0 < W) {
-            if (x.d >= 0)
-                for (int p = dst_ptr[x.d]; p < dst_ptr[x.d + 1]; ++p) add8(ehid + ((base + p) * 3 + x.c) * W + k0, v);
-        } else {
-            for (int p = src_ptr[x.b]; p < src_ptr[x.b + 1]; ++p)
-                add8(ehid + ((base + src_list[p]) * 3 + x.c) * W + k0 - W, v);
+        const bool dsum = k0 < W;
+        const int pk = dsum ? x.e : x.f;
+        const int p0 = pk & 0xFFFFFF, cnt = (int)((unsigned)pk >> 24);
+        const int col = dsum ? k0 : k0 - W;
+        for (int t = 0; t < cnt; t += 4) {
+            int er[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = min(p0 + t + u, p0 + cnt - 1);
+                er[u] = dsum ? p : __ldg(src_list + p);
+            }
+            float4 a[4][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float* pr = ehid + ((base + er[u]) * 3 + x.c) * W + col;
+                a[u][0] = ldg4_if(pr, t + u < cnt);
+                a[u][1] = ldg4_if(pr + 4, t + u < cnt);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[0] += a[u][0].x; v[1] += a[u][0].y; v[2] += a[u][0].z; v[3] += a[u][0].w;
+                v[4] += a[u][1].x; v[5] += a[u][1].y; v[6] += a[u][1].z; v[7] += a[u][1].w;
+            }
         }
     }
     static constexpr bool kHasResid = true;
     __device__ float4 resid4(const RowCtx& x, int n) const {
         return x.d >= 0 ? ld4(dacc + (((long)x.a * Rr + x.d) * 3 + x.c) * W + n) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(dh_next + (long)x.e * W + n, v); }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(dh_next + self(x) * W + n, v); }
 };
 
 struct NodeEncBwd : BwdBase {
@@ -720,6 +767,13 @@ struct EdgeEncBwd : BwdBase {
     __device__ void out(const RowCtx& x, int n, float v) const { dd[(long)x.e * 6 + n] = v; }
     static constexpr bool kHasIn8 = true;
     __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(de + (long)x.e * W + k0, v); }
+    // warp-specialised producer: one input row (b stays zero, nothing loaded for it)
+    __device__ void in8_pair(const RowCtx& x, int k0, float4* a, float4* b) const {
+        const float* pa = de + (long)x.e * W + k0;
+        a[0] = __ldg(reinterpret_cast<const float4*>(pa));
+        a[1] = __ldg(reinterpret_cast<const float4*>(pa + 4));
+        b[0] = b[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 };
 
 // One warp per (stage, seed s): A^{s n}, B^s and c^s from the pulled-back cotangents.
@@ -939,7 +993,12 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
             EdgeEncBwd op{};
             fill_bwd(op, c, c->mlp[1], k0, 0, true, (long)Ns * RE * 3, RE);
             op.de = de_in; op.dd = c->d_dd; op.er_edge = d.er_edge[K - 1];
-            GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[1]), st));
+            const TcW tw = tc_bwd(c, c->mlp[1]);
+            if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p <= 32) {
+                GM_TRY(launch_ws_bwd(c, op, tw, st));
+            } else {
+                GM_TRY(launch_mlp(c, op, tw, st));
+            }
         }
         {
             const long warps = (long)Ns * M;

@@ -93,6 +93,11 @@ __device__ __forceinline__ void tc_ld32(unsigned taddr, float* v) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Programmatic dependent launch: let the next kernel of the stream start its prologue now,
+// and wait until the previous kernel has completed (its writes visible) before reading any
+// data it produced.  Both are no-ops for a launch without the programmatic attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned bf2(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -393,9 +398,16 @@ __host__ __device__ constexpr size_t tc_region_a() {
     return (size_t)P * ((size_t)TC_M * tc_kc<P>() * 2 > (size_t)TC_M * W * 2 ? (size_t)TC_M * tc_kc<P>() * 2
                                                                                : (size_t)TC_M * W * 2);
 }
+// Weight-chunk buffers (chunk g in buffer g % NBUF; the chunk NBUF ahead is copied as soon as
+// the MMAs that read a buffer have completed).  One: a second buffer for the three-piece
+// forward form measured no faster, the chunks being bound by the MMAs themselves.
+template <int P>
+__host__ __device__ constexpr int tc_nbuf() {
+    return 1;
+}
 template <int W, int P>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-    return tc_region_a<W, P>() + (size_t)P * TC_NB * tc_kc<P>() * 2;
+    return tc_region_a<W, P>() + (size_t)tc_nbuf<P>() * P * TC_NB * tc_kc<P>() * 2;
 }
 // Launch size: at least TC_SMEM_MIN, so that no more than two CTAs share an SM (what two
 // TC_TMEM_COLS allocations fill) and the output tile of tc_out_rows fits.
@@ -409,10 +421,11 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char* sA = tsm;                          // P pieces of the A chunk, K-major with K = KC
     unsigned char* sH = tsm;                          // P pieces of the hidden tile, K = W (after GEMM1)
-    unsigned char* sB = tsm + tc_region_a<W, P>();    // P pieces of the B chunk (bulk copies)
+    constexpr int NBUF = tc_nbuf<P>();
+    unsigned char* sB0 = tsm + tc_region_a<W, P>();   // NBUF buffers of P pieces of a B chunk (bulk copies)
     __shared__ RowCtx rc[TC_M];
     __shared__ __align__(8) unsigned long long mbar;    // MMA completion (tcgen05.commit)
-    __shared__ __align__(8) unsigned long long bbar;    // B chunk arrival (bulk-copy bytes)
+    __shared__ __align__(8) unsigned long long bbar[NBUF];   // B chunk arrival (bulk-copy bytes)
     __shared__ unsigned tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long row0 = (long)blockIdx.x * TC_M;
@@ -420,16 +433,39 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     constexpr bool kSingle = (Op::kMode == 2);
     const int nch = (w.K1p + KC - 1) / KC;
     const int kc2 = tc_chunk_b2(w.N2p);
-    unsigned bphase = 0;        // thread 0: completed B chunk arrivals
-    bool b_pending = false;     // thread 0: a bulk copy has been issued and not yet waited for
+    // B chunks in order: g < nch are the K chunks of B1, then (two products) the K chunks of B2;
+    // chunk g lives in buffer g % NBUF.  Thread 0 tracks each buffer's arrivals.
+    const int n2 = kSingle ? 0 : (W + kc2 - 1) / kc2;
+    const int ng = nch + n2;
+    unsigned bphase[NBUF];
+    bool b_pending[NBUF];
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) {
+        bphase[b] = 0;
+        b_pending[b] = false;
+    }
+    auto load_b = [&](int g) {
+        const int b = g % NBUF;
+        unsigned char* dst = sB0 + (size_t)b * P * B_BYTES;
+        if (g < nch) {
+            tc_load_b<P>(dst, B_BYTES, w.B1, W, g * KC, min(KC, w.K1p - g * KC), &bbar[b]);
+        } else {
+            const int k0 = (g - nch) * kc2;
+            tc_load_b<P>(dst, B_BYTES, w.B2, w.N2p, k0, min(kc2, W - k0), &bbar[b]);
+        }
+        b_pending[b] = true;
+    };
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar)));
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[b])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_load_b<P>(sB, B_BYTES, w.B1, W, 0, min(KC, w.K1p), &bbar);   // first chunk, under the prologue
-        b_pending = true;
+        for (int g = 0; g < NBUF && g < ng; ++g) load_b(g);              // first chunks, under the prologue
     }
+    // the prologue reads only weights and the static row indices (op.prep): it overlaps the
+    // previous kernel's tail under programmatic dependent launch
+    pdl_launch_dependents();
     for (int m = tid; m < TC_M; m += TC_T) rc[m] = op.prep(row0 + m < rows ? row0 + m : -1);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -439,6 +475,7 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    pdl_wait();
     // D1 [128 x W] and, once the hidden epilogue has read it, D2 [128 x N2p] in the same columns
     const unsigned tD = tmem_base;
     bool ok = true;
@@ -459,16 +496,18 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
 
     // thread 0: wait for the staged B chunk, issue the chunk's MMAs, commit them to mbar (the
     // commit arrives even when nothing was issued, so the other threads never wait in vain)
-    auto issue = [&](unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b_sbo, int kc, int N, bool first) {
+    auto issue = [&](int g, unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b_sbo, int kc, int N, bool first) {
+        const int b = g % NBUF;
         bool okb = false;
-        if (b_pending) {
-            okb = tc_wait(&bbar, bphase & 1, w.status);
+        if (b_pending[b]) {
+            okb = tc_wait(&bbar[b], bphase[b] & 1, w.status);
             if (okb) {
-                ++bphase;
-                b_pending = false;
+                ++bphase[b];
+                b_pending[b] = false;
             }
         }
-        if (okb) tc_issue<P>(tD, a0, a_piece, a_sbo, smem_u32(sB), B_BYTES, b_sbo, kc, N, first);
+        if (okb)
+            tc_issue<P>(tD, a0, a_piece, a_sbo, smem_u32(sB0 + (size_t)b * P * B_BYTES), B_BYTES, b_sbo, kc, N, first);
         tc_commit(&mbar);
         return okb;
     };
@@ -488,19 +527,13 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (tid == 0) ok = issue(smem_u32(sA), A_BYTES, KC * 16, kc * 16, kc, W, c == 0) && ok;
+        if (tid == 0) ok = issue(c, smem_u32(sA), A_BYTES, KC * 16, kc * 16, kc, W, c == 0) && ok;
         if (kAhead && k0 + 2 * KC <= w.K1p) tc_load_a_full<KC>(op, rc, row0, rows, k0 + KC, tid, xa);
         ok = tc_wait(&mbar, phase & 1, w.status) && ok;   // A and B buffers are free again
         ++phase;
-        if (tid == 0 && ok && !b_pending) {
-            if (c + 1 < nch) {
-                tc_load_b<P>(sB, B_BYTES, w.B1, W, k0 + KC, min(KC, w.K1p - k0 - KC), &bbar);
-                b_pending = true;
-            } else if (!kSingle) {
-                tc_load_b<P>(sB, B_BYTES, w.B2, w.N2p, 0, min(kc2, W), &bbar);   // under the epilogue
-                b_pending = true;
-            }
-        }
+        // the buffer chunk c used is free again: the chunk NBUF ahead goes into it (for the
+        // last GEMM1 chunks these are the first GEMM2 chunks, copied under the epilogue)
+        if (tid == 0 && ok && c + NBUF < ng && !b_pending[c % NBUF]) load_b(c + NBUF);
     }
     ok = __syncthreads_and(ok) != 0;           // warp-collective TMEM loads below need a uniform decision
     tc_fence_after();
@@ -562,13 +595,11 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
         for (int k0 = 0; k0 < W; k0 += kc2) {
             const int kc = min(kc2, W - k0);
             // hidden tile: K-major with K = W; the chunk starts k0/8 core matrices along K
-            if (tid == 0) ok = issue(smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, kc * 16, kc, w.N2p, k0 == 0) && ok;
+            const int g = nch + k0 / kc2;
+            if (tid == 0) ok = issue(g, smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, kc * 16, kc, w.N2p, k0 == 0) && ok;
             ok = tc_wait(&mbar, phase & 1, w.status) && ok;
             ++phase;
-            if (tid == 0 && ok && !b_pending && k0 + kc2 < W) {
-                tc_load_b<P>(sB, B_BYTES, w.B2, w.N2p, k0 + kc2, min(kc2, W - k0 - kc2), &bbar);
-                b_pending = true;
-            }
+            if (tid == 0 && ok && g + NBUF < ng && !b_pending[g % NBUF]) load_b(g + NBUF);
         }
         ok = __syncthreads_and(ok) != 0;
         tc_fence_after();
@@ -584,7 +615,10 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
         }
     }
     // a bulk copy whose wait gave up may still be landing: wait (bounded) before the CTA exits
-    if (tid == 0 && b_pending) tc_wait(&bbar, bphase & 1, nullptr);
+    if (tid == 0)
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b)
+            if (b_pending[b]) tc_wait(&bbar[b], bphase[b] & 1, nullptr);
     tc_fence_before();
     __syncthreads();
     if (warp == 0)

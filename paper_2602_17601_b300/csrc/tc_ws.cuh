@@ -1,10 +1,12 @@
-// Warp-specialised persistent form of the reverse two-layer MLP with a stored hidden
-// cotangent and a residual output (the edge-update reverse step, W = 128, two BF16 pieces).
+// Warp-specialised persistent form of a reverse two-layer MLP (W = 128, two BF16 pieces):
+// the edge-update reverse step (stored hidden cotangent, residual output, 128 outputs) and
+// the edge-encoder reverse step (no stored hidden, no residual, a few outputs).
 //
 // Per 128-row tile:  D1  = A . B1^T            (A: the row cotangents, K = 128)
-//                    H   = mask . D1           (ReLU mask of the forward pass; stored as FP32)
-//                    out = D2 = A . I + H . B2^T
-// The residual (out = A + H B2^T) is added by the tensor cores: D2 starts as the BF16 pieces
+//                    H   = mask . D1           (ReLU mask of the forward pass; stored as FP32
+//                                               when Op::kWsHid)
+//                    out = D2 = [A . I +] H . B2^T   (N2p = 128, or 16 / 32 columns)
+// With Op::kWsResid the residual (out = A + H B2^T) is added by the tensor cores: D2 starts as the BF16 pieces
 // of A times a 16 x 16 identity block (a_hi + a_lo, within 2^-18 |a| of the FP32 input), so
 // the output epilogue loads nothing.
 //
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
         sI[tc_off(n, k, 16) / 2] = __float2bfloat16(n == k ? 1.f : 0.f);
     }
     fence_async_smem();
+    pdl_launch_dependents();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    pdl_wait();                  // before any read of data an earlier kernel produced
     const unsigned tmem = tmem_base;
     auto tile_row0 = [&](int i) { return (blockIdx.x + (long)i * G) * TC_M; };
 
@@ -191,9 +195,9 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
             bool ok = true;
             bool b_pending = true;
             {
-                const unsigned bytes = (unsigned)WS_PIECE;
+                const unsigned bytes = (unsigned)WS_PIECE, bytes2 = (unsigned)w.N2p * WS_W * 2;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bbar)),
-                             "r"(4 * bytes) : "memory");
+                             "r"(WS_P * (bytes + bytes2)) : "memory");
 #pragma unroll
                 for (int p = 0; p < WS_P; ++p) {
                     asm volatile(
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
                             smem_u32(sB1 + p * WS_PIECE)), "l"(w.B1[p]), "r"(bytes), "r"(smem_u32(&bbar)) : "memory");
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            smem_u32(sB2 + p * WS_PIECE)), "l"(w.B2[p]), "r"(bytes), "r"(smem_u32(&bbar)) : "memory");
+                            smem_u32(sB2 + p * WS_PIECE)), "l"(w.B2[p]), "r"(bytes2), "r"(smem_u32(&bbar)) : "memory");
                 }
             }
             if (nt > 0) {
@@ -228,29 +232,33 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
                 for (int j = 0; j < 2; ++j)
                     tc_issue<WS_P>(tD1, a0 + j * 1024, WS_PIECE, WS_W * 16, b10 + j * (WS_W * 64 * 2), WS_PIECE,
                                    64 * 16, 64, WS_W, j == 0);
-                for (int j = 0; j < WS_W / 16; ++j)
+                if constexpr (Op::kWsResid)
+                    for (int j = 0; j < WS_W / 16; ++j)
 #pragma unroll
-                    for (int p = 0; p < WS_P; ++p)
-                        tc_mma(tD2 + (unsigned)(16 * j), tc_desc(a0 + p * WS_PIECE + j * 256, WS_W * 16), bdI,
-                               tc_idesc(TC_M, 16), p > 0 ? 1u : 0u);
+                        for (int p = 0; p < WS_P; ++p)
+                            tc_mma(tD2 + (unsigned)(16 * j), tc_desc(a0 + p * WS_PIECE + j * 256, WS_W * 16), bdI,
+                                   tc_idesc(TC_M, 16), p > 0 ? 1u : 0u);
                 tc_commit(&a_free);
                 tc_commit(&d1_full[s]);
             };
-            // GEMM2 of tile i: D2 += H . B2^T with H's pieces in tensor memory (K-block kk of
-            // piece q at column 16 kk + 8 q of the slot)
+            // GEMM2 of tile i: D2 (+)= H . B2^T with H's pieces in tensor memory (K-block kk of
+            // piece q at column 16 kk + 8 q of the slot); B2 chunks (K 64) are N2p x 64 apart
             auto gemm2 = [&](int i) {
                 const int s = i & 1;
                 const unsigned tH = tmem + (unsigned)(s * 256), tD2 = tH + 128;
                 tc_fence_after();
-                const unsigned idesc = tc_idesc(TC_M, WS_W);
+                const unsigned idesc = tc_idesc(TC_M, w.N2p);
+                bool acc = Op::kWsResid;
                 for (int kk = 0; kk < WS_W / 16; ++kk) {
-                    const unsigned boff = (unsigned)((kk >> 2) * (WS_W * 64 * 2) + (kk & 3) * 256);
+                    const unsigned boff = (unsigned)((kk >> 2) * (w.N2p * 64 * 2) + (kk & 3) * 256);
 #pragma unroll
                     for (int qa = 0; qa < WS_P; ++qa)
 #pragma unroll
-                        for (int qb = 0; qa + qb < WS_P; ++qb)
+                        for (int qb = 0; qa + qb < WS_P; ++qb) {
                             ws_mma_ta(tD2, tH + (unsigned)(16 * kk + 8 * qa),
-                                      tc_desc(b20 + qb * WS_PIECE + boff, 64 * 16), idesc, 1u);
+                                      tc_desc(b20 + qb * WS_PIECE + boff, 64 * 16), idesc, acc ? 1u : 0u);
+                            acc = true;
+                        }
                 }
                 tc_commit(&d2_full[s]);
             };
@@ -397,10 +405,11 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
                     ws_st16(tD1 + (unsigned)(c32 + 16 * kb), wd);
                 }
                 // stored hidden (FP32, masked D1)
-                ws_rows32(lane, v, [&](int r, int c, float4 x) {
-                    const int grow = q * 32 + r;
-                    if (row0 + grow < rows) op.store_hid4(rc[grow], c32 + c, x);
-                });
+                if constexpr (Op::kWsHid)
+                    ws_rows32(lane, v, [&](int r, int c, float4 x) {
+                        const int grow = q * 32 + r;
+                        if (row0 + grow < rows) op.store_hid4(rc[grow], c32 + c, x);
+                    });
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
@@ -421,14 +430,29 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
             if (!ws_bar_and(3, 32 * WS_NOUT, ok)) break;
             tc_fence_after();
             const unsigned tD2 = tmem + (unsigned)(s * 256) + 128 + lane_off;
+            bool wide = false;
+            if constexpr (Op::kHasOut4) wide = w.N2p == WS_W;
+            if (wide) {
+                if constexpr (Op::kHasOut4) {
 #pragma unroll 1
-            for (int c32 = 64 * half; c32 < 64 * half + 64; c32 += 32) {
+                    for (int c32 = 64 * half; c32 < 64 * half + 64; c32 += 32) {
+                        float v[32];
+                        tc_ld32(tD2 + (unsigned)c32, v);
+                        ws_rows32(lane, v, [&](int r, int c, float4 x) {
+                            const int grow = q * 32 + r;
+                            if (row0 + grow < rows) op.out4(rc[grow], c32 + c, x);
+                        });
+                    }
+                }
+            } else if (half == 0) {
+                // a few outputs per row (N2p <= 32): one lane per row, op.nout values
                 float v[32];
-                tc_ld32(tD2 + (unsigned)c32, v);
-                ws_rows32(lane, v, [&](int r, int c, float4 x) {
-                    const int grow = q * 32 + r;
-                    if (row0 + grow < rows) op.out4(rc[grow], c32 + c, x);
-                });
+                tc_ld32(tD2, v);
+                const int lrow = q * 32 + lane;
+                if (row0 + lrow < rows)
+#pragma unroll
+                    for (int n = 0; n < 32; ++n)
+                        if (n < op.nout) op.out(rc[lrow], n, v[n]);
             }
             tc_fence_before();
             ws_arrive(&out_free[s]);
