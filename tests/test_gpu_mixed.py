@@ -150,3 +150,28 @@ def test_bf16_form_runs(lib):
     prob.step(wl.x0)
     st = prob.read_stats()
     assert st["converged"] == 1 and st["kkt_prim"] <= 10 * wl.tol
+
+
+def test_mixed_linearize_multi_tile_against_fp32_form(lib):
+    """The split-BF16 reverse pass at a size where each persistent CTA walks many 128-row tiles
+    with a ragged last tile (chain of 150 nodes, K = 3, W = 128: about 1.6k tiles for the
+    largest reverse edge-MLP launch), against the FP32 form on the same inputs (the FP32 form
+    is pinned to the oracle element by element in test_gpu_parity).  Both reverse passes use
+    the forward ReLU pattern of their own rollout, so a few units near a kink may differ; the
+    test bounds the 99.99th percentile of the error and its maximum separately."""
+    from synth import paper_chain
+    wl = paper_chain(seed=3, M=150, N=4, nu=8)
+    u_hat = np.random.default_rng(4).uniform(-0.3, 0.3, (wl.N, wl.nu)).astype(np.float32)
+    out = {}
+    for prec in (0, GM_PREC_MIXED):
+        prob = lib.RTIProblem.from_workload(wl, precision=prec)
+        out[prec] = [t.cpu().numpy().astype(np.float64) for t in prob.linearize(wl.x0, u_hat)]
+        del prob
+    (xm, Am, Bm, cm), (xf, Af, Bf, cf) = out[GM_PREC_MIXED], out[0]
+    assert max_rel_err(xm, xf) <= 1e-5
+    for got, ref in ((Am, Af), (Bm, Bf)):
+        e = np.abs(got - ref) / np.abs(ref).max()
+        assert np.quantile(e, 0.9999) <= REL_MIXED and e.max() <= 5e-2, (np.quantile(e, 0.9999), e.max())
+    # c: a difference of larger terms, measured against x_hat's scale
+    e = np.abs(cm - cf) / np.abs(xf).max()
+    assert np.quantile(e, 0.9999) <= REL_MIXED, np.quantile(e, 0.9999)
