@@ -390,20 +390,23 @@ __host__ __device__ constexpr int tc_kc() {
     return TC_CHUNK;
 }
 
-// Shared memory: [A chunk | hidden tile] (the hidden tile reuses the A buffer once GEMM1
-// is done) followed by the B chunk (TC_NB rows x KC; GEMM2 products wider than TC_NB
-// stage half-K chunks of the same size).
-template <int W, int P>
-__host__ __device__ constexpr size_t tc_region_a() {
-    return (size_t)P * ((size_t)TC_M * tc_kc<P>() * 2 > (size_t)TC_M * W * 2 ? (size_t)TC_M * tc_kc<P>() * 2
-                                                                               : (size_t)TC_M * W * 2);
-}
-// Weight-chunk buffers (chunk g in buffer g % NBUF; the chunk NBUF ahead is copied as soon as
-// the MMAs that read a buffer have completed).  One: a second buffer for the three-piece
-// forward form measured no faster, the chunks being bound by the MMAs themselves.
+// Shared memory: [A chunk buffers | hidden tile] (the hidden tile reuses the A buffers once
+// GEMM1 is done) followed by the B chunk buffers (TC_NB rows x KC; GEMM2 products wider than
+// TC_NB stage half-K chunks of the same size).
+// Chunk pipeline depth: the A chunk and the weight chunk each get NBUF buffers (chunk g in
+// buffer g % NBUF; with two, chunk c + 1 is staged and its weights copied while chunk c
+// multiplies).  One: two buffers for the three-piece forward form take the CTA to 192 KB of
+// shared memory, and the smaller L1 left beside it slows the gathered node-row loads of the
+// forward more than the overlap gains (measured 0.6 ms per step slower).
 template <int P>
 __host__ __device__ constexpr int tc_nbuf() {
     return 1;
+}
+template <int W, int P>
+__host__ __device__ constexpr size_t tc_region_a() {
+    return (size_t)P * ((size_t)tc_nbuf<P>() * TC_M * tc_kc<P>() * 2 > (size_t)TC_M * W * 2
+                            ? (size_t)tc_nbuf<P>() * TC_M * tc_kc<P>() * 2
+                            : (size_t)TC_M * W * 2);
 }
 template <int W, int P>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
@@ -419,12 +422,12 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     constexpr int KC = tc_kc<P>();
     constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = TC_NB * KC * 2, H_BYTES = TC_M * W * 2;
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char* sA = tsm;                          // P pieces of the A chunk, K-major with K = KC
+    unsigned char* sA = tsm;                          // NBUF x P pieces of the A chunk, K-major with K = KC
     unsigned char* sH = tsm;                          // P pieces of the hidden tile, K = W (after GEMM1)
     constexpr int NBUF = tc_nbuf<P>();
     unsigned char* sB0 = tsm + tc_region_a<W, P>();   // NBUF buffers of P pieces of a B chunk (bulk copies)
     __shared__ RowCtx rc[TC_M];
-    __shared__ __align__(8) unsigned long long mbar;    // MMA completion (tcgen05.commit)
+    __shared__ __align__(8) unsigned long long mbar[tc_nbuf<P>()];   // MMA completion per buffer (tcgen05.commit)
     __shared__ __align__(8) unsigned long long bbar[NBUF];   // B chunk arrival (bulk-copy bytes)
     __shared__ unsigned tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -456,9 +459,11 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
         b_pending[b] = true;
     };
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
 #pragma unroll
-        for (int b = 0; b < NBUF; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[b])));
+        for (int b = 0; b < NBUF; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[b])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (int g = 0; g < NBUF && g < ng; ++g) load_b(g);              // first chunks, under the prologue
@@ -479,7 +484,17 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     // D1 [128 x W] and, once the hidden epilogue has read it, D2 [128 x N2p] in the same columns
     const unsigned tD = tmem_base;
     bool ok = true;
-    unsigned phase = 0;
+    unsigned mph[NBUF];                 // completed MMA commits per buffer barrier
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) mph[b] = 0;
+    // all threads: wait for the MMAs of chunk g (A buffer and B buffer g % NBUF are then free);
+    // thread 0 then copies the weight chunk NBUF ahead into the freed B buffer
+    auto wait_chunk = [&](int g) {
+        const int b = g % NBUF;
+        ok = tc_wait(&mbar[b], mph[b] & 1, w.status) && ok;
+        ++mph[b];
+        if (tid == 0 && ok && g + NBUF < ng && !b_pending[b]) load_b(g + NBUF);
+    };
     constexpr int CSTEP = 32 * (TC_T / 128);
     const int lrow = (warp & 3) * 32 + lane;
     const int cgrp = warp >> 2;
@@ -508,7 +523,7 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
         }
         if (okb)
             tc_issue<P>(tD, a0, a_piece, a_sbo, smem_u32(sB0 + (size_t)b * P * B_BYTES), B_BYTES, b_sbo, kc, N, first);
-        tc_commit(&mbar);
+        tc_commit(&mbar[b]);
         return okb;
     };
 
@@ -518,23 +533,25 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     constexpr bool kAhead = !kSingle;
     TcAReg<KC> xa;
     if (kAhead && nch > 0 && KC <= w.K1p) tc_load_a_full<KC>(op, rc, row0, rows, 0, tid, xa);
+    // Chunk c goes into A buffer c % NBUF, whose previous chunk (c - NBUF) was waited for at the
+    // end of iteration c - 1; chunk c's MMAs then run while chunk c + 1 is staged.
     for (int c = 0; c < nch; ++c) {
         const int k0 = c * KC;
         const int kc = min(KC, w.K1p - k0);        // multiple of 16
-        if (kAhead && kc == KC) tc_store_a_full<P, KC>(sA, A_BYTES, tid, xa);
-        else tc_stage_a<P, KC>(op, rc, row0, rows, sA, A_BYTES, k0, kc, tid);
+        unsigned char* sAc = sA + (size_t)(c % NBUF) * P * A_BYTES;
+        if (kAhead && kc == KC) tc_store_a_full<P, KC>(sAc, A_BYTES, tid, xa);
+        else tc_stage_a<P, KC>(op, rc, row0, rows, sAc, A_BYTES, k0, kc, tid);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (tid == 0) ok = issue(c, smem_u32(sA), A_BYTES, KC * 16, kc * 16, kc, W, c == 0) && ok;
+        if (tid == 0) ok = issue(c, smem_u32(sAc), A_BYTES, KC * 16, kc * 16, kc, W, c == 0) && ok;
         if (kAhead && k0 + 2 * KC <= w.K1p) tc_load_a_full<KC>(op, rc, row0, rows, k0 + KC, tid, xa);
-        ok = tc_wait(&mbar, phase & 1, w.status) && ok;   // A and B buffers are free again
-        ++phase;
-        // the buffer chunk c used is free again: the chunk NBUF ahead goes into it (for the
-        // last GEMM1 chunks these are the first GEMM2 chunks, copied under the epilogue)
-        if (tid == 0 && ok && c + NBUF < ng && !b_pending[c % NBUF]) load_b(c + NBUF);
+        // the chunk NBUF - 1 back has finished: its buffers take chunk c + 1 (A) and the weight
+        // chunk NBUF ahead of it (for the last GEMM1 chunks, the first GEMM2 chunks)
+        if (c - NBUF + 1 >= 0) wait_chunk(c - NBUF + 1);
     }
+    for (int g = max(0, nch - NBUF + 1); g < nch; ++g) wait_chunk(g);   // GEMM1 complete
     ok = __syncthreads_and(ok) != 0;           // warp-collective TMEM loads below need a uniform decision
     tc_fence_after();
 
@@ -597,10 +614,9 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
             // hidden tile: K-major with K = W; the chunk starts k0/8 core matrices along K
             const int g = nch + k0 / kc2;
             if (tid == 0) ok = issue(g, smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, kc * 16, kc, w.N2p, k0 == 0) && ok;
-            ok = tc_wait(&mbar, phase & 1, w.status) && ok;
-            ++phase;
-            if (tid == 0 && ok && g + NBUF < ng && !b_pending[g % NBUF]) load_b(g + NBUF);
+            if (g - NBUF + 1 >= nch) wait_chunk(g - NBUF + 1);
         }
+        for (int g = max(nch, ng - NBUF + 1); g < ng; ++g) wait_chunk(g);   // GEMM2 complete
         ok = __syncthreads_and(ok) != 0;
         tc_fence_after();
         if constexpr (Op::kHasOut4) {
