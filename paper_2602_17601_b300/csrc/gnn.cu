@@ -379,20 +379,24 @@ static gm_status launch_tc_w(int W, const Op& op, const TcW& tw, cudaStream_t st
     }
 }
 
-// Reverse edge-update and edge-encoder MLPs in the mixed form at W = 128: the
+// Reverse edge-update, edge-encoder and node-encoder MLPs in the mixed form at W = 128: the
 // warp-specialised persistent kernel (tc_ws.cuh), one CTA per SM.
 template <class Op>
 static gm_status launch_ws_bwd(const gm_ctx* c, const Op& op, const TcW& tw, cudaStream_t st) {
     if (op.rows <= 0) return GM_OK;
+    if (WsLayout<Op>::kLand && tw.N2p != WS_N2_LAND) {
+        set_error("landing form of the warp-specialised MLP needs N2p = %d (got %d)", WS_N2_LAND, tw.N2p);
+        return GM_ERR_INVALID_ARG;
+    }
     static bool attr_set = false;
     if (!attr_set) {
         GM_CUDA_TRY(cudaFuncSetAttribute(tc_ws_bwd_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)WS_SMEM));
+                                         (int)WsLayout<Op>::smem));
         attr_set = true;
     }
     const long tiles = cdiv(op.rows, TC_M);
     const int grid = (int)std::min<long>(tiles, std::max(1, c->num_sms));
-    GM_CUDA_TRY(launch_pdl(tc_ws_bwd_kernel<Op>, dim3((unsigned)grid), dim3(WS_T), WS_SMEM, st, op, tw));
+    GM_CUDA_TRY(launch_pdl(tc_ws_bwd_kernel<Op>, dim3((unsigned)grid), dim3(WS_T), WsLayout<Op>::smem, st, op, tw));
     GM_LAUNCH_CHECK();
     return GM_OK;
 }
@@ -534,6 +538,7 @@ struct BwdBase {
     static constexpr bool kHasResid = false;   // out4 value = resid4 + product (loads first)
     static constexpr bool kWsHid = false;      // warp-specialised kernel: store the masked hidden
     static constexpr bool kWsResid = false;    // warp-specialised kernel: out = A + product
+    static constexpr bool kWsLand = false;     // warp-specialised kernel: rows by bulk copy (land_row)
     long rows;
     int kin, nout;
     const float *B1, *b1 = nullptr, *B2, *b2 = nullptr;
@@ -749,6 +754,9 @@ struct NodeEncBwd : BwdBase {
     __device__ void out(const RowCtx& x, int n, float v) const { dxn[(long)x.e * nout + n] = v; }
     static constexpr bool kHasIn8 = true;
     __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(dh + (long)x.e * W + k0, v); }
+    // warp-specialised kernel: the input row arrives whole by bulk copy
+    static constexpr bool kWsLand = true;
+    __device__ const float* land_row(const RowCtx& x) const { return dh + (long)x.e * W; }
 };
 
 struct EdgeEncBwd : BwdBase {
@@ -767,13 +775,9 @@ struct EdgeEncBwd : BwdBase {
     __device__ void out(const RowCtx& x, int n, float v) const { dd[(long)x.e * 6 + n] = v; }
     static constexpr bool kHasIn8 = true;
     __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(de + (long)x.e * W + k0, v); }
-    // warp-specialised producer: one input row (b stays zero, nothing loaded for it)
-    __device__ void in8_pair(const RowCtx& x, int k0, float4* a, float4* b) const {
-        const float* pa = de + (long)x.e * W + k0;
-        a[0] = __ldg(reinterpret_cast<const float4*>(pa));
-        a[1] = __ldg(reinterpret_cast<const float4*>(pa + 4));
-        b[0] = b[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    // warp-specialised kernel: the input row arrives whole by bulk copy
+    static constexpr bool kWsLand = true;
+    __device__ const float* land_row(const RowCtx& x) const { return de + (long)x.e * W; }
 };
 
 // One warp per (stage, seed s): A^{s n}, B^s and c^s from the pulled-back cotangents.
@@ -986,7 +990,12 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
             NodeEncBwd op{};
             fill_bwd(op, c, c->mlp[0], k0, 0, false, (long)Ns * RK * 3, RK);
             op.dh = X; op.dxn = c->d_dxn; op.nr_node = d.nr_node[K];
-            GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[0]), st));
+            const TcW tw = tc_bwd(c, c->mlp[0]);
+            if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_N2_LAND) {
+                GM_TRY(launch_ws_bwd(c, op, tw, st));
+            } else {
+                GM_TRY(launch_mlp(c, op, tw, st));
+            }
         }
         const int RE = d.er_count[K - 1];
         if (RE > 0) {
@@ -994,7 +1003,7 @@ gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float
             fill_bwd(op, c, c->mlp[1], k0, 0, true, (long)Ns * RE * 3, RE);
             op.de = de_in; op.dd = c->d_dd; op.er_edge = d.er_edge[K - 1];
             const TcW tw = tc_bwd(c, c->mlp[1]);
-            if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p <= 32) {
+            if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_N2_LAND) {
                 GM_TRY(launch_ws_bwd(c, op, tw, st));
             } else {
                 GM_TRY(launch_mlp(c, op, tw, st));

@@ -1,6 +1,7 @@
 // Warp-specialised persistent form of a reverse two-layer MLP (W = 128, two BF16 pieces):
 // the edge-update reverse step (stored hidden cotangent, residual output, 128 outputs) and
-// the edge-encoder reverse step (no stored hidden, no residual, a few outputs).
+// the edge- and node-encoder reverse steps (no stored hidden, no residual, a few outputs;
+// their input rows arrive whole by bulk copy into a landing tile, Op::kWsLand).
 //
 // Per 128-row tile:  D1  = A . B1^T            (A: the row cotangents, K = 128)
 //                    H   = mask . D1           (ReLU mask of the forward pass; stored as FP32
@@ -48,13 +49,25 @@ constexpr int WS_HID0 = 12, WS_NHID = 8;   // hidden-epilogue warps 12..19
 constexpr int WS_OUT0 = 20, WS_NOUT = 8;   // output-epilogue warps 20..27
 constexpr int WS_PIECE = TC_M * WS_W * 2;  // bytes of one BF16 piece of a 128 x 128 operand
 constexpr int WS_NRC = 4;                  // row-context slots
-constexpr size_t WS_OFF_B1 = 0;
-constexpr size_t WS_OFF_B2 = WS_OFF_B1 + (size_t)WS_P * WS_PIECE;
-constexpr size_t WS_OFF_A = WS_OFF_B2 + (size_t)WS_P * WS_PIECE;
-constexpr size_t WS_OFF_RC = WS_OFF_A + (size_t)WS_P * WS_PIECE;
-constexpr size_t WS_OFF_ID = WS_OFF_RC + (size_t)WS_NRC * TC_M * sizeof(RowCtx);   // 16 x 16 identity
-constexpr size_t WS_SMEM = WS_OFF_ID + 16 * 16 * 2;
-static_assert(WS_SMEM <= 226 * 1024, "warp-specialised MLP exceeds the shared memory of one CTA");
+constexpr int WS_LROW = WS_W + 4;          // landing-tile row pitch (floats): 512 bytes + 16 of pad
+constexpr int WS_N2_LAND = 16;             // GEMM2 width of the landing form
+
+// Shared-memory layout of one op: [B1 | B2 | A | landing tile | row contexts | identity].
+// Ops with kWsLand (one contiguous 512-byte input row per tile row, GEMM2 of 16 columns) keep
+// a small B2 and an FP32 landing tile that per-row bulk copies fill one tile ahead.
+template <class Op>
+struct WsLayout {
+    static constexpr bool kLand = Op::kWsLand;
+    static constexpr size_t b2_piece = kLand ? (size_t)WS_N2_LAND * WS_W * 2 : (size_t)WS_PIECE;
+    static constexpr size_t off_b1 = 0;
+    static constexpr size_t off_b2 = off_b1 + (size_t)WS_P * WS_PIECE;
+    static constexpr size_t off_a = off_b2 + (size_t)WS_P * b2_piece;
+    static constexpr size_t off_land = off_a + (size_t)WS_P * WS_PIECE;
+    static constexpr size_t off_rc = off_land + (kLand ? (size_t)TC_M * WS_LROW * 4 : 0);
+    static constexpr size_t off_id = off_rc + (size_t)WS_NRC * TC_M * sizeof(RowCtx);   // 16 x 16 identity
+    static constexpr size_t smem = off_id + 16 * 16 * 2;
+    static_assert(smem <= 226 * 1024, "warp-specialised MLP exceeds the shared memory of one CTA");
+};
 
 __device__ __forceinline__ bool ws_bar_and(int id, int n, bool p) {
     unsigned r;
@@ -65,6 +78,7 @@ __device__ __forceinline__ bool ws_bar_and(int id, int n, bool p) {
         : "memory");
     return r != 0;
 }
+__device__ __forceinline__ void ws_bar_sync(int id, int n) { asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ void ws_arrive(void* mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
@@ -140,12 +154,14 @@ __device__ __forceinline__ void ws_rows32(int lane, const float* v, F&& store) {
 template <class Op>
 __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
     extern __shared__ __align__(1024) unsigned char wsm[];
-    unsigned char* sB1 = wsm + WS_OFF_B1;
-    unsigned char* sB2 = wsm + WS_OFF_B2;
-    unsigned char* sA = wsm + WS_OFF_A;
-    RowCtx* rcs = reinterpret_cast<RowCtx*>(wsm + WS_OFF_RC);          // [WS_NRC][TC_M]
-    __nv_bfloat16* sI = reinterpret_cast<__nv_bfloat16*>(wsm + WS_OFF_ID);
-    __shared__ __align__(8) unsigned long long bbar, a_full, a_free, fin;
+    using LY = WsLayout<Op>;
+    unsigned char* sB1 = wsm + LY::off_b1;
+    unsigned char* sB2 = wsm + LY::off_b2;
+    unsigned char* sA = wsm + LY::off_a;
+    float* sL = reinterpret_cast<float*>(wsm + LY::off_land);          // [TC_M][WS_LROW] (kWsLand)
+    RowCtx* rcs = reinterpret_cast<RowCtx*>(wsm + LY::off_rc);          // [WS_NRC][TC_M]
+    __nv_bfloat16* sI = reinterpret_cast<__nv_bfloat16*>(wsm + LY::off_id);
+    __shared__ __align__(8) unsigned long long bbar, a_full, a_free, fin, land_full;
     __shared__ __align__(8) unsigned long long d1_full[2], h_full[2], d2_full[2], out_free[2];
     __shared__ __align__(8) unsigned long long rc_full[WS_NRC], rc_free[WS_NRC];
     __shared__ unsigned tmem_base;
@@ -158,7 +174,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
         auto init = [](unsigned long long* b, unsigned n) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(n));
         };
-        init(&bbar, 1); init(&a_full, 32 * WS_NPROD); init(&a_free, 1); init(&fin, 1);
+        init(&bbar, 1); init(&a_full, 32 * WS_NPROD); init(&a_free, 1); init(&fin, 1); init(&land_full, 1);
         for (int k = 0; k < 2; ++k) {
             init(&d1_full[k], 1);
             init(&h_full[k], 32 * WS_NHID);
@@ -205,7 +221,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
                             smem_u32(sB1 + p * WS_PIECE)), "l"(w.B1[p]), "r"(bytes), "r"(smem_u32(&bbar)) : "memory");
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            smem_u32(sB2 + p * WS_PIECE)), "l"(w.B2[p]), "r"(bytes2), "r"(smem_u32(&bbar)) : "memory");
+                            smem_u32(sB2 + p * LY::b2_piece)), "l"(w.B2[p]), "r"(bytes2), "r"(smem_u32(&bbar)) : "memory");
                 }
             }
             if (nt > 0) {
@@ -256,7 +272,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
 #pragma unroll
                         for (int qb = 0; qa + qb < WS_P; ++qb) {
                             ws_mma_ta(tD2, tH + (unsigned)(16 * kk + 8 * qa),
-                                      tc_desc(b20 + qb * WS_PIECE + boff, 64 * 16), idesc, acc ? 1u : 0u);
+                                      tc_desc(b20 + qb * (unsigned)LY::b2_piece + boff, 64 * 16), idesc, acc ? 1u : 0u);
                             acc = true;
                         }
                 }
@@ -317,6 +333,74 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
         };
         bool ok = true;
         if (nt > 0) prep(0);
+        if constexpr (LY::kLand) {
+            // Landing form: thread m < 128 bulk-copies tile row m (512 bytes) into the padded
+            // landing tile, the byte count registered on land_full by thread 0; the group then
+            // splits the landed tile into the A buffer.  The next tile's rows are copied as soon
+            // as this one has been read, so they land while this tile's MMAs and epilogues run.
+            int issued = 0, landed = 0;
+            auto issue_rows = [&](int i) {
+                const long row0 = tile_row0(i);
+                const int vr = (int)min((long)TC_M, rows - row0);
+                if (ptid == 0)
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&land_full)),
+                                 "r"((unsigned)vr * WS_W * 4) : "memory");
+                if (ptid < vr) {
+                    const RowCtx* rc = rcs + (i % WS_NRC) * TC_M;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(sL + ptid * WS_LROW)), "l"(op.land_row(rc[ptid])), "r"((unsigned)WS_W * 4),
+                        "r"(smem_u32(&land_full)) : "memory");
+                }
+                ++issued;
+            };
+            if (nt > 0) issue_rows(0);                  // thread m reads only its own row's context
+            for (int i = 0; i < nt; ++i) {
+                const long row0 = tile_row0(i);
+                ok = ws_wait(&land_full, i & 1, w.status) && ok;
+                if (ok) ++landed;
+                if (i >= 1) ok = ws_wait(&a_free, (i - 1) & 1, w.status) && ok;   // GEMM1 of the last tile done
+                if (!ws_bar_and(1, NP, ok)) break;
+#pragma unroll
+                for (int j = 0; j < NVT; ++j) {
+                    const int v = ptid + j * NP;
+                    if (v < NV) {
+                        int m, kv;
+                        tc_vec_rc(v, WS_W / 8, m, kv);
+                        float x8[8];
+                        if (row0 + m < rows) {
+                            const float4 u0 = *reinterpret_cast<const float4*>(sL + m * WS_LROW + kv * 8);
+                            const float4 u1 = *reinterpret_cast<const float4*>(sL + m * WS_LROW + kv * 8 + 4);
+                            x8[0] = u0.x; x8[1] = u0.y; x8[2] = u0.z; x8[3] = u0.w;
+                            x8[4] = u1.x; x8[5] = u1.y; x8[6] = u1.z; x8[7] = u1.w;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) x8[e] = 0.f;
+                        }
+                        uint4 pc[WS_P];
+                        pack8<WS_P>(x8, pc);
+                        const int o = tc_off(m, kv * 8, WS_W);
+#pragma unroll
+                        for (int p = 0; p < WS_P; ++p) *reinterpret_cast<uint4*>(sA + p * WS_PIECE + o) = pc[p];
+                    }
+                }
+                fence_async_smem();
+                ws_bar_sync(4, NP);                    // the landing tile has been read by every thread
+                ws_arrive(&a_full);
+                const int in = i + 1;
+                if (in < nt) {
+                    if (in >= WS_NRC) ok = ws_wait(&rc_free[in % WS_NRC], ((in / WS_NRC) - 1) & 1, w.status) && ok;
+                    if (!ws_bar_and(1, NP, ok)) break;
+                    prep(in);
+                    issue_rows(in);
+                }
+            }
+            // copies still landing after a failed wait finish before the CTA exits
+            while (landed < issued) {
+                ws_wait(&land_full, landed & 1, nullptr);
+                ++landed;
+            }
+        } else {
         for (int i = 0; i < nt; ++i) {
             const long row0 = tile_row0(i);
             const RowCtx* rc = rcs + (i % WS_NRC) * TC_M;
@@ -365,6 +449,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
             for (int j = H1; j < NVT; ++j) store(j);
             fence_async_smem();
             ws_arrive(&a_full);
+        }
         }
     } else if (warp < WS_OUT0) {
         // ------------------------------------------------------------------ hidden epilogue
