@@ -283,6 +283,27 @@ gm_status gm_qp_solve(gm_ctx* ctx, const float* H, const float* g, const float* 
                       gm_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------
+ * gm_qp_solve_ipm — the same QP by a primal-dual interior-point method (the
+ *   solver class of the paper's controller, Sec. VI-A), for comparison with
+ *   ADMM: Mehrotra predictor-corrector on G U <= h with G = [I; -I; S C~],
+ *   h = [u_hi; -u_lo; S d~] (S the row scales 1/|C~_r|), slacks s > 0 and
+ *   duals z > 0.  Each iteration forms Phi = H + G'diag(z/s)G (FP32 Gram),
+ *   factors it in FP64 and solves the predictor and corrector systems in
+ *   FP64.  Stops when |G U + s - h|_inf, |H U + g + G'z|_inf and max_i s_i z_i
+ *   are all <= settings.tol, or after max_iter iterations (1..1000).
+ *   Arguments as gm_qp_solve (no warm start); y [nU + N M n_c] (out, nullable)
+ *   receives z_hi - z_lo for the box rows and S z for the half-space rows.
+ *   stats: iters, converged, r_prim = |r_p|_inf, r_dual = |r_d|_inf of the
+ *   last iterate, and the FP64 KKT certificate of (U, y).  The host reads a
+ *   device flag every two iterations (stream synchronisation), so this call
+ *   cannot be captured into a CUDA graph.
+ * Returns GM_OK even when it did not converge; stats->status says so.
+ * ---------------------------------------------------------------------- */
+gm_status gm_qp_solve_ipm(gm_ctx* ctx, const float* H, const float* g, const float* Ct,
+                          const float* dt, const float* u_lo, const float* u_hi, int max_iter,
+                          float* U, float* y, gm_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
  * gm_rti_step — one iteration of Algorithm 1 on the device:
  *   u_hat <- context trajectory (zero after gm_ctx_create / gm_ctx_reset,
  *            else the shifted previous solution (U*_1..U*_{N-1}, U*_{N-1}));

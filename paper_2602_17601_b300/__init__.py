@@ -102,6 +102,7 @@ def _load():
         "gm_condense": ([vp, vp, vp, vp, vp, C.POINTER(Cost), C.POINTER(Constr), vp, vp, vp, vp, vp],
                         C.c_int),
         "gm_qp_solve": ([vp] * 12 + [vp], C.c_int),
+        "gm_qp_solve_ipm": ([vp] * 7 + [C.c_int] + [vp] * 4, C.c_int),
         "gm_rti_step": ([vp, vp, C.POINTER(Cost), C.POINTER(Constr), vp, vp, vp, vp], C.c_int),
         "gm_ctx_reset": ([vp, vp], C.c_int),
         "gm_ctx_info": ([vp, C.POINTER(Info)], C.c_int),
@@ -140,7 +141,7 @@ _lib = _load()
 HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_destroy",
                     "gm_gnn_load", "gm_gnn_destroy", "gm_ctx_workspace_size", "gm_ctx_create",
                     "gm_ctx_destroy", "gm_jac_pattern", "gm_linearize", "gm_condense",
-                    "gm_qp_solve", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
+                    "gm_qp_solve", "gm_qp_solve_ipm", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
                     "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count", "gm_qp_solve_noalloc",
                     "gm_ctx_set_graph", "gm_ctx_graph_state", "gm_ctx_set_kernel_timing",
                     "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
@@ -335,6 +336,12 @@ def gm_condense(ctx, x_hat, A, B, c, cost, constr, H, g, Ct=None, dt=None, strea
     _check("gm_condense", _lib.gm_condense(ctx, _ptr(x_hat), _ptr(A), _ptr(B), _ptr(c), C.byref(cost),
                                            C.byref(constr), _ptr(H), _ptr(g), _ptr(Ct), _ptr(dt),
                                            _stream(stream)))
+
+
+def gm_qp_solve_ipm(ctx, H, g, Ct, dt, u_lo, u_hi, U, y=None, stats=None, max_iter=60, stream=None):
+    _check("gm_qp_solve_ipm", _lib.gm_qp_solve_ipm(ctx, _ptr(H), _ptr(g), _ptr(Ct), _ptr(dt), _ptr(u_lo),
+                                                   _ptr(u_hi), int(max_iter), _ptr(U), _ptr(y), _ptr(stats),
+                                                   _stream(stream)))
 
 
 def gm_qp_solve(ctx, H, g, Ct, dt, u_lo, u_hi, U, y=None, stats=None, warm_U=None, warm_y=None,

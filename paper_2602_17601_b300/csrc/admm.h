@@ -73,6 +73,11 @@ struct AdmmPlan {
 };
 
 gm_status admm_solve(const AdmmPlan& p);
+
+// Interior-point solve of the same QP (ipm.cu): workspace sizes of its row and vector arrays.
+constexpr int kIpmRowArrays = 7;
+constexpr int kIpmVecArrays = 16;
+constexpr int kIpmScalars = 32;
 size_t admm2_smem_bytes(int n);
 const void* admm2_kernel_ptr(int n);
 

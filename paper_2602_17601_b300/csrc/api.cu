@@ -345,6 +345,8 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_row_begin = cv.take<int>(kMaxAdmmGrid + 1);
     c->d_kkt = cv.take<double>(nU + 4);
     c->d_stats = cv.take<gm_stats>(1);
+    c->d_ipm_rows = cv.take<double>((size_t)kIpmRowArrays * std::max(1L, c->rows_c));
+    c->d_ipm_vec = cv.take<double>((size_t)kIpmVecArrays * nU + kIpmScalars);
 }
 
 }  // namespace gmi

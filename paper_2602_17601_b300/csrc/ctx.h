@@ -126,7 +126,9 @@ struct gm_ctx {
     double *d_L = nullptr, *d_Linv = nullptr;
     float *d_P = nullptr, *d_Pinv = nullptr, *d_G = nullptr;
     gmi::AdmmState* d_admm = nullptr;
-    float *d_acc = nullptr;      // ADMM reduction buffers [3][2 nU + 2]
+    float *d_acc = nullptr;      // ADMM reduction buffers [3][admm_acc_stride(nU)]
+    double* d_ipm_rows = nullptr; // interior-point row arrays [kIpmRowArrays][max(rows, 1)]
+    double* d_ipm_vec = nullptr; // interior-point vectors [kIpmVecArrays][nU] + scalars
     unsigned* d_bar = nullptr;   // grid barrier counters
     int* d_status = nullptr;     // device status word(s)
     int* d_row_begin = nullptr;  // ADMM row partition [grid+1]

@@ -44,6 +44,18 @@ gm_status ws_features(gm_ctx* c, const float* h, const float* x_ref, float* feat
 int gram_blocks(int n);
 int gram_split(int n, int sms, int cap);
 gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStream_t st);
+// qp.cu: row scales 1/|C~_r| and the FP64 KKT certificate of (U, y)
+__global__ void row_norm_kernel(long rows, int nu, int Mnc, const float* __restrict__ Ct, float* __restrict__ rs);
+__global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* __restrict__ Ct,
+                                const float* __restrict__ dt, const float* __restrict__ U,
+                                const float* __restrict__ y, double* kkt);
+__global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float* __restrict__ g,
+                                 const float* __restrict__ lo, const float* __restrict__ hi,
+                                 const float* __restrict__ U, const float* __restrict__ y,
+                                 const double* __restrict__ kkt, const int* status, gm_stats* stats);
+// ipm.cu: interior-point solve of the condensed QP
+gm_status ipm_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, const float* dt, const float* u_lo,
+                    const float* u_hi, int max_iter, float* U, float* y, gm_stats* stats, cudaStream_t st);
 __global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
                                    const float* __restrict__ diag_add, float diag_scale,
                                    float* __restrict__ G);

@@ -10,7 +10,7 @@ import numpy as np
 
 from . import (GM_PREC_FP32, STATS_BYTES, gm_condense, gm_ctx_create, gm_ctx_destroy, gm_ctx_graph_state,
                gm_ctx_reset, gm_ctx_set_graph, gm_ctx_workspace_size, gm_gnn_destroy, gm_gnn_load, gm_graph_create, gm_graph_destroy,
-               gm_jac_pattern, gm_linearize, gm_qp_solve, gm_rti_step, make_constr, make_cost,
+               gm_jac_pattern, gm_linearize, gm_qp_solve, gm_qp_solve_ipm, gm_rti_step, make_constr, make_cost,
                make_settings, read_stats)
 
 
@@ -114,6 +114,14 @@ class RTIProblem:
         y = self.empty(self.nU + self.rows_c)
         gm_qp_solve(self.ctx, H, g, Ct if self.n_c else None, dt if self.n_c else None, self.u_lo,
                     self.u_hi, U, y, self.stats, warm_U, warm_y)
+        return U, y
+
+    def qp_solve_ipm(self, H, g, Ct=None, dt=None, max_iter=60):
+        """The same QP by the interior-point method (gm_qp_solve_ipm)."""
+        U = self.empty(self.nU)
+        y = self.empty(self.nU + self.rows_c)
+        gm_qp_solve_ipm(self.ctx, H, g, Ct if self.n_c else None, dt if self.n_c else None, self.u_lo,
+                        self.u_hi, U, y, self.stats, max_iter)
         return U, y
 
     def step(self, x_meas, U=None, u0=None):
