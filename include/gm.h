@@ -378,9 +378,11 @@ gm_status gm_ctx_set_graph(gm_ctx* ctx, int on);
  * i with (x_meas[i], costs[i], cons[i], U[i], stats[i]).  The first call runs
  * the instances one after another with plain launches; the next captures
  * every instance's step as a child graph of one parent graph with no
- * dependencies between instances, and every later call with the same
- * arguments replays that graph with a single launch on the stream, the
- * instances' kernels running side by side.  Changing any argument captures
+ * instances in L lanes (instance i after instance i - L, L = SMs / the
+ * largest cooperative ADMM or factor grid of the members, so that the
+ * cooperative grids of the steps running at once fit on the SMs together),
+ * and every later call with the same arguments replays that graph with a
+ * single launch on the stream, the lanes running side by side.  Changing any argument captures
  * anew.  x_meas, U, stats: host arrays of n device pointers (stats may be
  * NULL); costs, cons: host arrays of n structs.  Contexts of a batch must not
  * be stepped elsewhere while the batch runs.  gm_batch_state: as
@@ -391,6 +393,8 @@ void gm_batch_destroy(gm_batch* b);
 gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_cost* costs, const gm_constr* cons,
                             float* const* U, gm_stats* const* stats, void* stream);
 gm_status gm_batch_state(const gm_batch* b, int* replayed, int* captures);
+/* Lanes of the last captured batch graph (1 before the first capture). */
+gm_status gm_batch_lanes(const gm_batch* b, int* lanes);
 gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures);
 
 /* Launch timing of the dominant kernel, the reverse edge-update MLP (one launch per

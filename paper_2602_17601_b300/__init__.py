@@ -127,6 +127,7 @@ def _load():
         "gm_batch_destroy": ([vp], None),
         "gm_batch_rti_step": ([vp, C.POINTER(vp), vp, vp, C.POINTER(vp), C.POINTER(vp), vp], C.c_int),
         "gm_batch_state": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+        "gm_batch_lanes": ([vp, C.POINTER(C.c_int)], C.c_int),
         "gm_ctx_kernel_stats": ([vp, C.POINTER(C.c_int)] + [C.POINTER(C.c_double)] * 3, C.c_int),
         "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
@@ -147,7 +148,8 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
                     "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
-                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_rollout")
+                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes",
+                    "gm_rollout")
 
 GM_NOALLOC_MAX_NU = 64
 GM_NOALLOC_MAX_ROWS = 8192

@@ -50,6 +50,11 @@ class Batch:
         _check("gm_batch_state", _lib.gm_batch_state(self.h, C.byref(r), C.byref(n)))
         return r.value, n.value
 
+    def lanes(self):
+        n = C.c_int()
+        _check("gm_batch_lanes", _lib.gm_batch_lanes(self.h, C.byref(n)))
+        return n.value
+
     def U(self, i):
         return self.problems[i]._U
 
@@ -147,9 +152,10 @@ def main(argv=None):
            "steps": a.steps, "sequential_ms_per_batch_step": ms_seq, "batched_ms_per_batch_step": ms_batch,
            "sequential_instance_steps_per_s": a.n * 1000.0 / ms_seq,
            "batched_instance_steps_per_s": a.n * 1000.0 / ms_batch, "speedup": ms_seq / ms_batch,
-           "graph": dict(zip(("replayed", "captures"), batch.state())),
+           "graph": dict(zip(("replayed", "captures"), batch.state())), "lanes": batch.lanes(),
            "converged": int(sum(s["converged"] for s in st)), "status_nonzero": int(sum(s["status"] != 0 for s in st)),
            "infeasible": int(sum(s["status"] == GM_ERR_INFEASIBLE for s in st)),
+           "status_counts": {str(k): int(v) for k, v in zip(*np.unique([s["status"] for s in st], return_counts=True))},
            "admm_iters_mean": float(np.mean([s["iters"] for s in st])), "admm_max_iter": a.max_iter,
            "admm_iters_converged_mean": float(np.mean([s["iters"] for s in st if s["converged"]] or [0])),
            "workspace_gb": float(sum(p.workspace.numel() for p in probs) / 2**30),

@@ -85,6 +85,7 @@ const void* admm2_kernel_ptr(int n);
 // (factor.cu); gate (nullable) skips it when no factorisation is due.  L and Linv hold
 // factor_pad(n)^2 doubles; bar[0] is used (and reset) as the grid barrier counter.
 int factor_pad(int n);
+int factor_grid();            // default CTAs of the factor kernel (cooperative)
 gm_status factor_pinv(int n, const float* P, double* L, double* Linv, float* Pinv, int* status,
                       const AdmmState* gate, unsigned* bar, long long max_spins, int grid, cudaStream_t st);
 

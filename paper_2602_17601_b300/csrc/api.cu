@@ -840,6 +840,11 @@ gm_status gm_batch_create(gm_ctx* const* ctxs, int n, gm_batch** out) {
     }
     gm_batch* b = new gm_batch;
     b->ctx.assign(ctxs, ctxs + n);
+    // side by side, instances fill the GPU: programmatic early launches would only hold SMs
+    for (int i = 0; i < n; ++i) {
+        ctxs[i]->pdl = false;
+        ctxs[i]->graph_key.clear();      // a context graph captured earlier is re-captured without it
+    }
     *out = b;
     return GM_OK;
 }
@@ -875,16 +880,30 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
                             st, false));
         return GM_OK;
     }
-    // every instance's step as a child graph of one parent, no edges between instances
+    // Every instance's step as a child graph of one parent, in L lanes: instance i follows
+    // instance i - L.  A step holds cooperative launches (the ADMM and factor grids), and
+    // cooperative grids running side by side can each hold part of their CTAs resident while
+    // waiting for the rest, so L is chosen such that the grids of L steps fit on the SMs at
+    // once (otherwise such a standoff lasts until a grid barrier's bound runs out).
+    int gmax = 1;
+    for (int i = 0; i < n; ++i) {
+        const gm_ctx* c = b->ctx[i];
+        const int fg = c->s.factor_grid > 0 ? std::max(2, std::min(c->s.factor_grid, factor_grid())) : factor_grid();
+        gmax = std::max(gmax, std::max(c->admm_grid, fg));
+    }
+    const int lanes = std::max(1, std::min(n, std::max(1, b->ctx[0]->num_sms) / gmax));
+    b->lanes = lanes;
     cudaGraph_t parent = nullptr;
     GM_CUDA_TRY(cudaGraphCreate(&parent, 0));
     gm_status r = GM_OK;
+    std::vector<cudaGraphNode_t> nodes(n);
     for (int i = 0; i < n && r == GM_OK; ++i) {
         cudaGraph_t g = nullptr;
         r = capture_step(b->ctx[i], x_meas[i], &costs[i], &cons[i], U[i], nullptr, stats ? stats[i] : nullptr, &g);
         if (r != GM_OK) break;
-        cudaGraphNode_t node;
-        if (cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, g) != cudaSuccess) {
+        cudaGraphNode_t& node = nodes[i];
+        const cudaGraphNode_t* dep = i >= lanes ? &nodes[i - lanes] : nullptr;
+        if (cudaGraphAddChildGraphNode(&node, parent, dep, dep ? 1 : 0, g) != cudaSuccess) {
             set_error("adding instance %d to the batch graph failed", i);
             r = GM_ERR_CUDA;
         }
@@ -903,6 +922,13 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
     ++b->captures;
     GM_CUDA_TRY(cudaGraphLaunch(b->exec, st));
     b->replayed = true;
+    return GM_OK;
+}
+
+gm_status gm_batch_lanes(const gm_batch* b, int* lanes) {
+    clear_error();
+    GM_CHECK_ARG(b && lanes, "NULL argument");
+    *lanes = b->lanes;
     return GM_OK;
 }
 

@@ -22,6 +22,7 @@ struct gm_ctx;
 // A batch of contexts stepped as one CUDA graph (gm_batch_rti_step).
 struct gm_batch {
     std::vector<gm_ctx*> ctx;
+    int lanes = 1;                 // independent chains of instance steps in the batch graph
     cudaGraphExec_t exec = nullptr;
     std::vector<uintptr_t> key;
     int eager = 0, captures = 0;
@@ -89,6 +90,7 @@ struct gm_ctx {
     long rows_c = 0;          // N * M * n_c
     long ct_len = 0;          // packed C~ length
     int num_sms = 0;
+    bool pdl = true;             // programmatic dependent launch of the MLP kernels (off in a batch)
     int stage_chunk = 1;      // stages per reverse-pass launch group
 
     // host copies

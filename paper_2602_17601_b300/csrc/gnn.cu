@@ -333,11 +333,13 @@ __global__ void agg_kernel(int M, int W, const int* __restrict__ in_ptr, const f
     agg[t] = s;
 }
 
-// Launch with programmatic stream serialization: the kernel may start while the previous
-// kernel of the stream finishes; it waits (griddepcontrol.wait) before reading its inputs.
+// Launch with programmatic stream serialization (when pdl): the kernel may start while the
+// previous kernel of the stream finishes; it waits (griddepcontrol.wait) before reading its
+// inputs.  Contexts stepped in a batch launch without it: there many instances fill the GPU
+// side by side, and early CTAs waiting for their predecessor only hold SMs.
 template <class... KArgs, class... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                              Args&&... args) {
+static cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -347,12 +349,12 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <int W, int P, class Op>
-static gm_status launch_tc(const Op& op, const TcW& tw, cudaStream_t st) {
+static gm_status launch_tc(bool pdl, const Op& op, const TcW& tw, cudaStream_t st) {
     constexpr size_t smem = tc_smem_bytes<W, P>() > TC_SMEM_MIN ? tc_smem_bytes<W, P>() : TC_SMEM_MIN;
     static_assert(W <= TC_NB, "GEMM1 width must fit the staged B chunk");
     if (tw.N2p > TC_TMEM_COLS || tw.N2p % 16 || tw.K1p % 16) {
@@ -365,16 +367,17 @@ static gm_status launch_tc(const Op& op, const TcW& tw, cudaStream_t st) {
                                          (int)smem));
         attr_set = true;
     }
-    GM_CUDA_TRY(launch_pdl(tc_mlp_kernel<W, Op, P>, dim3((unsigned)cdiv(op.rows, TC_M)), dim3(TC_T), smem, st, op, tw));
+    GM_CUDA_TRY(launch_pdl(pdl, tc_mlp_kernel<W, Op, P>, dim3((unsigned)cdiv(op.rows, TC_M)), dim3(TC_T), smem, st, op,
+                           tw));
     return GM_OK;
 }
 
 template <int P, class Op>
-static gm_status launch_tc_w(int W, const Op& op, const TcW& tw, cudaStream_t st) {
+static gm_status launch_tc_w(bool pdl, int W, const Op& op, const TcW& tw, cudaStream_t st) {
     switch (W) {
-        case 32: return launch_tc<32, P>(op, tw, st);
-        case 64: return launch_tc<64, P>(op, tw, st);
-        case 128: return launch_tc<128, P>(op, tw, st);
+        case 32: return launch_tc<32, P>(pdl, op, tw, st);
+        case 64: return launch_tc<64, P>(pdl, op, tw, st);
+        case 128: return launch_tc<128, P>(pdl, op, tw, st);
         default: set_error("unsupported W %d", W); return GM_ERR_INVALID_ARG;
     }
 }
@@ -396,7 +399,8 @@ static gm_status launch_ws_bwd(const gm_ctx* c, const Op& op, const TcW& tw, cud
     }
     const long tiles = cdiv(op.rows, TC_M);
     const int grid = (int)std::min<long>(tiles, std::max(1, c->num_sms));
-    GM_CUDA_TRY(launch_pdl(tc_ws_bwd_kernel<Op>, dim3((unsigned)grid), dim3(WS_T), WsLayout<Op>::smem, st, op, tw));
+    GM_CUDA_TRY(launch_pdl(c->pdl, tc_ws_bwd_kernel<Op>, dim3((unsigned)grid), dim3(WS_T), WsLayout<Op>::smem, st, op,
+                           tw));
     GM_LAUNCH_CHECK();
     return GM_OK;
 }
@@ -411,12 +415,12 @@ static gm_status launch_mlp(const gm_ctx* c, const Op& op, const TcW& tw, cudaSt
     const int W = c->W;
     if (c->s.precision == GM_PREC_MIXED) {
         if constexpr (Op::kMode == 0) {
-            GM_TRY(launch_tc_w<3>(W, op, tw, st));
+            GM_TRY(launch_tc_w<3>(c->pdl, W, op, tw, st));
         } else {
-            GM_TRY(launch_tc_w<2>(W, op, tw, st));
+            GM_TRY(launch_tc_w<2>(c->pdl, W, op, tw, st));
         }
     } else if (c->s.precision == GM_PREC_BF16) {
-        GM_TRY(launch_tc_w<1>(W, op, tw, st));
+        GM_TRY(launch_tc_w<1>(c->pdl, W, op, tw, st));
     } else {
         int grid = cdiv(op.rows, BM);
         switch (W) {

@@ -470,7 +470,6 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     }
     // the prologue reads only weights and the static row indices (op.prep): it overlaps the
     // previous kernel's tail under programmatic dependent launch
-    pdl_launch_dependents();
     for (int m = tid; m < TC_M; m += TC_T) rc[m] = op.prep(row0 + m < rows ? row0 + m : -1);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -630,6 +629,10 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
             }
         }
     }
+    // this CTA's work is done: the next kernel may start its prologue (triggered at the end, not
+    // the start, so that early CTAs of the next kernel do not hold SMs for this kernel's
+    // whole duration when many instances run side by side)
+    pdl_launch_dependents();
     // a bulk copy whose wait gave up may still be landing: wait (bounded) before the CTA exits
     if (tid == 0)
 #pragma unroll

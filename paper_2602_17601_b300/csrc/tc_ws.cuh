@@ -193,7 +193,6 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
         sI[tc_off(n, k, 16) / 2] = __float2bfloat16(n == k ? 1.f : 0.f);
     }
     fence_async_smem();
-    pdl_launch_dependents();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -547,6 +546,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    pdl_launch_dependents();     // all tiles of this CTA done: the next kernel may start its prologue
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
