@@ -378,11 +378,12 @@ gm_status gm_ctx_set_graph(gm_ctx* ctx, int on);
  * i with (x_meas[i], costs[i], cons[i], U[i], stats[i]).  The first call runs
  * the instances one after another with plain launches; the next captures
  * every instance's step as a child graph of one parent graph with no
- * instances in L lanes (instance i after instance i - L, L = SMs / the
- * largest cooperative ADMM or factor grid of the members, so that the
- * cooperative grids of the steps running at once fit on the SMs together),
- * and every later call with the same arguments replays that graph with a
- * single launch on the stream, the lanes running side by side.  Changing any argument captures
+ * instances in lanes planned by gm_batch_plan (width: the larger of an
+ * instance's cooperative ADMM and factor grids; cost: M * N * (1 + nU/64)),
+ * so that the cooperative grids of the steps running at once fit on the
+ * SMs together, and every later call with the same arguments replays that
+ * graph with a single launch on the stream, the lanes running side by
+ * side.  Changing any argument captures
  * anew.  x_meas, U, stats: host arrays of n device pointers (stats may be
  * NULL); costs, cons: host arrays of n structs.  Contexts of a batch must not
  * be stepped elsewhere while the batch runs.  gm_batch_state: as
@@ -395,6 +396,21 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
 gm_status gm_batch_state(const gm_batch* b, int* replayed, int* captures);
 /* Lanes of the last captured batch graph (1 before the first capture). */
 gm_status gm_batch_lanes(const gm_batch* b, int* lanes);
+
+/* Host-only lane plan for n instance steps that each run cooperative grids
+ * of up to width[i] CTAs (one CTA per SM assumed) and cost cost[i] (any
+ * unit).  Instances of one lane run one after another; lanes run side by
+ * side.  The plan groups the widths into classes (each instance goes to the
+ * narrowest class at least as wide as it; the narrowest classes merge into
+ * wider ones until one lane per class fits in sms, and a width above sms
+ * counts as sms), gives each class one lane and then adds lanes, one at a
+ * time, to the class with the largest cost per lane while the sum of all
+ * lanes' class widths stays <= sms and the class has more instances than
+ * lanes; inside a class the costliest instance goes first to the least
+ * loaded lane.  So at most one grid per lane runs at a time and the widths
+ * of the running grids sum to <= sms.  Writes lane[i] in [0, *n_lanes).
+ * width[i] >= 1 and cost[i] >= 0, else GM_ERR_INVALID_ARG; n == 0 gives 0 lanes. */
+gm_status gm_batch_plan(int n, const int* width, const double* cost, int sms, int* lane, int* n_lanes);
 gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures);
 
 /* Launch timing of the dominant kernel, the reverse edge-update MLP (one launch per

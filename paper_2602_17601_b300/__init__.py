@@ -128,6 +128,7 @@ def _load():
         "gm_batch_rti_step": ([vp, C.POINTER(vp), vp, vp, C.POINTER(vp), C.POINTER(vp), vp], C.c_int),
         "gm_batch_state": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "gm_batch_lanes": ([vp, C.POINTER(C.c_int)], C.c_int),
+        "gm_batch_plan": ([C.c_int, vp, vp, C.c_int, vp, C.POINTER(C.c_int)], C.c_int),
         "gm_ctx_kernel_stats": ([vp, C.POINTER(C.c_int)] + [C.POINTER(C.c_double)] * 3, C.c_int),
         "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
@@ -148,7 +149,7 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
                     "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
-                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes",
+                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_plan",
                     "gm_rollout")
 
 GM_NOALLOC_MAX_NU = 64
@@ -188,6 +189,17 @@ def gm_ctx_phase_ms(ctx):
 
 def gm_launch_count():
     return int(_lib.gm_launch_count())
+
+
+def gm_batch_plan(width, cost, sms):
+    """Lane plan for batched instance steps (host only): (lane per instance, number of lanes)."""
+    w = np.ascontiguousarray(width, np.int32)
+    c = np.ascontiguousarray(cost, np.float64)
+    lane = np.zeros(len(w), np.int32)
+    n = C.c_int()
+    _check("gm_batch_plan", _lib.gm_batch_plan(len(w), w.ctypes.data, c.ctypes.data, int(sms),
+                                                lane.ctypes.data, C.byref(n)))
+    return lane, n.value
 
 
 def gm_ctx_set_graph(ctx, on):

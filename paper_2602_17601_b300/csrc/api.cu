@@ -880,19 +880,23 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
                             st, false));
         return GM_OK;
     }
-    // Every instance's step as a child graph of one parent, in L lanes: instance i follows
-    // instance i - L.  A step holds cooperative launches (the ADMM and factor grids), and
-    // cooperative grids running side by side can each hold part of their CTAs resident while
-    // waiting for the rest, so L is chosen such that the grids of L steps fit on the SMs at
+    // Every instance's step as a child graph of one parent, chained in lanes (gm_batch_plan).
+    // A step holds cooperative launches (the ADMM and factor grids), and cooperative grids
+    // running side by side can each hold part of their CTAs resident while waiting for the
+    // rest, so the lanes are sized such that the widest grids of all lanes fit on the SMs at
     // once (otherwise such a standoff lasts until a grid barrier's bound runs out).
-    int gmax = 1;
+    std::vector<int> width(n), lane(n);
+    std::vector<double> cost(n);
     for (int i = 0; i < n; ++i) {
         const gm_ctx* c = b->ctx[i];
         const int fg = c->s.factor_grid > 0 ? std::max(2, std::min(c->s.factor_grid, factor_grid())) : factor_grid();
-        gmax = std::max(gmax, std::max(c->admm_grid, fg));
+        width[i] = std::max(c->admm_grid, fg);
+        cost[i] = (double)c->M * c->N * (1.0 + c->nU / 64.0);
     }
-    const int lanes = std::max(1, std::min(n, std::max(1, b->ctx[0]->num_sms) / gmax));
+    int lanes = 1;
+    GM_TRY(gm_batch_plan(n, width.data(), cost.data(), std::max(1, b->ctx[0]->num_sms), lane.data(), &lanes));
     b->lanes = lanes;
+    std::vector<int> tail(lanes, -1);
     cudaGraph_t parent = nullptr;
     GM_CUDA_TRY(cudaGraphCreate(&parent, 0));
     gm_status r = GM_OK;
@@ -902,7 +906,8 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
         r = capture_step(b->ctx[i], x_meas[i], &costs[i], &cons[i], U[i], nullptr, stats ? stats[i] : nullptr, &g);
         if (r != GM_OK) break;
         cudaGraphNode_t& node = nodes[i];
-        const cudaGraphNode_t* dep = i >= lanes ? &nodes[i - lanes] : nullptr;
+        const cudaGraphNode_t* dep = tail[lane[i]] >= 0 ? &nodes[tail[lane[i]]] : nullptr;
+        tail[lane[i]] = i;
         if (cudaGraphAddChildGraphNode(&node, parent, dep, dep ? 1 : 0, g) != cudaSuccess) {
             set_error("adding instance %d to the batch graph failed", i);
             r = GM_ERR_CUDA;
@@ -922,6 +927,62 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
     ++b->captures;
     GM_CUDA_TRY(cudaGraphLaunch(b->exec, st));
     b->replayed = true;
+    return GM_OK;
+}
+
+gm_status gm_batch_plan(int n, const int* width, const double* cost, int sms, int* lane, int* n_lanes) {
+    clear_error();
+    GM_CHECK_ARG(n >= 0 && sms >= 1, "n must be >= 0 and sms >= 1");
+    GM_CHECK_ARG(n == 0 || (width && cost && lane && n_lanes), "NULL argument");
+    if (!n_lanes) return GM_ERR_INVALID_ARG;
+    *n_lanes = 0;
+    for (int i = 0; i < n; ++i)
+        GM_CHECK_ARG(width[i] >= 1 && cost[i] >= 0.0, "instance %d: width must be >= 1 and cost >= 0", i);
+    if (n == 0) return GM_OK;
+    // width classes, widest first; the narrowest class merges into the next wider one
+    // until one lane per class fits (a single class wider than the SMs gets one lane)
+    std::vector<int> cls;
+    for (int i = 0; i < n; ++i) cls.push_back(std::min(width[i], sms));
+    std::sort(cls.begin(), cls.end(), std::greater<int>());
+    cls.erase(std::unique(cls.begin(), cls.end()), cls.end());
+    auto sum = [&] { return std::accumulate(cls.begin(), cls.end(), 0L); };
+    while (cls.size() > 1 && sum() > sms) cls.pop_back();
+    const int nc = (int)cls.size();
+    auto class_of = [&](int i) {     // the narrowest class at least as wide as the instance
+        int k = 0;
+        while (k + 1 < nc && cls[k + 1] >= std::min(width[i], sms)) ++k;
+        return k;
+    };
+    std::vector<int> count(nc, 0), nl(nc, 1);
+    std::vector<double> load(nc, 0.0);
+    for (int i = 0; i < n; ++i) { ++count[class_of(i)]; load[class_of(i)] += cost[i]; }
+    long left = sms - sum();
+    for (;;) {                       // one more lane for the class with the largest load per lane
+        int best = -1;
+        for (int k = 0; k < nc; ++k)
+            if (nl[k] < count[k] && cls[k] <= left && (best < 0 || load[k] * nl[best] > load[best] * nl[k]))
+                best = k;
+        if (best < 0) break;
+        ++nl[best];
+        left -= cls[best];
+    }
+    // longest processing time first inside each class: the costliest instance goes to the
+    // least loaded of its class's lanes
+    std::vector<int> first(nc, 0);
+    for (int k = 1; k < nc; ++k) first[k] = first[k - 1] + nl[k - 1];
+    std::vector<double> lane_load(first[nc - 1] + nl[nc - 1], 0.0);
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (int i : order) {
+        const int k = class_of(i);
+        int best = first[k];
+        for (int l = first[k] + 1; l < first[k] + nl[k]; ++l)
+            if (lane_load[l] < lane_load[best]) best = l;
+        lane[i] = best;
+        lane_load[best] += cost[i];
+    }
+    *n_lanes = (int)lane_load.size();
     return GM_OK;
 }
 

@@ -86,3 +86,44 @@ def test_no_cuda_device_fails_loudly():
     from synth import small_chain
     with pytest.raises(Exception):
         gm.RTIProblem.from_workload(small_chain())
+
+
+def _check_plan(gm, width, cost, sms):
+    lane, n = gm.gm_batch_plan(width, cost, sms)
+    w = np.minimum(np.asarray(width), sms)
+    assert n >= 1 and lane.min() >= 0 and lane.max() < n and len(np.unique(lane)) == n
+    # the widest grid of every lane, summed over the lanes, fits on the SMs
+    lane_w = np.array([w[lane == l].max() for l in range(n)])
+    assert lane_w.sum() <= sms, (lane_w, sms)
+    return lane, n
+
+
+def test_batch_plan_lanes_fit_and_balance():
+    import paper_2602_17601_b300 as gm
+    rng = np.random.default_rng(0)
+    # one width: SMs // width lanes, and the costs spread within the LPT bound
+    cost = rng.uniform(1, 10, 200)
+    lane, n = _check_plan(gm, [32] * 200, cost, 148)
+    assert n == 4
+    loads = np.array([cost[lane == l].sum() for l in range(n)])
+    assert loads.max() <= cost.sum() / n + cost.max()      # greedy list-scheduling bound
+    # two widths: a lane of the wide class plus lanes of the narrow one, more than 148 // 32
+    width = [32] * 20 + [16] * 100
+    lane, n = _check_plan(gm, width, np.ones(120), 148)
+    assert n > 4
+    # a width above the SMs counts as the SMs: one lane
+    lane, n = _check_plan(gm, [200, 8, 8], [1, 1, 1], 148)
+    assert n == 1
+    # fewer instances than lanes: one lane each
+    lane, n = _check_plan(gm, [8, 8, 8], [3, 2, 1], 148)
+    assert n == 3
+    # random widths and costs
+    for seed in range(20):
+        r = np.random.default_rng(seed)
+        k = int(r.integers(1, 60))
+        _check_plan(gm, r.choice([2, 8, 16, 32, 64, 128], k), r.uniform(0, 5, k), int(r.integers(1, 200)))
+    assert gm.gm_batch_plan([], [], 148)[1] == 0
+    with pytest.raises(gm.GMError):
+        gm.gm_batch_plan([0], [1.0], 148)
+    with pytest.raises(gm.GMError):
+        gm.gm_batch_plan([4], [-1.0], 148)
