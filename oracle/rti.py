@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import barrier as br
 from . import condense as cd
 from . import gnn as gm
 from . import qp
@@ -42,8 +43,12 @@ def linearize_dense(gnn, g, x_hat, u_hat):
 
 
 def rti_step(wl, u_hat=None, activation="relu", solver="exact", condensing="recursive",
-             return_all=False, scale_rows=True, adapt_every=25):
-    """One RTI step on workload wl.  Returns U* [N, nu] (and intermediates)."""
+             return_all=False, scale_rows=True, adapt_every=25, barrier=None):
+    """One RTI step on workload wl.  Returns U* [N, nu] (and intermediates).
+
+    barrier = (mu, delta): the obstacle rows enter the cost as relaxed log barriers
+    (``oracle.barrier``, Sec. VI-B) instead of constraints; the QP keeps the box only.
+    """
     gnn, g = model_of(wl, activation)
     u_hat = np.zeros((wl.N, wl.nu)) if u_hat is None else np.asarray(u_hat, np.float64)
     x_hat = gm.rollout(gnn, g, wl.x0, u_hat)
@@ -68,6 +73,9 @@ def rti_step(wl, u_hat=None, activation="relu", solver="exact", condensing="recu
             dx if dx is not None else np.zeros((wl.N, wl.M, 0)))
     lo = wl.u_lo.reshape(-1).astype(np.float64)
     hi = wl.u_hi.reshape(-1).astype(np.float64)
+    if barrier is not None:
+        H, gv = br.barrier_fold(H, gv, Ct, dt, u_hat.reshape(-1), barrier[0], barrier[1])
+        Ct, dt = np.zeros((0, H.shape[0])), np.zeros(0)
     if solver == "exact":
         U, y, info = qp.solve_exact(H, gv, lo, hi, Ct, dt)
     else:
