@@ -231,6 +231,10 @@ typedef struct {
     int n_spheres;        /* > 0: ignore Cx/dx and linearise these spheres at x_hat instead
                              (requires n_c == n_spheres) */
     const float* spheres; /* [n_spheres][4]  centre xyz, radius */
+    float barrier_mu;     /* > 0: gm_rti_step puts the state rows (spheres or Cx/dx) into the
+                             cost as relaxed log barriers of weight barrier_mu (gm_barrier_fold)
+                             instead of constraints; 0: constraints */
+    float barrier_delta;  /* relaxation point of the barrier (> 0 when barrier_mu > 0) */
 } gm_constr;
 
 /* ------------------------------------------------------------------------
@@ -271,7 +275,8 @@ gm_status gm_condense(gm_ctx* ctx, const float* x_hat, const float* A, const flo
  *   and h'max(dy, 0) + l'min(dy, 0) <= -1e-4 |dy|_inf over the finite
  *   bounds; when it holds no U satisfies the constraints, ADMM stops and
  *   stats->status is GM_ERR_INFEASIBLE (U holds the last iterate).
- *   H, g, Ct, dt, u_lo, u_hi  as from gm_condense / gm_constr
+ *   H, g, Ct, dt, u_lo, u_hi  as from gm_condense / gm_constr; Ct = dt = NULL
+ *     solves the box-only QP (the barrier variant) even when n_c > 0
  *   warm_U [nU], warm_y [nU + N M n_c]  nullable warm start (U^0, y^0)
  *   U [nU] (out), y [nU + N M n_c] (out, nullable)  multipliers, box rows first
  *   stats  DEVICE gm_stats* (out, nullable)
@@ -281,6 +286,32 @@ gm_status gm_qp_solve(gm_ctx* ctx, const float* H, const float* g, const float* 
                       const float* dt, const float* u_lo, const float* u_hi,
                       const float* warm_U, const float* warm_y, float* U, float* y,
                       gm_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gm_barrier_fold — barrier-cost obstacle variant (Sec. VI-B: one barrier
+ *   term per node and obstacle in the cost; the paper gives no formula).
+ *   Row r of the condensed constraints gives the clearance
+ *   s_r(U) = d~_r - C~_r U (for spheres: the distance to the sphere along
+ *   the normal at the rollout).  Each row adds mu beta(s_r) to the cost,
+ *   beta the relaxed logarithmic barrier of Feller and Ebenbauer (2017):
+ *   -ln s for s > delta, 1/2 (((s - 2 delta)/delta)^2 - 1) - ln delta
+ *   below (convex, twice continuously differentiable, finite for s <= 0).
+ *   s_r is affine in U, so the second-order model at U_hat is exact to second
+ *   order; this call folds it into the QP in place:
+ *     H <- H + C~' diag(mu beta''(s^)) C~
+ *     g <- g - C~' (mu beta'(s^) + mu beta''(s^) C~ U_hat),  s^ = d~ - C~ U_hat
+ *   after which gm_qp_solve with Ct = dt = NULL solves the box-only QP: one
+ *   Newton step on the barrier-augmented cost under the input box.
+ *   Ct, dt   DEVICE, as from gm_condense (n_c > 0; with n_c = 0 nothing changes)
+ *   U_hat    DEVICE [nU] the linearisation point (the shifted previous solution)
+ *   mu > 0, delta > 0, else GM_ERR_INVALID_ARG
+ *   H [nU][nU], g [nU]  DEVICE, updated in place
+ *   Uses the context's interior-point scratch (not concurrently with
+ *   gm_qp_solve_ipm on the same context).  FP64 row terms and C~' v, FP32
+ *   weighted Gram (as for rho C~'C~ in gm_qp_solve).
+ * ---------------------------------------------------------------------- */
+gm_status gm_barrier_fold(gm_ctx* ctx, const float* Ct, const float* dt, const float* U_hat,
+                          float mu, float delta, float* H, float* g, void* stream);
 
 /* ------------------------------------------------------------------------
  * gm_qp_solve_ipm — the same QP by a primal-dual interior-point method (the

@@ -58,7 +58,8 @@ class Cost(C.Structure):
 
 class Constr(C.Structure):
     _fields_ = [("u_lo", C.c_void_p), ("u_hi", C.c_void_p), ("Cx", C.c_void_p),
-                ("dx", C.c_void_p), ("n_spheres", C.c_int), ("spheres", C.c_void_p)]
+                ("dx", C.c_void_p), ("n_spheres", C.c_int), ("spheres", C.c_void_p),
+                ("barrier_mu", C.c_float), ("barrier_delta", C.c_float)]
 
 
 class Info(C.Structure):
@@ -129,6 +130,7 @@ def _load():
         "gm_batch_state": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "gm_batch_lanes": ([vp, C.POINTER(C.c_int)], C.c_int),
         "gm_batch_plan": ([C.c_int, vp, vp, C.c_int, vp, C.POINTER(C.c_int)], C.c_int),
+        "gm_barrier_fold": ([vp, vp, vp, vp, C.c_float, C.c_float, vp, vp, vp], C.c_int),
         "gm_ctx_kernel_stats": ([vp, C.POINTER(C.c_int)] + [C.POINTER(C.c_double)] * 3, C.c_int),
         "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
@@ -149,7 +151,7 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
                     "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
-                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_plan",
+                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_plan", "gm_barrier_fold",
                     "gm_rollout")
 
 GM_NOALLOC_MAX_NU = 64
@@ -341,9 +343,16 @@ def make_cost(Qdiag, Rdiag, x_ref, u_ref):
     return Cost(_ptr(Qdiag), _ptr(Rdiag), _ptr(x_ref), _ptr(u_ref))
 
 
-def make_constr(u_lo, u_hi, Cx=None, dx=None, spheres=None):
+def make_constr(u_lo, u_hi, Cx=None, dx=None, spheres=None, barrier=None):
+    """barrier = (mu, delta): the state rows enter the cost as relaxed log barriers."""
     ns = 0 if spheres is None else int(spheres.shape[0])
-    return Constr(_ptr(u_lo), _ptr(u_hi), _ptr(Cx), _ptr(dx), ns, _ptr(spheres))
+    mu, delta = (0.0, 0.0) if barrier is None else (float(barrier[0]), float(barrier[1]))
+    return Constr(_ptr(u_lo), _ptr(u_hi), _ptr(Cx), _ptr(dx), ns, _ptr(spheres), mu, delta)
+
+
+def gm_barrier_fold(ctx, Ct, dt, U_hat, mu, delta, H, g, stream=None):
+    _check("gm_barrier_fold", _lib.gm_barrier_fold(ctx, _ptr(Ct), _ptr(dt), _ptr(U_hat), float(mu), float(delta),
+                                                   _ptr(H), _ptr(g), _stream(stream)))
 
 
 def gm_condense(ctx, x_hat, A, B, c, cost, constr, H, g, Ct=None, dt=None, stream=None):

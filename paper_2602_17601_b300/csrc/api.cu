@@ -688,6 +688,9 @@ static gm_status check_cost(const gm_ctx* ctx, const gm_cost* cost, const gm_con
     } else if (ctx->n_c > 0) {
         GM_CHECK_ARG(cons->Cx && cons->dx, "Cx/dx are NULL with n_c = %d", ctx->n_c);
     }
+    GM_CHECK_ARG(cons->barrier_mu >= 0.f && (cons->barrier_mu == 0.f || cons->barrier_delta > 0.f),
+                 "barrier_mu must be >= 0, and barrier_delta > 0 when barrier_mu > 0 (got %g, %g)",
+                 (double)cons->barrier_mu, (double)cons->barrier_delta);
     return GM_OK;
 }
 
@@ -714,7 +717,7 @@ gm_status gm_qp_solve(gm_ctx* ctx, const float* H, const float* g, const float* 
                       float* U, float* y, gm_stats* stats, void* stream) {
     clear_error();
     GM_CHECK_ARG(ctx && H && g && u_lo && u_hi && U, "NULL argument");
-    GM_CHECK_ARG(ctx->n_c == 0 || (Ct && dt), "Ct/dt are NULL with n_c = %d", ctx->n_c);
+    GM_CHECK_ARG(!Ct == !dt, "Ct and dt must both be given or both be NULL (box only)");
     return qp_solve(ctx, H, g, Ct, dt, u_lo, u_hi, warm_U, warm_y, U, y, stats ? stats : ctx->d_stats,
                     static_cast<cudaStream_t>(stream));
 }
@@ -741,9 +744,15 @@ static gm_status rti_body(gm_ctx* c, const float* x_meas, const gm_cost* cost, c
         dx = c->d_dx;
     }
     GM_TRY(condense(c, c->d_x_hat, c->d_A, c->d_B, c->d_c, cost, Cx, dx, c->d_H, c->d_g, c->d_Ct, c->d_dt, st));
+    // barrier variant: the state rows go into the cost, the QP keeps the box
+    const bool barrier = cons->barrier_mu > 0.f && c->n_c > 0;
+    if (barrier)
+        GM_TRY(barrier_fold(c, c->d_Ct, c->d_dt, c->d_u_hat, cons->barrier_mu, cons->barrier_delta, c->d_H, c->d_g,
+                            st));
     if (timed) GM_CUDA_TRY(cudaEventRecord(ev[3], st));
-    GM_TRY(qp_solve(c, c->d_H, c->d_g, c->d_Ct, c->d_dt, cons->u_lo, cons->u_hi, nullptr, nullptr, c->d_U,
-                    c->d_y, stats ? stats : c->d_stats, st, timed ? ev[4] : nullptr));
+    GM_TRY(qp_solve(c, c->d_H, c->d_g, barrier ? nullptr : c->d_Ct, barrier ? nullptr : c->d_dt, cons->u_lo,
+                    cons->u_hi, nullptr, nullptr, c->d_U, c->d_y, stats ? stats : c->d_stats, st,
+                    timed ? ev[4] : nullptr));
     if (timed) GM_CUDA_TRY(cudaEventRecord(ev[5], st));
     GM_CUDA_TRY(cudaMemcpyAsync(U, c->d_U, sizeof(float) * c->nU, cudaMemcpyDeviceToDevice, st));
     if (u0) GM_CUDA_TRY(cudaMemcpyAsync(u0, c->d_U, sizeof(float) * c->nu, cudaMemcpyDeviceToDevice, st));
@@ -758,9 +767,12 @@ static std::vector<uintptr_t> graph_key(const gm_ctx* c, const float* x_meas, co
     std::vector<uintptr_t> k = {P(x_meas), P(cost->Qdiag), P(cost->Rdiag), P(cost->x_ref), P(cost->u_ref),
                                 P(cons->u_lo), P(cons->u_hi), P(cons->Cx), P(cons->dx), (uintptr_t)cons->n_spheres,
                                 P(cons->spheres), P(U), P(u0), P(stats)};
-    uint32_t rho, tol;
+    uint32_t rho, tol, bmu, bdelta;
     std::memcpy(&rho, &c->s.rho, 4);
     std::memcpy(&tol, &c->s.tol, 4);
+    std::memcpy(&bmu, &cons->barrier_mu, 4);
+    std::memcpy(&bdelta, &cons->barrier_delta, 4);
+    k.insert(k.end(), {(uintptr_t)bmu, (uintptr_t)bdelta});
     k.insert(k.end(), {(uintptr_t)rho, (uintptr_t)tol, (uintptr_t)c->s.max_iter, (uintptr_t)c->s.scale_rows,
                        (uintptr_t)c->s.adapt_rho, (uintptr_t)c->s.timeout_spins, (uintptr_t)c->s.polish});
     return k;

@@ -53,6 +53,9 @@ __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float
                                  const float* __restrict__ lo, const float* __restrict__ hi,
                                  const float* __restrict__ U, const float* __restrict__ y,
                                  const double* __restrict__ kkt, const int* status, gm_stats* stats);
+// barrier.cu: relaxed log-barrier obstacle rows folded into H and g
+gm_status barrier_fold(gm_ctx* c, const float* Ct, const float* dt, const float* U_hat, float mu, float delta,
+                       float* H, float* g, cudaStream_t st);
 // ipm.cu: interior-point solve of the condensed QP
 gm_status ipm_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, const float* dt, const float* u_lo,
                     const float* u_hi, int max_iter, float* U, float* y, gm_stats* stats, cudaStream_t st);

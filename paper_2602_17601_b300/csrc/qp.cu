@@ -174,7 +174,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
                    const float* u_lo, const float* u_hi, const float* warm_U, const float* warm_y,
                    float* U, float* y, gm_stats* stats, cudaStream_t st, cudaEvent_t ev_mid) {
     const int n = c->nU;
-    const long rows = c->rows_c;
+    const long rows = Ct && dt ? c->rows_c : 0;    // no rows: the box-only QP
     const bool scale = rows > 0 && c->s.scale_rows;
     AdmmPlan p{};
     p.n = n; p.nu = c->nu; p.Mnc = std::max(c->M * c->n_c, 1); p.N = c->N; p.rows = rows;
@@ -188,7 +188,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     p.rho0 = c->s.rho; p.tol = c->s.tol; p.max_iter = c->s.max_iter;
     p.adapt_every = c->s.adapt_rho ? 25 : 0;
     p.rounds = c->s.adapt_rho ? 6 : 1;
-    p.grid = c->admm_grid;
+    p.grid = rows > 0 ? c->admm_grid : 1;
     p.factor_grid = c->s.factor_grid;
     p.max_spins = c->s.timeout_spins > 0 ? c->s.timeout_spins : (1LL << 26);
     p.st = st;

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (GM_PREC_FP32, STATS_BYTES, gm_condense, gm_ctx_create, gm_ctx_destroy, gm_ctx_graph_state,
+from . import (GM_PREC_FP32, STATS_BYTES, gm_barrier_fold, gm_condense, gm_ctx_create, gm_ctx_destroy, gm_ctx_graph_state,
                gm_ctx_reset, gm_ctx_set_graph, gm_ctx_workspace_size, gm_gnn_destroy, gm_gnn_load, gm_graph_create, gm_graph_destroy,
                gm_jac_pattern, gm_linearize, gm_qp_solve, gm_qp_solve_ipm, gm_rti_step, make_constr, make_cost,
                make_settings, read_stats)
@@ -20,13 +20,14 @@ class RTIProblem:
     Arguments mirror the paper's problem statement: graph (M, src, dst), inputs
     (nu, act_node), GNN (K, W, dt, weight blob), horizon N, cost (Qdiag, Rdiag,
     x_ref, u_ref), input box (u_lo, u_hi) and either explicit position
-    half-spaces (Cx, dx) or spheres linearised at the rollout.
+    half-spaces (Cx, dx) or spheres linearised at the rollout.  barrier = (mu, delta)
+    makes step() put those rows into the cost as relaxed log barriers (gm_barrier_fold).
     """
 
     def __init__(self, M, src, dst, nu, act_node, K, W, dt, blob, N, Qdiag, Rdiag, x_ref, u_ref, u_lo,
                  u_hi, Cx=None, dx=None, spheres=None, rho=0.1, tol=1e-6, max_iter=4000,
                  precision=GM_PREC_FP32, polish=0, timeout_spins=0, scale_rows=1, adapt_rho=1,
-                 graph=False, admm_grid=0, factor_grid=0, chunk_mb=0, device="cuda"):
+                 graph=False, admm_grid=0, factor_grid=0, chunk_mb=0, barrier=None, device="cuda"):
         import torch
         self.torch = torch
         self.M, self.nu, self.N, self.K, self.W = int(M), int(nu), int(N), int(K), int(W)
@@ -55,7 +56,7 @@ class RTIProblem:
         self.Qdiag, self.Rdiag, self.x_ref, self.u_ref = f32(Qdiag), f32(Rdiag), f32(x_ref), f32(u_ref)
         self.u_lo, self.u_hi = f32(u_lo), f32(u_hi)
         self.cost = make_cost(self.Qdiag, self.Rdiag, self.x_ref, self.u_ref)
-        self.constr = make_constr(self.u_lo, self.u_hi, self.Cx, self.dx, self.spheres)
+        self.constr = make_constr(self.u_lo, self.u_hi, self.Cx, self.dx, self.spheres, barrier)
         self.row_ptr, self.col = gm_jac_pattern(self.ctx, self.M)
         self.nnzb = int(self.col.size)
         self.stats = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=device)
@@ -109,12 +110,21 @@ class RTIProblem:
                     Ct if self.n_c else None, dt if self.n_c else None)
         return H, g, Ct[:self.ct_len], dt[:self.rows_c]
 
-    def qp_solve(self, H, g, Ct=None, dt=None, warm_U=None, warm_y=None):
+    def qp_solve(self, H, g, Ct=None, dt=None, warm_U=None, warm_y=None, box_only=False):
+        """ADMM on the condensed QP; box_only drops the half-space rows (barrier variant)."""
         U = self.empty(self.nU)
         y = self.empty(self.nU + self.rows_c)
-        gm_qp_solve(self.ctx, H, g, Ct if self.n_c else None, dt if self.n_c else None, self.u_lo,
+        rows = self.n_c and not box_only
+        gm_qp_solve(self.ctx, H, g, Ct if rows else None, dt if rows else None, self.u_lo,
                     self.u_hi, U, y, self.stats, warm_U, warm_y)
         return U, y
+
+    def barrier_fold(self, H, g, Ct, dt, U_hat, mu, delta):
+        """H, g with the relaxed log-barrier model of the rows folded in (in place; returned)."""
+        t = self.torch
+        U_hat = t.as_tensor(U_hat, dtype=t.float32, device=self.Qdiag.device).reshape(-1).contiguous()
+        gm_barrier_fold(self.ctx, Ct, dt, U_hat, mu, delta, H, g)
+        return H, g
 
     def qp_solve_ipm(self, H, g, Ct=None, dt=None, max_iter=60):
         """The same QP by the interior-point method (gm_qp_solve_ipm)."""
