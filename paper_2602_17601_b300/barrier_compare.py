@@ -2,7 +2,9 @@
 
     python -m paper_2602_17601_b300.barrier_compare [--steps 20] [--mu 1e-3] [--delta 5e-3]
 
-The chain of 1000 nodes (K = 3, W = 128, N = 20, nu = 8, 5 spheres) in the mixed form with the
+The chain of 1000 nodes (K = 3, W = 128, N = 20, nu = 8, 5 spheres of radius 0.02) in two
+scenarios: spheres 0.15 from their node at the initial state ("far", the benchmark workload)
+and 0.01 from it ("near").  Each runs in the mixed form with the
 step replayed as a CUDA graph, stepped repeatedly from its initial state (each step shifts
 its own solution into the next linearisation point), once with the linearised sphere rows as
 QP constraints and once with them in the cost as relaxed log barriers (gm_constr
@@ -30,10 +32,9 @@ def main(argv=None):
     ap.add_argument("--mu", type=float, default=1e-3)
     ap.add_argument("--delta", type=float, default=5e-3)
     a = ap.parse_args(argv)
-    wl = paper_chain()
-    sph = wl.spheres.astype(np.float64)
 
-    def run(barrier):
+    def run(wl, barrier):
+        sph = wl.spheres.astype(np.float64)
         prob = RTIProblem.from_workload(wl, precision=GM_PREC_MIXED, graph=True, barrier=barrier)
         x = torch.as_tensor(wl.x0.reshape(-1), dtype=torch.float32, device="cuda")
         U = prob.empty(prob.nU)
@@ -58,9 +59,12 @@ def main(argv=None):
         return out
 
     rep = {"workload": "chain1000_K3_W128_N20_nu8_spheres5", "form": "mixed, graph replay",
-           "steps": a.steps, "warmup": a.warmup, "mu": a.mu, "delta": a.delta,
-           "constraints": run(None), "barrier": run((a.mu, a.delta)),
-           "device": torch.cuda.get_device_name()}
+           "steps": a.steps, "warmup": a.warmup, "mu": a.mu, "delta": a.delta}
+    for name, clear in (("far", 0.15), ("near", 0.01)):
+        wl = paper_chain(sphere_clear=clear)
+        rep[name] = {"sphere_clearance_at_x0": clear, "constraints": run(wl, None),
+                     "barrier": run(wl, (a.mu, a.delta))}
+    rep["device"] = torch.cuda.get_device_name()
     print(json.dumps(rep), flush=True)
     return rep
 

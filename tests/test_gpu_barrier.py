@@ -24,9 +24,9 @@ def _fold_bounds(H, g, Ct, dt, U_hat, mu, delta):
     return 1e-5 * absH + 1e-6, 1e-5 * absg + 1e-6
 
 
-@pytest.mark.parametrize("offset", [1e-4, -2e-3])
-def test_barrier_fold_matches_oracle(lib, offset):
-    """Rows at clearance offset from the rollout (negative: inside, the relaxed branch)."""
+@pytest.mark.parametrize("clearance", [(1e-3, 2e-2), (-4e-3, 2e-2)])
+def test_barrier_fold_matches_oracle(lib, clearance):
+    """Rows at clearances drawn from a range around delta (negative: inside an obstacle)."""
     wl = small_chain()
     u_hat = np.random.default_rng(3).uniform(-0.5, 0.5, (wl.N, wl.nu))
     xo, Ao, Bo, co = oracle_linearize(wl, u_hat)
@@ -36,7 +36,7 @@ def test_barrier_fold_matches_oracle(lib, offset):
     n = rng.normal(0, 1, (wl.N, wl.M, 2, 3))
     n /= np.linalg.norm(n, axis=-1, keepdims=True)
     p = xo[1:, :, None, :3]
-    dx = np.einsum("kics,kics->kic", n, np.broadcast_to(p, n.shape)) + offset * rng.uniform(0.5, 20, n.shape[:3])
+    dx = np.einsum("kics,kics->kic", n, np.broadcast_to(p, n.shape)) + rng.uniform(*clearance, n.shape[:3])
     H, g, Ct, dt, _, _ = ocd.condense_recursive(ocd.blocks_from_dense(Ao, Bo, co, nbh), xo[0].reshape(-1),
                                                 wl.Qdiag, wl.Rdiag, wl.x_ref, wl.u_ref, n, dx)
     H, g, Ct, dt = (np.asarray(a, np.float32).astype(np.float64) for a in (H, g, Ct, dt))
@@ -44,6 +44,7 @@ def test_barrier_fold_matches_oracle(lib, offset):
     mu, delta = 1e-3, 5e-3
     s = dt - Ct @ U_hat
     assert (s > delta).any() and (s <= delta).any()       # both branches of the barrier
+    assert (s < 0).any() == (clearance[0] < 0)
     Hx, gx = obr.barrier_fold(H, g, Ct, dt, U_hat, mu, delta)
     prob = lib.RTIProblem(wl.M, wl.src, wl.dst, wl.nu, wl.act_node, wl.K, wl.W, wl.dt, wl.blob, wl.N,
                           wl.Qdiag, wl.Rdiag, wl.x_ref, wl.u_ref, wl.u_lo, wl.u_hi,
