@@ -26,14 +26,25 @@ def _cases():
     }
 
 
+def _degenerate_cases():
+    """Smallest shapes the method admits: one node with no edges and a one-stage horizon, a
+    one-stage horizon on a graph, several inputs sharing an actuator node."""
+    return {
+        "M1_N1_nu1_sphere": lambda: random_instance(5, M=1, N=1, nu=1, K=1, W=32, reach=1, p=0.0,
+                                                    n_spheres=1),
+        "rand6_N1": lambda: random_instance(6, M=6, N=1, nu=2, K=2, W=32, reach=2, p=0.8),
+        "M3_nu5_shared_nodes": lambda: random_instance(7, M=3, N=3, nu=5, K=2, W=32, reach=2, p=1.0),
+    }
+
+
 def _u_hat(wl, seed=0):
     return np.random.default_rng(seed).uniform(-0.5, 0.5, (wl.N, wl.nu)).astype(np.float32)
 
 
-@pytest.mark.parametrize("case", list(_cases()))
+@pytest.mark.parametrize("case", list(_cases()) + list(_degenerate_cases()))
 def test_linearize_parity(lib, case):
     """x_hat (Eq. forward_dynamics) and A, B, c (Eq. linearized_dynamics) against the oracle."""
-    wl = _cases()[case]()
+    wl = {**_cases(), **_degenerate_cases()}[case]()
     u_hat = _u_hat(wl)
     prob = lib.RTIProblem.from_workload(wl)
     x_hat, A, B, c = (t.cpu().numpy().astype(np.float64) for t in prob.linearize(wl.x0, u_hat))
@@ -173,6 +184,19 @@ def test_rti_step_matches_oracle_two_steps(lib):
         lam = np.linalg.eigvalsh(rx["H"]).min()
         assert np.abs(U - rx["U"]).max() <= 2 * max(st["r_dual"], st["kkt_stat"]) / lam + 1e-5
         u_prev = ro["U"]
+
+
+@pytest.mark.parametrize("case", list(_degenerate_cases()))
+def test_rti_step_degenerate_shapes(lib, case):
+    """One real-time iteration on the smallest shapes: U against the oracle's exact optimum."""
+    wl = _degenerate_cases()[case]()
+    prob = lib.RTIProblem.from_workload(wl)
+    U = prob.step(wl.x0).cpu().numpy().astype(np.float64).reshape(wl.N, wl.nu)
+    st = prob.read_stats()
+    rx = orti.rti_step(wl, solver="exact", return_all=True)
+    assert st["status"] == 0 and st["converged"] == 1, st
+    lam = np.linalg.eigvalsh(rx["H"]).min()
+    assert np.abs(U - rx["U"]).max() <= 2 * max(st["r_dual"], st["kkt_stat"]) / lam + 1e-5, case
 
 
 def _simulate_blocks(A, B, c, x0, U, row_ptr, col, M):
