@@ -43,7 +43,7 @@ sys.path.insert(0, ROOT)
 METRIC = "RTI MPC steps/s at 1000 nodes, N=20 (chosen vs plain GPU form, same residual)"
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     p.add_argument("--workload", default="chain1000", choices=["chain1000", "chain10"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def workload(name):
@@ -244,15 +244,13 @@ def timed_steps(torch, prob, x_dev, U, steps, stream):
 
 def run_ours(args):
     import torch
-    import torch.distributed as dist
 
     import paper_2602_17601_b300 as gm
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    from paper_2602_17601_b300.replicas import Replicas
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    reps = Replicas("nccl", device="cuda")
+    world = reps.world
     wl = workload(args.workload)
     precs = {"fp32": gm.GM_PREC_FP32, "mixed": gm.GM_PREC_MIXED, "bf16": gm.GM_PREC_BF16}
     graph = not args.no_graph
@@ -263,15 +261,8 @@ def run_ours(args):
     U = prob.empty(prob.nU)
     warmup = max(args.warmup, 3)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(v):
-        t = torch.tensor([v], device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = reps.barrier
+    max_over_ranks = reps.max_over_ranks
 
     # ---- the chosen form, device-resident inputs; the first warm-up step runs eagerly and
     # counts the kernels of one step, the second is captured (graph replay from then on)
@@ -341,14 +332,13 @@ def run_ours(args):
         barrier()
         ms_p = max_over_ranks(timed_steps(torch, pp, x_dev, U, args.steps, stream))
         sp = pp.read_stats()
-        plain = {"form": "fp32, eager launches", "value": world * 1000.0 / ms_p, "unit": "steps/s",
+        plain = {"form": "fp32, eager launches", "value": reps.steps_per_s(ms_p), "unit": "steps/s",
                  "ms_per_step": ms_p, "admm_iters_last_step": sp["iters"], "kkt_stat_last_step": sp["kkt_stat"],
                  "r_dual_last_step": sp["r_dual"], "status_last_step": sp["status"]}
         del pp
 
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
+    if not reps.leader:
+        reps.close()
         return
 
     peaks = {}
@@ -372,7 +362,7 @@ def run_ours(args):
             "tensor_peak_tflops": peaks.get("bf16_tflops_sustained"),
             "share_of_step": k_ms / ms,
             "phase_ms": per_phase}
-    out = {"metric": METRIC, "value": world * 1000.0 / ms, "unit": "steps/s", "n_gpus": world,
+    out = {"metric": METRIC, "value": reps.steps_per_s(ms), "unit": "steps/s", "n_gpus": world,
            "steps": args.steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": {"fp32": "f32", "mixed": "bf16x3/f32", "bf16": "bf16/f32"}[args.form] + " (f64 Cholesky, KKT)",
@@ -384,7 +374,7 @@ def run_ours(args):
                "admm_iters_last_step": st["iters"], "kkt_stat_last_step": st["kkt_stat"],
                "r_dual_last_step": st["r_dual"], "status_last_step": st["status"]}),
            "clocks": clocks,
-           "e2e": {"value": world * 1000.0 / ms_e2e, "unit": "steps/s",
+           "e2e": {"value": reps.steps_per_s(ms_e2e), "unit": "steps/s",
                    "h2d_bytes_per_step": int(wl.x0.nbytes), "d2h_bytes_per_step": int(prob_nU(wl) * 4)},
            "gpu_launches": int(kernels_per_step * args.steps),
            "roofline": roof,
@@ -399,8 +389,7 @@ def run_ours(args):
                                "kind": "oracle", "sample": SAMPLE_DESC.replace("4 sampled", "24 sampled"),
                                "seconds_per_step": secs, "parts_s": parts}
     print(json.dumps(out), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    reps.close()
 
 
 def prob_nU(wl):
