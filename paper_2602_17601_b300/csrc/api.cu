@@ -261,7 +261,6 @@ static size_t blob_floats(int K, int W, int nu) {
 
 // ---------------------------------------------------------------- workspace layout
 static constexpr int kMaxAdmmGrid = 2048;
-static constexpr int kMaxGramSplit = 64;
 
 static void plan(gm_ctx* c, Carver& cv) {
     const Cones& C = c->cones;
@@ -332,7 +331,7 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_z = cv.take<float>(nU + c->rows_c);
     c->d_rs = cv.take<float>(std::max(1L, c->rows_c));
     const long T = (nU + 31) / 32;
-    c->d_gram_part = cv.take<float>(std::max((long)kMaxGramSplit * T * T * 1024, 4L * 1024 * nU));
+    c->d_gram_part = cv.take<float>(std::max((long)kGramSplitCap * T * T * 1024, 4L * 1024 * nU));
     c->d_L = cv.take<double>((size_t)factor_pad(nU) * factor_pad(nU));
     c->d_Linv = cv.take<double>((size_t)factor_pad(nU) * factor_pad(nU));
     c->d_P = cv.take<float>((size_t)nU * nU);
