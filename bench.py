@@ -205,7 +205,7 @@ def run_reference(args):
 KERNEL_TC = ("tc_ws_bwd_kernel<EdgeMpBwd> (reverse edge-update MLP, warp-specialised persistent, "
              "split-BF16 tcgen05)")
 KERNEL_FP32 = "mlp2_kernel<128, EdgeMpBwd> (reverse edge-update MLP, FP32 SIMT)"
-TRAFFIC_SOURCES = ("paper_2602_17601_b300/csrc/tc_mlp.cuh", "paper_2602_17601_b300/csrc/tc_ws.cuh",
+TRAFFIC_SOURCES = ("paper_2602_17601_b300/csrc/tc_prim.cuh", "paper_2602_17601_b300/csrc/tc_mlp.cuh", "paper_2602_17601_b300/csrc/tc_ws.cuh",
                    "paper_2602_17601_b300/csrc/gnn.cu")
 
 

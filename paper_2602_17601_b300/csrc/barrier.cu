@@ -13,8 +13,8 @@
 // after which the QP keeps only the input box.
 //
 // Kernels: one warp per row for the row terms (FP64 dot products of the packed row with
-// U_hat), the weighted Gram kernel of the condensing for C~' diag(w) C~ (FP32, as for
-// rho C~'C~), and a transposed sweep that accumulates C~' v in FP64.
+// U_hat), the weighted Gram product C~' diag(w) C~ (the tensor-core Gram of the ADMM set-up,
+// FP32 operand precision), and a transposed sweep that accumulates C~' v in FP64.
 #include "admm.h"
 #include "kernels.h"
 

@@ -22,13 +22,15 @@ __global__ void row_norm_kernel(long rows, int nu, int Mnc, const float* __restr
     const int ks = (int)(r / Mnc);
     const int L = (ks + 1) * nu;
     const long off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (r - (long)ks * Mnc) * L;
-    double s = 0.0;
+    // FP32 sum of squares: the scale only preconditions the rows (any positive value leaves
+    // the feasible set and U* unchanged), and FP64 would run on the slow FP64 pipe
+    float s = 0.f;
     for (int c = lane; c < L; c += 32) {
-        const double v = Ct[off + c];
-        s += v * v;
+        const float v = Ct[off + c];
+        s = fmaf(v, v, s);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) rs[r] = (float)(1.0 / fmax(sqrt(s), 1e-8));   // floor keeps s_r^2 finite in FP32
+    if (lane == 0) rs[r] = 1.f / fmaxf(sqrtf(s), 1e-8f);   // floor keeps s_r^2 finite in FP32
 }
 
 // ---------------------------------------------------------------- FP64 KKT certificate
@@ -46,21 +48,28 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NW = blockDim.x >> 5;
     extern __shared__ double dsm[];          // [NW][n]
-    double part[KKT_MAXC];
-    for (int m = 0; m < KKT_MAXC; ++m) part[m] = 0.0;
+    double part[KKT_MAXC], ud[KKT_MAXC];
+#pragma unroll
+    for (int m = 0; m < KKT_MAXC; ++m) {
+        part[m] = 0.0;
+        ud[m] = lane + 32 * m < n ? (double)U[lane + 32 * m] : 0.0;   // converted once
+    }
     double prim = 0.0, dual = 0.0, comp = 0.0;
     for (long r = (long)blockIdx.x * NW + warp; r < rows; r += (long)gridDim.x * NW) {
         const int ks = (int)(r / Mnc);
         const int wi = (int)(r - (long)ks * Mnc);
         const int L = (ks + 1) * nu;
+        const int nm = (L + 31) >> 5;              // 32-column blocks the row reaches (warp-uniform)
         const long off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (long)wi * L;
         const double yr = y[n + r];
         double dot = 0.0;
+#pragma unroll
         for (int m = 0; m < KKT_MAXC; ++m) {
+            if (m >= nm) break;                    // FP64 issue slots only for the row's blocks
             const int c = lane + 32 * m;
             if (c < L) {
                 const double v = Ct[off + c];
-                dot += v * (double)U[c];
+                dot += v * ud[m];
                 part[m] += v * yr;
             }
         }
