@@ -73,22 +73,25 @@ __global__ void __launch_bounds__(GT_T, 1) gram_tc_kernel(GramRows R, int n, flo
     const unsigned idesc = tc_idesc(128, npad);
     bool ok = true, acc0 = false, acc1 = false;
     int issued = 0;                                             // tiles whose MMAs were committed
-    for (int t = 0; t < nt; ++t) {
-        const int b = t & 1;
-        if (t >= 2 && ok) ok = tc_wait(&mma_done[b], ((t - 2) >> 1) & 1, status);   // buffer b free again
-        if (!__syncthreads_and(ok)) break;
+    // item (m, i8) of a tile: column m of tile rows 8 i8 .. 8 i8 + 7, one 16-byte store per
+    // piece; the lanes of a warp take consecutive m, so every row read is coalesced.  The
+    // rows of tile t + 1 are loaded into registers (and its 64 row weights by threads 0..63)
+    // before tile t is converted and stored, so their round trip overlaps the staging and the
+    // MMAs of tile t.  The weight factors sqrt(w) (or w) of a tile sit in sw[tile & 1].
+    __shared__ float sw[2][GT_KT];
+    constexpr int MAXIT = 256 * (GT_KT / 8) / GT_T;
+    const int nit = npad * (GT_KT / 8);
+    float y[MAXIT][8], yn[MAXIT][8];
+    auto tile_of = [&](int t, int& k, int& rb) {
         const long id = blockIdx.x + (long)t * G;
-        const int k = (int)(id / tps) + 1;                     // stage (1-based), rows of length k nu
-        const int rb = (int)(id % tps) * GT_KT;
+        k = (int)(id / tps) + 1;                               // stage (1-based), rows of length k nu
+        rb = (int)(id % tps) * GT_KT;
+    };
+    auto load = [&](int t, float (&yy)[MAXIT][8]) {
+        int k, rb;
+        tile_of(t, k, rb);
         const int L = k * R.nu;
         const long base = (long)R.rows_per_stage * R.nu * ((long)k * (k - 1) / 2);
-        unsigned char* buf = gsm + (size_t)b * GT_P * piece;
-        // item (m, i8): column m of tile rows 8 i8 .. 8 i8 + 7, one 16-byte store per piece;
-        // the lanes of a warp take consecutive m, so every row read is coalesced.  All of a
-        // thread's loads are issued before the first conversion.
-        constexpr int MAXIT = 256 * (GT_KT / 8) / GT_T;
-        const int nit = npad * (GT_KT / 8);
-        float y[MAXIT][8];
 #pragma unroll
         for (int u = 0; u < MAXIT; ++u) {
             const int it = tid + u * GT_T;
@@ -96,36 +99,51 @@ __global__ void __launch_bounds__(GT_T, 1) gram_tc_kernel(GramRows R, int n, flo
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int r = rb + 8 * i8 + j;
-                y[u][j] = it < nit && m < L && r < R.rows_per_stage ? R.X[base + (long)r * L + m] : 0.f;
+                yy[u][j] = it < nit && r < R.rows_per_stage && m < L ? R.X[base + (long)r * L + m] : 0.f;
             }
         }
-        if (R.wts) {
-#pragma unroll
-            for (int u = 0; u < MAXIT; ++u) {
-                const int it = tid + u * GT_T;
-                const int i8 = it / npad;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int r = rb + 8 * i8 + j;
-                    if (it < nit && r < R.rows_per_stage) {
-                        const float w = R.wts[(long)(k - R.wts_k0) * R.rows_per_stage + r];
-                        y[u][j] *= R.wts_square ? w : sqrtf(w);
-                    }
-                }
-            }
+    };
+    auto weight = [&](int t) {                                 // thread tid < 64: row tid of tile t
+        int k, rb;
+        tile_of(t, k, rb);
+        const int r = rb + tid;
+        return R.wts && r < R.rows_per_stage ? R.wts[(long)(k - R.wts_k0) * R.rows_per_stage + r] : 1.f;
+    };
+    auto factor = [&](float w) { return R.wts_square ? w : sqrtf(w); };
+    if (nt > 0) {
+        load(0, y);
+        if (tid < GT_KT) sw[0][tid] = factor(weight(0));
+    }
+    for (int t = 0; t < nt; ++t) {
+        const int b = t & 1;
+        float wnext = 1.f;
+        if (t + 1 < nt) {
+            if (tid < GT_KT) wnext = weight(t + 1);
+            load(t + 1, yn);
         }
+        if (t >= 2 && ok) ok = tc_wait(&mma_done[b], ((t - 2) >> 1) & 1, status);   // buffer b free again
+        if (!__syncthreads_and(ok)) break;
+        int k, rb;
+        tile_of(t, k, rb);
+        const int L = k * R.nu;
+        unsigned char* buf = gsm + (size_t)b * GT_P * piece;
 #pragma unroll
         for (int u = 0; u < MAXIT; ++u) {
             const int it = tid + u * GT_T;
             if (it < nit) {
                 const int m = it % npad, i8 = it / npad;
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = y[u][j] * sw[b][8 * i8 + j];
                 uint4 pc[GT_P];
-                pack8<GT_P>(y[u], pc);
+                pack8<GT_P>(v, pc);
                 const int o = tc_off(m, 8 * i8, GT_KT);
 #pragma unroll
                 for (int p = 0; p < GT_P; ++p) *reinterpret_cast<uint4*>(buf + p * piece + o) = pc[p];
             }
         }
+        // sw[b ^ 1] was last read while tile t - 1 was staged, before the barrier above
+        if (t + 1 < nt && tid < GT_KT) sw[b ^ 1][tid] = factor(wnext);
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -151,6 +169,10 @@ __global__ void __launch_bounds__(GT_T, 1) gram_tc_kernel(GramRows R, int n, flo
             if (acc1) d1_used = 1;
         }
         ++issued;
+#pragma unroll
+        for (int u = 0; u < MAXIT; ++u)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) y[u][j] = yn[u][j];
     }
     // every MMA issued has completed before tensor memory is read and released
     if (tid == 0) tc_commit(&fin);
