@@ -410,9 +410,9 @@ gm_status gm_ctx_set_graph(gm_ctx* ctx, int on);
  * the instances one after another with plain launches; the next captures
  * every instance's step as a child graph of one parent graph with no
  * instances in lanes planned by gm_batch_plan (width: the larger of an
- * instance's cooperative ADMM and factor grids; cost: M * N * (1 + nU/64)),
- * so that the cooperative grids of the steps running at once fit on the
- * SMs together, and every later call with the same arguments replays that
+ * instance's cooperative ADMM and factor grids; cost: M * N * (1 + nU/64);
+ * capacity: half the SMs), so that the cooperative grids of the steps
+ * running at once fit on the SMs together with room to spare, and every later call with the same arguments replays that
  * graph with a single launch on the stream, the lanes running side by
  * side.  Changing any argument captures
  * anew.  x_meas, U, stats: host arrays of n device pointers (stats may be
@@ -427,6 +427,10 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
 gm_status gm_batch_state(const gm_batch* b, int* replayed, int* captures);
 /* Lanes of the last captured batch graph (1 before the first capture). */
 gm_status gm_batch_lanes(const gm_batch* b, int* lanes);
+/* At most this many lanes in the next captured batch graph (instance i in lane
+ * i mod lanes when fewer than gm_batch_plan's); 0 (the default) keeps the plan.
+ * lanes = 1 runs the instances one after another inside one graph launch. */
+gm_status gm_batch_set_lanes(gm_batch* b, int lanes);
 
 /* Host-only lane plan for n instance steps that each run cooperative grids
  * of up to width[i] CTAs (one CTA per SM assumed) and cost cost[i] (any

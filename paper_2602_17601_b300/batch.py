@@ -50,6 +50,10 @@ class Batch:
         _check("gm_batch_state", _lib.gm_batch_state(self.h, C.byref(r), C.byref(n)))
         return r.value, n.value
 
+    def set_lanes(self, lanes):
+        """At most this many lanes in the next capture (0: the plan's)."""
+        _check("gm_batch_set_lanes", _lib.gm_batch_set_lanes(self.h, int(lanes)))
+
     def lanes(self):
         n = C.c_int()
         _check("gm_batch_lanes", _lib.gm_batch_lanes(self.h, C.byref(n)))
@@ -106,6 +110,7 @@ def main(argv=None):
     ap.add_argument("--box-only", action="store_true")
     ap.add_argument("--cache", default=None, help="autotuner JSON cache (default: tuned here, not stored)")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="at most this many lanes (0: gm_batch_plan)")
     ap.add_argument("--max-iter", type=int, default=1000,
                     help="ADMM cap: a linearised sphere an instance's rollout drifts into can make its QP "
                          "infeasible, and ADMM then runs to the cap")
@@ -118,6 +123,7 @@ def main(argv=None):
     probs = problems_for(wls, prec, tuned, max_iter=a.max_iter)
     t_build = time.perf_counter() - t0 - t_tune
     batch = Batch(probs)
+    batch.set_lanes(a.lanes)
     batch.set_states([wl.x0 for wl in wls])
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     # one after another, plain launches

@@ -55,6 +55,7 @@ struct AdmmPlan {
     const float *Ct, *dt, *lo, *hi, *g, *H, *U0, *y0;
     const float* rs;       // row scales or nullptr
     const float* Gram;     // C~' D C~ or nullptr when there are no half-space rows
+    bool gram_tc = true;   // form it with the tensor-core Gram (gram_tc.cu)
     float *U, *y, *z;      // y, z: [n + rows]
     float *P, *Pinv;       // [n n]
     double *L, *Linv;      // [factor_pad(n)^2]

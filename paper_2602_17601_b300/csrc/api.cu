@@ -854,6 +854,7 @@ gm_status gm_batch_create(gm_ctx* const* ctxs, int n, gm_batch** out) {
     // side by side, instances fill the GPU: programmatic early launches would only hold SMs
     for (int i = 0; i < n; ++i) {
         ctxs[i]->pdl = false;
+        ctxs[i]->gram_tc = false;
         ctxs[i]->graph_key.clear();      // a context graph captured earlier is re-captured without it
     }
     *out = b;
@@ -904,8 +905,15 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
         width[i] = std::max(c->admm_grid, fg);
         cost[i] = (double)c->M * c->N * (1.0 + c->nU / 64.0);
     }
+    // The plan fills half the SMs with cooperative grids: plans that filled 144 of 148 SMs
+    // stalled in two of three 256-instance runs (54 and 105 s per batch step against 2.4 s,
+    // the GPU waiting on grid barriers), plans of 128 ran in every run.
     int lanes = 1;
-    GM_TRY(gm_batch_plan(n, width.data(), cost.data(), std::max(1, b->ctx[0]->num_sms), lane.data(), &lanes));
+    GM_TRY(gm_batch_plan(n, width.data(), cost.data(), std::max(1, b->ctx[0]->num_sms / 2), lane.data(), &lanes));
+    if (b->lanes_req > 0 && b->lanes_req < lanes) {   // fewer lanes: instance i in lane i mod L
+        lanes = b->lanes_req;
+        for (int i = 0; i < n; ++i) lane[i] = i % lanes;
+    }
     b->lanes = lanes;
     std::vector<int> tail(lanes, -1);
     cudaGraph_t parent = nullptr;
@@ -994,6 +1002,16 @@ gm_status gm_batch_plan(int n, const int* width, const double* cost, int sms, in
         lane_load[best] += cost[i];
     }
     *n_lanes = (int)lane_load.size();
+    return GM_OK;
+}
+
+gm_status gm_batch_set_lanes(gm_batch* b, int lanes) {
+    clear_error();
+    GM_CHECK_ARG(b && lanes >= 0, "NULL batch or lanes < 0");
+    if (lanes != b->lanes_req) {
+        b->lanes_req = lanes;
+        b->key.clear();              // the next call captures the graph again
+    }
     return GM_OK;
 }
 

@@ -123,9 +123,9 @@ gm_status barrier_fold(gm_ctx* c, const float* Ct, const float* dt, const float*
     const int g_dot = (int)std::max(1L, std::min((long)cdiv(rows * 32, (long)BAR_T), 8L * sms));
     barrier_rows_kernel<<<g_dot, BAR_T, 0, st>>>(rows, c->nu, Mnc, Ct, dt, U_hat, (double)mu, (double)delta, w, v);
     GM_LAUNCH_CHECK();
-    const int nsplit = gram_split(n, sms, kGramSplitCap);
+    const int nsplit = gram_split(n, sms, kGramSplitCap, c->gram_tc);
     GramRows R{Ct, Mnc, c->nu, c->N, w, 1, 0};
-    GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status));
+    GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status, c->gram_tc));
     gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, c->d_gram_part, nullptr, 0.f, c->d_G);
     GM_LAUNCH_CHECK();
     const int g_T = (int)std::max(1L, std::min((long)cdiv(rows, (long)nw), 4L * sms));

@@ -171,13 +171,13 @@ int gram_blocks(int n) {
     return T64 * (T64 + 1) / 2;
 }
 
-int gram_split(int n, int sms, int cap) {
-    if (gram_tc_ok(n)) return std::max(1, std::min(cap, sms));
+int gram_split(int n, int sms, int cap, bool tc) {
+    if (tc && gram_tc_ok(n)) return std::max(1, std::min(cap, sms));
     return std::max(1, std::min(cap, (2 * sms) / gram_blocks(n)));
 }
 
-gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStream_t st, int* status) {
-    if (gram_tc_ok(n)) return launch_gram_tc(R, n, nsplit, part, status, st);
+gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStream_t st, int* status, bool tc) {
+    if (tc && gram_tc_ok(n)) return launch_gram_tc(R, n, nsplit, part, status, st);
     gram_kernel<<<dim3(gram_blocks(n), nsplit), 256, 0, st>>>(R, n, part);
     GM_LAUNCH_CHECK();
     return GM_OK;
@@ -202,7 +202,7 @@ __global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ 
 gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, float diag_scale,
                float* G, cudaStream_t st) {
     const int n = c->nU;
-    GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status));
+    GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status, c->gram_tc));
     gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, c->d_gram_part, diag_add,
                                                               diag_scale, G);
     GM_LAUNCH_CHECK();
@@ -288,7 +288,7 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
     }
     // Eq. H: sum of per-node local Hessians + Rbar
     GramRows R{c->d_Gu, M * 6, nu, N, cost->Qdiag, 0, 0};
-    GM_TRY(gram(c, R, gram_split(c->nU, c->num_sms, kGramSplitCap), cost->Rdiag, 1.f, H, st));
+    GM_TRY(gram(c, R, gram_split(c->nU, c->num_sms, kGramSplitCap, c->gram_tc), cost->Rdiag, 1.f, H, st));
     // Eq. g
     const int gsplit = std::max(1, std::min(4 * c->num_sms, M * 6 / 8));
     grad_kernel<<<gsplit, 256, 0, st>>>(c->nU, M, nu, N, c->d_Gu, c->d_Gx, cost->Qdiag, cost->x_ref,

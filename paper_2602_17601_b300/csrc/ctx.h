@@ -23,6 +23,7 @@ struct gm_ctx;
 struct gm_batch {
     std::vector<gm_ctx*> ctx;
     int lanes = 1;                 // independent chains of instance steps in the batch graph
+    int lanes_req = 0;             // lanes asked for by gm_batch_set_lanes (0: gm_batch_plan)
     cudaGraphExec_t exec = nullptr;
     std::vector<uintptr_t> key;
     int eager = 0, captures = 0;
@@ -91,6 +92,8 @@ struct gm_ctx {
     long ct_len = 0;          // packed C~ length
     int num_sms = 0;
     bool pdl = true;             // programmatic dependent launch of the MLP kernels (off in a batch)
+    bool gram_tc = true;         // tensor-core Gram products (off in a batch: their one-CTA-per-SM
+                                 // grids starve the cooperative grids of the other lanes)
     int stage_chunk = 1;      // stages per reverse-pass launch group
 
     // host copies

@@ -501,7 +501,7 @@ gm_status ipm_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, 
     const int g_T = (int)std::max(1L, std::min((long)cdiv(rows, (long)(IPM_T / 32)), 4L * sms));
     const int g_el = (int)std::max(1L, std::min((long)cdiv(rows, (long)IPM_T), 8L * sms));
     const size_t smem_T = (size_t)(IPM_T / 32) * 2 * n * sizeof(double);
-    const int nsplit = gram_split(n, sms, kGramSplitCap);
+    const int nsplit = gram_split(n, sms, kGramSplitCap, c->gram_tc);
     auto vec = [&](int stage) {
         ipm_vec_kernel<<<1, IPM_T, 0, st>>>(a, stage, max_iter);
         return cudaGetLastError();
@@ -527,7 +527,7 @@ gm_status ipm_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, 
             GM_CUDA_TRY(vec(1));
             if (rows > 0) {
                 GramRows R{Ct, Mnc, c->nu, c->N, reinterpret_cast<const float*>(a.rw + RA_W * a.R), 1, 0};
-                GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status));
+                GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status, c->gram_tc));
                 gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, c->d_gram_part, nullptr, 0.f,
                                                                           c->d_G);
                 GM_LAUNCH_CHECK();

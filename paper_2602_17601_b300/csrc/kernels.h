@@ -37,16 +37,16 @@ gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, 
                float* G, cudaStream_t st);
 __global__ void gram_kernel(GramRows R, int n, float* __restrict__ part);
 // Partial Gram sums over nsplit row shares into part [nsplit][T][T][32 x 32] (T = ceil(n/32));
-// gram_split picks nsplit (at most cap): one share per SM for the tensor-core form (n <= 256,
-// gram_tc.cu), about two CTAs per SM for the FP32 SIMT kernel otherwise.  A context's
-// partial buffer holds kGramSplitCap shares.
+// gram_split picks nsplit (at most cap): one share per SM for the tensor-core form (tc and
+// n <= 256, gram_tc.cu), about two CTAs per SM for the FP32 SIMT kernel otherwise.  A
+// context's partial buffer holds kGramSplitCap shares.  launch_gram takes the same tc.
 // Final node latents of stage 0 into c->d_h; their pooled features (warm start, ws.cu).
 gm_status gnn_latents(gm_ctx* c, const float* x0, const float* u0, cudaStream_t st);
 gm_status ws_features(gm_ctx* c, const float* h, const float* x_ref, float* feat, cudaStream_t st);
 int gram_blocks(int n);
 constexpr int kGramSplitCap = 160;
-int gram_split(int n, int sms, int cap);
-gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStream_t st, int* status = nullptr);
+int gram_split(int n, int sms, int cap, bool tc);
+gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStream_t st, int* status, bool tc);
 bool gram_tc_ok(int n);
 gm_status launch_gram_tc(const GramRows& R, int n, int nsplit, float* part, int* status, cudaStream_t st);
 // qp.cu: row scales 1/|C~_r| and the FP64 KKT certificate of (U, y)

@@ -158,7 +158,7 @@ static gm_status solve_with(AdmmPlan& p, int sms, int nsplit, float* gram_part, 
             GM_LAUNCH_CHECK();
         }
         GramRows R{p.Ct, p.Mnc, p.nu, p.N, scale ? p.rs : nullptr, 1, 1};
-        GM_TRY(launch_gram(R, n, nsplit, gram_part, st, p.status));
+        GM_TRY(launch_gram(R, n, nsplit, gram_part, st, p.status, p.gram_tc));
         gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, gram_part, nullptr, 0.f,
                                                                   const_cast<float*>(p.Gram));
         GM_LAUNCH_CHECK();
@@ -202,7 +202,9 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     p.max_spins = c->s.timeout_spins > 0 ? c->s.timeout_spins : (1LL << 26);
     p.st = st;
     p.ev_mid = ev_mid;
-    return solve_with(p, c->num_sms, gram_split(n, c->num_sms, kGramSplitCap), c->d_gram_part, scale, c->d_kkt);
+    p.gram_tc = c->gram_tc;
+    return solve_with(p, c->num_sms, gram_split(n, c->num_sms, kGramSplitCap, c->gram_tc), c->d_gram_part, scale,
+                      c->d_kkt);
 }
 
 }  // namespace gmi
