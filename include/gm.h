@@ -465,7 +465,7 @@ gm_status gm_ctx_kernel_stats(gm_ctx* ctx, int* launches, double* ms, double* by
  * A 3-layer MLP  in -> H -> H -> out  (Linear-ReLU-Linear-ReLU-Linear) maps
  * the features of an MPC instance to a primal input sequence and box duals
  * (out = 2 nU: U^0 then y^0), which warm-start gm_qp_solve.  Cold-start
- * ADMM stays the judge: it runs whenever the warm-started solve does not
+ * ADMM stays the fallback: it runs whenever the warm-started solve does not
  * converge.  Features (gm_ws_features, [2W + 3M]): the mean and the max over
  * nodes of the final node latents h^K of stage 0 at (x_meas, the context's
  * current u_hat[0]; zeros after gm_ctx_reset), then the stage-1 reference
