@@ -504,6 +504,12 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
         set_error("no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(GM_ERR_CUDA);
     }
+    if (c->E > 0 && (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        set_error("side stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(GM_ERR_CUDA);
+    }
     const Cones& C = c->cones;
     const int K = c->K;
     std::vector<gm_status> rs;

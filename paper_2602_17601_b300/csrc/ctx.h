@@ -153,6 +153,9 @@ struct gm_ctx {
     std::vector<uintptr_t> graph_key;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // the edge encoder of a rollout stage runs on this stream beside the node encoder
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // launch timing of the reverse edge-update MLP (events around each launch of the last step)
     bool ktiming = false;
     int kev_n = 0;
@@ -166,5 +169,8 @@ struct gm_ctx {
             for (auto ev : e) cudaEventDestroy(ev);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (side_stream) cudaStreamDestroy(side_stream);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
     }
 };

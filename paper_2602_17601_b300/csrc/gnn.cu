@@ -410,17 +410,18 @@ static gm_status launch_ws_bwd(const gm_ctx* c, const Op& op, const TcW& tw, cud
 // pattern and x_hat match an FP32 evaluation) and the Jacobian products with two pieces;
 // GM_PREC_BF16 uses one piece everywhere.
 template <class Op>
-static gm_status launch_mlp(const gm_ctx* c, const Op& op, const TcW& tw, cudaStream_t st) {
+static gm_status launch_mlp(const gm_ctx* c, const Op& op, const TcW& tw, cudaStream_t st, bool pdl_ok = true) {
     if (op.rows <= 0) return GM_OK;
     const int W = c->W;
+    const bool pdl = c->pdl && pdl_ok;
     if (c->s.precision == GM_PREC_MIXED) {
         if constexpr (Op::kMode == 0) {
-            GM_TRY(launch_tc_w<3>(c->pdl, W, op, tw, st));
+            GM_TRY(launch_tc_w<3>(pdl, W, op, tw, st));
         } else {
-            GM_TRY(launch_tc_w<2>(c->pdl, W, op, tw, st));
+            GM_TRY(launch_tc_w<2>(pdl, W, op, tw, st));
         }
     } else if (c->s.precision == GM_PREC_BF16) {
-        GM_TRY(launch_tc_w<1>(c->pdl, W, op, tw, st));
+        GM_TRY(launch_tc_w<1>(pdl, W, op, tw, st));
     } else {
         int grid = cdiv(op.rows, BM);
         switch (W) {
@@ -476,16 +477,25 @@ uint32_t* edge_mask(const gm_ctx* c, int k, int layer) {
 // when xn is given, the decoder and the Euler update x_{k+1} = xn.  ReLU masks of stage k kept.
 static gm_status forward_stage(gm_ctx* c, int k, const float* xk, const float* uk, float* xn, cudaStream_t st) {
     const int M = c->M, E = c->E, W = c->W, K = c->K;
-    NodeEncFwd ne{};
-    fill_fwd(ne, c, 0, M, node_mask(c, k, 0));
-    ne.x = xk; ne.u = uk; ne.act = c->d_act; ne.h = c->d_h; ne.W = W; ne.nu = c->nu;
-    GM_TRY(launch_mlp(c, ne, tc_fwd(c, c->mlp[0]), st));
+    // the two encoders read only x_k: the edge encoder runs on the side stream beside the
+    // node encoder (a fork and a join of events, kept as graph branches when captured)
+    const bool fork = E > 0 && c->side_stream;
+    if (fork) {
+        GM_CUDA_TRY(cudaEventRecord(c->ev_fork, st));
+        GM_CUDA_TRY(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    }
     if (E > 0) {
         EdgeEncFwd ee{};
         fill_fwd(ee, c, 1, E, edge_mask(c, k, 0));
         ee.x = xk; ee.src = c->d_src; ee.dst = c->d_dst; ee.e = c->d_e; ee.W = W;
-        GM_TRY(launch_mlp(c, ee, tc_fwd(c, c->mlp[1]), st));
+        GM_TRY(launch_mlp(c, ee, tc_fwd(c, c->mlp[1]), fork ? c->side_stream : st, !fork));
     }
+    if (fork) GM_CUDA_TRY(cudaEventRecord(c->ev_join, c->side_stream));
+    NodeEncFwd ne{};
+    fill_fwd(ne, c, 0, M, node_mask(c, k, 0));
+    ne.x = xk; ne.u = uk; ne.act = c->d_act; ne.h = c->d_h; ne.W = W; ne.nu = c->nu;
+    GM_TRY(launch_mlp(c, ne, tc_fwd(c, c->mlp[0]), st));
+    if (fork) GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
     for (int t = 0; t < K; ++t) {
         if (E > 0) {
             EdgeMpFwd em{};
