@@ -403,6 +403,16 @@ unsigned long long gm_launch_count(void);
  * replayed a graph, 0 otherwise; captures counts the captures so far. */
 gm_status gm_ctx_set_graph(gm_ctx* ctx, int on);
 
+/* Receding-horizon warm start of gm_rti_step's ADMM (Algorithm 1 shifts the
+ * solution into the next linearisation point; with on != 0 the QP solve
+ * starts from it too): U^0 = u_hat (the previous U* shifted by one stage,
+ * last stage repeated) and y^0 = the previous multipliers shifted alike, box
+ * rows and half-space rows stage by stage, and rho starts where the previous
+ * solve's adaptation left it.  After gm_ctx_reset all three are back to the
+ * cold start (zeros, settings.rho).  Off by default.  The solve still runs to
+ * settings.tol, so the optimum is the same; only the iteration count changes. */
+gm_status gm_ctx_set_warm(gm_ctx* ctx, int on);
+
 /* Batched real-time iterations (no paper counterpart: many independent MPC
  * instances on one GPU).  A batch holds n contexts of any sizes (node count,
  * horizon, inputs, GNN); gm_batch_rti_step runs gm_rti_step on every instance

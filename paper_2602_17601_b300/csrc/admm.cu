@@ -57,9 +57,12 @@ __device__ __forceinline__ float wmaxf(float v) {
     return v;
 }
 
-__global__ void admm_state_init_kernel(AdmmState* S, float rho0) {
+// keep_rho: start from the rho the previous solve ended with (a receding-horizon warm start),
+// when it is a valid one; otherwise rho0.
+__global__ void admm_state_init_kernel(AdmmState* S, float rho0, int keep_rho) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        S->rho = rho0;
+        const float r = S->rho;
+        S->rho = keep_rho && r >= 1e-6f && r <= 1e6f ? r : rho0;
         S->need_factor = 1;
         S->done = 0;
         S->started = 0;
@@ -678,7 +681,7 @@ const void* admm2_kernel_ptr(int n) {
 gm_status admm_solve(const AdmmPlan& p) {
     cudaStream_t st = p.st;
     const int n = p.n;
-    admm_state_init_kernel<<<1, 32, 0, st>>>(p.S, p.rho0);
+    admm_state_init_kernel<<<1, 32, 0, st>>>(p.S, p.rho0, p.keep_rho ? 1 : 0);
     GM_LAUNCH_CHECK();
     admm_partition_kernel<<<cdiv(p.grid + 1, 128), 128, 0, st>>>(p.rows, p.nu, std::max(p.Mnc, 1), p.grid,
                                                                  p.row_begin);

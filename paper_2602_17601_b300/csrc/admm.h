@@ -56,6 +56,7 @@ struct AdmmPlan {
     const float* rs;       // row scales or nullptr
     const float* Gram;     // C~' D C~ or nullptr when there are no half-space rows
     bool gram_tc = true;   // form it with the tensor-core Gram (gram_tc.cu)
+    bool keep_rho = false; // start from the previous solve's final rho (warm start)
     float *U, *y, *z;      // y, z: [n + rows]
     float *P, *Pinv;       // [n n]
     double *L, *Linv;      // [factor_pad(n)^2]

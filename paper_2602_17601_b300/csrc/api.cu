@@ -328,6 +328,7 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_dt = cv.take<float>(std::max(1L, c->rows_c));
     c->d_U = cv.take<float>(nU);
     c->d_y = cv.take<float>(nU + c->rows_c);
+    c->d_yw = cv.take<float>(nU + c->rows_c);
     c->d_z = cv.take<float>(nU + c->rows_c);
     c->d_rs = cv.take<float>(std::max(1L, c->rows_c));
     const long T = (nU + 31) / 32;
@@ -556,6 +557,8 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
         if (r != GM_OK) return fail(r);
     if (cudaMemsetAsync(c->d_status, 0, sizeof(int) * 4, st) != cudaSuccess ||
         cudaMemsetAsync(c->d_u_hat, 0, sizeof(float) * c->N * c->nu, st) != cudaSuccess ||
+        cudaMemsetAsync(c->d_y, 0, sizeof(float) * (c->nU + c->rows_c), st) != cudaSuccess ||
+        cudaMemsetAsync(c->d_admm, 0, sizeof(AdmmState), st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("context upload failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(GM_ERR_CUDA);
@@ -660,6 +663,8 @@ gm_status gm_ctx_reset(gm_ctx* ctx, void* stream) {
     clear_error();
     GM_CHECK_ARG(ctx, "ctx is NULL");
     GM_CUDA_TRY(cudaMemsetAsync(ctx->d_u_hat, 0, sizeof(float) * ctx->N * ctx->nu, static_cast<cudaStream_t>(stream)));
+    GM_CUDA_TRY(cudaMemsetAsync(ctx->d_y, 0, sizeof(float) * (ctx->nU + ctx->rows_c), static_cast<cudaStream_t>(stream)));
+    GM_CUDA_TRY(cudaMemsetAsync(ctx->d_admm, 0, sizeof(AdmmState), static_cast<cudaStream_t>(stream)));
     return GM_OK;
 }
 
@@ -754,10 +759,13 @@ static gm_status rti_body(gm_ctx* c, const float* x_meas, const gm_cost* cost, c
     if (barrier)
         GM_TRY(barrier_fold(c, c->d_Ct, c->d_dt, c->d_u_hat, cons->barrier_mu, cons->barrier_delta, c->d_H, c->d_g,
                             st));
+    // receding-horizon warm start: U^0 = u_hat (the shifted previous solution), y^0 = the previous
+    // multipliers shifted by one stage alike (zero after gm_ctx_reset)
+    if (c->warm) GM_TRY(shift_duals(c, c->d_y, c->d_yw, st));
     if (timed) GM_CUDA_TRY(cudaEventRecord(ev[3], st));
     GM_TRY(qp_solve(c, c->d_H, c->d_g, barrier ? nullptr : c->d_Ct, barrier ? nullptr : c->d_dt, cons->u_lo,
-                    cons->u_hi, nullptr, nullptr, c->d_U, c->d_y, stats ? stats : c->d_stats, st,
-                    timed ? ev[4] : nullptr));
+                    cons->u_hi, c->warm ? c->d_u_hat : nullptr, c->warm ? c->d_yw : nullptr, c->d_U, c->d_y,
+                    stats ? stats : c->d_stats, st, timed ? ev[4] : nullptr, c->warm));
     if (timed) GM_CUDA_TRY(cudaEventRecord(ev[5], st));
     GM_CUDA_TRY(cudaMemcpyAsync(U, c->d_U, sizeof(float) * c->nU, cudaMemcpyDeviceToDevice, st));
     if (u0) GM_CUDA_TRY(cudaMemcpyAsync(u0, c->d_U, sizeof(float) * c->nu, cudaMemcpyDeviceToDevice, st));
@@ -777,7 +785,7 @@ static std::vector<uintptr_t> graph_key(const gm_ctx* c, const float* x_meas, co
     std::memcpy(&tol, &c->s.tol, 4);
     std::memcpy(&bmu, &cons->barrier_mu, 4);
     std::memcpy(&bdelta, &cons->barrier_delta, 4);
-    k.insert(k.end(), {(uintptr_t)bmu, (uintptr_t)bdelta});
+    k.insert(k.end(), {(uintptr_t)bmu, (uintptr_t)bdelta, (uintptr_t)c->warm});
     k.insert(k.end(), {(uintptr_t)rho, (uintptr_t)tol, (uintptr_t)c->s.max_iter, (uintptr_t)c->s.scale_rows,
                        (uintptr_t)c->s.adapt_rho, (uintptr_t)c->s.timeout_spins, (uintptr_t)c->s.polish});
     return k;
@@ -1036,6 +1044,13 @@ gm_status gm_batch_state(const gm_batch* b, int* replayed, int* captures) {
     return GM_OK;
 }
 
+gm_status gm_ctx_set_warm(gm_ctx* ctx, int on) {
+    clear_error();
+    GM_CHECK_ARG(ctx, "ctx is NULL");
+    ctx->warm = on != 0;
+    return GM_OK;
+}
+
 gm_status gm_ctx_set_graph(gm_ctx* ctx, int on) {
     clear_error();
     GM_CHECK_ARG(ctx, "ctx is NULL");
@@ -1103,6 +1118,30 @@ __global__ void shift_kernel(int N, int nu, const float* __restrict__ U, float* 
 
 gm_status shift_inputs(gm_ctx* c, const float* U, float* u_hat, cudaStream_t st) {
     shift_kernel<<<cdiv(c->N * c->nu, 128), 128, 0, st>>>(c->N, c->nu, U, u_hat);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
+// The multipliers shifted like the inputs: box rows [N][nu] and half-space rows [N][M n_c]
+// (stage-major) take stage k + 1's values, the last stage keeps its own.
+__global__ void shift_duals_kernel(int N, int nu, long Mnc, const float* __restrict__ y, float* __restrict__ yw) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long nU = (long)N * nu, total = nU + N * Mnc;
+    if (t >= total) return;
+    if (t < nU) {
+        const int k = (int)(t / nu), a = (int)(t % nu);
+        yw[t] = y[(long)(k + 1 < N ? k + 1 : N - 1) * nu + a];
+    } else {
+        const long r = t - nU;
+        const int k = (int)(r / Mnc);
+        yw[t] = y[nU + (long)(k + 1 < N ? k + 1 : N - 1) * Mnc + (r - (long)k * Mnc)];
+    }
+}
+
+gm_status shift_duals(gm_ctx* c, const float* y, float* yw, cudaStream_t st) {
+    const long Mnc = (long)c->M * c->n_c;
+    const long total = c->nU + (long)c->N * Mnc;
+    shift_duals_kernel<<<(unsigned)cdiv(total, 256L), 256, 0, st>>>(c->N, c->nu, Mnc, y, yw);
     GM_LAUNCH_CHECK();
     return GM_OK;
 }

@@ -92,6 +92,7 @@ struct gm_ctx {
     long ct_len = 0;          // packed C~ length
     int num_sms = 0;
     bool pdl = true;             // programmatic dependent launch of the MLP kernels (off in a batch)
+    bool warm = false;           // ADMM of gm_rti_step starts from the shifted previous (U, y)
     bool gram_tc = true;         // tensor-core Gram products (off in a batch: their one-CTA-per-SM
                                  // grids starve the cooperative grids of the other lanes)
     int stage_chunk = 1;      // stages per reverse-pass launch group
@@ -116,6 +117,7 @@ struct gm_ctx {
     gmi::DCones dc{};
     // rollout
     float *d_h = nullptr, *d_e = nullptr, *d_agg = nullptr;
+    float* d_yw = nullptr;       // shifted previous multipliers (ADMM warm start) [nU + rows]
     uint32_t *d_mask_node = nullptr, *d_mask_edge = nullptr;   // [N][layers][units][W/32]
     // reverse pass (per stage chunk)
     float *d_dhA = nullptr, *d_dhB = nullptr, *d_dacc = nullptr, *d_dagg = nullptr;

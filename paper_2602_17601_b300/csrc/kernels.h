@@ -74,15 +74,18 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
                    float* Ct, float* dt, cudaStream_t st);
 
 // qp.cu
-// ev_mid (nullable) is recorded between the set-up (P, Cholesky, inverse) and the iterations.
+// ev_mid (nullable) is recorded between the set-up (P, Cholesky, inverse) and the iterations;
+// keep_rho starts from the rho the previous solve on c ended with.
 gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, const float* dt,
                    const float* u_lo, const float* u_hi, const float* warm_U, const float* warm_y,
-                   float* U, float* y, gm_stats* stats, cudaStream_t st, cudaEvent_t ev_mid = nullptr);
+                   float* U, float* y, gm_stats* stats, cudaStream_t st, cudaEvent_t ev_mid = nullptr,
+                   bool keep_rho = false);
 
 size_t admm_smem_bytes(const gm_ctx* c);
 const void* admm_kernel_ptr(const gm_ctx* c);
 
 // small device utilities (api.cu)
 gm_status shift_inputs(gm_ctx* c, const float* U, float* u_hat, cudaStream_t st);
+gm_status shift_duals(gm_ctx* c, const float* y, float* yw, cudaStream_t st);
 
 }  // namespace gmi

@@ -181,7 +181,7 @@ const void* admm_kernel_ptr(const gm_ctx* c) { return admm2_kernel_ptr(c->nU); }
 
 gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, const float* dt,
                    const float* u_lo, const float* u_hi, const float* warm_U, const float* warm_y,
-                   float* U, float* y, gm_stats* stats, cudaStream_t st, cudaEvent_t ev_mid) {
+                   float* U, float* y, gm_stats* stats, cudaStream_t st, cudaEvent_t ev_mid, bool keep_rho) {
     const int n = c->nU;
     const long rows = Ct && dt ? c->rows_c : 0;    // no rows: the box-only QP
     const bool scale = rows > 0 && c->s.scale_rows;
@@ -195,6 +195,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     p.acc = c->d_acc; p.bar = c->d_bar; p.status = c->d_status; p.row_begin = c->d_row_begin;
     p.S = c->d_admm; p.stats = stats;
     p.rho0 = c->s.rho; p.tol = c->s.tol; p.max_iter = c->s.max_iter;
+    p.keep_rho = keep_rho;
     p.adapt_every = c->s.adapt_rho ? 25 : 0;
     p.rounds = c->s.adapt_rho ? 6 : 1;
     p.grid = rows > 0 ? c->admm_grid : 1;

@@ -9,6 +9,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import (GM_PREC_FP32, STATS_BYTES, gm_barrier_fold, gm_condense, gm_ctx_create, gm_ctx_destroy, gm_ctx_graph_state,
+               gm_ctx_set_warm,
                gm_ctx_reset, gm_ctx_set_graph, gm_ctx_workspace_size, gm_gnn_destroy, gm_gnn_load, gm_graph_create, gm_graph_destroy,
                gm_jac_pattern, gm_linearize, gm_qp_solve, gm_qp_solve_ipm, gm_rti_step, make_constr, make_cost,
                make_settings, read_stats)
@@ -22,12 +23,13 @@ class RTIProblem:
     x_ref, u_ref), input box (u_lo, u_hi) and either explicit position
     half-spaces (Cx, dx) or spheres linearised at the rollout.  barrier = (mu, delta)
     makes step() put those rows into the cost as relaxed log barriers (gm_barrier_fold).
+    warm=True starts each step's ADMM from the shifted previous solution (gm_ctx_set_warm).
     """
 
     def __init__(self, M, src, dst, nu, act_node, K, W, dt, blob, N, Qdiag, Rdiag, x_ref, u_ref, u_lo,
                  u_hi, Cx=None, dx=None, spheres=None, rho=0.1, tol=1e-6, max_iter=4000,
                  precision=GM_PREC_FP32, polish=0, timeout_spins=0, scale_rows=1, adapt_rho=1,
-                 graph=False, admm_grid=0, factor_grid=0, chunk_mb=0, barrier=None, device="cuda"):
+                 graph=False, admm_grid=0, factor_grid=0, chunk_mb=0, barrier=None, warm=False, device="cuda"):
         import torch
         self.torch = torch
         self.M, self.nu, self.N, self.K, self.W = int(M), int(nu), int(N), int(K), int(W)
@@ -65,6 +67,8 @@ class RTIProblem:
         self._U = torch.zeros(self.nU, dtype=torch.float32, device=device)
         if graph:
             gm_ctx_set_graph(self.ctx, 1)
+        if warm:
+            gm_ctx_set_warm(self.ctx, 1)
 
     @classmethod
     def from_workload(cls, wl, **kw):

@@ -42,6 +42,26 @@ def test_closed_loop_matches_oracle(lib):
     assert np.abs(S - So).max() <= 1e-4, np.abs(S - So).max()
 
 
+def test_warm_started_closed_loop_matches_oracle_in_fewer_iterations(lib):
+    """The receding-horizon warm start (gm_ctx_set_warm: each step's ADMM starts from the
+    shifted previous U*, y*) follows the oracle's closed loop as closely as cold starts do,
+    and needs fewer ADMM iterations once the loop runs."""
+    from paper_2602_17601_b300 import closed_loop
+    wl = small_chain()
+    x0 = np.asarray(wl.x0, np.float64).copy()
+    S, U, st_w = closed_loop.run(lib.RTIProblem.from_workload(wl, warm=True), x0, 6)
+    _, _, st_c = closed_loop.run(lib.RTIProblem.from_workload(small_chain()), x0, 6)
+    assert all(s["converged"] == 1 for s in st_w)
+    So, Uo = _oracle_loop(small_chain(), 6)
+    assert np.abs(U - Uo).max() <= 1e-4, np.abs(U - Uo).max()
+    assert np.abs(S - So).max() <= 1e-4, np.abs(S - So).max()
+    assert st_w[0]["iters"] == st_c[0]["iters"]                 # the first step starts cold
+    warm_its = sum(s["iters"] for s in st_w[1:])
+    cold_its = sum(s["iters"] for s in st_c[1:])
+    print(f"closed loop, steps 2-6: ADMM iterations warm {warm_its}, cold {cold_its}")
+    assert warm_its < cold_its, (warm_its, cold_its)
+
+
 def test_rollout_matches_oracle_step(lib):
     from paper_2602_17601_b300 import gm_rollout
     wl = small_chain()
