@@ -79,13 +79,14 @@ def cfg4_instances(n=256, first_seed=1000, constrained=True, Ms=(50, 1000), Ns=(
     return out
 
 
-def problems_for(workloads, precision, tuned=None, chunk_mb=256, max_iter=None):
-    """RTIProblem per workload with the autotuned launch shapes of its bucket (if given)."""
+def problems_for(workloads, precision, tuned=None, chunk_mb=256, max_iter=None, warm=False):
+    """RTIProblem per workload with the autotuned launch shapes of its bucket (if given); warm
+    starts each instance's ADMM from its own shifted previous solution (gm_ctx_set_warm)."""
     from .autotune import bucket_of
     from .rti import RTIProblem
     probs = []
     for wl in workloads:
-        kw = dict(precision=precision, chunk_mb=chunk_mb)
+        kw = dict(precision=precision, chunk_mb=chunk_mb, warm=warm)
         if max_iter:
             kw["max_iter"] = max_iter
         if tuned:
@@ -111,6 +112,7 @@ def main(argv=None):
     ap.add_argument("--cache", default=None, help="autotuner JSON cache (default: tuned here, not stored)")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--lanes", type=int, default=0, help="at most this many lanes (0: gm_batch_plan)")
+    ap.add_argument("--warm", action="store_true", help="receding-horizon ADMM warm start per instance")
     ap.add_argument("--max-iter", type=int, default=1000,
                     help="ADMM cap: a linearised sphere an instance's rollout drifts into can make its QP "
                          "infeasible, and ADMM then runs to the cap")
@@ -120,7 +122,7 @@ def main(argv=None):
     wls = cfg4_instances(a.n, constrained=not a.box_only)
     tuned = None if a.no_tune else load_or_tune(a.cache, prec)
     t_tune = time.perf_counter() - t0
-    probs = problems_for(wls, prec, tuned, max_iter=a.max_iter)
+    probs = problems_for(wls, prec, tuned, max_iter=a.max_iter, warm=a.warm)
     t_build = time.perf_counter() - t0 - t_tune
     batch = Batch(probs)
     batch.set_lanes(a.lanes)
@@ -152,7 +154,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     ms_batch = ev[2].elapsed_time(ev[3]) / a.steps
     st = [read_stats(p.stats) for p in probs]
-    rep = {"instances": a.n, "form": a.form, "constraints": "box" if a.box_only else "box + 5 spheres",
+    rep = {"instances": a.n, "form": a.form, "admm_warm_start": bool(a.warm),
+           "constraints": "box" if a.box_only else "box + 5 spheres",
            "M_range": [int(min(w.M for w in wls)), int(max(w.M for w in wls))],
            "N_values": sorted({int(w.N) for w in wls}), "nu_values": sorted({int(w.nu) for w in wls}),
            "steps": a.steps, "sequential_ms_per_batch_step": ms_seq, "batched_ms_per_batch_step": ms_batch,
