@@ -127,3 +127,21 @@ def test_batch_plan_lanes_fit_and_balance():
         gm.gm_batch_plan([0], [1.0], 148)
     with pytest.raises(gm.GMError):
         gm.gm_batch_plan([4], [-1.0], 148)
+
+
+def test_null_handles_are_rejected_on_the_host():
+    """Entry points taking a handle validate it before any CUDA call (GM_ERR_INVALID_ARG = 1)."""
+    import paper_2602_17601_b300 as gm
+    lib = ctypes.CDLL(gm.LIB_PATH)
+    lib.gm_ctx_set_warm.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.gm_ctx_set_graph.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.gm_batch_set_lanes.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.gm_barrier_fold.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_float] * 2 + [ctypes.c_void_p] * 3
+    lib.gm_qp_solve_ipm.argtypes = [ctypes.c_void_p] * 7 + [ctypes.c_int] + [ctypes.c_void_p] * 4
+    assert lib.gm_ctx_set_warm(None, 1) == 1
+    assert lib.gm_ctx_set_graph(None, 1) == 1
+    assert lib.gm_batch_set_lanes(None, 2) == 1
+    assert lib.gm_barrier_fold(None, None, None, None, 1e-3, 5e-3, None, None, None) == 1
+    assert lib.gm_qp_solve_ipm(None, None, None, None, None, None, None, 10, None, None, None, None) == 1
+    lib.gm_last_error.restype = ctypes.c_char_p
+    assert b"NULL" in lib.gm_last_error()
