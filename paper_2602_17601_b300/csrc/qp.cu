@@ -63,14 +63,23 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
         const long off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (long)wi * L;
         const double yr = y[n + r];
         double dot = 0.0;
+        if (yr != 0.0) {                           // warp-uniform: rows with a multiplier add C~_r' y_r
 #pragma unroll
-        for (int m = 0; m < KKT_MAXC; ++m) {
-            if (m >= nm) break;                    // FP64 issue slots only for the row's blocks
-            const int c = lane + 32 * m;
-            if (c < L) {
-                const double v = Ct[off + c];
-                dot += v * ud[m];
-                part[m] += v * yr;
+            for (int m = 0; m < KKT_MAXC; ++m) {
+                if (m >= nm) break;                // FP64 issue slots only for the row's blocks
+                const int c = lane + 32 * m;
+                if (c < L) {
+                    const double v = Ct[off + c];
+                    dot += v * ud[m];
+                    part[m] += v * yr;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < KKT_MAXC; ++m) {
+                if (m >= nm) break;
+                const int c = lane + 32 * m;
+                if (c < L) dot += (double)Ct[off + c] * ud[m];
             }
         }
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
