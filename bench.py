@@ -10,7 +10,12 @@ to residual 1e-4.
 
 One step = one gm_rti_step (rollout, Jacobians, condensing, QP set-up, ADMM,
 FP64 KKT check) on device-resident inputs; `e2e` adds the host->device copy of
-the measured state and the device->host copy of U* each step.
+the measured state and the device->host copy of U* each step.  The measured
+states are distinct: before timing, the controller runs the closed loop
+(Algorithm 1's outer loop) with the GNN itself as the plant, and timed step i
+uses the loop's state i, so every step linearises, condenses and warm-starts
+as in a receding-horizon run.  The same form with cold ADMM is timed on the
+same states beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--form mixed|bf16|fp32] [--no-graph] [--no-plain] [--workload chain1000|chain10]
@@ -172,31 +177,89 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-SAMPLE_DESC = ("one GNN stage x N, 4 sampled local Jacobian rows x N*M/4, condensing + ADMM on a "
+SAMPLE_DESC = ("one GNN stage x N, {n_jac} sampled local Jacobian rows x N*M/{n_jac}, condensing + ADMM on a "
                "50-node chain with the same N, nu, radius and spheres x M/50; extrapolated to one step")
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def full_oracle_steps():
+    """Measured (not extrapolated) full RTI steps of the FP64 oracle (oracle.rti.rti_step with its
+    ADMM, the method's own solver): the chain of 10 (K=2, W=32, N=10) and a chain of 50 with the
+    paper-scale GNN and horizon (K=3, W=128, N=20, nu=8, 5 spheres), each with all host cores and
+    with one BLAS thread."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle import rti as orti
+    from synth import paper_chain, small_chain
+    out = {}
+    for name, wl, reps in (("chain10_K2_W32_N10_nu4", small_chain(), 10),
+                           ("chain50_K3_W128_N20_nu8_spheres5", paper_chain(M=50), 1)):
+        ent = {}
+        for mode, limit in (("all_cores", None), ("one_thread", 1)):
+            with threadpool_limits(limits=limit):
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    orti.rti_step(wl, solver="admm")
+                sec = (time.perf_counter() - t0) / reps
+            ent[mode] = {"seconds_per_step": sec, "steps_per_s": 1.0 / sec, "steps_timed": reps}
+        out[name] = ent
+    return out
+
+
+def cpu_baseline(wl, n_jac=24):
+    """The oracle on the host cores: the bench workload's step extrapolated from a bounded
+    sample (its own key), and measured full steps at two smaller workloads."""
+    secs, parts = oracle_sample_seconds(wl, n_jac=n_jac)
+    return {"value": 1.0 / secs, "unit": "steps/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": SAMPLE_DESC.format(n_jac=n_jac),
+            "value_is": f"extrapolated: {wl.name} step from the sample above",
+            "extrapolated": {"workload": wl.name, "seconds_per_step": secs, "parts_s": parts},
+            "measured_full_steps": full_oracle_steps(),
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+
+
 def run_reference(args):
+    """The oracle as it stands on the host cores.  One reference step is one bounded sample of
+    the workload's step (oracle_sample_seconds), so the run ends within minutes: ms_per_step is
+    the measured wall time of a sample, and value is the full step's rate extrapolated from the
+    samples (the sample's share of the full step's work is fixed)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl = workload(args.workload)
     for _ in range(args.warmup):
         oracle_sample_seconds(wl)
-    secs = []
+    secs, walls = [], []
     t_wall = time.perf_counter()
     for s in range(args.steps):
+        t0 = time.perf_counter()
         t, _ = oracle_sample_seconds(wl, seed=s)
+        walls.append(time.perf_counter() - t0)
         secs.append(t)
     wall = time.perf_counter() - t_wall
-    ms = 1000.0 * statistics.mean(secs)
-    value = 1000.0 / ms
+    sample_ms = 1000.0 * statistics.mean(walls)
+    full_ms = 1000.0 * statistics.mean(secs)
+    value = 1000.0 / full_ms
+    full = full_oracle_steps()
     out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": sample_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
            "config": config_of(wl, "fp64-oracle"),
+           "step_is": "one bounded sample of the workload's step (ms_per_step: its measured wall time); "
+                      "value: the full step's rate extrapolated from the samples",
+           "extrapolated_full_step_ms": full_ms,
            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cpu_cores(), "kind": "oracle",
-                            "sample": SAMPLE_DESC},
+                            "sample": SAMPLE_DESC.format(n_jac=4), "measured_full_steps": full,
+                            "nproc": os.cpu_count(), "cpu_model": cpu_model()},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": wall}
     print(json.dumps(out), flush=True)
@@ -232,15 +295,32 @@ def kernel_traffic(form):
         return None
 
 
-def timed_steps(torch, prob, x_dev, U, steps, stream):
+def timed_steps(torch, prob, X, U, first, steps, stream):
+    """Device time per step of `steps` RTI steps at the measured states X[first + i]."""
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        prob.step(x_dev, U)
+    for i in range(steps):
+        prob.step(X[first + i], U)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps
+
+
+def closed_loop_states(prob, wl, n):
+    """Measured states of an n-step closed loop (Algorithm 1's outer loop): this problem's
+    controller drives the GNN itself as the plant from wl.x0 (gm_rollout applies u_0).
+    Returns the states [n][M*6] on the device and the per-step solve statistics."""
+    import torch
+
+    from paper_2602_17601_b300 import closed_loop
+    S, _, stats = closed_loop.run(prob, wl.x0, n)
+    X = torch.as_tensor(S[:n].reshape(n, -1), dtype=torch.float32, device="cuda").contiguous()
+    return X, stats
+
+
+def mean_iters(stats):
+    return float(statistics.mean(s["iters"] for s in stats)) if stats else None
 
 
 def run_ours(args):
@@ -257,31 +337,36 @@ def run_ours(args):
     graph = not args.no_graph
     warm = not args.no_warm
     prob = gm.RTIProblem.from_workload(wl, precision=precs[args.form], graph=graph, warm=warm)
-    info = gm.gm_ctx_info(prob.ctx)
     stream = torch.cuda.current_stream()
-    x_dev = torch.as_tensor(wl.x0, device="cuda").contiguous()
     U = prob.empty(prob.nU)
     warmup = max(args.warmup, 3)
-
+    n_states = warmup + args.steps
     barrier = reps.barrier
     max_over_ranks = reps.max_over_ranks
 
-    # ---- the chosen form, device-resident inputs; the first warm-up step runs eagerly and
-    # counts the kernels of one step, the second is captured (graph replay from then on)
-    prob.reset()
+    # ---- one eager step counts the kernels of a step (a fresh context's first step is eager)
     gm.gm_ctx_set_kernel_timing(prob.ctx, True)
     l0 = gm.gm_launch_count()
-    prob.step(x_dev, U)
+    prob.step(wl.x0, U)
     torch.cuda.synchronize()
     kernels_per_step = gm.gm_launch_count() - l0
-    for _ in range(warmup - 1):
-        prob.step(x_dev, U)
+
+    # ---- distinct measured states: the closed loop of this controller with the GNN as the plant,
+    # run once before timing; the timed steps then step through the same states in order, so each
+    # step's linearisation point, QP and warm start are those of a receding-horizon run
+    X, loop_stats = closed_loop_states(prob, wl, n_states)
+    timed_stats = loop_stats[warmup:]
+
+    # ---- the chosen form on device-resident states (graph replay from the second step on)
+    prob.reset()
+    for i in range(warmup):
+        prob.step(X[i], U)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    ms = timed_steps(torch, prob, x_dev, U, args.steps, stream)
+    ms = timed_steps(torch, prob, X, U, warmup, args.steps, stream)
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -290,12 +375,13 @@ def run_ours(args):
     st = prob.read_stats()
     ms = max_over_ranks(ms)
 
-    # ---- end to end through the public API: pinned host state in, U* out, every step
-    x_host = torch.as_tensor(wl.x0).pin_memory()
+    # ---- end to end through the public API: each step's state from pinned host memory in, U* out
+    X_host = X.cpu().pin_memory()
+    x_dev = torch.empty_like(X[0])
     U_host = torch.empty(prob.nU, dtype=torch.float32).pin_memory()
     prob.reset()
-    for _ in range(warmup):
-        x_dev.copy_(x_host, non_blocking=True)
+    for i in range(warmup):
+        x_dev.copy_(X_host[i], non_blocking=True)
         prob.step(x_dev, U)
         U_host.copy_(U, non_blocking=True)
     torch.cuda.synchronize()
@@ -303,8 +389,8 @@ def run_ours(args):
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     e2.record(stream)
-    for _ in range(args.steps):
-        x_dev.copy_(x_host, non_blocking=True)
+    for i in range(warmup, n_states):
+        x_dev.copy_(X_host[i], non_blocking=True)
         prob.step(x_dev, U)
         U_host.copy_(U, non_blocking=True)
     e3.record(stream)
@@ -315,24 +401,50 @@ def run_ours(args):
     gm.gm_ctx_set_kernel_timing(prob.ctx, False)
     gm.gm_ctx_set_timing(prob.ctx, True)
     gm.gm_ctx_phase_ms(prob.ctx)
-    for _ in range(3):
-        prob.step(x_dev, U)
+    prob.reset()
+    for i in range(warmup):
+        prob.step(X[i], U)
+    gm.gm_ctx_phase_ms(prob.ctx)
+    for i in range(warmup, min(warmup + 3, n_states)):
+        prob.step(X[i], U)
     phases, nrec = gm.gm_ctx_phase_ms(prob.ctx)
     gm.gm_ctx_set_timing(prob.ctx, False)
     per_phase = {k: v / max(nrec, 1) for k, v in phases.items()}
 
-    # ---- the plain GPU form: FP32 everywhere, eager launches, same inputs and residual
+    # ---- the same form with cold ADMM every step, on the same states
+    cold = None
+    if warm:
+        del prob
+        torch.cuda.empty_cache()
+        pc = gm.RTIProblem.from_workload(wl, precision=precs[args.form], graph=graph, warm=False)
+        pc.reset()
+        for i in range(warmup):
+            pc.step(X[i], U)
+        torch.cuda.synchronize()
+        barrier()
+        ms_c = max_over_ranks(timed_steps(torch, pc, X, U, warmup, args.steps, stream))
+        cstats = []
+        for i in range(warmup, n_states):              # untimed pass: iterations of each step
+            pc.step(X[i], U)
+            cstats.append(pc.read_stats())
+        cold = {"form": "same form, cold ADMM every step", "value": reps.steps_per_s(ms_c), "unit": "steps/s",
+                "ms_per_step": ms_c, "admm_iters_mean": mean_iters(cstats),
+                "statuses": sorted({s["status"] for s in cstats})}
+        del pc
+    else:
+        del prob
+
+    # ---- the plain GPU form: FP32 everywhere, eager launches, cold ADMM, same states and residual
     plain = None
     if not args.no_plain and args.form != "fp32":
-        del prob
         torch.cuda.empty_cache()
         pp = gm.RTIProblem.from_workload(wl, precision=gm.GM_PREC_FP32, graph=False)
         pp.reset()
-        for _ in range(warmup):
-            pp.step(x_dev, U)
+        for i in range(warmup):
+            pp.step(X[i], U)
         torch.cuda.synchronize()
         barrier()
-        ms_p = max_over_ranks(timed_steps(torch, pp, x_dev, U, args.steps, stream))
+        ms_p = max_over_ranks(timed_steps(torch, pp, X, U, warmup, args.steps, stream))
         sp = pp.read_stats()
         plain = {"form": "fp32, eager launches, cold ADMM", "value": reps.steps_per_s(ms_p), "unit": "steps/s",
                  "ms_per_step": ms_p, "admm_iters_last_step": sp["iters"], "kkt_stat_last_step": sp["kkt_stat"],
@@ -372,8 +484,14 @@ def run_ours(args):
            "config": config_of(wl, args.form, {
                "graph_replay": bool(replayed), "graph_captures": captures,
                "admm_warm_start": "shifted previous U*, y* (receding horizon)" if warm else "cold",
+               "states": f"closed-loop trajectory: {n_states} distinct measured states, the GNN as the plant "
+                         "driven by this controller (computed before timing; timed step i uses state i)",
                "parallelism": f"replicas{world}",
                "l2": "inputs larger than L2: the step streams ~2 GB of Jacobian/condensing buffers",
+               "admm_iters_mean": mean_iters(timed_stats),
+               "admm_iters_per_step": [s["iters"] for s in timed_stats],
+               "admm_iters_source": "the closed-loop pass that produced the states (same states, same warm starts)",
+               "statuses": sorted({s["status"] for s in timed_stats}),
                "admm_iters_last_step": st["iters"], "kkt_stat_last_step": st["kkt_stat"],
                "r_dual_last_step": st["r_dual"], "status_last_step": st["status"]}),
            "clocks": clocks,
@@ -383,14 +501,13 @@ def run_ours(args):
            "roofline": roof,
            "context": "paper: 100 Hz closed loop up to 1000 nodes, N=20 on RTX 4090 + Ryzen 9 7950X3D "
                       "with its own (unstated-size) trunk GNN; not this workload"}
+    if cold is not None:
+        out["cold_admm_form"] = cold
     if plain is not None:
         out["plain_gpu_form"] = plain
         out["speedup_vs_plain"] = plain["ms_per_step"] / ms
     if world == 1 and not args.no_cpu_baseline:
-        secs, parts = oracle_sample_seconds(wl, n_jac=24)
-        out["cpu_baseline"] = {"value": 1.0 / secs, "unit": "steps/s", "cores": cpu_cores(),
-                               "kind": "oracle", "sample": SAMPLE_DESC.replace("4 sampled", "24 sampled"),
-                               "seconds_per_step": secs, "parts_s": parts}
+        out["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(out), flush=True)
     reps.close()
 

@@ -277,7 +277,13 @@ gm_status gm_condense(gm_ctx* ctx, const float* x_hat, const float* A, const flo
  *   stats->status is GM_ERR_INFEASIBLE (U holds the last iterate).
  *   H, g, Ct, dt, u_lo, u_hi  as from gm_condense / gm_constr; Ct = dt = NULL
  *     solves the box-only QP (the barrier variant) even when n_c > 0
- *   warm_U [nU], warm_y [nU + N M n_c]  nullable warm start (U^0, y^0)
+ *   warm_U [nU], warm_y [nU + N M n_c]  nullable warm start (U^0, y^0).  A
+ *     warm-started solve watches its residual: when max(r_p, r_d) has not
+ *     fallen below half of its value 25 iterations earlier (a stall), or an
+ *     iterate turns NaN, it drops the warm start and restarts cold (U^0 = 0,
+ *     y^0 = 0, rho = settings.rho, P re-factored) inside the same call; a
+ *     restart that converges reports stats->status = GM_STALLED, and
+ *     stats->iters counts both parts.  A warm start may change rho once.
  *   U [nU] (out), y [nU + N M n_c] (out, nullable)  multipliers, box rows first
  *   stats  DEVICE gm_stats* (out, nullable)
  * Returns GM_OK even when ADMM did not converge; stats->status says so.
@@ -410,8 +416,20 @@ gm_status gm_ctx_set_graph(gm_ctx* ctx, int on);
  * rows and half-space rows stage by stage, and rho starts where the previous
  * solve's adaptation left it.  After gm_ctx_reset all three are back to the
  * cold start (zeros, settings.rho).  Off by default.  The solve still runs to
- * settings.tol, so the optimum is the same; only the iteration count changes. */
+ * settings.tol, so the optimum is the same; only the iteration count changes.
+ * A stalled warm start restarts cold inside the step (gm_qp_solve, GM_STALLED).
+ * After a step whose solve did not succeed (status other than GM_OK and
+ * GM_STALLED) the next step starts its duals at zero and rho at settings.rho;
+ * after GM_ERR_NUMERIC or GM_ERR_TIMEOUT, u_hat goes back to zero too
+ * (Algorithm 1's initial trajectory), with or without the warm start. */
 gm_status gm_ctx_set_warm(gm_ctx* ctx, int on);
+
+/* Cap on the device-side spin-waits (grid barriers of the cooperative ADMM and
+ * FP64 factor kernels) of this context's later calls, in polls; 0 restores the
+ * default (2^26).  A wait that runs out makes its kernel record GM_ERR_TIMEOUT
+ * in stats->status and return; the context stays usable.  spins < 0 is
+ * GM_ERR_INVALID_ARG.  (No paper counterpart: failure detection.) */
+gm_status gm_ctx_set_timeout_spins(gm_ctx* ctx, int spins);
 
 /* Batched real-time iterations (no paper counterpart: many independent MPC
  * instances on one GPU).  A batch holds n contexts of any sizes (node count,

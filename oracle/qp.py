@@ -172,7 +172,10 @@ def solve_exact(H, g, lo, hi, C=None, d=None):
 
 
 ROW_NORM_FLOOR = 1e-8
+REDUNDANT_MARGIN = 1e-4    # relative safety margin of the redundant-row test
 INFEAS_EVERY = 10          # ADMM iterations between infeasibility tests
+STALL_FACTOR = 0.5         # warm start stalls when max(r_p, r_d) is not below this fraction
+                           # of its value stall_every iterations earlier
 INFEAS_EPS = 1e-4          # relative tolerance of the certificate
 
 
@@ -202,6 +205,23 @@ def primal_infeasible(At, l, h, dy, eps=INFEAS_EPS):
     return bool(np.abs(At.T @ dy).max() <= e and wrong <= e and support <= -e)
 
 
+def redundant_rows(C, d, lo, hi, margin=None):
+    """Rows that no U in the input box can violate: the box's support in the row's direction,
+    max over lo <= U <= hi of C_r U = sum_c max(C_rc hi_c, C_rc lo_c), lies below d_r by more
+    than margin (|C_r|_1 max|bound| + |d_r|).  Such a row is inactive at every feasible U (its
+    multiplier is 0 at the optimum) and leaves the feasible set unchanged when dropped."""
+    margin = REDUNDANT_MARGIN if margin is None else margin
+    C = np.asarray(C, np.float64)
+    d = np.asarray(d, np.float64)
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    with np.errstate(invalid="ignore"):
+        sup = np.where(C > 0, C * hi, np.where(C < 0, C * lo, 0.0)).sum(axis=1)
+    bmax = np.maximum(np.abs(lo), np.abs(hi))
+    scale = np.where(C != 0, np.abs(C) * bmax, 0.0).sum(axis=1) + np.abs(d)
+    return sup < d - margin * scale
+
+
 def row_scaling(C):
     """s_r = 1 / max(|C_r|_2, 1e-8): unit rows, except rows that barely depend on U."""
     nr = np.sqrt((np.asarray(C, np.float64) ** 2).sum(axis=1))
@@ -209,7 +229,8 @@ def row_scaling(C):
 
 
 def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None, y0=None,
-         scale_rows=False, adapt_every=0, max_updates=5, detect_infeasible=True, return_info=False):
+         scale_rows=False, adapt_every=0, max_updates=5, detect_infeasible=True, return_info=False,
+         stall_every=0, drop_redundant=True):
     """ADMM on l <= A~U <= h (fixed rho, alpha = 1, sigma = 0, unscaled residuals).
 
         P     = H + rho A~'A~                      (factored once)
@@ -234,12 +255,34 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
     converged, stop when the dual step y - y_prev (on the rows the recurrence
     runs on) passes ``primal_infeasible``.
 
+    stall_every > 0 with a warm start (U0 or y0 given): the stall rule.  After
+    the first iteration, and again after each rho change, r = max(r_p, r_d) is
+    recorded; every stall_every iterations at which rho does not change, r is
+    compared with the record and becomes the new record.  When r is not below
+    STALL_FACTOR times the record (a stall), or an iterate is NaN, the warm
+    start is dropped and the recurrence restarts cold (U = 0, y = 0, rho = the
+    given rho, P re-factored, a fresh max_iter and max_updates) at the same
+    iteration count.  Before a restart rho may change once.
+
+    drop_redundant: half-space rows that no U in the input box can violate
+    (``redundant_rows``) take no part in the recurrence; their multipliers are
+    0 and their z is C_r U.  The optimum is the same.
+
     Returns U, z, y, iterations (number of U updates), r_p, r_d, converged;
-    return_info adds a dict {infeasible, dy} (dy for the original rows).
+    return_info adds a dict {infeasible, dy, restarted} (dy for the original
+    rows; restarted: the cold restart ran).
     """
     H = np.asarray(H, np.float64)
     g = np.asarray(g, np.float64)
     n = H.shape[0]
+    keep = None
+    if drop_redundant and C is not None and np.asarray(C).shape[0] > 0:
+        keep = np.nonzero(~redundant_rows(C, d, lo, hi))[0]
+        C_all, m_all = np.asarray(C, np.float64), np.asarray(C).shape[0]
+        C = C_all[keep]
+        d = np.asarray(d, np.float64)[keep]
+        if y0 is not None:
+            y0 = np.concatenate([np.asarray(y0, np.float64)[:n], np.asarray(y0, np.float64)[n:][keep]])
     s = None
     if scale_rows and C is not None and np.asarray(C).shape[0] > 0:
         s = row_scaling(C)
@@ -248,6 +291,7 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
         if y0 is not None:
             y0 = np.concatenate([y0[:n], y0[n:] / s])
     At, l, h = stack_rows(np.asarray(lo, np.float64), np.asarray(hi, np.float64), C, d)
+    rho0 = rho
     P = H + rho * At.T @ At
     L = np.linalg.cholesky(P)
     U = np.zeros(n) if U0 is None else np.asarray(U0, np.float64).copy()
@@ -255,10 +299,14 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
     z = np.clip(At @ U, l, h)
     r_p = r_d = np.inf
     it = 0
-    ok = infeasible = False
+    ok = infeasible = restarted = False
     dy = np.zeros_like(y)
     updates = 0
-    for it in range(1, max_iter + 1):
+    stall_on = stall_every > 0 and (U0 is not None or y0 is not None)
+    stall_ref = None
+    it0 = 0                                   # iteration count where the current start began
+    while True:
+        it += 1
         rhs = At.T @ (rho * z - y) - g
         U = np.linalg.solve(L.T, np.linalg.solve(L, rhs))
         a = At @ U
@@ -270,26 +318,58 @@ def admm(H, g, lo, hi, C=None, d=None, rho=0.1, tol=1e-6, max_iter=4000, U0=None
         if r_p <= tol and r_d <= tol:
             ok = True
             break
-        if detect_infeasible and it % INFEAS_EVERY == 0:
+        bad = not (np.isfinite(r_p) and np.isfinite(r_d))
+        if not bad and detect_infeasible and it % INFEAS_EVERY == 0:
             dy = y - y_prev
             if primal_infeasible(At, l, h, dy):
                 infeasible = True
                 break
-        if adapt_every and it % adapt_every == 0 and updates < max_updates:
-            ps = max(np.abs(a).max(), np.abs(z).max(), 1e-30)
-            ds = max(np.abs(H @ U).max(), np.abs(At.T @ y).max(), np.abs(g).max(), 1e-30)
-            ratio = (r_p / ps) / max(r_d / ds, 1e-30)
-            rn = min(max(rho * np.sqrt(ratio), 1e-6), 1e6)
-            if rn > 5 * rho or rn < 0.2 * rho:
-                rho = rn
-                updates += 1
-                L = np.linalg.cholesky(H + rho * At.T @ At)
+        if bad and stall_on:
+            stalled = True
+        else:
+            if bad or it - it0 >= max_iter:
+                break
+            stalled = False
+            may_adapt = updates < max_updates and not (stall_on and updates >= 1)
+            if adapt_every and it % adapt_every == 0 and may_adapt:
+                ps = max(np.abs(a).max(), np.abs(z).max(), 1e-30)
+                ds = max(np.abs(H @ U).max(), np.abs(At.T @ y).max(), np.abs(g).max(), 1e-30)
+                ratio = (r_p / ps) / max(r_d / ds, 1e-30)
+                rn = min(max(rho * np.sqrt(ratio), 1e-6), 1e6)
+                if rn > 5 * rho or rn < 0.2 * rho:
+                    rho = rn
+                    updates += 1
+                    L = np.linalg.cholesky(H + rho * At.T @ At)
+                    stall_ref = None                  # the residuals' scale changed: new record
+                    continue
+            if stall_on:
+                r = max(r_p, r_d)
+                if stall_ref is None:
+                    stall_ref = r
+                elif (it - it0) % stall_every == 0:
+                    stalled = not (r <= STALL_FACTOR * stall_ref)
+                    stall_ref = r
+        if stalled:
+            # drop the warm start: cold from here, with the initial rho
+            stall_on, restarted, it0, updates, rho = False, True, it, 0, rho0
+            L = np.linalg.cholesky(H + rho * At.T @ At)
+            U = np.zeros(n)
+            y = np.zeros(At.shape[0])
+            z = np.clip(At @ U, l, h)
+            continue
     if s is not None:
         y = np.concatenate([y[:n], y[n:] * s])
         z = np.concatenate([z[:n], z[n:] / s])
         dy = np.concatenate([dy[:n], dy[n:] * s])
+    if keep is not None:
+        # dropped rows: multiplier 0, z = C_r U
+        yf, df_ = np.zeros(n + m_all), np.zeros(n + m_all)
+        zf = np.concatenate([z[:n], C_all @ U])
+        yf[:n], df_[:n] = y[:n], dy[:n]
+        yf[n + keep], zf[n + keep], df_[n + keep] = y[n:], z[n:], dy[n:]
+        y, z, dy = yf, zf, df_
     if return_info:
-        return U, z, y, it, r_p, r_d, ok, dict(infeasible=infeasible, dy=dy)
+        return U, z, y, it, r_p, r_d, ok, dict(infeasible=infeasible, dy=dy, restarted=restarted)
     return U, z, y, it, r_p, r_d, ok
 
 

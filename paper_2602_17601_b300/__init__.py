@@ -130,6 +130,7 @@ def _load():
         "gm_batch_state": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "gm_batch_lanes": ([vp, C.POINTER(C.c_int)], C.c_int),
         "gm_ctx_set_warm": ([vp, C.c_int], C.c_int),
+        "gm_ctx_set_timeout_spins": ([vp, C.c_int], C.c_int),
         "gm_batch_set_lanes": ([vp, C.c_int], C.c_int),
         "gm_batch_plan": ([C.c_int, vp, vp, C.c_int, vp, C.POINTER(C.c_int)], C.c_int),
         "gm_barrier_fold": ([vp, vp, vp, vp, C.c_float, C.c_float, vp, vp, vp], C.c_int),
@@ -153,7 +154,7 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
                     "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
-                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_set_lanes", "gm_batch_plan", "gm_ctx_set_warm", "gm_barrier_fold",
+                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_set_lanes", "gm_batch_plan", "gm_ctx_set_warm", "gm_barrier_fold", "gm_ctx_set_timeout_spins",
                     "gm_rollout")
 
 GM_NOALLOC_MAX_NU = 64
@@ -208,6 +209,10 @@ def gm_batch_plan(width, cost, sms):
 
 def gm_ctx_set_warm(ctx, on):
     _check("gm_ctx_set_warm", _lib.gm_ctx_set_warm(ctx, int(bool(on))))
+
+
+def gm_ctx_set_timeout_spins(ctx, spins):
+    _check("gm_ctx_set_timeout_spins", _lib.gm_ctx_set_timeout_spins(ctx, int(spins)))
 
 
 def gm_ctx_set_graph(ctx, on):

@@ -58,11 +58,15 @@ __device__ __forceinline__ float wmaxf(float v) {
 }
 
 // keep_rho: start from the rho the previous solve ended with (a receding-horizon warm start),
-// when it is a valid one; otherwise rho0.
-__global__ void admm_state_init_kernel(AdmmState* S, float rho0, int keep_rho) {
+// when it is a valid one and that solve succeeded; otherwise rho0.  warm: U0 or y0 are given,
+// which turns on the stall test and the cold restart.
+__global__ void admm_state_init_kernel(AdmmState* S, float rho0, int keep_rho, int warm) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const float r = S->rho;
-        S->rho = keep_rho && r >= 1e-6f && r <= 1e6f ? r : rho0;
+        const int prev = S->final_status;
+        const bool prev_ok = prev == GM_OK || prev == GM_STALLED;
+        S->rho = keep_rho && prev_ok && r >= 1e-6f && r <= 1e6f ? r : rho0;
+        S->rho0 = rho0;
         S->need_factor = 1;
         S->done = 0;
         S->started = 0;
@@ -70,6 +74,11 @@ __global__ void admm_state_init_kernel(AdmmState* S, float rho0, int keep_rho) {
         S->updates = 0;
         S->converged = 0;
         S->rp = S->rd = 0.f;
+        S->warm = warm;
+        S->cold = 0;
+        S->fell_back = 0;
+        S->it0 = 0;
+        S->stall_ref = -1.f;
     }
 }
 
@@ -86,24 +95,35 @@ __global__ void admm_form_p_kernel(int n, const float* __restrict__ H, const flo
     P[t] = v;
 }
 
-// Tile of one stage: rows [t0, t0 + tr) of length L, starting at float offset off.
+// Tile of one stage: rows [t0, t0 + tr) of length L, starting at float offset off; live when
+// it holds a row that is not redundant (a tile of redundant rows is neither loaded nor passed).
 struct Tile {
     long t0, off;
     int tr, L;
+    bool live;
 };
 
 // Next tile of the row range [r, r1) after a tile ending at row r.
-__device__ __forceinline__ Tile next_tile(long r, long r1, int Mnc, int nu, int tile_floats, int tile_rows) {
+__device__ __forceinline__ Tile next_tile(long r, long r1, int Mnc, int nu, int tile_floats, int tile_rows,
+                                          const int* kpos, const int* kcnt) {
     Tile t;
     const int ks = (int)(r / Mnc);
     t.L = (ks + 1) * nu;
-    const long stage_end = min((long)(ks + 1) * Mnc, r1);
+    const long stage_end_all = (long)(ks + 1) * Mnc;
+    const long stage_end = min(stage_end_all, r1);
     int tr = max(1, tile_floats / t.L);
     tr = min(tr, tile_rows);
     tr = (int)min((long)tr, stage_end - r);
     t.t0 = r;
     t.tr = tr;
     t.off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (r - (long)ks * Mnc) * t.L;
+    if (kpos) {
+        const long e = r + tr;
+        const int p1 = e < stage_end_all ? __ldg(kpos + e) : __ldg(kcnt + ks);
+        t.live = p1 > __ldg(kpos + r);
+    } else {
+        t.live = true;
+    }
     return t;
 }
 
@@ -157,11 +177,21 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
     const float inv_rho = 1.f / rho;
     const bool first = !S->started;
     int it = S->iters;
+    // the warm inputs, unless a stall or a NaN made this solve restart cold
+    const bool cold = S->cold != 0;
+    const float* U0 = cold ? nullptr : a.U0;
+    const float* y0 = cold ? nullptr : a.y0;
+    const bool stall_on = S->warm && !cold;    // the stall test watches warm starts only
+    float stall_ref = S->stall_ref;
+    const int it0 = S->it0;
+    const int updates0 = S->updates;
     for (int c = tid; c < n; c += ADMM_T) {
         if (first) {
-            su[c] = a.U0 ? a.U0[c] : 0.f;
-            yb[c] = a.y0 ? a.y0[c] : 0.f;
-            zb[c] = fminf(fmaxf(su[c], a.lo[c]), a.hi[c]);
+            su[c] = U0 ? U0[c] : 0.f;
+            yb[c] = y0 ? y0[c] : 0.f;
+            // z = clip(U0); a NaN stays NaN (fminf/fmaxf would drop it), so a NaN warm start
+            // shows in the first iterate
+            zb[c] = su[c] == su[c] ? fminf(fmaxf(su[c], a.lo[c]), a.hi[c]) : su[c];
         } else {
             su[c] = S->u[c];
             zb[c] = S->zb[c];
@@ -186,6 +216,10 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
         int cur_L = -1;
         __syncthreads();
         auto issue = [&](const Tile& t, int b) {
+            if (!t.live) {                                     // an empty group keeps the count
+                cp_async_commit();
+                return;
+            }
             float* dst = tbuf[b];
             const float* src = a.Ct + t.off;
             const int cnt = t.tr * t.L;
@@ -198,7 +232,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             for (int i = tid; i < t.tr; i += ADMM_T) {
                 const long r = t.t0 + i;
                 if (init) {
-                    if (a.y0) cp_async4(rsb + i, a.y0 + n + r);
+                    if (y0) cp_async4(rsb + i, y0 + n + r);
                 } else {
                     cp_async4(rsb + i, a.y + n + r);
                     cp_async4(rsb + a.tile_rows + i, a.z + n + r);
@@ -212,7 +246,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
         Tile q[NB];
         int head = 0, nq = 0;                                  // tiles in flight: slots head .. head+nq-1
         for (int k = 0; k < NB - 1 && rnext < r1; ++k) {
-            q[k] = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows);
+            q[k] = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows, a.kpos, a.kcnt);
             rnext = q[k].t0 + q[k].tr;
             issue(q[k], k);
             ++nq;
@@ -220,7 +254,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
         while (nq > 0) {
             if (rnext < r1 && nq < NB) {
                 const int sl = (head + nq) % NB;
-                q[sl] = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows);
+                q[sl] = next_tile(rnext, r1, a.Mnc, a.nu, a.tile_floats, a.tile_rows, a.kpos, a.kcnt);
                 rnext = q[sl].t0 + q[sl].tr;
                 issue(q[sl], sl);
                 ++nq;
@@ -229,6 +263,11 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             __syncthreads();
             const int b = head;
             const Tile cur = q[b];
+            if (!cur.live) {                                   // redundant rows only (uniform)
+                head = (head + 1) % NB;
+                --nq;
+                continue;
+            }
             const float* T = tbuf[b];
             float* rsb = rstate[b];
             const int L = cur.L, tr = cur.tr;
@@ -252,7 +291,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
                 const float d = rsb[2 * a.tile_rows + i] * s;
                 float yv, zv;
                 if (init) {
-                    yv = a.y0 ? rsb[i] / s : 0.f;
+                    yv = y0 && s > 0.f ? rsb[i] / s : 0.f;          // s = 0: a redundant row
                     zv = fminf(av, d);
                 } else {
                     const float yo = rsb[i];
@@ -402,7 +441,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
 
     unsigned phase = 0;
     int pass = 0;
-    bool ok = true, done = false, converged = false, adapt = false;
+    bool ok = true, done = false, converged = false, adapt = false, restart = false;
     float rp_last = S->rp, rd_last = S->rd;
     if (first) {
         if (blockIdx.x == 0)
@@ -545,13 +584,20 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             const float e = kInfeasEps * dmax;
             infeasible = dmax > 0.f && ad <= e && nmaxf(v[4], s_misc[4]) <= e && v[5] + s_misc[5] <= -e;
         }
+        if (bad && stall_on) {
+            // a NaN warm start: the next launch re-factors P(rho0) and starts cold
+            restart = true;
+            break;
+        }
         if (bad && blockIdx.x == 0 && tid == 0) dev_fail(a.status, GM_ERR_NUMERIC);
         if (infeasible && blockIdx.x == 0 && tid == 0) dev_fail(a.status, GM_ERR_INFEASIBLE);
-        if (converged || bad || infeasible || it >= a.max_iter) {
+        if (converged || bad || infeasible || it - it0 >= a.max_iter) {
             done = true;
             break;
         }
-        if (a.adapt_every > 0 && !a.last_round && it % a.adapt_every == 0) {
+        // a warm start may change rho once; a second change waits for the stall test
+        const bool may_adapt = !a.last_round && updates0 < kMaxRhoUpdates && !(stall_on && updates0 >= 1);
+        if (a.adapt_every > 0 && may_adapt && it % a.adapt_every == 0) {
             // relative residuals: r_p / max(|a|, |z|) against r_d / max(|H U|, |A~'y|, |g|)
             float hu = 0.f, gm = 0.f, ym = 0.f;
             for (int c = warp; c < n; c += NW) {
@@ -578,6 +624,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             __syncthreads();
             if (rn > 5.f * rho || rn < 0.2f * rho) {
                 adapt = true;
+                stall_ref = -1.f;                     // the residuals' scale changes: new record
                 if (blockIdx.x == 0 && tid == 0) {
                     S->rho = rn;
                     S->updates = S->updates + 1;
@@ -585,8 +632,42 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
                 break;
             }
         }
+        // stall test of a warm start at iterations where rho did not change (uniform over the
+        // grid: every CTA holds the same residuals): max(r_p, r_d) must fall below kStallFactor
+        // of its value kStallEvery iterations earlier
+        if (stall_on) {
+            const float r = fmaxf(rp, rd);
+            if (stall_ref < 0.f) {
+                stall_ref = r;
+            } else if ((it - it0) % kStallEvery == 0) {
+                const bool stalled = !(r <= kStallFactor * stall_ref);
+                stall_ref = r;
+                if (stalled) {
+                    // abandon the warm start: the next launch re-factors P(rho0) and starts cold
+                    restart = true;
+                    break;
+                }
+            }
+        }
     }
     // save the state (CTA 0) / finish
+    if (restart) {
+        if (blockIdx.x == 0 && tid == 0) {
+            S->started = 0;
+            S->cold = 1;
+            S->fell_back = 1;
+            S->rho = S->rho0;
+            S->need_factor = 1;
+            S->updates = 0;
+            S->iters = it;
+            S->it0 = it;
+            S->converged = 0;
+            S->rp = rp_last;
+            S->rd = rd_last;
+            S->done = 0;
+        }
+        return;
+    }
     if (blockIdx.x == 0) {
         for (int c = tid; c < n; c += ADMM_T) {
             S->u[c] = su[c];
@@ -603,6 +684,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             S->converged = converged ? 1 : 0;
             S->need_factor = adapt ? 1 : 0;
             S->done = (done || !ok) ? 1 : 0;
+            S->stall_ref = stall_ref;
         }
     }
     if (done || !ok) {
@@ -611,7 +693,7 @@ __global__ void __launch_bounds__(ADMM_T) admm2_kernel(Admm2Args a) {
             for (long r = r0 + tid; r < r1; r += ADMM_T) {
                 const float s = a.rs[r];
                 a.y[n + r] *= s;
-                a.z[n + r] /= s;
+                a.z[n + r] = s > 0.f ? a.z[n + r] / s : 0.f;
             }
         if (blockIdx.x == 0) {
             for (int c = tid; c < n; c += ADMM_T) {
@@ -681,7 +763,7 @@ const void* admm2_kernel_ptr(int n) {
 gm_status admm_solve(const AdmmPlan& p) {
     cudaStream_t st = p.st;
     const int n = p.n;
-    admm_state_init_kernel<<<1, 32, 0, st>>>(p.S, p.rho0, p.keep_rho ? 1 : 0);
+    admm_state_init_kernel<<<1, 32, 0, st>>>(p.S, p.rho0, p.keep_rho ? 1 : 0, p.warm ? 1 : 0);
     GM_LAUNCH_CHECK();
     admm_partition_kernel<<<cdiv(p.grid + 1, 128), 128, 0, st>>>(p.rows, p.nu, std::max(p.Mnc, 1), p.grid,
                                                                  p.row_begin);
@@ -690,6 +772,7 @@ gm_status admm_solve(const AdmmPlan& p) {
     a.n = n; a.nu = p.nu; a.Mnc = std::max(p.Mnc, 1); a.rows = p.rows;
     a.Ct = p.Ct; a.dt = p.dt; a.lo = p.lo; a.hi = p.hi; a.g = p.g; a.H = p.H; a.Pinv = p.Pinv;
     a.rs = p.rs; a.U0 = p.U0; a.y0 = p.y0; a.U = p.U; a.y = p.y; a.z = p.z; a.acc = p.acc;
+    a.kpos = p.rows > 0 ? p.kpos : nullptr; a.kcnt = p.rows > 0 ? p.kcnt : nullptr;
     a.bar = p.bar; a.status = p.status; a.row_begin = p.row_begin; a.S = p.S; a.stats = p.stats;
     a.tol = p.tol; a.max_iter = p.max_iter; a.adapt_every = p.adapt_every; a.max_spins = p.max_spins;
     a.tile_floats = admm2_tile_floats(n);

@@ -13,6 +13,12 @@ constexpr int kAdmmTileRows = 512;      // rows per tile at most
 constexpr int kAdmmMaxN = 256;          // N nu
 constexpr int kInfeasEvery = 10;        // iterations between primal-infeasibility tests
 constexpr float kInfeasEps = 1e-4f;     // relative tolerance of the infeasibility certificate
+constexpr int kStallEvery = 25;         // warm-started solves: iterations between stall tests
+constexpr float kStallFactor = 0.5f;    // a stall: max(r_p, r_d) not below this fraction of its
+                                        // value kStallEvery iterations earlier
+constexpr int kWarmRounds = 2;          // launches a warm-started solve may use (one rho update)
+constexpr int kMaxRhoUpdates = 5;       // rho changes per start (warm or cold)
+constexpr float kRedundantMargin = 1e-4f; // relative margin of the redundant-row test (qp.cu)
 
 // Floats of one rotating accumulator: sums of s C~'z, s C~'y, s C~'dy ([3n]) and 8 scalars
 // (max |a - z|, |a|, |z|, |dy|, wrong-sign dy; sum of the bound support of dy).
@@ -28,6 +34,13 @@ struct AdmmState {
     int updates;       // rho changes so far
     int converged;
     float rp, rd;
+    float rho0;        // the settings' rho (the cold restart starts from it)
+    int warm;          // this solve started from warm inputs: the stall test is on
+    int cold;          // the warm start was abandoned: U0, y0 are ignored from now on
+    int fell_back;     // the cold restart ran (reported as GM_STALLED when it converged)
+    int it0;           // iteration count when the current start (warm or cold) began
+    float stall_ref;   // max(r_p, r_d) at the last stall test (< 0: not yet taken)
+    int final_status;  // gm_status of the last finished solve (next step's warm start reads it)
     float u[kAdmmMaxN], zb[kAdmmMaxN], yb[kAdmmMaxN], atz[kAdmmMaxN], aty[kAdmmMaxN];
 };
 
@@ -35,6 +48,7 @@ struct Admm2Args {
     int n, nu, Mnc;
     long rows;
     const float *Ct, *dt, *lo, *hi, *g, *H, *Pinv, *rs, *U0, *y0;
+    const int *kpos, *kcnt;   // kept-row positions per stage and counts (nullable: no skipping)
     float *U, *y, *z, *acc;
     unsigned* bar;
     int* status;
@@ -53,10 +67,13 @@ struct AdmmPlan {
     int n, nu, Mnc, N;
     long rows;
     const float *Ct, *dt, *lo, *hi, *g, *H, *U0, *y0;
-    const float* rs;       // row scales or nullptr
+    const float* rs;       // row scales (0: a redundant row) or nullptr when there are no rows
+    const unsigned char* keep;   // [rows] 0 for redundant rows
+    const int *kpos, *kcnt;      // [rows] position among the stage's kept rows, [N] kept per stage
     const float* Gram;     // C~' D C~ or nullptr when there are no half-space rows
     bool gram_tc = true;   // form it with the tensor-core Gram (gram_tc.cu)
     bool keep_rho = false; // start from the previous solve's final rho (warm start)
+    bool warm = false;     // U0 or y0 given: stall test, cold restart on a stall or a NaN
     float *U, *y, *z;      // y, z: [n + rows]
     float *P, *Pinv;       // [n n]
     double *L, *Linv;      // [factor_pad(n)^2]

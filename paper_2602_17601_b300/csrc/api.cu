@@ -322,6 +322,7 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_dx = cv.take<float>(std::max(1L, c->rows_c));
     c->d_Gu = cv.take<float>((size_t)M * 6 * nu * ((size_t)N * (N + 1) / 2));
     c->d_Gx = cv.take<float>((size_t)(N + 1) * M * 6);
+    c->d_defect = cv.take<float>((size_t)N * M * 6);
     c->d_H = cv.take<float>((size_t)nU * nU);
     c->d_g = cv.take<float>(nU);
     c->d_Ct = cv.take<float>(std::max(1L, c->ct_len));
@@ -331,6 +332,9 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_yw = cv.take<float>(nU + c->rows_c);
     c->d_z = cv.take<float>(nU + c->rows_c);
     c->d_rs = cv.take<float>(std::max(1L, c->rows_c));
+    c->d_keep = cv.take<unsigned char>(std::max(1L, c->rows_c));
+    c->d_kpos = cv.take<int>(std::max(1L, c->rows_c));
+    c->d_kcnt = cv.take<int>(c->N);
     const long T = (nU + 31) / 32;
     c->d_gram_part = cv.take<float>(std::max((long)kGramSplitCap * T * T * 1024, 4L * 1024 * nU));
     c->d_L = cv.take<double>((size_t)factor_pad(nU) * factor_pad(nU));
@@ -1051,6 +1055,14 @@ gm_status gm_ctx_set_warm(gm_ctx* ctx, int on) {
     return GM_OK;
 }
 
+gm_status gm_ctx_set_timeout_spins(gm_ctx* ctx, int spins) {
+    clear_error();
+    GM_CHECK_ARG(ctx, "ctx is NULL");
+    GM_CHECK_ARG(spins >= 0, "spins must be >= 0 (got %d)", spins);
+    ctx->s.timeout_spins = spins;       // part of a captured step's key: the next step re-captures
+    return GM_OK;
+}
+
 gm_status gm_ctx_set_graph(gm_ctx* ctx, int on) {
     clear_error();
     GM_CHECK_ARG(ctx, "ctx is NULL");
@@ -1108,26 +1120,42 @@ gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures) {
 namespace gmi {
 
 // Algorithm 1 "update lin. trajectory": u_hat_k = U*_{k+1} (k < N-1), u_hat_{N-1} = U*_{N-1}.
-__global__ void shift_kernel(int N, int nu, const float* __restrict__ U, float* __restrict__ u_hat) {
+// A solve that ended in NaN or gave up on a device wait leaves no usable U*: the trajectory
+// then goes back to Algorithm 1's initial one (zeros), so that one failed step does not
+// poison the steps after it.
+__global__ void shift_kernel(int N, int nu, const float* __restrict__ U, float* __restrict__ u_hat,
+                             const AdmmState* S) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * nu) return;
+    const int prev = S->final_status;
+    if (prev == GM_ERR_NUMERIC || prev == GM_ERR_TIMEOUT) {
+        u_hat[t] = 0.f;
+        return;
+    }
     int k = t / nu, a = t % nu;
     int src = k + 1 < N ? k + 1 : N - 1;
     u_hat[t] = U[src * nu + a];
 }
 
 gm_status shift_inputs(gm_ctx* c, const float* U, float* u_hat, cudaStream_t st) {
-    shift_kernel<<<cdiv(c->N * c->nu, 128), 128, 0, st>>>(c->N, c->nu, U, u_hat);
+    shift_kernel<<<cdiv(c->N * c->nu, 128), 128, 0, st>>>(c->N, c->nu, U, u_hat, c->d_admm);
     GM_LAUNCH_CHECK();
     return GM_OK;
 }
 
 // The multipliers shifted like the inputs: box rows [N][nu] and half-space rows [N][M n_c]
-// (stage-major) take stage k + 1's values, the last stage keeps its own.
-__global__ void shift_duals_kernel(int N, int nu, long Mnc, const float* __restrict__ y, float* __restrict__ yw) {
+// (stage-major) take stage k + 1's values, the last stage keeps its own.  After a solve that
+// did not succeed (status other than GM_OK and GM_STALLED) the duals start at zero.
+__global__ void shift_duals_kernel(int N, int nu, long Mnc, const float* __restrict__ y, float* __restrict__ yw,
+                                   const AdmmState* S) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long nU = (long)N * nu, total = nU + N * Mnc;
     if (t >= total) return;
+    const int prev = S->final_status;
+    if (prev != GM_OK && prev != GM_STALLED) {
+        yw[t] = 0.f;
+        return;
+    }
     if (t < nU) {
         const int k = (int)(t / nu), a = (int)(t % nu);
         yw[t] = y[(long)(k + 1 < N ? k + 1 : N - 1) * nu + a];
@@ -1141,7 +1169,7 @@ __global__ void shift_duals_kernel(int N, int nu, long Mnc, const float* __restr
 gm_status shift_duals(gm_ctx* c, const float* y, float* yw, cudaStream_t st) {
     const long Mnc = (long)c->M * c->n_c;
     const long total = c->nU + (long)c->N * Mnc;
-    shift_duals_kernel<<<(unsigned)cdiv(total, 256L), 256, 0, st>>>(c->N, c->nu, Mnc, y, yw);
+    shift_duals_kernel<<<(unsigned)cdiv(total, 256L), 256, 0, st>>>(c->N, c->nu, Mnc, y, yw, c->d_admm);
     GM_LAUNCH_CHECK();
     return GM_OK;
 }

@@ -7,6 +7,7 @@
 // Gamma_u^i.  Stage k reads stage k-1 of the nodes in the K-hop neighbourhood
 // of i only, so one stage costs O(M) (Thm. 1).
 #include "ctx.h"
+#include "ff.cuh"
 #include "kernels.h"
 
 namespace gmi {
@@ -49,12 +50,49 @@ __host__ __device__ static inline long gu_offset(int M, int nu, int k) {   // st
     return (long)M * 6 * nu * ((long)k * (k - 1) / 2);
 }
 
+// Gamma_x is kept as its offset from the rollout, D_k = Gamma_x_k - x_hat_k (D_0 = 0), which
+// follows the recursion of Eq. sparse_gamma_i_xb with c substituted:
+//   D_{k+1} = sum_j A^{ij}_k D^j_k + e^i_k,   e^i_k = c^i_k - x_hat^i_{k+1} + sum_j A^{ij}_k x_hat^j_k
+// (e = -B u_hat in exact arithmetic).  Gamma_x holds absolute positions of order one while the
+// quantities that use it (Gamma_x - x_ref, the clearance d - C Gamma_x) are small, so the FP32
+// recursion on Gamma_x itself would lose their low bits to cancellation; e is summed in
+// float-float pairs and D stays small.  One warp per (stage, node), lanes over the blocks'
+// (j, t) columns.
+__global__ void defect_kernel(int N, int M, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                              long nnzb, const float* __restrict__ A, const float* __restrict__ cvec,
+                              const float* __restrict__ x_hat, float* __restrict__ e) {
+    const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (long)N * M) return;
+    const int k = (int)(w / M), i = (int)(w % M);
+    const float* xk = x_hat + (long)k * M * 6;
+    const float* Ak = A + (long)k * nnzb * 36;
+    const int b0 = row_ptr[i], nb = row_ptr[i + 1] - b0;
+    FF s[6];
+    for (int q = lane; q < nb * 6; q += 32) {
+        const int b = q / 6, t = q % 6;
+        const float x = xk[(long)col[b0 + b] * 6 + t];
+        const float* Ab = Ak + (long)(b0 + b) * 36 + t;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) ff_add_prod(s[a], Ab[a * 6], x);
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        FF t = ff_warp_sum(s[a]);
+        if (lane == 0) {
+            ff_add(t, cvec[((long)k * M + i) * 6 + a]);
+            ff_add(t, -x_hat[((long)(k + 1) * M + i) * 6 + a]);
+            e[((long)k * M + i) * 6 + a] = ff_value(t);
+        }
+    }
+}
+
 // Stage k -> k+1 for one node per block:
 //   (Gamma_u^i)_{k+1} last block row = [sum_j A^{ij}_k (Gamma_u^j)_k last row , B^i_k]
-//   (Gamma_x^i)_{k+1} last block     =  sum_j A^{ij}_k (Gamma_x^j)_k last block + c^i_k
+//   D^i_{k+1}                         =  sum_j A^{ij}_k D^j_k + e^i_k     (see defect_kernel)
 __global__ void recursion_kernel(int k, int M, int nu, const int* __restrict__ row_ptr,
                                  const int* __restrict__ col, const float* __restrict__ A,
-                                 const float* __restrict__ B, const float* __restrict__ cvec,
+                                 const float* __restrict__ B, const float* __restrict__ ek,
                                  const float* __restrict__ Gu_k, const float* __restrict__ Gx_k,
                                  float* __restrict__ Gu_k1, float* __restrict__ Gx_k1) {
     extern __shared__ float sA[];
@@ -85,7 +123,7 @@ __global__ void recursion_kernel(int k, int M, int nu, const int* __restrict__ r
                 Gu_k1[((long)i * 6 + a) * Lk1 + cc] = B[((long)i * 6 + a) * nu + (cc - Lk)];
         } else {
 #pragma unroll
-            for (int a = 0; a < 6; ++a) o[a] = cvec[(long)i * 6 + a];
+            for (int a = 0; a < 6; ++a) o[a] = ek[(long)i * 6 + a];
             for (int b = 0; b < nb; ++b) {
                 const int j = sj[b];
 #pragma unroll
@@ -209,10 +247,12 @@ gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, 
     return GM_OK;
 }
 
-// g = -Rbar u_ref + sum_k sum_{i,a} Gu_k[i,a]^T Q^i_k[a] (Gx_k[i,a] - x_ref_k[i,a])
+// g = -Rbar u_ref + sum_k sum_{i,a} Gu_k[i,a]^T Q^i_k[a] (Gx_k[i,a] - x_ref_k[i,a]),
+// with Gx - x_ref = (x_hat - x_ref) + D (D = Gamma_x - x_hat, see recursion_kernel)
 __global__ void grad_kernel(int n, int M, int nu, int N, const float* __restrict__ Gu,
-                            const float* __restrict__ Gx, const float* __restrict__ Q,
-                            const float* __restrict__ xr, float* __restrict__ part) {
+                            const float* __restrict__ Gx, const float* __restrict__ xh,
+                            const float* __restrict__ Q, const float* __restrict__ xr,
+                            float* __restrict__ part) {
     const int sp = blockIdx.x, nsplit = gridDim.x;
     const int rows = M * 6;
     for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
@@ -225,7 +265,7 @@ __global__ void grad_kernel(int n, int M, int nu, int N, const float* __restrict
             const int r0 = sp * per, r1 = min(rows, r0 + per);
             for (int r = r0; r < r1; ++r) {
                 const long qi = (long)k * rows + r;
-                const float w = Q[qi] * (Gx[qi] - xr[qi]);
+                const float w = Q[qi] * ((xh[qi] - xr[qi]) + Gx[qi]);
                 if (w != 0.f) acc = fmaf(Gu[base + (long)r * L + cc], w, acc);
             }
         }
@@ -243,12 +283,12 @@ __global__ void grad_reduce_kernel(int n, int nsplit, const float* __restrict__ 
     g[cc] = s;
 }
 
-// C~ row (k, i, c) = C^{x,i}_k[c] . Gamma_u^i position rows of stage k; d~ = d - C . Gamma_x position.
-// One warp per (k, i).
+// C~ row (k, i, c) = C^{x,i}_k[c] . Gamma_u^i position rows of stage k; d~ = d - C . Gamma_x position
+// = (d - C . x_hat position) - C . D position (D = Gamma_x - x_hat).  One warp per (k, i).
 __global__ void constraint_kernel(int N, int M, int nu, int n_c, const float* __restrict__ Gu,
-                                  const float* __restrict__ Gx, const float* __restrict__ Cx,
-                                  const float* __restrict__ dx, float* __restrict__ Ct,
-                                  float* __restrict__ dt) {
+                                  const float* __restrict__ Gx, const float* __restrict__ xh,
+                                  const float* __restrict__ Cx, const float* __restrict__ dx,
+                                  float* __restrict__ Ct, float* __restrict__ dt) {
     const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= (long)N * M) return;
@@ -264,7 +304,8 @@ __global__ void constraint_kernel(int N, int M, int nu, int n_c, const float* __
             out[col] = a0 * g0[col] + a1 * g0[L + col] + a2 * g0[2 * L + col];
         if (lane == 0) {
             const float* gx = Gx + ((long)k * M + i) * 6;
-            dt[crow] = dx[crow] - (a0 * gx[0] + a1 * gx[1] + a2 * gx[2]);
+            const float* xp = xh + ((long)k * M + i) * 6;
+            dt[crow] = (dx[crow] - (a0 * xp[0] + a1 * xp[1] + a2 * xp[2])) - (a0 * gx[0] + a1 * gx[1] + a2 * gx[2]);
         }
     }
 }
@@ -273,16 +314,22 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
                    const gm_cost* cost, const float* Cx, const float* dx, float* H, float* g,
                    float* Ct, float* dt, cudaStream_t st) {
     const int M = c->M, nu = c->nu, N = c->N;
-    // Gamma_x stage 0 is the measured state (x_hat_0)
-    GM_CUDA_TRY(cudaMemcpyAsync(c->d_Gx, x_hat, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, st));
+    // Gamma_x stage 0 is the measured state x_hat_0: offset D_0 = 0
+    GM_CUDA_TRY(cudaMemsetAsync(c->d_Gx, 0, sizeof(float) * M * 6, st));
     int maxnb = 0;
     for (int i = 0; i < M; ++i) maxnb = std::max(maxnb, c->jac_row_ptr[i + 1] - c->jac_row_ptr[i]);
     const size_t smem = (size_t)maxnb * 36 * sizeof(float) + (size_t)maxnb * sizeof(int);
+    {
+        const long warps = (long)N * M;
+        defect_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(N, M, c->dc.nr_ptr_K, c->d_jac_col, c->nnzb, A, cvec,
+                                                            x_hat, c->d_defect);
+        GM_LAUNCH_CHECK();
+    }
     for (int k = 0; k < N; ++k) {
         const float* Guk = k > 0 ? c->d_Gu + gu_offset(M, nu, k) : nullptr;
         recursion_kernel<<<M, 128, smem, st>>>(
             k, M, nu, c->dc.nr_ptr_K, c->d_jac_col, A + (long)k * c->nnzb * 36,
-            B + (long)k * M * 6 * nu, cvec + (long)k * M * 6, Guk, c->d_Gx + (long)k * M * 6,
+            B + (long)k * M * 6 * nu, c->d_defect + (long)k * M * 6, Guk, c->d_Gx + (long)k * M * 6,
             c->d_Gu + gu_offset(M, nu, k + 1), c->d_Gx + (long)(k + 1) * M * 6);
         GM_LAUNCH_CHECK();
     }
@@ -291,7 +338,7 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
     GM_TRY(gram(c, R, gram_split(c->nU, c->num_sms, kGramSplitCap, c->gram_tc), cost->Rdiag, 1.f, H, st));
     // Eq. g
     const int gsplit = std::max(1, std::min(4 * c->num_sms, M * 6 / 8));
-    grad_kernel<<<gsplit, 256, 0, st>>>(c->nU, M, nu, N, c->d_Gu, c->d_Gx, cost->Qdiag, cost->x_ref,
+    grad_kernel<<<gsplit, 256, 0, st>>>(c->nU, M, nu, N, c->d_Gu, c->d_Gx, x_hat, cost->Qdiag, cost->x_ref,
                                        c->d_gram_part);
     GM_LAUNCH_CHECK();
     grad_reduce_kernel<<<cdiv(c->nU, 128), 128, 0, st>>>(c->nU, gsplit, c->d_gram_part, cost->Rdiag,
@@ -300,7 +347,7 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
     // stacked constraints
     if (c->n_c > 0) {
         const long warps = (long)N * M;
-        constraint_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(N, M, nu, c->n_c, c->d_Gu, c->d_Gx,
+        constraint_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(N, M, nu, c->n_c, c->d_Gu, c->d_Gx, x_hat,
                                                                 Cx, dx, Ct, dt);
         GM_LAUNCH_CHECK();
     }

@@ -127,8 +127,11 @@ struct gm_ctx {
     float *d_u_hat = nullptr, *d_x_hat = nullptr, *d_A = nullptr, *d_B = nullptr, *d_c = nullptr;
     float *d_Cx = nullptr, *d_dx = nullptr;
     float *d_Gu = nullptr, *d_Gx = nullptr;
+    float* d_defect = nullptr;   // condensing: e_k = c_k - x_hat_{k+1} + A_k x_hat_k  [N][M][6]
     float *d_H = nullptr, *d_g = nullptr, *d_Ct = nullptr, *d_dt = nullptr;
     float *d_U = nullptr, *d_y = nullptr, *d_z = nullptr, *d_rs = nullptr;
+    unsigned char* d_keep = nullptr;   // ADMM: 0 for redundant half-space rows
+    int *d_kpos = nullptr, *d_kcnt = nullptr;   // kept-row positions per stage, kept rows per stage
     float *d_gram_part = nullptr;
     double *d_L = nullptr, *d_Linv = nullptr;
     float *d_P = nullptr, *d_Pinv = nullptr, *d_G = nullptr;

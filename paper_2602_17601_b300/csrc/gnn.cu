@@ -16,6 +16,7 @@
 // the host.  This differentiates each subsystem's local dynamics independently
 // (Sec. V-A "Linearization") with work proportional to the cone sizes.
 #include "ctx.h"
+#include "ff.cuh"
 #include "kernels.h"
 
 namespace gmi {
@@ -813,7 +814,9 @@ __global__ void jac_assemble_kernel(int Ns, int k0, int M, int nu, int K, float 
     const int ncol = 6 + nu;
     const float* xk = x_hat + (long)k * M * 6;
     const float* xk1 = x_hat + (long)(k + 1) * M * 6;
-    float cacc[6] = {0, 0, 0, 0, 0, 0};
+    // c = x_hat_{k+1} - A x_hat_k - B u_hat is small beside its terms (positions of order one):
+    // its sums run in float-float pairs so that c keeps its own relative precision
+    FF cacc[6];
     for (int q = nr_ptr_K[s] + lane; q < nr_ptr_K[s + 1]; q += 32) {
         const int n = nr_node_K[q];
         float J[3][6];
@@ -846,16 +849,11 @@ __global__ void jac_assemble_kernel(int Ns, int k0, int M, int nu, int K, float 
             float* Ab = A + ((long)k * nnzb + q) * 36;
             for (int i = 0; i < 36; ++i) Ab[i] = blk[i];
         }
-        for (int a6 = 0; a6 < 6; ++a6) {
-            float acc = 0.f;
-            for (int t = 0; t < 6; ++t) acc += blk[a6 * 6 + t] * xk[n * 6 + t];
-            cacc[a6] += acc;
-        }
+        for (int a6 = 0; a6 < 6; ++a6)
+            for (int t = 0; t < 6; ++t) ff_add_prod(cacc[a6], blk[a6 * 6 + t], xk[n * 6 + t]);
     }
-    for (int a6 = 0; a6 < 6; ++a6)
-        for (int o = 16; o > 0; o >>= 1) cacc[a6] += __shfl_xor_sync(0xffffffffu, cacc[a6], o);
     // B^s: the node-encoder cotangent of input channel 6 + a at the actuator's node
-    float bu[6] = {0, 0, 0, 0, 0, 0};
+    // the B u_hat terms go into the same sums
     for (int a = lane; a < nu; a += 32) {
         const int q = b_row[s * nu + a];
         float col[6];
@@ -867,14 +865,22 @@ __global__ void jac_assemble_kernel(int Ns, int k0, int M, int nu, int K, float 
         const float ua = u_hat[(long)k * nu + a];
         for (int r6 = 0; r6 < 6; ++r6) {
             if (B) B[(((long)k * M + s) * 6 + r6) * nu + a] = col[r6];
-            bu[r6] += col[r6] * ua;
+            ff_add_prod(cacc[r6], col[r6], ua);
         }
     }
-    for (int r6 = 0; r6 < 6; ++r6)
-        for (int o = 16; o > 0; o >>= 1) bu[r6] += __shfl_xor_sync(0xffffffffu, bu[r6], o);
-    if (lane == 0 && cvec) {
-        for (int r6 = 0; r6 < 6; ++r6)
-            cvec[((long)k * M + s) * 6 + r6] = xk1[s * 6 + r6] - cacc[r6] - bu[r6];
+    if (cvec) {
+        for (int r6 = 0; r6 < 6; ++r6) {
+            FF t = ff_warp_sum(cacc[r6]);
+            if (lane == 0) {
+                FF cv;
+                cv.hi = xk1[s * 6 + r6];
+                cv.lo = 0.f;
+                t.hi = -t.hi;
+                t.lo = -t.lo;
+                ff_add_ff(cv, t);
+                cvec[((long)k * M + s) * 6 + r6] = ff_value(cv);
+            }
+        }
     }
 }
 

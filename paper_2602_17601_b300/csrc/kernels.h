@@ -57,7 +57,8 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
 __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float* __restrict__ g,
                                  const float* __restrict__ lo, const float* __restrict__ hi,
                                  const float* __restrict__ U, const float* __restrict__ y,
-                                 const double* __restrict__ kkt, const int* status, gm_stats* stats);
+                                 const double* __restrict__ kkt, const int* status, gm_stats* stats,
+                                 AdmmState* S);   // S nullable: records the final status, GM_STALLED
 // barrier.cu: relaxed log-barrier obstacle rows folded into H and g
 gm_status barrier_fold(gm_ctx* c, const float* Ct, const float* dt, const float* U_hat, float mu, float delta,
                        float* H, float* g, cudaStream_t st);

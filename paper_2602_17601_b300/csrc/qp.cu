@@ -33,6 +33,75 @@ __global__ void row_norm_kernel(long rows, int nu, int Mnc, const float* __restr
     if (lane == 0) rs[r] = 1.f / fmaxf(sqrtf(s), 1e-8f);   // floor keeps s_r^2 finite in FP32
 }
 
+// Row preparation of the ADMM: the row scale and the redundant-row test.  A row that no U in
+// the input box can violate, because the box's support in its direction,
+//     sup_r = max over lo <= U <= hi of C~_r U = sum_c max(C~_rc hi_c, C~_rc lo_c),
+// lies below d~_r by more than kRedundantMargin (|C~_r|_1 max|bound| + |d~_r|), is inactive at
+// every feasible U (its multiplier is 0 at the optimum) and does not change the feasible set.
+// It gets s_r = 0, which takes it out of C~'S^2 C~ and out of every ADMM pass (keep_r = 0).
+// Otherwise s_r = 1 / max(|C~_r|_2, 1e-8) (scale) or 1.  NaN rows are kept.  One warp per row.
+__global__ void row_prep_kernel(long rows, int nu, int Mnc, const float* __restrict__ Ct,
+                                const float* __restrict__ dt, const float* __restrict__ lo,
+                                const float* __restrict__ hi, int scale, float* __restrict__ rs,
+                                unsigned char* __restrict__ keep) {
+    const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const int ks = (int)(r / Mnc);
+    const int L = (ks + 1) * nu;
+    const long off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (r - (long)ks * Mnc) * L;
+    float ss = 0.f, sup = 0.f, sc = 0.f;
+    for (int c = lane; c < L; c += 32) {
+        const float v = Ct[off + c];
+        ss = fmaf(v, v, ss);
+        if (v != 0.f) {
+            const float l = lo[c], h = hi[c];
+            sup += v > 0.f ? v * h : v * l;
+            sc += fabsf(v) * fmaxf(fabsf(l), fabsf(h));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        sup += __shfl_xor_sync(0xffffffffu, sup, o);
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+    }
+    if (lane == 0) {
+        const float d = dt[r];
+        const bool redundant = sup < d - kRedundantMargin * (sc + fabsf(d));
+        keep[r] = redundant ? 0 : 1;
+        rs[r] = redundant ? 0.f : (scale ? 1.f / fmaxf(sqrtf(ss), 1e-8f) : 1.f);
+    }
+}
+
+// Positions of the kept rows inside their stage (pos, exclusive) and kept rows per stage (cnt):
+// one block per stage, blockDim rows at a time with a block-wide scan.
+__global__ void keep_scan_kernel(int Mnc, const unsigned char* __restrict__ keep, int* __restrict__ pos,
+                                 int* __restrict__ cnt) {
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const long base = (long)blockIdx.x * Mnc;
+    int carry = 0;
+    for (int c0 = 0; c0 < Mnc; c0 += blockDim.x) {
+        const int v = c0 + tid < Mnc ? keep[base + c0 + tid] : 0;
+        int x = v;                                          // inclusive warp scan
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) before += wsum[w];
+            total += wsum[w];
+        }
+        if (c0 + tid < Mnc) pos[base + c0 + tid] = carry + before + x - v;
+        carry += total;
+        __syncthreads();
+    }
+    if (tid == 0) cnt[blockIdx.x] = carry;
+}
+
 // ---------------------------------------------------------------- FP64 KKT certificate
 // kkt[0..n): A~'y (rows part), kkt[n]: max primal violation, kkt[n+1]: max wrong-sign y,
 // kkt[n+2]: max complementarity, all over the C~ rows.
@@ -108,7 +177,8 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
 __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float* __restrict__ g,
                                  const float* __restrict__ lo, const float* __restrict__ hi,
                                  const float* __restrict__ U, const float* __restrict__ y,
-                                 const double* __restrict__ kkt, const int* status, gm_stats* stats) {
+                                 const double* __restrict__ kkt, const int* status, gm_stats* stats,
+                                 AdmmState* S) {
     __shared__ double red[4][32];
     double stat = 0.0, prim = 0.0, comp = 0.0;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
@@ -149,8 +219,11 @@ __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float
         else if (st & (1 << GM_ERR_NUMERIC)) code = GM_ERR_NUMERIC;
         else if (st & (1 << GM_ERR_INFEASIBLE)) code = GM_ERR_INFEASIBLE;
         else if (!stats->converged) code = GM_ERR_NOT_CONVERGED;
-        if (!(stat == stat)) code = GM_ERR_NUMERIC;
+        if (!(stat == stat) && code != GM_ERR_TIMEOUT) code = GM_ERR_NUMERIC;   // a timeout leaves garbage
+        // a warm start abandoned for a cold restart that then converged
+        if (S && code == GM_OK && S->fell_back) code = GM_STALLED;
         stats->status = code;
+        if (S) S->final_status = code;
     }
 }
 
@@ -162,11 +235,16 @@ static gm_status solve_with(AdmmPlan& p, int sms, int nsplit, float* gram_part, 
     // status[0..1]: this solve; status[2]: the GNN kernels of the same step (kept)
     GM_CUDA_TRY(cudaMemsetAsync(p.status, 0, sizeof(int) * 2, st));
     if (rows > 0) {
-        if (scale) {
-            row_norm_kernel<<<cdiv(rows * 32, 256), 256, 0, st>>>(rows, p.nu, p.Mnc, p.Ct, const_cast<float*>(p.rs));
-            GM_LAUNCH_CHECK();
-        }
-        GramRows R{p.Ct, p.Mnc, p.nu, p.N, scale ? p.rs : nullptr, 1, 1};
+        row_prep_kernel<<<cdiv(rows * 32, 256), 256, 0, st>>>(rows, p.nu, p.Mnc, p.Ct, p.dt, p.lo, p.hi,
+                                                              scale ? 1 : 0, const_cast<float*>(p.rs),
+                                                              const_cast<unsigned char*>(p.keep));
+        GM_LAUNCH_CHECK();
+        keep_scan_kernel<<<(unsigned)(rows / p.Mnc), 1024, 0, st>>>(p.Mnc, p.keep, const_cast<int*>(p.kpos),
+                                                                    const_cast<int*>(p.kcnt));
+        GM_LAUNCH_CHECK();
+        // the multipliers of rows the ADMM skips stay 0
+        GM_CUDA_TRY(cudaMemsetAsync(p.y + p.n, 0, sizeof(float) * rows, st));
+        GramRows R{p.Ct, p.Mnc, p.nu, p.N, p.rs, 1, 1};
         GM_TRY(launch_gram(R, n, nsplit, gram_part, st, p.status, p.gram_tc));
         gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, gram_part, nullptr, 0.f,
                                                                   const_cast<float*>(p.Gram));
@@ -180,7 +258,7 @@ static gm_status solve_with(AdmmPlan& p, int sms, int nsplit, float* gram_part, 
                           st>>>(n, p.nu, p.Mnc, rows, p.Ct, p.dt, p.U, p.y, kkt);
         GM_LAUNCH_CHECK();
     }
-    kkt_final_kernel<<<1, 256, 0, st>>>(n, p.H, p.g, p.lo, p.hi, p.U, p.y, kkt, p.status, p.stats);
+    kkt_final_kernel<<<1, 256, 0, st>>>(n, p.H, p.g, p.lo, p.hi, p.U, p.y, kkt, p.status, p.stats, p.S);
     GM_LAUNCH_CHECK();
     return GM_OK;
 }
@@ -197,7 +275,8 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     AdmmPlan p{};
     p.n = n; p.nu = c->nu; p.Mnc = std::max(c->M * c->n_c, 1); p.N = c->N; p.rows = rows;
     p.Ct = Ct; p.dt = dt; p.lo = u_lo; p.hi = u_hi; p.g = g; p.H = H; p.U0 = warm_U; p.y0 = warm_y;
-    p.rs = scale ? c->d_rs : nullptr;
+    p.rs = rows > 0 ? c->d_rs : nullptr;
+    p.keep = c->d_keep; p.kpos = c->d_kpos; p.kcnt = c->d_kcnt;
     p.Gram = rows > 0 ? c->d_G : nullptr;
     p.U = U; p.y = y ? y : c->d_y; p.z = c->d_z;
     p.P = c->d_P; p.Pinv = c->d_Pinv; p.L = c->d_L; p.Linv = c->d_Linv;
@@ -205,8 +284,10 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     p.S = c->d_admm; p.stats = stats;
     p.rho0 = c->s.rho; p.tol = c->s.tol; p.max_iter = c->s.max_iter;
     p.keep_rho = keep_rho;
+    p.warm = warm_U != nullptr || warm_y != nullptr;
     p.adapt_every = c->s.adapt_rho ? 25 : 0;
-    p.rounds = c->s.adapt_rho ? 6 : 1;
+    // a warm start may take kWarmRounds launches before a cold restart takes the usual ones
+    p.rounds = (c->s.adapt_rho ? 6 : 1) + (p.warm ? kWarmRounds : 0);
     p.grid = rows > 0 ? c->admm_grid : 1;
     p.factor_grid = c->s.factor_grid;
     p.max_spins = c->s.timeout_spins > 0 ? c->s.timeout_spins : (1LL << 26);
@@ -268,6 +349,9 @@ extern "C" gm_status gm_qp_solve_noalloc(int N, int nu, int Mnc, const gm_settin
     float* z = cv.take<float>(n + rows);
     float* ys = cv.take<float>(n + rows);
     float* rs = cv.take<float>(std::max(rows, 1L));
+    unsigned char* keep = cv.take<unsigned char>(std::max(rows, 1L));
+    int* kpos = cv.take<int>(std::max(rows, 1L));
+    int* kcnt = cv.take<int>(N);
     float* acc = cv.take<float>(3 * (size_t)admm_acc_stride(n));
     unsigned* bar = cv.take<unsigned>(4);
     int* status = cv.take<int>(4);
@@ -287,7 +371,8 @@ extern "C" gm_status gm_qp_solve_noalloc(int N, int nu, int Mnc, const gm_settin
     AdmmPlan p{};
     p.n = n; p.nu = nu; p.Mnc = std::max(Mnc, 1); p.N = N; p.rows = rows;
     p.Ct = Ct; p.dt = dt; p.lo = u_lo; p.hi = u_hi; p.g = g; p.H = H; p.U0 = nullptr; p.y0 = nullptr;
-    p.rs = scale ? rs : nullptr;
+    p.rs = rows > 0 ? rs : nullptr;
+    p.keep = keep; p.kpos = kpos; p.kcnt = kcnt;
     p.Gram = rows > 0 ? Gm : nullptr;
     p.U = U; p.y = y ? y : ys; p.z = z;
     p.P = P; p.Pinv = Pinv; p.L = L; p.Linv = Linv;

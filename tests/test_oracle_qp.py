@@ -208,3 +208,85 @@ def test_infeasibility_verdict_matches_linear_programming(seed):
         assert qp.primal_infeasible(At, l, h, info["dy"], eps=1e-3)
     else:
         assert ok and not info["infeasible"]
+
+
+def stall_qp(seed=5):
+    """A QP with the condensed stage structure (N = 4 stages, 2 inputs, 3 half-spaces per
+    stage acting on the inputs up to their stage) whose feasible set has active rows."""
+    N, NU, MNC = 4, 2, 3
+    rng = np.random.default_rng(seed)
+    n, m = N * NU, N * MNC
+    L = rng.normal(0, 1, (n, n))
+    H = L @ L.T + 0.1 * np.eye(n)
+    g = rng.normal(0, 3.0, n)
+    C = rng.normal(0, 1, (m, n))
+    for k in range(N):
+        C[k * MNC:(k + 1) * MNC, (k + 1) * NU:] = 0.0
+    d = rng.uniform(0.2, 1.5, m)
+    kw = dict(rho=0.1, tol=1e-6, max_iter=20000, scale_rows=True, adapt_every=25)
+    return H, g, -np.ones(n), np.ones(n), C, d, kw
+
+
+def stall_warm_duals(n, m, seed=5, scale=1e4):
+    """A deliberately bad warm start: half-space duals of size 1e4."""
+    y0 = np.zeros(n + m)
+    y0[n:] = np.random.default_rng(seed).normal(0.0, 1.0, m) * scale
+    return y0
+
+
+def test_stalled_warm_start_restarts_as_the_cold_solve():
+    """Duals 1e4 off: without the stall rule the recurrence does not reach tol in 20000
+    iterations; with it the warm start is dropped at a stall test, and since that test falls
+    on a multiple of the adaptation period the restarted run takes exactly the cold solve's
+    iterates (same U to rounding, count = restart iteration + cold count)."""
+    H, g, lo, hi, C, d, kw = stall_qp()
+    n = H.shape[0]
+    y0 = stall_warm_duals(n, C.shape[0])
+    w = qp.admm(H, g, lo, hi, C, d, U0=np.zeros(n), y0=y0, stall_every=25, return_info=True, **kw)
+    c = qp.admm(H, g, lo, hi, C, d, **kw)
+    assert w[7]["restarted"] and w[6] and c[6]
+    assert (w[3] - c[3]) % 25 == 0 and w[3] > c[3]          # the restart came at a stall test
+    assert np.abs(w[0] - c[0]).max() <= 1e-12
+    nr = qp.admm(H, g, lo, hi, C, d, U0=np.zeros(n), y0=y0, **kw)
+    assert not nr[6] and nr[3] == kw["max_iter"]
+
+
+def test_good_warm_start_is_kept_and_a_nan_one_restarts_at_once():
+    H, g, lo, hi, C, d, kw = stall_qp()
+    n = H.shape[0]
+    Ue, ye, _ = qp.solve_exact(H, g, lo, hi, C, d)
+    w = qp.admm(H, g, lo, hi, C, d, U0=Ue, y0=ye, stall_every=25, return_info=True, **kw)
+    assert w[6] and not w[7]["restarted"] and w[3] <= 3
+    U0 = np.zeros(n)
+    U0[3] = np.nan
+    w = qp.admm(H, g, lo, hi, C, d, U0=U0, stall_every=25, return_info=True, **kw)
+    assert w[6] and w[7]["restarted"] and np.isfinite(w[0]).all()
+    assert np.abs(w[0] - Ue).max() <= 10 * kw["tol"] / kw["rho"]
+
+
+def test_redundant_rows_cannot_be_violated_and_dropping_them_keeps_the_optimum():
+    """The redundant-row test against sampling: no U in the box (vertices included) violates a
+    row it drops; the ADMM with and without the drop reaches the exact optimum of the full QP,
+    with zero multipliers on the dropped rows and a valid KKT certificate."""
+    rng = np.random.default_rng(2)
+    H, g, lo, hi, C, d = random_qp(6, 40, 4)
+    d = d + rng.uniform(0.0, 4.0, d.size)               # a mix of redundant and binding rows
+    red = qp.redundant_rows(C, d, lo, hi)
+    assert 0 < red.sum() < red.size
+    Us = rng.uniform(lo, hi, (20000, lo.size))
+    Us = np.vstack([Us, np.where(rng.random((2000, lo.size)) < 0.5, lo, hi)])
+    assert (Us @ C[red].T <= d[red]).all()
+    # the support is attained at a vertex: a row just above the margin is kept
+    sup = np.maximum(C * hi, C * lo).sum(1)
+    assert not qp.redundant_rows(C, sup + 1e-9, lo, hi).any()
+    Ue, ye, _ = qp.solve_exact(H, g, lo, hi, C, d)
+    assert np.abs(ye[lo.size:][red]).max() <= 1e-9
+    for drop in (True, False):
+        U, z, y, it, rp, rd, ok = qp.admm(H, g, lo, hi, C, d, rho=0.1, tol=1e-9, max_iter=20000,
+                                          scale_rows=True, adapt_every=25, drop_redundant=drop)
+        assert ok and np.abs(U - Ue).max() <= 1e-6, (drop, np.abs(U - Ue).max())
+        if drop:
+            assert (y[lo.size:][red] == 0).all()
+        At, l, h = qp.stack_rows(lo, hi, C, d)
+        cert = qp.kkt_certificate(H, g, At, l, h, U, y)
+        assert max(cert.values()) <= 1e-6, cert
