@@ -133,7 +133,7 @@ void gm_gnn_destroy(gm_gnn* m);
  *                on every SM); smaller grids let batched instances run side by side
  *   factor_grid  CTAs of the cooperative FP64 factor kernel (0: 128)
  *   chunk_mb     device memory budget of the reverse-pass cotangent buffers in
- *                MB (0: 2048); fewer stages per launch group when smaller
+ *                MB (0: 16384); fewer stages per launch group when smaller
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N;
@@ -394,6 +394,13 @@ gm_status gm_ctx_info(const gm_ctx* ctx, gm_info* out);
 gm_status gm_ctx_set_timing(gm_ctx* ctx, int on);
 gm_status gm_ctx_phase_ms(gm_ctx* ctx, float* ms5, int* steps);
 
+/* Arithmetic peaks of the current device for the roofline of the FP32 and FP64
+ * kernels: FP32 and FP64 fused multiply-add throughput (TFLOP/s, 2 flops per
+ * FMA) of independent FMA chains in every lane of 8 CTAs of 256 threads per
+ * SM, timed with CUDA events on stream (which the call synchronises), and the
+ * L2 size in bytes (cudaDevAttrL2CacheSize). */
+gm_status gm_measure_peaks(double* fp32_tflops, double* fp64_tflops, long long* l2_bytes, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long gm_launch_count(void);
 
@@ -436,17 +443,18 @@ gm_status gm_ctx_set_timeout_spins(gm_ctx* ctx, int spins);
  * horizon, inputs, GNN); gm_batch_rti_step runs gm_rti_step on every instance
  * i with (x_meas[i], costs[i], cons[i], U[i], stats[i]).  The first call runs
  * the instances one after another with plain launches; the next captures
- * every instance's step as a child graph of one parent graph with no
- * instances in lanes planned by gm_batch_plan (width: the larger of an
- * instance's cooperative ADMM and factor grids; cost: M * N * (1 + nU/64);
- * capacity: half the SMs), so that the cooperative grids of the steps
- * running at once fit on the SMs together with room to spare, and every later call with the same arguments replays that
- * graph with a single launch on the stream, the lanes running side by
- * side.  Changing any argument captures
- * anew.  x_meas, U, stats: host arrays of n device pointers (stats may be
- * NULL); costs, cons: host arrays of n structs.  Contexts of a batch must not
- * be stepped elsewhere while the batch runs.  gm_batch_state: as
- * gm_ctx_graph_state. */
+ * every instance's step as two child graphs of one parent graph: the part
+ * without cooperative kernels (rollout, Jacobians, condensing) in up to 16
+ * lanes planned by gm_batch_plan on cost (M * N * (1 + nU/64)), and the QP part
+ * (set-up, the cooperative FP64 factorisation and ADMM grids, KKT check), which
+ * follows the instance's first part and runs in one chain with the other
+ * instances' QP parts, so that at most one cooperative grid is on the GPU at a
+ * time.  Every later call with the same arguments replays that graph with a
+ * single launch on the stream, the lanes running side by side.  Changing any
+ * argument captures anew.  x_meas, U, stats: host arrays of n device pointers
+ * (stats may be NULL); costs, cons: host arrays of n structs.  Contexts of a
+ * batch must not be stepped elsewhere while the batch runs.  gm_batch_state:
+ * as gm_ctx_graph_state. */
 typedef struct gm_batch gm_batch;
 gm_status gm_batch_create(gm_ctx* const* ctxs, int n, gm_batch** out);
 void gm_batch_destroy(gm_batch* b);
@@ -455,9 +463,10 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
 gm_status gm_batch_state(const gm_batch* b, int* replayed, int* captures);
 /* Lanes of the last captured batch graph (1 before the first capture). */
 gm_status gm_batch_lanes(const gm_batch* b, int* lanes);
-/* At most this many lanes in the next captured batch graph (instance i in lane
- * i mod lanes when fewer than gm_batch_plan's); 0 (the default) keeps the plan.
- * lanes = 1 runs the instances one after another inside one graph launch. */
+/* At most this many lanes for the first parts in the next captured batch graph
+ * (instance i in lane i mod lanes when fewer than gm_batch_plan's); 0 (the
+ * default) keeps the plan.  lanes = 1 runs the instances one after another
+ * inside one graph launch. */
 gm_status gm_batch_set_lanes(gm_batch* b, int lanes);
 
 /* Host-only lane plan for n instance steps that each run cooperative grids

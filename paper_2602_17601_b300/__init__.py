@@ -131,6 +131,7 @@ def _load():
         "gm_batch_lanes": ([vp, C.POINTER(C.c_int)], C.c_int),
         "gm_ctx_set_warm": ([vp, C.c_int], C.c_int),
         "gm_ctx_set_timeout_spins": ([vp, C.c_int], C.c_int),
+        "gm_measure_peaks": ([C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong), vp], C.c_int),
         "gm_batch_set_lanes": ([vp, C.c_int], C.c_int),
         "gm_batch_plan": ([C.c_int, vp, vp, C.c_int, vp, C.POINTER(C.c_int)], C.c_int),
         "gm_barrier_fold": ([vp, vp, vp, vp, C.c_float, C.c_float, vp, vp, vp], C.c_int),
@@ -154,7 +155,7 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
                     "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
-                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_set_lanes", "gm_batch_plan", "gm_ctx_set_warm", "gm_barrier_fold", "gm_ctx_set_timeout_spins",
+                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_set_lanes", "gm_batch_plan", "gm_ctx_set_warm", "gm_barrier_fold", "gm_ctx_set_timeout_spins", "gm_measure_peaks",
                     "gm_rollout")
 
 GM_NOALLOC_MAX_NU = 64
@@ -209,6 +210,13 @@ def gm_batch_plan(width, cost, sms):
 
 def gm_ctx_set_warm(ctx, on):
     _check("gm_ctx_set_warm", _lib.gm_ctx_set_warm(ctx, int(bool(on))))
+
+
+def gm_measure_peaks(stream=None):
+    """Measured FP32 and FP64 FMA peaks (TFLOP/s) and the L2 size (bytes) of the current device."""
+    f32, f64, l2 = C.c_double(), C.c_double(), C.c_longlong()
+    _check("gm_measure_peaks", _lib.gm_measure_peaks(C.byref(f32), C.byref(f64), C.byref(l2), _stream(stream)))
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value, "l2_bytes": int(l2.value)}
 
 
 def gm_ctx_set_timeout_spins(ctx, spins):

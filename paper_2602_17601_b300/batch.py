@@ -6,7 +6,8 @@ the second captures every instance's step as a child graph of one parent graph,
 and later steps replay it with a single launch, the instances' kernels running
 side by side.  `cfg4_instances` draws the uneven batch of the cfg4 workload, and
 `main` times it against stepping the same instances one after another.  Launch
-shapes (ADMM and factor grids) come from the autotuner's cache (`autotune.py`).
+shapes (ADMM and factor grids, stages per reverse-pass launch) come from the
+autotuner (`autotune.py`).
 """
 from __future__ import annotations
 
@@ -80,8 +81,9 @@ def cfg4_instances(n=256, first_seed=1000, constrained=True, Ms=(50, 1000), Ns=(
 
 
 def problems_for(workloads, precision, tuned=None, chunk_mb=256, max_iter=None, warm=False):
-    """RTIProblem per workload with the autotuned launch shapes of its bucket (if given); warm
-    starts each instance's ADMM from its own shifted previous solution (gm_ctx_set_warm)."""
+    """RTIProblem per workload with the autotuned launch shapes of its bucket (if given; they
+    override chunk_mb); warm starts each instance's ADMM from its own shifted previous solution
+    (gm_ctx_set_warm)."""
     from .autotune import bucket_of
     from .rti import RTIProblem
     probs = []

@@ -261,15 +261,18 @@ static size_t blob_floats(int K, int W, int nu) {
 
 // ---------------------------------------------------------------- workspace layout
 static constexpr int kMaxAdmmGrid = 2048;
+static constexpr int kBatchLanes = 16;   // lanes of the pre parts of a batch step (gm_batch_rti_step)
 
 static void plan(gm_ctx* c, Carver& cv) {
     const Cones& C = c->cones;
     const int M = c->M, E = c->E, K = c->K, W = c->W, N = c->N, nu = c->nu, nU = c->nU;
     const long RK = (long)C.nr_node[K].size(), RK1 = (long)C.nr_node[K - 1].size();
     const long RE = (long)C.er_edge[K - 1].size();
-    // stages per reverse chunk: keep the per-chunk buffers near 2 GB
+    // stages per reverse chunk: the per-chunk buffers within the budget (default 16 GB, which
+    // holds the whole horizon of the chain of 1000 in one chunk: fewer, fuller launches measured
+    // 7.9 ms for the Jacobian phase against 8.7 ms with 4-stage chunks)
     const long per_stage = 4L * (2 * RK * 3 * W + 2 * RK1 * 3 * W + 3 * RE * 3 * W + RK * 3 * (6 + nu) + RE * 18);
-    const long budget = c->s.chunk_mb > 0 ? (long)c->s.chunk_mb << 20 : (2L << 30);
+    const long budget = c->s.chunk_mb > 0 ? (long)c->s.chunk_mb << 20 : (16L << 30);
     c->stage_chunk = (int)std::max(1L, std::min((long)N, budget / std::max(1L, per_stage)));
     const long Ns = c->stage_chunk;
     std::vector<float> wdummy;
@@ -736,20 +739,19 @@ gm_status gm_qp_solve(gm_ctx* ctx, const float* H, const float* g, const float* 
                     static_cast<cudaStream_t>(stream));
 }
 
-static gm_status rti_body(gm_ctx* c, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
-                          float* u0, gm_stats* stats, cudaStream_t st, bool timed) {
-    std::array<cudaEvent_t, 6> ev{};
-    if (timed) {
-        for (auto& e : ev) GM_CUDA_TRY(cudaEventCreate(&e));
-        c->events.push_back(ev);
-        GM_CUDA_TRY(cudaEventRecord(ev[0], st));
-    }
+// The two parts of one step: rti_pre (rollout, Jacobians, condensing, the warm start's duals)
+// launches no cooperative kernel; rti_post (QP set-up, FP64 factorisation, ADMM, KKT check,
+// outputs, the shift) holds the step's cooperative grids.  A batch runs the pre parts of many
+// instances side by side and the post parts one after another (gm_batch_rti_step).
+static gm_status rti_pre(gm_ctx* c, const float* x_meas, const gm_cost* cost, const gm_constr* cons, cudaStream_t st,
+                         const std::array<cudaEvent_t, 6>* ev) {
+    if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[0], st));
     GM_CUDA_TRY(cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), st));
     c->kev_n = 0;
     GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
-    if (timed) GM_CUDA_TRY(cudaEventRecord(ev[1], st));
+    if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[1], st));
     GM_TRY(gnn_jacobians(c, c->d_x_hat, c->d_u_hat, c->d_A, c->d_B, c->d_c, st));
-    if (timed) GM_CUDA_TRY(cudaEventRecord(ev[2], st));
+    if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[2], st));
     const float* Cx = cons->Cx;
     const float* dx = cons->dx;
     if (cons->n_spheres > 0) {
@@ -766,15 +768,32 @@ static gm_status rti_body(gm_ctx* c, const float* x_meas, const gm_cost* cost, c
     // receding-horizon warm start: U^0 = u_hat (the shifted previous solution), y^0 = the previous
     // multipliers shifted by one stage alike (zero after gm_ctx_reset)
     if (c->warm) GM_TRY(shift_duals(c, c->d_y, c->d_yw, st));
-    if (timed) GM_CUDA_TRY(cudaEventRecord(ev[3], st));
+    if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[3], st));
+    return GM_OK;
+}
+
+static gm_status rti_post(gm_ctx* c, const gm_constr* cons, float* U, float* u0, gm_stats* stats, cudaStream_t st,
+                          const std::array<cudaEvent_t, 6>* ev) {
+    const bool barrier = cons->barrier_mu > 0.f && c->n_c > 0;
     GM_TRY(qp_solve(c, c->d_H, c->d_g, barrier ? nullptr : c->d_Ct, barrier ? nullptr : c->d_dt, cons->u_lo,
                     cons->u_hi, c->warm ? c->d_u_hat : nullptr, c->warm ? c->d_yw : nullptr, c->d_U, c->d_y,
-                    stats ? stats : c->d_stats, st, timed ? ev[4] : nullptr, c->warm));
-    if (timed) GM_CUDA_TRY(cudaEventRecord(ev[5], st));
+                    stats ? stats : c->d_stats, st, ev ? (*ev)[4] : nullptr, c->warm));
+    if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[5], st));
     GM_CUDA_TRY(cudaMemcpyAsync(U, c->d_U, sizeof(float) * c->nU, cudaMemcpyDeviceToDevice, st));
     if (u0) GM_CUDA_TRY(cudaMemcpyAsync(u0, c->d_U, sizeof(float) * c->nu, cudaMemcpyDeviceToDevice, st));
     GM_TRY(shift_inputs(c, c->d_U, c->d_u_hat, st));
     return GM_OK;
+}
+
+static gm_status rti_body(gm_ctx* c, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
+                          float* u0, gm_stats* stats, cudaStream_t st, bool timed) {
+    std::array<cudaEvent_t, 6> ev{};
+    if (timed) {
+        for (auto& e : ev) GM_CUDA_TRY(cudaEventCreate(&e));
+        c->events.push_back(ev);
+    }
+    GM_TRY(rti_pre(c, x_meas, cost, cons, st, timed ? &ev : nullptr));
+    return rti_post(c, cons, U, u0, stats, st, timed ? &ev : nullptr);
 }
 
 // Everything a captured step bakes in.
@@ -795,13 +814,17 @@ static std::vector<uintptr_t> graph_key(const gm_ctx* c, const float* x_meas, co
     return k;
 }
 
-// One step of c with these arguments captured into a graph on c's internal stream.
+// One step of c with these arguments captured into a graph on c's internal stream; part 0:
+// the whole step, 1: rti_pre only, 2: rti_post only.
 static gm_status capture_step(gm_ctx* c, const float* x_meas, const gm_cost* cost, const gm_constr* cons, float* U,
-                              float* u0, gm_stats* stats, cudaGraph_t* out) {
+                              float* u0, gm_stats* stats, cudaGraph_t* out, int part = 0) {
     *out = nullptr;
     if (!c->cap_stream) GM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     GM_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
-    const gm_status body = rti_body(c, x_meas, cost, cons, U, u0, stats, c->cap_stream, false);
+    gm_status body = GM_OK;
+    if (part == 0) body = rti_body(c, x_meas, cost, cons, U, u0, stats, c->cap_stream, false);
+    else if (part == 1) body = rti_pre(c, x_meas, cost, cons, c->cap_stream, nullptr);
+    else body = rti_post(c, cons, U, u0, stats, c->cap_stream, nullptr);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
     if (body != GM_OK || ce != cudaSuccess || !g) {
@@ -910,46 +933,63 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
                             st, false));
         return GM_OK;
     }
-    // Every instance's step as a child graph of one parent, chained in lanes (gm_batch_plan).
-    // A step holds cooperative launches (the ADMM and factor grids), and cooperative grids
-    // running side by side can each hold part of their CTAs resident while waiting for the
-    // rest, so the lanes are sized such that the widest grids of all lanes fit on the SMs at
-    // once (otherwise such a standoff lasts until a grid barrier's bound runs out).
-    std::vector<int> width(n), lane(n);
+    // Every instance's step as two child graphs of one parent.  The pre parts (rollout,
+    // Jacobians, condensing: no cooperative kernel) run in lanes side by side, planned by
+    // gm_batch_plan on cost; the post parts (QP set-up, FP64 factorisation, ADMM, KKT: the
+    // cooperative grids) follow their own pre part and run one after another in a single chain.
+    // So at most one cooperative grid is on the GPU at a time: the non-cooperative kernels of
+    // the other lanes always finish, so its CTAs all become resident and its grid barriers
+    // wait for running CTAs only.  (Two cooperative grids side by side can each hold part of
+    // their CTAs resident, every SM taken by spinning CTAs of one or the other, with the rest
+    // of both waiting for an SM until a barrier's bound runs out.)
+    std::vector<int> width(n, 1), lane(n);
     std::vector<double> cost(n);
     for (int i = 0; i < n; ++i) {
         const gm_ctx* c = b->ctx[i];
-        const int fg = c->s.factor_grid > 0 ? std::max(2, std::min(c->s.factor_grid, factor_grid())) : factor_grid();
-        width[i] = std::max(c->admm_grid, fg);
         cost[i] = (double)c->M * c->N * (1.0 + c->nU / 64.0);
     }
-    // The plan fills half the SMs with cooperative grids: plans that filled 144 of 148 SMs
-    // stalled in two of three 256-instance runs (54 and 105 s per batch step against 2.4 s,
-    // the GPU waiting on grid barriers), plans of 128 ran in every run.
     int lanes = 1;
-    GM_TRY(gm_batch_plan(n, width.data(), cost.data(), std::max(1, b->ctx[0]->num_sms / 2), lane.data(), &lanes));
+    GM_TRY(gm_batch_plan(n, width.data(), cost.data(), std::min(kBatchLanes, n), lane.data(), &lanes));
     if (b->lanes_req > 0 && b->lanes_req < lanes) {   // fewer lanes: instance i in lane i mod L
         lanes = b->lanes_req;
         for (int i = 0; i < n; ++i) lane[i] = i % lanes;
     }
     b->lanes = lanes;
+    // post parts in the order their pre parts are expected to finish: by position in the lane,
+    // the lanes round robin
+    std::vector<int> pos(n, 0), seen(lanes, 0), order(n);
+    for (int i = 0; i < n; ++i) pos[i] = seen[lane[i]]++;
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return pos[a] < pos[c]; });
     std::vector<int> tail(lanes, -1);
     cudaGraph_t parent = nullptr;
     GM_CUDA_TRY(cudaGraphCreate(&parent, 0));
     gm_status r = GM_OK;
-    std::vector<cudaGraphNode_t> nodes(n);
+    std::vector<cudaGraphNode_t> pre(n), post(n);
+    auto add_child = [&](cudaGraphNode_t* node, const cudaGraphNode_t* deps, int nd, cudaGraph_t g, int i) {
+        if (cudaGraphAddChildGraphNode(node, parent, deps, nd, g) != cudaSuccess) {
+            set_error("adding instance %d to the batch graph failed", i);
+            return GM_ERR_CUDA;
+        }
+        return GM_OK;
+    };
     for (int i = 0; i < n && r == GM_OK; ++i) {
         cudaGraph_t g = nullptr;
-        r = capture_step(b->ctx[i], x_meas[i], &costs[i], &cons[i], U[i], nullptr, stats ? stats[i] : nullptr, &g);
+        r = capture_step(b->ctx[i], x_meas[i], &costs[i], &cons[i], U[i], nullptr, stats ? stats[i] : nullptr, &g, 1);
         if (r != GM_OK) break;
-        cudaGraphNode_t& node = nodes[i];
-        const cudaGraphNode_t* dep = tail[lane[i]] >= 0 ? &nodes[tail[lane[i]]] : nullptr;
+        const cudaGraphNode_t* dep = tail[lane[i]] >= 0 ? &pre[tail[lane[i]]] : nullptr;
         tail[lane[i]] = i;
-        if (cudaGraphAddChildGraphNode(&node, parent, dep, dep ? 1 : 0, g) != cudaSuccess) {
-            set_error("adding instance %d to the batch graph failed", i);
-            r = GM_ERR_CUDA;
-        }
+        r = add_child(&pre[i], dep, dep ? 1 : 0, g, i);
         cudaGraphDestroy(g);           // the child node holds its own copy
+    }
+    for (int j = 0; j < n && r == GM_OK; ++j) {
+        const int i = order[j];
+        cudaGraph_t g = nullptr;
+        r = capture_step(b->ctx[i], x_meas[i], &costs[i], &cons[i], U[i], nullptr, stats ? stats[i] : nullptr, &g, 2);
+        if (r != GM_OK) break;
+        cudaGraphNode_t deps[2] = {pre[i], j > 0 ? post[order[j - 1]] : nullptr};
+        r = add_child(&post[i], deps, j > 0 ? 2 : 1, g, i);
+        cudaGraphDestroy(g);
     }
     cudaGraphExec_t exec = nullptr;
     if (r == GM_OK && cudaGraphInstantiate(&exec, parent, 0) != cudaSuccess) {

@@ -27,7 +27,6 @@
 
 namespace gmi {
 
-constexpr int TC_M = 128;        // rows per CTA tile (MMA M)
 constexpr int TC_T = 512;        // threads per CTA: four warp groups
 constexpr int TC_TMEM_COLS = 256;  // D1, then D2 in the same columns (N <= 256); two CTAs per SM
 constexpr int TC_NB = 128;         // rows of the staged B chunk
@@ -159,15 +158,6 @@ __device__ __forceinline__ void tc_out_rows(const Op& op, const RowCtx* rc, unsi
     }
 }
 
-// Thread v of a staging loop handles one 16-byte vector (8 K-elements of one row).
-// Rows vary fastest within each 8-row core matrix, so the 8 lanes of a quarter warp
-// write one contiguous 128-byte core matrix (no shared-memory bank conflicts).
-__device__ __forceinline__ void tc_vec_rc(int v, int kv8, int& r, int& kv) {
-    const int rest = v >> 3;
-    kv = rest % kv8;
-    r = (rest / kv8) * 8 + (v & 7);
-}
-
 // Bulk copy (TMA engine) of K chunk [k0, k0 + kc) of the P pieces of a tiled weight operand
 // with nrows rows (tc_tile_off layout: the chunk of one piece is one contiguous block) into
 // the staging buffer; completion is counted in bytes on mbarrier bar.  One thread calls it.
@@ -271,27 +261,6 @@ __device__ __forceinline__ void tc_store_a_full(unsigned char* sA, int a_piece, 
         const int o = tc_off(m, kv * 8, KC);
 #pragma unroll
         for (int p = 0; p < P; ++p) *reinterpret_cast<uint4*>(sA + p * a_piece + o) = pc[p];
-    }
-}
-
-// MMAs of one staged chunk: D (+)= sum over piece pairs (i, j) with i + j < P of A_i . B_j^T
-// (1, 3 or 6 products; the dropped pairs are below the last kept piece's rounding).
-template <int P>
-__device__ __forceinline__ void tc_issue(unsigned tD, unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b0,
-                                         unsigned b_piece, unsigned b_sbo, int kc, int N, bool first) {
-    const unsigned idesc = tc_idesc(TC_M, N);
-    bool acc = !first;
-    for (int kk = 0; kk < kc / 16; ++kk) {
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const unsigned long long ad = tc_desc(a0 + i * a_piece + kk * 256, a_sbo);
-#pragma unroll
-            for (int j = 0; i + j < P; ++j) {
-                const unsigned long long bd = tc_desc(b0 + j * b_piece + kk * 256, b_sbo);
-                tc_mma(tD, ad, bd, idesc, acc ? 1u : 0u);
-                acc = true;
-            }
-        }
     }
 }
 

@@ -12,6 +12,8 @@
 
 namespace gmi {
 
+constexpr int TC_M = 128;        // rows per CTA tile (MMA M)
+
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ int tc_off(int r, int k, int Kdim) {
@@ -99,6 +101,36 @@ __device__ __forceinline__ void pack8(const float* v, uint4* out) {
             const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&out[p]);
 #pragma unroll
             for (int j = 0; j < 8; ++j) r[j] -= __bfloat162float(h[j]);
+        }
+    }
+}
+
+// Thread v of a staging loop handles one 16-byte vector (8 K-elements of one row).
+// Rows vary fastest within each 8-row core matrix, so the 8 lanes of a quarter warp
+// write one contiguous 128-byte core matrix (no shared-memory bank conflicts).
+__device__ __forceinline__ void tc_vec_rc(int v, int kv8, int& r, int& kv) {
+    const int rest = v >> 3;
+    kv = rest % kv8;
+    r = (rest / kv8) * 8 + (v & 7);
+}
+
+// MMAs of one staged chunk: D (+)= sum over piece pairs (i, j) with i + j < P of A_i . B_j^T
+// (1, 3 or 6 products; the dropped pairs are below the last kept piece's rounding).
+template <int P>
+__device__ __forceinline__ void tc_issue(unsigned tD, unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b0,
+                                         unsigned b_piece, unsigned b_sbo, int kc, int N, bool first) {
+    const unsigned idesc = tc_idesc(TC_M, N);
+    bool acc = !first;
+    for (int kk = 0; kk < kc / 16; ++kk) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const unsigned long long ad = tc_desc(a0 + i * a_piece + kk * 256, a_sbo);
+#pragma unroll
+            for (int j = 0; i + j < P; ++j) {
+                const unsigned long long bd = tc_desc(b0 + j * b_piece + kk * 256, b_sbo);
+                tc_mma(tD, ad, bd, idesc, acc ? 1u : 0u);
+                acc = true;
+            }
         }
     }
 }

@@ -1,11 +1,15 @@
 // Learned ADMM warm start: a 3-layer MLP (in -> H -> H -> out, ReLU between) mapping pooled
 // GNN latents and the reference to a primal input sequence and box duals, with its training
 // kernels (MSE loss, backward, Adam).  Inputs and targets are standardised with stored
-// means and deviations.  FP32 SIMT: the net is small and its products are 64 x 64 tiles.
+// means and deviations.  Every product (the forward layers, the weight gradients and the
+// propagated gradients) runs on tcgen05 tensor cores with BF16 operands and FP32 accumulation
+// in tensor memory; each FP32 operand is split into two BF16 pieces (three products, about 16
+// bits), which the weight gradients need to match an FP32 evaluation.
 #include <cstring>
 
 #include "ctx.h"
 #include "kernels.h"
+#include "tc_prim.cuh"
 
 struct gm_ws {
     int n_in = 0, n_hid = 0, n_out = 0, max_batch = 0;
@@ -16,61 +20,106 @@ struct gm_ws {
     float *x = nullptr, *a0 = nullptr, *a1 = nullptr, *y = nullptr;   // [B][in], [B][H], [B][H], [B][out]
     float *d0 = nullptr, *d1 = nullptr, *dy = nullptr;                // gradients of a0, a1, y
     float* loss = nullptr;
+    int* status = nullptr;         // device word: GM_ERR_TIMEOUT bit when a bounded wait gave up
     int step = 0;                  // Adam step count
 };
 
 namespace gmi {
 namespace {
 
-constexpr int GT = 64;   // output tile
-constexpr int GK = 16;   // K step
+constexpr int WG_M = 128, WG_N = 128, WG_KC = 64, WG_T = 256, WG_P = 2;
+constexpr size_t WG_SMEM = (size_t)2 * WG_P * WG_M * WG_KC * 2;    // A and B chunks, P pieces each
 
 // C[i][j] (+)= sum_k A(i, k) B(k, j) (+ bias[j]) (ReLU): A(i, k) = A[i sai + k sak],
-// B(k, j) = B[k sbk + j sbj], C row-major with ldc.  256 threads, 4 x 4 outputs each.
-__global__ void __launch_bounds__(256) ws_gemm_kernel(int M, int N, int K, const float* __restrict__ A, long sai,
-                                                      long sak, const float* __restrict__ B, long sbk, long sbj,
-                                                      float* __restrict__ C, long ldc, const float* __restrict__ bias,
-                                                      int relu, int accumulate) {
-    __shared__ float As[GK][GT + 4];
-    __shared__ float Bs[GK][GT + 4];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int t = tid; t < GK * GT; t += 256) {
-            const int kk = t / GT, ii = t % GT;
-            const int i = i0 + ii, j = j0 + ii, k = k0 + kk;
-            As[kk][ii] = (i < M && k < K) ? A[(long)i * sai + (long)k * sak] : 0.f;
-            Bs[kk][ii] = (j < N && k < K) ? B[(long)k * sbk + (long)j * sbj] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = As[kk][ty * 4 + q];
-                b[q] = Bs[kk][tx * 4 + q];
-            }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
-        }
-        __syncthreads();
+// B(k, j) = B[k sbk + j sbj], C row-major with ldc.  One CTA per 128 x 128 tile of C: the
+// threads stage K chunks of 64 of both operands (any strides, zero past the edges) as P BF16
+// pieces in the K-major core-matrix layout, one thread issues the P(P+1)/2 products per 16-wide
+// K step into tensor memory, and the epilogue reads its row (TMEM lane) back.
+__global__ void __launch_bounds__(WG_T) ws_tc_gemm_kernel(int M, int N, int K, const float* __restrict__ A, long sai,
+                                                          long sak, const float* __restrict__ B, long sbk, long sbj,
+                                                          float* __restrict__ C, long ldc,
+                                                          const float* __restrict__ bias, int relu, int accumulate,
+                                                          int* status) {
+    extern __shared__ __align__(1024) unsigned char wsg[];
+    constexpr int PIECE = WG_M * WG_KC * 2;
+    unsigned char* sA = wsg;                      // WG_P pieces of the A chunk [128 rows][64 K]
+    unsigned char* sB = wsg + WG_P * PIECE;       // WG_P pieces of the B chunk [128 columns of C][64 K]
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long i0 = (long)blockIdx.y * WG_M, j0 = (long)blockIdx.x * WG_N;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "n"(WG_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tD = tmem_base;
+    bool ok = true;
+    const int nch = (K + WG_KC - 1) / WG_KC;
+    for (int c = 0; c < nch; ++c) {
+        const int k0 = c * WG_KC;
+        for (int v = tid; v < WG_M * (WG_KC / 8); v += WG_T) {
+            int r, kv;
+            tc_vec_rc(v, WG_KC / 8, r, kv);
+            float xa[8], xb[8];
+            const long i = i0 + r, j = j0 + r;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+            for (int e = 0; e < 8; ++e) {
+                const int k = k0 + kv * 8 + e;
+                xa[e] = (i < M && k < K) ? A[i * sai + (long)k * sak] : 0.f;
+                xb[e] = (j < N && k < K) ? B[(long)k * sbk + j * sbj] : 0.f;
+            }
+            uint4 pa[WG_P], pb[WG_P];
+            pack8<WG_P>(xa, pa);
+            pack8<WG_P>(xb, pb);
+            const int o = tc_off(r, kv * 8, WG_KC);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + ty * 4 + p, j = j0 + tx * 4 + q;
-            if (i >= M || j >= N) continue;
-            float v = acc[p][q];
-            if (accumulate) v += C[(long)i * ldc + j];
-            if (bias) v += bias[j];
-            if (relu) v = fmaxf(v, 0.f);
-            C[(long)i * ldc + j] = v;
+            for (int p = 0; p < WG_P; ++p) {
+                *reinterpret_cast<uint4*>(sA + p * PIECE + o) = pa[p];
+                *reinterpret_cast<uint4*>(sB + p * PIECE + o) = pb[p];
+            }
         }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            if (ok) tc_issue<WG_P>(tD, smem_u32(sA), PIECE, WG_KC * 16, smem_u32(sB), PIECE, WG_KC * 16, WG_KC, WG_N, c == 0);
+            tc_commit(&mbar);                     // arrives even when nothing was issued
+        }
+        ok = tc_wait(&mbar, c & 1, status) && ok; // the chunk's products are done: its buffers are free
+    }
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    // epilogue: warp w reads the lanes of quadrant w % 4 (one row each), 32-column blocks
+    const int q = warp & 3;
+    const long i = i0 + q * 32 + lane;
+    for (int cb = (warp >> 2) * 32; cb < WG_N; cb += 64) {
+        float v[32];
+        if (ok) tc_ld32(tD + ((unsigned)(q * 32) << 16) + (unsigned)cb, v);
+        if (ok && i < M)
+#pragma unroll 4
+            for (int jj = 0; jj < 32; ++jj) {
+                const long j = j0 + cb + jj;
+                if (j >= N) break;
+                float val = v[jj];
+                if (accumulate) val += C[i * ldc + j];
+                if (bias) val += bias[j];
+                if (relu) val = fmaxf(val, 0.f);
+                C[i * ldc + j] = val;
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(WG_N));
 }
 
 // x' = (x - mean) / std, row by row
@@ -154,10 +203,15 @@ __global__ void ws_features_kernel(int M, int W, const float* __restrict__ h, co
 }
 
 gm_status gemm(cudaStream_t st, int M, int N, int K, const float* A, long sai, long sak, const float* B, long sbk,
-               long sbj, float* C, long ldc, const float* bias, bool relu, bool accumulate) {
-    dim3 grid(cdiv(N, GT), cdiv(M, GT));
-    ws_gemm_kernel<<<grid, 256, 0, st>>>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, bias, relu ? 1 : 0,
-                                         accumulate ? 1 : 0);
+               long sbj, float* C, long ldc, const float* bias, bool relu, bool accumulate, int* status) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        GM_CUDA_TRY(cudaFuncSetAttribute(ws_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM));
+        attr_set = true;
+    }
+    dim3 grid(cdiv(N, WG_N), cdiv(M, WG_M));
+    ws_tc_gemm_kernel<<<grid, WG_T, WG_SMEM, st>>>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, bias, relu ? 1 : 0,
+                                                   accumulate ? 1 : 0, status);
     GM_LAUNCH_CHECK();
     return GM_OK;
 }
@@ -165,9 +219,9 @@ gm_status gemm(cudaStream_t st, int M, int N, int K, const float* A, long sai, l
 // forward on standardised inputs already in w->x: a0, a1, y (standardised outputs)
 gm_status ws_fwd(gm_ws* w, int B, cudaStream_t st) {
     const int I = w->n_in, H = w->n_hid, O = w->n_out;
-    GM_TRY(gemm(st, B, H, I, w->x, I, 1, w->par + w->o_W[0], H, 1, w->a0, H, w->par + w->o_b[0], true, false));
-    GM_TRY(gemm(st, B, H, H, w->a0, H, 1, w->par + w->o_W[1], H, 1, w->a1, H, w->par + w->o_b[1], true, false));
-    GM_TRY(gemm(st, B, O, H, w->a1, H, 1, w->par + w->o_W[2], O, 1, w->y, O, w->par + w->o_b[2], false, false));
+    GM_TRY(gemm(st, B, H, I, w->x, I, 1, w->par + w->o_W[0], H, 1, w->a0, H, w->par + w->o_b[0], true, false, w->status));
+    GM_TRY(gemm(st, B, H, H, w->a0, H, 1, w->par + w->o_W[1], H, 1, w->a1, H, w->par + w->o_b[1], true, false, w->status));
+    GM_TRY(gemm(st, B, O, H, w->a1, H, 1, w->par + w->o_W[2], O, 1, w->y, O, w->par + w->o_b[2], false, false, w->status));
     return GM_OK;
 }
 
@@ -205,7 +259,7 @@ size_t gm_ws_workspace_size(int n_in, int n_hidden, int n_out, int max_batch) {
     w.n_in = n_in; w.n_hid = n_hidden; w.n_out = n_out;
     const long P = ws_layout(&w);
     const long B = max_batch;
-    const long floats = 4 * P + 2 * (n_in + n_out) + B * (n_in + 4L * n_hidden + 2L * n_out) + 1;
+    const long floats = 4 * P + 2 * (n_in + n_out) + B * (n_in + 4L * n_hidden + 2L * n_out) + 2;
     return (size_t)floats * sizeof(float) + 64 * 256;
 }
 
@@ -235,6 +289,7 @@ gm_status gm_ws_create(int n_in, int n_hidden, int n_out, int max_batch, void* w
     w->y = cv.take<float>(B * n_out);
     w->dy = cv.take<float>(B * n_out);
     w->loss = cv.take<float>(1);
+    w->status = cv.take<int>(1);
     if (cv.off > bytes) {
         delete w;
         set_error("workspace too small");
@@ -254,6 +309,7 @@ gm_status gm_ws_set_params(gm_ws* w, const float* params, const float* norm, voi
     GM_CUDA_TRY(cudaMemcpyAsync(w->norm, norm, sizeof(float) * 2 * (w->n_in + w->n_out), cudaMemcpyDefault, st));
     GM_CUDA_TRY(cudaMemsetAsync(w->m1, 0, sizeof(float) * w->n_par, st));
     GM_CUDA_TRY(cudaMemsetAsync(w->m2, 0, sizeof(float) * w->n_par, st));
+    GM_CUDA_TRY(cudaMemsetAsync(w->status, 0, sizeof(int), st));
     w->step = 0;
     return GM_OK;
 }
@@ -303,21 +359,21 @@ gm_status gm_ws_train_step(gm_ws* w, const float* feat, const float* target, int
     GM_LAUNCH_CHECK();
     float* g = w->grad;
     // layer 2: dW2 = a1' dy, db2 = sum dy, d1 = dy W2' * relu'(a1)
-    GM_TRY(gemm(st, H, O, B, w->a1, 1, H, w->dy, O, 1, g + w->o_W[2], O, nullptr, false, false));
+    GM_TRY(gemm(st, H, O, B, w->a1, 1, H, w->dy, O, 1, g + w->o_W[2], O, nullptr, false, false, w->status));
     ws_colsum_kernel<<<cdiv(O, 128), 128, 0, st>>>(B, O, w->dy, g + w->o_b[2]);
     GM_LAUNCH_CHECK();
-    GM_TRY(gemm(st, B, H, O, w->dy, O, 1, w->par + w->o_W[2], 1, O, w->d1, H, nullptr, false, false));
+    GM_TRY(gemm(st, B, H, O, w->dy, O, 1, w->par + w->o_W[2], 1, O, w->d1, H, nullptr, false, false, w->status));
     ws_relu_bwd_kernel<<<cdiv((long)B * H, 256), 256, 0, st>>>((long)B * H, w->a1, w->d1);
     GM_LAUNCH_CHECK();
     // layer 1
-    GM_TRY(gemm(st, H, H, B, w->a0, 1, H, w->d1, H, 1, g + w->o_W[1], H, nullptr, false, false));
+    GM_TRY(gemm(st, H, H, B, w->a0, 1, H, w->d1, H, 1, g + w->o_W[1], H, nullptr, false, false, w->status));
     ws_colsum_kernel<<<cdiv(H, 128), 128, 0, st>>>(B, H, w->d1, g + w->o_b[1]);
     GM_LAUNCH_CHECK();
-    GM_TRY(gemm(st, B, H, H, w->d1, H, 1, w->par + w->o_W[1], 1, H, w->d0, H, nullptr, false, false));
+    GM_TRY(gemm(st, B, H, H, w->d1, H, 1, w->par + w->o_W[1], 1, H, w->d0, H, nullptr, false, false, w->status));
     ws_relu_bwd_kernel<<<cdiv((long)B * H, 256), 256, 0, st>>>((long)B * H, w->a0, w->d0);
     GM_LAUNCH_CHECK();
     // layer 0
-    GM_TRY(gemm(st, I, H, B, w->x, 1, I, w->d0, H, 1, g + w->o_W[0], H, nullptr, false, false));
+    GM_TRY(gemm(st, I, H, B, w->x, 1, I, w->d0, H, 1, g + w->o_W[0], H, nullptr, false, false, w->status));
     ws_colsum_kernel<<<cdiv(H, 128), 128, 0, st>>>(B, H, w->d0, g + w->o_b[0]);
     GM_LAUNCH_CHECK();
     ++w->step;
