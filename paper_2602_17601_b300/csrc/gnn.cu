@@ -15,6 +15,7 @@
 // rows of every level are the (seed, unit) pairs of all cones, precomputed on
 // the host.  This differentiates each subsystem's local dynamics independently
 // (Sec. V-A "Linearization") with work proportional to the cone sizes.
+
 #include "ctx.h"
 #include "ff.cuh"
 #include "kernels.h"

@@ -297,82 +297,75 @@ __host__ __device__ constexpr size_t tc_smem_bytes() {
 constexpr size_t TC_SMEM_MIN = 100 * 1024;
 static_assert(TC_OUT_BYTES <= TC_SMEM_MIN, "output tile must fit the minimum launch size");
 
+// Barrier and pipeline state of a CTA that runs tiles of the tensor-core MLP: the MMA-completion
+// and weight-arrival mbarriers of each buffer, their completed phases, and the weight chunks in
+// flight.  A CTA that runs several tiles (the persistent rollout) keeps it across tiles.
+struct TcTileState {
+    unsigned long long* mbar;     // [NBUF] MMA completion (tcgen05.commit)
+    unsigned long long* bbar;     // [NBUF] weight chunk arrival (bulk-copy bytes)
+    unsigned mph[2], bphase[2];   // completed phases (NBUF <= 2)
+    bool b_pending[2];
+};
+
+// Thread 0: bulk-copy weight chunk g of a tile (g < nch: the K chunks of B1; then the K chunks of
+// B2) into buffer g % NBUF.
+template <int W, int P>
+__device__ __forceinline__ void tc_load_chunk(const TcW& w, unsigned char* sB0, TcTileState& S, int g, int nch,
+                                              int kc2) {
+    constexpr int KC = tc_kc<P>(), NBUF = tc_nbuf<P>(), B_BYTES = TC_NB * KC * 2;
+    const int b = g % NBUF;
+    unsigned char* dst = sB0 + (size_t)b * P * B_BYTES;
+    if (g < nch) {
+        tc_load_b<P>(dst, B_BYTES, w.B1, W, g * KC, min(KC, w.K1p - g * KC), &S.bbar[b]);
+    } else {
+        const int k0 = (g - nch) * kc2;
+        tc_load_b<P>(dst, B_BYTES, w.B2, w.N2p, k0, min(kc2, W - k0), &S.bbar[b]);
+    }
+    S.b_pending[b] = true;
+}
+
+// Thread 0: the first weight chunks of a tile (issued early, under the tile's prologue).
 template <int W, class Op, int P>
-__global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
+__device__ __forceinline__ void tc_tile_prefetch(const TcW& w, unsigned char* tsm, TcTileState& S) {
+    constexpr int NBUF = tc_nbuf<P>();
+    constexpr bool kSingle = (Op::kMode == 2);
+    const int nch = (w.K1p + tc_kc<P>() - 1) / tc_kc<P>();
+    const int kc2 = tc_chunk_b2(w.N2p);
+    const int ng = nch + (kSingle ? 0 : (W + kc2 - 1) / kc2);
+    unsigned char* sB0 = tsm + tc_region_a<W, P>();
+    for (int g = 0; g < NBUF && g < ng; ++g) tc_load_chunk<W, P>(w, sB0, S, g, nch, kc2);
+}
+
+// One 128-row tile of the fused MLP (rows row0 ..), run by all TC_T threads of the CTA:
+//   GEMM1 over K chunks -> hidden epilogue (bias + ReLU + mask bits, or the saved mask) ->
+//   GEMM2 over K chunks -> output epilogue (or the single-product epilogue).
+// rc: the tile's row contexts, prepared by the caller (visible after a __syncthreads); tD: the
+// CTA's TC_TMEM_COLS tensor-memory columns; the weight chunks of tc_tile_prefetch must have been
+// issued.  Returns the CTA-uniform ok (false after a bounded wait gave up).
+template <int W, class Op, int P>
+__device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row0, unsigned char* tsm,
+                                            const RowCtx* rc, unsigned tD, TcTileState& S) {
     constexpr int KC = tc_kc<P>();
     constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = TC_NB * KC * 2, H_BYTES = TC_M * W * 2;
-    extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char* sA = tsm;                          // NBUF x P pieces of the A chunk, K-major with K = KC
     unsigned char* sH = tsm;                          // P pieces of the hidden tile, K = W (after GEMM1)
     constexpr int NBUF = tc_nbuf<P>();
     unsigned char* sB0 = tsm + tc_region_a<W, P>();   // NBUF buffers of P pieces of a B chunk (bulk copies)
-    __shared__ RowCtx rc[TC_M];
-    __shared__ __align__(8) unsigned long long mbar[tc_nbuf<P>()];   // MMA completion per buffer (tcgen05.commit)
-    __shared__ __align__(8) unsigned long long bbar[NBUF];   // B chunk arrival (bulk-copy bytes)
-    __shared__ unsigned tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long row0 = (long)blockIdx.x * TC_M;
     const long rows = op.rows;
     constexpr bool kSingle = (Op::kMode == 2);
     const int nch = (w.K1p + KC - 1) / KC;
     const int kc2 = tc_chunk_b2(w.N2p);
-    // B chunks in order: g < nch are the K chunks of B1, then (two products) the K chunks of B2;
-    // chunk g lives in buffer g % NBUF.  Thread 0 tracks each buffer's arrivals.
     const int n2 = kSingle ? 0 : (W + kc2 - 1) / kc2;
     const int ng = nch + n2;
-    unsigned bphase[NBUF];
-    bool b_pending[NBUF];
-#pragma unroll
-    for (int b = 0; b < NBUF; ++b) {
-        bphase[b] = 0;
-        b_pending[b] = false;
-    }
-    auto load_b = [&](int g) {
-        const int b = g % NBUF;
-        unsigned char* dst = sB0 + (size_t)b * P * B_BYTES;
-        if (g < nch) {
-            tc_load_b<P>(dst, B_BYTES, w.B1, W, g * KC, min(KC, w.K1p - g * KC), &bbar[b]);
-        } else {
-            const int k0 = (g - nch) * kc2;
-            tc_load_b<P>(dst, B_BYTES, w.B2, w.N2p, k0, min(kc2, W - k0), &bbar[b]);
-        }
-        b_pending[b] = true;
-    };
-    if (tid == 0) {
-#pragma unroll
-        for (int b = 0; b < NBUF; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[b])));
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int g = 0; g < NBUF && g < ng; ++g) load_b(g);              // first chunks, under the prologue
-    }
-    // the prologue reads only weights and the static row indices (op.prep): it overlaps the
-    // previous kernel's tail under programmatic dependent launch
-    for (int m = tid; m < TC_M; m += TC_T) rc[m] = op.prep(row0 + m < rows ? row0 + m : -1);
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "n"(TC_TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    pdl_wait();
-    // D1 [128 x W] and, once the hidden epilogue has read it, D2 [128 x N2p] in the same columns
-    const unsigned tD = tmem_base;
     bool ok = true;
-    unsigned mph[NBUF];                 // completed MMA commits per buffer barrier
-#pragma unroll
-    for (int b = 0; b < NBUF; ++b) mph[b] = 0;
     // all threads: wait for the MMAs of chunk g (A buffer and B buffer g % NBUF are then free);
     // thread 0 then copies the weight chunk NBUF ahead into the freed B buffer
     auto wait_chunk = [&](int g) {
         const int b = g % NBUF;
-        ok = tc_wait(&mbar[b], mph[b] & 1, w.status) && ok;
-        ++mph[b];
-        if (tid == 0 && ok && g + NBUF < ng && !b_pending[b]) load_b(g + NBUF);
+        ok = tc_wait(&S.mbar[b], S.mph[b] & 1, w.status) && ok;
+        ++S.mph[b];
+        if (tid == 0 && ok && g + NBUF < ng && !S.b_pending[b]) tc_load_chunk<W, P>(w, sB0, S, g + NBUF, nch, kc2);
     };
     constexpr int CSTEP = 32 * (TC_T / 128);
     const int lrow = (warp & 3) * 32 + lane;
@@ -393,16 +386,16 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     auto issue = [&](int g, unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b_sbo, int kc, int N, bool first) {
         const int b = g % NBUF;
         bool okb = false;
-        if (b_pending[b]) {
-            okb = tc_wait(&bbar[b], bphase[b] & 1, w.status);
+        if (S.b_pending[b]) {
+            okb = tc_wait(&S.bbar[b], S.bphase[b] & 1, w.status);
             if (okb) {
-                ++bphase[b];
-                b_pending[b] = false;
+                ++S.bphase[b];
+                S.b_pending[b] = false;
             }
         }
         if (okb)
             tc_issue<P>(tD, a0, a_piece, a_sbo, smem_u32(sB0 + (size_t)b * P * B_BYTES), B_BYTES, b_sbo, kc, N, first);
-        tc_commit(&mbar[b]);
+        tc_commit(&S.mbar[b]);
         return okb;
     };
 
@@ -509,19 +502,79 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
             }
         }
     }
+    return ok;
+}
+
+// Set-up of a CTA that runs tensor-core MLP tiles: barrier init (thread 0) and the tensor-memory
+// allocation (warp 0); tc_cta_teardown waits for weight copies still in flight and frees it.
+template <int P>
+__device__ __forceinline__ void tc_cta_init(TcTileState& S, unsigned long long* mbar, unsigned long long* bbar) {
+    constexpr int NBUF = tc_nbuf<P>();
+    S.mbar = mbar;
+    S.bbar = bbar;
+    for (int b = 0; b < 2; ++b) {
+        S.mph[b] = 0;
+        S.bphase[b] = 0;
+        S.b_pending[b] = false;
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bbar[b])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+}
+__device__ __forceinline__ void tc_tmem_alloc(unsigned* tmem_base) {
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_base)),
+                     "n"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+}
+template <int P>
+__device__ __forceinline__ void tc_cta_teardown(TcTileState& S, unsigned tmem_base) {
+    constexpr int NBUF = tc_nbuf<P>();
+    // a bulk copy whose wait gave up may still be landing: wait (bounded) before the CTA exits
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b)
+            if (S.b_pending[b]) tc_wait(&S.bbar[b], S.bphase[b] & 1, nullptr);
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(TC_TMEM_COLS));
+}
+
+// One tile per CTA (tile blockIdx.x).
+template <int W, class Op, int P>
+__global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ RowCtx rc[TC_M];
+    __shared__ __align__(8) unsigned long long mbar[tc_nbuf<P>()];   // MMA completion per buffer (tcgen05.commit)
+    __shared__ __align__(8) unsigned long long bbar[tc_nbuf<P>()];   // B chunk arrival (bulk-copy bytes)
+    __shared__ unsigned tmem_base;
+    TcTileState S;
+    tc_cta_init<P>(S, mbar, bbar);
+    const long row0 = (long)blockIdx.x * TC_M;
+    const long rows = op.rows;
+    if (threadIdx.x == 0) tc_tile_prefetch<W, Op, P>(w, tsm, S);      // first chunks, under the prologue
+    // the prologue reads only weights and the static row indices (op.prep): it overlaps the
+    // previous kernel's tail under programmatic dependent launch
+    for (int m = threadIdx.x; m < TC_M; m += TC_T) rc[m] = op.prep(row0 + m < rows ? row0 + m : -1);
+    tc_tmem_alloc(&tmem_base);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    pdl_wait();
+    tc_mlp_tile<W, Op, P>(op, w, row0, tsm, rc, tmem_base, S);
     // this CTA's work is done: the next kernel may start its prologue (triggered at the end, not
     // the start, so that early CTAs of the next kernel do not hold SMs for this kernel's
     // whole duration when many instances run side by side)
     pdl_launch_dependents();
-    // a bulk copy whose wait gave up may still be landing: wait (bounded) before the CTA exits
-    if (tid == 0)
-#pragma unroll
-        for (int b = 0; b < NBUF; ++b)
-            if (b_pending[b]) tc_wait(&bbar[b], bphase[b] & 1, nullptr);
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(TC_TMEM_COLS));
+    tc_cta_teardown<P>(S, tmem_base);
 }
 
 }  // namespace gmi
