@@ -262,6 +262,7 @@ static size_t blob_floats(int K, int W, int nu) {
 // ---------------------------------------------------------------- workspace layout
 static constexpr int kMaxAdmmGrid = 2048;
 static constexpr int kBatchLanes = 16;   // lanes of the pre parts of a batch step (gm_batch_rti_step)
+static constexpr int kOverlapChunks = 4; // reverse-pass chunks of the horizon (overlap with the rollout)
 
 static void plan(gm_ctx* c, Carver& cv) {
     const Cones& C = c->cones;
@@ -274,6 +275,9 @@ static void plan(gm_ctx* c, Carver& cv) {
     const long per_stage = 4L * (2 * RK * 3 * W + 2 * RK1 * 3 * W + 3 * RE * 3 * W + RK * 3 * (6 + nu) + RE * 18);
     const long budget = c->s.chunk_mb > 0 ? (long)c->s.chunk_mb << 20 : (16L << 30);
     c->stage_chunk = (int)std::max(1L, std::min((long)N, budget / std::max(1L, per_stage)));
+    // by default chunks of at most a quarter of the horizon: the reverse pass of the first chunk
+    // starts while the rollout of the later stages still runs (gnn_linearize)
+    if (c->s.chunk_mb == 0) c->stage_chunk = std::min(c->stage_chunk, (N + kOverlapChunks - 1) / kOverlapChunks);
     const long Ns = c->stage_chunk;
     std::vector<float> wdummy;
     c->d_src = cv.take<int>(std::max(E, 1));
@@ -512,11 +516,32 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
         set_error("no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(GM_ERR_CUDA);
     }
-    if (c->E > 0 && (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+    // the rollout's streams take the highest priority: its launches are short and dependent, and
+    // the reverse pass that overlaps it would otherwise fill the SMs first
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+        set_error("stream priority query failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(GM_ERR_CUDA);
+    }
+    if (c->E > 0 && (cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
                      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
         set_error("side stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(GM_ERR_CUDA);
+    }
+    const int n_chunks = (c->N + c->stage_chunk - 1) / c->stage_chunk;
+    if (cudaStreamCreateWithPriority(&c->roll_stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_roll, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("rollout stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(GM_ERR_CUDA);
+    }
+    for (int i = 0; i < n_chunks; ++i) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            set_error("event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(GM_ERR_CUDA);
+        }
+        c->ev_stage.push_back(ev);
     }
     const Cones& C = c->cones;
     const int K = c->K;
@@ -681,8 +706,7 @@ gm_status gm_linearize(gm_ctx* ctx, const float* x0, const float* u_hat, float* 
     GM_CHECK_ARG(ctx && x0 && u_hat && x_hat, "NULL argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     GM_CUDA_TRY(cudaMemsetAsync(ctx->d_status + 2, 0, sizeof(int), st));
-    GM_TRY(gnn_rollout(ctx, x0, u_hat, x_hat, st));
-    GM_TRY(gnn_jacobians(ctx, x_hat, u_hat, A, B, c, st));
+    GM_TRY(gnn_linearize(ctx, x0, u_hat, x_hat, A, B, c, st));
     return GM_OK;
 }
 
@@ -748,10 +772,14 @@ static gm_status rti_pre(gm_ctx* c, const float* x_meas, const gm_cost* cost, co
     if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[0], st));
     GM_CUDA_TRY(cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), st));
     c->kev_n = 0;
-    GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
-    if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[1], st));
-    GM_TRY(gnn_jacobians(c, c->d_x_hat, c->d_u_hat, c->d_A, c->d_B, c->d_c, st));
-    if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[2], st));
+    if (ev) {   // phase timing: the rollout and the reverse pass one after the other
+        GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
+        GM_CUDA_TRY(cudaEventRecord((*ev)[1], st));
+        GM_TRY(gnn_jacobians(c, c->d_x_hat, c->d_u_hat, c->d_A, c->d_B, c->d_c, st));
+        GM_CUDA_TRY(cudaEventRecord((*ev)[2], st));
+    } else {
+        GM_TRY(gnn_linearize(c, x_meas, c->d_u_hat, c->d_x_hat, c->d_A, c->d_B, c->d_c, st));
+    }
     const float* Cx = cons->Cx;
     const float* dx = cons->dx;
     if (cons->n_spheres > 0) {
@@ -857,7 +885,7 @@ gm_status gm_rti_step(gm_ctx* ctx, const float* x_meas, const gm_cost* cost, con
     // capture on an internal stream (the caller's may be the legacy default stream), replay on st
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
-    if (capture_step(c, x_meas, cost, cons, U, u0, stats, &g) == GM_OK && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+    if (capture_step(c, x_meas, cost, cons, U, u0, stats, &g) == GM_OK && cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess) {
         cudaGraphDestroy(g);
         if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = exec;
@@ -992,7 +1020,7 @@ gm_status gm_batch_rti_step(gm_batch* b, const float* const* x_meas, const gm_co
         cudaGraphDestroy(g);
     }
     cudaGraphExec_t exec = nullptr;
-    if (r == GM_OK && cudaGraphInstantiate(&exec, parent, 0) != cudaSuccess) {
+    if (r == GM_OK && cudaGraphInstantiate(&exec, parent, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
         set_error("batch graph instantiation failed: %s", cudaGetErrorString(cudaGetLastError()));
         r = GM_ERR_CUDA;
     }

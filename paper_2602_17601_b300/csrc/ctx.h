@@ -161,6 +161,12 @@ struct gm_ctx {
     // the edge encoder of a rollout stage runs on this stream beside the node encoder
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the rollout runs on this high-priority stream while the reverse pass of the stages it has
+    // finished runs on the caller's stream (ev_stage[c]: the stages of reverse chunk c are rolled out)
+    cudaStream_t roll_stream = nullptr;
+    int ws_grid = 0;             // CTAs of the persistent reverse kernels (0: one per SM)
+    cudaEvent_t ev_roll = nullptr;
+    std::vector<cudaEvent_t> ev_stage;
     // launch timing of the reverse edge-update MLP (events around each launch of the last step)
     bool ktiming = false;
     int kev_n = 0;
@@ -175,6 +181,9 @@ struct gm_ctx {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (side_stream) cudaStreamDestroy(side_stream);
+        if (roll_stream) cudaStreamDestroy(roll_stream);
+        if (ev_roll) cudaEventDestroy(ev_roll);
+        for (auto ev : ev_stage) cudaEventDestroy(ev);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
     }

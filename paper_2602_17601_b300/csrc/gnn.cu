@@ -400,7 +400,8 @@ static gm_status launch_ws_bwd(const gm_ctx* c, const Op& op, const TcW& tw, cud
         attr_set = true;
     }
     const long tiles = cdiv(op.rows, TC_M);
-    const int grid = (int)std::min<long>(tiles, std::max(1, c->num_sms));
+    const int sms = c->ws_grid > 0 ? std::min(c->ws_grid, c->num_sms) : c->num_sms;
+    const int grid = (int)std::min<long>(tiles, std::max(1, sms));
     GM_CUDA_TRY(launch_pdl(c->pdl, tc_ws_bwd_kernel<Op>, dim3((unsigned)grid), dim3(WS_T), WsLayout<Op>::smem, st, op,
                            tw));
     GM_LAUNCH_CHECK();
@@ -945,99 +946,142 @@ static int kernel_timing_begin(gm_ctx* c, int r, int Ns, cudaStream_t st) {
 }
 
 // Reverse pass over all stages (in chunks): A, B, c of Eq. linearized_dynamics.
-gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float* A, float* B,
-                        float* cvec, cudaStream_t st) {
+// Reverse pass of the stages k0 .. k0 + Ns - 1 (one chunk): A, B, c of Eq. linearized_dynamics.
+static gm_status jacobians_chunk(gm_ctx* c, int k0, int Ns, const float* x_hat, const float* u_hat, float* A,
+                                 float* B, float* cvec, cudaStream_t st) {
     const int K = c->K, W = c->W, M = c->M;
     const DCones& d = c->dc;
-    for (int k0 = 0; k0 < c->N; k0 += c->stage_chunk) {
+    float* X = c->d_dhA;
+    float* Y = c->d_dhB;
+    float* de_in = nullptr;
+    float* de_out = c->d_deA;
+    {   // decoder: seeds e_0, e_1, e_2 at dv^s
+        DecBwd op{};
+        fill_bwd(op, c, c->mlp[2 + 2 * K], k0, K + 1, false, (long)Ns * M * 3, M, W);
+        op.kin = 3;
+        op.dh = X;
+        GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[2 + 2 * K]), st));
+    }
+    for (int t = K - 1; t >= 0; --t) {
+        const int r = K - 1 - t;
+        const int Rn = d.nr_count[r], Re = d.er_count[r];
+        {
+            NodeMpBwd op{};
+            fill_bwd(op, c, c->mlp[3 + 2 * t], k0, 1 + t, false, (long)Ns * Rn * 3, Rn, 2 * W);
+            op.dh = X; op.dacc = c->d_dacc; op.dagg = c->d_dagg; op.nr_node = d.nr_node[r];
+            GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[3 + 2 * t]), st));
+        }
+        if (Re > 0) {
+            EdgeMpBwd op{};
+            const MlpOff& m = c->mlp[2 + 2 * t];
+            fill_bwd(op, c, m, k0, 1 + t, true, (long)Ns * Re * 3, Re, W);
+            op.B2 = c->d_wts + m.Wc;             // only the e-part of W1 (carry of e)
+            op.dagg = c->d_dagg; op.de_in = de_in; op.ehid = c->d_ehid; op.de_out = de_out;
+            op.er_edge = d.er_edge[r]; op.er_dstrow = d.er_dstrow[r]; op.er_prev = d.er_prev[r];
+            op.Rn = Rn; op.Rp = r > 0 ? d.er_count[r - 1] : 0;
+            const int kt = c->ktiming ? kernel_timing_begin(c, r, Ns, st) : -1;
+            const TcW tw = tc_edge_bwd(c, m);
+            if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_W) {
+                GM_TRY(launch_ws_bwd(c, op, tw, st));
+            } else {
+                GM_TRY(launch_mlp(c, op, tw, st));
+            }
+            if (kt >= 0) GM_CUDA_TRY(record_kev(c->kev[kt][1], st));
+        }
+        {
+            const int Rn1 = d.nr_count[r + 1];
+            NodeSumBwd op{};
+            const MlpOff& m = c->mlp[2 + 2 * t];
+            op.rows = (long)Ns * Rn1 * 3; op.kin = 2 * W; op.nout = W;
+            op.B1 = c->d_wts + m.Bab;            // [Sdst | Ssrc] -> dh
+            op.B2 = nullptr; op.wwords = W / 32; op.R = Rn1; op.W = W;
+            op.mask = nullptr; op.mstride = 0;
+            op.ehid = c->d_ehid; op.dacc = c->d_dacc; op.dh_next = Y;
+            op.nr_prev = d.nr_prev[r + 1]; op.dst_ptr = d.er_dst_ptr[r];
+            op.src_ptr = d.er_src_ptr[r]; op.src_list = d.er_src_list[r];
+            op.Rr = Rn; op.Re = Re;
+            GM_TRY(launch_mlp(c, op, tc_nodesum(c, m), st));
+        }
+        std::swap(X, Y);
+        de_in = de_out;
+        de_out = (de_out == c->d_deA) ? c->d_deB : c->d_deA;
+    }
+    {
+        const int RK = d.nr_count[K];
+        NodeEncBwd op{};
+        fill_bwd(op, c, c->mlp[0], k0, 0, false, (long)Ns * RK * 3, RK);
+        op.dh = X; op.dxn = c->d_dxn; op.nr_node = d.nr_node[K];
+        const TcW tw = tc_bwd(c, c->mlp[0]);
+        if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_N2_LAND) {
+            GM_TRY(launch_ws_bwd(c, op, tw, st));
+        } else {
+            GM_TRY(launch_mlp(c, op, tw, st));
+        }
+    }
+    const int RE = d.er_count[K - 1];
+    if (RE > 0) {
+        EdgeEncBwd op{};
+        fill_bwd(op, c, c->mlp[1], k0, 0, true, (long)Ns * RE * 3, RE);
+        op.de = de_in; op.dd = c->d_dd; op.er_edge = d.er_edge[K - 1];
+        const TcW tw = tc_bwd(c, c->mlp[1]);
+        if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_N2_LAND) {
+            GM_TRY(launch_ws_bwd(c, op, tw, st));
+        } else {
+            GM_TRY(launch_mlp(c, op, tw, st));
+        }
+    }
+    {
+        const long warps = (long)Ns * M;
+        jac_assemble_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(
+            Ns, k0, M, c->nu, K, c->dt, d.nr_ptr_K, d.nr_node[K], d.enc_dst_ptr,
+            d.enc_dst_list, d.er_src_ptr[K - 1], d.er_src_list[K - 1], d.b_row, d.nr_count[K],
+            RE, c->d_dxn, c->d_dd, x_hat, u_hat, A, B, cvec, c->nnzb);
+        GM_LAUNCH_CHECK();
+    }
+    return GM_OK;
+}
+
+// Reverse pass over all stages (in chunks).
+gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float* A, float* B,
+                        float* cvec, cudaStream_t st) {
+    for (int k0 = 0; k0 < c->N; k0 += c->stage_chunk)
+        GM_TRY(jacobians_chunk(c, k0, std::min(c->stage_chunk, c->N - k0), x_hat, u_hat, A, B, cvec, st));
+    return GM_OK;
+}
+
+// Rollout and Jacobians overlapped: the rollout runs on the context's high-priority stream,
+// forked from st, and records an event when the stages of a reverse chunk are rolled out; the
+// reverse pass of that chunk waits for the event on st and then runs beside the rollout of the
+// later stages.  The last chunk's event joins the rollout back into st.  (The reverse pass of
+// stage k needs x_hat[k], x_hat[k + 1], u_hat[k] and the ReLU masks of stage k, all written by
+// the rollout of stage k; the two use separate working buffers.)
+gm_status gnn_linearize(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, float* A, float* B,
+                        float* cvec, cudaStream_t st) {
+    const int n_chunks = (c->N + c->stage_chunk - 1) / c->stage_chunk;
+    if (!c->roll_stream || (int)c->ev_stage.size() < n_chunks) {
+        GM_TRY(gnn_rollout(c, x0, u_hat, x_hat, st));
+        return gnn_jacobians(c, x_hat, u_hat, A, B, cvec, st);
+    }
+    cudaStream_t rs = c->roll_stream;
+    GM_CUDA_TRY(cudaEventRecord(c->ev_roll, st));
+    GM_CUDA_TRY(cudaStreamWaitEvent(rs, c->ev_roll, 0));
+    const int M = c->M;
+    if (x_hat != x0) GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, rs));
+    for (int ci = 0, k0 = 0; k0 < c->N; ++ci, k0 += c->stage_chunk) {
         const int Ns = std::min(c->stage_chunk, c->N - k0);
-        float* X = c->d_dhA;
-        float* Y = c->d_dhB;
-        float* de_in = nullptr;
-        float* de_out = c->d_deA;
-        {   // decoder: seeds e_0, e_1, e_2 at dv^s
-            DecBwd op{};
-            fill_bwd(op, c, c->mlp[2 + 2 * K], k0, K + 1, false, (long)Ns * M * 3, M, W);
-            op.kin = 3;
-            op.dh = X;
-            GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[2 + 2 * K]), st));
-        }
-        for (int t = K - 1; t >= 0; --t) {
-            const int r = K - 1 - t;
-            const int Rn = d.nr_count[r], Re = d.er_count[r];
-            {
-                NodeMpBwd op{};
-                fill_bwd(op, c, c->mlp[3 + 2 * t], k0, 1 + t, false, (long)Ns * Rn * 3, Rn, 2 * W);
-                op.dh = X; op.dacc = c->d_dacc; op.dagg = c->d_dagg; op.nr_node = d.nr_node[r];
-                GM_TRY(launch_mlp(c, op, tc_bwd(c, c->mlp[3 + 2 * t]), st));
-            }
-            if (Re > 0) {
-                EdgeMpBwd op{};
-                const MlpOff& m = c->mlp[2 + 2 * t];
-                fill_bwd(op, c, m, k0, 1 + t, true, (long)Ns * Re * 3, Re, W);
-                op.B2 = c->d_wts + m.Wc;             // only the e-part of W1 (carry of e)
-                op.dagg = c->d_dagg; op.de_in = de_in; op.ehid = c->d_ehid; op.de_out = de_out;
-                op.er_edge = d.er_edge[r]; op.er_dstrow = d.er_dstrow[r]; op.er_prev = d.er_prev[r];
-                op.Rn = Rn; op.Rp = r > 0 ? d.er_count[r - 1] : 0;
-                const int kt = c->ktiming ? kernel_timing_begin(c, r, Ns, st) : -1;
-                const TcW tw = tc_edge_bwd(c, m);
-                if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_W) {
-                    GM_TRY(launch_ws_bwd(c, op, tw, st));
-                } else {
-                    GM_TRY(launch_mlp(c, op, tw, st));
-                }
-                if (kt >= 0) GM_CUDA_TRY(record_kev(c->kev[kt][1], st));
-            }
-            {
-                const int Rn1 = d.nr_count[r + 1];
-                NodeSumBwd op{};
-                const MlpOff& m = c->mlp[2 + 2 * t];
-                op.rows = (long)Ns * Rn1 * 3; op.kin = 2 * W; op.nout = W;
-                op.B1 = c->d_wts + m.Bab;            // [Sdst | Ssrc] -> dh
-                op.B2 = nullptr; op.wwords = W / 32; op.R = Rn1; op.W = W;
-                op.mask = nullptr; op.mstride = 0;
-                op.ehid = c->d_ehid; op.dacc = c->d_dacc; op.dh_next = Y;
-                op.nr_prev = d.nr_prev[r + 1]; op.dst_ptr = d.er_dst_ptr[r];
-                op.src_ptr = d.er_src_ptr[r]; op.src_list = d.er_src_list[r];
-                op.Rr = Rn; op.Re = Re;
-                GM_TRY(launch_mlp(c, op, tc_nodesum(c, m), st));
-            }
-            std::swap(X, Y);
-            de_in = de_out;
-            de_out = (de_out == c->d_deA) ? c->d_deB : c->d_deA;
-        }
-        {
-            const int RK = d.nr_count[K];
-            NodeEncBwd op{};
-            fill_bwd(op, c, c->mlp[0], k0, 0, false, (long)Ns * RK * 3, RK);
-            op.dh = X; op.dxn = c->d_dxn; op.nr_node = d.nr_node[K];
-            const TcW tw = tc_bwd(c, c->mlp[0]);
-            if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_N2_LAND) {
-                GM_TRY(launch_ws_bwd(c, op, tw, st));
-            } else {
-                GM_TRY(launch_mlp(c, op, tw, st));
-            }
-        }
-        const int RE = d.er_count[K - 1];
-        if (RE > 0) {
-            EdgeEncBwd op{};
-            fill_bwd(op, c, c->mlp[1], k0, 0, true, (long)Ns * RE * 3, RE);
-            op.de = de_in; op.dd = c->d_dd; op.er_edge = d.er_edge[K - 1];
-            const TcW tw = tc_bwd(c, c->mlp[1]);
-            if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.K1p == WS_W && tw.N2p == WS_N2_LAND) {
-                GM_TRY(launch_ws_bwd(c, op, tw, st));
-            } else {
-                GM_TRY(launch_mlp(c, op, tw, st));
-            }
-        }
-        {
-            const long warps = (long)Ns * M;
-            jac_assemble_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(
-                Ns, k0, M, c->nu, K, c->dt, d.nr_ptr_K, d.nr_node[K], d.enc_dst_ptr,
-                d.enc_dst_list, d.er_src_ptr[K - 1], d.er_src_list[K - 1], d.b_row, d.nr_count[K],
-                RE, c->d_dxn, c->d_dd, x_hat, u_hat, A, B, cvec, c->nnzb);
-            GM_LAUNCH_CHECK();
-        }
+        for (int k = k0; k < k0 + Ns; ++k)
+            GM_TRY(forward_stage(c, k, x_hat + (long)k * M * 6, u_hat + (long)k * c->nu, x_hat + (long)(k + 1) * M * 6,
+                                 rs));
+        GM_CUDA_TRY(cudaEventRecord(c->ev_stage[ci], rs));
+        GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_stage[ci], 0));
+        // the persistent reverse kernels hold their SMs for the whole launch: while the rollout
+        // still runs they leave it enough SMs for its widest launch; the last chunk starts after
+        // the rollout has finished and takes every SM
+        const bool last = k0 + Ns >= c->N;
+        c->ws_grid = last ? 0 : std::max(1, c->num_sms - (int)std::min<long>(c->num_sms / 2, cdiv(c->E, TC_M)));
+        const gm_status r = jacobians_chunk(c, k0, Ns, x_hat, u_hat, A, B, cvec, st);
+        c->ws_grid = 0;
+        GM_TRY(r);
     }
     return GM_OK;
 }

@@ -22,6 +22,10 @@ gm_status gnn_rollout_steps(gm_ctx* c, const float* x0, const float* u_hat, floa
                             cudaStream_t st);
 gm_status gnn_jacobians(gm_ctx* c, const float* x_hat, const float* u_hat, float* A, float* B,
                         float* cvec, cudaStream_t st);
+// rollout and Jacobians with the reverse pass of each stage chunk overlapping the rollout of
+// the later stages (rollout on the context's high-priority stream, joined back into st)
+gm_status gnn_linearize(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat, float* A, float* B,
+                        float* cvec, cudaStream_t st);
 
 // condense.cu
 // Packed stage-major rows (a stage-k row has k nu leading non-zeros) for Gram products.
