@@ -19,6 +19,10 @@ same states beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--form mixed|bf16|fp32] [--no-graph] [--no-plain] [--workload chain1000|chain10]
+  python bench.py --compare ipm       # ADMM against the interior-point solve on the step's QP
+  python bench.py --compare barrier   # obstacles as QP rows against obstacles as barrier costs
+
+The two comparisons print their own JSON line (not the metric line above).
 
 The chosen form (default): GNN MLPs and their Jacobian products on tcgen05 tensor
 cores with split-BF16 operands (forward rollout three pieces, reverse two), FP32
@@ -58,14 +62,28 @@ def parse(argv=None):
     p.add_argument("--no-graph", action="store_true", help="eager launches instead of CUDA-graph replay")
     p.add_argument("--no-warm", action="store_true", help="cold ADMM every step (no receding-horizon warm start)")
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
-    p.add_argument("--workload", default="chain1000", choices=["chain1000", "chain10"])
+    p.add_argument("--workload", default="chain1000", choices=["chain1000", "chain200", "chain10"],
+                   help="chain200: the chain-of-1000 configuration on 200 nodes (a small case for "
+                        "counter captures of the same kernels)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--compare", default=None, choices=["ipm", "barrier"],
+                   help="ipm: gm_qp_solve against gm_qp_solve_ipm on the chain-of-1000 step's QP; barrier: "
+                        "sphere rows as constraints against relaxed log barriers, spheres far and near")
+    p.add_argument("--reps", type=int, default=5, help="--compare ipm: timed solves (median)")
+    p.add_argument("--time-oracle-step", default=None, choices=list(FULL_STEP_WORKLOADS),
+                   help=argparse.SUPPRESS)   # child process of full_oracle_steps
+    p.add_argument("--mu", type=float, default=1e-3, help="--compare barrier: barrier weight")
+    p.add_argument("--delta", type=float, default=5e-3, help="--compare barrier: relaxation threshold")
     return p.parse_args(argv)
 
 
 def workload(name):
     from synth import paper_chain, small_chain
-    return paper_chain() if name == "chain1000" else small_chain()
+    if name == "chain1000":
+        return paper_chain()
+    if name == "chain200":
+        return paper_chain(M=200)
+    return small_chain()
 
 
 def config_of(wl, form, extra=None):
@@ -169,11 +187,15 @@ def oracle_sample_seconds(wl, n_jac=4, m_reduced=50, seed=0):
 
 
 def cpu_cores():
+    """Host threads the oracle's BLAS may use: the thread-count variables if set, else the cores
+    this process may run on."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var, "")
+        if v.isdigit() and int(v) > 0:
+            return int(v)
     try:
-        from threadpoolctl import threadpool_info
-        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
-        return int(n)
-    except Exception:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
         return os.cpu_count() or 1
 
 
@@ -191,26 +213,40 @@ def cpu_model():
     return "unknown"
 
 
+FULL_STEP_WORKLOADS = ("chain10_K2_W32_N10_nu4", "chain50_K3_W128_N20_nu8_spheres5")
+
+
+def time_full_oracle_step(name, reps):
+    """Seconds per full RTI step of the FP64 oracle on one of FULL_STEP_WORKLOADS (run in a child
+    process, so that its BLAS thread count follows the child's environment)."""
+    from oracle import rti as orti
+    from synth import paper_chain, small_chain
+    wl = small_chain() if name.startswith("chain10_") else paper_chain(M=50)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        orti.rti_step(wl, solver="admm")
+    return (time.perf_counter() - t0) / reps
+
+
 def full_oracle_steps():
     """Measured (not extrapolated) full RTI steps of the FP64 oracle (oracle.rti.rti_step with its
     ADMM, the method's own solver): the chain of 10 (K=2, W=32, N=10) and a chain of 50 with the
     paper-scale GNN and horizon (K=3, W=128, N=20, nu=8, 5 spheres), each with all host cores and
-    with one BLAS thread."""
-    from threadpoolctl import threadpool_limits
-
-    from oracle import rti as orti
-    from synth import paper_chain, small_chain
+    with one BLAS thread (a child process per leg with the thread-count variables set)."""
     out = {}
-    for name, wl, reps in (("chain10_K2_W32_N10_nu4", small_chain(), 10),
-                           ("chain50_K3_W128_N20_nu8_spheres5", paper_chain(M=50), 1)):
+    one = {v: "1" for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for name, reps in zip(FULL_STEP_WORKLOADS, (10, 1)):
         ent = {}
-        for mode, limit in (("all_cores", None), ("one_thread", 1)):
-            with threadpool_limits(limits=limit):
-                t0 = time.perf_counter()
-                for _ in range(reps):
-                    orti.rti_step(wl, solver="admm")
-                sec = (time.perf_counter() - t0) / reps
-            ent[mode] = {"seconds_per_step": sec, "steps_per_s": 1.0 / sec, "steps_timed": reps}
+        for mode, extra in (("all_cores", {}), ("one_thread", one)):
+            env = dict(os.environ, **extra)
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--time-oracle-step", name,
+                                "--reps", str(reps)], env=env, capture_output=True, text=True, timeout=900)
+            if r.returncode != 0:
+                raise RuntimeError(f"oracle step timing failed ({name}, {mode}):\n{r.stderr[-2000:]}")
+            rep = json.loads(r.stdout.strip().splitlines()[-1])
+            sec = rep["seconds_per_step"]
+            ent[mode] = {"seconds_per_step": sec, "steps_per_s": 1.0 / sec, "steps_timed": reps,
+                         "threads": rep["threads"]}
         out[name] = ent
     return out
 
@@ -371,6 +407,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     kst = gm.gm_ctx_kernel_stats(prob.ctx)        # dominant kernel, last timed step
+    klaunch = [gm.gm_ctx_kernel_launch(prob.ctx, i) for i in range(kst["launches"])]
     replayed, captures = prob.graph_state()
     st = prob.read_stats()
     ms = max_over_ranks(ms)
@@ -476,6 +513,15 @@ def run_ours(args):
             "tensor_peak_tflops": peaks.get("bf16_tflops_sustained"),
             "share_of_step": k_ms / ms,
             "phase_ms": per_phase}
+    # the launches that had the whole GPU (the last chunk's, after the rollout): the kernel's own
+    # rate; the earlier chunks' launches share the SMs and HBM with the rollout of later stages
+    full = [L for L in klaunch if L["ctas"] >= max(x["ctas"] for x in klaunch)] if klaunch else []
+    f_ms, f_by = sum(L["ms"] for L in full), sum(L["bytes"] for L in full)
+    if f_ms > 0 and len(full) < len(klaunch):
+        roof["beside_rollout"] = {"launches": len(klaunch) - len(full),
+                                  "ctas": sorted({L["ctas"] for L in klaunch if L not in full})}
+        roof["alone"] = {"launches": len(full), "ctas": full[0]["ctas"], "ms": f_ms,
+                         "achieved": f_by / (f_ms * 1e-3) / 1e9, "frac": f_by / (f_ms * 1e-3) / 1e9 / hbm_peak}
     out = {"metric": METRIC, "value": reps.steps_per_s(ms), "unit": "steps/s", "n_gpus": world,
            "steps": args.steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -516,9 +562,103 @@ def prob_nU(wl):
     return wl.N * wl.nu
 
 
+def compare_ipm(args):
+    """ADMM (gm_qp_solve, adaptive rho) against the interior-point method (gm_qp_solve_ipm,
+    Mehrotra predictor-corrector) on the condensed QP of the chain of 1000 nodes at the first
+    step's point (u_hat = 0), mixed form, both to the workload's tolerance.  Device ms from CUDA
+    events around each call (the IPM's host reads of its done flag included), median of reps
+    after one warm-up."""
+    import numpy as np
+    import torch
+
+    import paper_2602_17601_b300 as gm
+    wl = workload("chain1000")
+    prob = gm.RTIProblem.from_workload(wl, precision=gm.GM_PREC_MIXED)
+    x_hat, A, B, c = prob.linearize(wl.x0, np.zeros((wl.N, wl.nu), np.float32))
+    H, g, Ct, dt = prob.condense(x_hat, A, B, c)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        out, ms = None, []
+        for _ in range(args.reps + 1):
+            torch.cuda.synchronize()
+            ev[0].record()
+            out = fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return out, float(np.median(ms[1:])), prob.read_stats()
+
+    (Ua, _), ms_a, st_a = timed(lambda: prob.qp_solve(H, g, Ct, dt))
+    (Ui, _), ms_i, st_i = timed(lambda: prob.qp_solve_ipm(H, g, Ct, dt, max_iter=80))
+    keep = ("status", "iters", "converged", "r_prim", "r_dual", "kkt_stat", "kkt_prim", "kkt_dual", "kkt_comp")
+    print(json.dumps({"compare": "ipm", "workload": "chain1000_K3_W128_N20_nu8_spheres5", "n": int(prob.nU),
+                      "rows": int(prob.rows_c), "tol": wl.tol, "reps": args.reps,
+                      "admm": {"ms": ms_a, **{k: st_a[k] for k in keep}},
+                      "ipm": {"ms": ms_i, **{k: st_i[k] for k in keep}},
+                      "max_abs_U_diff": float((Ua - Ui).abs().max()), "max_abs_U": float(Ua.abs().max()),
+                      "device": torch.cuda.get_device_name()}), flush=True)
+
+
+def compare_barrier(args):
+    """The chain of 1000 nodes with its 5 spheres (radius 0.02) 0.15 ("far", the benchmark
+    workload) and 0.01 ("near") from their nodes at the initial state, each stepped from that
+    state (the step's own solution shifted into the next linearisation point), mixed form, graph
+    replay: sphere rows as QP constraints against relaxed log barriers in the cost (gm_constr
+    barrier_mu / barrier_delta).  Device ms per step (CUDA events over args.steps steps after
+    args.warmup), the last step's ADMM iterations and status, and the smallest sphere clearance
+    of the GNN rollout under the returned inputs."""
+    import numpy as np
+    import torch
+
+    import paper_2602_17601_b300 as gm
+    from synth import paper_chain
+
+    def run(wl, barrier):
+        sph = wl.spheres.astype(np.float64)
+        prob = gm.RTIProblem.from_workload(wl, precision=gm.GM_PREC_MIXED, graph=True, barrier=barrier)
+        x = torch.as_tensor(wl.x0.reshape(-1), dtype=torch.float32, device="cuda")
+        U = prob.empty(prob.nU)
+        for _ in range(args.warmup):
+            prob.step(x, U)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(args.steps):
+            prob.step(x, U)
+        ev[1].record()
+        torch.cuda.synchronize()
+        st = prob.read_stats()
+        xs = prob.empty(wl.N + 1, wl.M, 6)
+        gm.gm_rollout(prob.ctx, x, U, wl.N, xs)
+        p = xs.cpu().numpy().astype(np.float64)[1:, :, :3]
+        clear = np.linalg.norm(p[:, :, None, :] - sph[None, None, :, :3], axis=-1) - sph[None, None, :, 3]
+        out = {"ms_per_step": ev[0].elapsed_time(ev[1]) / args.steps, "admm_iters": st["iters"],
+               "status": st["status"], "converged": st["converged"], "min_clearance": float(clear.min()),
+               "max_abs_U": float(U.abs().max())}
+        prob.close()
+        return out
+
+    rep = {"compare": "barrier", "workload": "chain1000_K3_W128_N20_nu8_spheres5", "form": "mixed, graph replay",
+           "steps": args.steps, "warmup": args.warmup, "mu": args.mu, "delta": args.delta}
+    for name, clear in (("far", 0.15), ("near", 0.01)):
+        wl = paper_chain(sphere_clear=clear)
+        rep[name] = {"sphere_clearance_at_x0": clear, "constraints": run(wl, None),
+                     "barrier": run(wl, (args.mu, args.delta))}
+    rep["device"] = torch.cuda.get_device_name()
+    print(json.dumps(rep), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.time_oracle_step:
+        print(json.dumps({"seconds_per_step": time_full_oracle_step(args.time_oracle_step, args.reps),
+                          "threads": cpu_cores()}), flush=True)
+    elif args.compare == "ipm":
+        compare_ipm(args)
+    elif args.compare == "barrier":
+        compare_barrier(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -133,7 +133,13 @@ void gm_gnn_destroy(gm_gnn* m);
  *                on every SM); smaller grids let batched instances run side by side
  *   factor_grid  CTAs of the cooperative FP64 factor kernel (0: 128)
  *   chunk_mb     device memory budget of the reverse-pass cotangent buffers in
- *                MB (0: 16384); fewer stages per launch group when smaller
+ *                MB (0: 16384, and at most a quarter of the horizon per chunk);
+ *                fewer stages per launch group when smaller.  gm_linearize and
+ *                gm_rti_step run the rollout on a high-priority internal stream
+ *                and the reverse pass of each chunk as soon as its stages are
+ *                rolled out, beside the rollout of the later stages (with at
+ *                most SMs - ceil(E/128) CTAs per persistent reverse launch until
+ *                the rollout ends)
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N;
@@ -401,6 +407,16 @@ gm_status gm_ctx_phase_ms(gm_ctx* ctx, float* ms5, int* steps);
  * L2 size in bytes (cudaDevAttrL2CacheSize). */
 gm_status gm_measure_peaks(double* fp32_tflops, double* fp64_tflops, long long* l2_bytes, void* stream);
 
+/* HBM rates of three streams over a caller-owned device buffer buf of bytes
+ * (16-byte aligned, at least 64 MB; use well above the L2 size): read-only
+ * (the first half), write-only (the second half) and copy (first half to
+ * second), 16-byte accesses, CUDA events on stream (which the call
+ * synchronises), best of repeats after one warm-up; GB/s counts the bytes read
+ * plus written.  The buffer is overwritten with zeros.  For the roofline of
+ * kernels whose traffic is mostly reads or mostly writes, beside the copy peak. */
+gm_status gm_measure_hbm(void* buf, size_t bytes, int repeats, double* read_gbs, double* write_gbs,
+                         double* copy_gbs, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long gm_launch_count(void);
 
@@ -496,6 +512,11 @@ gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures);
  * FLOPs (all zero before the first recorded step). */
 gm_status gm_ctx_set_kernel_timing(gm_ctx* ctx, int on);
 gm_status gm_ctx_kernel_stats(gm_ctx* ctx, int* launches, double* ms, double* bytes, double* flops);
+/* Launch i (0 <= i < the launches of gm_ctx_kernel_stats) of the last recorded step: its
+ * milliseconds, algorithmic bytes and CTAs (one per SM; fewer than the SMs for a launch that
+ * ran beside the rollout of later stages: gm_settings chunk_mb).  GM_ERR_INVALID_ARG for
+ * an index out of range. */
+gm_status gm_ctx_kernel_launch(gm_ctx* ctx, int i, double* ms, double* bytes, int* ctas);
 
 /* ------------------------------------------------------------------------
  * Learned ADMM warm start (no paper counterpart; an added systems pattern).
@@ -556,8 +577,11 @@ gm_status gm_ws_features(gm_ctx* ctx, const float* x_meas, const float* x_ref, f
  *   H, g, Ct, dt, u_lo, u_hi, U, y, stats   as for gm_qp_solve (device
  *           pointers; Ct/dt NULL when Mnc == 0; y and stats nullable)
  * The first call on a device looks up the array's device address on that
- * device (the device must be current); make that first call before any
- * stream capture.  Every call uses the same array and leaves the last
+ * device (the device must be current).  That first call is also when CUDA
+ * loads the library's kernel modules onto the device (lazy loading), which
+ * reserves their device memory, the array included, and may synchronise the
+ * device: a caller that must not allocate once running makes one call at
+ * initialisation, before any stream capture; later calls allocate nothing.  Every call uses the same array and leaves the last
  * call's contents in it (the call clears what must start at zero): calls
  * whose kernels overlap on the GPU (other streams, other host threads) race
  * and give wrong results; serialise them.

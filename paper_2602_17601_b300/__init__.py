@@ -132,10 +132,14 @@ def _load():
         "gm_ctx_set_warm": ([vp, C.c_int], C.c_int),
         "gm_ctx_set_timeout_spins": ([vp, C.c_int], C.c_int),
         "gm_measure_peaks": ([C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong), vp], C.c_int),
+        "gm_measure_hbm": ([vp, C.c_size_t, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                            C.POINTER(C.c_double), vp], C.c_int),
         "gm_batch_set_lanes": ([vp, C.c_int], C.c_int),
         "gm_batch_plan": ([C.c_int, vp, vp, C.c_int, vp, C.POINTER(C.c_int)], C.c_int),
         "gm_barrier_fold": ([vp, vp, vp, vp, C.c_float, C.c_float, vp, vp, vp], C.c_int),
         "gm_ctx_kernel_stats": ([vp, C.POINTER(C.c_int)] + [C.POINTER(C.c_double)] * 3, C.c_int),
+        "gm_ctx_kernel_launch": ([vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)],
+                                 C.c_int),
         "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -152,10 +156,10 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_qp_solve", "gm_qp_solve_ipm", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
                     "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count", "gm_qp_solve_noalloc",
                     "gm_ctx_set_graph", "gm_ctx_graph_state", "gm_ctx_set_kernel_timing",
-                    "gm_ctx_kernel_stats", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
+                    "gm_ctx_kernel_stats", "gm_ctx_kernel_launch", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
                     "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
-                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_set_lanes", "gm_batch_plan", "gm_ctx_set_warm", "gm_barrier_fold", "gm_ctx_set_timeout_spins", "gm_measure_peaks",
+                    "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_set_lanes", "gm_batch_plan", "gm_ctx_set_warm", "gm_barrier_fold", "gm_ctx_set_timeout_spins", "gm_measure_peaks", "gm_measure_hbm",
                     "gm_rollout")
 
 GM_NOALLOC_MAX_NU = 64
@@ -219,6 +223,14 @@ def gm_measure_peaks(stream=None):
     return {"fp32_tflops": f32.value, "fp64_tflops": f64.value, "l2_bytes": int(l2.value)}
 
 
+def gm_measure_hbm(buf, repeats=5, stream=None):
+    """HBM GB/s of read-only, write-only and copy streams over the device tensor buf (overwritten)."""
+    r, w, c = C.c_double(), C.c_double(), C.c_double()
+    _check("gm_measure_hbm", _lib.gm_measure_hbm(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
+                                                 int(repeats), C.byref(r), C.byref(w), C.byref(c), _stream(stream)))
+    return {"read_gbs": r.value, "write_gbs": w.value, "copy_gbs": c.value}
+
+
 def gm_ctx_set_timeout_spins(ctx, spins):
     _check("gm_ctx_set_timeout_spins", _lib.gm_ctx_set_timeout_spins(ctx, int(spins)))
 
@@ -237,6 +249,13 @@ def gm_ctx_kernel_stats(ctx):
     ms, by, fl = C.c_double(), C.c_double(), C.c_double()
     _check("gm_ctx_kernel_stats", _lib.gm_ctx_kernel_stats(ctx, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
     return dict(launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
+
+
+def gm_ctx_kernel_launch(ctx, i):
+    """Launch i of the last recorded step's reverse edge-MLP launches: dict(ms, bytes, ctas)."""
+    ms, by, n = C.c_double(), C.c_double(), C.c_int()
+    _check("gm_ctx_kernel_launch", _lib.gm_ctx_kernel_launch(ctx, int(i), C.byref(ms), C.byref(by), C.byref(n)))
+    return dict(ms=ms.value, bytes=by.value, ctas=n.value)
 
 
 def gm_ctx_graph_state(ctx):

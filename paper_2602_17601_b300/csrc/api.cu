@@ -1175,6 +1175,19 @@ gm_status gm_ctx_kernel_stats(gm_ctx* ctx, int* launches, double* ms, double* by
     return GM_OK;
 }
 
+gm_status gm_ctx_kernel_launch(gm_ctx* ctx, int i, double* ms, double* bytes, int* ctas) {
+    clear_error();
+    GM_CHECK_ARG(ctx && ms && bytes && ctas, "NULL argument");
+    GM_CHECK_ARG(i >= 0 && i < ctx->kev_n && i < (int)ctx->kev.size(), "launch index %d out of range", i);
+    GM_CUDA_TRY(cudaEventSynchronize(ctx->kev[i][1]));
+    float t = 0.f;
+    GM_CUDA_TRY(cudaEventElapsedTime(&t, ctx->kev[i][0], ctx->kev[i][1]));
+    *ms = t;
+    *bytes = ctx->kev_bytes[i];
+    *ctas = ctx->kev_ctas[i];
+    return GM_OK;
+}
+
 gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures) {
     clear_error();
     GM_CHECK_ARG(ctx, "ctx is NULL");

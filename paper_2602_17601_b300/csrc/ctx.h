@@ -172,6 +172,7 @@ struct gm_ctx {
     int kev_n = 0;
     std::vector<std::array<cudaEvent_t, 2>> kev;
     std::vector<double> kev_bytes, kev_flops;
+    std::vector<int> kev_ctas;   // CTAs of each timed launch (fewer than the SMs while the rollout runs beside it)
 
     ~gm_ctx() {
         for (auto& e : kev)

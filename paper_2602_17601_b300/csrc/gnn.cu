@@ -926,6 +926,7 @@ static int kernel_timing_begin(gm_ctx* c, int r, int Ns, cudaStream_t st) {
         c->kev.push_back(e);
         c->kev_bytes.push_back(0.0);
         c->kev_flops.push_back(0.0);
+        c->kev_ctas.push_back(0);
     }
     const Cones& C = c->cones;
     const double W = c->W, Re = (double)C.er_edge[r].size(), Rn = (double)C.nr_node[r].size();
@@ -941,6 +942,9 @@ static int kernel_timing_begin(gm_ctx* c, int r, int Ns, cudaStream_t st) {
     const double rows = 3.0 * Ns * Re;
     c->kev_bytes[i] = 4.0 * W * (2.0 * rows + 3.0 * Ns * carried + 3.0 * Ns * Rn) + Ns * edges * W / 8.0;
     c->kev_flops[i] = 4.0 * W * W * rows;
+    const long tiles = (long)((rows + TC_M - 1) / TC_M);
+    const int sms = c->ws_grid > 0 ? std::min(c->ws_grid, c->num_sms) : c->num_sms;
+    c->kev_ctas[i] = (int)std::min<long>(tiles, std::max(1, sms));
     if (record_kev(c->kev[i][0], st) != cudaSuccess) return -1;
     return i;
 }

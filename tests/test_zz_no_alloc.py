@@ -76,3 +76,53 @@ def test_noalloc_rejects_sizes_beyond_its_limit(lib):
     with pytest.raises(lib.GMError) as e:      # 8 * 1100 = 8800 rows > 8192
         lib.gm_qp_solve_noalloc(8, 4, 1100, s, z, z, z, z, z, z, z)
     assert e.value.code == lib.GM_ERR_INVALID_ARG
+
+
+_FRESH = r"""
+import sys, ctypes
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import torch
+import paper_2602_17601_b300 as gm
+torch.cuda.init()
+N, nu, Mnc = 4, 2, 3
+rng = np.random.default_rng(0)
+L = rng.normal(0, 1, (N * nu, N * nu))
+H = (L @ L.T + 0.1 * np.eye(N * nu)).astype(np.float32)
+g = rng.normal(0, 1, N * nu).astype(np.float32)
+Ct = rng.normal(0, 1, Mnc * nu * N * (N + 1) // 2).astype(np.float32)
+dt = np.full(N * Mnc, 1.0, np.float32)
+dev = lambda a: torch.as_tensor(a, device="cuda")
+H_d, g_d, Ct_d, dt_d = dev(H), dev(g), dev(Ct), dev(dt)
+lo, hi = dev(-np.ones(N * nu, np.float32)), dev(np.ones(N * nu, np.float32))
+U = torch.empty(N * nu, device="cuda")
+stats = torch.zeros(gm.STATS_BYTES, dtype=torch.uint8, device="cuda")
+s = gm.make_settings(N, 1, rho=0.1, tol=1e-6, max_iter=4000)
+torch.cuda.synchronize()
+gm.gm_qp_solve_noalloc(N, nu, Mnc, s, H_d, g_d, Ct_d, dt_d, lo, hi, U, None, stats)   # first call: loads the modules
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+for _ in range(2):
+    gm.gm_qp_solve_noalloc(N, nu, Mnc, s, H_d, g_d, Ct_d, dt_d, lo, hi, U, None, stats)
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+st = gm.read_stats(stats)
+print(free0, free1, st["status"], st["converged"])
+"""
+
+
+def test_noalloc_later_calls_leave_free_device_memory_unchanged(lib, tmp_path):
+    """In a fresh process whose only library call is the no-allocation solve: after the first
+    call (which loads the library's modules onto the device), two more calls leave the device's
+    free memory (cudaMemGetInfo) unchanged."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "fresh_noalloc.py"
+    script.write_text(_FRESH)
+    r = subprocess.run([sys.executable, str(script), root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    free0, free1, status, conv = (int(v) for v in r.stdout.split()[-4:])
+    assert status == lib.GM_OK and conv == 1, r.stdout
+    assert free1 == free0, (free0, free1)
