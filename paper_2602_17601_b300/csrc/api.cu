@@ -238,8 +238,8 @@ static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::v
         auto up16 = [](int v) { return (v + 15) / 16 * 16; };
         mo.in_p = up16(in);
         mo.out_p = up16(out);
-        mo.fk1 = put_bf(wp, hid, mo.in_p, TC_CHUNK, [&](int j, int i) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
-        mo.fk2 = put_bf(wp, mo.out_p, hid, tc_chunk_b2(mo.out_p), [&](int o, int j) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
+        mo.fk1 = put_bf(wp, hid, mo.in_p, TC_CHUNK_F, [&](int j, int i) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
+        mo.fk2 = put_bf(wp, mo.out_p, hid, tc_chunk_b2_fwd(mo.out_p), [&](int o, int j) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
         mo.bk1 = put_bf(wp, hid, mo.out_p, TC_CHUNK, [&](int j, int o) { return o < out ? W2[(size_t)j * out + o] : 0.f; });
         mo.bk2 = put_bf(wp, mo.in_p, hid, tc_chunk_b2(mo.in_p), [&](int i, int j) { return i < in ? W1[(size_t)i * hid + j] : 0.f; });
         if (edge_mp) {

@@ -357,7 +357,8 @@ static cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim
 
 template <int W, int P, class Op>
 static gm_status launch_tc(bool pdl, const Op& op, const TcW& tw, cudaStream_t st) {
-    constexpr size_t smem = tc_smem_bytes<W, P>() > TC_SMEM_MIN ? tc_smem_bytes<W, P>() : TC_SMEM_MIN;
+    constexpr bool F = (Op::kMode == 0);
+    constexpr size_t smem = tc_smem_bytes<W, F, P>() > TC_SMEM_MIN ? tc_smem_bytes<W, F, P>() : TC_SMEM_MIN;
     static_assert(W <= TC_NB, "GEMM1 width must fit the staged B chunk");
     if (tw.N2p > TC_TMEM_COLS || tw.N2p % 16 || tw.K1p % 16) {
         set_error("tensor-core MLP shape out of range (K1p %d, N2p %d)", tw.K1p, tw.N2p);

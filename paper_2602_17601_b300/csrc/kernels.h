@@ -12,6 +12,13 @@ namespace gmi {
 // wider than 128 rows, whose chunks must still fit the 128 x 64 staging buffer.
 constexpr int TC_CHUNK = 64;
 inline __host__ __device__ int tc_chunk_b2(int rows) { return rows > 128 ? TC_CHUNK / 2 : TC_CHUNK; }
+// forward (rollout) MLPs: K chunk width and weight/A buffers.  Measured on the chain of 1000
+// (rollout phase): 64 / 1: 3.35 ms; 64 / 2: 4.07 ms; 32 / 2: 4.25 ms; 32 / 3: 4.47 ms
+constexpr int TC_CHUNK_F = 64;
+constexpr int TC_NBUF_F = 1;
+constexpr int TC_NBUF_MAX = 2;   // buffers the tile state tracks
+static_assert(TC_NBUF_F <= TC_NBUF_MAX, "forward chunk buffers exceed the tile state");
+inline __host__ __device__ int tc_chunk_b2_fwd(int rows) { return rows > 128 ? TC_CHUNK_F / 2 : TC_CHUNK_F; }
 inline __host__ __device__ long tc_tile_off(int n, int k, int kc) {
     return (long)(n >> 3) * 8 * kc + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
 }

@@ -264,33 +264,40 @@ __device__ __forceinline__ void tc_store_a_full(unsigned char* sA, int a_piece, 
     }
 }
 
-// K per staged chunk (the tiled weight layout's chunk width).
-template <int P>
+// K per staged chunk (the tiled weight layout's chunk width): TC_CHUNK_F for the forward
+// (rollout) MLPs, F = true, whose weights are tiled with it; TC_CHUNK for the reverse MLPs.
+template <bool F, int P>
 __host__ __device__ constexpr int tc_kc() {
-    return TC_CHUNK;
+    return F ? TC_CHUNK_F : TC_CHUNK;
+}
+// K per staged chunk of the second product (half a chunk for products wider than TC_NB rows).
+template <bool F>
+__host__ __device__ inline int tc_kc2(int n2p) {
+    return F ? tc_chunk_b2_fwd(n2p) : tc_chunk_b2(n2p);
 }
 
 // Shared memory: [A chunk buffers | hidden tile] (the hidden tile reuses the A buffers once
 // GEMM1 is done) followed by the B chunk buffers (TC_NB rows x KC; GEMM2 products wider than
 // TC_NB stage half-K chunks of the same size).
 // Chunk pipeline depth: the A chunk and the weight chunk each get NBUF buffers (chunk g in
-// buffer g % NBUF; with two, chunk c + 1 is staged and its weights copied while chunk c
-// multiplies).  One: two buffers for the three-piece forward form take the CTA to 192 KB of
-// shared memory, and the smaller L1 left beside it slows the gathered node-row loads of the
-// forward more than the overlap gains (measured 0.6 ms per step slower).
-template <int P>
+// buffer g % NBUF; the weight chunk NBUF - 1 ahead is in flight while chunk c multiplies).
+// One buffer everywhere: for the three-piece forward, two full-width buffers (192 KB of shared
+// memory, less L1 for its gathered node-row loads) and two or three half-width ones (more
+// chunks, each with its barrier and MMA-issue round) all measured slower; the reverse MLPs run
+// two CTAs per SM with one buffer.
+template <bool F, int P>
 __host__ __device__ constexpr int tc_nbuf() {
-    return 1;
+    return F ? TC_NBUF_F : 1;
 }
-template <int W, int P>
+template <int W, bool F, int P>
 __host__ __device__ constexpr size_t tc_region_a() {
-    return (size_t)P * ((size_t)tc_nbuf<P>() * TC_M * tc_kc<P>() * 2 > (size_t)TC_M * W * 2
-                            ? (size_t)tc_nbuf<P>() * TC_M * tc_kc<P>() * 2
+    return (size_t)P * ((size_t)tc_nbuf<F, P>() * TC_M * tc_kc<F, P>() * 2 > (size_t)TC_M * W * 2
+                            ? (size_t)tc_nbuf<F, P>() * TC_M * tc_kc<F, P>() * 2
                             : (size_t)TC_M * W * 2);
 }
-template <int W, int P>
+template <int W, bool F, int P>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-    return tc_region_a<W, P>() + (size_t)tc_nbuf<P>() * P * TC_NB * tc_kc<P>() * 2;
+    return tc_region_a<W, F, P>() + (size_t)tc_nbuf<F, P>() * P * TC_NB * tc_kc<F, P>() * 2;
 }
 // Launch size: at least TC_SMEM_MIN, so that no more than two CTAs share an SM (what two
 // TC_TMEM_COLS allocations fill) and the output tile of tc_out_rows fits.
@@ -303,16 +310,16 @@ static_assert(TC_OUT_BYTES <= TC_SMEM_MIN, "output tile must fit the minimum lau
 struct TcTileState {
     unsigned long long* mbar;     // [NBUF] MMA completion (tcgen05.commit)
     unsigned long long* bbar;     // [NBUF] weight chunk arrival (bulk-copy bytes)
-    unsigned mph[2], bphase[2];   // completed phases (NBUF <= 2)
-    bool b_pending[2];
+    unsigned mph[TC_NBUF_MAX], bphase[TC_NBUF_MAX];   // completed phases
+    bool b_pending[TC_NBUF_MAX];
 };
 
 // Thread 0: bulk-copy weight chunk g of a tile (g < nch: the K chunks of B1; then the K chunks of
 // B2) into buffer g % NBUF.
-template <int W, int P>
+template <int W, bool F, int P>
 __device__ __forceinline__ void tc_load_chunk(const TcW& w, unsigned char* sB0, TcTileState& S, int g, int nch,
                                               int kc2) {
-    constexpr int KC = tc_kc<P>(), NBUF = tc_nbuf<P>(), B_BYTES = TC_NB * KC * 2;
+    constexpr int KC = tc_kc<F, P>(), NBUF = tc_nbuf<F, P>(), B_BYTES = TC_NB * KC * 2;
     const int b = g % NBUF;
     unsigned char* dst = sB0 + (size_t)b * P * B_BYTES;
     if (g < nch) {
@@ -327,13 +334,14 @@ __device__ __forceinline__ void tc_load_chunk(const TcW& w, unsigned char* sB0, 
 // Thread 0: the first weight chunks of a tile (issued early, under the tile's prologue).
 template <int W, class Op, int P>
 __device__ __forceinline__ void tc_tile_prefetch(const TcW& w, unsigned char* tsm, TcTileState& S) {
-    constexpr int NBUF = tc_nbuf<P>();
+    constexpr bool F = (Op::kMode == 0);
+    constexpr int NBUF = tc_nbuf<F, P>();
     constexpr bool kSingle = (Op::kMode == 2);
-    const int nch = (w.K1p + tc_kc<P>() - 1) / tc_kc<P>();
-    const int kc2 = tc_chunk_b2(w.N2p);
+    const int nch = (w.K1p + tc_kc<F, P>() - 1) / tc_kc<F, P>();
+    const int kc2 = tc_kc2<F>(w.N2p);
     const int ng = nch + (kSingle ? 0 : (W + kc2 - 1) / kc2);
-    unsigned char* sB0 = tsm + tc_region_a<W, P>();
-    for (int g = 0; g < NBUF && g < ng; ++g) tc_load_chunk<W, P>(w, sB0, S, g, nch, kc2);
+    unsigned char* sB0 = tsm + tc_region_a<W, F, P>();
+    for (int g = 0; g < NBUF && g < ng; ++g) tc_load_chunk<W, F, P>(w, sB0, S, g, nch, kc2);
 }
 
 // One 128-row tile of the fused MLP (rows row0 ..), run by all TC_T threads of the CTA:
@@ -345,17 +353,18 @@ __device__ __forceinline__ void tc_tile_prefetch(const TcW& w, unsigned char* ts
 template <int W, class Op, int P>
 __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row0, unsigned char* tsm,
                                             const RowCtx* rc, unsigned tD, TcTileState& S) {
-    constexpr int KC = tc_kc<P>();
+    constexpr bool F = (Op::kMode == 0);
+    constexpr int KC = tc_kc<F, P>();
     constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = TC_NB * KC * 2, H_BYTES = TC_M * W * 2;
     unsigned char* sA = tsm;                          // NBUF x P pieces of the A chunk, K-major with K = KC
     unsigned char* sH = tsm;                          // P pieces of the hidden tile, K = W (after GEMM1)
-    constexpr int NBUF = tc_nbuf<P>();
-    unsigned char* sB0 = tsm + tc_region_a<W, P>();   // NBUF buffers of P pieces of a B chunk (bulk copies)
+    constexpr int NBUF = tc_nbuf<F, P>();
+    unsigned char* sB0 = tsm + tc_region_a<W, F, P>();   // NBUF buffers of P pieces of a B chunk (bulk copies)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long rows = op.rows;
     constexpr bool kSingle = (Op::kMode == 2);
     const int nch = (w.K1p + KC - 1) / KC;
-    const int kc2 = tc_chunk_b2(w.N2p);
+    const int kc2 = tc_kc2<F>(w.N2p);
     const int n2 = kSingle ? 0 : (W + kc2 - 1) / kc2;
     const int ng = nch + n2;
     bool ok = true;
@@ -365,7 +374,7 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
         const int b = g % NBUF;
         ok = tc_wait(&S.mbar[b], S.mph[b] & 1, w.status) && ok;
         ++S.mph[b];
-        if (tid == 0 && ok && g + NBUF < ng && !S.b_pending[b]) tc_load_chunk<W, P>(w, sB0, S, g + NBUF, nch, kc2);
+        if (tid == 0 && ok && g + NBUF < ng && !S.b_pending[b]) tc_load_chunk<W, F, P>(w, sB0, S, g + NBUF, nch, kc2);
     };
     constexpr int CSTEP = 32 * (TC_T / 128);
     const int lrow = (warp & 3) * 32 + lane;
@@ -507,12 +516,12 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
 
 // Set-up of a CTA that runs tensor-core MLP tiles: barrier init (thread 0) and the tensor-memory
 // allocation (warp 0); tc_cta_teardown waits for weight copies still in flight and frees it.
-template <int P>
+template <bool F, int P>
 __device__ __forceinline__ void tc_cta_init(TcTileState& S, unsigned long long* mbar, unsigned long long* bbar) {
-    constexpr int NBUF = tc_nbuf<P>();
+    constexpr int NBUF = tc_nbuf<F, P>();
     S.mbar = mbar;
     S.bbar = bbar;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < TC_NBUF_MAX; ++b) {
         S.mph[b] = 0;
         S.bphase[b] = 0;
         S.b_pending[b] = false;
@@ -534,9 +543,9 @@ __device__ __forceinline__ void tc_tmem_alloc(unsigned* tmem_base) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
 }
-template <int P>
+template <bool F, int P>
 __device__ __forceinline__ void tc_cta_teardown(TcTileState& S, unsigned tmem_base) {
-    constexpr int NBUF = tc_nbuf<P>();
+    constexpr int NBUF = tc_nbuf<F, P>();
     // a bulk copy whose wait gave up may still be landing: wait (bounded) before the CTA exits
     if (threadIdx.x == 0)
 #pragma unroll
@@ -553,11 +562,12 @@ template <int W, class Op, int P>
 __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ RowCtx rc[TC_M];
-    __shared__ __align__(8) unsigned long long mbar[tc_nbuf<P>()];   // MMA completion per buffer (tcgen05.commit)
-    __shared__ __align__(8) unsigned long long bbar[tc_nbuf<P>()];   // B chunk arrival (bulk-copy bytes)
+    constexpr bool F = (Op::kMode == 0);
+    __shared__ __align__(8) unsigned long long mbar[tc_nbuf<F, P>()];   // MMA completion per buffer (tcgen05.commit)
+    __shared__ __align__(8) unsigned long long bbar[tc_nbuf<F, P>()];   // B chunk arrival (bulk-copy bytes)
     __shared__ unsigned tmem_base;
     TcTileState S;
-    tc_cta_init<P>(S, mbar, bbar);
+    tc_cta_init<F, P>(S, mbar, bbar);
     const long row0 = (long)blockIdx.x * TC_M;
     const long rows = op.rows;
     if (threadIdx.x == 0) tc_tile_prefetch<W, Op, P>(w, tsm, S);      // first chunks, under the prologue
@@ -574,7 +584,7 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     // the start, so that early CTAs of the next kernel do not hold SMs for this kernel's
     // whole duration when many instances run side by side)
     pdl_launch_dependents();
-    tc_cta_teardown<P>(S, tmem_base);
+    tc_cta_teardown<F, P>(S, tmem_base);
 }
 
 }  // namespace gmi
