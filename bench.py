@@ -21,6 +21,7 @@ same states beside it.
                   [--form mixed|bf16|fp32] [--no-graph] [--no-plain] [--workload chain1000|chain10]
   python bench.py --compare ipm       # ADMM against the interior-point solve on the step's QP
   python bench.py --compare barrier   # obstacles as QP rows against obstacles as barrier costs
+  python bench.py --compare matrix-free  # cost estimate of forward-mode (matrix-free) condensing
 
 The two comparisons print their own JSON line (not the metric line above).
 
@@ -65,8 +66,11 @@ def parse(argv=None):
     p.add_argument("--workload", default="chain1000", choices=["chain1000", "chain200", "chain10"],
                    help="chain200: the chain-of-1000 configuration on 200 nodes (a small case for "
                         "counter captures of the same kernels)")
+    p.add_argument("--condensing", default="jacobian", choices=["jacobian", "matrix-free"],
+                   help="jacobian: local Jacobians by the reverse pass and the Thm. 1 recursion; matrix-free: "
+                        "forward-mode sensitivities (gm_settings.condensing = 1)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--compare", default=None, choices=["ipm", "barrier"],
+    p.add_argument("--compare", default=None, choices=["ipm", "barrier", "matrix-free"],
                    help="ipm: gm_qp_solve against gm_qp_solve_ipm on the chain-of-1000 step's QP; barrier: "
                         "sphere rows as constraints against relaxed log barriers, spheres far and near")
     p.add_argument("--reps", type=int, default=5, help="--compare ipm: timed solves (median)")
@@ -372,7 +376,8 @@ def run_ours(args):
     precs = {"fp32": gm.GM_PREC_FP32, "mixed": gm.GM_PREC_MIXED, "bf16": gm.GM_PREC_BF16}
     graph = not args.no_graph
     warm = not args.no_warm
-    prob = gm.RTIProblem.from_workload(wl, precision=precs[args.form], graph=graph, warm=warm)
+    cond = 1 if args.condensing == "matrix-free" else 0
+    prob = gm.RTIProblem.from_workload(wl, precision=precs[args.form], graph=graph, warm=warm, condensing=cond)
     stream = torch.cuda.current_stream()
     U = prob.empty(prob.nU)
     warmup = max(args.warmup, 3)
@@ -453,7 +458,7 @@ def run_ours(args):
     if warm:
         del prob
         torch.cuda.empty_cache()
-        pc = gm.RTIProblem.from_workload(wl, precision=precs[args.form], graph=graph, warm=False)
+        pc = gm.RTIProblem.from_workload(wl, precision=precs[args.form], graph=graph, warm=False, condensing=cond)
         pc.reset()
         for i in range(warmup):
             pc.step(X[i], U)
@@ -528,6 +533,7 @@ def run_ours(args):
            "dtype": {"fp32": "f32", "mixed": "bf16x3/f32", "bf16": "bf16/f32"}[args.form] + " (f64 Cholesky, KKT)",
            "data": "synthetic (seeded)",
            "config": config_of(wl, args.form, {
+               "condensing": args.condensing,
                "graph_replay": bool(replayed), "graph_captures": captures,
                "admm_warm_start": "shifted previous U*, y* (receding horizon)" if warm else "cold",
                "states": f"closed-loop trajectory: {n_states} distinct measured states, the GNN as the plant "
@@ -649,6 +655,125 @@ def compare_barrier(args):
     print(json.dumps(rep), flush=True)
 
 
+def tangent_row_counts(wl):
+    """MLP rows of a forward-mode (matrix-free) condensing pass restricted to non-zero tangents:
+    for every stage k, input column (i <= k, a) and layer l = 0..K, the nodes within
+    K (k - i) + l hops of actuator a along the edges and the edges with an endpoint among them."""
+    import collections
+
+    import numpy as np
+    out = collections.defaultdict(list)
+    for s_, d_ in zip(wl.src, wl.dst):
+        out[int(s_)].append(int(d_))
+    src, dst = np.asarray(wl.src), np.asarray(wl.dst)
+    nodes = edges = 0
+    for a in range(wl.nu):
+        hop = np.full(wl.M, 1 << 30)
+        hop[int(wl.act_node[a])] = 0
+        q = collections.deque([int(wl.act_node[a])])
+        while q:
+            v = q.popleft()
+            for w in out[v]:
+                if hop[w] > hop[v] + 1:
+                    hop[w] = hop[v] + 1
+                    q.append(w)
+        for k in range(wl.N):
+            for i in range(k + 1):
+                for layer in range(wl.K + 1):
+                    r = wl.K * (k - i) + layer
+                    nodes += int((hop <= r).sum())
+                    edges += int(((hop[src] <= r) | (hop[dst] <= r)).sum())
+    return nodes, edges
+
+
+def reverse_row_counts(wl):
+    """MLP rows of the reverse pass over cones: 3 channels x N stages x (the (seed, node) pairs
+    within r hops upstream for r = 0..K, and the edges into the nodes of levels 0..K-1)."""
+    import collections
+
+    import numpy as np
+    inn = collections.defaultdict(list)
+    for s_, d_ in zip(wl.src, wl.dst):
+        inn[int(d_)].append(int(s_))
+    indeg = np.bincount(np.asarray(wl.dst), minlength=wl.M)
+    nodes = edges = 0
+    for s0 in range(wl.M):
+        hop = {s0: 0}
+        q = collections.deque([s0])
+        while q:
+            v = q.popleft()
+            if hop[v] == wl.K:
+                continue
+            for w in inn[v]:
+                if w not in hop:
+                    hop[w] = hop[v] + 1
+                    q.append(w)
+        h = np.array(list(hop.values()))
+        deg = np.array([indeg[n] for n in hop])
+        for r in range(wl.K + 1):
+            nodes += int((h <= r).sum())
+            if r < wl.K:
+                edges += int(deg[h <= r].sum())
+    return 3 * wl.N * nodes, 3 * wl.N * edges
+
+
+def compare_matrix_free(args):
+    """Cost of matrix-free condensing (sensitivities S_k pushed through the GNN by forward-mode
+    products, no A_k) on the chain of 1000, from measurements of this library's kernels: the
+    tangent rows it evaluates (graph counting) times the per-row time of the forward MLP kernels
+    at full occupancy (the rollout of a 16000-node chain with the same GNN, CUDA events), beside
+    the measured rollout, reverse pass and condensing of the chosen form (phase timing).  A
+    tangent row is a forward MLP row without bias and ReLU evaluation (the masks are the
+    rollout's), so the forward kernels' per-row time is its cost."""
+    import numpy as np
+    import torch
+
+    import paper_2602_17601_b300 as gm
+    from synth import paper_chain
+    wl = workload("chain1000")
+    t_nodes, t_edges = tangent_row_counts(wl)
+    big = paper_chain(M=16000, n_spheres=0)
+    pb = gm.RTIProblem.from_workload(big, precision=gm.GM_PREC_MIXED)
+    x0 = torch.as_tensor(big.x0.reshape(-1), dtype=torch.float32, device="cuda")
+    U = torch.zeros(big.N, big.nu, dtype=torch.float32, device="cuda")
+    xs = torch.empty(big.N + 1, big.M, 6, dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        gm.gm_rollout(pb.ctx, x0, U, big.N, xs)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(args.reps):
+        gm.gm_rollout(pb.ctx, x0, U, big.N, xs)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms_big = ev[0].elapsed_time(ev[1]) / args.reps
+    E_big = len(big.src)
+    f_nodes = big.N * big.M * (big.K + 2)           # node encoder, K node updates, decoder
+    f_edges = big.N * E_big * (big.K + 1)           # edge encoder, K edge updates
+    us_per_row = ms_big * 1e3 / (f_nodes + f_edges)
+    pb.close()
+    del pb
+    torch.cuda.empty_cache()
+    prob = gm.RTIProblem.from_workload(wl, precision=gm.GM_PREC_MIXED)
+    gm.gm_ctx_set_timing(prob.ctx, 1)
+    x = torch.as_tensor(wl.x0.reshape(-1), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        prob.step(x)
+    torch.cuda.synchronize()
+    phase, n = gm.gm_ctx_phase_ms(prob.ctx)
+    r_nodes, r_edges = reverse_row_counts(wl)
+    est = us_per_row * (t_nodes + t_edges) / 1e3
+    print(json.dumps({
+        "compare": "matrix-free", "workload": "chain1000_K3_W128_N20_nu8",
+        "tangent_rows": {"node": t_nodes, "edge": t_edges},
+        "reverse_rows": {"node": r_nodes, "edge": r_edges},
+        "forward_kernels_at_full_occupancy": {"workload": "chain16000_K3_W128_N20_nu8 rollout", "ms": ms_big,
+                                              "mlp_rows": f_nodes + f_edges, "us_per_row": us_per_row},
+        "tangent_pass_ms_estimate": est,
+        "chosen_form_phase_ms": {k: v / max(n, 1) for k, v in phase.items()},
+        "device": torch.cuda.get_device_name()}), flush=True)
+
+
 def main():
     args = parse()
     if args.time_oracle_step:
@@ -658,6 +783,8 @@ def main():
         compare_ipm(args)
     elif args.compare == "barrier":
         compare_barrier(args)
+    elif args.compare == "matrix-free":
+        compare_matrix_free(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -140,6 +140,13 @@ void gm_gnn_destroy(gm_gnn* m);
  *                rolled out, beside the rollout of the later stages (with at
  *                most SMs - ceil(E/128) CTAs per persistent reverse launch until
  *                the rollout ends)
+ *   condensing   0: local Jacobians A_k, B_k, c_k by the reverse pass and the
+ *                recursion of Thm. 1 (Eq. sparse_gamma_i_u); 1: matrix-free: the
+ *                sensitivities d x_k / d U pushed through the GNN by forward-mode
+ *                products, one tangent per input column on its support (the
+ *                nodes the column's actuator reaches in K (k - i) edges), no A_k
+ *                formed; the same H, g, C~, d~ up to rounding.  Used by
+ *                gm_rti_step and gm_condense_matrix_free.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N;
@@ -155,6 +162,7 @@ typedef struct {
     int admm_grid;
     int factor_grid;
     int chunk_mb;
+    int condensing;
 } gm_settings;
 
 /* Per-solve statistics, written to DEVICE memory by the QP calls. */
@@ -263,6 +271,22 @@ typedef struct {
 gm_status gm_condense(gm_ctx* ctx, const float* x_hat, const float* A, const float* B,
                       const float* c, const gm_cost* cost, const gm_constr* cons,
                       float* H, float* g, float* Ct, float* dt, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gm_condense_matrix_free — the condensed QP of gm_condense without local
+ * Jacobians (needs a context created with gm_settings.condensing = 1): the
+ * rollout x_hat from x0 along u_hat (Eq. forward_dynamics), then the
+ * sensitivities Gamma_u = d x / d U by forward-mode products through the GNN
+ * at the rollout, one tangent per input column restricted to the nodes its
+ * actuator reaches (the product A_k S_k + B_k E_k of Eq. sparse_gamma_i_u as one
+ * directional derivative of the stage map), Gamma_x = x_hat - Gamma_u u_hat,
+ * and H, g, C~, d~ as gm_condense (spheres of cons linearised at x_hat).
+ *   x0 [M][6], u_hat [N][nu]; x_hat [N+1][M][6] (out); H, g, Ct, dt as gm_condense.
+ * GM_ERR_INVALID_ARG on a context created with condensing = 0.
+ * ---------------------------------------------------------------------- */
+gm_status gm_condense_matrix_free(gm_ctx* ctx, const float* x0, const float* u_hat, const gm_cost* cost,
+                                  const gm_constr* cons, float* x_hat, float* H, float* g, float* Ct, float* dt,
+                                  void* stream);
 
 /* ------------------------------------------------------------------------
  * gm_qp_solve — ADMM on the condensed QP (no relaxation):

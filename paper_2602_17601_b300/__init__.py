@@ -41,7 +41,8 @@ class Settings(C.Structure):
     _fields_ = [("N", C.c_int), ("n_c", C.c_int), ("precision", C.c_int), ("rho", C.c_float),
                 ("tol", C.c_float), ("max_iter", C.c_int), ("polish", C.c_int),
                 ("timeout_spins", C.c_int), ("scale_rows", C.c_int), ("adapt_rho", C.c_int),
-                ("admm_grid", C.c_int), ("factor_grid", C.c_int), ("chunk_mb", C.c_int)]
+                ("admm_grid", C.c_int), ("factor_grid", C.c_int), ("chunk_mb", C.c_int),
+                ("condensing", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -100,6 +101,8 @@ def _load():
         "gm_ctx_destroy": ([vp], None),
         "gm_jac_pattern": ([vp, C.POINTER(C.c_int), C.POINTER(i32p), C.POINTER(i32p)], C.c_int),
         "gm_linearize": ([vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "gm_condense_matrix_free": ([vp, vp, vp, C.POINTER(Cost), C.POINTER(Constr), vp, vp, vp, vp, vp, vp],
+                                    C.c_int),
         "gm_condense": ([vp, vp, vp, vp, vp, C.POINTER(Cost), C.POINTER(Constr), vp, vp, vp, vp, vp],
                         C.c_int),
         "gm_qp_solve": ([vp] * 12 + [vp], C.c_int),
@@ -152,7 +155,7 @@ def _load():
 _lib = _load()
 HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_destroy",
                     "gm_gnn_load", "gm_gnn_destroy", "gm_ctx_workspace_size", "gm_ctx_create",
-                    "gm_ctx_destroy", "gm_jac_pattern", "gm_linearize", "gm_condense",
+                    "gm_ctx_destroy", "gm_jac_pattern", "gm_linearize", "gm_condense", "gm_condense_matrix_free",
                     "gm_qp_solve", "gm_qp_solve_ipm", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
                     "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count", "gm_qp_solve_noalloc",
                     "gm_ctx_set_graph", "gm_ctx_graph_state", "gm_ctx_set_kernel_timing",
@@ -330,10 +333,11 @@ def gm_gnn_destroy(m):
 
 
 def make_settings(N, n_c=0, precision=GM_PREC_FP32, rho=0.1, tol=1e-6, max_iter=4000, polish=0,
-                  timeout_spins=0, scale_rows=1, adapt_rho=1, admm_grid=0, factor_grid=0, chunk_mb=0):
+                  timeout_spins=0, scale_rows=1, adapt_rho=1, admm_grid=0, factor_grid=0, chunk_mb=0,
+                  condensing=0):
     return Settings(int(N), int(n_c), int(precision), float(rho), float(tol), int(max_iter), int(polish),
                     int(timeout_spins), int(scale_rows), int(adapt_rho), int(admm_grid), int(factor_grid),
-                    int(chunk_mb))
+                    int(chunk_mb), int(condensing))
 
 
 def gm_ctx_workspace_size(graph, gnn, settings):
@@ -397,6 +401,12 @@ def gm_condense(ctx, x_hat, A, B, c, cost, constr, H, g, Ct=None, dt=None, strea
     _check("gm_condense", _lib.gm_condense(ctx, _ptr(x_hat), _ptr(A), _ptr(B), _ptr(c), C.byref(cost),
                                            C.byref(constr), _ptr(H), _ptr(g), _ptr(Ct), _ptr(dt),
                                            _stream(stream)))
+
+
+def gm_condense_matrix_free(ctx, x0, u_hat, cost, constr, x_hat, H, g, Ct=None, dt=None, stream=None):
+    _check("gm_condense_matrix_free", _lib.gm_condense_matrix_free(
+        ctx, _ptr(x0), _ptr(u_hat), C.byref(cost), C.byref(constr), _ptr(x_hat), _ptr(H), _ptr(g), _ptr(Ct),
+        _ptr(dt), _stream(stream)))
 
 
 def gm_qp_solve_ipm(ctx, H, g, Ct, dt, u_lo, u_hi, U, y=None, stats=None, max_iter=60, stream=None):

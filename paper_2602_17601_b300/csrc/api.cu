@@ -35,6 +35,78 @@ static int row_of(const std::vector<int>& node, const std::vector<int>& ptr, int
     return (it != e && *it == n) ? (int)(it - node.begin()) : -1;
 }
 
+// Supports of the forward-mode sensitivity columns (matrix-free condensing, struct Tangents).
+static void build_tangents(const gm_graph& g, int K, int N, Tangents& T) {
+    const int M = g.M, E = g.E, nu = g.nu;
+    T.Rmax = K * N;
+    const int R1 = T.Rmax + 1;
+    std::vector<std::vector<int>> out(M);
+    for (int q = 0; q < E; ++q) out[g.src[q]].push_back(g.dst[q]);
+    T.norder.assign((size_t)nu * M, 0);
+    T.npos.assign((size_t)nu * M, 0);
+    T.ncnt.assign((size_t)nu * R1, 0);
+    T.eorder.assign((size_t)nu * std::max(E, 1), 0);
+    T.epos.assign((size_t)nu * std::max(E, 1), 0);
+    T.ecnt.assign((size_t)nu * R1, 0);
+    const int INF = 1 << 30;
+    std::vector<int> hop(M), ehop(std::max(E, 1)), idx;
+    for (int a = 0; a < nu; ++a) {
+        std::fill(hop.begin(), hop.end(), INF);
+        std::vector<int> q{g.act_node[a]};
+        hop[g.act_node[a]] = 0;
+        for (size_t h = 0; h < q.size(); ++h)
+            for (int w : out[q[h]])
+                if (hop[w] == INF) {
+                    hop[w] = hop[q[h]] + 1;
+                    q.push_back(w);
+                }
+        idx.resize(M);
+        for (int n = 0; n < M; ++n) idx[n] = n;
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return hop[x] < hop[y]; });
+        for (int p = 0; p < M; ++p) {
+            T.norder[(size_t)a * M + p] = idx[p];
+            T.npos[(size_t)a * M + idx[p]] = p;
+        }
+        for (int n = 0; n < M; ++n)
+            if (hop[n] <= T.Rmax) T.ncnt[(size_t)a * R1 + hop[n]]++;
+        for (int R = 1; R < R1; ++R) T.ncnt[(size_t)a * R1 + R] += T.ncnt[(size_t)a * R1 + R - 1];
+        if (E > 0) {
+            for (int q2 = 0; q2 < E; ++q2) ehop[q2] = std::min(hop[g.src[q2]], hop[g.dst[q2]]);
+            idx.resize(E);
+            for (int q2 = 0; q2 < E; ++q2) idx[q2] = q2;
+            std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return ehop[x] < ehop[y]; });
+            for (int p = 0; p < E; ++p) {
+                T.eorder[(size_t)a * E + p] = idx[p];
+                T.epos[(size_t)a * E + idx[p]] = p;
+            }
+            for (int q2 = 0; q2 < E; ++q2)
+                if (ehop[q2] <= T.Rmax) T.ecnt[(size_t)a * R1 + ehop[q2]]++;
+            for (int R = 1; R < R1; ++R) T.ecnt[(size_t)a * R1 + R] += T.ecnt[(size_t)a * R1 + R - 1];
+        }
+    }
+    const int L = N * nu + 1;
+    T.noff.assign((size_t)N * (K + 1) * L, 0);
+    T.eoff.assign((size_t)N * (K + 1) * L, 0);
+    T.max_nrows = T.max_erows = 0;
+    for (int k = 0; k < N; ++k)
+        for (int l = 0; l <= K; ++l) {
+            const size_t base = (size_t)(k * (K + 1) + l) * L;
+            long on = 0, oe = 0;
+            for (int t = 0; t < (k + 1) * nu; ++t) {
+                const int i = t / nu, a = t % nu, r0 = K * (k - i);
+                T.noff[base + t] = (int)on;
+                T.eoff[base + t] = (int)oe;
+                on += T.ncnt[(size_t)a * R1 + std::min(r0 + l, T.Rmax)];
+                const int Re = l == 0 ? (i < k ? r0 : -1) : r0 + l - 1;
+                if (Re >= 0 && E > 0) oe += T.ecnt[(size_t)a * R1 + std::min(Re, T.Rmax)];
+            }
+            T.noff[base + (k + 1) * nu] = (int)on;
+            T.eoff[base + (k + 1) * nu] = (int)oe;
+            T.max_nrows = std::max(T.max_nrows, on);
+            T.max_erows = std::max(T.max_erows, oe);
+        }
+}
+
 static void build_cones(const gm_graph& g, int K, Cones& C) {
     const int M = g.M;
     C.K = K;
@@ -358,6 +430,22 @@ static void plan(gm_ctx* c, Carver& cv) {
     c->d_stats = cv.take<gm_stats>(1);
     c->d_ipm_rows = cv.take<double>((size_t)kIpmRowArrays * std::max(1L, c->rows_c));
     c->d_ipm_vec = cv.take<double>((size_t)kIpmVecArrays * nU + kIpmScalars);
+    if (c->s.condensing == 1) {
+        const Tangents& Tn = c->tan;
+        c->dtan.norder = cv.take<int>(Tn.norder.size());
+        c->dtan.npos = cv.take<int>(Tn.npos.size());
+        c->dtan.ncnt = cv.take<int>(Tn.ncnt.size());
+        c->dtan.eorder = cv.take<int>(Tn.eorder.size());
+        c->dtan.epos = cv.take<int>(Tn.epos.size());
+        c->dtan.ecnt = cv.take<int>(Tn.ecnt.size());
+        c->dtan.noff = cv.take<int>(Tn.noff.size());
+        c->dtan.eoff = cv.take<int>(Tn.eoff.size());
+        c->d_thA = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
+        c->d_thB = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
+        c->d_tagg = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
+        c->d_teA = cv.take<float>((size_t)std::max(1L, Tn.max_erows) * W);
+        c->d_teB = cv.take<float>((size_t)std::max(1L, Tn.max_erows) * W);
+    }
 }
 
 }  // namespace gmi
@@ -435,6 +523,7 @@ static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* 
     GM_CHECK_ARG(s->admm_grid >= 0 && s->factor_grid >= 0 && s->chunk_mb >= 0,
                  "admm_grid, factor_grid and chunk_mb must be >= 0");
     GM_CHECK_ARG((long)s->N * g->nu <= 256, "N * nu must be <= 256 (got %d)", s->N * g->nu);
+    GM_CHECK_ARG(s->condensing == 0 || s->condensing == 1, "condensing must be 0 or 1 (got %d)", s->condensing);
     c->s = *s;
     c->M = g->M; c->E = g->E; c->nu = g->nu; c->K = m->d.K; c->W = m->d.W; c->N = s->N;
     c->nU = s->N * g->nu; c->n_c = s->n_c; c->dt = m->d.dt;
@@ -461,6 +550,11 @@ static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* 
     c->jac_col = c->cones.nr_node[c->K];
     c->nnzb = (int)c->jac_col.size();
     build_weights(*m, g->nu, c->wts_host, c->mlp, c->wbp_host);
+    if (s->condensing == 1) {
+        build_tangents(*g, c->K, c->N, c->tan);
+        GM_CHECK_ARG(c->tan.max_nrows < (1L << 31) && c->tan.max_erows < (1L << 31),
+                     "too many tangent rows for matrix-free condensing");
+    }
     return GM_OK;
 }
 
@@ -569,6 +663,17 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
     rs.push_back(up(c->dc.enc_dst_list, C.enc_dst_list, st));
     rs.push_back(up(c->dc.nr_ptr_K, C.nr_ptr[K], st));
     rs.push_back(up(c->dc.b_row, C.b_row, st));
+    if (c->s.condensing == 1) {
+        const Tangents& Tn = c->tan;
+        rs.push_back(up(c->dtan.norder, Tn.norder, st));
+        rs.push_back(up(c->dtan.npos, Tn.npos, st));
+        rs.push_back(up(c->dtan.ncnt, Tn.ncnt, st));
+        rs.push_back(up(c->dtan.eorder, Tn.eorder, st));
+        rs.push_back(up(c->dtan.epos, Tn.epos, st));
+        rs.push_back(up(c->dtan.ecnt, Tn.ecnt, st));
+        rs.push_back(up(c->dtan.noff, Tn.noff, st));
+        rs.push_back(up(c->dtan.eoff, Tn.eoff, st));
+    }
     // ADMM: co-resident CTAs (cooperative launch); the row split is made on the device per solve
     {
         int occ = 0;
@@ -753,6 +858,27 @@ gm_status gm_condense(gm_ctx* ctx, const float* x_hat, const float* A, const flo
     return condense(ctx, x_hat, A, B, c, cost, Cx, dx, H, g, Ct, dt, st);
 }
 
+gm_status gm_condense_matrix_free(gm_ctx* ctx, const float* x0, const float* u_hat, const gm_cost* cost,
+                                  const gm_constr* cons, float* x_hat, float* H, float* g, float* Ct, float* dt,
+                                  void* stream) {
+    clear_error();
+    GM_CHECK_ARG(ctx && x0 && u_hat && x_hat && H && g, "NULL argument");
+    GM_CHECK_ARG(ctx->s.condensing == 1, "the context was created with condensing = 0");
+    GM_TRY(check_cost(ctx, cost, cons));
+    GM_CHECK_ARG(ctx->n_c == 0 || (Ct && dt), "Ct/dt are NULL with n_c = %d", ctx->n_c);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GM_TRY(gnn_rollout(ctx, x0, u_hat, x_hat, st));
+    GM_TRY(gnn_sensitivities(ctx, u_hat, st));
+    const float* Cx = cons->Cx;
+    const float* dx = cons->dx;
+    if (cons->n_spheres > 0) {
+        GM_TRY(sphere_halfspaces(ctx, x_hat, cons->spheres, cons->n_spheres, ctx->d_Cx, ctx->d_dx, st));
+        Cx = ctx->d_Cx;
+        dx = ctx->d_dx;
+    }
+    return condense_tail(ctx, x_hat, cost, Cx, dx, H, g, Ct, dt, st);
+}
+
 gm_status gm_qp_solve(gm_ctx* ctx, const float* H, const float* g, const float* Ct, const float* dt,
                       const float* u_lo, const float* u_hi, const float* warm_U, const float* warm_y,
                       float* U, float* y, gm_stats* stats, void* stream) {
@@ -772,7 +898,13 @@ static gm_status rti_pre(gm_ctx* c, const float* x_meas, const gm_cost* cost, co
     if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[0], st));
     GM_CUDA_TRY(cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), st));
     c->kev_n = 0;
-    if (ev) {   // phase timing: the rollout and the reverse pass one after the other
+    const bool mf = c->s.condensing == 1;
+    if (mf) {   // matrix-free: the rollout, then the sensitivities by forward-mode products
+        GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
+        if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[1], st));
+        GM_TRY(gnn_sensitivities(c, c->d_u_hat, st));
+        if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[2], st));
+    } else if (ev) {   // phase timing: the rollout and the reverse pass one after the other
         GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
         GM_CUDA_TRY(cudaEventRecord((*ev)[1], st));
         GM_TRY(gnn_jacobians(c, c->d_x_hat, c->d_u_hat, c->d_A, c->d_B, c->d_c, st));
@@ -787,7 +919,8 @@ static gm_status rti_pre(gm_ctx* c, const float* x_meas, const gm_cost* cost, co
         Cx = c->d_Cx;
         dx = c->d_dx;
     }
-    GM_TRY(condense(c, c->d_x_hat, c->d_A, c->d_B, c->d_c, cost, Cx, dx, c->d_H, c->d_g, c->d_Ct, c->d_dt, st));
+    if (mf) GM_TRY(condense_tail(c, c->d_x_hat, cost, Cx, dx, c->d_H, c->d_g, c->d_Ct, c->d_dt, st));
+    else GM_TRY(condense(c, c->d_x_hat, c->d_A, c->d_B, c->d_c, cost, Cx, dx, c->d_H, c->d_g, c->d_Ct, c->d_dt, st));
     // barrier variant: the state rows go into the cost, the QP keeps the box
     const bool barrier = cons->barrier_mu > 0.f && c->n_c > 0;
     if (barrier)

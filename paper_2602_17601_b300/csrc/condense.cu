@@ -46,9 +46,6 @@ gm_status sphere_halfspaces(gm_ctx* c, const float* x_hat, const float* spheres,
     return GM_OK;
 }
 
-__host__ __device__ static inline long gu_offset(int M, int nu, int k) {   // start of stage k (k >= 1)
-    return (long)M * 6 * nu * ((long)k * (k - 1) / 2);
-}
 
 // Gamma_x is kept as its offset from the rollout, D_k = Gamma_x_k - x_hat_k (D_0 = 0), which
 // follows the recursion of Eq. sparse_gamma_i_xb with c substituted:
@@ -333,6 +330,12 @@ gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B
             c->d_Gu + gu_offset(M, nu, k + 1), c->d_Gx + (long)(k + 1) * M * 6);
         GM_LAUNCH_CHECK();
     }
+    return condense_tail(c, x_hat, cost, Cx, dx, H, g, Ct, dt, st);
+}
+
+gm_status condense_tail(gm_ctx* c, const float* x_hat, const gm_cost* cost, const float* Cx, const float* dx,
+                        float* H, float* g, float* Ct, float* dt, cudaStream_t st) {
+    const int M = c->M, nu = c->nu, N = c->N;
     // Eq. H: sum of per-node local Hessians + Rbar
     GramRows R{c->d_Gu, M * 6, nu, N, cost->Qdiag, 0, 0};
     GM_TRY(gram(c, R, gram_split(c->nU, c->num_sms, kGramSplitCap, c->gram_tc), cost->Rdiag, 1.f, H, st));

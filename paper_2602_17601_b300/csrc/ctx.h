@@ -82,6 +82,27 @@ struct DCones {
     int er_count[8];
 };
 
+// Matrix-free condensing (gm_settings.condensing = 1): the supports of the forward-mode
+// sensitivity columns.  Column t = i nu + a (input a of stage i) is non-zero at stage k > i on the
+// nodes that act_node[a] reaches in K (k - i) edges, and inside stage k its tangent grows by one
+// hop per message-passing layer.  Nodes (edges) are ordered per actuator by hop distance (by the
+// smaller hop distance of their two ends), so the support of radius R is a prefix of that order.
+struct Tangents {
+    int Rmax = 0;                                  // largest radius used: K N
+    std::vector<int> norder, npos, ncnt;           // [nu][M], [nu][M], [nu][Rmax + 1]
+    std::vector<int> eorder, epos, ecnt;           // [nu][E], [nu][E], [nu][Rmax + 1]
+    // rows of each (stage k, layer l = 0..K) launch: tangent t's rows are off[t] .. off[t + 1];
+    // node layer l has radius K (k - i) + l; edge layer 0 (encoder) K (k - i) for i < k and
+    // none for i = k; edge layer l >= 1 K (k - i) + l - 1
+    std::vector<int> noff, eoff;                   // [N][K + 1][N nu + 1]
+    long max_nrows = 0, max_erows = 0;
+};
+struct DTangents {
+    int *norder = nullptr, *npos = nullptr, *ncnt = nullptr;
+    int *eorder = nullptr, *epos = nullptr, *ecnt = nullptr;
+    int *noff = nullptr, *eoff = nullptr;
+};
+
 }  // namespace gmi
 
 struct gm_ctx {
@@ -104,6 +125,7 @@ struct gm_ctx {
     std::vector<uint16_t> wbp_host[3];
     std::vector<int> jac_row_ptr, jac_col;
     gmi::Cones cones;
+    gmi::Tangents tan;           // matrix-free condensing only
     std::vector<gmi::MlpOff> mlp;   // blob order: ne, ee, (em, nm) x K, dec
     int nnzb = 0;
 
@@ -115,6 +137,9 @@ struct gm_ctx {
     float* d_wts = nullptr;
     uint16_t* d_wbp[3] = {nullptr, nullptr, nullptr};
     gmi::DCones dc{};
+    gmi::DTangents dtan{};
+    float *d_thA = nullptr, *d_thB = nullptr, *d_tagg = nullptr;   // forward-mode node tangents
+    float *d_teA = nullptr, *d_teB = nullptr;                      // forward-mode edge tangents
     // rollout
     float *d_h = nullptr, *d_e = nullptr, *d_agg = nullptr;
     float* d_yw = nullptr;       // shifted previous multipliers (ADMM warm start) [nU + rows]

@@ -1092,3 +1092,5 @@ gm_status gnn_linearize(gm_ctx* c, const float* x0, const float* u_hat, float* x
 }
 
 }  // namespace gmi
+
+#include "tangent.cuh"

@@ -84,6 +84,16 @@ gm_status sphere_halfspaces(gm_ctx* c, const float* x_hat, const float* spheres,
 gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B, const float* cvec,
                    const gm_cost* cost, const float* Cx, const float* dx, float* H, float* g,
                    float* Ct, float* dt, cudaStream_t st);
+// H, g, C~, d~ from Gamma_u (c->d_Gu) and the offset form of Gamma_x (c->d_Gx) as they stand
+gm_status condense_tail(gm_ctx* c, const float* x_hat, const gm_cost* cost, const float* Cx, const float* dx,
+                        float* H, float* g, float* Ct, float* dt, cudaStream_t st);
+// Gamma_u block row k (k >= 1) of node i, component a, column t: d_Gu[gu_offset(M, nu, k) + (i 6 + a) k nu + t]
+__host__ __device__ inline long gu_offset(int M, int nu, int k) {
+    return (long)M * 6 * nu * ((long)k * (k - 1) / 2);
+}
+// gnn.cu (matrix-free condensing): Gamma_u stages 1..N and the offset D_k = Gamma_x_k - x_hat_k
+// from forward-mode products along the rollout (its ReLU masks in c); needs gm_settings.condensing = 1
+gm_status gnn_sensitivities(gm_ctx* c, const float* u_hat, cudaStream_t st);
 
 // qp.cu
 // ev_mid (nullable) is recorded between the set-up (P, Cholesky, inverse) and the iterations;

@@ -1,0 +1,360 @@
+// Matrix-free condensing: the sensitivities S_k = d x_k / d U (the block rows of Gamma_u) pushed
+// through the GNN by forward-mode products, one tangent per input column, instead of forming the
+// local Jacobians A_k and running the recursion of Eq. sparse_gamma_i_u (Thm. 1 proof):
+//
+//   S_{k+1}[:, t] = dF/dx(x_hat_k, u_hat_k) S_k[:, t] + dF/du(x_hat_k, u_hat_k) e_t   (t in stage k)
+//
+// Each tangent runs through the stage's MLPs as their linearisation at the rollout: the same
+// weights, no biases, the hidden layer multiplied by the ReLU mask the rollout stored
+// (Eq. linearized_dynamics), and the residual connections carried.  Column t = i nu + a is zero
+// for k <= i and, for k > i, outside the nodes that act_node[a] reaches in K (k - i) edges; within
+// stage k its tangent gains one hop per message-passing layer.  The rows of a launch are, tangent
+// by tangent, the nodes (edges) of that support in the per-actuator hop order of the context's
+// tables (struct Tangents), so every gather of the previous layer is a position in that order
+// compared with the previous support's size.  Gamma_x follows from the rollout: the prediction
+// Gamma_u U + Gamma_x reproduces x_hat at U = u_hat, so D_k = Gamma_x_k - x_hat_k = -S_k u_hat.
+//
+// Included by gnn.cu (uses its launch helpers and ReLU-mask layout).
+#pragma once
+
+namespace gmi {
+
+// Row -> (tangent, position in its support) of one (stage, layer) launch.
+struct TanBase : BwdBase {
+    const int* off;          // [T + 1] row offsets of the tangents in this launch
+    int T, nu, K, k, M, E, Rmax;
+    const int *norder, *npos, *ncnt, *eorder, *epos, *ecnt;
+    const uint32_t* mlmask;  // the rollout's ReLU mask of this MLP at stage k: [units][W/32]
+    __device__ int find(long r) const {
+        int lo = 0, hi = T;                  // off[lo] <= r < off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= r) lo = mid;
+            else hi = mid;
+        }
+        return lo;
+    }
+    __device__ int node_count(int a, int R) const { return R < 0 ? 0 : ncnt[a * (Rmax + 1) + min(R, Rmax)]; }
+    __device__ int edge_count(int a, int R) const { return R < 0 ? 0 : ecnt[a * (Rmax + 1) + min(R, Rmax)]; }
+    // row of (tangent t, node n) in a node layer with offsets poff and radius R, or -1 outside
+    __device__ int node_row(const int* poff, int t, int a, int n, int R) const {
+        const int p = npos[a * M + n];
+        return p < node_count(a, R) ? poff[t] + p : -1;
+    }
+    __device__ int edge_row(const int* poff, int t, int a, int q, int R) const {
+        const int p = epos[a * E + q];
+        return p < edge_count(a, R) ? poff[t] + p : -1;
+    }
+    __device__ uint32_t mask_word(const RowCtx& x, int wd) const { return mlmask[(long)x.d * wwords + wd]; }
+};
+
+// Node encoder: input [dx (6) | m u (nu)] of node n: dx = S_k[n][:, t] (i < k), du = e_a at
+// act_node[a] (i = k).  RowCtx: a row, b node, c tangent, d node (mask), e 1 if i < k, f the input
+// index 6 + a carrying the unit tangent at the actuated node (i = k), else -1.
+struct NodeEncTan : TanBase {
+    const float* Sk;         // Gamma_u block row k (k >= 1), row length L = k nu
+    const int* act;
+    float* th;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, -1};
+        if (r < 0) return x;
+        const int t = find(r), i = t / nu, a = t % nu;
+        const int n = norder[a * M + (int)(r - off[t])];
+        x.a = (int)r; x.b = n; x.c = t; x.d = n;
+        x.e = i < k ? 1 : 0;
+        x.f = (i == k && act[a] == n) ? 6 + a : -1;
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int kk) const {
+        if (kk < 6) return x.e ? Sk[((long)x.b * 6 + kk) * (k * nu) + x.c] : 0.f;
+        return kk == x.f ? 1.f : 0.f;
+    }
+    __device__ void out(const RowCtx& x, int n, float v) const { th[(long)x.a * W + n] = v; }
+    static constexpr bool kHasOut4 = true;
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(th + (long)x.a * W + n, v); }
+};
+
+// Edge encoder (edges j -> i, input x_i - x_j): rows only for tangents with i < k.
+// RowCtx: a row, b dst, c src, d edge (mask), e tangent.
+struct EdgeEncTan : TanBase {
+    const float* Sk;
+    const int *src, *dst;
+    float* te;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, 0};
+        if (r < 0) return x;
+        const int t = find(r), a = t % nu;
+        const int q = eorder[a * E + (int)(r - off[t])];
+        x.a = (int)r; x.b = dst[q]; x.c = src[q]; x.d = q; x.e = t;
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int kk) const {
+        if (kk >= 6) return 0.f;
+        const long L = (long)k * nu;
+        return Sk[((long)x.b * 6 + kk) * L + x.e] - Sk[((long)x.c * 6 + kk) * L + x.e];
+    }
+    __device__ void out(const RowCtx& x, int n, float v) const { te[(long)x.a * W + n] = v; }
+    static constexpr bool kHasOut4 = true;
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(te + (long)x.a * W + n, v); }
+};
+
+// Edge update of layer l: te_l = te_{l-1} + J [th_{l-1}(dst) | th_{l-1}(src) | te_{l-1}].
+// RowCtx: a row, b th row of dst, c th row of src, d edge (mask), e te row of the edge (-1: 0).
+struct EdgeMpTan : TanBase {
+    const int *src, *dst;
+    const int *noff_prev, *eoff_prev;   // offsets of the node layer l - 1 and the edge layer l - 1
+    int Rn_prev_base, Re_prev_base;     // radius of those layers minus K (k - i)
+    const float *th_prev, *te_prev;
+    float* te;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, -1, -1, 0, -1, 0};
+        if (r < 0) return x;
+        const int t = find(r), i = t / nu, a = t % nu;
+        const int q = eorder[a * E + (int)(r - off[t])];
+        const int r0 = K * (k - i);
+        x.a = (int)r; x.d = q;
+        x.b = node_row(noff_prev, t, a, dst[q], r0 + Rn_prev_base);
+        x.c = node_row(noff_prev, t, a, src[q], r0 + Rn_prev_base);
+        // the edge encoder has no rows for the tangents of stage k (their x tangent is zero)
+        const int Re = (Re_prev_base < 0 && i == k) ? -1 : r0 + (Re_prev_base < 0 ? 0 : Re_prev_base);
+        x.e = edge_row(eoff_prev, t, a, q, Re);
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int kk) const {
+        if (kk < W) return x.b >= 0 ? th_prev[(long)x.b * W + kk] : 0.f;
+        if (kk < 2 * W) return x.c >= 0 ? th_prev[(long)x.c * W + kk - W] : 0.f;
+        return x.e >= 0 ? te_prev[(long)x.e * W + kk - 2 * W] : 0.f;
+    }
+    __device__ void out(const RowCtx& x, int n, float v) const {
+        te[(long)x.a * W + n] = (x.e >= 0 ? te_prev[(long)x.e * W + n] : 0.f) + v;
+    }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true, kHasResid = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const {
+        const int row = k0 < W ? x.b : (k0 < 2 * W ? x.c : x.e);
+        const float* base = k0 < 2 * W ? th_prev : te_prev;
+        if (row >= 0) {
+            ld8(base + (long)row * W + (k0 % W), v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        }
+    }
+    __device__ float4 resid4(const RowCtx& x, int n) const {
+        return x.e >= 0 ? ld4(te_prev + (long)x.e * W + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(te + (long)x.a * W + n, v); }
+};
+
+// Node update of layer l: th_l = th_{l-1} + J [th_{l-1} | tagg_l].  RowCtx: a row (also the
+// row of tagg_l, same layer), b th row of the node in layer l - 1 (-1: 0), d node (mask).
+struct NodeMpTan : TanBase {
+    const int* noff_prev;
+    int Rn_prev_base;
+    const float *th_prev, *tagg;
+    float* th;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, -1, 0, 0, 0, 0};
+        if (r < 0) return x;
+        const int t = find(r), i = t / nu, a = t % nu;
+        const int n = norder[a * M + (int)(r - off[t])];
+        x.a = (int)r; x.d = n;
+        x.b = node_row(noff_prev, t, a, n, K * (k - i) + Rn_prev_base);
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int kk) const {
+        if (kk < W) return x.b >= 0 ? th_prev[(long)x.b * W + kk] : 0.f;
+        return tagg[(long)x.a * W + kk - W];
+    }
+    __device__ void out(const RowCtx& x, int n, float v) const {
+        th[(long)x.a * W + n] = (x.b >= 0 ? th_prev[(long)x.b * W + n] : 0.f) + v;
+    }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true, kHasResid = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const {
+        if (k0 >= W) {
+            ld8(tagg + (long)x.a * W + k0 - W, v);
+        } else if (x.b >= 0) {
+            ld8(th_prev + (long)x.b * W + k0, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        }
+    }
+    __device__ float4 resid4(const RowCtx& x, int n) const {
+        return x.b >= 0 ? ld4(th_prev + (long)x.b * W + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(th + (long)x.a * W + n, v); }
+};
+
+// Decoder and Euler update (semi-implicit, Eq. forward_dynamics): dv' = J th_K, v' = dv_x + dv',
+// p' = dp_x + dt v', written to Gamma_u block row k + 1.  RowCtx: a row, b node, c tangent,
+// d node (mask), e 1 if i < k (the tangent has an x part).
+struct DecTan : TanBase {
+    const float* Sk;         // block row k (k >= 1), row length k nu
+    float* Sk1;              // block row k + 1, row length (k + 1) nu
+    const float* th;
+    float dt;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, 0, 0, 0, 0, 0};
+        if (r < 0) return x;
+        const int t = find(r), i = t / nu, a = t % nu;
+        const int n = norder[a * M + (int)(r - off[t])];
+        x.a = (int)r; x.b = n; x.c = t; x.d = n; x.e = i < k ? 1 : 0;
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int kk) const { return th[(long)x.a * W + kk]; }
+    static constexpr bool kHasIn8 = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(th + (long)x.a * W + k0, v); }
+    __device__ void out(const RowCtx& x, int n, float dv) const {
+        const long L = (long)k * nu, L1 = (long)(k + 1) * nu;
+        const float vx = x.e ? Sk[((long)x.b * 6 + 3 + n) * L + x.c] : 0.f;
+        const float px = x.e ? Sk[((long)x.b * 6 + n) * L + x.c] : 0.f;
+        const float v1 = vx + dv;
+        Sk1[((long)x.b * 6 + 3 + n) * L1 + x.c] = v1;
+        Sk1[((long)x.b * 6 + n) * L1 + x.c] = px + dt * v1;
+    }
+};
+
+// Message sum of layer l for every node row (tangent t, node n): sum over the edges into n that
+// lie in the edge layer's support.  One warp per row, four columns per lane.
+__global__ void tan_agg_kernel(long rows, int T, int nu, int K, int k, int M, int E, int Rmax, int W,
+                               const int* __restrict__ noff, const int* __restrict__ eoff, int Re_base,
+                               const int* __restrict__ norder, const int* __restrict__ epos,
+                               const int* __restrict__ ecnt, const int* __restrict__ in_ptr,
+                               const float* __restrict__ te, float* __restrict__ tagg) {
+    const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    int lo = 0, hi = T;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (noff[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    const int t = lo, i = t / nu, a = t % nu;
+    const int n = norder[a * M + (int)(r - noff[t])];
+    const int R = K * (k - i) + Re_base;
+    const int cnt = ecnt[a * (Rmax + 1) + min(R, Rmax)];
+    for (int c0 = lane * 4; c0 < W; c0 += 128) {
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = in_ptr[n]; q < in_ptr[n + 1]; ++q) {
+            const int p = epos[a * E + q];
+            if (p < cnt) s = add4(s, ld4(te + ((long)eoff[t] + p) * W + c0));
+        }
+        st4(tagg + r * W + c0, s);
+    }
+}
+
+// D_k = Gamma_x_k - x_hat_k = -S_k u_hat for k = 1..N (D_0 = 0), one warp per (k, node, component).
+__global__ void tan_offset_kernel(int N, int M, int nu, const float* __restrict__ Gu,
+                                  const float* __restrict__ u_hat, float* __restrict__ D) {
+    const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (long)N * M * 6) return;
+    const int k = (int)(w / ((long)M * 6)) + 1;
+    const long ia = w % ((long)M * 6);
+    const int L = k * nu;
+    const float* row = Gu + gu_offset(M, nu, k) + ia * L;
+    float s = 0.f;
+    for (int t = lane; t < L; t += 32) s = fmaf(row[t], u_hat[t], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) D[(long)k * M * 6 + ia] = -s;
+}
+
+template <class Op>
+static void fill_tan(Op& op, const gm_ctx* c, const MlpOff& m, int k, int layer_off, bool edge, const uint32_t* mask) {
+    const Tangents& T = c->tan;
+    const int L = c->N * c->nu + 1;
+    const int* offs = edge ? c->dtan.eoff : c->dtan.noff;
+    op.off = offs + (long)(k * (c->K + 1) + layer_off) * L;
+    const std::vector<int>& hoff = edge ? T.eoff : T.noff;
+    const int Tk = (k + 1) * c->nu;
+    op.rows = hoff[(size_t)(k * (c->K + 1) + layer_off) * L + Tk];
+    op.T = Tk; op.nu = c->nu; op.K = c->K; op.k = k; op.M = c->M; op.E = c->E; op.Rmax = T.Rmax;
+    op.norder = c->dtan.norder; op.npos = c->dtan.npos; op.ncnt = c->dtan.ncnt;
+    op.eorder = c->dtan.eorder; op.epos = c->dtan.epos; op.ecnt = c->dtan.ecnt;
+    op.kin = m.in;
+    op.nout = m.out;
+    op.B1 = c->d_wts + m.W1;          // the forward orientation: the tangent map is the linearised forward MLP
+    op.B2 = c->d_wts + m.W2;
+    op.mlmask = mask;
+    op.wwords = c->W / 32;
+    op.W = c->W;
+    op.R = 0;
+}
+
+static long tan_rows(const gm_ctx* c, int k, int layer, bool edge) {
+    const int L = c->N * c->nu + 1;
+    const std::vector<int>& hoff = edge ? c->tan.eoff : c->tan.noff;
+    return hoff[(size_t)(k * (c->K + 1) + layer) * L + (k + 1) * c->nu];
+}
+
+gm_status gnn_sensitivities(gm_ctx* c, const float* u_hat, cudaStream_t st) {
+    if (c->s.condensing != 1 || !c->dtan.noff) {
+        set_error("matrix-free condensing needs a context created with gm_settings.condensing = 1");
+        return GM_ERR_INVALID_ARG;
+    }
+    const int M = c->M, K = c->K, N = c->N, nu = c->nu, W = c->W;
+    const int L = N * nu + 1;
+    float* th[2] = {c->d_thA, c->d_thB};
+    float* te[2] = {c->d_teA, c->d_teB};
+    for (int k = 0; k < N; ++k) {
+        const float* Sk = k > 0 ? c->d_Gu + gu_offset(M, nu, k) : nullptr;
+        float* Sk1 = c->d_Gu + gu_offset(M, nu, k + 1);
+        GM_CUDA_TRY(cudaMemsetAsync(Sk1, 0, sizeof(float) * M * 6 * (k + 1) * nu, st));
+        {   // node encoder (node layer 0)
+            NodeEncTan op{};
+            fill_tan(op, c, c->mlp[0], k, 0, false, node_mask(c, k, 0));
+            op.Sk = Sk; op.act = c->d_act; op.th = th[0];
+            GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[0]), st));
+        }
+        if (k > 0 && c->E > 0) {   // edge encoder (edge layer 0): tangents of earlier stages only
+            EdgeEncTan op{};
+            fill_tan(op, c, c->mlp[1], k, 0, true, edge_mask(c, k, 0));
+            op.Sk = Sk; op.src = c->d_src; op.dst = c->d_dst; op.te = te[0];
+            GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[1]), st));
+        }
+        for (int l = 1; l <= K; ++l) {
+            const int* noff_prev = c->dtan.noff + (long)(k * (K + 1) + l - 1) * L;
+            const int* eoff_prev = c->dtan.eoff + (long)(k * (K + 1) + l - 1) * L;
+            if (c->E > 0) {
+                EdgeMpTan em{};
+                fill_tan(em, c, c->mlp[2 + 2 * (l - 1)], k, l, true, edge_mask(c, k, l));
+                em.src = c->d_src; em.dst = c->d_dst;
+                em.noff_prev = noff_prev; em.eoff_prev = eoff_prev;
+                em.Rn_prev_base = l - 1;
+                em.Re_prev_base = l == 1 ? -1 : l - 2;   // -1: the encoder's layer (none for i = k)
+                em.th_prev = th[(l - 1) & 1]; em.te_prev = te[(l - 1) & 1]; em.te = te[l & 1];
+                GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * (l - 1)]), st));
+            }
+            const long nrows = tan_rows(c, k, l, false);
+            if (nrows > 0) {
+                if (c->E > 0) {
+                    tan_agg_kernel<<<cdiv(nrows * 32, 256), 256, 0, st>>>(
+                        nrows, (k + 1) * nu, nu, K, k, M, c->E, c->tan.Rmax, W,
+                        c->dtan.noff + (long)(k * (K + 1) + l) * L, c->dtan.eoff + (long)(k * (K + 1) + l) * L,
+                        l - 1, c->dtan.norder, c->dtan.epos, c->dtan.ecnt, c->d_in_ptr, te[l & 1], c->d_tagg);
+                    GM_LAUNCH_CHECK();
+                } else {
+                    GM_CUDA_TRY(cudaMemsetAsync(c->d_tagg, 0, sizeof(float) * nrows * W, st));
+                }
+            }
+            NodeMpTan nm{};
+            fill_tan(nm, c, c->mlp[3 + 2 * (l - 1)], k, l, false, node_mask(c, k, l));
+            nm.noff_prev = noff_prev; nm.Rn_prev_base = l - 1;
+            nm.th_prev = th[(l - 1) & 1]; nm.tagg = c->d_tagg; nm.th = th[l & 1];
+            GM_TRY(launch_mlp(c, nm, tc_fwd(c, c->mlp[3 + 2 * (l - 1)]), st));
+        }
+        DecTan de{};
+        fill_tan(de, c, c->mlp[2 + 2 * K], k, K, false, node_mask(c, k, K + 1));
+        de.Sk = Sk; de.Sk1 = Sk1; de.th = th[K & 1]; de.dt = c->dt;
+        GM_TRY(launch_mlp(c, de, tc_fwd(c, c->mlp[2 + 2 * K]), st));
+    }
+    GM_CUDA_TRY(cudaMemsetAsync(c->d_Gx, 0, sizeof(float) * M * 6, st));
+    const long warps = (long)N * M * 6;
+    tan_offset_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(N, M, nu, c->d_Gu, u_hat, c->d_Gx);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
+}  // namespace gmi

@@ -8,7 +8,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (GM_PREC_FP32, STATS_BYTES, gm_barrier_fold, gm_condense, gm_ctx_create, gm_ctx_destroy, gm_ctx_graph_state,
+from . import (GM_PREC_FP32, STATS_BYTES, gm_barrier_fold, gm_condense, gm_condense_matrix_free, gm_ctx_create,
+               gm_ctx_destroy, gm_ctx_graph_state,
                gm_ctx_set_warm,
                gm_ctx_reset, gm_ctx_set_graph, gm_ctx_workspace_size, gm_gnn_destroy, gm_gnn_load, gm_graph_create, gm_graph_destroy,
                gm_jac_pattern, gm_linearize, gm_qp_solve, gm_qp_solve_ipm, gm_rti_step, make_constr, make_cost,
@@ -24,12 +25,14 @@ class RTIProblem:
     half-spaces (Cx, dx) or spheres linearised at the rollout.  barrier = (mu, delta)
     makes step() put those rows into the cost as relaxed log barriers (gm_barrier_fold).
     warm=True starts each step's ADMM from the shifted previous solution (gm_ctx_set_warm).
+    condensing=1 builds the condensed QP matrix-free (forward-mode sensitivities, no A_k).
     """
 
     def __init__(self, M, src, dst, nu, act_node, K, W, dt, blob, N, Qdiag, Rdiag, x_ref, u_ref, u_lo,
                  u_hi, Cx=None, dx=None, spheres=None, rho=0.1, tol=1e-6, max_iter=4000,
                  precision=GM_PREC_FP32, polish=0, timeout_spins=0, scale_rows=1, adapt_rho=1,
-                 graph=False, admm_grid=0, factor_grid=0, chunk_mb=0, barrier=None, warm=False, device="cuda"):
+                 graph=False, admm_grid=0, factor_grid=0, chunk_mb=0, barrier=None, warm=False, condensing=0,
+                 device="cuda"):
         import torch
         self.torch = torch
         self.M, self.nu, self.N, self.K, self.W = int(M), int(nu), int(N), int(K), int(W)
@@ -51,7 +54,7 @@ class RTIProblem:
         self.graph = gm_graph_create(M, src, dst, nu, act_node)
         self.gnn = gm_gnn_load(K, W, nu, dt, blob)
         self.settings = make_settings(N, n_c, precision, rho, tol, max_iter, polish, timeout_spins,
-                                      scale_rows, adapt_rho, admm_grid, factor_grid, chunk_mb)
+                                      scale_rows, adapt_rho, admm_grid, factor_grid, chunk_mb, condensing)
         nbytes = gm_ctx_workspace_size(self.graph, self.gnn, self.settings)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.ctx = gm_ctx_create(self.graph, self.gnn, self.settings, self.workspace)
@@ -113,6 +116,20 @@ class RTIProblem:
         gm_condense(self.ctx, x_hat, A, B, c, self.cost, self.constr, H, g,
                     Ct if self.n_c else None, dt if self.n_c else None)
         return H, g, Ct[:self.ct_len], dt[:self.rows_c]
+
+    def condense_matrix_free(self, x0, u_hat):
+        """(x_hat, H, g, C~, d~) without local Jacobians (a context built with condensing=1)."""
+        t = self.torch
+        x0 = t.as_tensor(x0, dtype=t.float32, device=self.Qdiag.device).contiguous()
+        u_hat = t.as_tensor(u_hat, dtype=t.float32, device=self.Qdiag.device).contiguous()
+        x_hat = self.empty(self.N + 1, self.M, 6)
+        H = self.empty(self.nU, self.nU)
+        g = self.empty(self.nU)
+        Ct = self.empty(max(self.ct_len, 1))
+        dt = self.empty(max(self.rows_c, 1))
+        gm_condense_matrix_free(self.ctx, x0, u_hat, self.cost, self.constr, x_hat, H, g,
+                                Ct if self.n_c else None, dt if self.n_c else None)
+        return x_hat, H, g, Ct[:self.ct_len], dt[:self.rows_c]
 
     def qp_solve(self, H, g, Ct=None, dt=None, warm_U=None, warm_y=None, box_only=False):
         """ADMM on the condensed QP; box_only drops the half-space rows (barrier variant)."""
