@@ -637,6 +637,14 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
         }
         c->ev_stage.push_back(ev);
     }
+    for (int i = 0; c->s.condensing == 1 && i < c->N; ++i) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            set_error("event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(GM_ERR_CUDA);
+        }
+        c->ev_tan.push_back(ev);
+    }
     const Cones& C = c->cones;
     const int K = c->K;
     std::vector<gm_status> rs;
@@ -867,8 +875,7 @@ gm_status gm_condense_matrix_free(gm_ctx* ctx, const float* x0, const float* u_h
     GM_TRY(check_cost(ctx, cost, cons));
     GM_CHECK_ARG(ctx->n_c == 0 || (Ct && dt), "Ct/dt are NULL with n_c = %d", ctx->n_c);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    GM_TRY(gnn_rollout(ctx, x0, u_hat, x_hat, st));
-    GM_TRY(gnn_sensitivities(ctx, u_hat, st));
+    GM_TRY(gnn_rollout_sensitivities(ctx, x0, u_hat, x_hat, st));
     const float* Cx = cons->Cx;
     const float* dx = cons->dx;
     if (cons->n_spheres > 0) {
@@ -899,11 +906,13 @@ static gm_status rti_pre(gm_ctx* c, const float* x_meas, const gm_cost* cost, co
     GM_CUDA_TRY(cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), st));
     c->kev_n = 0;
     const bool mf = c->s.condensing == 1;
-    if (mf) {   // matrix-free: the rollout, then the sensitivities by forward-mode products
+    if (mf && ev) {   // matrix-free, phase timing: the rollout, then the sensitivities
         GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
-        if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[1], st));
+        GM_CUDA_TRY(cudaEventRecord((*ev)[1], st));
         GM_TRY(gnn_sensitivities(c, c->d_u_hat, st));
-        if (ev) GM_CUDA_TRY(cudaEventRecord((*ev)[2], st));
+        GM_CUDA_TRY(cudaEventRecord((*ev)[2], st));
+    } else if (mf) {
+        GM_TRY(gnn_rollout_sensitivities(c, x_meas, c->d_u_hat, c->d_x_hat, st));
     } else if (ev) {   // phase timing: the rollout and the reverse pass one after the other
         GM_TRY(gnn_rollout(c, x_meas, c->d_u_hat, c->d_x_hat, st));
         GM_CUDA_TRY(cudaEventRecord((*ev)[1], st));

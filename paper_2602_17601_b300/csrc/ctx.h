@@ -192,6 +192,7 @@ struct gm_ctx {
     int ws_grid = 0;             // CTAs of the persistent reverse kernels (0: one per SM)
     cudaEvent_t ev_roll = nullptr;
     std::vector<cudaEvent_t> ev_stage;
+    std::vector<cudaEvent_t> ev_tan;   // matrix-free: stage k of the rollout is done (tangent pass of k may start)
     // launch timing of the reverse edge-update MLP (events around each launch of the last step)
     bool ktiming = false;
     int kev_n = 0;
@@ -210,6 +211,7 @@ struct gm_ctx {
         if (roll_stream) cudaStreamDestroy(roll_stream);
         if (ev_roll) cudaEventDestroy(ev_roll);
         for (auto ev : ev_stage) cudaEventDestroy(ev);
+        for (auto ev : ev_tan) cudaEventDestroy(ev);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
     }

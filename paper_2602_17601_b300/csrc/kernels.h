@@ -94,6 +94,10 @@ __host__ __device__ inline long gu_offset(int M, int nu, int k) {
 // gnn.cu (matrix-free condensing): Gamma_u stages 1..N and the offset D_k = Gamma_x_k - x_hat_k
 // from forward-mode products along the rollout (its ReLU masks in c); needs gm_settings.condensing = 1
 gm_status gnn_sensitivities(gm_ctx* c, const float* u_hat, cudaStream_t st);
+// the rollout (x_hat) and the sensitivities, the tangent pass of each stage beside the rollout of
+// the later stages
+gm_status gnn_rollout_sensitivities(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat,
+                                    cudaStream_t st);
 
 // qp.cu
 // ev_mid (nullable) is recorded between the set-up (P, Cholesky, inverse) and the iterations;

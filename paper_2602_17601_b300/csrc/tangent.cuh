@@ -289,72 +289,111 @@ static long tan_rows(const gm_ctx* c, int k, int layer, bool edge) {
     return hoff[(size_t)(k * (c->K + 1) + layer) * L + (k + 1) * c->nu];
 }
 
-gm_status gnn_sensitivities(gm_ctx* c, const float* u_hat, cudaStream_t st) {
-    if (c->s.condensing != 1 || !c->dtan.noff) {
-        set_error("matrix-free condensing needs a context created with gm_settings.condensing = 1");
-        return GM_ERR_INVALID_ARG;
-    }
+// Tangent pass of stage k: S_{k+1} from S_k and the rollout's ReLU masks of stage k.
+static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
     const int M = c->M, K = c->K, N = c->N, nu = c->nu, W = c->W;
     const int L = N * nu + 1;
     float* th[2] = {c->d_thA, c->d_thB};
     float* te[2] = {c->d_teA, c->d_teB};
-    for (int k = 0; k < N; ++k) {
-        const float* Sk = k > 0 ? c->d_Gu + gu_offset(M, nu, k) : nullptr;
-        float* Sk1 = c->d_Gu + gu_offset(M, nu, k + 1);
-        GM_CUDA_TRY(cudaMemsetAsync(Sk1, 0, sizeof(float) * M * 6 * (k + 1) * nu, st));
-        {   // node encoder (node layer 0)
-            NodeEncTan op{};
-            fill_tan(op, c, c->mlp[0], k, 0, false, node_mask(c, k, 0));
-            op.Sk = Sk; op.act = c->d_act; op.th = th[0];
-            GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[0]), st));
-        }
-        if (k > 0 && c->E > 0) {   // edge encoder (edge layer 0): tangents of earlier stages only
-            EdgeEncTan op{};
-            fill_tan(op, c, c->mlp[1], k, 0, true, edge_mask(c, k, 0));
-            op.Sk = Sk; op.src = c->d_src; op.dst = c->d_dst; op.te = te[0];
-            GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[1]), st));
-        }
-        for (int l = 1; l <= K; ++l) {
-            const int* noff_prev = c->dtan.noff + (long)(k * (K + 1) + l - 1) * L;
-            const int* eoff_prev = c->dtan.eoff + (long)(k * (K + 1) + l - 1) * L;
-            if (c->E > 0) {
-                EdgeMpTan em{};
-                fill_tan(em, c, c->mlp[2 + 2 * (l - 1)], k, l, true, edge_mask(c, k, l));
-                em.src = c->d_src; em.dst = c->d_dst;
-                em.noff_prev = noff_prev; em.eoff_prev = eoff_prev;
-                em.Rn_prev_base = l - 1;
-                em.Re_prev_base = l == 1 ? -1 : l - 2;   // -1: the encoder's layer (none for i = k)
-                em.th_prev = th[(l - 1) & 1]; em.te_prev = te[(l - 1) & 1]; em.te = te[l & 1];
-                GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * (l - 1)]), st));
-            }
-            const long nrows = tan_rows(c, k, l, false);
-            if (nrows > 0) {
-                if (c->E > 0) {
-                    tan_agg_kernel<<<cdiv(nrows * 32, 256), 256, 0, st>>>(
-                        nrows, (k + 1) * nu, nu, K, k, M, c->E, c->tan.Rmax, W,
-                        c->dtan.noff + (long)(k * (K + 1) + l) * L, c->dtan.eoff + (long)(k * (K + 1) + l) * L,
-                        l - 1, c->dtan.norder, c->dtan.epos, c->dtan.ecnt, c->d_in_ptr, te[l & 1], c->d_tagg);
-                    GM_LAUNCH_CHECK();
-                } else {
-                    GM_CUDA_TRY(cudaMemsetAsync(c->d_tagg, 0, sizeof(float) * nrows * W, st));
-                }
-            }
-            NodeMpTan nm{};
-            fill_tan(nm, c, c->mlp[3 + 2 * (l - 1)], k, l, false, node_mask(c, k, l));
-            nm.noff_prev = noff_prev; nm.Rn_prev_base = l - 1;
-            nm.th_prev = th[(l - 1) & 1]; nm.tagg = c->d_tagg; nm.th = th[l & 1];
-            GM_TRY(launch_mlp(c, nm, tc_fwd(c, c->mlp[3 + 2 * (l - 1)]), st));
-        }
-        DecTan de{};
-        fill_tan(de, c, c->mlp[2 + 2 * K], k, K, false, node_mask(c, k, K + 1));
-        de.Sk = Sk; de.Sk1 = Sk1; de.th = th[K & 1]; de.dt = c->dt;
-        GM_TRY(launch_mlp(c, de, tc_fwd(c, c->mlp[2 + 2 * K]), st));
+    const float* Sk = k > 0 ? c->d_Gu + gu_offset(M, nu, k) : nullptr;
+    float* Sk1 = c->d_Gu + gu_offset(M, nu, k + 1);
+    GM_CUDA_TRY(cudaMemsetAsync(Sk1, 0, sizeof(float) * M * 6 * (k + 1) * nu, st));
+    {   // node encoder (node layer 0)
+        NodeEncTan op{};
+        fill_tan(op, c, c->mlp[0], k, 0, false, node_mask(c, k, 0));
+        op.Sk = Sk; op.act = c->d_act; op.th = th[0];
+        GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[0]), st));
     }
+    if (k > 0 && c->E > 0) {   // edge encoder (edge layer 0): tangents of earlier stages only
+        EdgeEncTan op{};
+        fill_tan(op, c, c->mlp[1], k, 0, true, edge_mask(c, k, 0));
+        op.Sk = Sk; op.src = c->d_src; op.dst = c->d_dst; op.te = te[0];
+        GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[1]), st));
+    }
+    for (int l = 1; l <= K; ++l) {
+        const int* noff_prev = c->dtan.noff + (long)(k * (K + 1) + l - 1) * L;
+        const int* eoff_prev = c->dtan.eoff + (long)(k * (K + 1) + l - 1) * L;
+        if (c->E > 0) {
+            EdgeMpTan em{};
+            fill_tan(em, c, c->mlp[2 + 2 * (l - 1)], k, l, true, edge_mask(c, k, l));
+            em.src = c->d_src; em.dst = c->d_dst;
+            em.noff_prev = noff_prev; em.eoff_prev = eoff_prev;
+            em.Rn_prev_base = l - 1;
+            em.Re_prev_base = l == 1 ? -1 : l - 2;   // -1: the encoder's layer (none for i = k)
+            em.th_prev = th[(l - 1) & 1]; em.te_prev = te[(l - 1) & 1]; em.te = te[l & 1];
+            GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * (l - 1)]), st));
+        }
+        const long nrows = tan_rows(c, k, l, false);
+        if (nrows > 0) {
+            if (c->E > 0) {
+                tan_agg_kernel<<<cdiv(nrows * 32, 256), 256, 0, st>>>(
+                    nrows, (k + 1) * nu, nu, K, k, M, c->E, c->tan.Rmax, W,
+                    c->dtan.noff + (long)(k * (K + 1) + l) * L, c->dtan.eoff + (long)(k * (K + 1) + l) * L,
+                    l - 1, c->dtan.norder, c->dtan.epos, c->dtan.ecnt, c->d_in_ptr, te[l & 1], c->d_tagg);
+                GM_LAUNCH_CHECK();
+            } else {
+                GM_CUDA_TRY(cudaMemsetAsync(c->d_tagg, 0, sizeof(float) * nrows * W, st));
+            }
+        }
+        NodeMpTan nm{};
+        fill_tan(nm, c, c->mlp[3 + 2 * (l - 1)], k, l, false, node_mask(c, k, l));
+        nm.noff_prev = noff_prev; nm.Rn_prev_base = l - 1;
+        nm.th_prev = th[(l - 1) & 1]; nm.tagg = c->d_tagg; nm.th = th[l & 1];
+        GM_TRY(launch_mlp(c, nm, tc_fwd(c, c->mlp[3 + 2 * (l - 1)]), st));
+    }
+    DecTan de{};
+    fill_tan(de, c, c->mlp[2 + 2 * K], k, K, false, node_mask(c, k, K + 1));
+    de.Sk = Sk; de.Sk1 = Sk1; de.th = th[K & 1]; de.dt = c->dt;
+    GM_TRY(launch_mlp(c, de, tc_fwd(c, c->mlp[2 + 2 * K]), st));
+    return GM_OK;
+}
+
+static gm_status tangent_offset(gm_ctx* c, const float* u_hat, cudaStream_t st) {
+    const int M = c->M, N = c->N;
     GM_CUDA_TRY(cudaMemsetAsync(c->d_Gx, 0, sizeof(float) * M * 6, st));
     const long warps = (long)N * M * 6;
-    tan_offset_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(N, M, nu, c->d_Gu, u_hat, c->d_Gx);
+    tan_offset_kernel<<<cdiv(warps * 32, 256), 256, 0, st>>>(N, M, c->nu, c->d_Gu, u_hat, c->d_Gx);
     GM_LAUNCH_CHECK();
     return GM_OK;
+}
+
+static gm_status check_mf(const gm_ctx* c) {
+    if (c->s.condensing != 1 || !c->dtan.noff) {
+        set_error("matrix-free condensing needs a context created with gm_settings.condensing = 1");
+        return GM_ERR_INVALID_ARG;
+    }
+    return GM_OK;
+}
+
+gm_status gnn_sensitivities(gm_ctx* c, const float* u_hat, cudaStream_t st) {
+    GM_TRY(check_mf(c));
+    for (int k = 0; k < c->N; ++k) GM_TRY(tangent_stage(c, k, st));
+    return tangent_offset(c, u_hat, st);
+}
+
+// Rollout and sensitivities overlapped: the rollout runs on the context's high-priority stream,
+// forked from st, and records an event after each stage; the tangent pass of stage k waits for it
+// on st (it reads only stage k's ReLU masks and S_k) and runs beside the rollout of later stages.
+gm_status gnn_rollout_sensitivities(gm_ctx* c, const float* x0, const float* u_hat, float* x_hat,
+                                    cudaStream_t st) {
+    GM_TRY(check_mf(c));
+    const int M = c->M, N = c->N;
+    if (!c->roll_stream || (int)c->ev_tan.size() < N) {
+        GM_TRY(gnn_rollout(c, x0, u_hat, x_hat, st));
+        return gnn_sensitivities(c, u_hat, st);
+    }
+    cudaStream_t rs = c->roll_stream;
+    GM_CUDA_TRY(cudaEventRecord(c->ev_roll, st));
+    GM_CUDA_TRY(cudaStreamWaitEvent(rs, c->ev_roll, 0));
+    if (x_hat != x0) GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, rs));
+    for (int k = 0; k < N; ++k) {
+        GM_TRY(forward_stage(c, k, x_hat + (long)k * M * 6, u_hat + (long)k * c->nu, x_hat + (long)(k + 1) * M * 6,
+                             rs));
+        GM_CUDA_TRY(cudaEventRecord(c->ev_tan[k], rs));
+        GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_tan[k], 0));
+        GM_TRY(tangent_stage(c, k, st));
+    }
+    return tangent_offset(c, u_hat, st);
 }
 
 }  // namespace gmi
