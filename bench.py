@@ -8,7 +8,7 @@ MLPs, 8 actuators, horizon N = 20, input box |u| <= 1, 5 sphere obstacles
 linearised to half-spaces on every node and stage (100k rows), ADMM rho = 0.1
 to residual 1e-4.
 
-One step = one gm_rti_step (rollout, Jacobians, condensing, QP set-up, ADMM,
+One step = one gm_rti_step (rollout, sensitivities, condensing, QP set-up, ADMM,
 FP64 KKT check) on device-resident inputs; `e2e` adds the host->device copy of
 the measured state and the device->host copy of U* each step.  The measured
 states are distinct: before timing, the controller runs the closed loop
@@ -18,18 +18,23 @@ as in a receding-horizon run.  The same form with cold ADMM is timed on the
 same states beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--form mixed|bf16|fp32] [--no-graph] [--no-plain] [--workload chain1000|chain10]
+                  [--form mixed|bf16|fp32] [--condensing matrix-free|jacobian] [--no-graph]
+                  [--no-plain] [--workload chain1000|chain200|chain10]
   python bench.py --compare ipm       # ADMM against the interior-point solve on the step's QP
   python bench.py --compare barrier   # obstacles as QP rows against obstacles as barrier costs
-  python bench.py --compare matrix-free  # cost estimate of forward-mode (matrix-free) condensing
+  python bench.py --compare matrix-free  # cost estimate of forward-mode condensing from row counts
 
-The two comparisons print their own JSON line (not the metric line above).
+The comparisons print their own JSON line (not the metric line above).
 
-The chosen form (default): GNN MLPs and their Jacobian products on tcgen05 tensor
-cores with split-BF16 operands (forward rollout three pieces, reverse two), FP32
-condensing and ADMM, FP64 Cholesky and KKT check, the whole step replayed as a
-CUDA graph.  The same run times the plain GPU form (FP32 everywhere, eager
-launches) on the same inputs to the same ADMM residual and reports the speedup.
+The chosen form (default): matrix-free condensing (the sensitivities pushed through
+the GNN by forward-mode products on their supports, the tangent pass of each stage
+beside the rollout of the later stages), GNN MLPs and their tangent products on
+tcgen05 tensor cores with split-BF16 operands (forward rollout three pieces,
+tangents two), FP32 condensing and ADMM, FP64 Cholesky and KKT check, the whole
+step replayed as a CUDA graph.  `--condensing jacobian` runs the Jacobian path
+(reverse pass over cones, Thm. 1 recursion) instead.  The same run times the
+plain GPU form (FP32 everywhere, eager launches, cold ADMM, Jacobian path) on the
+same inputs to the same ADMM residual and reports the speedup.
 
 Multi-GPU: one process per GPU (torchrun); every rank runs its own MPC
 instance (the path does not shard inside an instance: replicas), value = all
@@ -66,7 +71,7 @@ def parse(argv=None):
     p.add_argument("--workload", default="chain1000", choices=["chain1000", "chain200", "chain10"],
                    help="chain200: the chain-of-1000 configuration on 200 nodes (a small case for "
                         "counter captures of the same kernels)")
-    p.add_argument("--condensing", default="jacobian", choices=["jacobian", "matrix-free"],
+    p.add_argument("--condensing", default="matrix-free", choices=["jacobian", "matrix-free"],
                    help="jacobian: local Jacobians by the reverse pass and the Thm. 1 recursion; matrix-free: "
                         "forward-mode sensitivities (gm_settings.condensing = 1)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -309,6 +314,9 @@ def run_reference(args):
 KERNEL_TC = ("tc_ws_bwd_kernel<EdgeMpBwd> (reverse edge-update MLP, warp-specialised persistent, "
              "split-BF16 tcgen05)")
 KERNEL_FP32 = "mlp2_kernel<128, EdgeMpBwd> (reverse edge-update MLP, FP32 SIMT)"
+KERNEL_TAN = ("tc_mlp_kernel<128, EdgeMpTan, 2> (tangent edge-update MLP of matrix-free condensing, "
+              "split-BF16 tcgen05)")
+KERNEL_TAN_FP32 = "mlp2_kernel<128, EdgeMpTan> (tangent edge-update MLP of matrix-free condensing, FP32 SIMT)"
 TRAFFIC_SOURCES = ("paper_2602_17601_b300/csrc/tc_prim.cuh", "paper_2602_17601_b300/csrc/tc_mlp.cuh", "paper_2602_17601_b300/csrc/tc_ws.cuh",
                    "paper_2602_17601_b300/csrc/gnn.cu")
 
@@ -386,7 +394,6 @@ def run_ours(args):
     max_over_ranks = reps.max_over_ranks
 
     # ---- one eager step counts the kernels of a step (a fresh context's first step is eager)
-    gm.gm_ctx_set_kernel_timing(prob.ctx, True)
     l0 = gm.gm_launch_count()
     prob.step(wl.x0, U)
     torch.cuda.synchronize()
@@ -411,8 +418,6 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    kst = gm.gm_ctx_kernel_stats(prob.ctx)        # dominant kernel, last timed step
-    klaunch = [gm.gm_ctx_kernel_launch(prob.ctx, i) for i in range(kst["launches"])]
     replayed, captures = prob.graph_state()
     st = prob.read_stats()
     ms = max_over_ranks(ms)
@@ -439,8 +444,26 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e2.elapsed_time(e3) / args.steps)
 
-    # ---- per-phase breakdown (events at phase boundaries force eager steps: not timed above)
+    # ---- the dominant kernel's launches: the same timed steps again with an event pair around each
+    # of its launches (kept out of the headline pass, whose step the event records would lengthen);
+    # every step's launches are read back after the step
+    gm.gm_ctx_set_kernel_timing(prob.ctx, True)
+    prob.reset()
+    for i in range(warmup):
+        prob.step(X[i], U)
+    klaunch = []                                            # per step: its timed launches
+    kst = {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0}
+    for i in range(warmup, n_states):
+        prob.step(X[i], U)
+        s_ = gm.gm_ctx_kernel_stats(prob.ctx)
+        klaunch.append([gm.gm_ctx_kernel_launch(prob.ctx, j) for j in range(s_["launches"])])
+        for key in kst:
+            kst[key] += s_[key]
+    k_steps = max(n_states - warmup, 1)
+    kst = {key: v / k_steps for key, v in kst.items()}      # per step
     gm.gm_ctx_set_kernel_timing(prob.ctx, False)
+
+    # ---- per-phase breakdown (events at phase boundaries force eager steps: not timed above)
     gm.gm_ctx_set_timing(prob.ctx, True)
     gm.gm_ctx_phase_ms(prob.ctx)
     prob.reset()
@@ -488,7 +511,8 @@ def run_ours(args):
         barrier()
         ms_p = max_over_ranks(timed_steps(torch, pp, X, U, warmup, args.steps, stream))
         sp = pp.read_stats()
-        plain = {"form": "fp32, eager launches, cold ADMM", "value": reps.steps_per_s(ms_p), "unit": "steps/s",
+        plain = {"form": "fp32, eager launches, cold ADMM, local Jacobians and the Thm. 1 recursion",
+                 "value": reps.steps_per_s(ms_p), "unit": "steps/s",
                  "ms_per_step": ms_p, "admm_iters_last_step": sp["iters"], "kkt_stat_last_step": sp["kkt_stat"],
                  "r_dual_last_step": sp["r_dual"], "status_last_step": sp["status"]}
         del pp
@@ -507,10 +531,14 @@ def run_ours(args):
     k_ms = kst["ms"]
     achieved = kst["bytes"] / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
     products = {"mixed": 3, "bf16": 1, "fp32": 1}[args.form]
-    roof = {"kernel": KERNEL_FP32 if args.form == "fp32" else KERNEL_TC.replace(", 2>", ", 1>" if args.form == "bf16" else ", 2>"),
+    if cond:
+        kname = KERNEL_TAN_FP32 if args.form == "fp32" else KERNEL_TAN.replace(", 2>", ", 1>" if args.form == "bf16" else ", 2>")
+    else:
+        kname = KERNEL_FP32 if args.form == "fp32" else KERNEL_TC.replace(", 2>", ", 1>" if args.form == "bf16" else ", 2>")
+    roof = {"kernel": kname,
             "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "peak_source": peak_src,
-            "traffic": kernel_traffic(args.form),
+            "traffic": None if cond else kernel_traffic(args.form),
             "launches_per_step": kst["launches"], "ms_per_step": k_ms,
             "algorithmic_bytes_per_launch": kst["bytes"] / max(kst["launches"], 1),
             "avg_launch_ms": k_ms / max(kst["launches"], 1),
@@ -518,14 +546,26 @@ def run_ours(args):
             "tensor_peak_tflops": peaks.get("bf16_tflops_sustained"),
             "share_of_step": k_ms / ms,
             "phase_ms": per_phase}
-    # the launches that had the whole GPU (the last chunk's, after the rollout): the kernel's own
-    # rate; the earlier chunks' launches share the SMs and HBM with the rollout of later stages
-    full = [L for L in klaunch if L["ctas"] >= max(x["ctas"] for x in klaunch)] if klaunch else []
+    # the launches that had the whole GPU (after the rollout): the kernel's own rate; the earlier
+    # launches share the SMs and HBM with the rollout of later stages.  Jacobian path: the last
+    # chunk's (the launches with every SM); matrix-free: the last stage's K launches
+    full, rest = [], []
+    for step_l in klaunch:
+        if not step_l:
+            continue
+        if cond:
+            f_ = step_l[-wl.K:] if len(step_l) > wl.K else []
+        else:
+            top = max(x["ctas"] for x in step_l)
+            f_ = [L for L in step_l if L["ctas"] >= top]
+        full += f_
+        rest += step_l[:len(step_l) - len(f_)] if cond else [L for L in step_l if L not in f_]
     f_ms, f_by = sum(L["ms"] for L in full), sum(L["bytes"] for L in full)
-    if f_ms > 0 and len(full) < len(klaunch):
-        roof["beside_rollout"] = {"launches": len(klaunch) - len(full),
-                                  "ctas": sorted({L["ctas"] for L in klaunch if L not in full})}
-        roof["alone"] = {"launches": len(full), "ctas": full[0]["ctas"], "ms": f_ms,
+    if f_ms > 0 and rest:
+        roof["beside_rollout"] = {"launches_per_step": len(rest) / k_steps,
+                                  "ctas": [min(L["ctas"] for L in rest), max(L["ctas"] for L in rest)]}
+        roof["alone"] = {"launches_per_step": len(full) / k_steps, "ctas": max(L["ctas"] for L in full),
+                         "ms_per_step": f_ms / k_steps,
                          "achieved": f_by / (f_ms * 1e-3) / 1e9, "frac": f_by / (f_ms * 1e-3) / 1e9 / hbm_peak}
     out = {"metric": METRIC, "value": reps.steps_per_s(ms), "unit": "steps/s", "n_gpus": world,
            "steps": args.steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -539,7 +579,8 @@ def run_ours(args):
                "states": f"closed-loop trajectory: {n_states} distinct measured states, the GNN as the plant "
                          "driven by this controller (computed before timing; timed step i uses state i)",
                "parallelism": f"replicas{world}",
-               "l2": "inputs larger than L2: the step streams ~2 GB of Jacobian/condensing buffers",
+               "l2": ("inputs larger than L2: the step streams ~9 GB of tangent rows" if cond else
+                      "inputs larger than L2: the step streams ~2 GB of Jacobian/condensing buffers"),
                "admm_iters_mean": mean_iters(timed_stats),
                "admm_iters_per_step": [s["iters"] for s in timed_stats],
                "admm_iters_source": "the closed-loop pass that produced the states (same states, same warm starts)",

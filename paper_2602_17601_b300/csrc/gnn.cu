@@ -917,9 +917,10 @@ static cudaError_t record_kev(cudaEvent_t ev, cudaStream_t st) {
                                                : cudaEventRecord(ev, st);
 }
 
-// Launch timing of the reverse edge-update MLP: event pair kev[i] for the i-th launch of
-// the step, with the launch's algorithmic bytes and FLOPs (level r, Ns stages).
-static int kernel_timing_begin(gm_ctx* c, int r, int Ns, cudaStream_t st) {
+// Launch timing of the dominant MLP (the reverse edge-update MLP; the tangent edge-update MLP in
+// matrix-free condensing): event pair kev[i] for the i-th timed launch of the step, with the
+// launch's algorithmic bytes and FLOPs and its CTAs.
+static int kev_begin(gm_ctx* c, double bytes, double flops, int ctas, cudaStream_t st) {
     const int i = c->kev_n++;
     if ((int)c->kev.size() <= i) {
         std::array<cudaEvent_t, 2> e{};
@@ -929,6 +930,16 @@ static int kernel_timing_begin(gm_ctx* c, int r, int Ns, cudaStream_t st) {
         c->kev_flops.push_back(0.0);
         c->kev_ctas.push_back(0);
     }
+    c->kev_bytes[i] = bytes;
+    c->kev_flops[i] = flops;
+    c->kev_ctas[i] = ctas;
+    if (record_kev(c->kev[i][0], st) != cudaSuccess) return -1;
+    return i;
+}
+
+// the reverse edge-update MLP of level r over Ns stages: 4W bytes for each hidden and carry row
+// written, each carried input row and each distinct aggregate row read; W/8 per distinct edge mask
+static int kernel_timing_begin(gm_ctx* c, int r, int Ns, cudaStream_t st) {
     const Cones& C = c->cones;
     const double W = c->W, Re = (double)C.er_edge[r].size(), Rn = (double)C.nr_node[r].size();
     double carried = 0.0;
@@ -941,13 +952,10 @@ static int kernel_timing_begin(gm_ctx* c, int r, int Ns, cudaStream_t st) {
             edges += 1.0;
         }
     const double rows = 3.0 * Ns * Re;
-    c->kev_bytes[i] = 4.0 * W * (2.0 * rows + 3.0 * Ns * carried + 3.0 * Ns * Rn) + Ns * edges * W / 8.0;
-    c->kev_flops[i] = 4.0 * W * W * rows;
     const long tiles = (long)((rows + TC_M - 1) / TC_M);
     const int sms = c->ws_grid > 0 ? std::min(c->ws_grid, c->num_sms) : c->num_sms;
-    c->kev_ctas[i] = (int)std::min<long>(tiles, std::max(1, sms));
-    if (record_kev(c->kev[i][0], st) != cudaSuccess) return -1;
-    return i;
+    return kev_begin(c, 4.0 * W * (2.0 * rows + 3.0 * Ns * carried + 3.0 * Ns * Rn) + Ns * edges * W / 8.0,
+                     4.0 * W * W * rows, (int)std::min<long>(tiles, std::max(1, sms)), st);
 }
 
 // Reverse pass over all stages (in chunks): A, B, c of Eq. linearized_dynamics.

@@ -321,7 +321,18 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
             em.Rn_prev_base = l - 1;
             em.Re_prev_base = l == 1 ? -1 : l - 2;   // -1: the encoder's layer (none for i = k)
             em.th_prev = th[(l - 1) & 1]; em.te_prev = te[(l - 1) & 1]; em.te = te[l & 1];
+            // timed launch: 4W bytes per edge row written, per carried edge row (the previous edge
+            // layer) and per node row of the previous node layer read, W/8 per edge mask; one
+            // product of 2 (3W W + W W) FLOPs per row
+            int kt = -1;
+            if (c->ktiming && em.rows > 0) {
+                const double rows = (double)em.rows, ep = (double)tan_rows(c, k, l - 1, true);
+                const double np = (double)tan_rows(c, k, l - 1, false);
+                kt = kev_begin(c, 4.0 * W * (rows + ep + np) + (double)c->E * W / 8.0, 8.0 * W * W * rows,
+                               (int)cdiv(em.rows, TC_M), st);
+            }
             GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * (l - 1)]), st));
+            if (kt >= 0) GM_CUDA_TRY(record_kev(c->kev[kt][1], st));
         }
         const long nrows = tan_rows(c, k, l, false);
         if (nrows > 0) {
