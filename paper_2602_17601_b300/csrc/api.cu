@@ -305,6 +305,16 @@ static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::v
                     t[(size_t)(W + j) * W + n] = W1[(size_t)(W + n) * hid + j];
                 }
             mo.Bab = put(w, t.data(), t.size());
+            t.assign((size_t)W * 2 * W, 0.f);
+            for (int k = 0; k < W; ++k)
+                for (int n = 0; n < W; ++n) {
+                    t[(size_t)k * 2 * W + n] = W1[(size_t)k * hid + n];
+                    t[(size_t)k * 2 * W + W + n] = W1[(size_t)(W + k) * hid + n];
+                }
+            mo.Pab = put(w, t.data(), t.size());
+            t.assign((size_t)W * W, 0.f);
+            for (int k = 0; k < W; ++k) t[(size_t)k * W + k] = 1.f;
+            mo.eye = put(w, t.data(), t.size());
         }
         // K-major BF16 operands of the tensor-core products (see MlpOff)
         auto up16 = [](int v) { return (v + 15) / 16 * 16; };
@@ -319,6 +329,11 @@ static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::v
             mo.babk = put_bf(wp, W, 2 * W, TC_CHUNK, [&](int n, int k) {
                 return k < W ? W1[(size_t)n * hid + k] : W1[(size_t)(W + n) * hid + (k - W)];
             });
+            mo.fck = put_bf(wp, hid, W, TC_CHUNK, [&](int j, int k) { return W1[(size_t)(2 * W + k) * hid + j]; });
+            mo.pabk = put_bf(wp, 2 * W, W, tc_chunk_b2(2 * W), [&](int n, int k) {
+                return n < W ? W1[(size_t)k * hid + n] : W1[(size_t)(W + k) * hid + (n - W)];
+            });
+            mo.eyek = put_bf(wp, W, W, TC_CHUNK, [&](int j, int k) { return j == k ? 1.f : 0.f; });
         }
         offs.push_back(mo);
     }
@@ -445,6 +460,7 @@ static void plan(gm_ctx* c, Carver& cv) {
         c->d_tagg = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
         c->d_teA = cv.take<float>((size_t)std::max(1L, Tn.max_erows) * W);
         c->d_teB = cv.take<float>((size_t)std::max(1L, Tn.max_erows) * W);
+        c->d_tproj = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * 2 * W);
     }
 }
 

@@ -48,6 +48,10 @@ struct MlpOff {
     long fk1 = 0, fk2 = 0;                  // forward:  W1^T [hid][in_p], W2^T [out_p][hid]
     long bk1 = 0, bk2 = 0;                  // reverse:  W2 [hid][out_p],   W1 [in_p][hid]
     long wck = 0, babk = 0;                 // edge MLPs: Wc^T [W][W], Bab^T [W][2W]
+    // edge MLPs, matrix-free tangents: the e-block of W1 and the node blocks [W_a | W_b] apart
+    long Pab = 0;                           // FP32 [W][2W]: Pab[k][n] = W1[k][n], Pab[k][W+n] = W1[W+k][n]
+    long eye = 0;                           // FP32 identity [W][W]
+    long fck = 0, pabk = 0, eyek = 0;       // BF16: W1 e-block^T [W][W], Pab^T [2W][W], identity [W][W]
 };
 
 // Rows of the reverse-mode cones (one seed = one output node s, 3 cotangent
@@ -140,6 +144,7 @@ struct gm_ctx {
     gmi::DTangents dtan{};
     float *d_thA = nullptr, *d_thB = nullptr, *d_tagg = nullptr;   // forward-mode node tangents
     float *d_teA = nullptr, *d_teB = nullptr;                      // forward-mode edge tangents
+    float* d_tproj = nullptr;    // node tangents projected by the edge MLP's node blocks [rows][2W]
     // rollout
     float *d_h = nullptr, *d_e = nullptr, *d_agg = nullptr;
     float* d_yw = nullptr;       // shifted previous multipliers (ADMM warm start) [nU + rows]

@@ -147,6 +147,9 @@ __global__ void __launch_bounds__(NT) mlp2_kernel(Op op) {
                     v = v > 0.f ? v : 0.f;
                 } else {
                     uint32_t w = (row0 + m < rows) ? op.mask_word(rc[m], n >> 5) : 0u;
+                    if constexpr (Op::kHidAdd) {
+                        if (row0 + m < rows) v += op.hid_val(rc[m], n);
+                    }
                     v = ((w >> (n & 31)) & 1u) ? v : 0.f;
                 }
                 Hs[m][n] = v;
@@ -557,6 +560,7 @@ struct BwdBase {
     static constexpr bool kWsHid = false;      // warp-specialised kernel: store the masked hidden
     static constexpr bool kWsResid = false;    // warp-specialised kernel: out = A + product
     static constexpr bool kWsLand = false;     // warp-specialised kernel: rows by bulk copy (land_row)
+    static constexpr bool kHidAdd = false;     // hid_add / hid_val: a per-row term added before the mask
     long rows;
     int kin, nout;
     const float *B1, *b1 = nullptr, *B2, *b2 = nullptr;

@@ -19,6 +19,11 @@
 
 namespace gmi {
 
+// Edge rows of a layer from which its first layer runs on per-node projections (NodeProjTan +
+// EdgeMpTan) instead of whole per edge row (EdgeMpTanK3).  Closed-loop step at the chain of
+// 1000: 8.45 ms from 40k or 100k rows, 8.55 ms without projections (no layer reaches 200k).
+constexpr long kTanSplitRows = 50000;
+
 // Row -> (tangent, position in its support) of one (stage, layer) launch.
 struct TanBase : BwdBase {
     const int* off;          // [T + 1] row offsets of the tangents in this launch
@@ -98,12 +103,14 @@ struct EdgeEncTan : TanBase {
     __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(te + (long)x.a * W + n, v); }
 };
 
-// Edge update of layer l: te_l = te_{l-1} + J [th_{l-1}(dst) | th_{l-1}(src) | te_{l-1}].
+// Edge update of layer l with the whole first layer per edge row:
+// te_l = te_{l-1} + J [th_{l-1}(dst) | th_{l-1}(src) | te_{l-1}] (K = 3W).  Used where a layer has
+// few edge rows (early stages), where one launch costs less than the projections' extra launch.
 // RowCtx: a row, b th row of dst, c th row of src, d edge (mask), e te row of the edge (-1: 0).
-struct EdgeMpTan : TanBase {
+struct EdgeMpTanK3 : TanBase {
     const int *src, *dst;
-    const int *noff_prev, *eoff_prev;   // offsets of the node layer l - 1 and the edge layer l - 1
-    int Rn_prev_base, Re_prev_base;     // radius of those layers minus K (k - i)
+    const int *noff_prev, *eoff_prev;
+    int Rn_prev_base, Re_prev_base;
     const float *th_prev, *te_prev;
     float* te;
     __device__ RowCtx prep(long r) const {
@@ -115,7 +122,6 @@ struct EdgeMpTan : TanBase {
         x.a = (int)r; x.d = q;
         x.b = node_row(noff_prev, t, a, dst[q], r0 + Rn_prev_base);
         x.c = node_row(noff_prev, t, a, src[q], r0 + Rn_prev_base);
-        // the edge encoder has no rows for the tangents of stage k (their x tangent is zero)
         const int Re = (Re_prev_base < 0 && i == k) ? -1 : r0 + (Re_prev_base < 0 ? 0 : Re_prev_base);
         x.e = edge_row(eoff_prev, t, a, q, Re);
         return x;
@@ -134,6 +140,84 @@ struct EdgeMpTan : TanBase {
         const float* base = k0 < 2 * W ? th_prev : te_prev;
         if (row >= 0) {
             ld8(base + (long)row * W + (k0 % W), v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        }
+    }
+    __device__ float4 resid4(const RowCtx& x, int n) const {
+        return x.e >= 0 ? ld4(te_prev + (long)x.e * W + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(te + (long)x.a * W + n, v); }
+};
+
+// The node blocks of an edge update's first layer, per node row of layer l - 1:
+// P = th_{l-1} [W_a | W_b] (2W columns), so that an edge row's first layer is P[dst][:W] +
+// P[src][W:] + te W_c.  Run as the tensor-core MLP with an identity first product and an all-ones
+// mask (GEMM1 only re-splits th into the operand pieces of GEMM2, N = 2W).
+// RowCtx: a row (also the row of P).
+struct NodeProjTan : TanBase {
+    const float* th_prev;
+    float* P;
+    __device__ RowCtx prep(long r) const { return RowCtx{r < 0 ? 0 : (int)r, 0, 0, 0, 0, 0}; }
+    __device__ float in(const RowCtx& x, int kk) const { return th_prev[(long)x.a * W + kk]; }
+    __device__ uint32_t mask_word(const RowCtx&, int) const { return 0xFFFFFFFFu; }
+    __device__ void out(const RowCtx& x, int n, float v) const { P[(long)x.a * 2 * W + n] = v; }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(th_prev + (long)x.a * W + k0, v); }
+    __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(P + (long)x.a * 2 * W + n, v); }
+};
+
+// Edge update of layer l: te_l = te_{l-1} + W2' (mask . (P[dst][:W] + P[src][W:] + te_{l-1} W_c)),
+// the node blocks of the first layer taken from the projections P of the node layer l - 1.
+// RowCtx: a row, b P row of dst (-1: 0), c P row of src (-1: 0), d edge (mask), e te row of the
+// edge in the previous edge layer (-1: 0).
+struct EdgeMpTan : TanBase {
+    static constexpr bool kHidAdd = true;
+    const int *src, *dst;
+    const int *noff_prev, *eoff_prev;   // offsets of the node layer l - 1 and the edge layer l - 1
+    int Rn_prev_base, Re_prev_base;     // radius of those layers minus K (k - i)
+    const float *P, *te_prev;
+    float* te;
+    __device__ RowCtx prep(long r) const {
+        RowCtx x{0, -1, -1, 0, -1, 0};
+        if (r < 0) return x;
+        const int t = find(r), i = t / nu, a = t % nu;
+        const int q = eorder[a * E + (int)(r - off[t])];
+        const int r0 = K * (k - i);
+        x.a = (int)r; x.d = q;
+        x.b = node_row(noff_prev, t, a, dst[q], r0 + Rn_prev_base);
+        x.c = node_row(noff_prev, t, a, src[q], r0 + Rn_prev_base);
+        // the edge encoder has no rows for the tangents of stage k (their x tangent is zero)
+        const int Re = (Re_prev_base < 0 && i == k) ? -1 : r0 + (Re_prev_base < 0 ? 0 : Re_prev_base);
+        x.e = edge_row(eoff_prev, t, a, q, Re);
+        return x;
+    }
+    __device__ float in(const RowCtx& x, int kk) const { return x.e >= 0 ? te_prev[(long)x.e * W + kk] : 0.f; }
+    __device__ float hid_val(const RowCtx& x, int n) const {
+        return (x.b >= 0 ? P[(long)x.b * 2 * W + n] : 0.f) + (x.c >= 0 ? P[(long)x.c * 2 * W + W + n] : 0.f);
+    }
+    // 32 hidden columns [c0, c0 + 32): both projected rows loaded before the adds
+    __device__ void hid_add(const RowCtx& x, int c0, float* v) const {
+        float4 pa[8], pb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            pa[q] = ldg4_if(P + (long)(x.b >= 0 ? x.b : 0) * 2 * W + c0 + 4 * q, x.b >= 0);
+            pb[q] = ldg4_if(P + (long)(x.c >= 0 ? x.c : 0) * 2 * W + W + c0 + 4 * q, x.c >= 0);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            v[4 * q] += pa[q].x + pb[q].x; v[4 * q + 1] += pa[q].y + pb[q].y;
+            v[4 * q + 2] += pa[q].z + pb[q].z; v[4 * q + 3] += pa[q].w + pb[q].w;
+        }
+    }
+    __device__ void out(const RowCtx& x, int n, float v) const {
+        te[(long)x.a * W + n] = (x.e >= 0 ? te_prev[(long)x.e * W + n] : 0.f) + v;
+    }
+    static constexpr bool kHasIn8 = true, kHasOut4 = true, kHasResid = true;
+    __device__ void in8(const RowCtx& x, int k0, float* v) const {
+        if (x.e >= 0) {
+            ld8(te_prev + (long)x.e * W + k0, v);
         } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) v[j] = 0.f;
@@ -314,24 +398,49 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
         const int* noff_prev = c->dtan.noff + (long)(k * (K + 1) + l - 1) * L;
         const int* eoff_prev = c->dtan.eoff + (long)(k * (K + 1) + l - 1) * L;
         if (c->E > 0) {
-            EdgeMpTan em{};
-            fill_tan(em, c, c->mlp[2 + 2 * (l - 1)], k, l, true, edge_mask(c, k, l));
-            em.src = c->d_src; em.dst = c->d_dst;
-            em.noff_prev = noff_prev; em.eoff_prev = eoff_prev;
-            em.Rn_prev_base = l - 1;
-            em.Re_prev_base = l == 1 ? -1 : l - 2;   // -1: the encoder's layer (none for i = k)
-            em.th_prev = th[(l - 1) & 1]; em.te_prev = te[(l - 1) & 1]; em.te = te[l & 1];
-            // timed launch: 4W bytes per edge row written, per carried edge row (the previous edge
-            // layer) and per node row of the previous node layer read, W/8 per edge mask; one
-            // product of 2 (3W W + W W) FLOPs per row
+            const MlpOff& m = c->mlp[2 + 2 * (l - 1)];
+            const long erows = tan_rows(c, k, l, true);
+            const double ep = (double)tan_rows(c, k, l - 1, true), np = (double)tan_rows(c, k, l - 1, false);
             int kt = -1;
-            if (c->ktiming && em.rows > 0) {
-                const double rows = (double)em.rows, ep = (double)tan_rows(c, k, l - 1, true);
-                const double np = (double)tan_rows(c, k, l - 1, false);
-                kt = kev_begin(c, 4.0 * W * (rows + ep + np) + (double)c->E * W / 8.0, 8.0 * W * W * rows,
-                               (int)cdiv(em.rows, TC_M), st);
+            if (erows >= kTanSplitRows) {
+                // the node blocks of the first layer on the node rows of layer l - 1, then the edge
+                // rows with the e-block alone (K = W)
+                NodeProjTan pj{};
+                fill_tan(pj, c, m, k, l - 1, false, nullptr);
+                pj.kin = W; pj.nout = 2 * W;
+                pj.B1 = c->d_wts + m.eye; pj.B2 = c->d_wts + m.Pab;
+                pj.th_prev = th[(l - 1) & 1]; pj.P = c->d_tproj;
+                GM_TRY(launch_mlp(c, pj, tc_w(c, m.eyek, m.pabk, W, 2 * W), st));
+                EdgeMpTan em{};
+                fill_tan(em, c, m, k, l, true, edge_mask(c, k, l));
+                em.kin = W;
+                em.B1 = c->d_wts + m.W1 + (long)2 * W * W;   // the e-block of W1, [W][hid]
+                em.src = c->d_src; em.dst = c->d_dst;
+                em.noff_prev = noff_prev; em.eoff_prev = eoff_prev;
+                em.Rn_prev_base = l - 1;
+                em.Re_prev_base = l == 1 ? -1 : l - 2;   // -1: the encoder's layer (none for i = k)
+                em.P = c->d_tproj; em.te_prev = te[(l - 1) & 1]; em.te = te[l & 1];
+                // timed: 4W bytes per edge row written and per carried edge row read, 8W per
+                // projected node row, W/8 per edge mask; one product of 2 (W W + W W) FLOPs per row
+                if (c->ktiming)
+                    kt = kev_begin(c, 4.0 * W * (erows + ep) + 8.0 * W * np + (double)c->E * W / 8.0,
+                                   4.0 * W * W * erows, (int)cdiv(erows, TC_M), st);
+                GM_TRY(launch_mlp(c, em, tc_w(c, m.fck, m.fk2, W, m.out_p), st));
+            } else if (erows > 0) {
+                EdgeMpTanK3 em{};
+                fill_tan(em, c, m, k, l, true, edge_mask(c, k, l));
+                em.src = c->d_src; em.dst = c->d_dst;
+                em.noff_prev = noff_prev; em.eoff_prev = eoff_prev;
+                em.Rn_prev_base = l - 1;
+                em.Re_prev_base = l == 1 ? -1 : l - 2;
+                em.th_prev = th[(l - 1) & 1]; em.te_prev = te[(l - 1) & 1]; em.te = te[l & 1];
+                // timed: 4W bytes per edge row written, per carried edge row and per node row of
+                // the previous layer read, W/8 per edge mask; one product of 2 (3W W + W W) FLOPs
+                if (c->ktiming)
+                    kt = kev_begin(c, 4.0 * W * (erows + ep + np) + (double)c->E * W / 8.0, 8.0 * W * W * erows,
+                                   (int)cdiv(erows, TC_M), st);
+                GM_TRY(launch_mlp(c, em, tc_fwd(c, m), st));
             }
-            GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * (l - 1)]), st));
             if (kt >= 0) GM_CUDA_TRY(record_kev(c->kev[kt][1], st));
         }
         const long nrows = tan_rows(c, k, l, false);

@@ -466,6 +466,9 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
                 if (valid) op.store_mask(rc[lrow], c0 >> 5, bits);
             } else {
                 const uint32_t mw = valid ? mwv[(c0 - cgrp * 32) / CSTEP] : 0u;
+                if constexpr (Op::kHidAdd) {
+                    if (valid) op.hid_add(rc[lrow], c0, v);     // terms of the first layer added per row
+                }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = ((mw >> j) & 1u) ? v[j] : 0.f;
                 if constexpr (Op::kStoreHid) {
