@@ -117,3 +117,36 @@ def test_matrix_free_against_the_jacobian_path_mixed_form(lib):
         steps[name] = out
     for a, b in zip(steps["mf"], steps["jac"]):
         assert np.abs(a - b).max() <= 2e-2 * max(np.abs(b).max(), 1e-3), np.abs(a - b).max()
+
+
+def test_matrix_free_barrier_step_matches_the_jacobian_path(lib):
+    """The barrier-cost variant (sphere rows folded into H and g, box-only QP) on a matrix-free
+    context against the same step on a Jacobian context."""
+    wl = small_chain(tol=1e-7, n_spheres=2, sphere_clear=0.15)
+    out = {}
+    for cond in (0, 1):
+        p = lib.RTIProblem.from_workload(wl, condensing=cond, barrier=(1e-3, 5e-3))
+        out[cond] = p.step(wl.x0).cpu().numpy().astype(np.float64)
+        assert p.read_stats()["converged"] == 1
+    assert np.abs(out[1] - out[0]).max() <= 10 * wl.tol / wl.rho + 1e-5, np.abs(out[1] - out[0]).max()
+
+
+def test_matrix_free_contexts_in_a_batch(lib):
+    """Matrix-free contexts stepped as one batch (gm_batch_*: plain launches, then the captured
+    graph) give each instance the U of its own single-instance steps."""
+    from paper_2602_17601_b300.batch import Batch
+    wls = [small_chain(), random_instance(7, M=8, N=6, nu=3, K=2, W=32),
+           paper_chain(seed=3, M=40, N=5, nu=2, K=2, W=32, w_seed=0, n_spheres=2)]
+    alone = []
+    for wl in wls:
+        p = lib.RTIProblem.from_workload(wl, condensing=1, admm_grid=8, factor_grid=16)
+        alone.append([p.step(wl.x0).cpu().numpy().copy() for _ in range(3)])
+    probs = [lib.RTIProblem.from_workload(wl, condensing=1, admm_grid=8, factor_grid=16) for wl in wls]
+    b = Batch(probs)
+    b.set_states([wl.x0 for wl in wls])
+    for k in range(3):
+        b.step()
+        for i, (wl, p) in enumerate(zip(wls, probs)):
+            assert p.read_stats()["converged"] == 1, (k, i)
+            U = p._U.cpu().numpy()
+            assert np.abs(U - alone[i][k]).max() <= 10 * wl.tol / wl.rho, (k, i, np.abs(U - alone[i][k]).max())
