@@ -174,6 +174,7 @@ struct NodeProjTan : TanBase {
 // edge in the previous edge layer (-1: 0).
 struct EdgeMpTan : TanBase {
     static constexpr bool kHidAdd = true;
+    static constexpr bool kWsResid = true;    // warp-specialised kernel: te_{l-1} added by the tensor cores
     const int *src, *dst;
     const int *noff_prev, *eoff_prev;   // offsets of the node layer l - 1 and the edge layer l - 1
     int Rn_prev_base, Re_prev_base;     // radius of those layers minus K (k - i)
@@ -227,6 +228,13 @@ struct EdgeMpTan : TanBase {
         return x.e >= 0 ? ld4(te_prev + (long)x.e * W + n) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(te + (long)x.a * W + n, v); }
+    // warp-specialised kernel: the A row is te_{l-1} (zero where the edge had no tangent)
+    __device__ void in8_pair(const RowCtx& x, int k0, float4* a, float4* b) const {
+        const float* pa = te_prev + (long)(x.e >= 0 ? x.e : 0) * W + k0;
+        a[0] = ldg4_if(pa, x.e >= 0);
+        a[1] = ldg4_if(pa + 4, x.e >= 0);
+        b[0] = b[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 };
 
 // Node update of layer l: th_l = th_{l-1} + J [th_{l-1} | tagg_l].  RowCtx: a row (also the
@@ -425,7 +433,12 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
                 if (c->ktiming)
                     kt = kev_begin(c, 4.0 * W * (erows + ep) + 8.0 * W * np + (double)c->E * W / 8.0,
                                    4.0 * W * W * erows, (int)cdiv(erows, TC_M), st);
-                GM_TRY(launch_mlp(c, em, tc_w(c, m.fck, m.fk2, W, m.out_p), st));
+                const TcW tw = tc_w(c, m.fck, m.fk2, W, m.out_p);
+                if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.N2p == WS_W) {
+                    GM_TRY(launch_ws_bwd(c, em, tw, st));     // warp-specialised persistent form
+                } else {
+                    GM_TRY(launch_mlp(c, em, tw, st));
+                }
             } else if (erows > 0) {
                 EdgeMpTanK3 em{};
                 fill_tan(em, c, m, k, l, true, edge_mask(c, k, l));

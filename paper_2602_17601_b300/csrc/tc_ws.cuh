@@ -475,6 +475,9 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
                 const int c32 = 64 * hh + 32 * blk;
                 float v[32];
                 tc_ld32(tD1 + (unsigned)c32, v);
+                if constexpr (Op::kHidAdd) {
+                    if (valid) op.hid_add(rc[lrow], c32, v);     // per-row terms of the first layer
+                }
                 const uint32_t bits = mw[blk];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = ((bits >> j) & 1u) ? v[j] : 0.f;
