@@ -198,6 +198,8 @@ struct gm_ctx {
     cudaEvent_t ev_roll = nullptr;
     std::vector<cudaEvent_t> ev_stage;
     std::vector<cudaEvent_t> ev_tan;   // matrix-free: stage k of the rollout is done (tangent pass of k may start)
+    cudaStream_t tan_stream = nullptr;  // matrix-free: the tangent pass (highest priority)
+    cudaEvent_t ev_tan_done = nullptr;
     // launch timing of the reverse edge-update MLP (events around each launch of the last step)
     bool ktiming = false;
     int kev_n = 0;
@@ -214,6 +216,8 @@ struct gm_ctx {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (side_stream) cudaStreamDestroy(side_stream);
         if (roll_stream) cudaStreamDestroy(roll_stream);
+        if (tan_stream) cudaStreamDestroy(tan_stream);
+        if (ev_tan_done) cudaEventDestroy(ev_tan_done);
         if (ev_roll) cudaEventDestroy(ev_roll);
         for (auto ev : ev_stage) cudaEventDestroy(ev);
         for (auto ev : ev_tan) cudaEventDestroy(ev);

@@ -516,17 +516,25 @@ gm_status gnn_rollout_sensitivities(gm_ctx* c, const float* x0, const float* u_h
         return gnn_sensitivities(c, u_hat, st);
     }
     cudaStream_t rs = c->roll_stream;
+    // the tangent pass on its own highest-priority stream when the context has one
+    cudaStream_t ts = c->tan_stream ? c->tan_stream : st;
     GM_CUDA_TRY(cudaEventRecord(c->ev_roll, st));
     GM_CUDA_TRY(cudaStreamWaitEvent(rs, c->ev_roll, 0));
+    if (ts != st) GM_CUDA_TRY(cudaStreamWaitEvent(ts, c->ev_roll, 0));
     if (x_hat != x0) GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, rs));
     for (int k = 0; k < N; ++k) {
         GM_TRY(forward_stage(c, k, x_hat + (long)k * M * 6, u_hat + (long)k * c->nu, x_hat + (long)(k + 1) * M * 6,
                              rs));
         GM_CUDA_TRY(cudaEventRecord(c->ev_tan[k], rs));
-        GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_tan[k], 0));
-        GM_TRY(tangent_stage(c, k, st));
+        GM_CUDA_TRY(cudaStreamWaitEvent(ts, c->ev_tan[k], 0));
+        GM_TRY(tangent_stage(c, k, ts));
     }
-    return tangent_offset(c, u_hat, st);
+    GM_TRY(tangent_offset(c, u_hat, ts));
+    if (ts != st) {   // join: the tangent pass (which waited for the whole rollout) into st
+        GM_CUDA_TRY(cudaEventRecord(c->ev_tan_done, ts));
+        GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_tan_done, 0));
+    }
+    return GM_OK;
 }
 
 }  // namespace gmi
