@@ -644,7 +644,10 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
     // it, so there the rollout takes the caller's priority and the tangent pass the highest
     // (closed-loop step 8.42 against 8.54 ms with the rollout at the highest priority)
     const int roll_prio = c->s.condensing == 1 ? prio_lo : prio_hi;
-    if (c->s.condensing == 1 && cudaStreamCreateWithPriority(&c->tan_stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
+    if (c->s.condensing == 1 && (cudaStreamCreateWithPriority(&c->tan_stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+                                 cudaStreamCreateWithPriority(&c->tan_side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+                                 cudaEventCreateWithFlags(&c->ev_tfork, cudaEventDisableTiming) != cudaSuccess ||
+                                 cudaEventCreateWithFlags(&c->ev_tjoin, cudaEventDisableTiming) != cudaSuccess)) {
         set_error("tangent stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(GM_ERR_CUDA);
     }

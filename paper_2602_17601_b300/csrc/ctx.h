@@ -200,6 +200,8 @@ struct gm_ctx {
     std::vector<cudaEvent_t> ev_tan;   // matrix-free: stage k of the rollout is done (tangent pass of k may start)
     cudaStream_t tan_stream = nullptr;  // matrix-free: the tangent pass (highest priority)
     cudaEvent_t ev_tan_done = nullptr;
+    cudaStream_t tan_side = nullptr;    // matrix-free: the edge-encoder tangents beside the node encoder's
+    cudaEvent_t ev_tfork = nullptr, ev_tjoin = nullptr;
     // launch timing of the reverse edge-update MLP (events around each launch of the last step)
     bool ktiming = false;
     int kev_n = 0;
@@ -217,6 +219,9 @@ struct gm_ctx {
         if (side_stream) cudaStreamDestroy(side_stream);
         if (roll_stream) cudaStreamDestroy(roll_stream);
         if (tan_stream) cudaStreamDestroy(tan_stream);
+        if (tan_side) cudaStreamDestroy(tan_side);
+        if (ev_tfork) cudaEventDestroy(ev_tfork);
+        if (ev_tjoin) cudaEventDestroy(ev_tjoin);
         if (ev_tan_done) cudaEventDestroy(ev_tan_done);
         if (ev_roll) cudaEventDestroy(ev_roll);
         for (auto ev : ev_stage) cudaEventDestroy(ev);

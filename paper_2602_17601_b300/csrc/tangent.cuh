@@ -390,18 +390,28 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
     const float* Sk = k > 0 ? c->d_Gu + gu_offset(M, nu, k) : nullptr;
     float* Sk1 = c->d_Gu + gu_offset(M, nu, k + 1);
     GM_CUDA_TRY(cudaMemsetAsync(Sk1, 0, sizeof(float) * M * 6 * (k + 1) * nu, st));
+    // the two encoders read only S_k: the edge encoder's tangents run on a side stream beside the
+    // node encoder's (a fork and a join of events, graph branches when captured)
+    const bool edges = k > 0 && c->E > 0;
+    const bool fork = edges && c->tan_side;
+    if (fork) {
+        GM_CUDA_TRY(cudaEventRecord(c->ev_tfork, st));
+        GM_CUDA_TRY(cudaStreamWaitEvent(c->tan_side, c->ev_tfork, 0));
+    }
+    if (edges) {   // edge encoder (edge layer 0): tangents of earlier stages only
+        EdgeEncTan op{};
+        fill_tan(op, c, c->mlp[1], k, 0, true, edge_mask(c, k, 0));
+        op.Sk = Sk; op.src = c->d_src; op.dst = c->d_dst; op.te = te[0];
+        GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[1]), fork ? c->tan_side : st, !fork));
+    }
+    if (fork) GM_CUDA_TRY(cudaEventRecord(c->ev_tjoin, c->tan_side));
     {   // node encoder (node layer 0)
         NodeEncTan op{};
         fill_tan(op, c, c->mlp[0], k, 0, false, node_mask(c, k, 0));
         op.Sk = Sk; op.act = c->d_act; op.th = th[0];
         GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[0]), st));
     }
-    if (k > 0 && c->E > 0) {   // edge encoder (edge layer 0): tangents of earlier stages only
-        EdgeEncTan op{};
-        fill_tan(op, c, c->mlp[1], k, 0, true, edge_mask(c, k, 0));
-        op.Sk = Sk; op.src = c->d_src; op.dst = c->d_dst; op.te = te[0];
-        GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[1]), st));
-    }
+    if (fork) GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_tjoin, 0));
     for (int l = 1; l <= K; ++l) {
         const int* noff_prev = c->dtan.noff + (long)(k * (K + 1) + l - 1) * L;
         const int* eoff_prev = c->dtan.eoff + (long)(k * (K + 1) + l - 1) * L;
