@@ -315,7 +315,11 @@ __global__ void tan_agg_kernel(long rows, int T, int nu, int K, int k, int M, in
                                const float* __restrict__ te, float* __restrict__ tagg) {
     const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (r >= rows) return;
+    pdl_wait();                  // launched with programmatic serialization: the edge update is done
+    if (r >= rows) {
+        pdl_launch_dependents();
+        return;
+    }
     int lo = 0, hi = T;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -334,6 +338,7 @@ __global__ void tan_agg_kernel(long rows, int T, int nu, int K, int k, int M, in
         }
         st4(tagg + r * W + c0, s);
     }
+    pdl_launch_dependents();
 }
 
 // D_k = Gamma_x_k - x_hat_k = -S_k u_hat for k = 1..N (D_0 = 0), one warp per (k, node, component).
@@ -389,7 +394,6 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
     float* te[2] = {c->d_teA, c->d_teB};
     const float* Sk = k > 0 ? c->d_Gu + gu_offset(M, nu, k) : nullptr;
     float* Sk1 = c->d_Gu + gu_offset(M, nu, k + 1);
-    GM_CUDA_TRY(cudaMemsetAsync(Sk1, 0, sizeof(float) * M * 6 * (k + 1) * nu, st));
     // the two encoders read only S_k: the edge encoder's tangents run on a side stream beside the
     // node encoder's (a fork and a join of events, graph branches when captured)
     const bool edges = k > 0 && c->E > 0;
@@ -469,11 +473,13 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
         const long nrows = tan_rows(c, k, l, false);
         if (nrows > 0) {
             if (c->E > 0) {
-                tan_agg_kernel<<<cdiv(nrows * 32, 256), 256, 0, st>>>(
-                    nrows, (k + 1) * nu, nu, K, k, M, c->E, c->tan.Rmax, W,
-                    c->dtan.noff + (long)(k * (K + 1) + l) * L, c->dtan.eoff + (long)(k * (K + 1) + l) * L,
-                    l - 1, c->dtan.norder, c->dtan.epos, c->dtan.ecnt, c->d_in_ptr, te[l & 1], c->d_tagg);
-                GM_LAUNCH_CHECK();
+                GM_CUDA_TRY(launch_pdl(c->pdl, tan_agg_kernel, dim3((unsigned)cdiv(nrows * 32, 256)), dim3(256), 0, st,
+                                       nrows, (k + 1) * nu, nu, K, k, M, c->E, c->tan.Rmax, W,
+                                       (const int*)(c->dtan.noff + (long)(k * (K + 1) + l) * L),
+                                       (const int*)(c->dtan.eoff + (long)(k * (K + 1) + l) * L), l - 1,
+                                       (const int*)c->dtan.norder, (const int*)c->dtan.epos,
+                                       (const int*)c->dtan.ecnt, (const int*)c->d_in_ptr, (const float*)te[l & 1],
+                                       c->d_tagg));
             } else {
                 GM_CUDA_TRY(cudaMemsetAsync(c->d_tagg, 0, sizeof(float) * nrows * W, st));
             }
@@ -508,8 +514,16 @@ static gm_status check_mf(const gm_ctx* c) {
     return GM_OK;
 }
 
+// Gamma_u block rows 1..N to zero before the tangent pass (DecTan writes only its supports).
+static gm_status tangent_clear(gm_ctx* c, cudaStream_t st) {
+    const long n = gu_offset(c->M, c->nu, c->N + 1) - gu_offset(c->M, c->nu, 1);
+    GM_CUDA_TRY(cudaMemsetAsync(c->d_Gu + gu_offset(c->M, c->nu, 1), 0, sizeof(float) * n, st));
+    return GM_OK;
+}
+
 gm_status gnn_sensitivities(gm_ctx* c, const float* u_hat, cudaStream_t st) {
     GM_TRY(check_mf(c));
+    GM_TRY(tangent_clear(c, st));
     for (int k = 0; k < c->N; ++k) GM_TRY(tangent_stage(c, k, st));
     return tangent_offset(c, u_hat, st);
 }
@@ -532,6 +546,7 @@ gm_status gnn_rollout_sensitivities(gm_ctx* c, const float* x0, const float* u_h
     GM_CUDA_TRY(cudaStreamWaitEvent(rs, c->ev_roll, 0));
     if (ts != st) GM_CUDA_TRY(cudaStreamWaitEvent(ts, c->ev_roll, 0));
     if (x_hat != x0) GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, rs));
+    GM_TRY(tangent_clear(c, ts));
     for (int k = 0; k < N; ++k) {
         GM_TRY(forward_stage(c, k, x_hat + (long)k * M * 6, u_hat + (long)k * c->nu, x_hat + (long)(k + 1) * M * 6,
                              rs));
