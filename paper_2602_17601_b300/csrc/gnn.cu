@@ -331,11 +331,14 @@ struct DecFwd : FwdBase {
 __global__ void agg_kernel(int M, int W, const int* __restrict__ in_ptr, const float* __restrict__ e,
                            float* __restrict__ agg) {
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)M * W) return;
-    int n = (int)(t / W), c = (int)(t % W);
-    float s = 0.f;
-    for (int q = in_ptr[n]; q < in_ptr[n + 1]; ++q) s += e[(long)q * W + c];
-    agg[t] = s;
+    pdl_wait();                  // under programmatic serialization: the edge update is done
+    if (t < (long)M * W) {
+        int n = (int)(t / W), c = (int)(t % W);
+        float s = 0.f;
+        for (int q = in_ptr[n]; q < in_ptr[n + 1]; ++q) s += e[(long)q * W + c];
+        agg[t] = s;
+    }
+    pdl_launch_dependents();
 }
 
 // Launch with programmatic stream serialization (when pdl): the kernel may start while the
@@ -509,8 +512,8 @@ static gm_status forward_stage(gm_ctx* c, int k, const float* xk, const float* u
             fill_fwd(em, c, 2 + 2 * t, E, edge_mask(c, k, 1 + t));
             em.h = c->d_h; em.src = c->d_src; em.dst = c->d_dst; em.e = c->d_e; em.W = W;
             GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * t]), st));
-            agg_kernel<<<cdiv((long)M * W, 256), 256, 0, st>>>(M, W, c->d_in_ptr, c->d_e, c->d_agg);
-            GM_LAUNCH_CHECK();
+            GM_CUDA_TRY(launch_pdl(c->pdl, agg_kernel, dim3((unsigned)cdiv((long)M * W, 256)), dim3(256), 0, st, M, W,
+                                   (const int*)c->d_in_ptr, (const float*)c->d_e, c->d_agg));
         } else {
             GM_CUDA_TRY(cudaMemsetAsync(c->d_agg, 0, sizeof(float) * M * W, st));
         }
