@@ -365,6 +365,9 @@ static void plan(gm_ctx* c, Carver& cv) {
     // by default chunks of at most a quarter of the horizon: the reverse pass of the first chunk
     // starts while the rollout of the later stages still runs (gnn_linearize)
     if (c->s.chunk_mb == 0) c->stage_chunk = std::min(c->stage_chunk, (N + kOverlapChunks - 1) / kOverlapChunks);
+    // a matrix-free context steps without the reverse pass: gm_linearize still works on it, one
+    // stage per launch group, with the smallest cotangent buffers
+    if (c->s.condensing == 1 && c->s.chunk_mb == 0) c->stage_chunk = 1;
     const long Ns = c->stage_chunk;
     std::vector<float> wdummy;
     c->d_src = cv.take<int>(std::max(E, 1));
