@@ -314,11 +314,12 @@ def run_reference(args):
 KERNEL_TC = ("tc_ws_bwd_kernel<EdgeMpBwd> (reverse edge-update MLP, warp-specialised persistent, "
              "split-BF16 tcgen05)")
 KERNEL_FP32 = "mlp2_kernel<128, EdgeMpBwd> (reverse edge-update MLP, FP32 SIMT)"
-KERNEL_TAN = ("tc_mlp_kernel<128, EdgeMpTan, 2> (tangent edge-update MLP of matrix-free condensing, "
-              "split-BF16 tcgen05)")
+KERNEL_TAN = ("EdgeMpTan: tangent edge update of matrix-free condensing, tc_ws_bwd_kernel<EdgeMpTan> "
+              "(warp-specialised persistent, projected first layer) on layers of 50k edge rows or more, "
+              "tc_mlp_kernel<128, EdgeMpTanK3, 2> below; split-BF16 tcgen05")
 KERNEL_TAN_FP32 = "mlp2_kernel<128, EdgeMpTan> (tangent edge-update MLP of matrix-free condensing, FP32 SIMT)"
 TRAFFIC_SOURCES = ("paper_2602_17601_b300/csrc/tc_prim.cuh", "paper_2602_17601_b300/csrc/tc_mlp.cuh", "paper_2602_17601_b300/csrc/tc_ws.cuh",
-                   "paper_2602_17601_b300/csrc/gnn.cu")
+                   "paper_2602_17601_b300/csrc/gnn.cu", "paper_2602_17601_b300/csrc/tangent.cuh")
 
 
 def sources_sha256():
@@ -474,7 +475,7 @@ def run_ours(args):
         prob.step(X[i], U)
     phases, nrec = gm.gm_ctx_phase_ms(prob.ctx)
     gm.gm_ctx_set_timing(prob.ctx, False)
-    per_phase = {k: v / max(nrec, 1) for k, v in phases.items()}
+    per_phase = {("sensitivities" if cond and k == "jacobian" else k): v / max(nrec, 1) for k, v in phases.items()}
 
     # ---- the same form with cold ADMM every step, on the same states
     cold = None
@@ -538,7 +539,7 @@ def run_ours(args):
     roof = {"kernel": kname,
             "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "peak_source": peak_src,
-            "traffic": None if cond else kernel_traffic(args.form),
+            "traffic": kernel_traffic(args.form + ("-matrix-free" if cond else "")),
             "launches_per_step": kst["launches"], "ms_per_step": k_ms,
             "algorithmic_bytes_per_launch": kst["bytes"] / max(kst["launches"], 1),
             "avg_launch_ms": k_ms / max(kst["launches"], 1),
