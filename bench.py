@@ -464,6 +464,24 @@ def run_ours(args):
     kst = {key: v / k_steps for key, v in kst.items()}      # per step
     gm.gm_ctx_set_kernel_timing(prob.ctx, False)
 
+    # ---- stage timeline of the overlapped rollout and tangent pass (matrix-free): when each
+    # rollout stage and each tangent stage ends, from where both start, mean over the same states
+    timeline = None
+    if cond:
+        gm.gm_ctx_set_stage_timing(prob.ctx, True)
+        prob.reset()
+        for i in range(warmup):
+            prob.step(X[i], U)
+        acc_r, acc_t = [0.0] * wl.N, [0.0] * wl.N
+        for i in range(warmup, n_states):
+            prob.step(X[i], U)
+            r_, t_ = gm.gm_ctx_stage_times(prob.ctx, wl.N)
+            acc_r = [a + b for a, b in zip(acc_r, r_)]
+            acc_t = [a + b for a, b in zip(acc_t, t_)]
+        gm.gm_ctx_set_stage_timing(prob.ctx, False)
+        timeline = {"rollout_stage_end_ms": [round(v / k_steps, 4) for v in acc_r],
+                    "tangent_stage_end_ms": [round(v / k_steps, 4) for v in acc_t]}
+
     # ---- per-phase breakdown (events at phase boundaries force eager steps: not timed above)
     gm.gm_ctx_set_timing(prob.ctx, True)
     gm.gm_ctx_phase_ms(prob.ctx)
@@ -547,6 +565,8 @@ def run_ours(args):
             "tensor_peak_tflops": peaks.get("bf16_tflops_sustained"),
             "share_of_step": k_ms / ms,
             "phase_ms": per_phase}
+    if timeline is not None:
+        roof["stage_timeline"] = timeline
     # the launches that had the whole GPU (after the rollout): the kernel's own rate; the earlier
     # launches share the SMs and HBM with the rollout of later stages.  Jacobian path: the last
     # chunk's (the launches with every SM); matrix-free: the last stage's K launches

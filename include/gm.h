@@ -525,8 +525,10 @@ gm_status gm_batch_set_lanes(gm_batch* b, int lanes);
 gm_status gm_batch_plan(int n, const int* width, const double* cost, int sms, int* lane, int* n_lanes);
 gm_status gm_ctx_graph_state(const gm_ctx* ctx, int* replayed, int* captures);
 
-/* Launch timing of the dominant kernel, the reverse edge-update MLP (one launch per
- * message-passing level and stage chunk; Eq. linearized_dynamics).  When on,
+/* Launch timing of the dominant kernel: the reverse edge-update MLP (one launch per
+ * message-passing level and stage chunk; Eq. linearized_dynamics), or on a context with
+ * gm_settings.condensing = 1 the tangent edge-update MLP (one launch per stage and
+ * message-passing layer; Eq. sparse_gamma_i_u by forward-mode products).  When on,
  * gm_rti_step records a CUDA event pair around each of these launches (inside
  * the captured graph in graph mode) and notes each launch's algorithmic DRAM
  * bytes (rows x 4W for the hidden and carry outputs, 4W per carried input row
@@ -541,6 +543,16 @@ gm_status gm_ctx_kernel_stats(gm_ctx* ctx, int* launches, double* ms, double* by
  * ran beside the rollout of later stages: gm_settings chunk_mb).  GM_ERR_INVALID_ARG for
  * an index out of range. */
 gm_status gm_ctx_kernel_launch(gm_ctx* ctx, int i, double* ms, double* bytes, int* ctas);
+
+/* Stage timeline of matrix-free condensing (gm_settings.condensing = 1; GM_ERR_INVALID_ARG
+ * on another context).  When on, gm_rti_step records a timing event where the rollout and the
+ * tangent pass start, one after each rollout stage and one after each tangent stage (inside
+ * the captured graph in graph mode).  gm_ctx_stage_times waits for the last recorded step and
+ * writes, for k = 0..N-1, the milliseconds from the start to the end of rollout stage k
+ * (roll_ms[k]) and of tangent stage k (tan_ms[k]); caller-owned host arrays of N floats.
+ * GM_ERR_INVALID_ARG while timing is off. */
+gm_status gm_ctx_set_stage_timing(gm_ctx* ctx, int on);
+gm_status gm_ctx_stage_times(gm_ctx* ctx, float* roll_ms, float* tan_ms);
 
 /* ------------------------------------------------------------------------
  * Learned ADMM warm start (no paper counterpart; an added systems pattern).

@@ -143,6 +143,8 @@ def _load():
         "gm_ctx_kernel_stats": ([vp, C.POINTER(C.c_int)] + [C.POINTER(C.c_double)] * 3, C.c_int),
         "gm_ctx_kernel_launch": ([vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)],
                                  C.c_int),
+        "gm_ctx_set_stage_timing": ([vp, C.c_int], C.c_int),
+        "gm_ctx_stage_times": ([vp, vp, vp], C.c_int),
         "gm_qp_solve_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(Settings)] + [vp] * 10, C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -159,7 +161,8 @@ HEADER_FUNCTIONS = ("gm_last_error", "gm_version", "gm_graph_create", "gm_graph_
                     "gm_qp_solve", "gm_qp_solve_ipm", "gm_rti_step", "gm_ctx_reset", "gm_ctx_info",
                     "gm_ctx_set_timing", "gm_ctx_phase_ms", "gm_launch_count", "gm_qp_solve_noalloc",
                     "gm_ctx_set_graph", "gm_ctx_graph_state", "gm_ctx_set_kernel_timing",
-                    "gm_ctx_kernel_stats", "gm_ctx_kernel_launch", "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
+                    "gm_ctx_kernel_stats", "gm_ctx_kernel_launch", "gm_ctx_set_stage_timing", "gm_ctx_stage_times",
+                    "gm_ws_workspace_size", "gm_ws_create", "gm_ws_destroy",
                     "gm_ws_param_count", "gm_ws_set_params", "gm_ws_get_params", "gm_ws_forward",
                     "gm_ws_train_step", "gm_ws_grad", "gm_ws_features", "gm_batch_create",
                     "gm_batch_destroy", "gm_batch_rti_step", "gm_batch_state", "gm_batch_lanes", "gm_batch_set_lanes", "gm_batch_plan", "gm_ctx_set_warm", "gm_barrier_fold", "gm_ctx_set_timeout_spins", "gm_measure_peaks", "gm_measure_hbm",
@@ -259,6 +262,19 @@ def gm_ctx_kernel_launch(ctx, i):
     ms, by, n = C.c_double(), C.c_double(), C.c_int()
     _check("gm_ctx_kernel_launch", _lib.gm_ctx_kernel_launch(ctx, int(i), C.byref(ms), C.byref(by), C.byref(n)))
     return dict(ms=ms.value, bytes=by.value, ctas=n.value)
+
+
+def gm_ctx_set_stage_timing(ctx, on):
+    _check("gm_ctx_set_stage_timing", _lib.gm_ctx_set_stage_timing(ctx, 1 if on else 0))
+
+
+def gm_ctx_stage_times(ctx, N):
+    """Last recorded step's stage timeline (matrix-free contexts): (roll_ms[N], tan_ms[N]),
+    milliseconds from the start of the rollout to the end of each rollout and tangent stage."""
+    roll = (C.c_float * N)()
+    tan = (C.c_float * N)()
+    _check("gm_ctx_stage_times", _lib.gm_ctx_stage_times(ctx, roll, tan))
+    return list(roll), list(tan)
 
 
 def gm_ctx_graph_state(ctx):

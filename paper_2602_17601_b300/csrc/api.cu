@@ -36,6 +36,67 @@ static int row_of(const std::vector<int>& node, const std::vector<int>& ptr, int
 }
 
 // Supports of the forward-mode sensitivity columns (matrix-free condensing, struct Tangents).
+// Row contexts of the tangent launches (struct Tangents): per (stage k, layer l), tangent t =
+// i nu + a, the support's positions p in actuator a's hop order.  The row of node n (edge q) in a
+// layer with radius R is that layer's offset of t plus n's (q's) position, if the position lies
+// within the first count(a, R) of the order, else -1.
+static void build_tangent_ctx(const gm_graph& g, int K, int N, Tangents& T) {
+    const int M = g.M, E = g.E, nu = g.nu, R1 = T.Rmax + 1, L = N * nu + 1;
+    auto ncount = [&](int a, int R) { return R < 0 ? 0 : T.ncnt[(size_t)a * R1 + std::min(R, T.Rmax)]; };
+    auto ecount = [&](int a, int R) { return R < 0 ? 0 : T.ecnt[(size_t)a * R1 + std::min(R, T.Rmax)]; };
+    T.nbase.assign((size_t)N * (K + 1), 0);
+    T.ebase.assign((size_t)N * (K + 1), 0);
+    long nb = 0, eb = 0;
+    for (int k = 0; k < N; ++k)
+        for (int l = 0; l <= K; ++l) {
+            const size_t kl = (size_t)k * (K + 1) + l, base = kl * L;
+            T.nbase[kl] = nb;
+            T.ebase[kl] = eb;
+            nb += T.noff[base + (k + 1) * nu];
+            eb += T.eoff[base + (k + 1) * nu];
+        }
+    T.nctx.assign((size_t)4 * nb, -1);
+    T.ectx.assign((size_t)4 * eb, -1);
+    for (int k = 0; k < N; ++k)
+        for (int l = 0; l <= K; ++l) {
+            const size_t kl = (size_t)k * (K + 1) + l, base = kl * L, pbase = base - (size_t)L;   // layer l - 1
+            for (int t = 0; t < (k + 1) * nu; ++t) {
+                const int i = t / nu, a = t % nu, r0 = K * (k - i);
+                // node rows of layer l (radius r0 + l)
+                int* nc = T.nctx.data() + 4 * (T.nbase[kl] + T.noff[base + t]);
+                const int nn = T.noff[base + t + 1] - T.noff[base + t];
+                const int nprev = l > 0 ? ncount(a, r0 + l - 1) : 0;
+                for (int p = 0; p < nn; ++p) {
+                    const int n = T.norder[(size_t)a * M + p];
+                    nc[4 * p] = p < nprev ? T.noff[pbase + t] + p : -1;
+                    nc[4 * p + 1] = t;
+                    nc[4 * p + 2] = n;
+                    nc[4 * p + 3] = i < k ? 1 : 0;
+                }
+                if (E == 0) continue;
+                // edge rows of layer l
+                int* ec = T.ectx.data() + 4 * (T.ebase[kl] + T.eoff[base + t]);
+                const int ne = T.eoff[base + t + 1] - T.eoff[base + t];
+                // the previous edge layer: the encoder's (radius r0, none for i = k) for l = 1
+                const int Rep = l == 1 ? (i < k ? r0 : -1) : r0 + l - 2;
+                const int eprev = l > 0 ? ecount(a, Rep) : 0;
+                const int np1 = l > 0 ? ncount(a, r0 + l - 1) : 0;
+                for (int p = 0; p < ne; ++p) {
+                    const int q = T.eorder[(size_t)a * E + p];
+                    if (l == 0) {
+                        ec[4 * p] = g.dst[q]; ec[4 * p + 1] = g.src[q]; ec[4 * p + 2] = q; ec[4 * p + 3] = t;
+                    } else {
+                        const int pd = T.npos[(size_t)a * M + g.dst[q]], ps = T.npos[(size_t)a * M + g.src[q]];
+                        ec[4 * p] = pd < np1 ? T.noff[pbase + t] + pd : -1;
+                        ec[4 * p + 1] = ps < np1 ? T.noff[pbase + t] + ps : -1;
+                        ec[4 * p + 2] = q;
+                        ec[4 * p + 3] = p < eprev ? T.eoff[pbase + t] + p : -1;
+                    }
+                }
+            }
+        }
+}
+
 static void build_tangents(const gm_graph& g, int K, int N, Tangents& T) {
     const int M = g.M, E = g.E, nu = g.nu;
     T.Rmax = K * N;
@@ -105,6 +166,7 @@ static void build_tangents(const gm_graph& g, int K, int N, Tangents& T) {
             T.max_nrows = std::max(T.max_nrows, on);
             T.max_erows = std::max(T.max_erows, oe);
         }
+    build_tangent_ctx(g, K, N, T);
 }
 
 static void build_cones(const gm_graph& g, int K, Cones& C) {
@@ -458,6 +520,8 @@ static void plan(gm_ctx* c, Carver& cv) {
         c->dtan.ecnt = cv.take<int>(Tn.ecnt.size());
         c->dtan.noff = cv.take<int>(Tn.noff.size());
         c->dtan.eoff = cv.take<int>(Tn.eoff.size());
+        c->dtan.nctx = cv.take<int4>(Tn.nctx.size() / 4 + 1);
+        c->dtan.ectx = cv.take<int4>(Tn.ectx.size() / 4 + 1);
         c->d_thA = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
         c->d_thB = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
         c->d_tagg = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
@@ -715,6 +779,8 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
         rs.push_back(up(c->dtan.ecnt, Tn.ecnt, st));
         rs.push_back(up(c->dtan.noff, Tn.noff, st));
         rs.push_back(up(c->dtan.eoff, Tn.eoff, st));
+        rs.push_back(up(reinterpret_cast<int*>(c->dtan.nctx), Tn.nctx, st));
+        rs.push_back(up(reinterpret_cast<int*>(c->dtan.ectx), Tn.ectx, st));
     }
     // ADMM: co-resident CTAs (cooperative launch); the row split is made on the device per solve
     {
@@ -1331,6 +1397,37 @@ gm_status gm_ctx_set_kernel_timing(gm_ctx* ctx, int on) {
     }
     ctx->ktiming = on != 0;
     ctx->kev_n = 0;
+    return GM_OK;
+}
+
+gm_status gm_ctx_set_stage_timing(gm_ctx* ctx, int on) {
+    clear_error();
+    GM_CHECK_ARG(ctx, "ctx is NULL");
+    GM_CHECK_ARG(ctx->s.condensing == 1, "stage timing needs a context created with gm_settings.condensing = 1");
+    while (on && (int)ctx->sev.size() < 2 * ctx->N + 1) {
+        cudaEvent_t ev;
+        GM_CUDA_TRY(cudaEventCreate(&ev));
+        ctx->sev.push_back(ev);
+    }
+    if ((on != 0) != ctx->stiming && ctx->graph_exec) {     // the captured step changes: capture anew
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+        ctx->graph_key.clear();
+    }
+    ctx->stiming = on != 0;
+    return GM_OK;
+}
+
+gm_status gm_ctx_stage_times(gm_ctx* ctx, float* roll_ms, float* tan_ms) {
+    clear_error();
+    GM_CHECK_ARG(ctx && roll_ms && tan_ms, "NULL argument");
+    GM_CHECK_ARG(ctx->stiming && (int)ctx->sev.size() >= 2 * ctx->N + 1, "stage timing is off");
+    const int N = ctx->N;
+    GM_CUDA_TRY(cudaEventSynchronize(ctx->sev[2 * N]));
+    for (int k = 0; k < N; ++k) {
+        GM_CUDA_TRY(cudaEventElapsedTime(&roll_ms[k], ctx->sev[0], ctx->sev[1 + k]));
+        GM_CUDA_TRY(cudaEventElapsedTime(&tan_ms[k], ctx->sev[0], ctx->sev[1 + N + k]));
+    }
     return GM_OK;
 }
 

@@ -100,11 +100,20 @@ struct Tangents {
     // none for i = k; edge layer l >= 1 K (k - i) + l - 1
     std::vector<int> noff, eoff;                   // [N][K + 1][N nu + 1]
     long max_nrows = 0, max_erows = 0;
+    // Row contexts of every launch, 4 ints per row, launch (k, l) from row nbase / ebase[k (K + 1) + l]:
+    //   node row (t, n):  {row of n in node layer l - 1 (-1: outside it or l = 0), t, n, 1 if i < k}
+    //   edge row (t, q), layer 0:  {dst q, src q, q, t}
+    //   edge row (t, q), layer l >= 1:  {row of dst q, row of src q in node layer l - 1,
+    //                                    q, row of q in edge layer l - 1}   (-1: outside)
+    // They depend only on the graph, K and N, so they are built once per context.
+    std::vector<int> nctx, ectx;
+    std::vector<long> nbase, ebase;                // [N (K + 1)]
 };
 struct DTangents {
     int *norder = nullptr, *npos = nullptr, *ncnt = nullptr;
     int *eorder = nullptr, *epos = nullptr, *ecnt = nullptr;
     int *noff = nullptr, *eoff = nullptr;
+    int4 *nctx = nullptr, *ectx = nullptr;         // row contexts (struct Tangents)
 };
 
 }  // namespace gmi
@@ -208,10 +217,15 @@ struct gm_ctx {
     std::vector<std::array<cudaEvent_t, 2>> kev;
     std::vector<double> kev_bytes, kev_flops;
     std::vector<int> kev_ctas;   // CTAs of each timed launch (fewer than the SMs while the rollout runs beside it)
+    // stage timeline of the overlapped rollout and tangent pass: sev[0] where both start,
+    // sev[1 + k] after rollout stage k, sev[1 + N + k] after tangent stage k (timing events)
+    bool stiming = false;
+    std::vector<cudaEvent_t> sev;
 
     ~gm_ctx() {
         for (auto& e : kev)
             for (auto ev : e) cudaEventDestroy(ev);
+        for (auto ev : sev) cudaEventDestroy(ev);
         for (auto& e : events)
             for (auto ev : e) cudaEventDestroy(ev);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);

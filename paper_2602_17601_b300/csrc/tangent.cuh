@@ -20,12 +20,16 @@
 namespace gmi {
 
 // Edge rows of a layer from which its first layer runs on per-node projections (NodeProjTan +
-// EdgeMpTan) instead of whole per edge row (EdgeMpTanK3).  Closed-loop step at the chain of
-// 1000: 8.45 ms from 40k or 100k rows, 8.55 ms without projections (no layer reaches 200k).
-constexpr long kTanSplitRows = 50000;
+// EdgeMpTan) instead of whole per edge row (EdgeMpTanK3).  Tangent pass of the closed-loop step
+// at the chain of 1000 (last tangent stage done, cold ADMM step): 6.85 / 8.65 ms from 20k rows,
+// 6.83 / 8.63 from 30k, 6.79 / 8.56 from 50k, 6.76 / 8.50 from 100k (no layer reaches 200k).
+constexpr long kTanSplitRows = 100000;
 
-// Row -> (tangent, position in its support) of one (stage, layer) launch.
+// Row -> (tangent, position in its support) of one (stage, layer) launch.  The ops read each
+// row's context from the launch's slice of the context's tables (struct Tangents: one 16-byte
+// load); off, find and the order tables remain for the counts and the message sum.
 struct TanBase : BwdBase {
+    const int4* ctx;         // row contexts of this launch, [rows]
     const int* off;          // [T + 1] row offsets of the tangents in this launch
     int T, nu, K, k, M, E, Rmax;
     const int *norder, *npos, *ncnt, *eorder, *epos, *ecnt;
@@ -63,11 +67,10 @@ struct NodeEncTan : TanBase {
     __device__ RowCtx prep(long r) const {
         RowCtx x{0, 0, 0, 0, 0, -1};
         if (r < 0) return x;
-        const int t = find(r), i = t / nu, a = t % nu;
-        const int n = norder[a * M + (int)(r - off[t])];
-        x.a = (int)r; x.b = n; x.c = t; x.d = n;
-        x.e = i < k ? 1 : 0;
-        x.f = (i == k && act[a] == n) ? 6 + a : -1;
+        const int4 v = __ldg(ctx + r);               // {-, t, n, i < k}
+        const int a = v.y % nu;
+        x.a = (int)r; x.b = v.z; x.c = v.y; x.d = v.z; x.e = v.w;
+        x.f = (v.w == 0 && act[a] == v.z) ? 6 + a : -1;
         return x;
     }
     __device__ float in(const RowCtx& x, int kk) const {
@@ -88,9 +91,8 @@ struct EdgeEncTan : TanBase {
     __device__ RowCtx prep(long r) const {
         RowCtx x{0, 0, 0, 0, 0, 0};
         if (r < 0) return x;
-        const int t = find(r), a = t % nu;
-        const int q = eorder[a * E + (int)(r - off[t])];
-        x.a = (int)r; x.b = dst[q]; x.c = src[q]; x.d = q; x.e = t;
+        const int4 v = __ldg(ctx + r);               // {dst, src, q, t}
+        x.a = (int)r; x.b = v.x; x.c = v.y; x.d = v.z; x.e = v.w;
         return x;
     }
     __device__ float in(const RowCtx& x, int kk) const {
@@ -116,14 +118,8 @@ struct EdgeMpTanK3 : TanBase {
     __device__ RowCtx prep(long r) const {
         RowCtx x{0, -1, -1, 0, -1, 0};
         if (r < 0) return x;
-        const int t = find(r), i = t / nu, a = t % nu;
-        const int q = eorder[a * E + (int)(r - off[t])];
-        const int r0 = K * (k - i);
-        x.a = (int)r; x.d = q;
-        x.b = node_row(noff_prev, t, a, dst[q], r0 + Rn_prev_base);
-        x.c = node_row(noff_prev, t, a, src[q], r0 + Rn_prev_base);
-        const int Re = (Re_prev_base < 0 && i == k) ? -1 : r0 + (Re_prev_base < 0 ? 0 : Re_prev_base);
-        x.e = edge_row(eoff_prev, t, a, q, Re);
+        const int4 v = __ldg(ctx + r);               // {dst row, src row, q, previous edge row}
+        x.a = (int)r; x.b = v.x; x.c = v.y; x.d = v.z; x.e = v.w;
         return x;
     }
     __device__ float in(const RowCtx& x, int kk) const {
@@ -183,15 +179,10 @@ struct EdgeMpTan : TanBase {
     __device__ RowCtx prep(long r) const {
         RowCtx x{0, -1, -1, 0, -1, 0};
         if (r < 0) return x;
-        const int t = find(r), i = t / nu, a = t % nu;
-        const int q = eorder[a * E + (int)(r - off[t])];
-        const int r0 = K * (k - i);
-        x.a = (int)r; x.d = q;
-        x.b = node_row(noff_prev, t, a, dst[q], r0 + Rn_prev_base);
-        x.c = node_row(noff_prev, t, a, src[q], r0 + Rn_prev_base);
-        // the edge encoder has no rows for the tangents of stage k (their x tangent is zero)
-        const int Re = (Re_prev_base < 0 && i == k) ? -1 : r0 + (Re_prev_base < 0 ? 0 : Re_prev_base);
-        x.e = edge_row(eoff_prev, t, a, q, Re);
+        // {dst row, src row, q, previous edge row}; the edge encoder has no rows for the tangents
+        // of stage k (their x tangent is zero)
+        const int4 v = __ldg(ctx + r);
+        x.a = (int)r; x.b = v.x; x.c = v.y; x.d = v.z; x.e = v.w;
         return x;
     }
     __device__ float in(const RowCtx& x, int kk) const { return x.e >= 0 ? te_prev[(long)x.e * W + kk] : 0.f; }
@@ -247,10 +238,8 @@ struct NodeMpTan : TanBase {
     __device__ RowCtx prep(long r) const {
         RowCtx x{0, -1, 0, 0, 0, 0};
         if (r < 0) return x;
-        const int t = find(r), i = t / nu, a = t % nu;
-        const int n = norder[a * M + (int)(r - off[t])];
-        x.a = (int)r; x.d = n;
-        x.b = node_row(noff_prev, t, a, n, K * (k - i) + Rn_prev_base);
+        const int4 v = __ldg(ctx + r);               // {previous row, t, n, -}
+        x.a = (int)r; x.b = v.x; x.d = v.z;
         return x;
     }
     __device__ float in(const RowCtx& x, int kk) const {
@@ -288,9 +277,8 @@ struct DecTan : TanBase {
     __device__ RowCtx prep(long r) const {
         RowCtx x{0, 0, 0, 0, 0, 0};
         if (r < 0) return x;
-        const int t = find(r), i = t / nu, a = t % nu;
-        const int n = norder[a * M + (int)(r - off[t])];
-        x.a = (int)r; x.b = n; x.c = t; x.d = n; x.e = i < k ? 1 : 0;
+        const int4 v = __ldg(ctx + r);               // {-, t, n, i < k}
+        x.a = (int)r; x.b = v.z; x.c = v.y; x.d = v.z; x.e = v.w;
         return x;
     }
     __device__ float in(const RowCtx& x, int kk) const { return th[(long)x.a * W + kk]; }
@@ -309,8 +297,8 @@ struct DecTan : TanBase {
 // Message sum of layer l for every node row (tangent t, node n): sum over the edges into n that
 // lie in the edge layer's support.  One warp per row, four columns per lane.
 __global__ void tan_agg_kernel(long rows, int T, int nu, int K, int k, int M, int E, int Rmax, int W,
-                               const int* __restrict__ noff, const int* __restrict__ eoff, int Re_base,
-                               const int* __restrict__ norder, const int* __restrict__ epos,
+                               const int4* __restrict__ nctx, const int* __restrict__ eoff, int Re_base,
+                               const int* __restrict__ epos,
                                const int* __restrict__ ecnt, const int* __restrict__ in_ptr,
                                const float* __restrict__ te, float* __restrict__ tagg) {
     const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -320,14 +308,8 @@ __global__ void tan_agg_kernel(long rows, int T, int nu, int K, int k, int M, in
         pdl_launch_dependents();
         return;
     }
-    int lo = 0, hi = T;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (noff[mid] <= r) lo = mid;
-        else hi = mid;
-    }
-    const int t = lo, i = t / nu, a = t % nu;
-    const int n = norder[a * M + (int)(r - noff[t])];
+    const int4 v = __ldg(nctx + r);              // {-, t, n, -}
+    const int t = v.y, i = t / nu, a = t % nu, n = v.z;
     const int R = K * (k - i) + Re_base;
     const int cnt = ecnt[a * (Rmax + 1) + min(R, Rmax)];
     for (int c0 = lane * 4; c0 < W; c0 += 128) {
@@ -364,6 +346,8 @@ static void fill_tan(Op& op, const gm_ctx* c, const MlpOff& m, int k, int layer_
     const int L = c->N * c->nu + 1;
     const int* offs = edge ? c->dtan.eoff : c->dtan.noff;
     op.off = offs + (long)(k * (c->K + 1) + layer_off) * L;
+    op.ctx = (edge ? c->dtan.ectx : c->dtan.nctx) +
+             (edge ? T.ebase : T.nbase)[(size_t)k * (c->K + 1) + layer_off];
     const std::vector<int>& hoff = edge ? T.eoff : T.noff;
     const int Tk = (k + 1) * c->nu;
     op.rows = hoff[(size_t)(k * (c->K + 1) + layer_off) * L + Tk];
@@ -475,9 +459,9 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
             if (c->E > 0) {
                 GM_CUDA_TRY(launch_pdl(c->pdl, tan_agg_kernel, dim3((unsigned)cdiv(nrows * 32, 256)), dim3(256), 0, st,
                                        nrows, (k + 1) * nu, nu, K, k, M, c->E, c->tan.Rmax, W,
-                                       (const int*)(c->dtan.noff + (long)(k * (K + 1) + l) * L),
+                                       (const int4*)(c->dtan.nctx + c->tan.nbase[(size_t)k * (K + 1) + l]),
                                        (const int*)(c->dtan.eoff + (long)(k * (K + 1) + l) * L), l - 1,
-                                       (const int*)c->dtan.norder, (const int*)c->dtan.epos,
+                                       (const int*)c->dtan.epos,
                                        (const int*)c->dtan.ecnt, (const int*)c->d_in_ptr, (const float*)te[l & 1],
                                        c->d_tagg));
             } else {
@@ -545,14 +529,18 @@ gm_status gnn_rollout_sensitivities(gm_ctx* c, const float* x0, const float* u_h
     GM_CUDA_TRY(cudaEventRecord(c->ev_roll, st));
     GM_CUDA_TRY(cudaStreamWaitEvent(rs, c->ev_roll, 0));
     if (ts != st) GM_CUDA_TRY(cudaStreamWaitEvent(ts, c->ev_roll, 0));
+    const bool tl = c->stiming && (int)c->sev.size() >= 2 * N + 1;
+    if (tl) GM_CUDA_TRY(record_kev(c->sev[0], rs));
     if (x_hat != x0) GM_CUDA_TRY(cudaMemcpyAsync(x_hat, x0, sizeof(float) * M * 6, cudaMemcpyDeviceToDevice, rs));
     GM_TRY(tangent_clear(c, ts));
     for (int k = 0; k < N; ++k) {
         GM_TRY(forward_stage(c, k, x_hat + (long)k * M * 6, u_hat + (long)k * c->nu, x_hat + (long)(k + 1) * M * 6,
                              rs));
         GM_CUDA_TRY(cudaEventRecord(c->ev_tan[k], rs));
+        if (tl) GM_CUDA_TRY(record_kev(c->sev[1 + k], rs));
         GM_CUDA_TRY(cudaStreamWaitEvent(ts, c->ev_tan[k], 0));
         GM_TRY(tangent_stage(c, k, ts));
+        if (tl) GM_CUDA_TRY(record_kev(c->sev[1 + N + k], ts));
     }
     GM_TRY(tangent_offset(c, u_hat, ts));
     if (ts != st) {   // join: the tangent pass (which waited for the whole rollout) into st

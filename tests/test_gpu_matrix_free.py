@@ -150,3 +150,25 @@ def test_matrix_free_contexts_in_a_batch(lib):
             assert p.read_stats()["converged"] == 1, (k, i)
             U = p._U.cpu().numpy()
             assert np.abs(U - alone[i][k]).max() <= 10 * wl.tol / wl.rho, (k, i, np.abs(U - alone[i][k]).max())
+
+
+def test_stage_timeline(lib):
+    """gm_ctx_stage_times on a graph-replayed matrix-free step: every tangent stage ends after
+    the rollout stage it reads and after the tangent stage before it; rejected while off and on a
+    Jacobian context."""
+    from paper_2602_17601_b300 import GMError
+    import paper_2602_17601_b300 as gm
+    wl = small_chain()
+    p = lib.RTIProblem.from_workload(wl, condensing=1, graph=True)
+    with pytest.raises(GMError):
+        gm.gm_ctx_stage_times(p.ctx, wl.N)
+    gm.gm_ctx_set_stage_timing(p.ctx, True)
+    for _ in range(2):
+        p.step(wl.x0)
+    roll, tan = gm.gm_ctx_stage_times(p.ctx, wl.N)
+    assert all(t >= r for r, t in zip(roll, tan))
+    assert all(b >= a for a, b in zip(tan, tan[1:])) and all(b >= a for a, b in zip(roll, roll[1:]))
+    assert roll[0] > 0
+    jp = lib.RTIProblem.from_workload(wl)
+    with pytest.raises(GMError):
+        gm.gm_ctx_set_stage_timing(jp.ctx, True)
