@@ -329,9 +329,10 @@ struct DecFwd : FwdBase {
 };
 
 __global__ void agg_kernel(int M, int W, const int* __restrict__ in_ptr, const float* __restrict__ e,
-                           float* __restrict__ agg) {
+                           float* __restrict__ agg, int early) {
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     pdl_wait();                  // under programmatic serialization: the edge update is done
+    if (early) pdl_launch_dependents();
     if (t < (long)M * W) {
         int n = (int)(t / W), c = (int)(t % W);
         float s = 0.f;
@@ -483,6 +484,15 @@ uint32_t* edge_mask(const gm_ctx* c, int k, int layer) {
     return c->d_mask_edge + ((long)(k * (c->K + 1) + layer) * c->E) * (c->W / 32);
 }
 
+// Whether the rollout's kernels let the next one of the stage start its prologue as soon as all
+// of their own CTAs have started (TcW::early).  Off: with it on, the closed-loop step at the
+// chain of 1000 took 7.99 against 7.69 ms (the waiting CTAs hold SMs the tangent pass needs).
+constexpr bool kRollPdlEarly = false;
+static TcW roll_w(TcW w) {
+    w.early = kRollPdlEarly ? 1 : 0;
+    return w;
+}
+
 // One stage of F: encoders and the K message-passing steps into c->d_h (node latents), then,
 // when xn is given, the decoder and the Euler update x_{k+1} = xn.  ReLU masks of stage k kept.
 static gm_status forward_stage(gm_ctx* c, int k, const float* xk, const float* uk, float* xn, cudaStream_t st) {
@@ -498,35 +508,35 @@ static gm_status forward_stage(gm_ctx* c, int k, const float* xk, const float* u
         EdgeEncFwd ee{};
         fill_fwd(ee, c, 1, E, edge_mask(c, k, 0));
         ee.x = xk; ee.src = c->d_src; ee.dst = c->d_dst; ee.e = c->d_e; ee.W = W;
-        GM_TRY(launch_mlp(c, ee, tc_fwd(c, c->mlp[1]), fork ? c->side_stream : st, !fork));
+        GM_TRY(launch_mlp(c, ee, roll_w(tc_fwd(c, c->mlp[1])), fork ? c->side_stream : st, !fork));
     }
     if (fork) GM_CUDA_TRY(cudaEventRecord(c->ev_join, c->side_stream));
     NodeEncFwd ne{};
     fill_fwd(ne, c, 0, M, node_mask(c, k, 0));
     ne.x = xk; ne.u = uk; ne.act = c->d_act; ne.h = c->d_h; ne.W = W; ne.nu = c->nu;
-    GM_TRY(launch_mlp(c, ne, tc_fwd(c, c->mlp[0]), st));
+    GM_TRY(launch_mlp(c, ne, roll_w(tc_fwd(c, c->mlp[0])), st));
     if (fork) GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
     for (int t = 0; t < K; ++t) {
         if (E > 0) {
             EdgeMpFwd em{};
             fill_fwd(em, c, 2 + 2 * t, E, edge_mask(c, k, 1 + t));
             em.h = c->d_h; em.src = c->d_src; em.dst = c->d_dst; em.e = c->d_e; em.W = W;
-            GM_TRY(launch_mlp(c, em, tc_fwd(c, c->mlp[2 + 2 * t]), st));
+            GM_TRY(launch_mlp(c, em, roll_w(tc_fwd(c, c->mlp[2 + 2 * t])), st));
             GM_CUDA_TRY(launch_pdl(c->pdl, agg_kernel, dim3((unsigned)cdiv((long)M * W, 256)), dim3(256), 0, st, M, W,
-                                   (const int*)c->d_in_ptr, (const float*)c->d_e, c->d_agg));
+                                   (const int*)c->d_in_ptr, (const float*)c->d_e, c->d_agg, kRollPdlEarly ? 1 : 0));
         } else {
             GM_CUDA_TRY(cudaMemsetAsync(c->d_agg, 0, sizeof(float) * M * W, st));
         }
         NodeMpFwd nm{};
         fill_fwd(nm, c, 3 + 2 * t, M, node_mask(c, k, 1 + t));
         nm.h = c->d_h; nm.agg = c->d_agg; nm.W = W;
-        GM_TRY(launch_mlp(c, nm, tc_fwd(c, c->mlp[3 + 2 * t]), st));
+        GM_TRY(launch_mlp(c, nm, roll_w(tc_fwd(c, c->mlp[3 + 2 * t])), st));
     }
     if (xn) {
         DecFwd de{};
         fill_fwd(de, c, 2 + 2 * K, M, node_mask(c, k, K + 1));
         de.h = c->d_h; de.x = xk; de.xn = xn; de.dt = c->dt; de.W = W;
-        GM_TRY(launch_mlp(c, de, tc_fwd(c, c->mlp[2 + 2 * K]), st));
+        GM_TRY(launch_mlp(c, de, roll_w(tc_fwd(c, c->mlp[2 + 2 * K])), st));
     }
     return GM_OK;
 }

@@ -25,6 +25,16 @@ namespace gmi {
 // 6.83 / 8.63 from 30k, 6.79 / 8.56 from 50k, 6.76 / 8.50 from 100k (no layer reaches 200k).
 constexpr long kTanSplitRows = 100000;
 
+// Whether each tangent kernel lets the next one of the stage start its prologue (weight chunks,
+// row contexts, tensor-memory allocation) as soon as all of its own CTAs have started.  Off: the
+// waiting CTAs hold SMs that the rollout of later stages needs (closed-loop step at the chain of
+// 1000: 7.69 ms off, 8.52 ms on; 8.31 ms with the rollout's kernels early as well).
+constexpr bool kTanPdlEarly = false;
+static TcW tan_w(TcW w) {
+    w.early = kTanPdlEarly ? 1 : 0;
+    return w;
+}
+
 // Row -> (tangent, position in its support) of one (stage, layer) launch.  The ops read each
 // row's context from the launch's slice of the context's tables (struct Tangents: one 16-byte
 // load); off, find and the order tables remain for the counts and the message sum.
@@ -300,10 +310,11 @@ __global__ void tan_agg_kernel(long rows, int T, int nu, int K, int k, int M, in
                                const int4* __restrict__ nctx, const int* __restrict__ eoff, int Re_base,
                                const int* __restrict__ epos,
                                const int* __restrict__ ecnt, const int* __restrict__ in_ptr,
-                               const float* __restrict__ te, float* __restrict__ tagg) {
+                               const float* __restrict__ te, float* __restrict__ tagg, int early) {
     const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     pdl_wait();                  // launched with programmatic serialization: the edge update is done
+    if (early) pdl_launch_dependents();
     if (r >= rows) {
         pdl_launch_dependents();
         return;
@@ -390,14 +401,14 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
         EdgeEncTan op{};
         fill_tan(op, c, c->mlp[1], k, 0, true, edge_mask(c, k, 0));
         op.Sk = Sk; op.src = c->d_src; op.dst = c->d_dst; op.te = te[0];
-        GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[1]), fork ? c->tan_side : st, !fork));
+        GM_TRY(launch_mlp(c, op, tan_w(tc_fwd(c, c->mlp[1])), fork ? c->tan_side : st, !fork));
     }
     if (fork) GM_CUDA_TRY(cudaEventRecord(c->ev_tjoin, c->tan_side));
     {   // node encoder (node layer 0)
         NodeEncTan op{};
         fill_tan(op, c, c->mlp[0], k, 0, false, node_mask(c, k, 0));
         op.Sk = Sk; op.act = c->d_act; op.th = th[0];
-        GM_TRY(launch_mlp(c, op, tc_fwd(c, c->mlp[0]), st));
+        GM_TRY(launch_mlp(c, op, tan_w(tc_fwd(c, c->mlp[0])), st));
     }
     if (fork) GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_tjoin, 0));
     for (int l = 1; l <= K; ++l) {
@@ -416,7 +427,7 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
                 pj.kin = W; pj.nout = 2 * W;
                 pj.B1 = c->d_wts + m.eye; pj.B2 = c->d_wts + m.Pab;
                 pj.th_prev = th[(l - 1) & 1]; pj.P = c->d_tproj;
-                GM_TRY(launch_mlp(c, pj, tc_w(c, m.eyek, m.pabk, W, 2 * W), st));
+                GM_TRY(launch_mlp(c, pj, tan_w(tc_w(c, m.eyek, m.pabk, W, 2 * W)), st));
                 EdgeMpTan em{};
                 fill_tan(em, c, m, k, l, true, edge_mask(c, k, l));
                 em.kin = W;
@@ -431,7 +442,7 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
                 if (c->ktiming)
                     kt = kev_begin(c, 4.0 * W * (erows + ep) + 8.0 * W * np + (double)c->E * W / 8.0,
                                    4.0 * W * W * erows, (int)cdiv(erows, TC_M), st);
-                const TcW tw = tc_w(c, m.fck, m.fk2, W, m.out_p);
+                const TcW tw = tan_w(tc_w(c, m.fck, m.fk2, W, m.out_p));
                 if (c->s.precision == GM_PREC_MIXED && W == WS_W && tw.N2p == WS_W) {
                     GM_TRY(launch_ws_bwd(c, em, tw, st));     // warp-specialised persistent form
                 } else {
@@ -450,7 +461,7 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
                 if (c->ktiming)
                     kt = kev_begin(c, 4.0 * W * (erows + ep + np) + (double)c->E * W / 8.0, 8.0 * W * W * erows,
                                    (int)cdiv(erows, TC_M), st);
-                GM_TRY(launch_mlp(c, em, tc_fwd(c, m), st));
+                GM_TRY(launch_mlp(c, em, tan_w(tc_fwd(c, m)), st));
             }
             if (kt >= 0) GM_CUDA_TRY(record_kev(c->kev[kt][1], st));
         }
@@ -463,7 +474,7 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
                                        (const int*)(c->dtan.eoff + (long)(k * (K + 1) + l) * L), l - 1,
                                        (const int*)c->dtan.epos,
                                        (const int*)c->dtan.ecnt, (const int*)c->d_in_ptr, (const float*)te[l & 1],
-                                       c->d_tagg));
+                                       c->d_tagg, kTanPdlEarly ? 1 : 0));
             } else {
                 GM_CUDA_TRY(cudaMemsetAsync(c->d_tagg, 0, sizeof(float) * nrows * W, st));
             }
@@ -472,12 +483,12 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
         fill_tan(nm, c, c->mlp[3 + 2 * (l - 1)], k, l, false, node_mask(c, k, l));
         nm.noff_prev = noff_prev; nm.Rn_prev_base = l - 1;
         nm.th_prev = th[(l - 1) & 1]; nm.tagg = c->d_tagg; nm.th = th[l & 1];
-        GM_TRY(launch_mlp(c, nm, tc_fwd(c, c->mlp[3 + 2 * (l - 1)]), st));
+        GM_TRY(launch_mlp(c, nm, tan_w(tc_fwd(c, c->mlp[3 + 2 * (l - 1)])), st));
     }
     DecTan de{};
     fill_tan(de, c, c->mlp[2 + 2 * K], k, K, false, node_mask(c, k, K + 1));
     de.Sk = Sk; de.Sk1 = Sk1; de.th = th[K & 1]; de.dt = c->dt;
-    GM_TRY(launch_mlp(c, de, tc_fwd(c, c->mlp[2 + 2 * K]), st));
+    GM_TRY(launch_mlp(c, de, tan_w(tc_fwd(c, c->mlp[2 + 2 * K])), st));
     return GM_OK;
 }
 

@@ -38,6 +38,9 @@ struct TcW {
     const __nv_bfloat16* B2[3];  // [N2p][W]  (unused in single-product mode)
     int K1p, N2p;
     int* status;
+    // 1: let the next kernel of the stream start its prologue as soon as every CTA of this one
+    // has started (programmatic dependent launch), not when each finishes
+    int early;
 };
 
 template <class Op>
@@ -582,6 +585,7 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     __syncthreads();
     tc_fence_after();
     pdl_wait();
+    if (w.early) pdl_launch_dependents();
     tc_mlp_tile<W, Op, P>(op, w, row0, tsm, rc, tmem_base, S);
     // this CTA's work is done: the next kernel may start its prologue (triggered at the end, not
     // the start, so that early CTAs of the next kernel do not hold SMs for this kernel's

@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(WS_T, 1) tc_ws_bwd_kernel(Op op, TcW w) {
     __syncthreads();
     tc_fence_after();
     pdl_wait();                  // before any read of data an earlier kernel produced
+    if (w.early) pdl_launch_dependents();
     const unsigned tmem = tmem_base;
     auto tile_row0 = [&](int i) { return (blockIdx.x + (long)i * G) * TC_M; };
 
