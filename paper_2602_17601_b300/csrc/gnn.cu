@@ -382,6 +382,26 @@ static gm_status launch_tc(bool pdl, const Op& op, const TcW& tw, cudaStream_t s
     return GM_OK;
 }
 
+template <int W, int P, class Op1, class Op2>
+static gm_status launch_tc_seq(bool pdl, const Op1& op1, const TcW& tw1, const Op2& op2, const TcW& tw2,
+                               cudaStream_t st) {
+    constexpr size_t smem = tc_smem_bytes<W, false, P>() > TC_SMEM_MIN ? tc_smem_bytes<W, false, P>() : TC_SMEM_MIN;
+    for (const TcW* tw : {&tw1, &tw2})
+        if (tw->N2p > TC_TMEM_COLS || tw->N2p % 16 || tw->K1p % 16) {
+            set_error("tensor-core MLP shape out of range (K1p %d, N2p %d)", tw->K1p, tw->N2p);
+            return GM_ERR_INVALID_ARG;
+        }
+    static bool attr_set = false;
+    if (!attr_set) {
+        GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_seq_kernel<W, Op1, Op2, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    GM_CUDA_TRY(launch_pdl(pdl, tc_mlp_seq_kernel<W, Op1, Op2, P>, dim3((unsigned)cdiv(op1.rows, TC_M)), dim3(TC_T),
+                           smem, st, op1, tw1, op2, tw2));
+    return GM_OK;
+}
+
 template <int P, class Op>
 static gm_status launch_tc_w(bool pdl, int W, const Op& op, const TcW& tw, cudaStream_t st) {
     switch (W) {
@@ -442,6 +462,36 @@ static gm_status launch_mlp(const gm_ctx* c, const Op& op, const TcW& tw, cudaSt
             default: set_error("unsupported W %d", W); return GM_ERR_INVALID_ARG;
         }
     }
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
+// Two reverse-mode MLPs over the same rows, the second row-local on the first's outputs: one
+// tensor-core launch (tc_mlp_seq_kernel) in the mixed and BF16 forms, two launches in FP32.
+template <class Op1, class Op2>
+static gm_status launch_mlp_seq(const gm_ctx* c, const Op1& op1, const TcW& tw1, const Op2& op2, const TcW& tw2,
+                                cudaStream_t st) {
+    if (op1.rows != op2.rows) {
+        set_error("sequenced MLPs need the same rows (%ld, %ld)", op1.rows, op2.rows);
+        return GM_ERR_INVALID_ARG;
+    }
+    if (op1.rows <= 0) return GM_OK;
+    const int P = c->s.precision == GM_PREC_MIXED ? 2 : (c->s.precision == GM_PREC_BF16 ? 1 : 0);
+    if (P == 0) {
+        GM_TRY(launch_mlp(c, op1, tw1, st));
+        return launch_mlp(c, op2, tw2, st);
+    }
+    gm_status r = GM_OK;
+    switch (c->W * 4 + P) {
+        case 32 * 4 + 1: r = launch_tc_seq<32, 1>(c->pdl, op1, tw1, op2, tw2, st); break;
+        case 32 * 4 + 2: r = launch_tc_seq<32, 2>(c->pdl, op1, tw1, op2, tw2, st); break;
+        case 64 * 4 + 1: r = launch_tc_seq<64, 1>(c->pdl, op1, tw1, op2, tw2, st); break;
+        case 64 * 4 + 2: r = launch_tc_seq<64, 2>(c->pdl, op1, tw1, op2, tw2, st); break;
+        case 128 * 4 + 1: r = launch_tc_seq<128, 1>(c->pdl, op1, tw1, op2, tw2, st); break;
+        case 128 * 4 + 2: r = launch_tc_seq<128, 2>(c->pdl, op1, tw1, op2, tw2, st); break;
+        default: set_error("unsupported W %d", c->W); return GM_ERR_INVALID_ARG;
+    }
+    GM_TRY(r);
     GM_LAUNCH_CHECK();
     return GM_OK;
 }

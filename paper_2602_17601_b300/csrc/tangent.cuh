@@ -404,11 +404,31 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
         GM_TRY(launch_mlp(c, op, tan_w(tc_fwd(c, c->mlp[1])), fork ? c->tan_side : st, !fork));
     }
     if (fork) GM_CUDA_TRY(cudaEventRecord(c->ev_tjoin, c->tan_side));
+    // The projections of an edge layer's node blocks (NodeProjTan, layers of kTanSplitRows edge
+    // rows or more) and the decoder are row-local on the node rows the node encoder or the node
+    // update just wrote: each runs in the same launch as its producer (tc_mlp_seq_kernel).
+    auto projected = [&](int l) { return c->E > 0 && l <= K && tan_rows(c, k, l, true) >= kTanSplitRows; };
+    auto proj_op = [&](int l, NodeProjTan& pj, TcW& tw) {    // P of edge layer l from node layer l - 1
+        const MlpOff& m = c->mlp[2 + 2 * (l - 1)];
+        fill_tan(pj, c, m, k, l - 1, false, nullptr);
+        pj.kin = W; pj.nout = 2 * W;
+        pj.B1 = c->d_wts + m.eye; pj.B2 = c->d_wts + m.Pab;
+        pj.th_prev = th[(l - 1) & 1]; pj.P = c->d_tproj;
+        tw = tan_w(tc_w(c, m.eyek, m.pabk, W, 2 * W));
+    };
     {   // node encoder (node layer 0)
         NodeEncTan op{};
         fill_tan(op, c, c->mlp[0], k, 0, false, node_mask(c, k, 0));
         op.Sk = Sk; op.act = c->d_act; op.th = th[0];
-        GM_TRY(launch_mlp(c, op, tan_w(tc_fwd(c, c->mlp[0])), st));
+        const TcW tw = tan_w(tc_fwd(c, c->mlp[0]));
+        if (projected(1)) {
+            NodeProjTan pj{};
+            TcW tp{};
+            proj_op(1, pj, tp);
+            GM_TRY(launch_mlp_seq(c, op, tw, pj, tp, st));
+        } else {
+            GM_TRY(launch_mlp(c, op, tw, st));
+        }
     }
     if (fork) GM_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_tjoin, 0));
     for (int l = 1; l <= K; ++l) {
@@ -419,15 +439,9 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
             const long erows = tan_rows(c, k, l, true);
             const double ep = (double)tan_rows(c, k, l - 1, true), np = (double)tan_rows(c, k, l - 1, false);
             int kt = -1;
-            if (erows >= kTanSplitRows) {
-                // the node blocks of the first layer on the node rows of layer l - 1, then the edge
-                // rows with the e-block alone (K = W)
-                NodeProjTan pj{};
-                fill_tan(pj, c, m, k, l - 1, false, nullptr);
-                pj.kin = W; pj.nout = 2 * W;
-                pj.B1 = c->d_wts + m.eye; pj.B2 = c->d_wts + m.Pab;
-                pj.th_prev = th[(l - 1) & 1]; pj.P = c->d_tproj;
-                GM_TRY(launch_mlp(c, pj, tan_w(tc_w(c, m.eyek, m.pabk, W, 2 * W)), st));
+            if (projected(l)) {
+                // the edge rows with the e-block of the first layer alone (K = W); the node blocks
+                // came with the launch that wrote node layer l - 1
                 EdgeMpTan em{};
                 fill_tan(em, c, m, k, l, true, edge_mask(c, k, l));
                 em.kin = W;
@@ -483,13 +497,22 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
         fill_tan(nm, c, c->mlp[3 + 2 * (l - 1)], k, l, false, node_mask(c, k, l));
         nm.noff_prev = noff_prev; nm.Rn_prev_base = l - 1;
         nm.th_prev = th[(l - 1) & 1]; nm.tagg = c->d_tagg; nm.th = th[l & 1];
-        GM_TRY(launch_mlp(c, nm, tan_w(tc_fwd(c, c->mlp[3 + 2 * (l - 1)])), st));
+        const TcW tn = tan_w(tc_fwd(c, c->mlp[3 + 2 * (l - 1)]));
+        if (l == K) {   // the decoder and the Euler update into S_{k+1}
+            DecTan de{};
+            fill_tan(de, c, c->mlp[2 + 2 * K], k, K, false, node_mask(c, k, K + 1));
+            de.Sk = Sk; de.Sk1 = Sk1; de.th = th[K & 1]; de.dt = c->dt;
+            GM_TRY(launch_mlp_seq(c, nm, tn, de, tan_w(tc_fwd(c, c->mlp[2 + 2 * K])), st));
+        } else if (projected(l + 1)) {
+            NodeProjTan pj{};
+            TcW tp{};
+            proj_op(l + 1, pj, tp);
+            GM_TRY(launch_mlp_seq(c, nm, tn, pj, tp, st));
+        } else {
+            GM_TRY(launch_mlp(c, nm, tn, st));
+        }
     }
-    DecTan de{};
-    fill_tan(de, c, c->mlp[2 + 2 * K], k, K, false, node_mask(c, k, K + 1));
-    de.Sk = Sk; de.Sk1 = Sk1; de.th = th[K & 1]; de.dt = c->dt;
-    GM_TRY(launch_mlp(c, de, tan_w(tc_fwd(c, c->mlp[2 + 2 * K])), st));
-    return GM_OK;
+    return GM_OK;   // (K >= 1: the decoder ran with the last node update)
 }
 
 static gm_status tangent_offset(gm_ctx* c, const float* u_hat, cudaStream_t st) {

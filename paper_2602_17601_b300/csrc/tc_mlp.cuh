@@ -594,4 +594,41 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     tc_cta_teardown<F, P>(S, tmem_base);
 }
 
+// Two MLPs in sequence on the same 128 rows (tile blockIdx.x), where the second reads only what
+// the first wrote for those rows (row-local): one launch instead of two.  The first tile's
+// output stores become visible to the CTA's threads at the barrier between the two; the second
+// tile's weight chunks are copied once the first tile's buffers are free.  Both ops run in
+// reverse (mask) mode with the same rows.
+template <int W, class Op1, class Op2, int P>
+__global__ void __launch_bounds__(TC_T) tc_mlp_seq_kernel(Op1 op1, TcW w1, Op2 op2, TcW w2) {
+    static_assert(Op1::kMode == 1 && Op2::kMode == 1, "sequenced MLP tiles run in reverse mode");
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ RowCtx rc[TC_M];
+    __shared__ __align__(8) unsigned long long mbar[tc_nbuf<false, P>()];
+    __shared__ __align__(8) unsigned long long bbar[tc_nbuf<false, P>()];
+    __shared__ unsigned tmem_base;
+    TcTileState S;
+    tc_cta_init<false, P>(S, mbar, bbar);
+    const long row0 = (long)blockIdx.x * TC_M;
+    if (threadIdx.x == 0) tc_tile_prefetch<W, Op1, P>(w1, tsm, S);
+    for (int m = threadIdx.x; m < TC_M; m += TC_T) rc[m] = op1.prep(row0 + m < op1.rows ? row0 + m : -1);
+    tc_tmem_alloc(&tmem_base);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    pdl_wait();
+    bool ok = tc_mlp_tile<W, Op1, P>(op1, w1, row0, tsm, rc, tmem_base, S);
+    // the first tile's stores and its reads of shared and tensor memory are complete
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0 && ok) tc_tile_prefetch<W, Op2, P>(w2, tsm, S);
+    for (int m = threadIdx.x; m < TC_M; m += TC_T) rc[m] = op2.prep(row0 + m < op2.rows ? row0 + m : -1);
+    __syncthreads();
+    if (ok) tc_mlp_tile<W, Op2, P>(op2, w2, row0, tsm, rc, tmem_base, S);
+    pdl_launch_dependents();
+    tc_cta_teardown<false, P>(S, tmem_base);
+}
+
 }  // namespace gmi
