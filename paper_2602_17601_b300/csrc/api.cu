@@ -57,6 +57,8 @@ static void build_tangent_ctx(const gm_graph& g, int K, int N, Tangents& T) {
         }
     T.nctx.assign((size_t)4 * nb, -1);
     T.ectx.assign((size_t)4 * eb, -1);
+    T.aptr.assign((size_t)nb + 1, 0);
+    T.alist.clear();
     for (int k = 0; k < N; ++k)
         for (int l = 0; l <= K; ++l) {
             const size_t kl = (size_t)k * (K + 1) + l, base = kl * L, pbase = base - (size_t)L;   // layer l - 1
@@ -66,12 +68,19 @@ static void build_tangent_ctx(const gm_graph& g, int K, int N, Tangents& T) {
                 int* nc = T.nctx.data() + 4 * (T.nbase[kl] + T.noff[base + t]);
                 const int nn = T.noff[base + t + 1] - T.noff[base + t];
                 const int nprev = l > 0 ? ncount(a, r0 + l - 1) : 0;
+                const int ecnt_l = l > 0 ? ecount(a, r0 + l - 1) : 0;   // edge layer l (message sum)
                 for (int p = 0; p < nn; ++p) {
                     const int n = T.norder[(size_t)a * M + p];
                     nc[4 * p] = p < nprev ? T.noff[pbase + t] + p : -1;
                     nc[4 * p + 1] = t;
                     nc[4 * p + 2] = n;
                     nc[4 * p + 3] = i < k ? 1 : 0;
+                    T.aptr[(size_t)(T.nbase[kl] + T.noff[base + t] + p)] = (int)T.alist.size();
+                    if (l > 0)
+                        for (int q = g.in_ptr[n]; q < g.in_ptr[n + 1]; ++q) {
+                            const int pe = T.epos[(size_t)a * E + q];
+                            if (pe < ecnt_l) T.alist.push_back(T.eoff[base + t] + pe);
+                        }
                 }
                 if (E == 0) continue;
                 // edge rows of layer l
@@ -167,6 +176,7 @@ static void build_tangents(const gm_graph& g, int K, int N, Tangents& T) {
             T.max_erows = std::max(T.max_erows, oe);
         }
     build_tangent_ctx(g, K, N, T);
+    T.aptr[T.aptr.size() - 1] = (int)T.alist.size();
 }
 
 static void build_cones(const gm_graph& g, int K, Cones& C) {
@@ -522,6 +532,8 @@ static void plan(gm_ctx* c, Carver& cv) {
         c->dtan.eoff = cv.take<int>(Tn.eoff.size());
         c->dtan.nctx = cv.take<int4>(Tn.nctx.size() / 4 + 1);
         c->dtan.ectx = cv.take<int4>(Tn.ectx.size() / 4 + 1);
+        c->dtan.aptr = cv.take<int>(Tn.aptr.size());
+        c->dtan.alist = cv.take<int>(Tn.alist.size() + 1);
         c->d_thA = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
         c->d_thB = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
         c->d_tagg = cv.take<float>((size_t)std::max(1L, Tn.max_nrows) * W);
@@ -781,6 +793,8 @@ gm_status gm_ctx_create(const gm_graph* g, const gm_gnn* m, const gm_settings* s
         rs.push_back(up(c->dtan.eoff, Tn.eoff, st));
         rs.push_back(up(reinterpret_cast<int*>(c->dtan.nctx), Tn.nctx, st));
         rs.push_back(up(reinterpret_cast<int*>(c->dtan.ectx), Tn.ectx, st));
+        rs.push_back(up(c->dtan.aptr, Tn.aptr, st));
+        rs.push_back(up(c->dtan.alist, Tn.alist, st));
     }
     // ADMM: co-resident CTAs (cooperative launch); the row split is made on the device per solve
     {

@@ -108,12 +108,16 @@ struct Tangents {
     // They depend only on the graph, K and N, so they are built once per context.
     std::vector<int> nctx, ectx;
     std::vector<long> nbase, ebase;                // [N (K + 1)]
+    // message sums: node row g (index into nctx / 4) sums the edge rows alist[aptr[g] .. aptr[g + 1])
+    // of the same stage and layer, its in-edges within that edge layer's support, in edge order
+    std::vector<int> aptr, alist;
 };
 struct DTangents {
     int *norder = nullptr, *npos = nullptr, *ncnt = nullptr;
     int *eorder = nullptr, *epos = nullptr, *ecnt = nullptr;
     int *noff = nullptr, *eoff = nullptr;
     int4 *nctx = nullptr, *ectx = nullptr;         // row contexts (struct Tangents)
+    int *aptr = nullptr, *alist = nullptr;         // message-sum lists (struct Tangents)
 };
 
 }  // namespace gmi

@@ -304,12 +304,10 @@ struct DecTan : TanBase {
     }
 };
 
-// Message sum of layer l for every node row (tangent t, node n): sum over the edges into n that
-// lie in the edge layer's support.  One warp per row, four columns per lane.
-__global__ void tan_agg_kernel(long rows, int T, int nu, int K, int k, int M, int E, int Rmax, int W,
-                               const int4* __restrict__ nctx, const int* __restrict__ eoff, int Re_base,
-                               const int* __restrict__ epos,
-                               const int* __restrict__ ecnt, const int* __restrict__ in_ptr,
+// Message sum of layer l for every node row (tangent t, node n): the sum of the edge rows of its
+// in-edges within the edge layer's support (the context's list, in edge order).  One warp per
+// row, four columns per lane; up to eight edge rows are loaded at once.
+__global__ void tan_agg_kernel(long rows, int W, const int* __restrict__ aptr, const int* __restrict__ alist,
                                const float* __restrict__ te, float* __restrict__ tagg, int early) {
     const long r = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -319,15 +317,19 @@ __global__ void tan_agg_kernel(long rows, int T, int nu, int K, int k, int M, in
         pdl_launch_dependents();
         return;
     }
-    const int4 v = __ldg(nctx + r);              // {-, t, n, -}
-    const int t = v.y, i = t / nu, a = t % nu, n = v.z;
-    const int R = K * (k - i) + Re_base;
-    const int cnt = ecnt[a * (Rmax + 1) + min(R, Rmax)];
+    const int j0 = __ldg(aptr + r), j1 = __ldg(aptr + r + 1);
     for (int c0 = lane * 4; c0 < W; c0 += 128) {
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int q = in_ptr[n]; q < in_ptr[n + 1]; ++q) {
-            const int p = epos[a * E + q];
-            if (p < cnt) s = add4(s, ld4(te + ((long)eoff[t] + p) * W + c0));
+        for (int jb = j0; jb < j1; jb += 8) {
+            int idx[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) idx[u] = jb + u < j1 ? __ldg(alist + jb + u) : -1;
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = idx[u] >= 0 ? ld4(te + (long)idx[u] * W + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (idx[u] >= 0) s = add4(s, v[u]);
         }
         st4(tagg + r * W + c0, s);
     }
@@ -483,12 +485,9 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
         if (nrows > 0) {
             if (c->E > 0) {
                 GM_CUDA_TRY(launch_pdl(c->pdl, tan_agg_kernel, dim3((unsigned)cdiv(nrows * 32, 256)), dim3(256), 0, st,
-                                       nrows, (k + 1) * nu, nu, K, k, M, c->E, c->tan.Rmax, W,
-                                       (const int4*)(c->dtan.nctx + c->tan.nbase[(size_t)k * (K + 1) + l]),
-                                       (const int*)(c->dtan.eoff + (long)(k * (K + 1) + l) * L), l - 1,
-                                       (const int*)c->dtan.epos,
-                                       (const int*)c->dtan.ecnt, (const int*)c->d_in_ptr, (const float*)te[l & 1],
-                                       c->d_tagg, kTanPdlEarly ? 1 : 0));
+                                       nrows, W, (const int*)(c->dtan.aptr + c->tan.nbase[(size_t)k * (K + 1) + l]),
+                                       (const int*)c->dtan.alist, (const float*)te[l & 1], c->d_tagg,
+                                       kTanPdlEarly ? 1 : 0));
             } else {
                 GM_CUDA_TRY(cudaMemsetAsync(c->d_tagg, 0, sizeof(float) * nrows * W, st));
             }
