@@ -105,6 +105,12 @@ __global__ void keep_scan_kernel(int Mnc, const unsigned char* __restrict__ keep
 // ---------------------------------------------------------------- FP64 KKT certificate
 // kkt[0..n): A~'y (rows part), kkt[n]: max primal violation, kkt[n+1]: max wrong-sign y,
 // kkt[n+2]: max complementarity, all over the C~ rows.
+// FP64 runs at about 2 FMA per clock per SM here, so each row is first tested in FP32: with
+// s = sum_c |C~_rc U_c| (FP32), the FP32 dot lies within 64 s 2^-24 of the exact one (at most
+// 8 sequential FMAs per lane and 5 levels of the lane sum, and s itself within that factor), so a
+// row whose FP32 dot plus that bound is below d~_r and whose multiplier is 0 is strictly feasible:
+// it adds nothing to any of the four quantities (the primal violation is clamped at 0).  Only
+// the other rows take the FP64 evaluation, whose results are therefore unchanged.
 constexpr int KKT_MAXC = 8;   // columns per lane: n <= 256
 
 __device__ __forceinline__ void atomic_max_pos(double* p, double v) {
@@ -131,6 +137,25 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
         const int nm = (L + 31) >> 5;              // 32-column blocks the row reaches (warp-uniform)
         const long off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (long)wi * L;
         const double yr = y[n + r];
+        if (yr == 0.0) {                           // warp-uniform: the FP32 test of a row without multiplier
+            float d32 = 0.f, a32 = 0.f;
+#pragma unroll
+            for (int m = 0; m < KKT_MAXC; ++m) {
+                if (m >= nm) break;
+                const int c = lane + 32 * m;
+                if (c < L) {
+                    const float p = Ct[off + c] * (float)ud[m];
+                    d32 += p;
+                    a32 += fabsf(p);
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                d32 += __shfl_xor_sync(0xffffffffu, d32, o);
+                a32 += __shfl_xor_sync(0xffffffffu, a32, o);
+            }
+            // (1e-30: an absolute allowance for products below FP32's normal range)
+            if ((double)d32 + 64.0 * 5.9604644775390625e-08 * (double)a32 + 1e-30 < (double)dt[r]) continue;
+        }
         double dot = 0.0;
         if (yr != 0.0) {                           // warp-uniform: rows with a multiplier add C~_r' y_r
 #pragma unroll

@@ -163,6 +163,10 @@ def test_qp_parity(lib, constrained):
     cert = oqp.kkt_certificate(H64, g64, At, l, h, U, y)
     assert abs(st["kkt_stat"] - cert["stationarity"]) <= 1e-6 * max(1.0, cert["stationarity"]) + 1e-9
     assert st["kkt_prim"] <= 10 * wl.tol
+    # the row parts of the certificate (the library tests most rows in FP32 with a rounding bound
+    # first) equal the FP64 evaluation here on the same FP32 rows (H64, Ct64 are the FP32 data)
+    for key, ck in (("kkt_prim", "primal"), ("kkt_comp", "complementarity"), ("kkt_dual", "dual")):
+        assert abs(st[key] - cert[ck]) <= 1e-9 * max(1.0, abs(cert[ck])) + 1e-12, (key, st[key], cert[ck])
     # distance to the exact optimum is bounded by the dual residual / lambda_min(H)
     lam = np.linalg.eigvalsh(H64).min()
     assert np.abs(U - Ux).max() <= 2 * max(st["r_dual"], st["kkt_stat"]) / lam + 1e-5
