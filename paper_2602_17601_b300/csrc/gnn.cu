@@ -362,10 +362,10 @@ static cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <int W, int P, class Op>
-static gm_status launch_tc(bool pdl, const Op& op, const TcW& tw, cudaStream_t st) {
+template <int W, int P, int NB, class Op>
+static gm_status launch_tc_nb(bool pdl, const Op& op, const TcW& tw, cudaStream_t st) {
     constexpr bool F = (Op::kMode == 0);
-    constexpr size_t smem = tc_smem_bytes<W, F, P>() > TC_SMEM_MIN ? tc_smem_bytes<W, F, P>() : TC_SMEM_MIN;
+    constexpr size_t smem = tc_smem_bytes<W, F, P, NB>() > TC_SMEM_MIN ? tc_smem_bytes<W, F, P, NB>() : TC_SMEM_MIN;
     static_assert(W <= TC_NB, "GEMM1 width must fit the staged B chunk");
     if (tw.N2p > TC_TMEM_COLS || tw.N2p % 16 || tw.K1p % 16) {
         set_error("tensor-core MLP shape out of range (K1p %d, N2p %d)", tw.K1p, tw.N2p);
@@ -373,19 +373,34 @@ static gm_status launch_tc(bool pdl, const Op& op, const TcW& tw, cudaStream_t s
     }
     static bool attr_set = false;
     if (!attr_set) {
-        GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_kernel<W, Op, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_kernel<W, Op, P, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
         attr_set = true;
     }
-    GM_CUDA_TRY(launch_pdl(pdl, tc_mlp_kernel<W, Op, P>, dim3((unsigned)cdiv(op.rows, TC_M)), dim3(TC_T), smem, st, op,
-                           tw));
+    GM_CUDA_TRY(launch_pdl(pdl, tc_mlp_kernel<W, Op, P, NB>, dim3((unsigned)cdiv(op.rows, TC_M)), dim3(TC_T), smem, st,
+                           op, tw));
     return GM_OK;
 }
 
-template <int W, int P, class Op1, class Op2>
-static gm_status launch_tc_seq(bool pdl, const Op1& op1, const TcW& tw1, const Op2& op2, const TcW& tw2,
-                               cudaStream_t st) {
-    constexpr size_t smem = tc_smem_bytes<W, false, P>() > TC_SMEM_MIN ? tc_smem_bytes<W, false, P>() : TC_SMEM_MIN;
+// Reverse-pass launches of the mixed form at W = 128 with at most one tile per SM take
+// TC_NBUF_SMALL chunk buffers: each CTA has an SM to itself, so the larger shared memory costs
+// no residency, and the next weight chunk is copied while the current one multiplies (Jacobian
+// path 12.69 against 12.79 ms per step).  Not the tangent pass: beside the rollout its 128 KB
+// CTAs measured slower (7.55 against 7.42 ms per step).
+template <int W, int P, class Op>
+static gm_status launch_tc(bool pdl, const Op& op, const TcW& tw, cudaStream_t st, int sms) {
+    if constexpr (Op::kMode == 1) {
+        if constexpr (!Op::kTangent && W == 128 && P == 2 && TC_NBUF_SMALL > 1)
+            if (cdiv(op.rows, TC_M) <= sms) return launch_tc_nb<W, P, TC_NBUF_SMALL>(pdl, op, tw, st);
+    }
+    return launch_tc_nb<W, P, tc_nbuf<(Op::kMode == 0), P>()>(pdl, op, tw, st);
+}
+
+template <int W, int P, int NB, class Op1, class Op2>
+static gm_status launch_tc_seq_nb(bool pdl, const Op1& op1, const TcW& tw1, const Op2& op2, const TcW& tw2,
+                                  cudaStream_t st) {
+    constexpr size_t smem =
+        tc_smem_bytes<W, false, P, NB>() > TC_SMEM_MIN ? tc_smem_bytes<W, false, P, NB>() : TC_SMEM_MIN;
     for (const TcW* tw : {&tw1, &tw2})
         if (tw->N2p > TC_TMEM_COLS || tw->N2p % 16 || tw->K1p % 16) {
             set_error("tensor-core MLP shape out of range (K1p %d, N2p %d)", tw->K1p, tw->N2p);
@@ -393,21 +408,28 @@ static gm_status launch_tc_seq(bool pdl, const Op1& op1, const TcW& tw1, const O
         }
     static bool attr_set = false;
     if (!attr_set) {
-        GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_seq_kernel<W, Op1, Op2, P>,
+        GM_CUDA_TRY(cudaFuncSetAttribute(tc_mlp_seq_kernel<W, Op1, Op2, P, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set = true;
     }
-    GM_CUDA_TRY(launch_pdl(pdl, tc_mlp_seq_kernel<W, Op1, Op2, P>, dim3((unsigned)cdiv(op1.rows, TC_M)), dim3(TC_T),
-                           smem, st, op1, tw1, op2, tw2));
+    GM_CUDA_TRY(launch_pdl(pdl, tc_mlp_seq_kernel<W, Op1, Op2, P, NB>, dim3((unsigned)cdiv(op1.rows, TC_M)),
+                           dim3(TC_T), smem, st, op1, tw1, op2, tw2));
     return GM_OK;
 }
 
+template <int W, int P, class Op1, class Op2>
+static gm_status launch_tc_seq(bool pdl, const Op1& op1, const TcW& tw1, const Op2& op2, const TcW& tw2,
+                               cudaStream_t st, int sms) {
+    (void)sms;
+    return launch_tc_seq_nb<W, P, tc_nbuf<false, P>()>(pdl, op1, tw1, op2, tw2, st);
+}
+
 template <int P, class Op>
-static gm_status launch_tc_w(bool pdl, int W, const Op& op, const TcW& tw, cudaStream_t st) {
+static gm_status launch_tc_w(bool pdl, int W, const Op& op, const TcW& tw, cudaStream_t st, int sms) {
     switch (W) {
-        case 32: return launch_tc<32, P>(pdl, op, tw, st);
-        case 64: return launch_tc<64, P>(pdl, op, tw, st);
-        case 128: return launch_tc<128, P>(pdl, op, tw, st);
+        case 32: return launch_tc<32, P>(pdl, op, tw, st, sms);
+        case 64: return launch_tc<64, P>(pdl, op, tw, st, sms);
+        case 128: return launch_tc<128, P>(pdl, op, tw, st, sms);
         default: set_error("unsupported W %d", W); return GM_ERR_INVALID_ARG;
     }
 }
@@ -447,12 +469,12 @@ static gm_status launch_mlp(const gm_ctx* c, const Op& op, const TcW& tw, cudaSt
     const bool pdl = c->pdl && pdl_ok;
     if (c->s.precision == GM_PREC_MIXED) {
         if constexpr (Op::kMode == 0) {
-            GM_TRY(launch_tc_w<3>(pdl, W, op, tw, st));
+            GM_TRY(launch_tc_w<3>(pdl, W, op, tw, st, c->num_sms));
         } else {
-            GM_TRY(launch_tc_w<2>(pdl, W, op, tw, st));
+            GM_TRY(launch_tc_w<2>(pdl, W, op, tw, st, c->num_sms));
         }
     } else if (c->s.precision == GM_PREC_BF16) {
-        GM_TRY(launch_tc_w<1>(pdl, W, op, tw, st));
+        GM_TRY(launch_tc_w<1>(pdl, W, op, tw, st, c->num_sms));
     } else {
         int grid = cdiv(op.rows, BM);
         switch (W) {
@@ -483,12 +505,12 @@ static gm_status launch_mlp_seq(const gm_ctx* c, const Op1& op1, const TcW& tw1,
     }
     gm_status r = GM_OK;
     switch (c->W * 4 + P) {
-        case 32 * 4 + 1: r = launch_tc_seq<32, 1>(c->pdl, op1, tw1, op2, tw2, st); break;
-        case 32 * 4 + 2: r = launch_tc_seq<32, 2>(c->pdl, op1, tw1, op2, tw2, st); break;
-        case 64 * 4 + 1: r = launch_tc_seq<64, 1>(c->pdl, op1, tw1, op2, tw2, st); break;
-        case 64 * 4 + 2: r = launch_tc_seq<64, 2>(c->pdl, op1, tw1, op2, tw2, st); break;
-        case 128 * 4 + 1: r = launch_tc_seq<128, 1>(c->pdl, op1, tw1, op2, tw2, st); break;
-        case 128 * 4 + 2: r = launch_tc_seq<128, 2>(c->pdl, op1, tw1, op2, tw2, st); break;
+        case 32 * 4 + 1: r = launch_tc_seq<32, 1>(c->pdl, op1, tw1, op2, tw2, st, c->num_sms); break;
+        case 32 * 4 + 2: r = launch_tc_seq<32, 2>(c->pdl, op1, tw1, op2, tw2, st, c->num_sms); break;
+        case 64 * 4 + 1: r = launch_tc_seq<64, 1>(c->pdl, op1, tw1, op2, tw2, st, c->num_sms); break;
+        case 64 * 4 + 2: r = launch_tc_seq<64, 2>(c->pdl, op1, tw1, op2, tw2, st, c->num_sms); break;
+        case 128 * 4 + 1: r = launch_tc_seq<128, 1>(c->pdl, op1, tw1, op2, tw2, st, c->num_sms); break;
+        case 128 * 4 + 2: r = launch_tc_seq<128, 2>(c->pdl, op1, tw1, op2, tw2, st, c->num_sms); break;
         default: set_error("unsupported W %d", c->W); return GM_ERR_INVALID_ARG;
     }
     GM_TRY(r);
@@ -623,6 +645,7 @@ struct BwdBase {
     static constexpr bool kWsHid = false;      // warp-specialised kernel: store the masked hidden
     static constexpr bool kWsResid = false;    // warp-specialised kernel: out = A + product
     static constexpr bool kWsLand = false;     // warp-specialised kernel: rows by bulk copy (land_row)
+    static constexpr bool kTangent = false;    // an MLP of the tangent pass (matrix-free condensing)
     static constexpr bool kHidAdd = false;     // hid_add / hid_val: a per-row term added before the mask
     long rows;
     int kin, nout;

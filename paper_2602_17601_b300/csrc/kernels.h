@@ -17,6 +17,7 @@ inline __host__ __device__ int tc_chunk_b2(int rows) { return rows > 128 ? TC_CH
 constexpr int TC_CHUNK_F = 64;
 constexpr int TC_NBUF_F = 1;
 constexpr int TC_NBUF_MAX = 2;   // buffers the tile state tracks
+constexpr int TC_NBUF_SMALL = 2; // reverse-mode launches of at most one tile per SM (mixed form, W = 128)
 static_assert(TC_NBUF_F <= TC_NBUF_MAX, "forward chunk buffers exceed the tile state");
 inline __host__ __device__ int tc_chunk_b2_fwd(int rows) { return rows > 128 ? TC_CHUNK_F / 2 : TC_CHUNK_F; }
 inline __host__ __device__ long tc_tile_off(int n, int k, int kc) {

@@ -39,6 +39,7 @@ static TcW tan_w(TcW w) {
 // row's context from the launch's slice of the context's tables (struct Tangents: one 16-byte
 // load); off, find and the order tables remain for the counts and the message sum.
 struct TanBase : BwdBase {
+    static constexpr bool kTangent = true;
     const int4* ctx;         // row contexts of this launch, [rows]
     const int* off;          // [T + 1] row offsets of the tangents in this launch
     int T, nu, K, k, M, E, Rmax;

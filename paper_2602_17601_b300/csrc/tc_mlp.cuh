@@ -292,15 +292,15 @@ template <bool F, int P>
 __host__ __device__ constexpr int tc_nbuf() {
     return F ? TC_NBUF_F : 1;
 }
-template <int W, bool F, int P>
+template <int W, bool F, int P, int NB = tc_nbuf<F, P>()>
 __host__ __device__ constexpr size_t tc_region_a() {
-    return (size_t)P * ((size_t)tc_nbuf<F, P>() * TC_M * tc_kc<F, P>() * 2 > (size_t)TC_M * W * 2
-                            ? (size_t)tc_nbuf<F, P>() * TC_M * tc_kc<F, P>() * 2
+    return (size_t)P * ((size_t)NB * TC_M * tc_kc<F, P>() * 2 > (size_t)TC_M * W * 2
+                            ? (size_t)NB * TC_M * tc_kc<F, P>() * 2
                             : (size_t)TC_M * W * 2);
 }
-template <int W, bool F, int P>
+template <int W, bool F, int P, int NB = tc_nbuf<F, P>()>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
-    return tc_region_a<W, F, P>() + (size_t)tc_nbuf<F, P>() * P * TC_NB * tc_kc<F, P>() * 2;
+    return tc_region_a<W, F, P, NB>() + (size_t)NB * P * TC_NB * tc_kc<F, P>() * 2;
 }
 // Launch size: at least TC_SMEM_MIN, so that no more than two CTAs share an SM (what two
 // TC_TMEM_COLS allocations fill) and the output tile of tc_out_rows fits.
@@ -319,10 +319,10 @@ struct TcTileState {
 
 // Thread 0: bulk-copy weight chunk g of a tile (g < nch: the K chunks of B1; then the K chunks of
 // B2) into buffer g % NBUF.
-template <int W, bool F, int P>
+template <int W, bool F, int P, int NBUF = tc_nbuf<F, P>()>
 __device__ __forceinline__ void tc_load_chunk(const TcW& w, unsigned char* sB0, TcTileState& S, int g, int nch,
                                               int kc2) {
-    constexpr int KC = tc_kc<F, P>(), NBUF = tc_nbuf<F, P>(), B_BYTES = TC_NB * KC * 2;
+    constexpr int KC = tc_kc<F, P>(), B_BYTES = TC_NB * KC * 2;
     const int b = g % NBUF;
     unsigned char* dst = sB0 + (size_t)b * P * B_BYTES;
     if (g < nch) {
@@ -335,16 +335,15 @@ __device__ __forceinline__ void tc_load_chunk(const TcW& w, unsigned char* sB0, 
 }
 
 // Thread 0: the first weight chunks of a tile (issued early, under the tile's prologue).
-template <int W, class Op, int P>
+template <int W, class Op, int P, int NBUF = tc_nbuf<(Op::kMode == 0), P>()>
 __device__ __forceinline__ void tc_tile_prefetch(const TcW& w, unsigned char* tsm, TcTileState& S) {
     constexpr bool F = (Op::kMode == 0);
-    constexpr int NBUF = tc_nbuf<F, P>();
     constexpr bool kSingle = (Op::kMode == 2);
     const int nch = (w.K1p + tc_kc<F, P>() - 1) / tc_kc<F, P>();
     const int kc2 = tc_kc2<F>(w.N2p);
     const int ng = nch + (kSingle ? 0 : (W + kc2 - 1) / kc2);
-    unsigned char* sB0 = tsm + tc_region_a<W, F, P>();
-    for (int g = 0; g < NBUF && g < ng; ++g) tc_load_chunk<W, F, P>(w, sB0, S, g, nch, kc2);
+    unsigned char* sB0 = tsm + tc_region_a<W, F, P, NBUF>();
+    for (int g = 0; g < NBUF && g < ng; ++g) tc_load_chunk<W, F, P, NBUF>(w, sB0, S, g, nch, kc2);
 }
 
 // One 128-row tile of the fused MLP (rows row0 ..), run by all TC_T threads of the CTA:
@@ -353,7 +352,7 @@ __device__ __forceinline__ void tc_tile_prefetch(const TcW& w, unsigned char* ts
 // rc: the tile's row contexts, prepared by the caller (visible after a __syncthreads); tD: the
 // CTA's TC_TMEM_COLS tensor-memory columns; the weight chunks of tc_tile_prefetch must have been
 // issued.  Returns the CTA-uniform ok (false after a bounded wait gave up).
-template <int W, class Op, int P>
+template <int W, class Op, int P, int NBUF = tc_nbuf<(Op::kMode == 0), P>()>
 __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row0, unsigned char* tsm,
                                             const RowCtx* rc, unsigned tD, TcTileState& S) {
     constexpr bool F = (Op::kMode == 0);
@@ -361,8 +360,7 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
     constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = TC_NB * KC * 2, H_BYTES = TC_M * W * 2;
     unsigned char* sA = tsm;                          // NBUF x P pieces of the A chunk, K-major with K = KC
     unsigned char* sH = tsm;                          // P pieces of the hidden tile, K = W (after GEMM1)
-    constexpr int NBUF = tc_nbuf<F, P>();
-    unsigned char* sB0 = tsm + tc_region_a<W, F, P>();   // NBUF buffers of P pieces of a B chunk (bulk copies)
+    unsigned char* sB0 = tsm + tc_region_a<W, F, P, NBUF>();   // NBUF buffers of P pieces of a B chunk (bulk copies)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long rows = op.rows;
     constexpr bool kSingle = (Op::kMode == 2);
@@ -377,7 +375,7 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
         const int b = g % NBUF;
         ok = tc_wait(&S.mbar[b], S.mph[b] & 1, w.status) && ok;
         ++S.mph[b];
-        if (tid == 0 && ok && g + NBUF < ng && !S.b_pending[b]) tc_load_chunk<W, F, P>(w, sB0, S, g + NBUF, nch, kc2);
+        if (tid == 0 && ok && g + NBUF < ng && !S.b_pending[b]) tc_load_chunk<W, F, P, NBUF>(w, sB0, S, g + NBUF, nch, kc2);
     };
     constexpr int CSTEP = 32 * (TC_T / 128);
     const int lrow = (warp & 3) * 32 + lane;
@@ -522,9 +520,8 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
 
 // Set-up of a CTA that runs tensor-core MLP tiles: barrier init (thread 0) and the tensor-memory
 // allocation (warp 0); tc_cta_teardown waits for weight copies still in flight and frees it.
-template <bool F, int P>
+template <bool F, int P, int NBUF = tc_nbuf<F, P>()>
 __device__ __forceinline__ void tc_cta_init(TcTileState& S, unsigned long long* mbar, unsigned long long* bbar) {
-    constexpr int NBUF = tc_nbuf<F, P>();
     S.mbar = mbar;
     S.bbar = bbar;
     for (int b = 0; b < TC_NBUF_MAX; ++b) {
@@ -549,9 +546,8 @@ __device__ __forceinline__ void tc_tmem_alloc(unsigned* tmem_base) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
 }
-template <bool F, int P>
+template <bool F, int P, int NBUF = tc_nbuf<F, P>()>
 __device__ __forceinline__ void tc_cta_teardown(TcTileState& S, unsigned tmem_base) {
-    constexpr int NBUF = tc_nbuf<F, P>();
     // a bulk copy whose wait gave up may still be landing: wait (bounded) before the CTA exits
     if (threadIdx.x == 0)
 #pragma unroll
@@ -564,19 +560,19 @@ __device__ __forceinline__ void tc_cta_teardown(TcTileState& S, unsigned tmem_ba
 }
 
 // One tile per CTA (tile blockIdx.x).
-template <int W, class Op, int P>
+template <int W, class Op, int P, int NB = tc_nbuf<(Op::kMode == 0), P>()>
 __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ RowCtx rc[TC_M];
     constexpr bool F = (Op::kMode == 0);
-    __shared__ __align__(8) unsigned long long mbar[tc_nbuf<F, P>()];   // MMA completion per buffer (tcgen05.commit)
-    __shared__ __align__(8) unsigned long long bbar[tc_nbuf<F, P>()];   // B chunk arrival (bulk-copy bytes)
+    __shared__ __align__(8) unsigned long long mbar[NB];   // MMA completion per buffer (tcgen05.commit)
+    __shared__ __align__(8) unsigned long long bbar[NB];   // B chunk arrival (bulk-copy bytes)
     __shared__ unsigned tmem_base;
     TcTileState S;
-    tc_cta_init<F, P>(S, mbar, bbar);
+    tc_cta_init<F, P, NB>(S, mbar, bbar);
     const long row0 = (long)blockIdx.x * TC_M;
     const long rows = op.rows;
-    if (threadIdx.x == 0) tc_tile_prefetch<W, Op, P>(w, tsm, S);      // first chunks, under the prologue
+    if (threadIdx.x == 0) tc_tile_prefetch<W, Op, P, NB>(w, tsm, S);      // first chunks, under the prologue
     // the prologue reads only weights and the static row indices (op.prep): it overlaps the
     // previous kernel's tail under programmatic dependent launch
     for (int m = threadIdx.x; m < TC_M; m += TC_T) rc[m] = op.prep(row0 + m < rows ? row0 + m : -1);
@@ -586,12 +582,12 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
     tc_fence_after();
     pdl_wait();
     if (w.early) pdl_launch_dependents();
-    tc_mlp_tile<W, Op, P>(op, w, row0, tsm, rc, tmem_base, S);
+    tc_mlp_tile<W, Op, P, NB>(op, w, row0, tsm, rc, tmem_base, S);
     // this CTA's work is done: the next kernel may start its prologue (triggered at the end, not
     // the start, so that early CTAs of the next kernel do not hold SMs for this kernel's
     // whole duration when many instances run side by side)
     pdl_launch_dependents();
-    tc_cta_teardown<F, P>(S, tmem_base);
+    tc_cta_teardown<F, P, NB>(S, tmem_base);
 }
 
 // Two MLPs in sequence on the same 128 rows (tile blockIdx.x), where the second reads only what
@@ -599,36 +595,36 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
 // output stores become visible to the CTA's threads at the barrier between the two; the second
 // tile's weight chunks are copied once the first tile's buffers are free.  Both ops run in
 // reverse (mask) mode with the same rows.
-template <int W, class Op1, class Op2, int P>
+template <int W, class Op1, class Op2, int P, int NB = tc_nbuf<false, P>()>
 __global__ void __launch_bounds__(TC_T) tc_mlp_seq_kernel(Op1 op1, TcW w1, Op2 op2, TcW w2) {
     static_assert(Op1::kMode == 1 && Op2::kMode == 1, "sequenced MLP tiles run in reverse mode");
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ RowCtx rc[TC_M];
-    __shared__ __align__(8) unsigned long long mbar[tc_nbuf<false, P>()];
-    __shared__ __align__(8) unsigned long long bbar[tc_nbuf<false, P>()];
+    __shared__ __align__(8) unsigned long long mbar[NB];
+    __shared__ __align__(8) unsigned long long bbar[NB];
     __shared__ unsigned tmem_base;
     TcTileState S;
-    tc_cta_init<false, P>(S, mbar, bbar);
+    tc_cta_init<false, P, NB>(S, mbar, bbar);
     const long row0 = (long)blockIdx.x * TC_M;
-    if (threadIdx.x == 0) tc_tile_prefetch<W, Op1, P>(w1, tsm, S);
+    if (threadIdx.x == 0) tc_tile_prefetch<W, Op1, P, NB>(w1, tsm, S);
     for (int m = threadIdx.x; m < TC_M; m += TC_T) rc[m] = op1.prep(row0 + m < op1.rows ? row0 + m : -1);
     tc_tmem_alloc(&tmem_base);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     pdl_wait();
-    bool ok = tc_mlp_tile<W, Op1, P>(op1, w1, row0, tsm, rc, tmem_base, S);
+    bool ok = tc_mlp_tile<W, Op1, P, NB>(op1, w1, row0, tsm, rc, tmem_base, S);
     // the first tile's stores and its reads of shared and tensor memory are complete
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (threadIdx.x == 0 && ok) tc_tile_prefetch<W, Op2, P>(w2, tsm, S);
+    if (threadIdx.x == 0 && ok) tc_tile_prefetch<W, Op2, P, NB>(w2, tsm, S);
     for (int m = threadIdx.x; m < TC_M; m += TC_T) rc[m] = op2.prep(row0 + m < op2.rows ? row0 + m : -1);
     __syncthreads();
-    if (ok) tc_mlp_tile<W, Op2, P>(op2, w2, row0, tsm, rc, tmem_base, S);
+    if (ok) tc_mlp_tile<W, Op2, P, NB>(op2, w2, row0, tsm, rc, tmem_base, S);
     pdl_launch_dependents();
-    tc_cta_teardown<false, P>(S, tmem_base);
+    tc_cta_teardown<false, P, NB>(S, tmem_base);
 }
 
 }  // namespace gmi
