@@ -147,6 +147,11 @@ void gm_gnn_destroy(gm_gnn* m);
  *                nodes the column's actuator reaches in K (k - i) edges), no A_k
  *                formed; the same H, g, C~, d~ up to rounding.  Used by
  *                gm_rti_step and gm_condense_matrix_free.
+ *   tan_split_rows  matrix-free condensing: the tangent edge rows of a message-
+ *                passing layer from which its first layer runs on per-node
+ *                projections of its two node blocks (one product per node row,
+ *                K = W per edge row) instead of whole (K = 3W per edge row);
+ *                0: 100000; 1: every layer.  >= 0.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N;
@@ -163,6 +168,7 @@ typedef struct {
     int factor_grid;
     int chunk_mb;
     int condensing;
+    int tan_split_rows;
 } gm_settings;
 
 /* Per-solve statistics, written to DEVICE memory by the QP calls. */

@@ -42,7 +42,7 @@ class Settings(C.Structure):
                 ("tol", C.c_float), ("max_iter", C.c_int), ("polish", C.c_int),
                 ("timeout_spins", C.c_int), ("scale_rows", C.c_int), ("adapt_rho", C.c_int),
                 ("admm_grid", C.c_int), ("factor_grid", C.c_int), ("chunk_mb", C.c_int),
-                ("condensing", C.c_int)]
+                ("condensing", C.c_int), ("tan_split_rows", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -350,10 +350,10 @@ def gm_gnn_destroy(m):
 
 def make_settings(N, n_c=0, precision=GM_PREC_FP32, rho=0.1, tol=1e-6, max_iter=4000, polish=0,
                   timeout_spins=0, scale_rows=1, adapt_rho=1, admm_grid=0, factor_grid=0, chunk_mb=0,
-                  condensing=0):
+                  condensing=0, tan_split_rows=0):
     return Settings(int(N), int(n_c), int(precision), float(rho), float(tol), int(max_iter), int(polish),
                     int(timeout_spins), int(scale_rows), int(adapt_rho), int(admm_grid), int(factor_grid),
-                    int(chunk_mb), int(condensing))
+                    int(chunk_mb), int(condensing), int(tan_split_rows))
 
 
 def gm_ctx_workspace_size(graph, gnn, settings):

@@ -619,6 +619,7 @@ static gm_status prepare(const gm_graph* g, const gm_gnn* m, const gm_settings* 
                  "admm_grid, factor_grid and chunk_mb must be >= 0");
     GM_CHECK_ARG((long)s->N * g->nu <= 256, "N * nu must be <= 256 (got %d)", s->N * g->nu);
     GM_CHECK_ARG(s->condensing == 0 || s->condensing == 1, "condensing must be 0 or 1 (got %d)", s->condensing);
+    GM_CHECK_ARG(s->tan_split_rows >= 0, "tan_split_rows must be >= 0 (got %d)", s->tan_split_rows);
     c->s = *s;
     c->M = g->M; c->E = g->E; c->nu = g->nu; c->K = m->d.K; c->W = m->d.W; c->N = s->N;
     c->nU = s->N * g->nu; c->n_c = s->n_c; c->dt = m->d.dt;

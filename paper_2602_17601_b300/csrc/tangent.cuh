@@ -23,7 +23,7 @@ namespace gmi {
 // EdgeMpTan) instead of whole per edge row (EdgeMpTanK3).  Tangent pass of the closed-loop step
 // at the chain of 1000 (last tangent stage done, cold ADMM step): 6.85 / 8.65 ms from 20k rows,
 // 6.83 / 8.63 from 30k, 6.79 / 8.56 from 50k, 6.76 / 8.50 from 100k (no layer reaches 200k).
-constexpr long kTanSplitRows = 100000;
+constexpr long kTanSplitRows = 100000;   // gm_settings.tan_split_rows = 0
 
 // Whether each tangent kernel lets the next one of the stage start its prologue (weight chunks,
 // row contexts, tensor-memory allocation) as soon as all of its own CTAs have started.  Off: the
@@ -410,7 +410,8 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
     // The projections of an edge layer's node blocks (NodeProjTan, layers of kTanSplitRows edge
     // rows or more) and the decoder are row-local on the node rows the node encoder or the node
     // update just wrote: each runs in the same launch as its producer (tc_mlp_seq_kernel).
-    auto projected = [&](int l) { return c->E > 0 && l <= K && tan_rows(c, k, l, true) >= kTanSplitRows; };
+    const long split = c->s.tan_split_rows > 0 ? c->s.tan_split_rows : kTanSplitRows;
+    auto projected = [&](int l) { return c->E > 0 && l <= K && tan_rows(c, k, l, true) >= split; };
     auto proj_op = [&](int l, NodeProjTan& pj, TcW& tw) {    // P of edge layer l from node layer l - 1
         const MlpOff& m = c->mlp[2 + 2 * (l - 1)];
         fill_tan(pj, c, m, k, l - 1, false, nullptr);

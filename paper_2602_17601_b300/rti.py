@@ -25,14 +25,15 @@ class RTIProblem:
     half-spaces (Cx, dx) or spheres linearised at the rollout.  barrier = (mu, delta)
     makes step() put those rows into the cost as relaxed log barriers (gm_barrier_fold).
     warm=True starts each step's ADMM from the shifted previous solution (gm_ctx_set_warm).
-    condensing=1 builds the condensed QP matrix-free (forward-mode sensitivities, no A_k).
+    condensing=1 builds the condensed QP matrix-free (forward-mode sensitivities, no A_k);
+    tan_split_rows sets where its edge updates switch to per-node projections (0: the default).
     """
 
     def __init__(self, M, src, dst, nu, act_node, K, W, dt, blob, N, Qdiag, Rdiag, x_ref, u_ref, u_lo,
                  u_hi, Cx=None, dx=None, spheres=None, rho=0.1, tol=1e-6, max_iter=4000,
                  precision=GM_PREC_FP32, polish=0, timeout_spins=0, scale_rows=1, adapt_rho=1,
                  graph=False, admm_grid=0, factor_grid=0, chunk_mb=0, barrier=None, warm=False, condensing=0,
-                 device="cuda"):
+                 tan_split_rows=0, device="cuda"):
         import torch
         self.torch = torch
         self.M, self.nu, self.N, self.K, self.W = int(M), int(nu), int(N), int(K), int(W)
@@ -54,7 +55,8 @@ class RTIProblem:
         self.graph = gm_graph_create(M, src, dst, nu, act_node)
         self.gnn = gm_gnn_load(K, W, nu, dt, blob)
         self.settings = make_settings(N, n_c, precision, rho, tol, max_iter, polish, timeout_spins,
-                                      scale_rows, adapt_rho, admm_grid, factor_grid, chunk_mb, condensing)
+                                      scale_rows, adapt_rho, admm_grid, factor_grid, chunk_mb, condensing,
+                                      tan_split_rows)
         nbytes = gm_ctx_workspace_size(self.graph, self.gnn, self.settings)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.ctx = gm_ctx_create(self.graph, self.gnn, self.settings, self.workspace)

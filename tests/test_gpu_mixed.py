@@ -176,3 +176,25 @@ def test_mixed_linearize_multi_tile_against_fp32_form(lib):
     # c: a difference of larger terms, measured against x_hat's scale
     e = np.abs(cm - cf) / np.abs(xf).max()
     assert np.quantile(e, 0.9999) <= REL_MIXED, np.quantile(e, 0.9999)
+
+
+@pytest.mark.parametrize("W", [32, 64, 128])
+@pytest.mark.parametrize("split", [0, 1])
+def test_mixed_matrix_free_h_g(lib, W, split):
+    """Matrix-free condensing in the split-BF16 form (tangent MLPs on tensor cores, the node-side
+    pairs in one launch): H and g against the oracle's condensing of its own linearisation, to
+    1e-4 of their max-abs.  split = 1 puts every edge layer on per-node projections of the first
+    layer's node blocks (gm_settings.tan_split_rows = 1; the warp-specialised kernel at W = 128),
+    split = 0 keeps the whole first layer on these small graphs."""
+    wl, u_hat = _kink_free(W)
+    prob = lib.RTIProblem.from_workload(wl, precision=GM_PREC_MIXED, condensing=1, tan_split_rows=split)
+    x_hat, H, g, _, _ = (t.cpu().numpy().astype(np.float64) for t in prob.condense_matrix_free(wl.x0, u_hat))
+    xo, Ao, Bo, co = oracle_linearize(wl, u_hat.astype(np.float64))
+    nbh = [list(prob.col[prob.row_ptr[i]:prob.row_ptr[i + 1]]) for i in range(wl.M)]
+    blocks = ocd.blocks_from_dense(Ao, Bo, co, nbh)
+    Ho, go, _, _, _, _ = ocd.condense_recursive(blocks, xo[0].reshape(-1), wl.Qdiag, wl.Rdiag, wl.x_ref, wl.u_ref,
+                                                np.zeros((wl.N, wl.M, 0, 3)), np.zeros((wl.N, wl.M, 0)))
+    R = np.diag(wl.Rdiag.reshape(-1).astype(np.float64))
+    assert max_rel_err(x_hat, xo) <= REL_MIXED
+    eh, eg = max_rel_err(H - R, Ho - R), max_rel_err(g, go)
+    assert eh <= REL_MIXED and eg <= REL_MIXED, (W, split, eh, eg)
