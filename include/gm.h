@@ -151,7 +151,7 @@ void gm_gnn_destroy(gm_gnn* m);
  *                passing layer from which its first layer runs on per-node
  *                projections of its two node blocks (one product per node row,
  *                K = W per edge row) instead of whole (K = 3W per edge row);
- *                0: 100000; 1: every layer.  >= 0.
+ *                0: 30000; 1: every layer.  >= 0.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N;

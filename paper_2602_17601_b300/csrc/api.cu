@@ -406,6 +406,9 @@ static void build_weights(const gm_gnn& m, int nu, std::vector<float>& w, std::v
                 return n < W ? W1[(size_t)k * hid + n] : W1[(size_t)(W + k) * hid + (n - W)];
             });
             mo.eyek = put_bf(wp, W, W, TC_CHUNK, [&](int j, int k) { return j == k ? 1.f : 0.f; });
+            mo.pabk1 = put_bf(wp, 2 * W, W, TC_CHUNK, [&](int n, int k) {
+                return n < W ? W1[(size_t)k * hid + n] : W1[(size_t)(W + k) * hid + (n - W)];
+            });
         }
         offs.push_back(mo);
     }

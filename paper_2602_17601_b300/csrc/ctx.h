@@ -52,6 +52,7 @@ struct MlpOff {
     long Pab = 0;                           // FP32 [W][2W]: Pab[k][n] = W1[k][n], Pab[k][W+n] = W1[W+k][n]
     long eye = 0;                           // FP32 identity [W][W]
     long fck = 0, pabk = 0, eyek = 0;       // BF16: W1 e-block^T [W][W], Pab^T [2W][W], identity [W][W]
+    long pabk1 = 0;                         // BF16: Pab^T [2W][W] in chunks of TC_CHUNK (one product)
 };
 
 // Rows of the reverse-mode cones (one seed = one output node s, 3 cotangent

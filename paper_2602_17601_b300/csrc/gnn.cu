@@ -369,7 +369,8 @@ static gm_status launch_tc_nb(bool pdl, const Op& op, const TcW& tw, cudaStream_
     constexpr bool F = (Op::kMode == 0);
     constexpr size_t smem = tc_smem_bytes<W, F, P, NB>() > TC_SMEM_MIN ? tc_smem_bytes<W, F, P, NB>() : TC_SMEM_MIN;
     static_assert(W <= TC_NB, "GEMM1 width must fit the staged B chunk");
-    if (tw.N2p > TC_TMEM_COLS || tw.N2p % 16 || tw.K1p % 16) {
+    if (tw.N2p > TC_TMEM_COLS || tw.N2p % 16 || tw.K1p % 16 || (tw.N1p && tw.N1p != W && tw.N1p != 2 * W) ||
+        (tw.N1p > W && (Op::kMode != 2 || 2 * W > TC_TMEM_COLS || tw.K1p != W))) {
         set_error("tensor-core MLP shape out of range (K1p %d, N2p %d)", tw.K1p, tw.N2p);
         return GM_ERR_INVALID_ARG;
     }
@@ -404,7 +405,9 @@ static gm_status launch_tc_seq_nb(bool pdl, const Op1& op1, const TcW& tw1, cons
     constexpr size_t smem =
         tc_smem_bytes<W, false, P, NB>() > TC_SMEM_MIN ? tc_smem_bytes<W, false, P, NB>() : TC_SMEM_MIN;
     for (const TcW* tw : {&tw1, &tw2})
-        if (tw->N2p > TC_TMEM_COLS || tw->N2p % 16 || tw->K1p % 16) {
+        if (tw->N2p > TC_TMEM_COLS || tw->N2p % 16 || tw->K1p % 16 || (tw->N1p && tw->N1p != W && tw->N1p != 2 * W) ||
+            (tw->N1p > W && (2 * W > TC_TMEM_COLS || tw->K1p != W)) || (tw == &tw1 && tw->N1p > W) ||
+            (tw == &tw2 && tw->N1p > W && Op2::kMode != 2)) {
             set_error("tensor-core MLP shape out of range (K1p %d, N2p %d)", tw->K1p, tw->N2p);
             return GM_ERR_INVALID_ARG;
         }

@@ -20,10 +20,10 @@
 namespace gmi {
 
 // Edge rows of a layer from which its first layer runs on per-node projections (NodeProjTan +
-// EdgeMpTan) instead of whole per edge row (EdgeMpTanK3).  Tangent pass of the closed-loop step
-// at the chain of 1000 (last tangent stage done, cold ADMM step): 6.85 / 8.65 ms from 20k rows,
-// 6.83 / 8.63 from 30k, 6.79 / 8.56 from 50k, 6.76 / 8.50 from 100k (no layer reaches 200k).
-constexpr long kTanSplitRows = 100000;   // gm_settings.tan_split_rows = 0
+// EdgeMpTan) instead of whole per edge row (EdgeMpTanK3).  With the projections as one wide
+// product in the node update's launch, the last tangent stage of the closed-loop step at the
+// chain of 1000 ends 6.15 ms into it from 30k rows, 6.18 from 60k, 6.22 from 100k.
+constexpr long kTanSplitRows = 30000;   // gm_settings.tan_split_rows = 0
 
 // Whether each tangent kernel lets the next one of the stage start its prologue (weight chunks,
 // row contexts, tensor-memory allocation) as soon as all of its own CTAs have started.  Off: the
@@ -173,6 +173,12 @@ struct NodeProjTan : TanBase {
     static constexpr bool kHasIn8 = true, kHasOut4 = true;
     __device__ void in8(const RowCtx& x, int k0, float* v) const { ld8(th_prev + (long)x.a * W + k0, v); }
     __device__ void out4(const RowCtx& x, int n, float4 v) const { st4(P + (long)x.a * 2 * W + n, v); }
+};
+
+// The same projections as one product on the tensor cores: P = th_{l-1} [W_a | W_b] with the
+// operand's 2W rows taken as two halves of W (TcW::N1p = 2W).
+struct NodeProjTan1 : NodeProjTan {
+    static constexpr int kMode = 2;
 };
 
 // Edge update of layer l: te_l = te_{l-1} + W2' (mask . (P[dst][:W] + P[src][W:] + te_{l-1} W_c)),
@@ -412,13 +418,26 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
     // update just wrote: each runs in the same launch as its producer (tc_mlp_seq_kernel).
     const long split = c->s.tan_split_rows > 0 ? c->s.tan_split_rows : kTanSplitRows;
     auto projected = [&](int l) { return c->E > 0 && l <= K && tan_rows(c, k, l, true) >= split; };
-    auto proj_op = [&](int l, NodeProjTan& pj, TcW& tw) {    // P of edge layer l from node layer l - 1
+    // P of edge layer l from node layer l - 1 after the launch of op (with tw): one product on the
+    // tensor cores, the identity-first-layer MLP in the FP32 form
+    auto with_proj = [&](int l, const auto& op, const TcW& tw) -> gm_status {
         const MlpOff& m = c->mlp[2 + 2 * (l - 1)];
-        fill_tan(pj, c, m, k, l - 1, false, nullptr);
-        pj.kin = W; pj.nout = 2 * W;
-        pj.B1 = c->d_wts + m.eye; pj.B2 = c->d_wts + m.Pab;
-        pj.th_prev = th[(l - 1) & 1]; pj.P = c->d_tproj;
-        tw = tan_w(tc_w(c, m.eyek, m.pabk, W, 2 * W));
+        auto fill = [&](NodeProjTan& pj) {
+            fill_tan(pj, c, m, k, l - 1, false, nullptr);
+            pj.kin = W; pj.nout = 2 * W;
+            pj.B1 = c->d_wts + m.eye; pj.B2 = c->d_wts + m.Pab;
+            pj.th_prev = th[(l - 1) & 1]; pj.P = c->d_tproj;
+        };
+        if (c->s.precision == GM_PREC_FP32) {
+            NodeProjTan pj{};
+            fill(pj);
+            return launch_mlp_seq(c, op, tw, pj, tan_w(tc_w(c, m.eyek, m.pabk, W, 2 * W)), st);
+        }
+        NodeProjTan1 pj{};
+        fill(pj);
+        TcW tp = tan_w(tc_w(c, m.pabk1, -1, W, 0));
+        tp.N1p = 2 * W;
+        return launch_mlp_seq(c, op, tw, pj, tp, st);
     };
     {   // node encoder (node layer 0)
         NodeEncTan op{};
@@ -426,10 +445,7 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
         op.Sk = Sk; op.act = c->d_act; op.th = th[0];
         const TcW tw = tan_w(tc_fwd(c, c->mlp[0]));
         if (projected(1)) {
-            NodeProjTan pj{};
-            TcW tp{};
-            proj_op(1, pj, tp);
-            GM_TRY(launch_mlp_seq(c, op, tw, pj, tp, st));
+            GM_TRY(with_proj(1, op, tw));
         } else {
             GM_TRY(launch_mlp(c, op, tw, st));
         }
@@ -505,10 +521,7 @@ static gm_status tangent_stage(gm_ctx* c, int k, cudaStream_t st) {
             de.Sk = Sk; de.Sk1 = Sk1; de.th = th[K & 1]; de.dt = c->dt;
             GM_TRY(launch_mlp_seq(c, nm, tn, de, tan_w(tc_fwd(c, c->mlp[2 + 2 * K])), st));
         } else if (projected(l + 1)) {
-            NodeProjTan pj{};
-            TcW tp{};
-            proj_op(l + 1, pj, tp);
-            GM_TRY(launch_mlp_seq(c, nm, tn, pj, tp, st));
+            GM_TRY(with_proj(l + 1, nm, tn));
         } else {
             GM_TRY(launch_mlp(c, nm, tn, st));
         }

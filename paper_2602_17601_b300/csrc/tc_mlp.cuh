@@ -41,6 +41,9 @@ struct TcW {
     // 1: let the next kernel of the stream start its prologue as soon as every CTA of this one
     // has started (programmatic dependent launch), not when each finishes
     int early;
+    // single-product form: output columns of the product (0: W; 2W: two halves of W rows of B1,
+    // each chunk of B1 holding both halves, written to tensor-memory columns 0.. and W..)
+    int N1p;
 };
 
 template <class Op>
@@ -166,7 +169,7 @@ __device__ __forceinline__ void tc_out_rows(const Op& op, const RowCtx* rc, unsi
 // the staging buffer; completion is counted in bytes on mbarrier bar.  One thread calls it.
 template <int P>
 __device__ __forceinline__ void tc_load_b(unsigned char* dst, int piece_bytes, const __nv_bfloat16* const* src,
-                                          int nrows, int k0, int kc, void* bar) {
+                                          int nrows, int k0, int kc, void* bar, long extra = 0) {
     const unsigned bytes = (unsigned)nrows * kc * 2;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes * P)
                  : "memory");
@@ -175,7 +178,7 @@ __device__ __forceinline__ void tc_load_b(unsigned char* dst, int piece_bytes, c
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_u32(dst + p * piece_bytes)),
-            "l"(src[p] + (long)nrows * k0), "r"(bytes), "r"(smem_u32(bar))
+            "l"(src[p] + (long)nrows * k0 + extra), "r"(bytes), "r"(smem_u32(bar))
             : "memory");
 }
 
@@ -321,11 +324,16 @@ struct TcTileState {
 // B2) into buffer g % NBUF.
 template <int W, bool F, int P, int NBUF = tc_nbuf<F, P>()>
 __device__ __forceinline__ void tc_load_chunk(const TcW& w, unsigned char* sB0, TcTileState& S, int g, int nch,
-                                              int kc2) {
+                                              int kc2, int nh = 1) {
     constexpr int KC = tc_kc<F, P>(), B_BYTES = TC_NB * KC * 2;
     const int b = g % NBUF;
     unsigned char* dst = sB0 + (size_t)b * P * B_BYTES;
-    if (g < nch) {
+    if (nh > 1 && g < nch * nh) {
+        // half h of chunk c of a B1 with nh W rows: the chunk's rows are 8-row groups in order,
+        // so the half is the contiguous block W kc elements after the chunk's start
+        const int c = g % nch, h = g / nch, kc = min(KC, w.K1p - c * KC);
+        tc_load_b<P>(dst, B_BYTES, w.B1, W, 0, kc, &S.bbar[b], (long)nh * W * c * KC + (long)h * W * kc);
+    } else if (g < nch) {
         tc_load_b<P>(dst, B_BYTES, w.B1, W, g * KC, min(KC, w.K1p - g * KC), &S.bbar[b]);
     } else {
         const int k0 = (g - nch) * kc2;
@@ -341,9 +349,10 @@ __device__ __forceinline__ void tc_tile_prefetch(const TcW& w, unsigned char* ts
     constexpr bool kSingle = (Op::kMode == 2);
     const int nch = (w.K1p + tc_kc<F, P>() - 1) / tc_kc<F, P>();
     const int kc2 = tc_kc2<F>(w.N2p);
-    const int ng = nch + (kSingle ? 0 : (W + kc2 - 1) / kc2);
+    const int nh = kSingle && w.N1p > W ? w.N1p / W : 1;
+    const int ng = kSingle ? nch * nh : nch + (W + kc2 - 1) / kc2;
     unsigned char* sB0 = tsm + tc_region_a<W, F, P, NBUF>();
-    for (int g = 0; g < NBUF && g < ng; ++g) tc_load_chunk<W, F, P, NBUF>(w, sB0, S, g, nch, kc2);
+    for (int g = 0; g < NBUF && g < ng; ++g) tc_load_chunk<W, F, P, NBUF>(w, sB0, S, g, nch, kc2, nh);
 }
 
 // One 128-row tile of the fused MLP (rows row0 ..), run by all TC_T threads of the CTA:
@@ -367,7 +376,9 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
     const int nch = (w.K1p + KC - 1) / KC;
     const int kc2 = tc_kc2<F>(w.N2p);
     const int n2 = kSingle ? 0 : (W + kc2 - 1) / kc2;
-    const int ng = nch + n2;
+    const int nh = kSingle && w.N1p > W ? w.N1p / W : 1;   // halves of a wide single product
+    const int n1 = nch * nh;                                 // B chunks of GEMM1
+    const int ng = n1 + n2;
     bool ok = true;
     // all threads: wait for the MMAs of chunk g (A buffer and B buffer g % NBUF are then free);
     // thread 0 then copies the weight chunk NBUF ahead into the freed B buffer
@@ -375,7 +386,8 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
         const int b = g % NBUF;
         ok = tc_wait(&S.mbar[b], S.mph[b] & 1, w.status) && ok;
         ++S.mph[b];
-        if (tid == 0 && ok && g + NBUF < ng && !S.b_pending[b]) tc_load_chunk<W, F, P, NBUF>(w, sB0, S, g + NBUF, nch, kc2);
+        if (tid == 0 && ok && g + NBUF < ng && !S.b_pending[b])
+            tc_load_chunk<W, F, P, NBUF>(w, sB0, S, g + NBUF, nch, kc2, nh);
     };
     constexpr int CSTEP = 32 * (TC_T / 128);
     const int lrow = (warp & 3) * 32 + lane;
@@ -393,7 +405,8 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
 
     // thread 0: wait for the staged B chunk, issue the chunk's MMAs, commit them to mbar (the
     // commit arrives even when nothing was issued, so the other threads never wait in vain)
-    auto issue = [&](int g, unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b_sbo, int kc, int N, bool first) {
+    auto issue = [&](int g, unsigned a0, unsigned a_piece, unsigned a_sbo, unsigned b_sbo, int kc, int N, bool first,
+                     unsigned dcol = 0) {
         const int b = g % NBUF;
         bool okb = false;
         if (S.b_pending[b]) {
@@ -404,7 +417,8 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
             }
         }
         if (okb)
-            tc_issue<P>(tD, a0, a_piece, a_sbo, smem_u32(sB0 + (size_t)b * P * B_BYTES), B_BYTES, b_sbo, kc, N, first);
+            tc_issue<P>(tD + dcol, a0, a_piece, a_sbo, smem_u32(sB0 + (size_t)b * P * B_BYTES), B_BYTES, b_sbo, kc, N,
+                        first);
         tc_commit(&S.mbar[b]);
         return okb;
     };
@@ -417,6 +431,23 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
     if (kAhead && nch > 0 && KC <= w.K1p) tc_load_a_full<KC>(op, rc, row0, rows, 0, tid, xa);
     // Chunk c goes into A buffer c % NBUF, whose previous chunk (c - NBUF) was waited for at the
     // end of iteration c - 1; chunk c's MMAs then run while chunk c + 1 is staged.
+    if (kSingle && nh > 1) {
+        // a wide single product (K1p = W, N = nh W): the whole input tile staged once in the
+        // K-major layout of the hidden tile, then its K chunks for each N half of W columns
+        tc_stage_a<P, W>(op, rc, row0, rows, sH, H_BYTES, 0, W, tid);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        for (int g1 = 0; g1 < n1; ++g1) {
+            const int c = g1 % nch, h = g1 / nch;
+            const int k0 = c * KC, kc = min(KC, w.K1p - k0);
+            if (tid == 0)
+                ok = issue(g1, smem_u32(sH) + (k0 / 8) * 128, H_BYTES, W * 16, kc * 16, kc, W, c == 0,
+                           (unsigned)(h * W)) && ok;
+            if (g1 - NBUF + 1 >= 0) wait_chunk(g1 - NBUF + 1);
+        }
+    } else {
     for (int c = 0; c < nch; ++c) {
         const int k0 = c * KC;
         const int kc = min(KC, w.K1p - k0);        // multiple of 16
@@ -433,7 +464,8 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
         // chunk NBUF ahead of it (for the last GEMM1 chunks, the first GEMM2 chunks)
         if (c - NBUF + 1 >= 0) wait_chunk(c - NBUF + 1);
     }
-    for (int g = max(0, nch - NBUF + 1); g < nch; ++g) wait_chunk(g);   // GEMM1 complete
+    }
+    for (int g = max(0, n1 - NBUF + 1); g < n1; ++g) wait_chunk(g);   // GEMM1 complete
     ok = __syncthreads_and(ok) != 0;           // warp-collective TMEM loads below need a uniform decision
     tc_fence_after();
 
@@ -443,7 +475,7 @@ __device__ __forceinline__ bool tc_mlp_tile(const Op& op, const TcW& w, long row
     const unsigned lane_off = (unsigned)((warp & 3) * 32) << 16;
     if (kSingle) {
         if constexpr (Op::kHasOut4) {
-            tc_out_rows(op, rc, tsm, tD, W, nullptr, row0, rows, ok);
+            tc_out_rows(op, rc, tsm, tD, W * nh, nullptr, row0, rows, ok);
         } else {
             for (int c0 = cgrp * 32; c0 < W; c0 += CSTEP) {
                 float v[32];
@@ -597,7 +629,8 @@ __global__ void __launch_bounds__(TC_T) tc_mlp_kernel(Op op, TcW w) {
 // reverse (mask) mode with the same rows.
 template <int W, class Op1, class Op2, int P, int NB = tc_nbuf<false, P>()>
 __global__ void __launch_bounds__(TC_T) tc_mlp_seq_kernel(Op1 op1, TcW w1, Op2 op2, TcW w2) {
-    static_assert(Op1::kMode == 1 && Op2::kMode == 1, "sequenced MLP tiles run in reverse mode");
+    static_assert(Op1::kMode == 1 && (Op2::kMode == 1 || Op2::kMode == 2),
+                  "sequenced MLP tiles run in reverse (or single-product) mode");
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ RowCtx rc[TC_M];
     __shared__ __align__(8) unsigned long long mbar[NB];
