@@ -42,6 +42,8 @@ def test_graph_and_gnn_validation():
         lambda: gm.gm_gnn_load(wl.K, wl.W, wl.nu, wl.dt, wl.blob[:-1]),   # wrong size
         lambda: gm.gm_gnn_load(wl.K, 48, wl.nu, wl.dt, wl.blob),          # unsupported width
         lambda: gm.gm_ctx_workspace_size(g, m, gm.make_settings(0)),      # N = 0
+        lambda: gm.gm_ctx_workspace_size(g, m, gm.make_settings(wl.N, condensing=2)),        # no such path
+        lambda: gm.gm_ctx_workspace_size(g, m, gm.make_settings(wl.N, condensing=1, tan_split_rows=-1)),
         lambda: gm.gm_ctx_workspace_size(g, gm.gm_gnn_load(wl.K, wl.W, 3, wl.dt,
                                                            np.zeros(_blob(wl.K, wl.W, 3), np.float32)), s),
     ]
