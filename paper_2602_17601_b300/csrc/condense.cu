@@ -227,9 +227,18 @@ __global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ 
     int a = c1 >= c2 ? c1 : c2, b = c1 >= c2 ? c2 : c1;     // lower-triangle element (a, b)
     const int T = (n + 31) / 32;
     int ti = a / 32, tj = b / 32;
-    float s = 0.f;
-    for (int sp = 0; sp < nsplit; ++sp)
-        s += part[((long)sp * T * T + (long)ti * T + tj) * 1024 + (a % 32) * 32 + (b % 32)];
+    // four independent partial sums, so that the loads of consecutive shares overlap
+    const long base = ((long)ti * T + tj) * 1024 + (a % 32) * 32 + (b % 32), stride = (long)T * T * 1024;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int sp = 0;
+    for (; sp + 4 <= nsplit; sp += 4) {
+        s0 += part[base + (long)sp * stride];
+        s1 += part[base + (long)(sp + 1) * stride];
+        s2 += part[base + (long)(sp + 2) * stride];
+        s3 += part[base + (long)(sp + 3) * stride];
+    }
+    for (; sp < nsplit; ++sp) s0 += part[base + (long)sp * stride];
+    float s = (s0 + s1) + (s2 + s3);
     if (c1 == c2 && diag_add) s += diag_scale * diag_add[c1];
     G[t] = s;
 }
@@ -270,14 +279,16 @@ __global__ void grad_kernel(int n, int M, int nu, int N, const float* __restrict
     }
 }
 
+// one warp per entry: the lanes stride over the partial sums, then a shuffle tree
 __global__ void grad_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
                                    const float* __restrict__ Rd, const float* __restrict__ ur,
                                    float* __restrict__ g) {
-    int cc = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cc = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (cc >= n) return;
-    float s = -Rd[cc] * ur[cc];
-    for (int sp = 0; sp < nsplit; ++sp) s += part[(long)sp * n + cc];
-    g[cc] = s;
+    float s = 0.f;
+    for (int sp = lane; sp < nsplit; sp += 32) s += part[(long)sp * n + cc];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) g[cc] = s - Rd[cc] * ur[cc];
 }
 
 // C~ row (k, i, c) = C^{x,i}_k[c] . Gamma_u^i position rows of stage k; d~ = d - C . Gamma_x position
@@ -344,8 +355,8 @@ gm_status condense_tail(gm_ctx* c, const float* x_hat, const gm_cost* cost, cons
     grad_kernel<<<gsplit, 256, 0, st>>>(c->nU, M, nu, N, c->d_Gu, c->d_Gx, x_hat, cost->Qdiag, cost->x_ref,
                                        c->d_gram_part);
     GM_LAUNCH_CHECK();
-    grad_reduce_kernel<<<cdiv(c->nU, 128), 128, 0, st>>>(c->nU, gsplit, c->d_gram_part, cost->Rdiag,
-                                                        cost->u_ref, g);
+    grad_reduce_kernel<<<cdiv((long)c->nU * 32, 256), 256, 0, st>>>(c->nU, gsplit, c->d_gram_part, cost->Rdiag,
+                                                                    cost->u_ref, g);
     GM_LAUNCH_CHECK();
     // stacked constraints
     if (c->n_c > 0) {
