@@ -2,7 +2,7 @@
 the HBM rates of read-only, write-only and copy streams over 4 GB (gm_measure_hbm).
 
 These are the roofline denominators of the FP32 kernels (condensing, ADMM) and the FP64
-kernels (factorisation, KKT check), beside the measured HBM copy and BF16 peaks; the
+kernels (factorisation, KKT check), beside the separately measured HBM copy and BF16 GEMM peaks; the
 one-way stream rates show whether a kernel's read/write mix bounds it below the copy peak.
 
   python -m paper_2602_17601_b300.peaks [--out FILE]

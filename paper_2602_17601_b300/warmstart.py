@@ -3,7 +3,7 @@
 A 3-layer MLP maps pooled GNN latents and the reference of an MPC instance to a
 primal input sequence U^0 and box duals y^0 that warm-start the condensed-QP
 ADMM.  Cold-start ADMM remains the fallback (the library restarts a stalled
-warm-started solve cold, `solve_with_fallback`) and the judge of the net's error.  Everything numeric runs in the library's kernels:
+warm-started solve cold, `solve_with_fallback`) and the arbiter of the net's error.  Everything numeric runs in the library's kernels:
 
 * features       gm_ws_features (stage-0 GNN latents, mean/max pooled, + reference)
 * inference      gm_ws_forward
