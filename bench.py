@@ -315,7 +315,7 @@ KERNEL_TC = ("tc_ws_bwd_kernel<EdgeMpBwd> (reverse edge-update MLP, warp-special
              "split-BF16 tcgen05)")
 KERNEL_FP32 = "mlp2_kernel<128, EdgeMpBwd> (reverse edge-update MLP, FP32 SIMT)"
 KERNEL_TAN = ("EdgeMpTan: tangent edge update of matrix-free condensing, tc_ws_bwd_kernel<EdgeMpTan> "
-              "(warp-specialised persistent, projected first layer) on layers of 100k edge rows or more, "
+              "(warp-specialised persistent, projected first layer) on layers of 30k edge rows or more, "
               "tc_mlp_kernel<128, EdgeMpTanK3, 2> below; split-BF16 tcgen05")
 KERNEL_TAN_FP32 = "mlp2_kernel<128, EdgeMpTan> (tangent edge-update MLP of matrix-free condensing, FP32 SIMT)"
 TRAFFIC_SOURCES = ("paper_2602_17601_b300/csrc/tc_prim.cuh", "paper_2602_17601_b300/csrc/tc_mlp.cuh", "paper_2602_17601_b300/csrc/tc_ws.cuh",
