@@ -148,20 +148,34 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
             __syncthreads();
             factor_diag(S, rd, k + 1, np, L, Linv, status);
         } else {
-            // entries (r, c), r0 <= c <= r < np, outside the next diagonal block, dealt over CTAs 1..G-1
-            const long ntri = (long)m * (m + 1) / 2;
-            for (long t = (b - 1) + (long)(G - 1) * tid; t < ntri; t += (long)(G - 1) * FT) {
-                // row-major lower-triangle index -> (r, c)
-                int r = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-                while ((long)(r + 1) * (r + 2) / 2 <= t) ++r;
-                while ((long)r * (r + 1) / 2 > t) --r;
-                const int c = (int)(t - (long)r * (r + 1) / 2);
-                if (r < FB) continue;             // inside the next diagonal block (CTA 0)
-                double v = 0.0;
-                for (int q = 0; q < FB; ++q)
-                    v += ldcg(&L[(long)(r0 + r) * np + k0 + q]) * ldcg(&L[(long)(r0 + c) * np + k0 + q]);
-                double* e = &L[(long)(r0 + r) * np + r0 + c];
-                *e = ldcg(e) - v;                 // last written by another CTA: read through L2
+            // blocks (i, j), k < j <= i < nb, of the trailing lower triangle other than the next
+            // diagonal block, dealt over CTAs 1..G-1: the two 16 x 16 panel blocks staged in shared
+            // memory (Dm, Pr), then A_ij -= L_ik L_jk^T entry by entry (256 threads, 16 FMAs each)
+            (void)m;
+            const int mb = nb - k - 1;                      // trailing block rows
+            const int nblk = mb * (mb + 1) / 2;             // lower-triangle blocks, (0, 0) is CTA 0's
+            for (int t = b; t < nblk; t += G - 1) {         // t = 0 is the next diagonal block: skipped
+                int bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+                while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+                while (bi * (bi + 1) / 2 > t) --bi;
+                const int bj = t - bi * (bi + 1) / 2;       // bj <= bi
+                const int ri = r0 + bi * FB, rj = r0 + bj * FB;
+                __syncthreads();                            // the previous block's reads of Dm, Pr are done
+                if (tid < FB * FB) {
+                    Dm[tid / FB][tid % FB] = ldcg(&L[(long)(ri + tid / FB) * np + k0 + tid % FB]);
+                    Pr[tid / FB][tid % FB] = ldcg(&L[(long)(rj + tid / FB) * np + k0 + tid % FB]);
+                }
+                __syncthreads();
+                if (tid < FB * FB) {
+                    const int r = tid / FB, c = tid % FB;
+                    if (bi != bj || c <= r) {
+                        double v = 0.0;
+#pragma unroll
+                        for (int q = 0; q < FB; ++q) v += Dm[r][q] * Pr[c][q];
+                        double* e = &L[(long)(ri + r) * np + rj + c];
+                        *e = ldcg(e) - v;                   // last written by another CTA: read through L2
+                    }
+                }
             }
         }
     }
