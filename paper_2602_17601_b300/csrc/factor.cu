@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
     // forward substitution on thread c)
     for (int i = b; i < nb; i += G) {
         if (tid < FB * FB) S[tid / FB][tid % FB] = ldcg(&L[(long)(i * FB + tid / FB) * np + i * FB + tid % FB]);
+        if (tid < FB) rd[tid] = ldcg(&Linv[(long)(i * FB + tid) * np + i * FB + tid]);   // 1 / L_ii[r][r]
         __syncthreads();
         if (tid < FB) {
             const int c = tid;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
                 double v = (r == c) ? 1.0 : 0.0;
 #pragma unroll
                 for (int q = 0; q < r; ++q) v -= S[r][q] * col[q];
-                col[r] = r < c ? 0.0 : v / S[r][r];
+                col[r] = r < c ? 0.0 : v * rd[r];
             }
 #pragma unroll
             for (int r = 0; r < FB; ++r) Linv[(long)(i * FB + r) * np + i * FB + c] = col[r];
