@@ -10,8 +10,13 @@
 //   trailing update A_ij -= L_ik L_jk^T run entry-parallel on all CTAs.  CTA 0
 //   updates the next diagonal block itself and factors it at once, so a block
 //   column costs two grid barriers;
-//   X = L^{-1} by block rows: X_ii = D_i, X_ij = -sum_{m=j}^{i-1} (D_i L_im) X_mj;
-//   P^{-1}[a][b] = sum_{q >= max(a,b)} X[q][a] X[q][b], stored FP32.
+//   D_k = L_kk^{-1} by column-wise forward substitution on an idle warp of the last CTA
+//   while the panel of block column k is solved (CTA 0 does the last block's);
+//   X = L^{-1} by columns, one column per CTA at a time, as a blocked forward
+//   substitution inside the CTA: x_i = D_i (e_i - sum_{m<i} L_im x_m), no grid barrier;
+//   P^{-1}[c][a] = sum_{q >= max(a,c)} X[q][c] X[q][a], row c by the CTA that owns
+//   column c, stored FP32 (the sum is the same product sequence for (c, a) and (a, c),
+//   so both halves agree bit for bit).
 // Items of the thin phases are dealt to CTAs round-robin so that no single SM's FP64
 // pipe carries a phase.  Values written by other CTAs are read through L2 (ld.cg).
 #include "admm.h"
@@ -22,42 +27,50 @@ namespace gmi {
 namespace {
 
 constexpr int FB = 16;            // block size
-constexpr int FT = 256;           // threads per CTA
+constexpr int FT = 256;           // threads per CTA: 16 x 16 in the column solve
+static_assert(FT == FB * FB, "the column solve maps 16 lanes to each row of a block row");
+constexpr size_t kFactorMaxSmem = 160 * 1024;   // the X column in shared memory: np <= 20480
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
-// Factor the FB x FB block S (row-major, lower part valid) in place with all threads of
-// the CTA: S <- L_kk, written to L at block (k, k), and rd[j] = 1 / L_kk[j][j].  A
-// non-positive pivot sets GM_ERR_NUMERIC and continues with 1.
+// Factor the FB x FB block S (row-major, lower part valid) in place with the CTA's 256 threads,
+// thread (r, c) = (tid / 16, tid % 16) holding entry (r, c) in a register: S <- L_kk, written to
+// L at block (k, k), and rd[j] = 1 / L_kk[j][j].  Step j subtracts S_rj S_cj / d_j from every
+// trailing entry (one FMA once the pivot's reciprocal is out); the owners of column j + 1 publish
+// it for the next step, and the owner of entry (j + 1, j + 1) takes the next pivot at once, so a
+// step costs one barrier.  L_rc = S_rc / sqrt(d_c) at the end.  A non-positive pivot sets
+// GM_ERR_NUMERIC and continues with 1.
 __device__ void factor_diag(double (*S)[FB + 1], double* rd, int k, int np, double* L, double* Linv, int* status) {
-    const int tid = threadIdx.x;
-    for (int j = 0; j < FB; ++j) {
-        if (tid == 0) {
-            double d = S[j][j];
-            if (!(d > 0.0)) {
-                dev_fail(status, GM_ERR_NUMERIC);
-                d = 1.0;
-            }
-            const double r = rsqrt(d);
-            S[j][j] = d * r;
-            rd[j] = r;
+    __shared__ double cb[2][FB];      // column j of the working block (not yet scaled), two buffers
+    __shared__ double iv[2];          // 1 / d_j
+    const int tid = threadIdx.x, rr = tid >> 4, cc = tid & 15;
+    const bool low = cc <= rr;
+    double v = low ? S[rr][cc] : 0.0;
+    auto pivot = [&](int j, int buf) {    // on thread (j, j), whose v is d_j
+        if (!(v > 0.0)) {
+            dev_fail(status, GM_ERR_NUMERIC);
+            v = 1.0;
         }
-        __syncthreads();
-        if (tid > j && tid < FB) S[tid][j] *= rd[j];
-        __syncthreads();
-        // rank-1 update of the trailing lower triangle: entry (r, c), j < c <= r
-        const int m = FB - 1 - j;
-        if (tid < m * (m + 1) / 2) {
-            int r = 0, t = tid;
-            while (t > r) {
-                t -= r + 1;
-                ++r;
+        const double r = rsqrt(v);
+        rd[j] = r;
+        iv[buf] = r * r;
+    };
+    if (cc == 0) cb[0][rr] = v;
+    if (tid == 0) pivot(0, 0);
+    __syncthreads();
+    for (int j = 0; j < FB - 1; ++j) {
+        const int buf = j & 1;
+        if (low && cc > j) {
+            v = fma(-(cb[buf][rr] * cb[buf][cc]), iv[buf], v);
+            if (cc == j + 1) {
+                cb[buf ^ 1][rr] = v;
+                if (rr == j + 1) pivot(j + 1, buf ^ 1);
             }
-            const int rr = j + 1 + r, cc = j + 1 + t;
-            S[rr][cc] -= S[rr][j] * S[cc][j];
         }
         __syncthreads();
     }
+    if (low) S[rr][cc] = v * rd[cc];
+    __syncthreads();
     for (int e = tid; e < FB * FB; e += blockDim.x) {
         const int r = e / FB, c = e % FB;
         L[(long)(k * FB + r) * np + k * FB + c] = c <= r ? S[r][c] : 0.0;
@@ -68,9 +81,25 @@ __device__ void factor_diag(double (*S)[FB + 1], double* rd, int k, int np, doub
     __syncthreads();
 }
 
+// Column c of D_k = L_kk^{-1} (S: L_kk, lower part; rd: its pivot reciprocals) by forward
+// substitution, into block (k, k) of Linv.  Entries above the diagonal are stored as exact zeros
+// and the diagonal as rd itself, so the parked reciprocals keep their bits.
+__device__ void diag_inverse_col(const double (*S)[FB + 1], const double* rd, int k, int np, double* Linv, int c) {
+    double col[FB];
+#pragma unroll
+    for (int r = 0; r < FB; ++r) {
+        double v = (r == c) ? 1.0 : 0.0;
+#pragma unroll
+        for (int q = 0; q < r; ++q) v -= S[r][q] * col[q];
+        col[r] = r < c ? 0.0 : v * rd[r];
+    }
+#pragma unroll
+    for (int r = 0; r < FB; ++r) Linv[(long)(k * FB + r) * np + k * FB + c] = col[r];
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* __restrict__ P, double* L,
+__global__ void __launch_bounds__(FT, 1) factor_kernel(int n, int np, const float* __restrict__ P, double* L,
                                                     double* Linv, float* __restrict__ Pinv, int* status,
                                                     const AdmmState* gate, unsigned* bar, long long max_spins) {
     if (gate && (gate->done || !gate->need_factor)) return;     // uniform over the grid
@@ -78,6 +107,8 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
     __shared__ double Dm[FB][FB + 1];
     __shared__ double Pr[FB][FB + 1];             // panel rows of the next diagonal block
     __shared__ double rd[FB];
+    __shared__ double rh[FB];                     // right-hand side of one block row of a column solve
+    extern __shared__ double xs[];                // [np]: the column of X in hand
     const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int nb = np / FB;
@@ -100,6 +131,7 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
         for (int e = tid; e < FB * FB; e += FT) S[e / FB][e % FB] = ldcg(&L[(long)(e / FB) * np + e % FB]);
         __syncthreads();
         factor_diag(S, rd, 0, np, L, Linv, status);
+        if (nb == 1 && tid < FB) diag_inverse_col(S, rd, 0, np, Linv, tid);
     }
     for (int k = 0; k < nb; ++k) {
         sync();                                  // L_kk and D_k final
@@ -124,6 +156,9 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
 #pragma unroll
             for (int c = 0; c < FB; ++c) L[(long)r * np + k0 + c] = x[c];
         }
+        // D_k on the last CTA's last warp (no panel rows there at this size; its writes to the
+        // diagonal of block (k, k) repeat the parked reciprocals bit for bit)
+        if (b == G - 1 && tid >= FT - 32 && tid < FT - 32 + FB) diag_inverse_col(Dm, rd, k, np, Linv, tid - (FT - 32));
         sync();
         if (!ok) return;
         // ---- trailing update of the lower triangle below/right of the block
@@ -139,14 +174,17 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
             if (tid < FB * FB) {
                 const int r = tid / FB, c = tid % FB;
                 if (c <= r) {
-                    double v = S[r][c];
+                    double u[4];
 #pragma unroll
-                    for (int q = 0; q < FB; ++q) v -= Pr[r][q] * Pr[c][q];
-                    S[r][c] = v;
+                    for (int q = 0; q < 4; ++q) u[q] = Pr[r][q] * Pr[c][q];
+#pragma unroll
+                    for (int q = 4; q < FB; ++q) u[q & 3] += Pr[r][q] * Pr[c][q];
+                    S[r][c] -= (u[0] + u[1]) + (u[2] + u[3]);
                 }
             }
             __syncthreads();
             factor_diag(S, rd, k + 1, np, L, Linv, status);
+            if (k + 1 == nb - 1 && tid < FB) diag_inverse_col(S, rd, k + 1, np, Linv, tid);
         } else {
             // blocks (i, j), k < j <= i < nb, of the trailing lower triangle other than the next
             // diagonal block, dealt over CTAs 1..G-1: the two 16 x 16 panel blocks staged in shared
@@ -179,72 +217,68 @@ __global__ void __launch_bounds__(FT) factor_kernel(int n, int np, const float* 
             }
         }
     }
-    // ---- D_i = L_ii^{-1} into the diagonal blocks of Linv (block i on CTA i mod G; column c by
-    // forward substitution on thread c)
-    for (int i = b; i < nb; i += G) {
-        if (tid < FB * FB) S[tid / FB][tid % FB] = ldcg(&L[(long)(i * FB + tid / FB) * np + i * FB + tid % FB]);
-        if (tid < FB) rd[tid] = ldcg(&Linv[(long)(i * FB + tid) * np + i * FB + tid]);   // 1 / L_ii[r][r]
-        __syncthreads();
-        if (tid < FB) {
-            const int c = tid;
-            double col[FB];
+    // ---- X = L^{-1} by columns.  Columns are dealt in a zig-zag (CTA b takes b, then 2G-1-b, ...)
+    // so that the long columns (small c) and the short ones pair up.  Column c: for each block
+    // row i from c's own, rh = e_c - sum_{m<i} L_im x_m (16 lanes per row, reduced in the half
+    // warp), then x_i = D_i rh; X[:, c] is kept in shared memory and written to Linv.
+    const int rr = tid >> 4, tt = tid & 15;
+    for (int p = 0; p * G < n; ++p) {
+        const int c = p * G + ((p & 1) ? G - 1 - b : b);
+        if (c >= n) continue;
+        const int ic = c / FB;
+        for (int i = ic; i < nb; ++i) {
+            const int R = i * FB + rr;
+            double d[FB];                         // row tid of D_i (zero above the diagonal)
+            if (tid < FB) {
 #pragma unroll
-            for (int r = 0; r < FB; ++r) {
-                double v = (r == c) ? 1.0 : 0.0;
-#pragma unroll
-                for (int q = 0; q < r; ++q) v -= S[r][q] * col[q];
-                col[r] = r < c ? 0.0 : v * rd[r];
+                for (int s = 0; s < FB; ++s) d[s] = s <= tid ? ldcg(&Linv[(long)(i * FB + tid) * np + i * FB + s]) : 0.0;
             }
+            double part = 0.0, part1 = 0.0;
+            int q = ic * FB + tt;
+            for (; q + FB < i * FB; q += 2 * FB) {
+                part += ldcg(&L[(long)R * np + q]) * xs[q];
+                part1 += ldcg(&L[(long)R * np + q + FB]) * xs[q + FB];
+            }
+            if (q < i * FB) part += ldcg(&L[(long)R * np + q]) * xs[q];
+            part += part1;
 #pragma unroll
-            for (int r = 0; r < FB; ++r) Linv[(long)(i * FB + r) * np + i * FB + c] = col[r];
+            for (int o = FB / 2; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (tt == 0) rh[rr] = (R == c ? 1.0 : 0.0) - part;
+            __syncthreads();
+            if (tid < FB) {
+                double u[4];
+#pragma unroll
+                for (int s = 0; s < 4; ++s) u[s] = d[s] * rh[s];
+#pragma unroll
+                for (int s = 4; s < FB; ++s) u[s & 3] += d[s] * rh[s];
+                const double v = (u[0] + u[1]) + (u[2] + u[3]);
+                xs[i * FB + tid] = v;
+                Linv[(long)(i * FB + tid) * np + c] = v;
+            }
+            __syncthreads();
         }
+    }
+    sync();
+    if (!ok) return;
+    // ---- P^{-1} row c = X[:, c]' X for each owned column c (X[q][a] = 0 for q < a)
+    for (int p = 0; p * G < n; ++p) {
+        const int c = p * G + ((p & 1) ? G - 1 - b : b);
+        if (c >= n) continue;
+        __syncthreads();                          // the previous row's reads of xs are done
+        for (int q = tid; q < n; q += FT) xs[q] = ldcg(&Linv[(long)q * np + c]);
         __syncthreads();
-    }
-    sync();
-    if (!ok) return;
-    // ---- Lt_im = D_i L_im for m < i, in place in L (one item per block row i and column of L)
-    for (int it = b + G * tid; it < (nb * (nb - 1) / 2) * FB; it += G * FT) {
-        int i = 1, rem = it;
-        while (rem >= i * FB) {
-            rem -= i * FB;
-            ++i;
+        for (int a = tid; a < n; a += FT) {
+            // four partial sums over q from max(a, c): the same sequence for (a, c) and (c, a)
+            double u[4] = {0.0, 0.0, 0.0, 0.0};
+            int q = a > c ? a : c;
+#pragma unroll 2
+            for (; q + 3 < n; q += 4) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) u[s] += ldcg(&Linv[(long)(q + s) * np + a]) * xs[q + s];
+            }
+            for (; q < n; ++q) u[0] += ldcg(&Linv[(long)q * np + a]) * xs[q];
+            Pinv[(long)c * n + a] = (float)((u[0] + u[1]) + (u[2] + u[3]));
         }
-        const int col = rem;                      // column in [0, 16 i)
-        double Lc[FB];
-        for (int s = 0; s < FB; ++s) Lc[s] = ldcg(&L[(long)(i * FB + s) * np + col]);
-        for (int r = 0; r < FB; ++r) {
-            double v = 0.0;
-            for (int s = 0; s <= r; ++s) v += ldcg(&Linv[(long)(i * FB + r) * np + i * FB + s]) * Lc[s];
-            L[(long)(i * FB + r) * np + col] = v;
-        }
-    }
-    sync();
-    if (!ok) return;
-    // ---- X = L^{-1} by block rows (X_ii = D_i already in Linv)
-    for (int i = 1; i < nb; ++i) {
-        const int ncol = i * FB;                  // columns left of the diagonal block
-        for (int t = b + G * tid; t < FB * ncol; t += G * FT) {
-            const int r = t / ncol, c = t % ncol;
-            const int j0 = (c / FB) * FB;         // first column of block j
-            double v = 0.0;
-            for (int q = j0; q < i * FB; ++q)
-                v -= ldcg(&L[(long)(i * FB + r) * np + q]) * ldcg(&Linv[(long)q * np + c]);
-            Linv[(long)(i * FB + r) * np + c] = v;
-        }
-        sync();
-        if (!ok) return;
-    }
-    // ---- P^{-1} = X' X (lower triangle computed, both halves stored)
-    const long ntri = (long)n * (n + 1) / 2;
-    for (long t = b + (long)G * tid; t < ntri; t += (long)G * FT) {
-        int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((long)(a + 1) * (a + 2) / 2 <= t) ++a;
-        while ((long)a * (a + 1) / 2 > t) --a;
-        const int c = (int)(t - (long)a * (a + 1) / 2);   // c <= a
-        double v = 0.0;
-        for (int q = a; q < np; ++q) v += ldcg(&Linv[(long)q * np + a]) * ldcg(&Linv[(long)q * np + c]);
-        Pinv[(long)a * n + c] = (float)v;
-        Pinv[(long)c * n + a] = (float)v;
     }
 }
 
@@ -264,12 +298,16 @@ int factor_grid() {
 gm_status factor_pinv(int n, const float* P, double* L, double* Linv, float* Pinv, int* status,
                       const AdmmState* gate, unsigned* bar, long long max_spins, int grid, cudaStream_t st) {
     const int np = factor_pad(n);
+    const size_t smem = (size_t)np * sizeof(double);          // one column of X
+    if (smem > kFactorMaxSmem) return GM_ERR_INVALID_ARG;
+    if (smem > 48 * 1024)
+        GM_CUDA_TRY(cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GM_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
     cudaLaunchConfig_t cfg{};
     // at least 2 CTAs: the trailing update runs on the CTAs other than CTA 0
     cfg.gridDim = dim3(grid > 0 ? std::max(2, std::min(grid, factor_grid())) : factor_grid());
     cfg.blockDim = dim3(FT);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
