@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(FT, 1) factor_kernel(int n, int np, const floa
     __shared__ double S[FB][FB + 1];
     __shared__ double Dm[FB][FB + 1];
     __shared__ double Pr[FB][FB + 1];             // panel rows of the next diagonal block
+    __shared__ double Mm[FB][FB + 1];             // L_kk[q][j] / L_kk[j][j]
     __shared__ double rd[FB];
     __shared__ double rh[FB];                     // right-hand side of one block row of a column solve
     extern __shared__ double xs[];                // [np]: the column of X in hand
@@ -138,23 +139,33 @@ __global__ void __launch_bounds__(FT, 1) factor_kernel(int n, int np, const floa
         if (!ok) return;
         if (k == nb - 1) break;
         const int k0 = k * FB, r0 = k0 + FB;
-        // ---- panel: L_ik = A_ik L_kk^{-T}, row by row (forward substitution, one thread per row)
-        if (tid < FB * FB) Dm[tid / FB][tid % FB] = ldcg(&L[(long)(k0 + tid / FB) * np + k0 + tid % FB]);
+        // ---- panel: L_ik = A_ik L_kk^{-T}, a row per 16-lane group with lane c holding z_c.  With
+        // M[q][j] = L_kk[q][j] / L_kk[j][j], once z_j is final it is broadcast in the group and every
+        // later lane takes z_q -= z_j M[q][j] (one FP64 instruction per step for the whole warp:
+        // FP64 issue, not lanes, is what a row costs here); x_c = z_c / L_kk[c][c] at the end.
+        if (tid < FB * FB) {
+            const int q = tid / FB, j = tid % FB;
+            const double v = ldcg(&L[(long)(k0 + q) * np + k0 + j]);
+            Dm[q][j] = v;
+            Mm[q][j] = v * ldcg(&Linv[(long)(k0 + j) * np + k0 + j]);
+        }
         if (tid < FB) rd[tid] = ldcg(&Linv[(long)(k0 + tid) * np + k0 + tid]);
         __syncthreads();
-        for (int r = r0 + b + G * tid; r < np; r += G * FT) {
-            double x[FB];
+        {
+            const int g = tid >> 4, c = tid & 15;
+            for (int base = r0 + b; base < np; base += G * (FT / FB)) {
+                const int r = base + G * g;
+                const bool valid = r < np;
+                if (__any_sync(0xffffffffu, valid)) {           // uniform over the warp
+                    double z = valid ? ldcg(&L[(long)r * np + k0 + c]) : 0.0;
 #pragma unroll
-            for (int c = 0; c < FB; ++c) x[c] = ldcg(&L[(long)r * np + k0 + c]);
-            // right-looking: once x_c is final it updates all later entries (independent FMAs)
-#pragma unroll
-            for (int c = 0; c < FB; ++c) {
-                x[c] *= rd[c];
-#pragma unroll
-                for (int q = c + 1; q < FB; ++q) x[q] -= x[c] * Dm[q][c];
+                    for (int j = 0; j < FB - 1; ++j) {
+                        const double zj = __shfl_sync(0xffffffffu, z, j, FB);
+                        if (c > j) z = fma(-zj, Mm[c][j], z);
+                    }
+                    if (valid) L[(long)r * np + k0 + c] = z * rd[c];
+                }
             }
-#pragma unroll
-            for (int c = 0; c < FB; ++c) L[(long)r * np + k0 + c] = x[c];
         }
         // D_k on the last CTA's last warp (no panel rows there at this size; its writes to the
         // diagonal of block (k, k) repeat the parked reciprocals bit for bit)
@@ -228,11 +239,9 @@ __global__ void __launch_bounds__(FT, 1) factor_kernel(int n, int np, const floa
         const int ic = c / FB;
         for (int i = ic; i < nb; ++i) {
             const int R = i * FB + rr;
-            double d[FB];                         // row tid of D_i (zero above the diagonal)
-            if (tid < FB) {
-#pragma unroll
-                for (int s = 0; s < FB; ++s) d[s] = s <= tid ? ldcg(&Linv[(long)(i * FB + tid) * np + i * FB + s]) : 0.0;
-            }
+            // D_i[rr][tt] (zero above the diagonal): x_i = D_i rh is applied by all 256 threads, a
+            // product each and a sum over the 16 lanes of a row, not by 16 threads in one warp
+            const double dv = tt <= rr ? ldcg(&Linv[(long)(i * FB + rr) * np + i * FB + tt]) : 0.0;
             double part = 0.0, part1 = 0.0;
             int q = ic * FB + tt;
             for (; q + FB < i * FB; q += 2 * FB) {
@@ -245,15 +254,12 @@ __global__ void __launch_bounds__(FT, 1) factor_kernel(int n, int np, const floa
             for (int o = FB / 2; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             if (tt == 0) rh[rr] = (R == c ? 1.0 : 0.0) - part;
             __syncthreads();
-            if (tid < FB) {
-                double u[4];
+            double v = dv * rh[tt];
 #pragma unroll
-                for (int s = 0; s < 4; ++s) u[s] = d[s] * rh[s];
-#pragma unroll
-                for (int s = 4; s < FB; ++s) u[s & 3] += d[s] * rh[s];
-                const double v = (u[0] + u[1]) + (u[2] + u[3]);
-                xs[i * FB + tid] = v;
-                Linv[(long)(i * FB + tid) * np + c] = v;
+            for (int o = FB / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (tt == 0) {
+                xs[R] = v;
+                Linv[(long)R * np + c] = v;
             }
             __syncthreads();
         }
