@@ -13,7 +13,10 @@
 // change by more than 5x ends the launch with the iterate kept in a device
 // state, the next round re-forms and re-factors P(rho_new) in FP64, and the
 // next ADMM launch resumes.  A fixed number of rounds is issued; device flags
-// make the unneeded ones return at once, so the host never waits.
+// make the unneeded ones return at once, so the host never waits.  When the
+// step is captured into a graph, rounds after the first sit in nested
+// conditional (IF) nodes whose condition a one-thread kernel sets from the
+// device state, so the rounds after convergence are not launched at all.
 //
 // One launch is a persistent cooperative kernel.  Each CTA owns a contiguous
 // range of C~ rows, split by cost (16 + row length per row), streams it as
@@ -125,6 +128,11 @@ __device__ __forceinline__ Tile next_tile(long r, long r1, int Mnc, int nu, int 
         t.live = true;
     }
     return t;
+}
+
+// Condition of the IF node around an ADMM round: run it while the solve is not done.
+__global__ void admm_round_cond_kernel(const AdmmState* S, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, S->done ? 0u : 1u);
 }
 
 template <bool PSMEM>
@@ -781,19 +789,20 @@ gm_status admm_solve(const AdmmPlan& p) {
     const bool psmem = admm2_psmem(n);
     const size_t smem = admm2_smem_bytes(n);
     GM_CUDA_TRY(cudaFuncSetAttribute(admm2_kernel_ptr(n), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    for (int r = 0; r < p.rounds; ++r) {
-        admm_form_p_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, p.H, p.Gram, p.S, p.P);
+    // one round on stream rs: re-form and re-factor P when due, then an ADMM launch
+    auto round = [&](int r, cudaStream_t rs) -> gm_status {
+        admm_form_p_kernel<<<cdiv((long)n * n, 256), 256, 0, rs>>>(n, p.H, p.Gram, p.S, p.P);
         GM_LAUNCH_CHECK();
-        GM_TRY(factor_pinv(n, p.P, p.L, p.Linv, p.Pinv, p.status, p.S, p.bar, p.max_spins, p.factor_grid, st));
-        if (r == 0 && p.ev_mid) GM_CUDA_TRY(cudaEventRecord(p.ev_mid, st));
-        GM_CUDA_TRY(cudaMemsetAsync(p.bar, 0, sizeof(unsigned) * 4, st));
-        GM_CUDA_TRY(cudaMemsetAsync(p.acc, 0, sizeof(float) * admm_acc_stride(n), st));
+        GM_TRY(factor_pinv(n, p.P, p.L, p.Linv, p.Pinv, p.status, p.S, p.bar, p.max_spins, p.factor_grid, rs));
+        if (r == 0 && p.ev_mid) GM_CUDA_TRY(cudaEventRecord(p.ev_mid, rs));
+        GM_CUDA_TRY(cudaMemsetAsync(p.bar, 0, sizeof(unsigned) * 4, rs));
+        GM_CUDA_TRY(cudaMemsetAsync(p.acc, 0, sizeof(float) * admm_acc_stride(n), rs));
         a.last_round = (r == p.rounds - 1) ? 1 : 0;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(p.grid);
         cfg.blockDim = dim3(ADMM_T);
         cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
+        cfg.stream = rs;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
         attr[0].val.cooperative = 1;
@@ -805,7 +814,56 @@ gm_status admm_solve(const AdmmPlan& p) {
             GM_CUDA_TRY(cudaLaunchKernelEx(&cfg, admm2_kernel<false>, a));
         }
         GM_LAUNCH_CHECK();
+        return GM_OK;
+    };
+    bool cond = false;
+    if (p.body_st && kAdmmCondRounds) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        GM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        cond = cs == cudaStreamCaptureStatusActive;
     }
+    // Rounds after the first are nested IF nodes: the body of round r's node holds round r, the
+    // condition kernel of round r + 1 and round r + 1's node, so the first false condition skips
+    // every later round.  Each body is captured on body_st once the enclosing one is complete.
+    cudaStream_t cap = st;                        // the stream whose capture takes the next IF node
+    auto add_if = [&](int r) -> gm_status {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edges = nullptr;
+        size_t nd = 0;
+        GM_CUDA_TRY(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        GM_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        admm_round_cond_kernel<<<1, 1, 0, cap>>>(p.S, h);
+        GM_LAUNCH_CHECK();
+        GM_CUDA_TRY(cudaStreamGetCaptureInfo(cap, &cs, nullptr, &g, &deps, &edges, &nd));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        GM_CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, nd, &np));
+        GM_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        if (cap != st) {                          // the enclosing body is complete
+            cudaGraph_t bg = nullptr;
+            cap = st;
+            GM_CUDA_TRY(cudaStreamEndCapture(p.body_st, &bg));
+        }
+        GM_CUDA_TRY(cudaStreamBeginCaptureToGraph(p.body_st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed));
+        cap = p.body_st;
+        return round(r, p.body_st);
+    };
+    gm_status rs = GM_OK;
+    for (int r = 0; r < p.rounds && rs == GM_OK; ++r) rs = (!cond || r == 0) ? round(r, st) : add_if(r);
+    if (cap != st) {                              // close the innermost body, also after an error
+        cudaGraph_t bg = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(p.body_st, &bg);
+        if (rs == GM_OK && ce != cudaSuccess) GM_CUDA_TRY(ce);
+    }
+    GM_TRY(rs);
     return GM_OK;
 }
 

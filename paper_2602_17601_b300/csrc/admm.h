@@ -16,6 +16,7 @@ constexpr float kInfeasEps = 1e-4f;     // relative tolerance of the infeasibili
 constexpr int kStallEvery = 25;         // warm-started solves: iterations between stall tests
 constexpr float kStallFactor = 0.5f;    // a stall: max(r_p, r_d) not below this fraction of its
                                         // value kStallEvery iterations earlier
+constexpr bool kAdmmCondRounds = true;     // IF nodes around rounds after the first under capture
 constexpr int kWarmRounds = 2;          // launches a warm-started solve may use (one rho update)
 constexpr int kMaxRhoUpdates = 5;       // rho changes per start (warm or cold)
 constexpr float kRedundantMargin = 1e-4f; // relative margin of the redundant-row test (qp.cu)
@@ -89,6 +90,10 @@ struct AdmmPlan {
     long long max_spins;
     cudaStream_t st;
     cudaEvent_t ev_mid;    // recorded after the first factorisation (nullable)
+    // while st is being captured into a graph: rounds after the first go into conditional (IF)
+    // nodes whose bodies are captured on this stream, so rounds after convergence are skipped
+    // (nullable: every round is launched)
+    cudaStream_t body_st;
 };
 
 gm_status admm_solve(const AdmmPlan& p);

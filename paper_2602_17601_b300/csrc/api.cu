@@ -1108,11 +1108,16 @@ static gm_status capture_step(gm_ctx* c, const float* x_meas, const gm_cost* cos
                               float* u0, gm_stats* stats, cudaGraph_t* out, int part = 0) {
     *out = nullptr;
     if (!c->cap_stream) GM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (!c->cond_stream) GM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cond_stream, cudaStreamNonBlocking));
     GM_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
     gm_status body = GM_OK;
+    // the whole-step graph skips ADMM rounds after convergence through IF nodes; the batch's
+    // per-lane pieces (parts 1 and 2) become child graphs and launch every round
+    c->cond_capture = part == 0;
     if (part == 0) body = rti_body(c, x_meas, cost, cons, U, u0, stats, c->cap_stream, false);
     else if (part == 1) body = rti_pre(c, x_meas, cost, cons, c->cap_stream, nullptr);
     else body = rti_post(c, cons, U, u0, stats, c->cap_stream, nullptr);
+    c->cond_capture = false;
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
     if (body != GM_OK || ce != cudaSuccess || !g) {

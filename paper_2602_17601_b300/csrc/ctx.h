@@ -202,6 +202,8 @@ struct gm_ctx {
     std::vector<uintptr_t> graph_key;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cond_stream = nullptr;   // bodies of the ADMM rounds' IF nodes while a step is captured
+    bool cond_capture = false;            // the capture in progress may use IF nodes (whole-step capture)
     // the edge encoder of a rollout stage runs on this stream beside the node encoder
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -235,6 +237,7 @@ struct gm_ctx {
             for (auto ev : e) cudaEventDestroy(ev);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (cond_stream) cudaStreamDestroy(cond_stream);
         if (side_stream) cudaStreamDestroy(side_stream);
         if (roll_stream) cudaStreamDestroy(roll_stream);
         if (tan_stream) cudaStreamDestroy(tan_stream);

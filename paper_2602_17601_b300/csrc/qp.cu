@@ -318,6 +318,7 @@ gm_status qp_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, c
     p.max_spins = c->s.timeout_spins > 0 ? c->s.timeout_spins : (1LL << 26);
     p.st = st;
     p.ev_mid = ev_mid;
+    p.body_st = c->cond_capture ? c->cond_stream : nullptr;
     p.gram_tc = c->gram_tc;
     return solve_with(p, c->num_sms, gram_split(n, c->num_sms, kGramSplitCap, c->gram_tc), c->d_gram_part, scale,
                       c->d_kkt);
