@@ -126,8 +126,7 @@ gm_status barrier_fold(gm_ctx* c, const float* Ct, const float* dt, const float*
     const int nsplit = gram_split(n, sms, kGramSplitCap, c->gram_tc);
     GramRows R{Ct, Mnc, c->nu, c->N, w, 1, 0};
     GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status, c->gram_tc));
-    gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, c->d_gram_part, nullptr, 0.f, c->d_G);
-    GM_LAUNCH_CHECK();
+    GM_TRY(launch_gram_reduce(n, nsplit, c->d_gram_part, nullptr, 0.f, c->d_G, st));
     const int g_T = (int)std::max(1L, std::min((long)cdiv(rows, (long)nw), 4L * sms));
     barrier_rowT_kernel<<<g_T, nw * 32, (size_t)nw * n * sizeof(double), st>>>(rows, c->nu, Mnc, n, Ct, v, acc);
     GM_LAUNCH_CHECK();

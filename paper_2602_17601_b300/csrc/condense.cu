@@ -218,39 +218,60 @@ gm_status launch_gram(const GramRows& R, int n, int nsplit, float* part, cudaStr
     return GM_OK;
 }
 
-__global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
-                                   const float* __restrict__ diag_add, float diag_scale,
-                                   float* __restrict__ G) {
-    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)n * n) return;
-    int c1 = (int)(t / n), c2 = (int)(t % n);
-    int a = c1 >= c2 ? c1 : c2, b = c1 >= c2 ? c2 : c1;     // lower-triangle element (a, b)
+// G = the sum of the nsplit partial Grams (tile layout [nsplit][T][T][32 x 32], T = ceil(n/32)), plus
+// diag_scale * diag_add on the diagonal.  Only lower-triangle elements are read and each is written
+// to both halves, so G is exactly symmetric.  Block (lower tile (ti, tj), row r of the tile): lane l
+// takes element (32 ti + r, 32 tj + l); the 8 warps take every 8th share, so each warp load is one
+// 128-byte line and about 19 loads per thread are in flight in a few round trips; the 8 partial sums
+// meet in shared memory in a fixed order.
+__global__ void __launch_bounds__(GR_WARPS * 32) gram_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
+                                                                    const float* __restrict__ diag_add,
+                                                                    float diag_scale, float* __restrict__ G) {
+    __shared__ float red[GR_WARPS][32];
     const int T = (n + 31) / 32;
-    int ti = a / 32, tj = b / 32;
-    // four independent partial sums, so that the loads of consecutive shares overlap
-    const long base = ((long)ti * T + tj) * 1024 + (a % 32) * 32 + (b % 32), stride = (long)T * T * 1024;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int sp = 0;
-    for (; sp + 4 <= nsplit; sp += 4) {
+    const int tile = blockIdx.x / 32, r = blockIdx.x % 32;
+    int ti = (int)((sqrtf(8.f * (float)tile + 1.f) - 1.f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    while (ti * (ti + 1) / 2 > tile) --ti;
+    const int tj = tile - ti * (ti + 1) / 2;                 // tj <= ti
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long base = ((long)ti * T + tj) * 1024 + r * 32 + lane, stride = (long)T * T * 1024;
+    float s0 = 0.f, s1 = 0.f;
+    int sp = warp;
+#pragma unroll 4
+    for (; sp + GR_WARPS < nsplit; sp += 2 * GR_WARPS) {
         s0 += part[base + (long)sp * stride];
-        s1 += part[base + (long)(sp + 1) * stride];
-        s2 += part[base + (long)(sp + 2) * stride];
-        s3 += part[base + (long)(sp + 3) * stride];
+        s1 += part[base + (long)(sp + GR_WARPS) * stride];
     }
-    for (; sp < nsplit; ++sp) s0 += part[base + (long)sp * stride];
-    float s = (s0 + s1) + (s2 + s3);
-    if (c1 == c2 && diag_add) s += diag_scale * diag_add[c1];
-    G[t] = s;
+    if (sp < nsplit) s0 += part[base + (long)sp * stride];
+    red[warp][lane] = s0 + s1;
+    __syncthreads();
+    if (warp == 0) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < GR_WARPS; ++w) s += red[w][lane];
+        const int a = 32 * ti + r, b = 32 * tj + lane;
+        if (a < n && b <= a) {
+            if (a == b && diag_add) s += diag_scale * diag_add[a];
+            G[(long)a * n + b] = s;
+            G[(long)b * n + a] = s;
+        }
+    }
+}
+
+gm_status launch_gram_reduce(int n, int nsplit, const float* part, const float* diag_add, float diag_scale, float* G,
+                             cudaStream_t st) {
+    const int T = (n + 31) / 32;
+    gram_reduce_kernel<<<T * (T + 1) / 2 * 32, GR_WARPS * 32, 0, st>>>(n, nsplit, part, diag_add, diag_scale, G);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
 }
 
 gm_status gram(gm_ctx* c, const GramRows& R, int nsplit, const float* diag_add, float diag_scale,
                float* G, cudaStream_t st) {
     const int n = c->nU;
     GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status, c->gram_tc));
-    gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, c->d_gram_part, diag_add,
-                                                              diag_scale, G);
-    GM_LAUNCH_CHECK();
-    return GM_OK;
+    return launch_gram_reduce(n, nsplit, c->d_gram_part, diag_add, diag_scale, G, st);
 }
 
 // g = -Rbar u_ref + sum_k sum_{i,a} Gu_k[i,a]^T Q^i_k[a] (Gx_k[i,a] - x_ref_k[i,a]),

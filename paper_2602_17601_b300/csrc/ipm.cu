@@ -528,9 +528,7 @@ gm_status ipm_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, 
             if (rows > 0) {
                 GramRows R{Ct, Mnc, c->nu, c->N, reinterpret_cast<const float*>(a.rw + RA_W * a.R), 1, 0};
                 GM_TRY(launch_gram(R, n, nsplit, c->d_gram_part, st, c->d_status, c->gram_tc));
-                gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, c->d_gram_part, nullptr, 0.f,
-                                                                          c->d_G);
-                GM_LAUNCH_CHECK();
+                GM_TRY(launch_gram_reduce(n, nsplit, c->d_gram_part, nullptr, 0.f, c->d_G, st));
             }
             ipm_phi_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(a);
             GM_LAUNCH_CHECK();

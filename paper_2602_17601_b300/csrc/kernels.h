@@ -77,9 +77,11 @@ gm_status barrier_fold(gm_ctx* c, const float* Ct, const float* dt, const float*
 // ipm.cu: interior-point solve of the condensed QP
 gm_status ipm_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, const float* dt, const float* u_lo,
                     const float* u_hi, int max_iter, float* U, float* y, gm_stats* stats, cudaStream_t st);
-__global__ void gram_reduce_kernel(int n, int nsplit, const float* __restrict__ part,
-                                   const float* __restrict__ diag_add, float diag_scale,
-                                   float* __restrict__ G);
+// G = the sum of nsplit partial Grams (launch_gram's tile layout) + diag_scale * diag_add on the
+// diagonal (diag_add nullable); G is written in full and exactly symmetric.
+constexpr int GR_WARPS = 8;
+gm_status launch_gram_reduce(int n, int nsplit, const float* part, const float* diag_add, float diag_scale, float* G,
+                             cudaStream_t st);
 gm_status sphere_halfspaces(gm_ctx* c, const float* x_hat, const float* spheres, int S, float* Cx,
                             float* dx, cudaStream_t st);
 gm_status condense(gm_ctx* c, const float* x_hat, const float* A, const float* B, const float* cvec,

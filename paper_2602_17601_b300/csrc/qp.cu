@@ -271,9 +271,7 @@ static gm_status solve_with(AdmmPlan& p, int sms, int nsplit, float* gram_part, 
         GM_CUDA_TRY(cudaMemsetAsync(p.y + p.n, 0, sizeof(float) * rows, st));
         GramRows R{p.Ct, p.Mnc, p.nu, p.N, p.rs, 1, 1};
         GM_TRY(launch_gram(R, n, nsplit, gram_part, st, p.status, p.gram_tc));
-        gram_reduce_kernel<<<cdiv((long)n * n, 256), 256, 0, st>>>(n, nsplit, gram_part, nullptr, 0.f,
-                                                                  const_cast<float*>(p.Gram));
-        GM_LAUNCH_CHECK();
+        GM_TRY(launch_gram_reduce(n, nsplit, gram_part, nullptr, 0.f, const_cast<float*>(p.Gram), st));
     }
     GM_TRY(admm_solve(p));
     GM_CUDA_TRY(cudaMemsetAsync(kkt, 0, sizeof(double) * (n + 4), st));
