@@ -124,10 +124,12 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
     const int NW = blockDim.x >> 5;
     extern __shared__ double dsm[];          // [NW][n]
     double part[KKT_MAXC], ud[KKT_MAXC];
+    float uf[KKT_MAXC];                      // U as given, for the FP32 test (no conversions per row)
 #pragma unroll
     for (int m = 0; m < KKT_MAXC; ++m) {
         part[m] = 0.0;
-        ud[m] = lane + 32 * m < n ? (double)U[lane + 32 * m] : 0.0;   // converted once
+        uf[m] = lane + 32 * m < n ? U[lane + 32 * m] : 0.f;
+        ud[m] = (double)uf[m];               // converted once
     }
     double prim = 0.0, dual = 0.0, comp = 0.0;
     for (long r = (long)blockIdx.x * NW + warp; r < rows; r += (long)gridDim.x * NW) {
@@ -136,15 +138,15 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
         const int L = (ks + 1) * nu;
         const int nm = (L + 31) >> 5;              // 32-column blocks the row reaches (warp-uniform)
         const long off = (long)Mnc * nu * ((long)ks * (ks + 1) / 2) + (long)wi * L;
-        const double yr = y[n + r];
-        if (yr == 0.0) {                           // warp-uniform: the FP32 test of a row without multiplier
+        const float yr32 = y[n + r];
+        if (yr32 == 0.f) {                         // warp-uniform: the FP32 test of a row without multiplier
             float d32 = 0.f, a32 = 0.f;
 #pragma unroll
             for (int m = 0; m < KKT_MAXC; ++m) {
                 if (m >= nm) break;
                 const int c = lane + 32 * m;
                 if (c < L) {
-                    const float p = Ct[off + c] * (float)ud[m];
+                    const float p = Ct[off + c] * uf[m];
                     d32 += p;
                     a32 += fabsf(p);
                 }
@@ -153,9 +155,12 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
                 d32 += __shfl_xor_sync(0xffffffffu, d32, o);
                 a32 += __shfl_xor_sync(0xffffffffu, a32, o);
             }
-            // (1e-30: an absolute allowance for products below FP32's normal range)
-            if ((double)d32 + 64.0 * 5.9604644775390625e-08 * (double)a32 + 1e-30 < (double)dt[r]) continue;
+            // d32 + 2^-18 a32 + 1e-30 rounded upwards, so the bound is never below its exact value and
+            // the test stays rigorous in FP32 without an FP64 instruction on the path (1e-30: an
+            // absolute allowance for products below FP32's normal range)
+            if (__fadd_ru(__fmaf_ru(0x1p-18f, a32, d32), 1e-30f) < dt[r]) continue;
         }
+        const double yr = (double)yr32;
         double dot = 0.0;
         if (yr != 0.0) {                           // warp-uniform: rows with a multiplier add C~_r' y_r
 #pragma unroll
