@@ -575,9 +575,7 @@ gm_status ipm_solve(gm_ctx* c, const float* H, const float* g, const float* Ct, 
                           (threads / 32) * n * sizeof(double), st>>>(n, c->nu, Mnc, rows, Ct, dt, U, yk, c->d_kkt);
         GM_LAUNCH_CHECK();
     }
-    kkt_final_kernel<<<1, 256, 0, st>>>(n, H, g, u_lo, u_hi, U, yk, c->d_kkt, c->d_status, stats, nullptr);
-    GM_LAUNCH_CHECK();
-    return GM_OK;
+    return launch_kkt_final(n, H, g, u_lo, u_hi, U, yk, c->d_kkt, c->d_status, stats, nullptr, st);
 }
 
 }  // namespace gmi

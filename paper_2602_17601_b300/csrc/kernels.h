@@ -66,11 +66,11 @@ __global__ void row_norm_kernel(long rows, int nu, int Mnc, const float* __restr
 __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* __restrict__ Ct,
                                 const float* __restrict__ dt, const float* __restrict__ U,
                                 const float* __restrict__ y, double* kkt);
-__global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float* __restrict__ g,
-                                 const float* __restrict__ lo, const float* __restrict__ hi,
-                                 const float* __restrict__ U, const float* __restrict__ y,
-                                 const double* __restrict__ kkt, const int* status, gm_stats* stats,
-                                 AdmmState* S);   // S nullable: records the final status, GM_STALLED
+// The FP64 stationarity rows (one warp per row, in place of kkt[0..n)), then the certificate's maxima
+// and the final status into stats (S nullable: records the final status, GM_STALLED).
+gm_status launch_kkt_final(int n, const float* H, const float* g, const float* lo, const float* hi, const float* U,
+                           const float* y, double* kkt, const int* status, gm_stats* stats, AdmmState* S,
+                           cudaStream_t st);
 // barrier.cu: relaxed log-barrier obstacle rows folded into H and g
 gm_status barrier_fold(gm_ctx* c, const float* Ct, const float* dt, const float* U_hat, float mu, float delta,
                        float* H, float* g, cudaStream_t st);

@@ -204,6 +204,24 @@ __global__ void kkt_rows_kernel(int n, int nu, int Mnc, long rows, const float* 
     }
 }
 
+// Stationarity rows in FP64, in place of kkt[c]: s_c = sum_j H_cj U_j + g_c + y_c + (C~'y)_c, one
+// warp per c with the lanes along j.  The FP64 products run on the grid's SMs rather than in one
+// block (160 dependent FMAs and 320 conversions per thread there took tens of microseconds).
+__global__ void kkt_stat_kernel(int n, const float* __restrict__ H, const float* __restrict__ g,
+                                const float* __restrict__ U, const float* __restrict__ y, double* kkt) {
+    const int c = blockIdx.x, lane = threadIdx.x;
+    double s0 = 0.0, s1 = 0.0;
+    int j = lane;
+    for (; j + 32 < n; j += 64) {
+        s0 += (double)H[(long)c * n + j] * (double)U[j];
+        s1 += (double)H[(long)c * n + j + 32] * (double)U[j + 32];
+    }
+    if (j < n) s0 += (double)H[(long)c * n + j] * (double)U[j];
+    double s = s0 + s1;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) kkt[c] = s + ((double)g[c] + (double)y[c] + kkt[c]);
+}
+
 __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float* __restrict__ g,
                                  const float* __restrict__ lo, const float* __restrict__ hi,
                                  const float* __restrict__ U, const float* __restrict__ y,
@@ -211,10 +229,10 @@ __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float
                                  AdmmState* S) {
     __shared__ double red[4][32];
     double stat = 0.0, prim = 0.0, comp = 0.0;
+    (void)H;
+    (void)g;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        double s = (double)g[c] + (double)y[c] + kkt[c];
-        for (int j = 0; j < n; ++j) s += (double)H[(long)c * n + j] * (double)U[j];
-        stat = nmax(stat, fabs(s));
+        stat = nmax(stat, fabs(kkt[c]));         // the stationarity row (kkt_stat_kernel)
         const double u = U[c], l = lo[c], h = hi[c], yc = y[c];
         prim = nmax(prim, nmax(u - h, l - u));
         comp = nmax(comp, nmax(yc, 0.0) * fabs(h - u));
@@ -258,6 +276,16 @@ __global__ void kkt_final_kernel(int n, const float* __restrict__ H, const float
 }
 
 // Row scales, Gram, ADMM rounds and KKT check on the given buffers.
+gm_status launch_kkt_final(int n, const float* H, const float* g, const float* lo, const float* hi, const float* U,
+                            const float* y, double* kkt, const int* status, gm_stats* stats, AdmmState* S,
+                            cudaStream_t st) {
+    kkt_stat_kernel<<<n, 32, 0, st>>>(n, H, g, U, y, kkt);
+    GM_LAUNCH_CHECK();
+    kkt_final_kernel<<<1, 256, 0, st>>>(n, H, g, lo, hi, U, y, kkt, status, stats, S);
+    GM_LAUNCH_CHECK();
+    return GM_OK;
+}
+
 static gm_status solve_with(AdmmPlan& p, int sms, int nsplit, float* gram_part, bool scale, double* kkt) {
     const int n = p.n;
     const long rows = p.rows;
@@ -286,9 +314,7 @@ static gm_status solve_with(AdmmPlan& p, int sms, int nsplit, float* gram_part, 
                           st>>>(n, p.nu, p.Mnc, rows, p.Ct, p.dt, p.U, p.y, kkt);
         GM_LAUNCH_CHECK();
     }
-    kkt_final_kernel<<<1, 256, 0, st>>>(n, p.H, p.g, p.lo, p.hi, p.U, p.y, kkt, p.status, p.stats, p.S);
-    GM_LAUNCH_CHECK();
-    return GM_OK;
+    return launch_kkt_final(n, p.H, p.g, p.lo, p.hi, p.U, p.y, kkt, p.status, p.stats, p.S, st);
 }
 
 size_t admm_smem_bytes(const gm_ctx* c) { return admm2_smem_bytes(c->nU); }
