@@ -457,6 +457,10 @@ unsigned long long gm_launch_count(void);
  * The graph bakes in every pointer and scalar of the call (x_meas, cost,
  * constraints, U, u0, stats, settings); a call that changes any of them is
  * captured anew.  Phase timing (gm_ctx_set_timing) runs the steps eagerly.
+ * In the graph, the ADMM rounds after the first (rho adaptation, warm-start
+ * restart) sit in nested conditional nodes that the device enables only while
+ * the solve is not done, so a step that converges early launches none of
+ * them; the eager step issues every round (the unneeded ones return at once).
  * If the capture fails the context falls back to eager steps and
  * gm_ctx_graph_state reports 0.  gm_ctx_graph_state: 1 when the last step
  * replayed a graph, 0 otherwise; captures counts the captures so far. */
